@@ -1,0 +1,241 @@
+"""Seeded synthetic workloads for the Intermediate State Method (ISM) hot path.
+
+Every generator draws its random numbers from ``numpy.random.default_rng(seed)`` in a fixed,
+documented order and returns plain arrays: dense real-symmetric ``H0`` and ``H1`` (the control
+Hamiltonian is H(u) = H0 + u*H1, Sec. 2, Eq. (dir)), the initial state, the target (a state for the
+overlap objective of Sec. 2, or an observable for the variant the paper calls straightforward),
+the time grid and the initial control.
+
+Both the CUDA path and the FP64 oracle consume exactly these arrays.  This module computes
+nothing of the method itself (no propagation, no intermediate states, no gradients): it only
+builds the physical model matrices and draws random numbers.
+
+Models
+------
+* ``spin_all_to_all``  : q spin-1/2 with H0 = sum_{i<j} J_ij Z_i Z_j, H1 = sum_i X_i.
+  Basis index s, spin i <-> bit i of s, Z_i|s> = (1 - 2 bit_i(s))|s>.
+* ``spin_chain``       : same with nearest-neighbour open-chain couplings only.
+* ``rotor``            : rigid rotor in the |j, m=0> basis, j = 0..jmax, H0 = diag(j(j+1)) (units
+  of B), H1 = -cos(theta) with <j|cos theta|j+1> = (j+1)/sqrt((2j+1)(2j+3)) (textbook m=0 matrix
+  element); the orientation objective is <psi(T)|cos theta|psi(T)> (Sec. 4, molecular orientation).
+* ``random_dense``     : random real-symmetric H0, H1 for generic parity tests.
+"""
+from __future__ import annotations
+
+from dataclasses import dataclass, field
+from typing import Optional
+
+import numpy as np
+
+__all__ = [
+    "Workload",
+    "spin_all_to_all",
+    "spin_chain",
+    "rotor",
+    "random_dense",
+    "rabi",
+    "config",
+    "CONFIG_NAMES",
+]
+
+
+@dataclass
+class Workload:
+    """One ISM control problem (Sec. 2) plus the run settings used with it."""
+
+    name: str
+    kind: str                    # structure hint for the CUDA path: "bitflip" | "tridiag" | "dense"
+    H0: np.ndarray               # (d, d) float64, real symmetric
+    H1: np.ndarray               # (d, d) float64, real symmetric
+    psi_i: np.ndarray            # (d,) complex128
+    objective: str               # "overlap" (target psi_f) | "observable" (target O)
+    psi_f: Optional[np.ndarray]  # (d,) complex128 when objective == "overlap"
+    O: Optional[np.ndarray]      # (d, d) float64 when objective == "observable"
+    T: float
+    Nt: int                      # number of piecewise-constant steps, tau = T / Nt
+    N: int                       # number of sub-intervals
+    u0: np.ndarray               # (Nt,) float64 initial control
+    alpha: Optional[np.ndarray] = None   # (Nt,) penalty weight at step midpoints, None = 0
+    iters: int = 20
+    rho: float = 0.1
+    local_iters: int = 1
+    precision: str = "fp64"      # "fp64" | "mixed"
+    meta: dict = field(default_factory=dict)
+
+    @property
+    def d(self) -> int:
+        return int(self.H0.shape[0])
+
+    @property
+    def tau(self) -> float:
+        return self.T / self.Nt
+
+    def with_(self, **kw) -> "Workload":
+        """Copy with some fields replaced (arrays are shared, not copied)."""
+        import dataclasses
+
+        return dataclasses.replace(self, **kw)
+
+
+def _basis(d: int, k: int) -> np.ndarray:
+    v = np.zeros(d, dtype=np.complex128)
+    v[k] = 1.0
+    return v
+
+
+def _zz_diagonal(q: int, pairs, J) -> np.ndarray:
+    d = 1 << q
+    s = np.arange(d)
+    z = 1.0 - 2.0 * ((s[:, None] >> np.arange(q)[None, :]) & 1)   # (d, q) eigenvalues of Z_i
+    diag = np.zeros(d)
+    for (i, j), Jij in zip(pairs, J):
+        diag += Jij * z[:, i] * z[:, j]
+    return diag
+
+
+def _x_field(q: int, weights=None) -> np.ndarray:
+    d = 1 << q
+    w = np.ones(q) if weights is None else np.asarray(weights, dtype=np.float64)
+    H1 = np.zeros((d, d))
+    s = np.arange(d)
+    for i in range(q):
+        H1[s, s ^ (1 << i)] += w[i]
+    return H1
+
+
+def spin_all_to_all(q: int, seed: int, *, T: float, Nt: int, N: int, u_amp: float = 0.1,
+                    name: str = "spin") -> Workload:
+    """q spins, all pairs i<j in lexicographic order, J_ij ~ U[0.5, 1.5]; then u0 ~ U[-u_amp, u_amp].
+
+    psi_i = |0...0>, psi_f = |1...1>, overlap objective, alpha = 0.
+    """
+    rng = np.random.default_rng(seed)
+    pairs = [(i, j) for i in range(q) for j in range(i + 1, q)]
+    J = rng.uniform(0.5, 1.5, size=len(pairs))
+    u0 = rng.uniform(-u_amp, u_amp, size=Nt)
+    d = 1 << q
+    return Workload(name=name, kind="bitflip", H0=np.diag(_zz_diagonal(q, pairs, J)), H1=_x_field(q),
+                    psi_i=_basis(d, 0), objective="overlap", psi_f=_basis(d, d - 1), O=None,
+                    T=T, Nt=Nt, N=N, u0=u0, meta={"q": q, "pairs": pairs, "J": J})
+
+
+def spin_chain(q: int, seed: int, *, T: float, Nt: int, N: int, u_amp: float = 0.1,
+               name: str = "ising") -> Workload:
+    """Open chain: J_i ~ U[0.5, 1.5] for bonds (i, i+1), i = 0..q-2; then u0 ~ U[-u_amp, u_amp]."""
+    rng = np.random.default_rng(seed)
+    pairs = [(i, i + 1) for i in range(q - 1)]
+    J = rng.uniform(0.5, 1.5, size=len(pairs))
+    u0 = rng.uniform(-u_amp, u_amp, size=Nt)
+    d = 1 << q
+    return Workload(name=name, kind="bitflip", H0=np.diag(_zz_diagonal(q, pairs, J)), H1=_x_field(q),
+                    psi_i=_basis(d, 0), objective="overlap", psi_f=_basis(d, d - 1), O=None,
+                    T=T, Nt=Nt, N=N, u0=u0, meta={"q": q, "pairs": pairs, "J": J})
+
+
+def rotor_cos_theta(jmax: int) -> np.ndarray:
+    """cos(theta) in the |j, m=0> basis, j = 0..jmax (tridiagonal, zero diagonal)."""
+    d = jmax + 1
+    j = np.arange(d - 1, dtype=np.float64)
+    c = (j + 1.0) / np.sqrt((2.0 * j + 1.0) * (2.0 * j + 3.0))
+    C = np.zeros((d, d))
+    C[np.arange(d - 1), np.arange(1, d)] = c
+    C[np.arange(1, d), np.arange(d - 1)] = c
+    return C
+
+
+def rotor(jmax: int, seed: int, *, T: float, Nt: int, N: int, u_amp: float = 1.0,
+          alpha0: float = 1e-3, objective: str = "observable", name: str = "rotor") -> Workload:
+    """Rigid rotor; u0 ~ U[-u_amp, u_amp] is the only random draw.
+
+    alpha(t) = alpha0 * (10 * ((t - T/2)/(T/2))**6 + 1), the shape of the paper's rotor penalty
+    (Sec. 4), sampled at step midpoints.  objective "observable" maximises <cos theta>(T);
+    objective "overlap" targets the max-eigenvalue eigenvector of cos theta restricted to j <= 4.
+    """
+    rng = np.random.default_rng(seed)
+    u0 = rng.uniform(-u_amp, u_amp, size=Nt)
+    d = jmax + 1
+    jj = np.arange(d, dtype=np.float64)
+    C = rotor_cos_theta(jmax)
+    tau = T / Nt
+    tm = (np.arange(Nt) + 0.5) * tau
+    alpha = alpha0 * (10.0 * ((tm - T / 2) / (T / 2)) ** 6 + 1.0)
+    psi_f = None
+    O = None
+    if objective == "observable":
+        O = C
+    else:
+        w, V = np.linalg.eigh(C[:5, :5])
+        psi_f = np.zeros(d, dtype=np.complex128)
+        psi_f[:5] = V[:, -1] * np.sign(V[0, -1])
+    return Workload(name=name, kind="tridiag", H0=np.diag(jj * (jj + 1.0)), H1=-C, psi_i=_basis(d, 0),
+                    objective=objective, psi_f=psi_f, O=O, T=T, Nt=Nt, N=N, u0=u0, alpha=alpha,
+                    meta={"jmax": jmax, "alpha0": alpha0})
+
+
+def random_dense(d: int, seed: int, *, T: float, Nt: int, N: int, u_amp: float = 0.5,
+                 objective: str = "overlap", name: str = "dense") -> Workload:
+    """Random real-symmetric H0, H1 (entries N(0,1), symmetrised, scaled by 1/sqrt(d)), random unit
+    psi_i and psi_f (or a random symmetric observable), u0 ~ U[-u_amp, u_amp].  Draw order: H0, H1,
+    psi_i (re, im), target, u0."""
+    rng = np.random.default_rng(seed)
+
+    def sym():
+        A = rng.standard_normal((d, d))
+        return (A + A.T) / np.sqrt(2.0 * d)
+
+    H0 = sym()
+    H1 = sym()
+
+    def unit():
+        v = rng.standard_normal(d) + 1j * rng.standard_normal(d)
+        return v / np.linalg.norm(v)
+
+    psi_i = unit()
+    psi_f = None
+    O = None
+    if objective == "overlap":
+        psi_f = unit()
+    else:
+        O = sym()
+    u0 = rng.uniform(-u_amp, u_amp, size=Nt)
+    return Workload(name=name, kind="dense", H0=H0, H1=H1, psi_i=psi_i, objective=objective,
+                    psi_f=psi_f, O=O, T=T, Nt=Nt, N=N, u0=u0)
+
+
+def rabi(delta: float, u: float, *, T: float, Nt: int, N: int = 1) -> Workload:
+    """Two-level system H = (delta/2) sigma_z + (u/2) sigma_x with a constant control u."""
+    H0 = np.diag([delta / 2.0, -delta / 2.0])
+    H1 = np.array([[0.0, 0.5], [0.5, 0.0]])
+    return Workload(name="rabi", kind="dense", H0=H0, H1=H1, psi_i=_basis(2, 0), objective="overlap",
+                    psi_f=_basis(2, 1), O=None, T=T, Nt=Nt, N=N, u0=np.full(Nt, float(u)))
+
+
+# ----------------------------------------------------------------------------------------------
+# The named benchmark configurations.  Seed = 1000 + configuration index.
+# ----------------------------------------------------------------------------------------------
+CONFIG_NAMES = ("spin16", "rotor41", "gp512", "ising1024")
+
+
+def config(name: str, *, N: Optional[int] = None, Nt: Optional[int] = None, iters: Optional[int] = None,
+           precision: Optional[str] = None) -> Workload:
+    """The synthetic stand-ins for the four benchmark problems.
+
+    spin16    : 4 spins (d=16), all-to-all ZZ, X control, |0000> -> |1111>, T=10, Nt=1000, N=4,
+                u0 ~ U[-0.1, 0.1], 20 iterations, FP64.
+    rotor41   : rigid rotor j=0..40 (d=41), maximise <cos theta>(T), T=pi, Nt=20000, N=128 (16 and
+                64 also used), u0 ~ U[-1, 1], 50 iterations, mixed precision.
+    ising1024 : 10-spin open Ising chain (d=1024), |0^10> -> |1^10>, T=10, Nt=50000, N=256,
+                u0 ~ U[-0.1, 0.1], 20 iterations, mixed precision.
+    """
+    if name == "spin16":
+        w = spin_all_to_all(4, 1000, T=10.0, Nt=Nt or 1000, N=N or 4, name=name)
+        w = w.with_(iters=iters or 20, rho=30.0, precision=precision or "fp64")
+    elif name == "rotor41":
+        w = rotor(40, 1001, T=float(np.pi), Nt=Nt or 20000, N=N or 128, name=name)
+        w = w.with_(iters=iters or 50, rho=1.0, precision=precision or "mixed")
+    elif name == "ising1024":
+        w = spin_chain(10, 1003, T=10.0, Nt=Nt or 50000, N=N or 256, name=name)
+        w = w.with_(iters=iters or 20, rho=0.2, precision=precision or "mixed")
+    else:
+        raise KeyError(name)
+    return w
