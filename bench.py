@@ -1,0 +1,320 @@
+#!/usr/bin/env python
+"""Benchmark of the ISM hot path on GB300.
+
+A step is one pass of Algorithm 1 (propagator assembly, chain and intermediate states, sub-interval
+forward/adjoint/gradient sweeps, control update) over the rigid-rotor problem (d = 41, Nt = 20000,
+N = 128, mixed precision).  Prints one JSON line.
+
+    python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference] [--batch B] [--N N]
+"""
+from __future__ import annotations
+
+import os
+
+for _v in ("OMP_NUM_THREADS", "OPENBLAS_NUM_THREADS", "MKL_NUM_THREADS"):
+    os.environ.setdefault(_v, "1")   # the oracle legs run single-threaded
+
+import argparse
+import json
+import statistics
+import subprocess
+import sys
+import tempfile
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+import numpy as np  # noqa: E402
+
+METRIC = "ISM gradient iters/s and complex state-steps/s vs plain FP64; p50/p99 solve latency"
+UNIT = "ISM iterations/s"
+FP32_LANES_PER_SM = 128
+SMS = 152
+SM_MAX_MHZ = 2070.0
+
+
+def parse():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=30)
+    ap.add_argument("--warmup", type=int, default=5)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--config", default="rotor41")
+    ap.add_argument("--N", type=int, default=128)
+    ap.add_argument("--batch", type=int, default=1)
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-fp64", action="store_true")
+    return ap.parse_args()
+
+
+def dist_env():
+    return int(os.environ.get("RANK", "0")), int(os.environ.get("LOCAL_RANK", "0")), int(os.environ.get("WORLD_SIZE", "1"))
+
+
+# ------------------------------------------------------------------------------ clocks sampling
+class Clocks:
+    Q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,clocks_event_reasons.hw_slowdown,"
+         "clocks_event_reasons.hw_thermal_slowdown,clocks_event_reasons.sw_thermal_slowdown,"
+         "clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu: int):
+        self.gpu = gpu
+        self.proc = None
+        self.f = tempfile.NamedTemporaryFile("w+", suffix=".csv", delete=False)
+
+    def start(self):
+        try:
+            self.proc = subprocess.Popen(["nvidia-smi", "-i", str(self.gpu), f"--query-gpu={self.Q}",
+                                          "--format=csv,noheader,nounits", "-lms", "200"],
+                                         stdout=self.f, stderr=subprocess.DEVNULL)
+        except Exception:
+            self.proc = None
+
+    def stop(self) -> dict:
+        if self.proc is None:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except Exception:
+            self.proc.kill()
+        self.f.flush()
+        rows = []
+        with open(self.f.name) as fh:
+            for line in fh:
+                parts = [p.strip() for p in line.split(",")]
+                if len(parts) >= 9:
+                    rows.append(parts)
+        os.unlink(self.f.name)
+        if not rows:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["no samples"]}
+
+        def num(x):
+            try:
+                return float(x)
+            except ValueError:
+                return None
+
+        sm = [num(r[1]) for r in rows if num(r[1]) is not None]
+        mx = [num(r[2]) for r in rows if num(r[2]) is not None]
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        reasons = sorted({names[i] for r in rows for i in range(4) if "Active" in r[5 + i] and "Not" not in r[5 + i]})
+        return {"sm_mhz": statistics.median(sm) if sm else None, "sm_max_mhz": max(mx) if mx else None,
+                "reasons": reasons, "samples": len(rows)}
+
+
+# ------------------------------------------------------------------------------ work accounting
+def nnz_of(kind: str, d: int) -> int:
+    if kind == "tridiag":
+        return 3 * d - 2
+    if kind == "bitflip":
+        return d * (1 + int(round(np.log2(d))))
+    return d * d
+
+
+def cheb_flops(kind: str, d: int, y_apps: int, terms: int, substeps: int) -> float:
+    """Algorithmic flops of the Chebyshev propagation: each application of the scaled Hamiltonian to
+    a complex d-vector costs 4 nnz (complex x real multiply-adds) + 2d (recurrence subtraction), each
+    accumulated term 4d, each exp sub-step's global phase 6d."""
+    return float(y_apps) * (4 * nnz_of(kind, d) + 2 * d) + float(terms) * 4 * d + float(substeps) * 6 * d
+
+
+def fp32_peak_tflops() -> float:
+    return SMS * FP32_LANES_PER_SM * 2 * SM_MAX_MHZ * 1e6 / 1e12
+
+
+# ------------------------------------------------------------------------------ CPU oracle
+def oracle_sample(cfg: str, N_full: int):
+    """One ISM iteration of the oracle on a time-truncated sample of the workload: Nt/8 steps with
+    N/8 sub-intervals (same steps per sub-interval, same d).  Returns (seconds, scale to full)."""
+    import workloads as W
+    from oracle import ism_oracle as O
+
+    full = W.config(cfg, N=N_full)
+    Nt_s = full.Nt // 8
+    N_s = max(1, N_full // 8)
+    w = W.config(cfg, N=N_s, Nt=Nt_s)
+    t0 = time.perf_counter()
+    O.ism_iteration(w, w.u0, w.rho, w.local_iters)
+    dt = time.perf_counter() - t0
+    return dt, Nt_s / full.Nt, f"one oracle ISM iteration on {cfg} truncated to Nt={Nt_s}, N={N_s} " \
+                               f"(same d and steps per sub-interval), scaled by Nt_sample/Nt = {Nt_s / full.Nt:g}"
+
+
+# ------------------------------------------------------------------------------ reference arm
+def run_reference(args):
+    rank, _, world = dist_env()
+    if rank != 0:
+        return 0
+    import workloads as W
+
+    full = W.config(args.config, N=args.N)
+    times = []
+    sample = ""
+    scale = 1.0
+    for s in range(args.warmup + args.steps):
+        dt, scale, sample = oracle_sample(args.config, args.N)
+        if s >= args.warmup:
+            times.append(dt)
+    tot = sum(times)
+    value = len(times) * scale / tot * 1.0    # full-size ISM iterations per second
+    line = {
+        "impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": args.gpus,
+        "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 / value, "higher_is_better": True,
+        "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+        "config": {"workload": f"{args.config} d={full.d} Nt={full.Nt} N={args.N}", "precision": "fp64 (oracle)"},
+        "cpu_baseline": {"value": value, "unit": UNIT, "cores": 1, "kind": "oracle", "sample": sample},
+        "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+    }
+    print(json.dumps(line), flush=True)
+    return 0
+
+
+# ------------------------------------------------------------------------------ our arm
+def run_ours(args):
+    import torch
+
+    rank, local_rank, world = dist_env()
+    if world > 1:
+        import torch.distributed as dist
+
+        dist.init_process_group("nccl", device_id=torch.device("cuda", local_rank))
+    torch.cuda.set_device(local_rank)
+    import __graft_entry__
+
+    __graft_entry__.build()
+    import paper_1603_01237_gb300 as P
+    import workloads as W
+
+    w = W.config(args.config, N=args.N)
+    B = args.batch
+    stream = torch.cuda.Stream()
+    plan = P.Plan(w, precision="mixed", batch=B, stream=stream)
+    rng = np.random.default_rng(2000 + rank)
+    U0 = np.stack([w.u0] + [rng.uniform(-1, 1, w.Nt) for _ in range(B - 1)])
+    u_dev = torch.tensor(U0, dtype=torch.float64, device="cuda").contiguous()
+    flush = torch.empty(512 * 1024 * 1024 // 4, dtype=torch.float32, device="cuda")   # 512 MB > L2
+
+    def step_device():
+        plan.ism_iterate(1, u_dev, None, None)
+
+    for _ in range(args.warmup):
+        step_device()
+    plan.ism_set_profiling(True)
+    plan.ism_get_stats(reset=True)
+    clocks = Clocks(local_rank)
+    ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(args.steps)]
+    if world > 1:
+        torch.distributed.barrier()
+    torch.cuda.synchronize()
+    clocks.start()
+    with torch.cuda.stream(stream):
+        for k in range(args.steps):
+            flush.zero_()                       # evict the previous step's working set from L2
+            ev[k][0].record(stream)
+            step_device()
+            ev[k][1].record(stream)
+    torch.cuda.synchronize()
+    if world > 1:
+        torch.distributed.barrier()
+    clk = clocks.stop()
+    step_ms = [a.elapsed_time(b) for a, b in ev]
+    tot_ms = sum(step_ms)
+    st = plan.ism_get_stats(reset=True)
+    plan.ism_set_profiling(False)
+    if world > 1:
+        t = torch.tensor([tot_ms], device="cuda")
+        torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
+        tot_ms = float(t.item())
+    iters_total = B * args.steps * world
+    value = iters_total / (tot_ms / 1e3)
+    state_steps = 5 * w.Nt                     # useful state-steps per ISM iteration (2 sweeps + 3 sub-interval)
+
+    # roofline of the dominant kernel (largest share of device time)
+    names = ["k_assemble", "k_chain", "k_subinterval"]
+    dom = int(np.argmax(st["ms"]))
+    per_launch_ms = st["ms"][dom] / max(1, st["launches"][dom])
+    roof = None
+    if dom in (0, 2):
+        k = 0 if dom == 0 else 1
+        flops = cheb_flops(plan.kind, w.d, st["y_apps"][k], st["terms"][k], st["substeps"][k]) / max(1, st["launches"][dom])
+        achieved = flops / (per_launch_ms / 1e3) / 1e12
+        peak = fp32_peak_tflops()
+        roof = {"kernel": names[dom], "bound": "alu", "achieved": achieved, "peak": peak, "unit": "TFLOP/s",
+                "frac": achieved / peak, "traffic": None,
+                "peak_source": "FP32 FMA units: 152 SMs x 128 lanes x 2 flop x 2070 MHz (derived, not measured)",
+                "flops_per_launch": flops, "ms_per_launch": per_launch_ms}
+    phase_share = {n: st["ms"][i] / max(1e-12, sum(st["ms"])) for i, n in enumerate(names)}
+
+    # e2e through the C ABI with host buffers: H2D of u, one iteration, D2H of u and Err
+    u_host = torch.tensor(U0, dtype=torch.float64).pin_memory()
+    err_host = torch.empty((B, 1), dtype=torch.float64).pin_memory()
+    for _ in range(2):
+        plan.ism_iterate(1, u_host, None, err_host)
+    e2e_t = []
+    for _ in range(max(3, args.steps // 2)):
+        t0 = time.perf_counter()
+        plan.ism_iterate(1, u_host, None, err_host)
+        e2e_t.append(time.perf_counter() - t0)
+    e2e = {"value": B / statistics.mean(e2e_t) * world, "unit": UNIT,
+           "h2d_bytes_per_step": int(u_host.numel() * 8),
+           "d2h_bytes_per_step": int(u_host.numel() * 8 + err_host.numel() * 8)}
+
+    # plain FP64, one problem per launch
+    fp64 = None
+    if not args.no_fp64:
+        p64 = P.Plan(w, precision="fp64", batch=1, stream=stream)
+        u64 = torch.tensor(w.u0, dtype=torch.float64, device="cuda").reshape(1, -1).contiguous()
+        p64.ism_iterate(1, u64, None, None)
+        n64 = 3
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        torch.cuda.synchronize()
+        with torch.cuda.stream(stream):
+            e0.record(stream)
+            p64.ism_iterate(n64, u64, None, None)
+            e1.record(stream)
+        torch.cuda.synchronize()
+        ms64 = e0.elapsed_time(e1) / n64
+        fp64 = {"value": 1e3 / ms64, "unit": UNIT, "ms_per_iteration": ms64, "batch": 1}
+        p64.close()
+
+    cpu = None
+    if rank == 0 and world == 1 and not args.no_cpu_baseline:
+        dt, scale, sample = oracle_sample(args.config, args.N)
+        cpu = {"value": scale / dt, "unit": UNIT, "cores": 1, "kind": "oracle", "sample": sample}
+
+    line = {
+        "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": tot_ms / args.steps, "higher_is_better": True, "scaling": "weak",
+        "vs_baseline": None, "dtype": "f32 propagation, f64 states/overlaps/update", "data": "synthetic",
+        "config": {"workload": f"{args.config}: rigid rotor j<=40 (d={w.d}), <cos theta>(T), T=pi, Nt={w.Nt}, "
+                               f"N={w.N}, batch={B} per GPU", "d": w.d, "Nt": w.Nt, "N": w.N, "batch": B,
+                   "precision": "mixed", "l2": "flushed between steps (512 MB write, outside the timed events)"},
+        "state_steps_per_s": value * state_steps,
+        "step_ms_p50": statistics.median(step_ms), "step_ms_p99": float(np.percentile(step_ms, 99)),
+        "fp64_plain": fp64,
+        "phase_share": phase_share,
+        "roofline": roof,
+        "cpu_baseline": cpu,
+        "e2e": e2e,
+        "gpu_launches": int(sum(st["launches"]) + args.steps) * 1,
+        "clocks": clk,
+    }
+    if rank == 0:
+        print(json.dumps(line), flush=True)
+    plan.close()
+    if world > 1:
+        torch.distributed.destroy_process_group()
+    return 0
+
+
+def main():
+    args = parse()
+    if args.impl == "reference":
+        return run_reference(args)
+    return run_ours(args)
+
+
+if __name__ == "__main__":
+    sys.exit(main())

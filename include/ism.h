@@ -1,0 +1,190 @@
+/*
+ * ism.h -- C ABI of the GB300 Intermediate State Method (ISM) library (libism.so).
+ *
+ * Method: M. K. Riahi, J. Salomon, S. J. Glaser, D. Sugny, "A fully efficient time-parallelized
+ * quantum optimal control algorithm" (arXiv:1603.01237).  Section references below are to that paper.
+ *
+ * Problem (Sec. 2, Eq. (dir)):  i d/dt psi = (H0 + u(t) H1) psi on [0, T], maximise
+ *     J[u] = Re<psi(T)|psi_f> - (1/2) int alpha(t) u(t)^2 dt          (ISM_OBJ_OVERLAP)
+ * or  J[u] = <psi(T)|O|psi(T)> - (1/2) int alpha(t) u(t)^2 dt         (ISM_OBJ_OBSERVABLE, the
+ *     observable variant that Sec. 2 calls a straightforward modification).
+ * Discretisation: Nt piecewise-constant steps of tau = T/Nt; step j applies
+ *     U_j = exp(-i tau (H0 + u_j H1)).
+ * Decomposition (Sec. 2): N sub-intervals with step boundaries j_n = floor(n Nt / N), t_n = j_n tau.
+ *
+ * Conventions shared by every entry point
+ *  - Complex vectors are interleaved (re, im) doubles, element index fastest: a state is 2*d doubles.
+ *  - A plan holds `batch` independent control problems that share H0, H1, psi_i, the target, T, Nt, N
+ *    and alpha, and differ only in their controls.  Batched arrays are problem-major:
+ *    u is [batch][Nt], phi is [batch][N+1][2d], grad is [batch][Nt], Jn is [batch][N].
+ *  - Array arguments of the compute calls may be host or device pointers; the library asks the CUDA
+ *    runtime which one it is (cudaPointerGetAttributes) and copies host data through its own
+ *    device buffers.  The caller owns every array it passes; the plan owns its device scratch and
+ *    its CUDA resources and frees them in ism_plan_destroy.
+ *  - Every compute call is ordered on the plan's stream and returns after that stream has
+ *    finished the call's work, so results in host or device memory are ready on return.
+ *  - Errors are returned as ism_status; ism_last_error() gives a message for the calling thread.
+ *    No C++ exception crosses the ABI and nothing aborts the process.  Non-finite inputs (or
+ *    results) give ISM_ENONFINITE.  A plan must not be used by two threads at once.
+ */
+#ifndef ISM_H_
+#define ISM_H_
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef enum {
+  ISM_OK = 0,
+  ISM_EINVAL = 1,          /* bad argument (null pointer, size out of range, inconsistent fields) */
+  ISM_ENOMEM = 2,          /* device allocation failed                                          */
+  ISM_ECUDA = 3,           /* a CUDA runtime call failed (message in ism_last_error)             */
+  ISM_ENONFINITE = 4,      /* NaN/Inf in an input array or in a result                          */
+  ISM_ETIMEOUT = 5,        /* a bounded device-side wait gave up                                 */
+  ISM_EUNSUPPORTED = 6     /* valid request that this build does not implement                  */
+} ism_status;
+
+typedef enum {
+  ISM_FP64 = 0,            /* everything in double precision                                    */
+  ISM_MIXED = 1            /* propagation in FP32; intermediate states, overlaps, norms,
+                              objective and the control update in FP64                          */
+} ism_precision;
+
+typedef enum {
+  /* H0 and H1 are d x d real symmetric, row-major, d <= 64.                                    */
+  ISM_H_DENSE = 0,
+  /* d = 2^q spins.  H0 is diagonal: H0[0..d-1] = diag(H0).  H1 = sum_i h_i X_i (bit flips of
+     basis index s, spin i <-> bit i): H1[0..q-1] = h_i.  d <= 64.                                */
+  ISM_H_BITFLIP = 1,
+  /* H0, H1 symmetric tridiagonal: H[0..d-1] = diagonal, H[d..2d-2] = first off-diagonal
+     (H[d+e] couples e and e+1).  d <= 64.                                                        */
+  ISM_H_TRIDIAG = 2
+} ism_hkind;
+
+typedef enum {
+  ISM_OBJ_OVERLAP = 0,     /* J = Re<psi(T)|psi_f>, chi(T) = psi_f (Eq. (adj))                    */
+  ISM_OBJ_OBSERVABLE = 1   /* J = <psi(T)|O|psi(T)>, chi(T) = O psi(T), weight 2 on Im-terms      */
+} ism_objective;
+
+/* The control problem (Sec. 2).  All pointers are HOST pointers read only during ism_plan. */
+typedef struct {
+  int d;                   /* Hilbert-space dimension                                            */
+  int kind;                /* ism_hkind: packed layout of H0 and H1                               */
+  const double* H0;        /* packed per kind (see ism_hkind)                                    */
+  const double* H1;        /* packed per kind                                                    */
+  const double* psi_i;     /* initial state, 2d interleaved                                       */
+  int objective;           /* ism_objective                                                        */
+  const double* psi_f;     /* target state, 2d interleaved (ISM_OBJ_OVERLAP)                      */
+  const double* O;         /* observable, d x d real symmetric row-major (ISM_OBJ_OBSERVABLE)     */
+  double T;                /* control time, > 0                                                   */
+  int Nt;                  /* number of piecewise-constant steps, >= 1                            */
+  int N;                   /* number of sub-intervals, 1 <= N <= Nt                               */
+  const double* alpha;     /* Nt penalty weights alpha_j = alpha(t at step midpoint), or NULL (0)  */
+  int batch;               /* independent control problems in the plan, >= 1 (0 is read as 1)    */
+} ism_problem;
+
+typedef struct {
+  int precision;           /* ism_precision                                                        */
+  int local_iters;         /* L >= 1 gradient steps per sub-interval per ISM iteration (Alg. 1 (c)) */
+  double rho;              /* constant step of the gradient ascent (Eq. (gradStep)), > 0          */
+  double cheb_tol;         /* truncation threshold of the Chebyshev series; 0 = default per
+                              precision (1e-17 FP64, 1e-10 mixed)                                 */
+  int max_spin_iters;      /* iteration cap for device-side waits; 0 = default                    */
+} ism_options;
+
+typedef struct ism_plan_s* ism_plan_t;
+
+/*
+ * ism_plan -- validate a problem, copy it to the device and allocate all scratch.
+ *   Defines the partition j_n = floor(n Nt/N), a_n = (T - t_n)/T, b_n = t_n/T (Eq. (cible)),
+ *   beta_n = T/(t_{n+1} - t_n) (Theorem 1) and alpha_n = alpha / beta_n (Sec. 2).
+ *   cuda_stream: a cudaStream_t (NULL = the legacy default stream) on which all work is ordered.
+ *   out: receives the plan handle on ISM_OK, untouched otherwise.
+ *   Errors: ISM_EINVAL (sizes, kind/layout mismatch, non-symmetric dense input), ISM_ENONFINITE,
+ *   ISM_EUNSUPPORTED (d beyond the kind's limit), ISM_ENOMEM, ISM_ECUDA.
+ */
+int ism_plan(const ism_problem* prob, const ism_options* opt, void* cuda_stream, ism_plan_t* out);
+
+/* ism_plan_destroy -- free every device buffer of the plan.  NULL is accepted (no-op). */
+int ism_plan_destroy(ism_plan_t plan);
+
+/*
+ * ism_intermediate_states -- Algorithm 1 steps (a) and (b): the trajectories psi and chi of
+ *   Eqs. (dir)/(adj) at the partition times, built through the propagator assembly of Sec. 3
+ *   (M_n = prod of U_j over sub-interval n, psi(t_{n+1}) = M_n psi(t_n), chi(t_n) = M_n^H chi(t_{n+1})),
+ *   and phi_n = ((T - t_n)/T) psi(t_n) + (t_n/T) chi(t_n) (Eq. (cible)), n = 0..N.
+ *   u:   [batch][Nt] controls (host or device).
+ *   phi: [batch][N+1][2d] output, FP64 in both precision modes (host or device).
+ */
+int ism_intermediate_states(ism_plan_t plan, const double* u, double* phi);
+
+/*
+ * ism_subinterval_grad -- Algorithm 1 step (c) for one gradient evaluation: for every sub-interval
+ *   n and problem, psi_n from psi_n(t_n) = phi_n (Eq. (dirpara)), chi_n backward from
+ *   chi_n(t_{n+1}) = phi_{n+1}, and
+ *     J_n    = w * (-1/2 ||psi_n(t_{n+1}) - phi_{n+1}||^2) - (tau/2) sum_j (alpha_j/beta_n) u_j^2,
+ *     grad_j = w (tau/2) [Im<chi_n|H1|psi_n>(t_{j+1}) + Im<chi_n|H1|psi_n>(t_j)] - tau (alpha_j/beta_n) u_j
+ *   (the derivative dJ_n/du_j in the trapezoid reading of the gradient in the proof of Theorem 2;
+ *   w = 1 for the overlap objective, 2 for the observable).  beta_n * grad equals the gradient of
+ *   J on that sub-interval when phi = phi^u (Theorem 2).
+ *   phi:  [batch][N+1][2d] (any states, not only phi^u); u: [batch][Nt];
+ *   grad: [batch][Nt] output; Jn: [batch][N] output or NULL.
+ */
+int ism_subinterval_grad(ism_plan_t plan, const double* phi, const double* u, double* grad, double* Jn);
+
+/*
+ * ism_iterate -- run `iters` passes of Algorithm 1 with the constant-step gradient sub-solver:
+ *   (a)-(b) as ism_intermediate_states, (c) L = local_iters ascent steps
+ *   u_j <- u_j + rho * beta_n * grad_j / tau on each sub-interval with phi fixed (Eq. (gradStep),
+ *   read as ascent since J is maximised), (d) the new controls are the concatenation, (e)
+ *   Err_k = sum_n sum_j |grad_j| of the first local step.
+ *   u_inout:  [batch][Nt] controls, updated in place (host or device).
+ *   J_hist:   [batch][iters+1] J[u^(k)] for k = 0..iters, or NULL (then the final objective
+ *             evaluation is skipped).
+ *   err_hist: [batch][iters] Err_k, or NULL.
+ */
+int ism_iterate(ism_plan_t plan, int iters, double* u_inout, double* J_hist, double* err_hist);
+
+/*
+ * ism_evaluate -- objective at u: J (with penalty) and F = |<psi(T)|psi_f>|^2 (overlap) or
+ *   <psi(T)|O|psi(T)> (observable), through the same assembly and chain as (a).
+ *   u: [batch][Nt]; J, F: [batch] outputs (host or device), either may be NULL.
+ */
+int ism_evaluate(ism_plan_t plan, const double* u, double* J, double* F);
+
+/* Work and time accounting of a plan, accumulated over calls until reset.
+ *   ms[p], launches[p]: device time (CUDA events around each kernel, only while profiling is on)
+ *                       and launches of phase p = 0 assembly, 1 chain, 2 sub-interval.
+ *   y_apps[k], terms[k], substeps[k]: for k = 0 assembly, 1 sub-interval sweeps, the number of
+ *     applications of the scaled Hamiltonian to one state, of accumulated Chebyshev terms and of
+ *     exponential sub-steps -- the algorithmic work from which flop counts follow. */
+typedef struct {
+  double ms[3];
+  long long launches[3];
+  unsigned long long y_apps[2];
+  unsigned long long terms[2];
+  unsigned long long substeps[2];
+} ism_stats;
+
+/* ism_set_profiling -- on != 0 records CUDA events around every kernel on the plan's stream. */
+int ism_set_profiling(ism_plan_t plan, int on);
+
+/* ism_get_stats -- copy the accumulated accounting into *out (synchronises the plan's stream);
+ *   reset != 0 zeroes it afterwards. */
+int ism_get_stats(ism_plan_t plan, ism_stats* out, int reset);
+
+/* ism_plan_info -- integer facts about a plan, for tests and benchmarks:
+ *   key 0: group lanes per state, 1: state elements per lane, 2: kernel launches per ISM
+ *   iteration (L = local_iters), 3: bytes of plan-owned device memory.  Returns -1 for a bad key. */
+long long ism_plan_info(ism_plan_t plan, int key);
+
+/* Message of the last error on the calling thread ("" if none).  Valid until the next call. */
+const char* ism_last_error(void);
+
+/* Library version string. */
+const char* ism_version(void);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* ISM_H_ */

@@ -1,0 +1,254 @@
+"""ctypes binding of libism.so (include/ism.h): the same entry points, argument marshalling only.
+
+Array arguments may be numpy float64 arrays (host) or torch tensors (host or CUDA); every step of
+the computation runs in the library's CUDA kernels.  There is no CPU fallback: if libism.so is
+missing or fails to load, ``load()`` raises.
+"""
+from __future__ import annotations
+
+import ctypes as C
+import os
+
+import numpy as np
+
+_LIB = None
+LIB_PATH = os.path.join(os.path.dirname(os.path.abspath(__file__)), "libism.so")
+
+ISM_OK, ISM_EINVAL, ISM_ENOMEM, ISM_ECUDA, ISM_ENONFINITE, ISM_ETIMEOUT, ISM_EUNSUPPORTED = range(7)
+ISM_FP64, ISM_MIXED = 0, 1
+ISM_H_DENSE, ISM_H_BITFLIP, ISM_H_TRIDIAG = 0, 1, 2
+ISM_OBJ_OVERLAP, ISM_OBJ_OBSERVABLE = 0, 1
+
+STATUS_NAMES = {0: "ISM_OK", 1: "ISM_EINVAL", 2: "ISM_ENOMEM", 3: "ISM_ECUDA", 4: "ISM_ENONFINITE",
+                5: "ISM_ETIMEOUT", 6: "ISM_EUNSUPPORTED"}
+
+EXPORTS = ("ism_plan", "ism_plan_destroy", "ism_intermediate_states", "ism_subinterval_grad",
+           "ism_iterate", "ism_evaluate", "ism_set_profiling", "ism_get_stats", "ism_plan_info",
+           "ism_last_error", "ism_version")
+
+
+class IsmProblem(C.Structure):
+    _fields_ = [("d", C.c_int), ("kind", C.c_int), ("H0", C.c_void_p), ("H1", C.c_void_p),
+                ("psi_i", C.c_void_p), ("objective", C.c_int), ("psi_f", C.c_void_p), ("O", C.c_void_p),
+                ("T", C.c_double), ("Nt", C.c_int), ("N", C.c_int), ("alpha", C.c_void_p), ("batch", C.c_int)]
+
+
+class IsmOptions(C.Structure):
+    _fields_ = [("precision", C.c_int), ("local_iters", C.c_int), ("rho", C.c_double),
+                ("cheb_tol", C.c_double), ("max_spin_iters", C.c_int)]
+
+
+class IsmStats(C.Structure):
+    _fields_ = [("ms", C.c_double * 3), ("launches", C.c_longlong * 3), ("y_apps", C.c_ulonglong * 2),
+                ("terms", C.c_ulonglong * 2), ("substeps", C.c_ulonglong * 2)]
+
+
+class IsmError(RuntimeError):
+    def __init__(self, status: int, message: str):
+        super().__init__(f"{STATUS_NAMES.get(status, status)}: {message}")
+        self.status = status
+
+
+def load(path: str | None = None):
+    """Load libism.so (once).  Raises OSError if it is missing: build it with
+    ``paper_1603_01237_gb300.build.build()``."""
+    global _LIB
+    if _LIB is not None:
+        return _LIB
+    p = path or LIB_PATH
+    if not os.path.exists(p):
+        raise OSError(f"libism.so not found at {p}; run paper_1603_01237_gb300.build.build()")
+    lib = C.CDLL(p)
+    vp, i, d = C.c_void_p, C.c_int, C.c_double
+    lib.ism_plan.argtypes = [C.POINTER(IsmProblem), C.POINTER(IsmOptions), vp, C.POINTER(vp)]
+    lib.ism_plan.restype = i
+    lib.ism_plan_destroy.argtypes = [vp]
+    lib.ism_plan_destroy.restype = i
+    lib.ism_intermediate_states.argtypes = [vp, vp, vp]
+    lib.ism_intermediate_states.restype = i
+    lib.ism_subinterval_grad.argtypes = [vp, vp, vp, vp, vp]
+    lib.ism_subinterval_grad.restype = i
+    lib.ism_iterate.argtypes = [vp, i, vp, vp, vp]
+    lib.ism_iterate.restype = i
+    lib.ism_evaluate.argtypes = [vp, vp, vp, vp]
+    lib.ism_evaluate.restype = i
+    lib.ism_set_profiling.argtypes = [vp, i]
+    lib.ism_set_profiling.restype = i
+    lib.ism_get_stats.argtypes = [vp, C.POINTER(IsmStats), i]
+    lib.ism_get_stats.restype = i
+    lib.ism_plan_info.argtypes = [vp, i]
+    lib.ism_plan_info.restype = C.c_longlong
+    lib.ism_last_error.argtypes = []
+    lib.ism_last_error.restype = C.c_char_p
+    lib.ism_version.argtypes = []
+    lib.ism_version.restype = C.c_char_p
+    _LIB = lib
+    return lib
+
+
+def _check(rc: int):
+    if rc != ISM_OK:
+        msg = load().ism_last_error().decode(errors="replace")
+        raise IsmError(rc, msg)
+
+
+def _ptr(x):
+    """Address of a numpy array / torch tensor (host or device), or None."""
+    if x is None:
+        return None
+    if isinstance(x, int):
+        return x
+    if isinstance(x, np.ndarray):
+        if not x.flags["C_CONTIGUOUS"]:
+            raise ValueError("arrays must be C-contiguous")
+        return x.ctypes.data
+    if hasattr(x, "data_ptr"):
+        if not x.is_contiguous():
+            raise ValueError("tensors must be contiguous")
+        return x.data_ptr()
+    raise TypeError(f"unsupported array type {type(x)}")
+
+
+def _c128_interleaved(v) -> np.ndarray:
+    v = np.ascontiguousarray(np.asarray(v, dtype=np.complex128))
+    return v.view(np.float64).copy()
+
+
+_KIND = {"dense": ISM_H_DENSE, "bitflip": ISM_H_BITFLIP, "tridiag": ISM_H_TRIDIAG}
+
+
+def pack_hamiltonian(kind: str, H0: np.ndarray, H1: np.ndarray):
+    """Dense real-symmetric (H0, H1) -> the packed layout of ism_hkind, checking the structure."""
+    H0 = np.asarray(H0, dtype=np.float64)
+    H1 = np.asarray(H1, dtype=np.float64)
+    d = H0.shape[0]
+    if kind == "dense":
+        return np.ascontiguousarray(H0).copy(), np.ascontiguousarray(H1).copy()
+    if kind == "tridiag":
+        for H in (H0, H1):
+            if np.any(np.triu(H, 2)) or np.any(np.tril(H, -2)):
+                raise ValueError("tridiag kind needs tridiagonal H0 and H1")
+        pk = lambda H: np.concatenate([np.diag(H), np.diag(H, 1)]).astype(np.float64)  # noqa: E731
+        return pk(H0), pk(H1)
+    if kind == "bitflip":
+        q = int(round(np.log2(d)))
+        if (1 << q) != d:
+            raise ValueError("bitflip kind needs d = 2^q")
+        if np.any(H0 - np.diag(np.diag(H0))):
+            raise ValueError("bitflip kind needs a diagonal H0")
+        h = np.array([H1[0, 1 << i] for i in range(q)], dtype=np.float64)
+        s = np.arange(d)
+        ref = np.zeros((d, d))
+        for i in range(q):
+            ref[s, s ^ (1 << i)] += h[i]
+        if not np.allclose(ref, H1, atol=0.0, rtol=0.0):
+            raise ValueError("bitflip kind needs H1 = sum_i h_i X_i")
+        return np.diag(H0).astype(np.float64).copy(), h
+    raise ValueError(kind)
+
+
+class Plan:
+    """An ism_plan over one workload (any object with the fields of workloads.Workload)."""
+
+    def __init__(self, w, *, precision: str | None = None, batch: int = 1, stream=None,
+                 local_iters: int | None = None, rho: float | None = None, kind: str | None = None,
+                 cheb_tol: float = 0.0):
+        lib = load()
+        self.w = w
+        self.kind = kind or w.kind
+        self.batch = int(batch)
+        self.d, self.Nt, self.N = int(w.d), int(w.Nt), int(w.N)
+        prec = precision or w.precision
+        self.precision = prec
+        H0p, H1p = pack_hamiltonian(self.kind, w.H0, w.H1)
+        self._keep = [H0p, H1p, _c128_interleaved(w.psi_i)]
+        psi_f = _c128_interleaved(w.psi_f) if w.objective == "overlap" else None
+        O = np.ascontiguousarray(w.O, dtype=np.float64) if w.objective == "observable" else None
+        alpha = None if w.alpha is None else np.ascontiguousarray(w.alpha, dtype=np.float64)
+        self._keep += [psi_f, O, alpha]
+        prob = IsmProblem(d=self.d, kind=_KIND[self.kind], H0=_ptr(H0p), H1=_ptr(H1p), psi_i=_ptr(self._keep[2]),
+                          objective=ISM_OBJ_OVERLAP if w.objective == "overlap" else ISM_OBJ_OBSERVABLE,
+                          psi_f=_ptr(psi_f), O=_ptr(O), T=float(w.T), Nt=self.Nt, N=self.N, alpha=_ptr(alpha),
+                          batch=self.batch)
+        opt = IsmOptions(precision=ISM_FP64 if prec == "fp64" else ISM_MIXED,
+                         local_iters=int(local_iters or w.local_iters), rho=float(w.rho if rho is None else rho),
+                         cheb_tol=float(cheb_tol), max_spin_iters=0)
+        h = C.c_void_p()
+        st = None
+        if stream is not None:
+            st = stream if isinstance(stream, int) else int(getattr(stream, "cuda_stream", stream))
+        _check(lib.ism_plan(C.byref(prob), C.byref(opt), st, C.byref(h)))
+        self.handle = h
+
+    # ---------------------------------------------------------------- raw entry points (same names)
+    def ism_intermediate_states(self, u, phi):
+        _check(load().ism_intermediate_states(self.handle, _ptr(u), _ptr(phi)))
+
+    def ism_subinterval_grad(self, phi, u, grad, Jn=None):
+        _check(load().ism_subinterval_grad(self.handle, _ptr(phi), _ptr(u), _ptr(grad), _ptr(Jn)))
+
+    def ism_iterate(self, iters, u_inout, J_hist=None, err_hist=None):
+        _check(load().ism_iterate(self.handle, int(iters), _ptr(u_inout), _ptr(J_hist), _ptr(err_hist)))
+
+    def ism_evaluate(self, u, J=None, F=None):
+        _check(load().ism_evaluate(self.handle, _ptr(u), _ptr(J), _ptr(F)))
+
+    def ism_set_profiling(self, on: bool):
+        _check(load().ism_set_profiling(self.handle, int(bool(on))))
+
+    def ism_get_stats(self, reset: bool = False) -> dict:
+        st = IsmStats()
+        _check(load().ism_get_stats(self.handle, C.byref(st), int(bool(reset))))
+        return {"ms": list(st.ms), "launches": list(st.launches), "y_apps": list(st.y_apps),
+                "terms": list(st.terms), "substeps": list(st.substeps)}
+
+    def info(self, key: int) -> int:
+        return int(load().ism_plan_info(self.handle, key))
+
+    # ---------------------------------------------------------------- numpy conveniences
+    def _u(self, u):
+        u = np.ascontiguousarray(np.asarray(u, dtype=np.float64))
+        return np.ascontiguousarray(np.broadcast_to(u, (self.batch, self.Nt))).copy()
+
+    def intermediate_states(self, u) -> np.ndarray:
+        phi = np.empty((self.batch, self.N + 1, self.d), dtype=np.complex128)
+        self.ism_intermediate_states(self._u(u), phi.view(np.float64))
+        return phi
+
+    def subinterval_grad(self, phi, u):
+        phi = np.ascontiguousarray(np.broadcast_to(np.asarray(phi, dtype=np.complex128),
+                                                   (self.batch, self.N + 1, self.d)))
+        grad = np.empty((self.batch, self.Nt))
+        Jn = np.empty((self.batch, self.N))
+        self.ism_subinterval_grad(phi.view(np.float64), self._u(u), grad, Jn)
+        return grad, Jn
+
+    def iterate(self, u, iters: int):
+        uu = self._u(u)
+        J = np.empty((self.batch, iters + 1))
+        E = np.empty((self.batch, max(iters, 1)))
+        self.ism_iterate(iters, uu, J, E)
+        return uu, J, E[:, :iters]
+
+    def evaluate(self, u):
+        J = np.empty(self.batch)
+        F = np.empty(self.batch)
+        self.ism_evaluate(self._u(u), J, F)
+        return J, F
+
+    def close(self):
+        if getattr(self, "handle", None) is not None and self.handle.value:
+            load().ism_plan_destroy(self.handle)
+            self.handle = C.c_void_p()
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *a):
+        self.close()

@@ -1,0 +1,585 @@
+// ism_api.cu -- the C ABI declared in include/ism.h: plan creation and validation, the partition
+// and weights of Sec. 2, spectral bounds for the Chebyshev propagator, and the orchestration of the
+// hot-path kernels on the plan's stream.
+#include <cmath>
+#include <cstdio>
+#include <cstring>
+#include <string>
+#include <vector>
+
+#include "ism.h"
+#include "ism_kernels.cuh"
+#include "ism_launch.h"
+
+namespace {
+
+thread_local std::string g_err;
+
+int fail(int code, const std::string& msg) {
+  g_err = msg;
+  return code;
+}
+
+#define ISM_CUDA_TRY(expr)                                                                    \
+  do {                                                                                        \
+    cudaError_t e_ = (expr);                                                                  \
+    if (e_ != cudaSuccess) return fail(ISM_ECUDA, std::string(#expr) + ": " + cudaGetErrorString(e_)); \
+  } while (0)
+
+bool all_finite(const double* x, long n) {
+  for (long i = 0; i < n; ++i)
+    if (!std::isfinite(x[i])) return false;
+  return true;
+}
+
+bool is_device_ptr(const void* p) {
+  cudaPointerAttributes a;
+  if (cudaPointerGetAttributes(&a, p) != cudaSuccess) {
+    cudaGetLastError();
+    return false;
+  }
+  return a.type == cudaMemoryTypeDevice || a.type == cudaMemoryTypeManaged;
+}
+
+__global__ void k_check_finite(const double* x, long n, int* status) {
+  for (long i = blockIdx.x * (long)blockDim.x + threadIdx.x; i < n; i += (long)gridDim.x * blockDim.x)
+    if (!isfinite(x[i])) { atomicOr(status, ism::ST_NONFINITE); return; }
+}
+
+// err_hist[b][k] = sum_n err[b][n]  (Algorithm 1 (e)), one warp per problem
+__global__ void k_err_sum(const double* err, int N, int B, double* hist, int stride, int k) {
+  const int b = blockIdx.x;
+  double s = 0.0;
+  for (int n = threadIdx.x; n < N; n += 32) s += err[(long)b * N + n];
+  for (int m = 16; m >= 1; m >>= 1) s += __shfl_xor_sync(0xffffffffu, s, m);
+  if (threadIdx.x == 0) hist[(long)b * stride + k] = s;
+}
+
+}  // namespace
+
+struct ism_plan_s {
+  int d = 0, kind = 0, obj = 0, Nt = 0, N = 0, B = 1, prec = 0, L = 1;
+  double T = 0, tau = 0, rho = 0, tol = 0, w = 1;
+  int max_spin = 0;
+  double c0 = 0, r0 = 0, h1n = 0;
+  ism::KernelSet ks;
+  int ldm = 0, dpad = 0;
+  size_t r2 = 0;  // bytes of one complex element of the propagation precision
+  cudaStream_t st = nullptr;
+  int dev = 0;
+  void* dH = nullptr;
+  int* djn = nullptr;
+  double* dbeta = nullptr;
+  double* dalpha = nullptr;
+  double* dO = nullptr;
+  double2* dpsi_i = nullptr;
+  double2* dpsi_f = nullptr;
+  void* dM = nullptr;
+  double2* dpsin = nullptr;
+  double2* dchin = nullptr;
+  double2* dphi = nullptr;
+  void* dtraj = nullptr;
+  double* du = nullptr;
+  double* dgrad = nullptr;
+  double* dJn = nullptr;
+  double* derr = nullptr;
+  double* dJ = nullptr;
+  double* dF = nullptr;
+  double* dJhist = nullptr;
+  double* derrhist = nullptr;
+  long hist_cap = 0;
+  int* dstatus = nullptr;
+  unsigned long long* dcount = nullptr;   // [6]: assembly (3), sub-interval (3)
+  bool profiling = false;
+  struct Ev { int phase; cudaEvent_t a, b; };
+  std::vector<Ev> pending;                // events recorded in the current call
+  std::vector<cudaEvent_t> pool;
+  double ms[3] = {0, 0, 0};
+  long long launches[3] = {0, 0, 0};
+  size_t chain_smem = 0;
+  size_t bytes = 0;
+  std::vector<void*> allocs;
+};
+
+namespace {
+
+template <class T>
+int dalloc(ism_plan_s* P, T** out, size_t count) {
+  void* p = nullptr;
+  size_t bytes = count * sizeof(T);
+  if (bytes == 0) bytes = 16;
+  cudaError_t e = cudaMalloc(&p, bytes);
+  if (e != cudaSuccess) {
+    cudaGetLastError();
+    return fail(e == cudaErrorMemoryAllocation ? ISM_ENOMEM : ISM_ECUDA,
+                std::string("cudaMalloc of ") + std::to_string(bytes) + " bytes: " + cudaGetErrorString(e));
+  }
+  P->allocs.push_back(p);
+  P->bytes += bytes;
+  *out = reinterpret_cast<T*>(p);
+  return ISM_OK;
+}
+
+void free_all(ism_plan_s* P) {
+  for (void* p : P->allocs) cudaFree(p);
+  P->allocs.clear();
+  for (auto& e : P->pending) { cudaEventDestroy(e.a); cudaEventDestroy(e.b); }
+  P->pending.clear();
+  for (auto e : P->pool) cudaEventDestroy(e);
+  P->pool.clear();
+}
+
+cudaEvent_t take_event(ism_plan_s* P) {
+  if (!P->pool.empty()) { cudaEvent_t e = P->pool.back(); P->pool.pop_back(); return e; }
+  cudaEvent_t e = nullptr;
+  cudaEventCreate(&e);
+  return e;
+}
+
+// Launch one phase kernel, bracketed by events when profiling is on.
+template <class F>
+cudaError_t timed(ism_plan_s* P, int phase, F&& launch) {
+  P->launches[phase] += 1;
+  if (!P->profiling) return launch();
+  ism_plan_s::Ev ev{phase, take_event(P), take_event(P)};
+  cudaEventRecord(ev.a, P->st);
+  cudaError_t e = launch();
+  cudaEventRecord(ev.b, P->st);
+  P->pending.push_back(ev);
+  return e;
+}
+
+void collect_events(ism_plan_s* P) {
+  for (auto& ev : P->pending) {
+    float ms = 0.f;
+    if (cudaEventElapsedTime(&ms, ev.a, ev.b) == cudaSuccess) P->ms[ev.phase] += ms;
+    P->pool.push_back(ev.a);
+    P->pool.push_back(ev.b);
+  }
+  P->pending.clear();
+}
+
+struct Bounds { double lo, hi, h1; };
+
+// Gershgorin enclosures: spec(H0) in [lo, hi], spectral radius of H1 <= h1.
+Bounds bounds_of(int kind, int d, const double* H0, const double* H1) {
+  Bounds b{0, 0, 0};
+  b.lo = INFINITY;
+  b.hi = -INFINITY;
+  if (kind == ISM_H_TRIDIAG) {
+    for (int e = 0; e < d; ++e) {
+      double r0 = (e > 0 ? std::fabs(H0[d + e - 1]) : 0.0) + (e < d - 1 ? std::fabs(H0[d + e]) : 0.0);
+      double r1 = std::fabs(H1[e]) + (e > 0 ? std::fabs(H1[d + e - 1]) : 0.0) + (e < d - 1 ? std::fabs(H1[d + e]) : 0.0);
+      b.lo = std::fmin(b.lo, H0[e] - r0);
+      b.hi = std::fmax(b.hi, H0[e] + r0);
+      b.h1 = std::fmax(b.h1, r1);
+    }
+  } else if (kind == ISM_H_BITFLIP) {
+    int q = 0;
+    while ((1 << q) < d) ++q;
+    for (int e = 0; e < d; ++e) { b.lo = std::fmin(b.lo, H0[e]); b.hi = std::fmax(b.hi, H0[e]); }
+    for (int i = 0; i < q; ++i) b.h1 += std::fabs(H1[i]);
+  } else {
+    for (int e = 0; e < d; ++e) {
+      double r0 = 0.0, r1 = 0.0;
+      for (int f = 0; f < d; ++f) {
+        if (f != e) r0 += std::fabs(H0[e * d + f]);
+        r1 += std::fabs(H1[e * d + f]);
+      }
+      b.lo = std::fmin(b.lo, H0[e * d + e] - r0);
+      b.hi = std::fmax(b.hi, H0[e * d + e] + r0);
+      b.h1 = std::fmax(b.h1, r1);
+    }
+  }
+  return b;
+}
+
+// Device layout of the op data in precision R (see ism_device.cuh).
+template <typename R>
+std::vector<R> pack_op(int kind, int d, const double* H0, const double* H1, int G, int E) {
+  std::vector<R> out;
+  if (kind == ISM_H_TRIDIAG) {
+    out.assign(4 * (size_t)d, R(0));
+    for (int e = 0; e < d; ++e) {
+      out[e] = (R)H0[e];
+      out[2 * d + e] = (R)H1[e];
+      if (e < d - 1) { out[d + e] = (R)H0[d + e]; out[3 * d + e] = (R)H1[d + e]; }
+    }
+  } else if (kind == ISM_H_BITFLIP) {
+    int q = 0;
+    while ((1 << q) < d) ++q;
+    out.assign((size_t)d + q, R(0));
+    for (int e = 0; e < d; ++e) out[e] = (R)H0[e];
+    for (int i = 0; i < q; ++i) out[d + i] = (R)H1[i];
+  } else {
+    const int DP = G * E;
+    out.assign(2 * (size_t)DP * DP, R(0));
+    for (int e = 0; e < d; ++e)
+      for (int f = 0; f < d; ++f) {
+        out[2 * ((size_t)e * DP + f)] = (R)H0[e * d + f];
+        out[2 * ((size_t)e * DP + f) + 1] = (R)H1[e * d + f];
+      }
+  }
+  return out;
+}
+
+int finish(ism_plan_s* P) {
+  cudaError_t e = cudaStreamSynchronize(P->st);
+  if (e != cudaSuccess) return fail(ISM_ECUDA, std::string("stream: ") + cudaGetErrorString(e));
+  collect_events(P);
+  int st = 0;
+  ISM_CUDA_TRY(cudaMemcpy(&st, P->dstatus, sizeof(int), cudaMemcpyDeviceToHost));
+  if (st & ism::ST_TIMEOUT) return fail(ISM_ETIMEOUT, "a bounded device-side wait gave up");
+  if (st & ism::ST_KOVERFLOW) return fail(ISM_EUNSUPPORTED, "Chebyshev series needed more terms than compiled");
+  if (st & ism::ST_NONFINITE) return fail(ISM_ENONFINITE, "non-finite value in a control or a result");
+  g_err.clear();
+  return ISM_OK;
+}
+
+int begin(ism_plan_s* P) {
+  ISM_CUDA_TRY(cudaSetDevice(P->dev));
+  ISM_CUDA_TRY(cudaMemsetAsync(P->dstatus, 0, sizeof(int), P->st));
+  return ISM_OK;
+}
+
+ism::KParams kparams(ism_plan_s* P, double* u) {
+  ism::KParams k{};
+  k.d = P->d; k.Nt = P->Nt; k.N = P->N; k.B = P->B; k.ldm = P->ldm; k.dpad = P->dpad;
+  k.tau = P->tau; k.T = P->T; k.c0 = P->c0; k.r0 = P->r0; k.h1n = P->h1n; k.tol = P->tol;
+  k.rho = P->rho; k.w = P->w;
+  k.jn = P->djn; k.beta = P->dbeta; k.alpha = P->dalpha; k.H = P->dH;
+  k.u = u; k.phi = P->dphi; k.M = P->dM; k.traj = P->dtraj;
+  k.grad = P->dgrad; k.Jn = P->dJn; k.err = P->derr; k.status = P->dstatus;
+  k.count = P->dcount;
+  k.update = 0; k.max_spin = P->max_spin;
+  return k;
+}
+
+// a-b of Algorithm 1: assemble M_n, chain, phi, J/F (optionally into Jhist[.][hist_k]).
+int run_states(ism_plan_s* P, const double* u, double* Jhist, int hist_stride, int hist_k) {
+  ism::KParams k = kparams(P, const_cast<double*>(u));
+  ISM_CUDA_TRY(timed(P, 0, [&] { return P->ks.assemble(k, P->st); }));
+  ism::ChainParams c{};
+  c.d = P->d; c.Nt = P->Nt; c.N = P->N; c.B = P->B; c.ldm = P->ldm; c.obj = P->obj;
+  c.tau = P->tau; c.T = P->T; c.M = P->dM; c.psi_i = P->dpsi_i; c.psi_f = P->dpsi_f; c.O = P->dO;
+  c.alpha = P->dalpha; c.u = u; c.jn = P->djn; c.psin = P->dpsin; c.chin = P->dchin; c.phi = P->dphi;
+  c.J = P->dJ; c.F = P->dF; c.Jhist = Jhist; c.hist_stride = hist_stride; c.hist_k = hist_k;
+  c.status = P->dstatus; c.max_spin = P->max_spin;
+  ISM_CUDA_TRY(timed(P, 1, [&] { return ism::launch_chain(P->prec, c, P->chain_smem, P->st); }));
+  return ISM_OK;
+}
+
+// Bring a caller array of n doubles to the device: device pointers are used in place, host data is
+// copied into `staging` after a finiteness check.
+int stage_in(ism_plan_s* P, const double* src, long n, double* staging, const double** out, bool check) {
+  if (is_device_ptr(src)) {
+    if (check) {
+      int blocks = (int)std::min<long>(1024, (n + 255) / 256);
+      if (blocks < 1) blocks = 1;
+      k_check_finite<<<blocks, 256, 0, P->st>>>(src, n, P->dstatus);
+      ISM_CUDA_TRY(cudaGetLastError());
+    }
+    *out = src;
+    return ISM_OK;
+  }
+  if (check && !all_finite(src, n)) return fail(ISM_ENONFINITE, "non-finite value in an input array");
+  ISM_CUDA_TRY(cudaMemcpyAsync(staging, src, n * sizeof(double), cudaMemcpyHostToDevice, P->st));
+  *out = staging;
+  return ISM_OK;
+}
+
+int copy_out(ism_plan_s* P, double* dst, const void* src, long n) {
+  if (!dst) return ISM_OK;
+  ISM_CUDA_TRY(cudaMemcpyAsync(dst, src, n * sizeof(double), cudaMemcpyDefault, P->st));
+  return ISM_OK;
+}
+
+int ensure_hist(ism_plan_s* P, long cap) {
+  if (cap <= P->hist_cap) return ISM_OK;
+  // old buffers stay in the plan's list and are freed at destroy
+  int rc = dalloc(P, &P->dJhist, (size_t)P->B * cap);
+  if (rc) return rc;
+  rc = dalloc(P, &P->derrhist, (size_t)P->B * cap);
+  if (rc) return rc;
+  P->hist_cap = cap;
+  return ISM_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
+const char* ism_last_error(void) { return g_err.c_str(); }
+
+const char* ism_version(void) { return "ism-gb300 0.1 (sm_103a)"; }
+
+int ism_plan(const ism_problem* prob, const ism_options* opt, void* cuda_stream, ism_plan_t* out) {
+  if (!prob || !opt || !out) return fail(ISM_EINVAL, "null problem, options or output handle");
+  const ism_problem& p = *prob;
+  const int d = p.d;
+  if (d < 1) return fail(ISM_EINVAL, "d must be >= 1");
+  if (p.Nt < 1) return fail(ISM_EINVAL, "Nt must be >= 1");
+  if (p.N < 1 || p.N > p.Nt) return fail(ISM_EINVAL, "need 1 <= N <= Nt");
+  if (!(p.T > 0.0) || !std::isfinite(p.T)) return fail(ISM_EINVAL, "T must be finite and > 0");
+  if (p.batch < 0) return fail(ISM_EINVAL, "batch must be >= 0");
+  if (p.kind < ISM_H_DENSE || p.kind > ISM_H_TRIDIAG) return fail(ISM_EINVAL, "unknown Hamiltonian kind");
+  if (p.objective != ISM_OBJ_OVERLAP && p.objective != ISM_OBJ_OBSERVABLE) return fail(ISM_EINVAL, "unknown objective");
+  if (!p.H0 || !p.H1 || !p.psi_i) return fail(ISM_EINVAL, "H0, H1 and psi_i are required");
+  if (p.objective == ISM_OBJ_OVERLAP && !p.psi_f) return fail(ISM_EINVAL, "psi_f is required for the overlap objective");
+  if (p.objective == ISM_OBJ_OBSERVABLE && !p.O) return fail(ISM_EINVAL, "O is required for the observable objective");
+  if (opt->precision != ISM_FP64 && opt->precision != ISM_MIXED) return fail(ISM_EINVAL, "unknown precision");
+  if (opt->local_iters < 0) return fail(ISM_EINVAL, "local_iters must be >= 1");
+  if (!(opt->rho >= 0.0) || !std::isfinite(opt->rho)) return fail(ISM_EINVAL, "rho must be finite and >= 0");
+  if (opt->cheb_tol < 0.0) return fail(ISM_EINVAL, "cheb_tol must be >= 0");
+  if (d > 64) return fail(ISM_EUNSUPPORTED, "this build supports d <= 64");
+  int q = 0;
+  if (p.kind == ISM_H_BITFLIP) {
+    while ((1 << q) < d) ++q;
+    if ((1 << q) != d || d < 2) return fail(ISM_EINVAL, "bit-flip kind needs d = 2^q >= 2");
+  }
+  const long nH = p.kind == ISM_H_DENSE ? (long)d * d : p.kind == ISM_H_TRIDIAG ? 2L * d - 1 : d;
+  const long nH1 = p.kind == ISM_H_DENSE ? (long)d * d : p.kind == ISM_H_TRIDIAG ? 2L * d - 1 : q;
+  if (!all_finite(p.H0, nH) || !all_finite(p.H1, nH1) || !all_finite(p.psi_i, 2L * d))
+    return fail(ISM_ENONFINITE, "non-finite value in H0, H1 or psi_i");
+  if (p.objective == ISM_OBJ_OVERLAP && !all_finite(p.psi_f, 2L * d)) return fail(ISM_ENONFINITE, "non-finite psi_f");
+  if (p.objective == ISM_OBJ_OBSERVABLE && !all_finite(p.O, (long)d * d)) return fail(ISM_ENONFINITE, "non-finite O");
+  if (p.alpha && !all_finite(p.alpha, p.Nt)) return fail(ISM_ENONFINITE, "non-finite alpha");
+  auto symmetric = [d](const double* A) {
+    double s = 0.0;
+    for (long i = 0; i < (long)d * d; ++i) s = std::fmax(s, std::fabs(A[i]));
+    for (int i = 0; i < d; ++i)
+      for (int j = 0; j < i; ++j)
+        if (std::fabs(A[i * d + j] - A[j * d + i]) > 1e-12 * (s + 1e-300)) return false;
+    return true;
+  };
+  if (p.kind == ISM_H_DENSE && (!symmetric(p.H0) || !symmetric(p.H1)))
+    return fail(ISM_EINVAL, "dense H0 and H1 must be real symmetric");
+  if (p.objective == ISM_OBJ_OBSERVABLE && !symmetric(p.O)) return fail(ISM_EINVAL, "O must be real symmetric");
+
+  ism_plan_s* P = new (std::nothrow) ism_plan_s();
+  if (!P) return fail(ISM_ENOMEM, "host allocation");
+  P->d = d; P->kind = p.kind; P->obj = p.objective; P->Nt = p.Nt; P->N = p.N; P->B = p.batch < 1 ? 1 : p.batch;
+  P->prec = opt->precision; P->L = opt->local_iters < 1 ? 1 : opt->local_iters;
+  P->T = p.T; P->tau = p.T / p.Nt; P->rho = opt->rho;
+  P->tol = opt->cheb_tol > 0 ? opt->cheb_tol : (P->prec == ISM_FP64 ? 1e-17 : 1e-10);
+  P->w = p.objective == ISM_OBJ_OVERLAP ? 1.0 : 2.0;
+  P->max_spin = opt->max_spin_iters > 0 ? opt->max_spin_iters : (1 << 22);
+  P->st = reinterpret_cast<cudaStream_t>(cuda_stream);
+  cudaGetDevice(&P->dev);
+
+  bool ok = p.kind == ISM_H_TRIDIAG   ? ism::kernels_tridiag(P->prec, d, &P->ks)
+            : p.kind == ISM_H_BITFLIP ? ism::kernels_bitflip(P->prec, d, &P->ks)
+                                      : ism::kernels_dense(P->prec, d, &P->ks);
+  if (!ok) { delete P; return fail(ISM_EUNSUPPORTED, "no compiled kernel for this kind and d"); }
+  const int gpw = 32 / P->ks.G;
+  P->dpad = (d + gpw - 1) / gpw * gpw;
+  P->ldm = d + (d & 1);
+  P->r2 = P->prec == ISM_FP64 ? sizeof(double2) : sizeof(float2);
+
+  Bounds bd = bounds_of(p.kind, d, p.H0, p.H1);
+  P->c0 = 0.5 * (bd.lo + bd.hi);
+  P->r0 = 0.5 * (bd.hi - bd.lo);
+  P->h1n = bd.h1;
+
+  // partition (Sec. 2): j_n = floor(n Nt / N), t_n = j_n tau, beta_n = T / (t_{n+1} - t_n)
+  std::vector<int> jn(P->N + 1);
+  for (int n = 0; n <= P->N; ++n) jn[n] = (int)(((long long)n * P->Nt) / P->N);
+  std::vector<double> beta(P->N);
+  for (int n = 0; n < P->N; ++n) beta[n] = P->T / (jn[n + 1] * P->tau - jn[n] * P->tau);
+
+  int rc = ISM_OK;
+  const int GE = P->ks.G * P->ks.E;
+  const size_t B = P->B;
+#define TRY_ALLOC(ptr, n) if ((rc = dalloc(P, &(ptr), (n))) != ISM_OK) { free_all(P); delete P; return rc; }
+  unsigned char* dHb = nullptr;
+  size_t hbytes;
+  std::vector<double> hd;
+  std::vector<float> hf;
+  if (P->prec == ISM_FP64) { hd = pack_op<double>(p.kind, d, p.H0, p.H1, P->ks.G, P->ks.E); hbytes = hd.size() * sizeof(double); }
+  else { hf = pack_op<float>(p.kind, d, p.H0, p.H1, P->ks.G, P->ks.E); hbytes = hf.size() * sizeof(float); }
+  TRY_ALLOC(dHb, hbytes);
+  P->dH = dHb;
+  TRY_ALLOC(P->djn, (size_t)P->N + 1);
+  TRY_ALLOC(P->dbeta, (size_t)P->N);
+  if (p.alpha) TRY_ALLOC(P->dalpha, (size_t)P->Nt);
+  TRY_ALLOC(P->dpsi_i, (size_t)d);
+  TRY_ALLOC(P->dpsi_f, (size_t)d);
+  if (p.objective == ISM_OBJ_OBSERVABLE) TRY_ALLOC(P->dO, (size_t)d * d);
+  unsigned char* dMb = nullptr;
+  TRY_ALLOC(dMb, B * P->N * (size_t)d * P->ldm * P->r2);
+  P->dM = dMb;
+  TRY_ALLOC(P->dpsin, B * (P->N + 1) * (size_t)d);
+  TRY_ALLOC(P->dchin, B * (P->N + 1) * (size_t)d);
+  TRY_ALLOC(P->dphi, B * (P->N + 1) * (size_t)d);
+  unsigned char* dTb = nullptr;
+  TRY_ALLOC(dTb, B * ((size_t)P->Nt + P->N) * GE * P->r2);
+  P->dtraj = dTb;
+  TRY_ALLOC(P->du, B * P->Nt);
+  TRY_ALLOC(P->dgrad, B * P->Nt);
+  TRY_ALLOC(P->dJn, B * P->N);
+  TRY_ALLOC(P->derr, B * P->N);
+  TRY_ALLOC(P->dJ, B);
+  TRY_ALLOC(P->dF, B);
+  TRY_ALLOC(P->dstatus, 1);
+  TRY_ALLOC(P->dcount, 6);
+#undef TRY_ALLOC
+
+  cudaError_t e = cudaSuccess;
+  auto h2d = [&](void* dst, const void* src, size_t n) {
+    if (e == cudaSuccess) e = cudaMemcpy(dst, src, n, cudaMemcpyHostToDevice);
+  };
+  h2d(P->dH, P->prec == ISM_FP64 ? (const void*)hd.data() : (const void*)hf.data(), hbytes);
+  h2d(P->djn, jn.data(), jn.size() * sizeof(int));
+  h2d(P->dbeta, beta.data(), beta.size() * sizeof(double));
+  if (p.alpha) h2d(P->dalpha, p.alpha, P->Nt * sizeof(double));
+  h2d(P->dpsi_i, p.psi_i, 2 * sizeof(double) * d);
+  if (p.objective == ISM_OBJ_OVERLAP) h2d(P->dpsi_f, p.psi_f, 2 * sizeof(double) * d);
+  else if (e == cudaSuccess) e = cudaMemset(P->dpsi_f, 0, 2 * sizeof(double) * d);
+  if (p.objective == ISM_OBJ_OBSERVABLE) h2d(P->dO, p.O, sizeof(double) * d * d);
+  if (e == cudaSuccess) e = cudaMemset(P->dstatus, 0, sizeof(int));
+  if (e == cudaSuccess) e = cudaMemset(P->dcount, 0, 6 * sizeof(unsigned long long));
+  if (e != cudaSuccess) {
+    free_all(P);
+    delete P;
+    return fail(ISM_ECUDA, std::string("plan upload: ") + cudaGetErrorString(e));
+  }
+  P->chain_smem = 2 * (size_t)d * P->ldm * P->r2 + 2 * 64 * P->r2;
+  *out = P;
+  g_err.clear();
+  return ISM_OK;
+}
+
+int ism_plan_destroy(ism_plan_t P) {
+  if (!P) return ISM_OK;
+  cudaSetDevice(P->dev);
+  cudaStreamSynchronize(P->st);
+  free_all(P);
+  delete P;
+  return ISM_OK;
+}
+
+long long ism_plan_info(ism_plan_t P, int key) {
+  if (!P) return -1;
+  switch (key) {
+    case 0: return P->ks.G;
+    case 1: return P->ks.E;
+    case 2: return 2 + P->L;
+    case 3: return (long long)P->bytes;
+    default: return -1;
+  }
+}
+
+int ism_set_profiling(ism_plan_t P, int on) {
+  if (!P) return fail(ISM_EINVAL, "null plan");
+  P->profiling = on != 0;
+  return ISM_OK;
+}
+
+int ism_get_stats(ism_plan_t P, ism_stats* out, int reset) {
+  if (!P || !out) return fail(ISM_EINVAL, "null argument");
+  ISM_CUDA_TRY(cudaSetDevice(P->dev));
+  ISM_CUDA_TRY(cudaStreamSynchronize(P->st));
+  collect_events(P);
+  unsigned long long c[6];
+  ISM_CUDA_TRY(cudaMemcpy(c, P->dcount, sizeof(c), cudaMemcpyDeviceToHost));
+  for (int i = 0; i < 3; ++i) { out->ms[i] = P->ms[i]; out->launches[i] = P->launches[i]; }
+  for (int k = 0; k < 2; ++k) { out->y_apps[k] = c[3 * k]; out->terms[k] = c[3 * k + 1]; out->substeps[k] = c[3 * k + 2]; }
+  if (reset) {
+    for (int i = 0; i < 3; ++i) { P->ms[i] = 0; P->launches[i] = 0; }
+    ISM_CUDA_TRY(cudaMemset(P->dcount, 0, sizeof(c)));
+  }
+  return ISM_OK;
+}
+
+int ism_intermediate_states(ism_plan_t P, const double* u, double* phi) {
+  if (!P || !u || !phi) return fail(ISM_EINVAL, "null argument");
+  int rc = begin(P);
+  if (rc) return rc;
+  const double* ud = nullptr;
+  if ((rc = stage_in(P, u, (long)P->B * P->Nt, P->du, &ud, true))) return rc;
+  if ((rc = run_states(P, ud, nullptr, 0, 0))) return rc;
+  if ((rc = copy_out(P, phi, P->dphi, 2L * P->B * (P->N + 1) * P->d))) return rc;
+  return finish(P);
+}
+
+int ism_subinterval_grad(ism_plan_t P, const double* phi, const double* u, double* grad, double* Jn) {
+  if (!P || !phi || !u || !grad) return fail(ISM_EINVAL, "null argument");
+  int rc = begin(P);
+  if (rc) return rc;
+  const double* ud = nullptr;
+  if ((rc = stage_in(P, u, (long)P->B * P->Nt, P->du, &ud, true))) return rc;
+  const long nphi = 2L * P->B * (P->N + 1) * P->d;
+  if (is_device_ptr(phi)) {
+    ISM_CUDA_TRY(cudaMemcpyAsync(P->dphi, phi, nphi * sizeof(double), cudaMemcpyDeviceToDevice, P->st));
+  } else {
+    if (!all_finite(phi, nphi)) return fail(ISM_ENONFINITE, "non-finite value in phi");
+    ISM_CUDA_TRY(cudaMemcpyAsync(P->dphi, phi, nphi * sizeof(double), cudaMemcpyHostToDevice, P->st));
+  }
+  ism::KParams k = kparams(P, const_cast<double*>(ud));
+  k.update = 0;
+  k.count = P->dcount + 3;
+  ISM_CUDA_TRY(timed(P, 2, [&] { return P->ks.subinterval(k, P->st); }));
+  if ((rc = copy_out(P, grad, P->dgrad, (long)P->B * P->Nt))) return rc;
+  if ((rc = copy_out(P, Jn, P->dJn, (long)P->B * P->N))) return rc;
+  return finish(P);
+}
+
+int ism_iterate(ism_plan_t P, int iters, double* u_inout, double* J_hist, double* err_hist) {
+  if (!P || !u_inout) return fail(ISM_EINVAL, "null argument");
+  if (iters < 0) return fail(ISM_EINVAL, "iters must be >= 0");
+  int rc = begin(P);
+  if (rc) return rc;
+  const long nu = (long)P->B * P->Nt;
+  const bool dev_u = is_device_ptr(u_inout);
+  double* ud = nullptr;
+  if (dev_u) {
+    const double* tmp = nullptr;
+    if ((rc = stage_in(P, u_inout, nu, P->du, &tmp, true))) return rc;
+    ud = u_inout;
+  } else {
+    const double* tmp = nullptr;
+    if ((rc = stage_in(P, u_inout, nu, P->du, &tmp, true))) return rc;
+    ud = P->du;
+  }
+  const long stride = (long)iters + 1;
+  if ((J_hist || err_hist) && (rc = ensure_hist(P, stride))) return rc;
+  for (int it = 0; it < iters; ++it) {
+    if ((rc = run_states(P, ud, J_hist ? P->dJhist : nullptr, (int)stride, it))) return rc;
+    for (int l = 0; l < P->L; ++l) {
+      ism::KParams k = kparams(P, ud);
+      k.update = 1;
+      k.err = l == 0 ? P->derr : nullptr;
+      k.Jn = l == 0 ? P->dJn : nullptr;
+      k.count = P->dcount + 3;
+      ISM_CUDA_TRY(timed(P, 2, [&] { return P->ks.subinterval(k, P->st); }));
+    }
+    if (err_hist) {
+      k_err_sum<<<P->B, 32, 0, P->st>>>(P->derr, P->N, P->B, P->derrhist, (int)stride, it);
+      ISM_CUDA_TRY(cudaGetLastError());
+    }
+  }
+  if (J_hist && (rc = run_states(P, ud, P->dJhist, (int)stride, iters))) return rc;
+  if (!dev_u) ISM_CUDA_TRY(cudaMemcpyAsync(u_inout, ud, nu * sizeof(double), cudaMemcpyDeviceToHost, P->st));
+  // J_hist is [B][iters+1]; err_hist is [B][iters] (packed from the stride-(iters+1) device rows)
+  if (J_hist) ISM_CUDA_TRY(cudaMemcpyAsync(J_hist, P->dJhist, (size_t)P->B * stride * sizeof(double), cudaMemcpyDefault, P->st));
+  if (err_hist && iters > 0)
+    ISM_CUDA_TRY(cudaMemcpy2DAsync(err_hist, iters * sizeof(double), P->derrhist, stride * sizeof(double),
+                                   iters * sizeof(double), P->B, cudaMemcpyDefault, P->st));
+  if ((rc = finish(P))) return rc;
+  if (!dev_u && !all_finite(u_inout, nu)) return fail(ISM_ENONFINITE, "controls became non-finite");
+  return ISM_OK;
+}
+
+int ism_evaluate(ism_plan_t P, const double* u, double* J, double* F) {
+  if (!P || !u) return fail(ISM_EINVAL, "null argument");
+  int rc = begin(P);
+  if (rc) return rc;
+  const double* ud = nullptr;
+  if ((rc = stage_in(P, u, (long)P->B * P->Nt, P->du, &ud, true))) return rc;
+  if ((rc = run_states(P, ud, nullptr, 0, 0))) return rc;
+  if ((rc = copy_out(P, J, P->dJ, P->B))) return rc;
+  if ((rc = copy_out(P, F, P->dF, P->B))) return rc;
+  return finish(P);
+}
+
+}  // extern "C"

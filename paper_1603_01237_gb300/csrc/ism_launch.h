@@ -1,0 +1,26 @@
+// ism_launch.h -- host-side table of the compiled kernel variants (one translation unit per
+// Hamiltonian structure, instantiated for FP32 and FP64 and for each supported dimension class).
+#pragma once
+#include <cuda_runtime.h>
+
+namespace ism {
+
+struct KParams;
+struct ChainParams;
+
+typedef cudaError_t (*LaunchFn)(const KParams&, cudaStream_t);
+
+struct KernelSet {
+  LaunchFn assemble = nullptr;
+  LaunchFn subinterval = nullptr;
+  int G = 0, E = 0;          // lanes per state, elements per lane
+  size_t op_smem = 0;        // dynamic shared memory of the op (dense H pairs)
+};
+
+// prec: 0 = FP64, 1 = FP32 propagation.  Return false when d is outside the compiled range.
+bool kernels_tridiag(int prec, int d, KernelSet* ks);
+bool kernels_bitflip(int prec, int d, KernelSet* ks);
+bool kernels_dense(int prec, int d, KernelSet* ks);
+cudaError_t launch_chain(int prec, const ChainParams& p, size_t smem, cudaStream_t st);
+
+}  // namespace ism

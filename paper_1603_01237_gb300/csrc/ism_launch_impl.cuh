@@ -1,0 +1,50 @@
+// ism_launch_impl.cuh -- launcher templates shared by the per-structure translation units.
+#pragma once
+#include "ism_kernels.cuh"
+#include "ism_launch.h"
+
+namespace ism {
+
+template <typename R, class Op>
+size_t op_smem_bytes() {
+  return Op::DP_SMEM ? (size_t)2 * Op::DP_SMEM * Op::DP_SMEM * sizeof(R) : 0;
+}
+
+template <typename R, class Op>
+cudaError_t launch_assemble_t(const KParams& p, cudaStream_t st) {
+  constexpr int GPB = 128 / Op::G;
+  const long groups = (long)p.B * p.N * p.dpad;
+  const long grid = (groups + GPB - 1) / GPB;
+  const size_t smem = op_smem_bytes<R, Op>();
+  if (smem > 48 * 1024) {
+    cudaError_t e = cudaFuncSetAttribute(k_assemble<R, Op>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    if (e != cudaSuccess) return e;
+  }
+  k_assemble<R, Op><<<(unsigned)grid, 128, smem, st>>>(p);
+  return cudaGetLastError();
+}
+
+template <typename R, class Op>
+cudaError_t launch_subinterval_t(const KParams& p, cudaStream_t st) {
+  constexpr int GPB = 128 / Op::G;
+  const long groups = (long)p.B * p.N;
+  const long grid = (groups + GPB - 1) / GPB;
+  const size_t smem = op_smem_bytes<R, Op>();
+  if (smem > 48 * 1024) {
+    cudaError_t e = cudaFuncSetAttribute(k_subinterval<R, Op>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    if (e != cudaSuccess) return e;
+  }
+  k_subinterval<R, Op><<<(unsigned)grid, 128, smem, st>>>(p);
+  return cudaGetLastError();
+}
+
+template <typename R, class Op>
+void fill_set(KernelSet* ks) {
+  ks->assemble = &launch_assemble_t<R, Op>;
+  ks->subinterval = &launch_subinterval_t<R, Op>;
+  ks->G = Op::G;
+  ks->E = Op::E;
+  ks->op_smem = op_smem_bytes<R, Op>();
+}
+
+}  // namespace ism

@@ -1,0 +1,129 @@
+"""Host-side checks of the C ABI that need no GPU: the library loads, exports every entry point
+that include/ism.h declares, and rejects malformed problems before touching the device."""
+import ctypes as C
+import os
+import re
+
+import numpy as np
+import pytest
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+
+
+@pytest.fixture(scope="module")
+def lib():
+    import __graft_entry__
+
+    __graft_entry__.build()
+    from paper_1603_01237_gb300 import abi
+
+    return abi.load()
+
+
+def declared_functions():
+    src = open(os.path.join(ROOT, "include", "ism.h")).read()
+    src = re.sub(r"/\*.*?\*/", "", src, flags=re.S)
+    return sorted(set(re.findall(r"\b(ism_[a-z_]+)\s*\(", src)))
+
+
+def test_header_declares_the_boundary():
+    names = declared_functions()
+    for f in ("ism_plan", "ism_intermediate_states", "ism_subinterval_grad", "ism_iterate", "ism_plan_destroy"):
+        assert f in names
+
+
+def test_library_exports_every_declared_symbol(lib):
+    for name in declared_functions():
+        assert hasattr(lib, name), name
+    from paper_1603_01237_gb300 import abi
+
+    assert set(abi.EXPORTS) <= set(declared_functions())
+
+
+def test_version(lib):
+    assert b"sm_103a" in lib.ism_version()
+
+
+def _problem(abi, **kw):
+    d = kw.pop("d", 4)
+    H0 = kw.pop("H0", np.zeros(d * d))
+    H1 = kw.pop("H1", np.eye(d).ravel())
+    psi = np.zeros(2 * d)
+    psi[0] = 1.0
+    base = dict(d=d, kind=abi.ISM_H_DENSE, H0=H0.ctypes.data, H1=H1.ctypes.data, psi_i=psi.ctypes.data,
+                objective=abi.ISM_OBJ_OVERLAP, psi_f=psi.ctypes.data, O=None, T=1.0, Nt=10, N=2, alpha=None,
+                batch=1)
+    base.update(kw)
+    keep = (H0, H1, psi)
+    return abi.IsmProblem(**base), keep
+
+
+@pytest.mark.parametrize("field,value,status", [
+    ("d", 0, 1), ("Nt", 0, 1), ("N", 0, 1), ("N", 11, 1), ("T", 0.0, 1), ("T", float("nan"), 1),
+    ("kind", 7, 1), ("objective", 5, 1), ("psi_f", None, 1), ("batch", -1, 1), ("d", 65, 6),
+])
+def test_plan_rejects_bad_problems(lib, field, value, status):
+    from paper_1603_01237_gb300 import abi
+
+    prob, keep = _problem(abi)
+    setattr(prob, field, value)
+    opt = abi.IsmOptions(precision=0, local_iters=1, rho=0.1, cheb_tol=0.0, max_spin_iters=0)
+    h = C.c_void_p()
+    rc = lib.ism_plan(C.byref(prob), C.byref(opt), None, C.byref(h))
+    assert rc == status
+    assert h.value is None
+    assert len(lib.ism_last_error()) > 0
+
+
+def test_plan_rejects_nonsymmetric_and_nonfinite(lib):
+    from paper_1603_01237_gb300 import abi
+
+    opt = abi.IsmOptions(precision=0, local_iters=1, rho=0.1, cheb_tol=0.0, max_spin_iters=0)
+    H0 = np.arange(16.0)
+    prob, keep = _problem(abi, H0=H0)
+    h = C.c_void_p()
+    assert lib.ism_plan(C.byref(prob), C.byref(opt), None, C.byref(h)) == abi.ISM_EINVAL
+    H0 = np.zeros(16)
+    H0[5] = np.inf
+    prob, keep = _problem(abi, H0=H0)
+    assert lib.ism_plan(C.byref(prob), C.byref(opt), None, C.byref(h)) == abi.ISM_ENONFINITE
+    bad = abi.IsmOptions(precision=3, local_iters=1, rho=0.1, cheb_tol=0.0, max_spin_iters=0)
+    prob, keep = _problem(abi)
+    assert lib.ism_plan(C.byref(prob), C.byref(bad), None, C.byref(h)) == abi.ISM_EINVAL
+
+
+def test_bitflip_needs_power_of_two(lib):
+    from paper_1603_01237_gb300 import abi
+
+    prob, keep = _problem(abi, d=6, kind=abi.ISM_H_BITFLIP, H0=np.zeros(6), H1=np.ones(3))
+    opt = abi.IsmOptions(precision=0, local_iters=1, rho=0.1, cheb_tol=0.0, max_spin_iters=0)
+    h = C.c_void_p()
+    assert lib.ism_plan(C.byref(prob), C.byref(opt), None, C.byref(h)) == abi.ISM_EINVAL
+
+
+def test_null_arguments(lib):
+    from paper_1603_01237_gb300 import abi
+
+    h = C.c_void_p()
+    assert lib.ism_plan(None, None, None, C.byref(h)) == abi.ISM_EINVAL
+    assert lib.ism_iterate(None, 1, None, None, None) == abi.ISM_EINVAL
+    assert lib.ism_intermediate_states(None, None, None) == abi.ISM_EINVAL
+    assert lib.ism_subinterval_grad(None, None, None, None, None) == abi.ISM_EINVAL
+    assert lib.ism_plan_destroy(None) == abi.ISM_OK
+    assert lib.ism_plan_info(None, 0) == -1
+
+
+def test_pack_hamiltonian_checks_structure():
+    import workloads as W
+    from paper_1603_01237_gb300 import abi
+
+    w = W.config("rotor41", Nt=10, N=2)
+    H0p, H1p = abi.pack_hamiltonian("tridiag", w.H0, w.H1)
+    assert H0p.shape == (2 * w.d - 1,) and np.allclose(H1p[:w.d], 0.0)
+    with pytest.raises(ValueError):
+        abi.pack_hamiltonian("bitflip", w.H0, w.H1)
+    s = W.config("spin16", Nt=10, N=2)
+    d0, h = abi.pack_hamiltonian("bitflip", s.H0, s.H1)
+    assert np.allclose(h, 1.0) and np.allclose(d0, np.diag(s.H0))
+    with pytest.raises(ValueError):
+        abi.pack_hamiltonian("tridiag", s.H0, s.H1)

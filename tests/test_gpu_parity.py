@@ -1,0 +1,184 @@
+"""CUDA path (through the C ABI) vs the FP64 oracle on identical seeded inputs.
+
+Tolerances: FP64 mode |dF| <= 1e-9 on the objective and tight element-wise bounds on states and
+gradients; mixed mode |dF| <= 1e-5 and gradient relative L2 <= 1e-4.
+"""
+import numpy as np
+import pytest
+
+import workloads as W
+from oracle import ism_oracle as O
+
+pytestmark = pytest.mark.gpu
+
+FP64_PHI = 1e-11
+FP64_GRAD = 1e-10
+MIX_PHI = 2e-5
+MIX_GRAD = 1e-4
+
+
+@pytest.fixture(scope="module")
+def P():
+    import __graft_entry__
+
+    __graft_entry__.build()
+    import paper_1603_01237_gb300 as P
+
+    return P
+
+
+def rel_l2(a, b):
+    return float(np.linalg.norm(np.ravel(a) - np.ravel(b)) / max(np.linalg.norm(np.ravel(b)), 1e-300))
+
+
+def _cases():
+    return [
+        ("spin16-fp64", W.config("spin16", Nt=400, N=4), "fp64"),
+        ("spin16-ragged", W.config("spin16", Nt=401, N=7), "fp64"),
+        ("rotor41-fp64", W.config("rotor41", Nt=1000, N=16), "fp64"),
+        ("rotor41-mixed", W.config("rotor41", Nt=1000, N=16), "mixed"),
+        ("dense5-fp64", W.random_dense(5, 61, T=2.0, Nt=203, N=6), "fp64"),
+        ("dense41-obs-fp64", W.random_dense(41, 62, T=2.0, Nt=150, N=9, objective="observable"), "fp64"),
+        ("dense64-fp64", W.random_dense(64, 63, T=2.0, Nt=120, N=5), "fp64"),
+        ("dense16-mixed", W.random_dense(16, 64, T=2.0, Nt=300, N=10), "mixed"),
+        ("tridiag2-fp64", W.rabi(0.7, 0.3, T=3.0, Nt=64, N=8).with_(kind="tridiag"), "fp64"),
+        ("bitflip2-fp64", W.spin_all_to_all(1, 5, T=3.0, Nt=64, N=4), "fp64"),
+        ("bitflip32-mixed", W.spin_chain(5, 66, T=4.0, Nt=500, N=20), "mixed"),
+        ("bitflip64-fp64", W.spin_chain(6, 67, T=2.0, Nt=200, N=8), "fp64"),
+    ]
+
+
+CASES = _cases()
+
+
+@pytest.mark.parametrize("name,w,prec", CASES, ids=[c[0] for c in CASES])
+def test_intermediate_states(P, name, w, prec):
+    phi_o = O.intermediate_states(w, w.u0)
+    with P.Plan(w, precision=prec) as pl:
+        phi = pl.intermediate_states(w.u0)[0]
+    tol = FP64_PHI if prec == "fp64" else MIX_PHI
+    assert np.max(np.abs(phi - phi_o)) <= tol, np.max(np.abs(phi - phi_o))
+    assert np.array_equal(phi[0], phi_o[0])            # phi_0 = psi_i exactly
+
+
+@pytest.mark.parametrize("name,w,prec", CASES, ids=[c[0] for c in CASES])
+def test_subinterval_grad(P, name, w, prec):
+    phi_o = O.intermediate_states(w, w.u0)
+    g_o, Jn_o = O.subinterval_all(w, phi_o, w.u0)
+    with P.Plan(w, precision=prec) as pl:
+        g, Jn = pl.subinterval_grad(phi_o, w.u0)
+    tol = FP64_GRAD if prec == "fp64" else MIX_GRAD
+    assert rel_l2(g[0], g_o) <= tol, rel_l2(g[0], g_o)
+    jt = 1e-12 if prec == "fp64" else 1e-6
+    assert np.max(np.abs(Jn[0] - Jn_o)) <= jt * max(1.0, np.abs(Jn_o).max())
+
+
+@pytest.mark.parametrize("name,w,prec", CASES[:4] + CASES[5:6], ids=[c[0] for c in CASES[:4] + CASES[5:6]])
+def test_iterate_matches_algorithm1(P, name, w, prec):
+    iters = 3
+    u_o, J_o, F_o, E_o = O.ism_solve(w, w.u0, iters, w.rho)
+    with P.Plan(w, precision=prec) as pl:
+        u, J, E = pl.iterate(w.u0, iters)
+        Jf, Ff = pl.evaluate(u[0])
+    tolF = 1e-9 if prec == "fp64" else 1e-5
+    assert np.max(np.abs(J[0] - J_o)) <= tolF
+    assert abs(Ff[0] - F_o[-1]) <= tolF
+    assert rel_l2(u[0] - w.u0, u_o - w.u0) <= (1e-9 if prec == "fp64" else 1e-4)
+    assert rel_l2(E[0], E_o) <= (1e-9 if prec == "fp64" else 1e-4)
+
+
+def test_spin16_full_config_fp64(P):
+    """The spin benchmark problem at its full size: 4 spins, Nt=1000, N=4, 20 iterations, FP64."""
+    w = W.config("spin16")
+    u_o, J_o, F_o, E_o = O.ism_solve(w, w.u0, w.iters, w.rho)
+    with P.Plan(w, precision="fp64") as pl:
+        u, J, E = pl.iterate(w.u0, w.iters)
+        _, F = pl.evaluate(u[0])
+    assert np.max(np.abs(J[0] - J_o)) <= 1e-9
+    assert abs(F[0] - F_o[-1]) <= 1e-9
+    assert np.max(np.abs(u[0] - u_o)) <= 1e-9
+
+
+def test_n_independence_on_gpu(P):
+    """L = 1: iterates do not depend on N (Theorem 2), here through the CUDA path in FP64."""
+    base = W.config("rotor41", Nt=600, N=1)
+    res = []
+    for N in (1, 4, 25, 600):
+        with P.Plan(base.with_(N=N), precision="fp64") as pl:
+            res.append(pl.iterate(base.u0, 2)[0][0])
+    for u in res[1:]:
+        assert np.max(np.abs(u - res[0])) <= 1e-10
+
+
+def test_batch_equals_singles(P):
+    w = W.config("rotor41", Nt=800, N=8)
+    rng = np.random.default_rng(5)
+    U = np.stack([w.u0, rng.uniform(-1, 1, w.Nt), rng.uniform(-2, 2, w.Nt)])
+    with P.Plan(w, precision="mixed", batch=3) as pl:
+        ub, Jb, Eb = pl.iterate(U, 2)
+    for b in range(3):
+        with P.Plan(w, precision="mixed") as pl:
+            u1, J1, E1 = pl.iterate(U[b], 2)
+        assert np.array_equal(ub[b], u1[0])
+        assert np.array_equal(Jb[b], J1[0])
+
+
+def test_local_iterations(P):
+    w = W.random_dense(6, 71, T=2.0, Nt=120, N=4)
+    u_o, J_o, _, _ = O.ism_solve(w, w.u0, 2, 0.2, L=3)
+    with P.Plan(w, precision="fp64", local_iters=3, rho=0.2) as pl:
+        u, J, E = pl.iterate(w.u0, 2)
+    assert np.max(np.abs(u[0] - u_o)) <= 1e-10
+    assert np.max(np.abs(J[0] - J_o)) <= 1e-10
+
+
+def test_device_pointers_and_torch_stream(P):
+    import torch
+
+    w = W.config("rotor41", Nt=500, N=10)
+    s = torch.cuda.Stream()
+    ud = torch.tensor(w.u0, dtype=torch.float64, device="cuda").reshape(1, -1).contiguous()
+    phi = torch.empty((1, w.N + 1, w.d, 2), dtype=torch.float64, device="cuda")
+    with P.Plan(w, precision="fp64", stream=s) as pl:
+        pl.ism_intermediate_states(ud, phi)
+        phi_h = pl.intermediate_states(w.u0)
+        Jd = torch.empty((1, 3), dtype=torch.float64, device="cuda")
+        pl.ism_iterate(2, ud, Jd, None)
+        uh, Jh, _ = pl.iterate(w.u0, 2)
+    p = phi.cpu().numpy()[..., 0] + 1j * phi.cpu().numpy()[..., 1]
+    assert np.array_equal(p, phi_h)
+    assert np.array_equal(ud.cpu().numpy(), uh)
+    assert np.array_equal(Jd.cpu().numpy(), Jh)
+
+
+def test_nonfinite_controls_rejected(P):
+    w = W.config("spin16", Nt=100, N=4)
+    u = w.u0.copy()
+    u[17] = np.nan
+    with P.Plan(w) as pl:
+        with pytest.raises(P.IsmError) as ei:
+            pl.iterate(u, 1)
+        assert ei.value.status == 4
+        import torch
+
+        ud = torch.tensor(u, dtype=torch.float64, device="cuda").reshape(1, -1)
+        with pytest.raises(P.IsmError) as ei:
+            pl.ism_evaluate(ud)
+        assert ei.value.status == 4
+        # the plan stays usable
+        J, F = pl.evaluate(w.u0)
+        assert np.isfinite(J).all()
+
+
+def test_stats_count_work(P):
+    w = W.config("rotor41", Nt=1000, N=10)
+    with P.Plan(w) as pl:
+        pl.ism_set_profiling(True)
+        pl.iterate(w.u0, 2)
+        st = pl.ism_get_stats(reset=True)
+    # 2 iterations + 1 final evaluation of J: 3 assemblies and chains, 2 sub-interval sweeps
+    assert st["launches"] == [3, 3, 2]
+    assert all(m > 0 for m in st["ms"])
+    # every assembly propagates d columns over all Nt steps (>= 1 sub-step each)
+    assert st["substeps"][0] >= 3 * w.d * w.Nt
+    assert st["substeps"][1] >= 2 * 2 * w.Nt
