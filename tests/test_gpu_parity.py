@@ -31,6 +31,13 @@ def rel_l2(a, b):
     return float(np.linalg.norm(np.ravel(a) - np.ravel(b)) / max(np.linalg.norm(np.ravel(b)), 1e-300))
 
 
+def _random_target(w, seed):
+    """Same problem with a random unit complex target, so the overlap and its gradient are O(1)."""
+    rng = np.random.default_rng(seed)
+    v = rng.standard_normal(w.d) + 1j * rng.standard_normal(w.d)
+    return w.with_(psi_f=v / np.linalg.norm(v))
+
+
 def _cases():
     return [
         ("spin16-fp64", W.config("spin16", Nt=400, N=4), "fp64"),
@@ -42,9 +49,9 @@ def _cases():
         ("dense64-fp64", W.random_dense(64, 63, T=2.0, Nt=120, N=5), "fp64"),
         ("dense16-mixed", W.random_dense(16, 64, T=2.0, Nt=300, N=10), "mixed"),
         ("tridiag2-fp64", W.rabi(0.7, 0.3, T=3.0, Nt=64, N=8).with_(kind="tridiag"), "fp64"),
-        ("bitflip2-fp64", W.spin_all_to_all(1, 5, T=3.0, Nt=64, N=4, u_amp=1.5), "fp64"),
-        ("bitflip32-mixed", W.spin_chain(5, 66, T=4.0, Nt=500, N=20, u_amp=1.5), "mixed"),
-        ("bitflip64-fp64", W.spin_chain(6, 67, T=2.0, Nt=200, N=8, u_amp=1.5), "fp64"),
+        ("bitflip2-fp64", _random_target(W.spin_all_to_all(1, 5, T=3.0, Nt=64, N=4, u_amp=1.5), 1), "fp64"),
+        ("bitflip32-mixed", _random_target(W.spin_chain(5, 66, T=4.0, Nt=500, N=20, u_amp=1.5), 2), "mixed"),
+        ("bitflip64-fp64", _random_target(W.spin_chain(6, 67, T=2.0, Nt=200, N=8, u_amp=1.5), 3), "fp64"),
         # near-zero overlap (|0..0> -> |1..1> at small u): gradients ~1e-12, compared in absolute terms
         ("bitflip64-tiny-fp64", W.spin_chain(6, 68, T=2.0, Nt=200, N=8), "fp64"),
     ]
