@@ -178,6 +178,29 @@ int ism_get_stats(ism_plan_t plan, ism_stats* out, int reset);
  *   iteration (L = local_iters), 3: bytes of plan-owned device memory.  Returns -1 for a bad key. */
 long long ism_plan_info(ism_plan_t plan, int key);
 
+/*
+ * ism_subinterval_grad_noalloc -- the computation of ism_subinterval_grad for callers that cannot
+ *   allocate device memory (code inside another framework's memory pool, allocation-free real-time
+ *   loops, processes with a device-memory budget fixed up front).  The paper has no counterpart: it
+ *   is an addition of this library.  Needs no plan and calls no cudaMalloc, cudaFree or allocating
+ *   library routine: all scratch (packed Hamiltonian, partition, penalty weights, status word and the
+ *   per-step H1 psi trajectory) lives in one static device array of ISM_NOALLOC_SCRATCH_BYTES that
+ *   every GPU loading the library holds until the process exits.
+ *   prob:      the problem (host struct and host arrays, as for ism_plan); precision: ism_precision.
+ *   phi, u:    [batch][N+1][2d] and [batch][Nt] inputs, DEVICE memory.
+ *   grad, Jn:  [batch][Nt] and [batch][N] (Jn may be NULL) outputs, DEVICE memory.
+ *   cuda_stream: the stream the work is ordered on; the call returns after it has finished.
+ *   The first call on a device looks up the array's device address (cudaGetSymbolAddress) with that
+ *   device current; make that first call before any stream capture.  All calls share the array and
+ *   it keeps the last call's contents (the status word is cleared on entry); calls whose work
+ *   overlaps on the GPU race on it.  A problem needing more scratch than the array holds is rejected
+ *   with ISM_EINVAL and a message giving both sizes; host pointers for phi, u, grad or Jn give
+ *   ISM_EINVAL.  Other errors as ism_subinterval_grad.
+ */
+#define ISM_NOALLOC_SCRATCH_BYTES (32u << 20)
+int ism_subinterval_grad_noalloc(const ism_problem* prob, int precision, const double* phi, const double* u,
+                                 double* grad, double* Jn, void* cuda_stream);
+
 /* Message of the last error on the calling thread ("" if none).  Valid until the next call. */
 const char* ism_last_error(void);
 

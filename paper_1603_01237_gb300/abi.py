@@ -24,7 +24,7 @@ STATUS_NAMES = {0: "ISM_OK", 1: "ISM_EINVAL", 2: "ISM_ENOMEM", 3: "ISM_ECUDA", 4
 
 EXPORTS = ("ism_plan", "ism_plan_destroy", "ism_intermediate_states", "ism_subinterval_grad",
            "ism_iterate", "ism_evaluate", "ism_set_profiling", "ism_get_stats", "ism_plan_info",
-           "ism_last_error", "ism_version")
+           "ism_subinterval_grad_noalloc", "ism_last_error", "ism_version")
 
 
 class IsmProblem(C.Structure):
@@ -78,6 +78,8 @@ def load(path: str | None = None):
     lib.ism_get_stats.restype = i
     lib.ism_plan_info.argtypes = [vp, i]
     lib.ism_plan_info.restype = C.c_longlong
+    lib.ism_subinterval_grad_noalloc.argtypes = [C.POINTER(IsmProblem), i, vp, vp, vp, vp, vp]
+    lib.ism_subinterval_grad_noalloc.restype = i
     lib.ism_last_error.argtypes = []
     lib.ism_last_error.restype = C.c_char_p
     lib.ism_version.argtypes = []
@@ -145,6 +147,28 @@ def pack_hamiltonian(kind: str, H0: np.ndarray, H1: np.ndarray):
             raise ValueError("bitflip kind needs H1 = sum_i h_i X_i")
         return np.diag(H0).astype(np.float64).copy(), h
     raise ValueError(kind)
+
+
+def subinterval_grad_noalloc(w, precision: str, phi, u, grad, Jn=None, *, batch: int = 1, stream=None,
+                             kind: str | None = None):
+    """Binding of ism_subinterval_grad_noalloc for callers that cannot allocate device memory: no plan,
+    the library uses only its static device scratch; phi, u, grad and Jn must be device buffers."""
+    lib = load()
+    k = kind or w.kind
+    H0p, H1p = pack_hamiltonian(k, w.H0, w.H1)
+    psi_i = _c128_interleaved(w.psi_i)
+    psi_f = _c128_interleaved(w.psi_f) if w.objective == "overlap" else None
+    O = np.ascontiguousarray(w.O, dtype=np.float64) if w.objective == "observable" else None
+    alpha = None if w.alpha is None else np.ascontiguousarray(w.alpha, dtype=np.float64)
+    prob = IsmProblem(d=int(w.d), kind=_KIND[k], H0=_ptr(H0p), H1=_ptr(H1p), psi_i=_ptr(psi_i),
+                      objective=ISM_OBJ_OVERLAP if w.objective == "overlap" else ISM_OBJ_OBSERVABLE,
+                      psi_f=_ptr(psi_f), O=_ptr(O), T=float(w.T), Nt=int(w.Nt), N=int(w.N), alpha=_ptr(alpha),
+                      batch=int(batch))
+    st = None
+    if stream is not None:
+        st = stream if isinstance(stream, int) else int(getattr(stream, "cuda_stream", stream))
+    _check(lib.ism_subinterval_grad_noalloc(C.byref(prob), ISM_FP64 if precision == "fp64" else ISM_MIXED,
+                                            _ptr(phi), _ptr(u), _ptr(grad), _ptr(Jn), st))
 
 
 class Plan:

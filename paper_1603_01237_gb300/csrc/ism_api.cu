@@ -20,6 +20,15 @@ int fail(int code, const std::string& msg) {
   return code;
 }
 
+}  // namespace
+
+namespace ism {
+int set_error(int code, const char* msg) { return fail(code, msg); }
+void clear_error() { g_err.clear(); }
+}  // namespace ism
+
+namespace {
+
 #define ISM_CUDA_TRY(expr)                                                                    \
   do {                                                                                        \
     cudaError_t e_ = (expr);                                                                  \
@@ -159,7 +168,9 @@ void collect_events(ism_plan_s* P) {
   P->pending.clear();
 }
 
-struct Bounds { double lo, hi, h1; };
+}  // namespace
+
+namespace ism {
 
 // Gershgorin enclosures: spec(H0) in [lo, hi], spectral radius of H1 <= h1.
 Bounds bounds_of(int kind, int d, const double* H0, const double* H1) {
@@ -222,6 +233,63 @@ std::vector<R> pack_op(int kind, int d, const double* H0, const double* H1, int 
   }
   return out;
 }
+template std::vector<float> pack_op<float>(int, int, const double*, const double*, int, int);
+template std::vector<double> pack_op<double>(int, int, const double*, const double*, int, int);
+
+// Shape and value checks shared by every entry point that takes an ism_problem.
+int validate_problem(const ism_problem& p, int precision) {
+  const int d = p.d;
+  if (d < 1) return fail(ISM_EINVAL, "d must be >= 1");
+  if (p.Nt < 1) return fail(ISM_EINVAL, "Nt must be >= 1");
+  if (p.N < 1 || p.N > p.Nt) return fail(ISM_EINVAL, "need 1 <= N <= Nt");
+  if (!(p.T > 0.0) || !std::isfinite(p.T)) return fail(ISM_EINVAL, "T must be finite and > 0");
+  if (p.batch < 0) return fail(ISM_EINVAL, "batch must be >= 0");
+  if (p.kind < ISM_H_DENSE || p.kind > ISM_H_TRIDIAG) return fail(ISM_EINVAL, "unknown Hamiltonian kind");
+  if (p.objective != ISM_OBJ_OVERLAP && p.objective != ISM_OBJ_OBSERVABLE) return fail(ISM_EINVAL, "unknown objective");
+  if (!p.H0 || !p.H1 || !p.psi_i) return fail(ISM_EINVAL, "H0, H1 and psi_i are required");
+  if (p.objective == ISM_OBJ_OVERLAP && !p.psi_f) return fail(ISM_EINVAL, "psi_f is required for the overlap objective");
+  if (p.objective == ISM_OBJ_OBSERVABLE && !p.O) return fail(ISM_EINVAL, "O is required for the observable objective");
+  if (precision != ISM_FP64 && precision != ISM_MIXED) return fail(ISM_EINVAL, "unknown precision");
+  if (d > 64) return fail(ISM_EUNSUPPORTED, "this build supports d <= 64");
+  int q = 0;
+  if (p.kind == ISM_H_BITFLIP) {
+    while ((1 << q) < d) ++q;
+    if ((1 << q) != d || d < 2) return fail(ISM_EINVAL, "bit-flip kind needs d = 2^q >= 2");
+  }
+  const long nH = p.kind == ISM_H_DENSE ? (long)d * d : p.kind == ISM_H_TRIDIAG ? 2L * d - 1 : d;
+  const long nH1 = p.kind == ISM_H_DENSE ? (long)d * d : p.kind == ISM_H_TRIDIAG ? 2L * d - 1 : q;
+  if (!all_finite(p.H0, nH) || !all_finite(p.H1, nH1) || !all_finite(p.psi_i, 2L * d))
+    return fail(ISM_ENONFINITE, "non-finite value in H0, H1 or psi_i");
+  if (p.objective == ISM_OBJ_OVERLAP && !all_finite(p.psi_f, 2L * d)) return fail(ISM_ENONFINITE, "non-finite psi_f");
+  if (p.objective == ISM_OBJ_OBSERVABLE && !all_finite(p.O, (long)d * d)) return fail(ISM_ENONFINITE, "non-finite O");
+  if (p.alpha && !all_finite(p.alpha, p.Nt)) return fail(ISM_ENONFINITE, "non-finite alpha");
+  auto symmetric = [d](const double* A) {
+    double s = 0.0;
+    for (long i = 0; i < (long)d * d; ++i) s = std::fmax(s, std::fabs(A[i]));
+    for (int i = 0; i < d; ++i)
+      for (int j = 0; j < i; ++j)
+        if (std::fabs(A[i * d + j] - A[j * d + i]) > 1e-12 * (s + 1e-300)) return false;
+    return true;
+  };
+  if (p.kind == ISM_H_DENSE && (!symmetric(p.H0) || !symmetric(p.H1)))
+    return fail(ISM_EINVAL, "dense H0 and H1 must be real symmetric");
+  if (p.objective == ISM_OBJ_OBSERVABLE && !symmetric(p.O)) return fail(ISM_EINVAL, "O must be real symmetric");
+  return ISM_OK;
+}
+
+bool select_kernels(int prec, int kind, int d, KernelSet* ks) {
+  return kind == ISM_H_TRIDIAG   ? kernels_tridiag(prec, d, ks)
+         : kind == ISM_H_BITFLIP ? kernels_bitflip(prec, d, ks)
+                                 : kernels_dense(prec, d, ks);
+}
+
+}  // namespace ism
+
+namespace {
+
+using ism::Bounds;
+using ism::bounds_of;
+using ism::pack_op;
 
 int finish(ism_plan_s* P) {
   cudaError_t e = cudaStreamSynchronize(P->st);
@@ -317,44 +385,13 @@ int ism_plan(const ism_problem* prob, const ism_options* opt, void* cuda_stream,
   if (!prob || !opt || !out) return fail(ISM_EINVAL, "null problem, options or output handle");
   const ism_problem& p = *prob;
   const int d = p.d;
-  if (d < 1) return fail(ISM_EINVAL, "d must be >= 1");
-  if (p.Nt < 1) return fail(ISM_EINVAL, "Nt must be >= 1");
-  if (p.N < 1 || p.N > p.Nt) return fail(ISM_EINVAL, "need 1 <= N <= Nt");
-  if (!(p.T > 0.0) || !std::isfinite(p.T)) return fail(ISM_EINVAL, "T must be finite and > 0");
-  if (p.batch < 0) return fail(ISM_EINVAL, "batch must be >= 0");
-  if (p.kind < ISM_H_DENSE || p.kind > ISM_H_TRIDIAG) return fail(ISM_EINVAL, "unknown Hamiltonian kind");
-  if (p.objective != ISM_OBJ_OVERLAP && p.objective != ISM_OBJ_OBSERVABLE) return fail(ISM_EINVAL, "unknown objective");
-  if (!p.H0 || !p.H1 || !p.psi_i) return fail(ISM_EINVAL, "H0, H1 and psi_i are required");
-  if (p.objective == ISM_OBJ_OVERLAP && !p.psi_f) return fail(ISM_EINVAL, "psi_f is required for the overlap objective");
-  if (p.objective == ISM_OBJ_OBSERVABLE && !p.O) return fail(ISM_EINVAL, "O is required for the observable objective");
-  if (opt->precision != ISM_FP64 && opt->precision != ISM_MIXED) return fail(ISM_EINVAL, "unknown precision");
+  {
+    int rc0 = ism::validate_problem(p, opt->precision);
+    if (rc0 != ISM_OK) return rc0;
+  }
   if (opt->local_iters < 0) return fail(ISM_EINVAL, "local_iters must be >= 1");
   if (!(opt->rho >= 0.0) || !std::isfinite(opt->rho)) return fail(ISM_EINVAL, "rho must be finite and >= 0");
   if (opt->cheb_tol < 0.0) return fail(ISM_EINVAL, "cheb_tol must be >= 0");
-  if (d > 64) return fail(ISM_EUNSUPPORTED, "this build supports d <= 64");
-  int q = 0;
-  if (p.kind == ISM_H_BITFLIP) {
-    while ((1 << q) < d) ++q;
-    if ((1 << q) != d || d < 2) return fail(ISM_EINVAL, "bit-flip kind needs d = 2^q >= 2");
-  }
-  const long nH = p.kind == ISM_H_DENSE ? (long)d * d : p.kind == ISM_H_TRIDIAG ? 2L * d - 1 : d;
-  const long nH1 = p.kind == ISM_H_DENSE ? (long)d * d : p.kind == ISM_H_TRIDIAG ? 2L * d - 1 : q;
-  if (!all_finite(p.H0, nH) || !all_finite(p.H1, nH1) || !all_finite(p.psi_i, 2L * d))
-    return fail(ISM_ENONFINITE, "non-finite value in H0, H1 or psi_i");
-  if (p.objective == ISM_OBJ_OVERLAP && !all_finite(p.psi_f, 2L * d)) return fail(ISM_ENONFINITE, "non-finite psi_f");
-  if (p.objective == ISM_OBJ_OBSERVABLE && !all_finite(p.O, (long)d * d)) return fail(ISM_ENONFINITE, "non-finite O");
-  if (p.alpha && !all_finite(p.alpha, p.Nt)) return fail(ISM_ENONFINITE, "non-finite alpha");
-  auto symmetric = [d](const double* A) {
-    double s = 0.0;
-    for (long i = 0; i < (long)d * d; ++i) s = std::fmax(s, std::fabs(A[i]));
-    for (int i = 0; i < d; ++i)
-      for (int j = 0; j < i; ++j)
-        if (std::fabs(A[i * d + j] - A[j * d + i]) > 1e-12 * (s + 1e-300)) return false;
-    return true;
-  };
-  if (p.kind == ISM_H_DENSE && (!symmetric(p.H0) || !symmetric(p.H1)))
-    return fail(ISM_EINVAL, "dense H0 and H1 must be real symmetric");
-  if (p.objective == ISM_OBJ_OBSERVABLE && !symmetric(p.O)) return fail(ISM_EINVAL, "O must be real symmetric");
 
   ism_plan_s* P = new (std::nothrow) ism_plan_s();
   if (!P) return fail(ISM_ENOMEM, "host allocation");
@@ -367,9 +404,7 @@ int ism_plan(const ism_problem* prob, const ism_options* opt, void* cuda_stream,
   P->st = reinterpret_cast<cudaStream_t>(cuda_stream);
   cudaGetDevice(&P->dev);
 
-  bool ok = p.kind == ISM_H_TRIDIAG   ? ism::kernels_tridiag(P->prec, d, &P->ks)
-            : p.kind == ISM_H_BITFLIP ? ism::kernels_bitflip(P->prec, d, &P->ks)
-                                      : ism::kernels_dense(P->prec, d, &P->ks);
+  bool ok = ism::select_kernels(P->prec, p.kind, d, &P->ks);
   if (!ok) { delete P; return fail(ISM_EUNSUPPORTED, "no compiled kernel for this kind and d"); }
   const int gpw = 32 / P->ks.G;
   P->dpad = (d + gpw - 1) / gpw * gpw;

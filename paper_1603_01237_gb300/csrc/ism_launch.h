@@ -22,5 +22,22 @@ bool kernels_tridiag(int prec, int d, KernelSet* ks);
 bool kernels_bitflip(int prec, int d, KernelSet* ks);
 bool kernels_dense(int prec, int d, KernelSet* ks);
 cudaError_t launch_chain(int prec, const ChainParams& p, size_t smem, cudaStream_t st);
+bool select_kernels(int prec, int kind, int d, KernelSet* ks);
+
+}  // namespace ism
+
+#include <vector>
+#include "ism.h"
+
+namespace ism {
+
+// Host helpers shared by the entry points (defined in ism_api.cu).
+struct Bounds { double lo, hi, h1; };
+Bounds bounds_of(int kind, int d, const double* H0, const double* H1);
+template <typename R>
+std::vector<R> pack_op(int kind, int d, const double* H0, const double* H1, int G, int E);
+int validate_problem(const ism_problem& p, int precision);
+int set_error(int code, const char* msg);
+void clear_error();
 
 }  // namespace ism

@@ -1,0 +1,152 @@
+// ism_noalloc.cu -- ism_subinterval_grad_noalloc, the sub-interval gradient sweep for callers that
+// cannot allocate device memory.
+//
+// Some callers cannot call cudaMalloc where they need this gradient: code running inside another
+// framework's memory pool (the pool owns the device memory and a private cudaMalloc would bypass or
+// fragment it), allocation-free real-time loops, and processes whose device-memory budget is fixed up
+// front.  ism_plan allocates the sweep's scratch (the packed Hamiltonian, the partition and the per-step
+// H1 psi trajectory) with cudaMalloc; this entry point keeps all of it in one file-scope __device__
+// array of ISM_NOALLOC_SCRATCH_BYTES instead and never calls cudaMalloc, cudaFree or any allocating
+// library routine.  The caller passes device buffers for the inputs and outputs.
+//
+// The array is statically part of the module: every GPU that loads libism.so holds it until the
+// process exits.  All calls share it, and it keeps the last call's contents; the only word that must
+// start at zero (the status word) is cleared at the start of every call, everything else is written
+// before it is read.  Two calls whose work overlaps on the GPU (different streams, or different host
+// threads on one device) race on the array.
+#include <cstring>
+#include <mutex>
+#include <string>
+
+#include "ism.h"
+#include "ism_kernels.cuh"
+#include "ism_launch.h"
+
+namespace {
+
+constexpr size_t kScratchBytes = (size_t)ISM_NOALLOC_SCRATCH_BYTES;
+__device__ __align__(256) unsigned char g_scratch[kScratchBytes];
+
+// In host code `g_scratch` names a host-side stand-in, not a device address; the device address is
+// looked up once per device with that device current and kept here.
+constexpr int kMaxDevices = 128;
+std::mutex g_mu;
+unsigned char* g_scratch_dev[kMaxDevices] = {};
+
+int scratch_for_current_device(unsigned char** out) {
+  int dev = -1;
+  cudaError_t e = cudaGetDevice(&dev);
+  if (e != cudaSuccess) return ism::set_error(ISM_ECUDA, (std::string("cudaGetDevice: ") + cudaGetErrorString(e)).c_str());
+  if (dev < 0 || dev >= kMaxDevices) return ism::set_error(ISM_EUNSUPPORTED, "device ordinal beyond the static scratch table");
+  std::lock_guard<std::mutex> lock(g_mu);
+  if (!g_scratch_dev[dev]) {
+    void* p = nullptr;
+    e = cudaGetSymbolAddress(&p, g_scratch);
+    if (e != cudaSuccess || !p)
+      return ism::set_error(ISM_ECUDA, (std::string("cudaGetSymbolAddress(scratch): ") + cudaGetErrorString(e)).c_str());
+    g_scratch_dev[dev] = static_cast<unsigned char*>(p);
+  }
+  *out = g_scratch_dev[dev];
+  return ISM_OK;
+}
+
+bool is_device_ptr(const void* p) {
+  cudaPointerAttributes a;
+  if (cudaPointerGetAttributes(&a, p) != cudaSuccess) {
+    cudaGetLastError();
+    return false;
+  }
+  return a.type == cudaMemoryTypeDevice || a.type == cudaMemoryTypeManaged;
+}
+
+size_t up256(size_t x) { return (x + 255) & ~size_t(255); }
+
+}  // namespace
+
+extern "C" int ism_subinterval_grad_noalloc(const ism_problem* prob, int precision, const double* phi,
+                                            const double* u, double* grad, double* Jn, void* cuda_stream) {
+  if (!prob || !phi || !u || !grad) return ism::set_error(ISM_EINVAL, "null argument");
+  const ism_problem& p = *prob;
+  int rc = ism::validate_problem(p, precision);
+  if (rc != ISM_OK) return rc;
+  if (!is_device_ptr(phi) || !is_device_ptr(u) || !is_device_ptr(grad) || (Jn && !is_device_ptr(Jn)))
+    return ism::set_error(ISM_EINVAL, "phi, u, grad and Jn must be device memory for the allocation-free entry point");
+  ism::KernelSet ks;
+  if (!ism::select_kernels(precision, p.kind, p.d, &ks)) return ism::set_error(ISM_EUNSUPPORTED, "no compiled kernel for this kind and d");
+
+  const int d = p.d, B = p.batch < 1 ? 1 : p.batch, GE = ks.G * ks.E;
+  const size_t r1 = precision == ISM_FP64 ? sizeof(double) : sizeof(float);
+  const size_t r2 = 2 * r1;
+  std::vector<double> hd;
+  std::vector<float> hf;
+  size_t op_bytes;
+  if (precision == ISM_FP64) { hd = ism::pack_op<double>(p.kind, d, p.H0, p.H1, ks.G, ks.E); op_bytes = hd.size() * r1; }
+  else { hf = ism::pack_op<float>(p.kind, d, p.H0, p.H1, ks.G, ks.E); op_bytes = hf.size() * r1; }
+
+  // scratch layout: op data | j_n | beta_n | alpha | status | trajectory
+  const size_t off_jn = up256(op_bytes);
+  const size_t off_beta = off_jn + up256(sizeof(int) * (p.N + 1));
+  const size_t off_alpha = off_beta + up256(sizeof(double) * p.N);
+  const size_t off_status = off_alpha + up256(p.alpha ? sizeof(double) * p.Nt : 0);
+  const size_t off_traj = off_status + 256;
+  const size_t need = off_traj + up256((size_t)B * ((size_t)p.Nt + p.N) * GE * r2);
+  if (need > kScratchBytes) {
+    std::string m = "problem needs " + std::to_string(need) + " bytes of scratch; the static scratch of the "
+                    "allocation-free entry point holds " + std::to_string(kScratchBytes) + " bytes";
+    return ism::set_error(ISM_EINVAL, m.c_str());
+  }
+  unsigned char* base = nullptr;
+  if ((rc = scratch_for_current_device(&base)) != ISM_OK) return rc;
+
+  std::vector<int> jn(p.N + 1);
+  for (int n = 0; n <= p.N; ++n) jn[n] = (int)(((long long)n * p.Nt) / p.N);
+  const double tau = p.T / p.Nt;
+  std::vector<double> beta(p.N);
+  for (int n = 0; n < p.N; ++n) beta[n] = p.T / (jn[n + 1] * tau - jn[n] * tau);
+  ism::Bounds bd = ism::bounds_of(p.kind, d, p.H0, p.H1);
+
+  cudaStream_t st = reinterpret_cast<cudaStream_t>(cuda_stream);
+  cudaError_t e = cudaSuccess;
+  auto h2d = [&](size_t off, const void* src, size_t n) {
+    if (e == cudaSuccess && n) e = cudaMemcpyAsync(base + off, src, n, cudaMemcpyHostToDevice, st);
+  };
+  h2d(0, precision == ISM_FP64 ? (const void*)hd.data() : (const void*)hf.data(), op_bytes);
+  h2d(off_jn, jn.data(), sizeof(int) * jn.size());
+  h2d(off_beta, beta.data(), sizeof(double) * beta.size());
+  if (p.alpha) h2d(off_alpha, p.alpha, sizeof(double) * p.Nt);
+  if (e == cudaSuccess) e = cudaMemsetAsync(base + off_status, 0, sizeof(int), st);
+  if (e != cudaSuccess) return ism::set_error(ISM_ECUDA, (std::string("scratch upload: ") + cudaGetErrorString(e)).c_str());
+
+  ism::KParams k{};
+  k.d = d; k.Nt = p.Nt; k.N = p.N; k.B = B; k.ldm = d + (d & 1); k.dpad = d;
+  k.tau = tau; k.T = p.T; k.c0 = 0.5 * (bd.lo + bd.hi); k.r0 = 0.5 * (bd.hi - bd.lo); k.h1n = bd.h1;
+  k.tol = precision == ISM_FP64 ? 1e-17 : 1e-10;
+  k.rho = 0.0; k.w = p.objective == ISM_OBJ_OVERLAP ? 1.0 : 2.0;
+  k.jn = reinterpret_cast<const int*>(base + off_jn);
+  k.beta = reinterpret_cast<const double*>(base + off_beta);
+  k.alpha = p.alpha ? reinterpret_cast<const double*>(base + off_alpha) : nullptr;
+  k.H = base;
+  k.u = const_cast<double*>(u);
+  k.phi = reinterpret_cast<const double2*>(phi);
+  k.M = nullptr;
+  k.traj = base + off_traj;
+  k.grad = grad;
+  k.Jn = Jn;
+  k.err = nullptr;
+  k.status = reinterpret_cast<int*>(base + off_status);
+  k.count = nullptr;
+  k.update = 0;
+  k.max_spin = 1 << 22;
+  if ((e = ks.subinterval(k, st)) != cudaSuccess)
+    return ism::set_error(ISM_ECUDA, (std::string("launch: ") + cudaGetErrorString(e)).c_str());
+  if ((e = cudaStreamSynchronize(st)) != cudaSuccess)
+    return ism::set_error(ISM_ECUDA, (std::string("stream: ") + cudaGetErrorString(e)).c_str());
+  int status = 0;
+  if ((e = cudaMemcpy(&status, base + off_status, sizeof(int), cudaMemcpyDeviceToHost)) != cudaSuccess)
+    return ism::set_error(ISM_ECUDA, (std::string("status read: ") + cudaGetErrorString(e)).c_str());
+  if (status & ism::ST_TIMEOUT) return ism::set_error(ISM_ETIMEOUT, "a bounded device-side wait gave up");
+  if (status & ism::ST_KOVERFLOW) return ism::set_error(ISM_EUNSUPPORTED, "Chebyshev series needed more terms than compiled");
+  if (status & ism::ST_NONFINITE) return ism::set_error(ISM_ENONFINITE, "non-finite value in a control or a result");
+  ism::clear_error();
+  return ISM_OK;
+}
