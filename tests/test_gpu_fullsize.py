@@ -1,0 +1,62 @@
+"""Full-size parity against stored oracle values (tests/golden/*.json, written by make_golden.py,
+which calls only the oracle): the rotor benchmark problem, d=41, Nt=20000, N=128, 50 iterations."""
+import json
+import os
+
+import numpy as np
+import pytest
+
+import workloads as W
+
+pytestmark = pytest.mark.gpu
+GOLD = os.path.join(os.path.dirname(os.path.abspath(__file__)), "golden")
+
+
+@pytest.fixture(scope="module")
+def P():
+    import __graft_entry__
+
+    __graft_entry__.build()
+    import paper_1603_01237_gb300 as P
+
+    return P
+
+
+def _load(name):
+    with open(os.path.join(GOLD, name)) as f:
+        return json.load(f)
+
+
+@pytest.mark.parametrize("prec,tolJ,tolu", [("fp64", 1e-9, 1e-9), ("mixed", 1e-5, 1e-4)])
+@pytest.mark.parametrize("N", [16, 128])
+def test_rotor41_50_iterations(P, prec, tolJ, tolu, N):
+    """J[u^(k)] for k = 0..50 and sampled final controls; with one local step the iterates do not depend
+    on N (Theorem 2), so one oracle history serves N = 16 and 128."""
+    g = _load("rotor41.json")
+    w = W.config("rotor41", N=N)
+    with P.Plan(w, precision=prec) as pl:
+        u, J, E = pl.iterate(w.u0, g["iters"])
+        _, F = pl.evaluate(u[0])
+    J_o = np.array(g["J_hist"])
+    assert np.max(np.abs(J[0] - J_o)) <= tolJ, np.max(np.abs(J[0] - J_o))
+    assert abs(F[0] - g["F_hist"][-1]) <= tolJ
+    idx = np.array(g["u_final_idx"])
+    du = u[0][idx] - np.array(g["u_final"])
+    assert np.linalg.norm(du) <= tolu * np.linalg.norm(np.array(g["u_final"]) - w.u0[idx])
+
+
+@pytest.mark.parametrize("prec,tol", [("fp64", 1e-10), ("mixed", 1e-4)])
+def test_rotor41_first_subinterval_gradient(P, prec, tol):
+    """Sub-interval gradient (literal sub-problems) at u0 with the FP64 intermediate states."""
+    g = _load("rotor41_grad.json")
+    w = W.config("rotor41")
+    with P.Plan(w, precision="fp64") as pl:
+        phi = pl.intermediate_states(w.u0)
+    ref_re, ref_im = np.array(g["phi_re_sample"]), np.array(g["phi_im_sample"])
+    assert np.max(np.abs(phi[0][::8] - (ref_re + 1j * ref_im))) <= 1e-10
+    with P.Plan(w, precision=prec) as pl:
+        grad, Jn = pl.subinterval_grad(phi, w.u0)
+    idx = np.array(g["grad_idx"])
+    ref = np.array(g["grad"])
+    assert np.linalg.norm(grad[0][idx] - ref) <= tol * np.linalg.norm(ref)
+    assert abs(np.linalg.norm(grad[0]) - g["grad_l2"]) <= tol * g["grad_l2"]

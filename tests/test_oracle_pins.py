@@ -244,3 +244,24 @@ def test_rotor_reduced_step_size_is_monotone():
     w = W.config("rotor41", Nt=800, N=16)
     _, J, _, _ = O.ism_solve(w, w.u0, 4, w.rho)
     assert np.all(np.diff(J) > 0)
+
+
+# --------------------------------------------------------------------- large-d propagation route
+def test_large_d_route_matches_eigh(monkeypatch):
+    """For d > 64 the oracle applies each step with scipy's expm_multiply on the sparse H(u_j); on a
+    d = 64 problem both routes must agree, forward and adjoint."""
+    w = W.spin_chain(6, 5, T=2.0, Nt=40, N=4, u_amp=1.0)
+    p1 = O.forward_trajectory(w, w.u0)
+    c1 = O.backward_trajectory(w, w.u0, p1[-1])
+    monkeypatch.setattr(O, "DENSE_MAX", 32)
+    p2 = O.forward_trajectory(w, w.u0)
+    c2 = O.backward_trajectory(w, w.u0, p1[-1])
+    assert np.abs(p1 - p2).max() < 1e-12 and np.abs(c1 - c2).max() < 1e-12
+
+
+def test_ising1024_norm_and_reversibility():
+    w = W.config("ising1024", Nt=60, N=4)
+    p = O.forward_trajectory(w, w.u0)
+    assert np.allclose(np.linalg.norm(p, axis=1), 1.0, atol=1e-12)
+    back = O.backward_trajectory(w, w.u0, p[-1])
+    assert np.abs(back[0] - w.psi_i).max() < 1e-12

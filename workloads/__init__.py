@@ -36,6 +36,9 @@ __all__ = [
     "rabi",
     "config",
     "CONFIG_NAMES",
+    "GPWorkload",
+    "gp_bec",
+    "gp_stationary_states",
 ]
 
 
@@ -239,3 +242,94 @@ def config(name: str, *, N: Optional[int] = None, Nt: Optional[int] = None, iter
     else:
         raise KeyError(name)
     return w
+
+
+# ----------------------------------------------------------------------------------------------
+# Gross-Pitaevskii condensate on a periodic grid (Sec. 4, Bose-Einstein condensates)
+# ----------------------------------------------------------------------------------------------
+@dataclass
+class GPWorkload:
+    """1D GP problem: i d/dt psi = (-1/2 d^2/dx^2 + V(x, u) + g |psi|^2) psi on a periodic grid,
+    V(x, u) = (x - u)^2 / 2, maximise J = Re<psi(T)|psi_f> with <a|b> = sum conj(a) b dx."""
+
+    name: str
+    n: int              # grid points
+    L: float            # box length; x_k = x_min + k L / n
+    x_min: float
+    g: float
+    psi_i: np.ndarray   # (n,) complex128, normalised sum |psi|^2 dx = 1
+    psi_f: np.ndarray
+    T: float
+    Nt: int
+    N: int
+    u0: np.ndarray
+    iters: int = 20
+    rho: float = 0.1
+    local_iters: int = 1
+    precision: str = "mixed"
+    kind: str = "gp"
+    objective: str = "overlap"
+    alpha: Optional[np.ndarray] = None
+
+    @property
+    def dx(self) -> float:
+        return self.L / self.n
+
+    @property
+    def x(self) -> np.ndarray:
+        return self.x_min + np.arange(self.n) * self.dx
+
+    @property
+    def k(self) -> np.ndarray:
+        return 2.0 * np.pi * np.fft.fftfreq(self.n, d=self.dx)
+
+    @property
+    def tau(self) -> float:
+        return self.T / self.Nt
+
+    def with_(self, **kw) -> "GPWorkload":
+        import dataclasses
+
+        return dataclasses.replace(self, **kw)
+
+
+def gp_stationary_states(n: int, L: float, x_min: float, g: float, *, dt: float = 1e-3, steps: int = 40000):
+    """Ground state and lowest odd state of -1/2 d^2 + x^2/2 + g|psi|^2 on the periodic grid, by
+    imaginary-time split steps with renormalisation (the odd state also antisymmetrised about x = 0
+    and orthogonalised against the ground state at every step).  Model set-up only."""
+    x = x_min + np.arange(n) * (L / n)
+    dx = L / n
+    kk = 2.0 * np.pi * np.fft.fftfreq(n, d=dx)
+    half = np.exp(-0.25 * dt * kk ** 2)
+    V = 0.5 * x ** 2
+
+    def norm(v):
+        return v / np.sqrt(np.sum(np.abs(v) ** 2) * dx)
+
+    def mirror(v):   # v(-x) on the grid x_k = x_min + k dx with x_min = -L/2: index (n - k) mod n
+        return v[(-np.arange(n)) % n]
+
+    g0 = norm(np.exp(-0.5 * x ** 2).astype(np.complex128))
+    e1 = norm((x * np.exp(-0.5 * x ** 2)).astype(np.complex128))
+    for _ in range(steps):
+        g0 = np.fft.ifft(half * np.fft.fft(g0))
+        g0 = g0 * np.exp(-dt * (V + g * np.abs(g0) ** 2))
+        g0 = norm(np.fft.ifft(half * np.fft.fft(g0)))
+        e1 = np.fft.ifft(half * np.fft.fft(e1))
+        e1 = e1 * np.exp(-dt * (V + g * np.abs(e1) ** 2))
+        e1 = np.fft.ifft(half * np.fft.fft(e1))
+        e1 = 0.5 * (e1 - mirror(e1))
+        e1 = e1 - np.sum(np.conj(g0) * e1) * dx * g0
+        e1 = norm(e1)
+    return g0, e1
+
+
+def gp_bec(n: int = 512, seed: int = 1002, *, T: float = 8.0, Nt: int = 10000, N: int = 64, g: float = 1.0,
+           u_amp: float = 0.1, steps: int = 40000, name: str = "gp512") -> GPWorkload:
+    """Grid of n points on [-10, 10) (periodic), g = 1, T = 8, ground state -> lowest odd state,
+    u0 ~ U[-u_amp, u_amp] (the only random draw)."""
+    rng = np.random.default_rng(seed)
+    u0 = rng.uniform(-u_amp, u_amp, size=Nt)
+    L, x_min = 20.0, -10.0
+    psi_i, psi_f = gp_stationary_states(n, L, x_min, g, steps=steps)
+    return GPWorkload(name=name, n=n, L=L, x_min=x_min, g=g, psi_i=psi_i, psi_f=psi_f, T=T, Nt=Nt, N=N, u0=u0)
