@@ -58,7 +58,15 @@ typedef enum {
   ISM_H_BITFLIP = 1,
   /* H0, H1 symmetric tridiagonal: H[0..d-1] = diagonal, H[d..2d-2] = first off-diagonal
      (H[d+e] couples e and e+1).  d <= 64.                                                        */
-  ISM_H_TRIDIAG = 2
+  ISM_H_TRIDIAG = 2,
+  /* Gross-Pitaevskii condensate (Sec. 4): i d/dt psi = (-1/2 d^2/dx^2 + (x - u)^2/2 + g|psi|^2) psi on a
+     periodic grid of d = 64, 512 or 4096 points x_k = x_min + k L/d, Strang splitting (Eq. (OS)),
+     <a|b> = sum conj(a) b L/d.  H0 = {L, x_min, g}; H1 unused (may be NULL); overlap objective only,
+     alpha must be NULL.  The sub-problems are the nonlinear variant of Sec. 4: initial states
+     psi(t_n) on the forward trajectory, targets chi(t_n) on the adjoint trajectory (the discrete
+     adjoint of the full problem), J_n = Re<psi_n(t_{n+1})|chi(t_{n+1})>, ascent u += rho grad/tau.
+     phi arrays of the entry points hold both sets: [batch][2][N+1][2d] = psi(t_n), then chi(t_n). */
+  ISM_H_GRID_GP = 3
 } ism_hkind;
 
 typedef enum {
@@ -90,6 +98,14 @@ typedef struct {
   double cheb_tol;         /* truncation threshold of the Chebyshev series; 0 = default per
                               precision (1e-17 FP64, 1e-10 mixed)                                 */
   int max_spin_iters;      /* iteration cap for device-side waits; 0 = default                    */
+  int subproblem_form;     /* gradient of the first local step in ism_iterate:
+                              1 = literal sub-problem (psi_n from phi_n, chi_n from phi_{n+1});
+                              2 = the two-trajectory form of the proof of Theorem 2 (psi from psi(t_n),
+                                  chi from chi(t_{n+1}), scaled by 1/beta_n): identical at phi = phi^u
+                                  in exact arithmetic, and free of the O(1/N) cancellation of
+                                  phi_{n+1} - psi_n(t_{n+1}) that FP32 propagation cannot resolve;
+                              0 = default: 2 in ISM_MIXED, 1 in ISM_FP64.  Later local steps
+                              (L > 1) and ism_subinterval_grad always use the literal form.      */
 } ism_options;
 
 typedef struct ism_plan_s* ism_plan_t;

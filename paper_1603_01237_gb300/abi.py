@@ -16,7 +16,7 @@ LIB_PATH = os.path.join(os.path.dirname(os.path.abspath(__file__)), "libism.so")
 
 ISM_OK, ISM_EINVAL, ISM_ENOMEM, ISM_ECUDA, ISM_ENONFINITE, ISM_ETIMEOUT, ISM_EUNSUPPORTED = range(7)
 ISM_FP64, ISM_MIXED = 0, 1
-ISM_H_DENSE, ISM_H_BITFLIP, ISM_H_TRIDIAG = 0, 1, 2
+ISM_H_DENSE, ISM_H_BITFLIP, ISM_H_TRIDIAG, ISM_H_GRID_GP = 0, 1, 2, 3
 ISM_OBJ_OVERLAP, ISM_OBJ_OBSERVABLE = 0, 1
 
 STATUS_NAMES = {0: "ISM_OK", 1: "ISM_EINVAL", 2: "ISM_ENOMEM", 3: "ISM_ECUDA", 4: "ISM_ENONFINITE",
@@ -35,7 +35,7 @@ class IsmProblem(C.Structure):
 
 class IsmOptions(C.Structure):
     _fields_ = [("precision", C.c_int), ("local_iters", C.c_int), ("rho", C.c_double),
-                ("cheb_tol", C.c_double), ("max_spin_iters", C.c_int)]
+                ("cheb_tol", C.c_double), ("max_spin_iters", C.c_int), ("subproblem_form", C.c_int)]
 
 
 class IsmStats(C.Structure):
@@ -116,7 +116,7 @@ def _c128_interleaved(v) -> np.ndarray:
     return v.view(np.float64).copy()
 
 
-_KIND = {"dense": ISM_H_DENSE, "bitflip": ISM_H_BITFLIP, "tridiag": ISM_H_TRIDIAG}
+_KIND = {"dense": ISM_H_DENSE, "bitflip": ISM_H_BITFLIP, "tridiag": ISM_H_TRIDIAG, "gp": ISM_H_GRID_GP}
 
 
 def pack_hamiltonian(kind: str, H0: np.ndarray, H1: np.ndarray):
@@ -176,15 +176,20 @@ class Plan:
 
     def __init__(self, w, *, precision: str | None = None, batch: int = 1, stream=None,
                  local_iters: int | None = None, rho: float | None = None, kind: str | None = None,
-                 cheb_tol: float = 0.0):
+                 cheb_tol: float = 0.0, subproblem_form: int = 0):
         lib = load()
         self.w = w
         self.kind = kind or w.kind
         self.batch = int(batch)
-        self.d, self.Nt, self.N = int(w.d), int(w.Nt), int(w.N)
+        self.gp = self.kind == "gp"
+        self.d = int(w.n) if self.gp else int(w.d)
+        self.Nt, self.N = int(w.Nt), int(w.N)
         prec = precision or w.precision
         self.precision = prec
-        H0p, H1p = pack_hamiltonian(self.kind, w.H0, w.H1)
+        if self.gp:   # grid kind: H0 = {L, x_min, g}
+            H0p, H1p = np.array([w.L, w.x_min, w.g], dtype=np.float64), None
+        else:
+            H0p, H1p = pack_hamiltonian(self.kind, w.H0, w.H1)
         self._keep = [H0p, H1p, _c128_interleaved(w.psi_i)]
         psi_f = _c128_interleaved(w.psi_f) if w.objective == "overlap" else None
         O = np.ascontiguousarray(w.O, dtype=np.float64) if w.objective == "observable" else None
@@ -196,7 +201,7 @@ class Plan:
                           batch=self.batch)
         opt = IsmOptions(precision=ISM_FP64 if prec == "fp64" else ISM_MIXED,
                          local_iters=int(local_iters or w.local_iters), rho=float(w.rho if rho is None else rho),
-                         cheb_tol=float(cheb_tol), max_spin_iters=0)
+                         cheb_tol=float(cheb_tol), max_spin_iters=0, subproblem_form=int(subproblem_form))
         h = C.c_void_p()
         st = None
         if stream is not None:
@@ -234,14 +239,17 @@ class Plan:
         u = np.ascontiguousarray(np.asarray(u, dtype=np.float64))
         return np.ascontiguousarray(np.broadcast_to(u, (self.batch, self.Nt))).copy()
 
+    def _phi_shape(self):
+        return (self.batch, 2, self.N + 1, self.d) if self.gp else (self.batch, self.N + 1, self.d)
+
     def intermediate_states(self, u) -> np.ndarray:
-        phi = np.empty((self.batch, self.N + 1, self.d), dtype=np.complex128)
+        """phi_n (N+1, d) per problem; for the grid kind the pair sets (2, N+1, d): psi(t_n), chi(t_n)."""
+        phi = np.empty(self._phi_shape(), dtype=np.complex128)
         self.ism_intermediate_states(self._u(u), phi.view(np.float64))
         return phi
 
     def subinterval_grad(self, phi, u):
-        phi = np.ascontiguousarray(np.broadcast_to(np.asarray(phi, dtype=np.complex128),
-                                                   (self.batch, self.N + 1, self.d)))
+        phi = np.ascontiguousarray(np.broadcast_to(np.asarray(phi, dtype=np.complex128), self._phi_shape()))
         grad = np.empty((self.batch, self.Nt))
         Jn = np.empty((self.batch, self.N))
         self.ism_subinterval_grad(phi.view(np.float64), self._u(u), grad, Jn)

@@ -10,6 +10,7 @@
 #include "ism.h"
 #include "ism_kernels.cuh"
 #include "ism_launch.h"
+#include "ism_gp.h"
 
 namespace {
 
@@ -70,15 +71,21 @@ struct ism_plan_s {
   int d = 0, kind = 0, obj = 0, Nt = 0, N = 0, B = 1, prec = 0, L = 1;
   double T = 0, tau = 0, rho = 0, tol = 0, w = 1;
   int max_spin = 0;
+  int form = 1;   // sub-problem form in ism_iterate: 1 literal, 2 Theorem 2 (first local step)
+  bool gp = false;                       // grid (Gross-Pitaevskii) kind
+  double gpL = 0, gpxmin = 0, gpg = 0;   // its grid length, origin and nonlinearity
   double c0 = 0, r0 = 0, h1n = 0;
   ism::KernelSet ks;
   int ldm = 0, dpad = 0;
+  long tst = 0;
   size_t r2 = 0;  // bytes of one complex element of the propagation precision
   cudaStream_t st = nullptr;
   int dev = 0;
   void* dH = nullptr;
+  double* dH0d = nullptr;   // FP64 diagonal of H0
   int* djn = nullptr;
   double* dbeta = nullptr;
+  double2* dab = nullptr;   // (a_n, b_n), n = 0..N
   double* dalpha = nullptr;
   double* dO = nullptr;
   double2* dpsi_i = nullptr;
@@ -106,6 +113,7 @@ struct ism_plan_s {
   double ms[3] = {0, 0, 0};
   long long launches[3] = {0, 0, 0};
   size_t chain_smem = 0;
+  int chain_stages = 2;
   size_t bytes = 0;
   std::vector<void*> allocs;
 };
@@ -244,7 +252,17 @@ int validate_problem(const ism_problem& p, int precision) {
   if (p.N < 1 || p.N > p.Nt) return fail(ISM_EINVAL, "need 1 <= N <= Nt");
   if (!(p.T > 0.0) || !std::isfinite(p.T)) return fail(ISM_EINVAL, "T must be finite and > 0");
   if (p.batch < 0) return fail(ISM_EINVAL, "batch must be >= 0");
-  if (p.kind < ISM_H_DENSE || p.kind > ISM_H_TRIDIAG) return fail(ISM_EINVAL, "unknown Hamiltonian kind");
+  if (p.kind < ISM_H_DENSE || p.kind > ISM_H_GRID_GP) return fail(ISM_EINVAL, "unknown Hamiltonian kind");
+  if (p.kind == ISM_H_GRID_GP) {
+    if (!p.H0 || !p.psi_i || !p.psi_f) return fail(ISM_EINVAL, "the grid kind needs H0 = {L, x_min, g}, psi_i and psi_f");
+    if (p.objective != ISM_OBJ_OVERLAP) return fail(ISM_EINVAL, "the grid kind supports the overlap objective only");
+    if (p.alpha) return fail(ISM_EINVAL, "the grid kind has no control penalty (alpha must be NULL)");
+    if (precision != ISM_FP64 && precision != ISM_MIXED) return fail(ISM_EINVAL, "unknown precision");
+    if (!gp_supported(d)) return fail(ISM_EUNSUPPORTED, "the grid kind supports d = 64, 512 or 4096 points");
+    if (!all_finite(p.H0, 3) || !(p.H0[0] > 0.0)) return fail(ISM_EINVAL, "grid parameters must be finite with L > 0");
+    if (!all_finite(p.psi_i, 2L * d) || !all_finite(p.psi_f, 2L * d)) return fail(ISM_ENONFINITE, "non-finite psi_i or psi_f");
+    return ISM_OK;
+  }
   if (p.objective != ISM_OBJ_OVERLAP && p.objective != ISM_OBJ_OBSERVABLE) return fail(ISM_EINVAL, "unknown objective");
   if (!p.H0 || !p.H1 || !p.psi_i) return fail(ISM_EINVAL, "H0, H1 and psi_i are required");
   if (p.objective == ISM_OBJ_OVERLAP && !p.psi_f) return fail(ISM_EINVAL, "psi_f is required for the overlap objective");
@@ -300,6 +318,8 @@ int finish(ism_plan_s* P) {
   if (st & ism::ST_TIMEOUT) return fail(ISM_ETIMEOUT, "a bounded device-side wait gave up");
   if (st & ism::ST_KOVERFLOW) return fail(ISM_EUNSUPPORTED, "Chebyshev series needed more terms than compiled");
   if (st & ism::ST_NONFINITE) return fail(ISM_ENONFINITE, "non-finite value in a control or a result");
+  if (st & ism::ST_SPECTRUM)
+    return fail(ISM_EUNSUPPORTED, "controls so large that a time step needs more Chebyshev sub-steps than the limit");
   g_err.clear();
   return ISM_OK;
 }
@@ -312,27 +332,47 @@ int begin(ism_plan_s* P) {
 
 ism::KParams kparams(ism_plan_s* P, double* u) {
   ism::KParams k{};
-  k.d = P->d; k.Nt = P->Nt; k.N = P->N; k.B = P->B; k.ldm = P->ldm; k.dpad = P->dpad;
+  k.d = P->d; k.Nt = P->Nt; k.N = P->N; k.B = P->B; k.ldm = P->ldm; k.dpad = P->dpad; k.tile_stride = P->tst;
   k.tau = P->tau; k.T = P->T; k.c0 = P->c0; k.r0 = P->r0; k.h1n = P->h1n; k.tol = P->tol;
   k.rho = P->rho; k.w = P->w;
-  k.jn = P->djn; k.beta = P->dbeta; k.alpha = P->dalpha; k.H = P->dH;
+  k.jn = P->djn; k.beta = P->dbeta; k.alpha = P->dalpha; k.H = P->dH; k.H0d = P->dH0d;
   k.u = u; k.phi = P->dphi; k.M = P->dM; k.traj = P->dtraj;
   k.grad = P->dgrad; k.Jn = P->dJn; k.err = P->derr; k.status = P->dstatus;
   k.count = P->dcount;
+  k.psin = P->dpsin; k.chin = P->dchin; k.form = 0;
   k.update = 0; k.max_spin = P->max_spin;
   return k;
 }
 
+ism::GPParams gparams(ism_plan_s* P, double* u) {
+  ism::GPParams g{};
+  g.n = P->d; g.Nt = P->Nt; g.N = P->N; g.B = P->B;
+  g.tau = P->tau; g.T = P->T; g.L = P->gpL; g.xmin = P->gpxmin; g.dx = P->gpL / P->d; g.g = P->gpg; g.rho = P->rho;
+  g.jn = P->djn; g.u = u; g.psi_i = P->dpsi_i; g.psi_f = P->dpsi_f; g.traj = P->dtraj;
+  g.psin = P->dpsin; g.chin = P->dchin; g.grad = P->dgrad; g.Jn = P->dJn; g.err = P->derr;
+  g.J = P->dJ; g.F = P->dF; g.Jhist = nullptr; g.hist_stride = 0; g.hist_k = 0;
+  g.status = P->dstatus; g.count = P->dcount; g.update = 0;
+  return g;
+}
+
 // a-b of Algorithm 1: assemble M_n, chain, phi, J/F (optionally into Jhist[.][hist_k]).
 int run_states(ism_plan_s* P, const double* u, double* Jhist, int hist_stride, int hist_k) {
+  if (P->gp) {   // nonlinear: sequential forward sweep (psi(t_n), J) then adjoint sweep (chi(t_n))
+    ism::GPParams g = gparams(P, const_cast<double*>(u));
+    g.Jhist = Jhist; g.hist_stride = hist_stride; g.hist_k = hist_k;
+    ISM_CUDA_TRY(timed(P, 0, [&] { return ism::launch_gp_forward(P->prec, g, P->st); }));
+    g.count = P->dcount + 1;
+    ISM_CUDA_TRY(timed(P, 1, [&] { return ism::launch_gp_adjoint(P->prec, g, P->st); }));
+    return ISM_OK;
+  }
   ism::KParams k = kparams(P, const_cast<double*>(u));
   ISM_CUDA_TRY(timed(P, 0, [&] { return P->ks.assemble(k, P->st); }));
   ism::ChainParams c{};
   c.d = P->d; c.Nt = P->Nt; c.N = P->N; c.B = P->B; c.ldm = P->ldm; c.obj = P->obj;
   c.tau = P->tau; c.T = P->T; c.M = P->dM; c.psi_i = P->dpsi_i; c.psi_f = P->dpsi_f; c.O = P->dO;
-  c.alpha = P->dalpha; c.u = u; c.jn = P->djn; c.psin = P->dpsin; c.chin = P->dchin; c.phi = P->dphi;
+  c.alpha = P->dalpha; c.u = u; c.jn = P->djn; c.ab = P->dab; c.psin = P->dpsin; c.chin = P->dchin; c.phi = P->dphi;
   c.J = P->dJ; c.F = P->dF; c.Jhist = Jhist; c.hist_stride = hist_stride; c.hist_k = hist_k;
-  c.status = P->dstatus; c.max_spin = P->max_spin;
+  c.status = P->dstatus; c.max_spin = P->max_spin; c.stages = P->chain_stages; c.tile_stride = P->tst;
   ISM_CUDA_TRY(timed(P, 1, [&] { return ism::launch_chain(P->prec, c, P->chain_smem, P->st); }));
   return ISM_OK;
 }
@@ -392,6 +432,7 @@ int ism_plan(const ism_problem* prob, const ism_options* opt, void* cuda_stream,
   if (opt->local_iters < 0) return fail(ISM_EINVAL, "local_iters must be >= 1");
   if (!(opt->rho >= 0.0) || !std::isfinite(opt->rho)) return fail(ISM_EINVAL, "rho must be finite and >= 0");
   if (opt->cheb_tol < 0.0) return fail(ISM_EINVAL, "cheb_tol must be >= 0");
+  if (opt->subproblem_form < 0 || opt->subproblem_form > 2) return fail(ISM_EINVAL, "subproblem_form must be 0, 1 or 2");
 
   ism_plan_s* P = new (std::nothrow) ism_plan_s();
   if (!P) return fail(ISM_ENOMEM, "host allocation");
@@ -401,14 +442,59 @@ int ism_plan(const ism_problem* prob, const ism_options* opt, void* cuda_stream,
   P->tol = opt->cheb_tol > 0 ? opt->cheb_tol : (P->prec == ISM_FP64 ? 1e-17 : 1e-10);
   P->w = p.objective == ISM_OBJ_OVERLAP ? 1.0 : 2.0;
   P->max_spin = opt->max_spin_iters > 0 ? opt->max_spin_iters : (1 << 22);
+  P->form = opt->subproblem_form != 0 ? opt->subproblem_form : (P->prec == ISM_MIXED ? 2 : 1);
   P->st = reinterpret_cast<cudaStream_t>(cuda_stream);
   cudaGetDevice(&P->dev);
 
+  if (p.kind == ISM_H_GRID_GP) {
+    P->gp = true;
+    P->gpL = p.H0[0];
+    P->gpxmin = p.H0[1];
+    P->gpg = p.H0[2];
+    P->r2 = P->prec == ISM_FP64 ? sizeof(double2) : sizeof(float2);
+    std::vector<int> jn(P->N + 1);
+    for (int n = 0; n <= P->N; ++n) jn[n] = (int)(((long long)n * P->Nt) / P->N);
+    int rc = ISM_OK;
+    const size_t B = P->B;
+#define TRY_GP(ptr, n) if ((rc = dalloc(P, &(ptr), (n))) != ISM_OK) { free_all(P); delete P; return rc; }
+    unsigned char* dTb = nullptr;
+    TRY_GP(dTb, B * ((size_t)P->Nt + 1) * d * P->r2);
+    P->dtraj = dTb;
+    TRY_GP(P->djn, (size_t)P->N + 1);
+    TRY_GP(P->dpsi_i, (size_t)d);
+    TRY_GP(P->dpsi_f, (size_t)d);
+    TRY_GP(P->dpsin, B * (P->N + 1) * (size_t)d);
+    TRY_GP(P->dchin, B * (P->N + 1) * (size_t)d);
+    TRY_GP(P->du, B * P->Nt);
+    TRY_GP(P->dgrad, B * P->Nt);
+    TRY_GP(P->dJn, B * P->N);
+    TRY_GP(P->derr, B * P->N);
+    TRY_GP(P->dJ, B);
+    TRY_GP(P->dF, B);
+    TRY_GP(P->dstatus, 1);
+    TRY_GP(P->dcount, 6);
+#undef TRY_GP
+    cudaError_t e = cudaMemcpy(P->djn, jn.data(), jn.size() * sizeof(int), cudaMemcpyHostToDevice);
+    if (e == cudaSuccess) e = cudaMemcpy(P->dpsi_i, p.psi_i, 2 * sizeof(double) * d, cudaMemcpyHostToDevice);
+    if (e == cudaSuccess) e = cudaMemcpy(P->dpsi_f, p.psi_f, 2 * sizeof(double) * d, cudaMemcpyHostToDevice);
+    if (e == cudaSuccess) e = cudaMemset(P->dstatus, 0, sizeof(int));
+    if (e == cudaSuccess) e = cudaMemset(P->dcount, 0, 6 * sizeof(unsigned long long));
+    if (e != cudaSuccess) {
+      free_all(P);
+      delete P;
+      return fail(ISM_ECUDA, std::string("plan upload: ") + cudaGetErrorString(e));
+    }
+    *out = P;
+    g_err.clear();
+    return ISM_OK;
+  }
+
   bool ok = ism::select_kernels(P->prec, p.kind, d, &P->ks);
   if (!ok) { delete P; return fail(ISM_EUNSUPPORTED, "no compiled kernel for this kind and d"); }
-  const int gpw = 32 / P->ks.G;
+  const int gpw = 32 / P->ks.GA;
   P->dpad = (d + gpw - 1) / gpw * gpw;
-  P->ldm = d + (d & 1);
+  P->ldm = d | 1;                                   // odd column stride
+  P->tst = ((long)d * P->ldm + 1) / 2 * 2;          // even tile stride: tiles are multiples of 16 bytes
   P->r2 = P->prec == ISM_FP64 ? sizeof(double2) : sizeof(float2);
 
   Bounds bd = bounds_of(p.kind, d, p.H0, p.H1);
@@ -434,14 +520,16 @@ int ism_plan(const ism_problem* prob, const ism_options* opt, void* cuda_stream,
   else { hf = pack_op<float>(p.kind, d, p.H0, p.H1, P->ks.G, P->ks.E); hbytes = hf.size() * sizeof(float); }
   TRY_ALLOC(dHb, hbytes);
   P->dH = dHb;
+  TRY_ALLOC(P->dH0d, (size_t)d);
   TRY_ALLOC(P->djn, (size_t)P->N + 1);
   TRY_ALLOC(P->dbeta, (size_t)P->N);
+  TRY_ALLOC(P->dab, (size_t)P->N + 1);
   if (p.alpha) TRY_ALLOC(P->dalpha, (size_t)P->Nt);
   TRY_ALLOC(P->dpsi_i, (size_t)d);
   TRY_ALLOC(P->dpsi_f, (size_t)d);
   if (p.objective == ISM_OBJ_OBSERVABLE) TRY_ALLOC(P->dO, (size_t)d * d);
   unsigned char* dMb = nullptr;
-  TRY_ALLOC(dMb, B * P->N * (size_t)d * P->ldm * P->r2);
+  TRY_ALLOC(dMb, B * P->N * (size_t)P->tst * P->r2);
   P->dM = dMb;
   TRY_ALLOC(P->dpsin, B * (P->N + 1) * (size_t)d);
   TRY_ALLOC(P->dchin, B * (P->N + 1) * (size_t)d);
@@ -464,8 +552,21 @@ int ism_plan(const ism_problem* prob, const ism_options* opt, void* cuda_stream,
     if (e == cudaSuccess) e = cudaMemcpy(dst, src, n, cudaMemcpyHostToDevice);
   };
   h2d(P->dH, P->prec == ISM_FP64 ? (const void*)hd.data() : (const void*)hf.data(), hbytes);
+  {
+    std::vector<double> h0d(d);
+    for (int e = 0; e < d; ++e) h0d[e] = p.kind == ISM_H_DENSE ? p.H0[(size_t)e * d + e] : p.H0[e];
+    h2d(P->dH0d, h0d.data(), d * sizeof(double));
+  }
   h2d(P->djn, jn.data(), jn.size() * sizeof(int));
   h2d(P->dbeta, beta.data(), beta.size() * sizeof(double));
+  {
+    std::vector<double2> ab(P->N + 1);   // Eq. (cible): a_n = (T - t_n)/T, b_n = t_n/T
+    for (int n = 0; n <= P->N; ++n) {
+      const double tn = jn[n] * P->tau;
+      ab[n] = make_double2((P->T - tn) / P->T, tn / P->T);
+    }
+    h2d(P->dab, ab.data(), ab.size() * sizeof(double2));
+  }
   if (p.alpha) h2d(P->dalpha, p.alpha, P->Nt * sizeof(double));
   h2d(P->dpsi_i, p.psi_i, 2 * sizeof(double) * d);
   if (p.objective == ISM_OBJ_OVERLAP) h2d(P->dpsi_f, p.psi_f, 2 * sizeof(double) * d);
@@ -478,7 +579,13 @@ int ism_plan(const ism_problem* prob, const ism_options* opt, void* cuda_stream,
     delete P;
     return fail(ISM_ECUDA, std::string("plan upload: ") + cudaGetErrorString(e));
   }
-  P->chain_smem = 2 * (size_t)d * P->ldm * P->r2 + 2 * 64 * P->r2;
+  {
+    // one ring of as many tile stages as fit in ~200 KB (1..16)
+    const size_t tile = (size_t)P->tst * P->r2, budget = 200 * 1024;
+    int st = (int)(budget / tile);
+    P->chain_stages = st < 1 ? 1 : (st > 16 ? 16 : st);
+    P->chain_smem = P->chain_stages * tile;
+  }
   *out = P;
   g_err.clear();
   return ISM_OK;
@@ -533,6 +640,13 @@ int ism_intermediate_states(ism_plan_t P, const double* u, double* phi) {
   const double* ud = nullptr;
   if ((rc = stage_in(P, u, (long)P->B * P->Nt, P->du, &ud, true))) return rc;
   if ((rc = run_states(P, ud, nullptr, 0, 0))) return rc;
+  if (P->gp) {
+    const size_t blk = 2 * sizeof(double) * (size_t)(P->N + 1) * P->d;   // one set of N+1 states
+    ISM_CUDA_TRY(cudaMemcpy2DAsync(phi, 2 * blk, P->dpsin, blk, blk, P->B, cudaMemcpyDefault, P->st));
+    ISM_CUDA_TRY(cudaMemcpy2DAsync(reinterpret_cast<char*>(phi) + blk, 2 * blk, P->dchin, blk, blk, P->B,
+                                   cudaMemcpyDefault, P->st));
+    return finish(P);
+  }
   if ((rc = copy_out(P, phi, P->dphi, 2L * P->B * (P->N + 1) * P->d))) return rc;
   return finish(P);
 }
@@ -543,6 +657,20 @@ int ism_subinterval_grad(ism_plan_t P, const double* phi, const double* u, doubl
   if (rc) return rc;
   const double* ud = nullptr;
   if ((rc = stage_in(P, u, (long)P->B * P->Nt, P->du, &ud, true))) return rc;
+  if (P->gp) {
+    const size_t blk = 2 * sizeof(double) * (size_t)(P->N + 1) * P->d;
+    if (!is_device_ptr(phi) && !all_finite(phi, 4L * P->B * (P->N + 1) * P->d))
+      return fail(ISM_ENONFINITE, "non-finite value in phi");
+    ISM_CUDA_TRY(cudaMemcpy2DAsync(P->dpsin, blk, phi, 2 * blk, blk, P->B, cudaMemcpyDefault, P->st));
+    ISM_CUDA_TRY(cudaMemcpy2DAsync(P->dchin, blk, reinterpret_cast<const char*>(phi) + blk, 2 * blk, blk, P->B,
+                                   cudaMemcpyDefault, P->st));
+    ism::GPParams g = gparams(P, const_cast<double*>(ud));
+    g.count = P->dcount + 3;
+    ISM_CUDA_TRY(timed(P, 2, [&] { return ism::launch_gp_sub(P->prec, g, P->st); }));
+    if ((rc = copy_out(P, grad, P->dgrad, (long)P->B * P->Nt))) return rc;
+    if ((rc = copy_out(P, Jn, P->dJn, (long)P->B * P->N))) return rc;
+    return finish(P);
+  }
   const long nphi = 2L * P->B * (P->N + 1) * P->d;
   if (is_device_ptr(phi)) {
     ISM_CUDA_TRY(cudaMemcpyAsync(P->dphi, phi, nphi * sizeof(double), cudaMemcpyDeviceToDevice, P->st));
@@ -580,9 +708,18 @@ int ism_iterate(ism_plan_t P, int iters, double* u_inout, double* J_hist, double
   if ((J_hist || err_hist) && (rc = ensure_hist(P, stride))) return rc;
   for (int it = 0; it < iters; ++it) {
     if ((rc = run_states(P, ud, J_hist ? P->dJhist : nullptr, (int)stride, it))) return rc;
-    for (int l = 0; l < P->L; ++l) {
+    for (int l = 0; l < P->L && P->gp; ++l) {
+      ism::GPParams g = gparams(P, ud);
+      g.update = 1;
+      g.err = l == 0 ? P->derr : nullptr;
+      g.Jn = l == 0 ? P->dJn : nullptr;
+      g.count = P->dcount + 3;
+      ISM_CUDA_TRY(timed(P, 2, [&] { return ism::launch_gp_sub(P->prec, g, P->st); }));
+    }
+    for (int l = 0; l < P->L && !P->gp; ++l) {
       ism::KParams k = kparams(P, ud);
       k.update = 1;
+      k.form = (l == 0 && P->form == 2) ? 1 : 0;
       k.err = l == 0 ? P->derr : nullptr;
       k.Jn = l == 0 ? P->dJn : nullptr;
       k.count = P->dcount + 3;

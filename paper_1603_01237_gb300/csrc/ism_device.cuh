@@ -9,9 +9,14 @@
 // Chebyshev expansion of the exponential (Jacobi-Anger):
 //     exp(-i x Y) = sum_k a_k (-i)^k T_k(Y),  a_0 = J_0(x), a_k = 2 J_k(x),
 // with Y = (H - c)/rad scaled into [-1, 1] (c, rad from Gershgorin bounds of H0 and H1 and the
-// largest |u| of the sub-interval), x = tau * rad, T_{k+1} = 2 Y T_k - T_{k-1}, and the global phase
-// exp(-i tau c).  J_k(x) is summed from its power series (Abramowitz & Stegun 9.1.10) in FP64.
-// The adjoint step U_j^H uses (+i)^k and exp(+i tau c).
+// largest |u| of the sub-interval), x = tau * rad, T_{k+1} = 2 Y T_k - T_{k-1}.  J_k(x) is summed from
+// its power series (Abramowitz & Stegun 9.1.10) in FP64.  The adjoint step U_j^H uses (+i)^k.
+//
+// The global phase exp(-i tau c) of every step is NOT applied here: callers apply the accumulated
+// phase exp(-i c t) of a whole segment once, in FP64.  In FP32 propagation the rounding of a per-step
+// phase, of the large diagonal (H0_ee - c)/rad and of the leading coefficients a_0, a_1 is the same at
+// every step, so it would grow linearly with the number of steps; here those quantities are held as
+// FP32 (hi, lo) pairs computed in FP64, and only rounding that varies from step to step remains.
 #pragma once
 #include <cuda_runtime.h>
 #include <stdint.h>
@@ -20,11 +25,13 @@ namespace ism {
 
 constexpr int KMAX = 32;        // Chebyshev terms held per group
 constexpr double XMAX = 4.0;    // largest tau*rad per sub-step (more -> sub-steps)
+constexpr int SMAX = 64;        // sub-steps per time step before a plan reports ST_SPECTRUM
 
 enum StatusBits : int {
   ST_TIMEOUT = 1,      // a bounded mbarrier wait gave up
   ST_KOVERFLOW = 2,    // Chebyshev series needed more than KMAX terms
   ST_NONFINITE = 4,    // NaN/Inf met in a control or a result
+  ST_SPECTRUM = 8,     // tau * spectral radius beyond SMAX sub-steps (controls too large)
 };
 
 template <typename R> struct C2;
@@ -73,11 +80,20 @@ __device__ inline double bessel_jk(int k, double x) {
 // in: even k -> a_k (-1)^(k/2) multiplies the vector itself, odd k -> a_k (-1)^((k-1)/2) multiplies
 // -i times the vector (forward); the adjoint flips the odd terms.
 template <typename R> struct Cheb {
-  R cf[KMAX];
-  R cph, sph;       // cos, sin of tau_s * c
-  R c, inv_rad;     // spectral centre and 1/rad
+  R cf[KMAX];       // signed a_k (used for k >= 2), high part
+  R cl[KMAX];       // low part (FP32 only: the rounding of a_k would repeat at every step)
+  R a0h, a0l;       // a_0 as hi + lo
+  R c0h, c0l;       // a_0 - 1 as hi + lo (compensated step)
+  R a1h, a1l;       // signed a_1 as hi + lo
+  R c, inv_rad;     // spectral centre and 1/rad (FP32 copies)
+  double cd, s2d;   // spectral centre and 2/rad in FP64
   int K, S;         // terms, sub-steps per time step
 };
+
+template <typename R> __device__ __forceinline__ void split2(double v, R& hi, R& lo) {
+  hi = (R)v;
+  lo = sizeof(R) == 4 ? (R)(v - (double)hi) : R(0);
+}
 
 // Fill `ch` for a group whose controls satisfy |u| <= umax.  All lanes of the warp must call this
 // (K and S are made warp-uniform).  lg = lane in group.
@@ -86,8 +102,12 @@ __device__ void cheb_setup(Cheb<R>& ch, int lg, double tau, double c0, double r0
                           double umax, double tol, int* status) {
   double rad = (r0 + umax * h1n) * (1.0 + 1e-12) + 1e-12;
   double x = tau * rad;
-  int S = (int)ceil(x / XMAX);
+  int S = x < XMAX * SMAX ? (int)ceil(x / XMAX) : SMAX + 1;
   if (S < 1) S = 1;
+  if (S > SMAX) {   // |u| beyond what the sub-step budget covers: flag it and keep the work bounded
+    if (lg == 0) atomicOr(status, ST_SPECTRUM);
+    S = SMAX;
+  }
   S = warp_max_i(S);
   const double xs = x / (double)S;
   int kneed = 0;
@@ -95,19 +115,29 @@ __device__ void cheb_setup(Cheb<R>& ch, int lg, double tau, double c0, double r0
     double a = bessel_jk(k, xs) * (k == 0 ? 1.0 : 2.0);
     if (fabs(a) >= tol) kneed = k + 1 > kneed ? k + 1 : kneed;
     double sg = ((k >> 1) & 1) ? -1.0 : 1.0;   // (-1)^(k/2) for even k, (-1)^((k-1)/2) for odd k
-    ch.cf[k] = (R)(sg * a);
+    split2<R>(sg * a, ch.cf[k], ch.cl[k]);
   }
   kneed = g_max<G>(kneed);
   if (kneed >= KMAX && lg == 0) atomicOr(status, ST_KOVERFLOW);
   int K = kneed < 2 ? 2 : kneed;
   K = warp_max_i(K);
   if (lg == 0) {
-    double sn, cs;
-    sincos(tau / (double)S * c0, &sn, &cs);
-    ch.cph = (R)cs;
-    ch.sph = (R)sn;
+    // a_0 - 1 from its own series (no cancellation): sum_{m>=1} (-1)^m (x/2)^(2m) / (m!)^2
+    const double h2 = 0.25 * xs * xs;
+    double t = 1.0, j0m1 = 0.0;
+    for (int m = 1; m < 60; ++m) {
+      t *= -h2 / ((double)m * (double)m);
+      j0m1 += t;
+      if (fabs(t) <= 1e-18 * fabs(j0m1)) break;
+    }
+    const double a1 = 2.0 * bessel_jk(1, xs);
+    split2<R>(1.0 + j0m1, ch.a0h, ch.a0l);
+    split2<R>(j0m1, ch.c0h, ch.c0l);
+    split2<R>(a1, ch.a1h, ch.a1l);
     ch.c = (R)c0;
     ch.inv_rad = (R)(1.0 / rad);
+    ch.cd = c0;
+    ch.s2d = 2.0 / rad;
     ch.K = K;
     ch.S = S;
   }
@@ -127,28 +157,40 @@ __device__ void cheb_setup(Cheb<R>& ch, int lg, double tau, double c0, double r0
 template <typename R, int G_, int E_>
 struct OpTridiag {
   static constexpr int G = G_, E = E_, DP_SMEM = 0;
-  R d0[E], d1[E], o0[E], o1[E];
-  R yd[E], yo[E], yom;   // 2Y diagonal, 2Y off-diagonal (e, e+1), 2Y off-diagonal (e0-1, e0)
+  R d1[E], o0[E], o1[E];
+  R ah[E], al[E];        // 2(H0_ee - c)/rad as hi + lo (FP64 set-up)
+  R yb[E], yo[E], yom;   // 2u H1_ee/rad, 2Y off-diagonal (e, e+1), 2Y off-diagonal (e0-1, e0)
   R h1m;                  // H1 off-diagonal (e0-1, e0)
+  bool hasb;              // H1 has a diagonal
 
-  __device__ void load(const R* H, int d, int lg, void*) {
+  // H: packed op data in R; H0d: FP64 diagonal of H0
+  __device__ void load(const R* H, const double* H0d, int d, int lg, void*) {
+    bool any = false;
 #pragma unroll
     for (int r = 0; r < E; ++r) {
       int e = lg * E + r;
       bool in = e < d;
-      d0[r] = in ? H[e] : R(0);
       o0[r] = in ? H[d + e] : R(0);
       d1[r] = in ? H[2 * d + e] : R(0);
       o1[r] = in ? H[3 * d + e] : R(0);
+      any |= d1[r] != R(0);
     }
+    hasb = __any_sync(0xffffffffu, any);
     R t = g_up<G>(o1[E - 1]);
     h1m = lg == 0 ? R(0) : t;
+  }
+  __device__ void scale(const double* H0d, int d, int lg, const Cheb<R>& ch) {
+#pragma unroll
+    for (int r = 0; r < E; ++r) {
+      int e = lg * E + r;
+      split2<R>(e < d ? (H0d[e] - ch.cd) * ch.s2d : 0.0, ah[r], al[r]);
+    }
   }
   __device__ __forceinline__ void set_u(R u, const Cheb<R>& ch, int lg) {
     const R s2 = R(2) * ch.inv_rad;
 #pragma unroll
     for (int r = 0; r < E; ++r) {
-      yd[r] = (d0[r] + u * d1[r] - ch.c) * s2;
+      yb[r] = u * d1[r] * s2;
       yo[r] = (o0[r] + u * o1[r]) * s2;
     }
     R t = g_up<G>(yo[E - 1]);
@@ -163,8 +205,12 @@ struct OpTridiag {
       R mre = r == 0 ? lre : in.re[r - 1], mim = r == 0 ? lim : in.im[r - 1];
       R pre = r == E - 1 ? rre : in.re[r + 1], pim = r == E - 1 ? rim : in.im[r + 1];
       R ym = r == 0 ? yom : yo[r - 1];
-      out.re[r] = fma(yd[r], in.re[r], fma(ym, mre, fma(yo[r], pre, -sub.re[r])));
-      out.im[r] = fma(yd[r], in.im[r], fma(ym, mim, fma(yo[r], pim, -sub.im[r])));
+      R xr = fma(ym, mre, fma(yo[r], pre, -sub.re[r]));
+      R xi = fma(ym, mim, fma(yo[r], pim, -sub.im[r]));
+      if (sizeof(R) == 4) { xr = fma(al[r], in.re[r], xr); xi = fma(al[r], in.im[r], xi); }
+      if (hasb) { xr = fma(yb[r], in.re[r], xr); xi = fma(yb[r], in.im[r], xi); }
+      out.re[r] = fma(ah[r], in.re[r], xr);
+      out.im[r] = fma(ah[r], in.im[r], xi);
     }
   }
   template <class V>
@@ -189,20 +235,20 @@ template <typename R, int G_, int E_>
 struct OpBitflip {
   static constexpr int G = G_, E = E_, DP_SMEM = 0;
   static constexpr int LE = Log2<E>::v, LG = Log2<G>::v, Q = LE + LG;
-  R d0[E], yd[E];
+  R ah[E], al[E];        // 2(H0_ee - c)/rad as hi + lo
   R h[Q > 0 ? Q : 1];
   R yh[Q > 0 ? Q : 1];
 
-  __device__ void load(const R* H, int d, int lg, void*) {
-#pragma unroll
-    for (int r = 0; r < E; ++r) d0[r] = H[lg * E + r];
+  __device__ void load(const R* H, const double*, int d, int lg, void*) {
 #pragma unroll
     for (int i = 0; i < Q; ++i) h[i] = H[d + i];
   }
+  __device__ void scale(const double* H0d, int d, int lg, const Cheb<R>& ch) {
+#pragma unroll
+    for (int r = 0; r < E; ++r) split2<R>((H0d[lg * E + r] - ch.cd) * ch.s2d, ah[r], al[r]);
+  }
   __device__ __forceinline__ void set_u(R u, const Cheb<R>& ch, int) {
     const R s2 = R(2) * ch.inv_rad;
-#pragma unroll
-    for (int r = 0; r < E; ++r) yd[r] = (d0[r] - ch.c) * s2;
 #pragma unroll
     for (int i = 0; i < Q; ++i) yh[i] = u * h[i] * s2;
   }
@@ -229,12 +275,16 @@ struct OpBitflip {
   }
   template <class V>
   __device__ __forceinline__ void rec(const V& in, const V& sub, V& out) const {
+    V t;
 #pragma unroll
     for (int r = 0; r < E; ++r) {
-      out.re[r] = fma(yd[r], in.re[r], -sub.re[r]);
-      out.im[r] = fma(yd[r], in.im[r], -sub.im[r]);
+      R xr = -sub.re[r], xi = -sub.im[r];
+      if (sizeof(R) == 4) { xr = fma(al[r], in.re[r], xr); xi = fma(al[r], in.im[r], xi); }
+      t.re[r] = fma(ah[r], in.re[r], xr);
+      t.im[r] = fma(ah[r], in.im[r], xi);
     }
-    flips(in, out, yh);
+    flips(in, t, yh);
+    out = t;
   }
   template <class V>
   __device__ __forceinline__ void h1(const V& in, V& out) const {
@@ -254,10 +304,11 @@ struct OpDense {
   int lg;
   R s2h, u2, cs2; // 2/rad, 2u/rad, 2c/rad
 
-  __device__ void load(const R*, int, int lg_, void* smem) {
+  __device__ void load(const R*, const double*, int, int lg_, void* smem) {
     Hs = reinterpret_cast<const R2*>(smem);
     lg = lg_;
   }
+  __device__ void scale(const double*, int, int, const Cheb<R>&) {}
   __device__ __forceinline__ void set_u(R u, const Cheb<R>& ch, int) {
     s2h = R(2) * ch.inv_rad;
     u2 = u * s2h;
@@ -302,8 +353,14 @@ struct OpDense {
 
 // ------------------------------------------------------------------ Chebyshev propagator step
 // v <- U v (ADJ = false) or U^H v (ADJ = true) for the op's current u.  Warp-uniform control flow.
-template <bool ADJ, typename R, int E, class Op>
-__device__ __forceinline__ void cheb_step(Vec<R, E>& v, const Op& op, const Cheb<R>& ch) {
+//
+// COMP (FP32 propagation): the state is carried as hi + lo.  One sub-step is written as
+// v_new = v + Delta with Delta = (a_0 - 1) v + sum_{k>=1} a_k (-i)^k T_k(Y) v, a quantity of size
+// ~x|v| whose rounding error is ~eps x |v|; hi + (Delta + lo) is then formed by an error-free
+// two-sum.  This cuts the per-step FP32 rounding from ~eps(1+x)|v| to ~eps x |v| (x = tau*rad per
+// sub-step).  The coefficients a_0 - 1 (COMP) or a_0 and a_1 enter as hi + lo pairs.
+template <bool ADJ, bool COMP, typename R, int E, class Op>
+__device__ __forceinline__ void cheb_step(Vec<R, E>& v, Vec<R, E>& lo, const Op& op, const Cheb<R>& ch) {
   const int K = ch.K;
   for (int s = 0; s < ch.S; ++s) {
     Vec<R, E> t0 = v, t1, acc;
@@ -313,62 +370,74 @@ __device__ __forceinline__ void cheb_step(Vec<R, E>& v, const Op& op, const Cheb
     op.rec(t0, zero, t1);   // t1 = 2 Y t0
 #pragma unroll
     for (int r = 0; r < E; ++r) { t1.re[r] *= R(0.5); t1.im[r] *= R(0.5); }
-    const R c0 = ch.cf[0], c1 = ch.cf[1];
+    // k = 0 (a_0, or a_0 - 1 when compensating) and k = 1 on -i*vector (forward) / +i*vector (adjoint)
+    const R sg = ADJ ? R(-1) : R(1);
+    const R b0h = COMP ? ch.c0h : ch.a0h, b0l = COMP ? ch.c0l : ch.a0l;
 #pragma unroll
     for (int r = 0; r < E; ++r) {
-      // even term k=0 on the vector, odd term k=1 on -i*vector (forward) / +i*vector (adjoint)
-      if (!ADJ) {
-        acc.re[r] = fma(c1, t1.im[r], c0 * t0.re[r]);
-        acc.im[r] = fma(-c1, t1.re[r], c0 * t0.im[r]);
-      } else {
-        acc.re[r] = fma(-c1, t1.im[r], c0 * t0.re[r]);
-        acc.im[r] = fma(c1, t1.re[r], c0 * t0.im[r]);
-      }
+      R xr = fma(sg * ch.a1l, t1.im[r], b0l * t0.re[r]);
+      R xi = fma(-sg * ch.a1l, t1.re[r], b0l * t0.im[r]);
+      xr = fma(sg * ch.a1h, t1.im[r], xr);
+      xi = fma(-sg * ch.a1h, t1.re[r], xi);
+      acc.re[r] = fma(b0h, t0.re[r], xr);
+      acc.im[r] = fma(b0h, t0.im[r], xi);
     }
+    // (t0, t1) = (T_{k-2}, T_{k-1}); each recurrence overwrites the older term in place
     for (int k = 2; k < K; k += 2) {
-      Vec<R, E> t2;
-      op.rec(t1, t0, t2);   // T_k
-      const R ce = ch.cf[k];
+      op.rec(t1, t0, t0);   // t0 <- T_k
+      const R ce = ch.cf[k], cel = ch.cl[k];
 #pragma unroll
       for (int r = 0; r < E; ++r) {
-        acc.re[r] = fma(ce, t2.re[r], acc.re[r]);
-        acc.im[r] = fma(ce, t2.im[r], acc.im[r]);
+        if (sizeof(R) == 4) {
+          acc.re[r] = fma(cel, t0.re[r], acc.re[r]);
+          acc.im[r] = fma(cel, t0.im[r], acc.im[r]);
+        }
+        acc.re[r] = fma(ce, t0.re[r], acc.re[r]);
+        acc.im[r] = fma(ce, t0.im[r], acc.im[r]);
       }
       if (k + 1 < K) {
-        op.rec(t2, t1, t0);   // T_{k+1} into t0
-        const R co = ch.cf[k + 1];
+        op.rec(t0, t1, t1);   // t1 <- T_{k+1}
+        const R co = sg * ch.cf[k + 1], col = sg * ch.cl[k + 1];
 #pragma unroll
         for (int r = 0; r < E; ++r) {
-          if (!ADJ) {
-            acc.re[r] = fma(co, t0.im[r], acc.re[r]);
-            acc.im[r] = fma(-co, t0.re[r], acc.im[r]);
-          } else {
-            acc.re[r] = fma(-co, t0.im[r], acc.re[r]);
-            acc.im[r] = fma(co, t0.re[r], acc.im[r]);
+          if (sizeof(R) == 4) {
+            acc.re[r] = fma(col, t1.im[r], acc.re[r]);
+            acc.im[r] = fma(-col, t1.re[r], acc.im[r]);
           }
+          acc.re[r] = fma(co, t1.im[r], acc.re[r]);
+          acc.im[r] = fma(-co, t1.re[r], acc.im[r]);
         }
-        // rotate: (t0, t1) <- (T_k, T_{k+1})
-#pragma unroll
-        for (int r = 0; r < E; ++r) {
-          R a = t2.re[r], b = t2.im[r];
-          t1.re[r] = t0.re[r]; t1.im[r] = t0.im[r];
-          t0.re[r] = a; t0.im[r] = b;
-        }
-        // now t0 = T_k, t1 = T_{k+1}
       }
     }
-    const R cp = ch.cph, sp = ch.sph;
 #pragma unroll
     for (int r = 0; r < E; ++r) {
-      if (!ADJ) {   // times exp(-i theta)
-        v.re[r] = fma(acc.re[r], cp, acc.im[r] * sp);
-        v.im[r] = fma(acc.im[r], cp, -acc.re[r] * sp);
-      } else {      // times exp(+i theta)
-        v.re[r] = fma(acc.re[r], cp, -acc.im[r] * sp);
-        v.im[r] = fma(acc.im[r], cp, acc.re[r] * sp);
+      if (!COMP) {
+        v.re[r] = acc.re[r];
+        v.im[r] = acc.im[r];
+      } else {
+        // v_new = v + acc (acc = (a_0 - 1) v + sum_{k>=1}): (hi, lo) <- two_sum(hi, acc + lo)
+        const R x = v.re[r], y = v.im[r];
+        const R tr = acc.re[r] + lo.re[r], ti = acc.im[r] + lo.im[r];
+        const R sr = x + tr, si = y + ti;
+        const R br = sr - x, bi = si - y;
+        lo.re[r] = (x - (sr - br)) + (tr - br);
+        lo.im[r] = (y - (si - bi)) + (ti - bi);
+        v.re[r] = sr;
+        v.im[r] = si;
       }
     }
   }
+}
+
+// exp(-i sgn phi) applied in FP64 to hi + lo, returned as (re, im) doubles per element.
+__device__ __forceinline__ void phase_rotate(double cp, double sp, bool adj, double xr, double xi, double& yr, double& yi) {
+  if (!adj) { yr = xr * cp + xi * sp; yi = xi * cp - xr * sp; }
+  else { yr = xr * cp - xi * sp; yi = xi * cp + xr * sp; }
+}
+
+template <bool ADJ, typename R, int E, class Op>
+__device__ __forceinline__ void cheb_step(Vec<R, E>& v, const Op& op, const Cheb<R>& ch) {
+  cheb_step<ADJ, false>(v, v, op, ch);
 }
 
 }  // namespace ism

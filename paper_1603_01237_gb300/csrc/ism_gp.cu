@@ -1,0 +1,434 @@
+// ism_gp.cu -- the Gross-Pitaevskii (condensate) variant of the ISM hot path (Sec. 4, condensates).
+//
+// Model: i d/dt psi = (-1/2 d^2/dx^2 + V(x, u) + g |psi|^2) psi on a periodic grid of n points,
+// V = (x - u)^2 / 2, J = Re<psi(T)|psi_f>, <a|b> = sum conj(a) b dx.  Time step (Strang, Eq. (OS)):
+// psi_{j+1} = K exp(-i tau theta_j) K psi_j with K = F^-1 diag(exp(-i tau k^2/4)) F and
+// theta_j = V(x, u_j) + g |K psi_j|^2.
+//
+// Representation: the sweeps carry a_j = K psi_j, so a step is one pointwise phase and one FFT pair,
+//   a_{j+1} = F^-1 [exp(-i tau k^2/2) F (exp(-i tau theta_j) a_j)].
+// The adjoint (reverse mode of the discrete map, dJ = Re<lambda_j|d psi_j>) carries nu_j = K^H lambda_j:
+//   mu_j = exp(+i tau theta_j) nu_{j+1},   w_j = mu_j + 2 tau g Im(conj(mu_j) a_j) a_j,
+//   nu_j = F^-1 [exp(+i tau k^2/2) F w_j],  dJ/du_j = tau sum_k dV/du(x_k) Im(conj(mu_j) a_j)_k dx,
+// with lambda_Nt = psi_f.  psi_j = K^H a_j and lambda_j = K nu_j are formed only where stored.
+//
+// One CTA of max(n/8, 32) threads per state; the FFT is a radix-8 Stockham transform in shared memory
+// with twiddles and kinetic factors computed in FP64.  Phase factors applied at every step are held
+// as (factor - 1) and applied as v + (factor - 1) v, so their rounding is relative to the change.
+//   k_gp_forward   full forward sweep: psi(t_n) at the partition, a_j for every step, J and F;
+//   k_gp_adjoint   full adjoint sweep: chi(t_n) = lambda_{j_n}, the sub-problem targets;
+//   k_gp_sub       all sub-problems at once (grid N x B): forward from psi(t_n) storing a_j, adjoint
+//                  from chi(t_{n+1}), gradient of J_n = Re<psi_n(t_{n+1})|chi(t_{n+1})>, ascent step.
+#include <cmath>
+
+#include "ism_device.cuh"
+#include "ism_gp.h"
+
+namespace ism {
+namespace {
+
+template <typename T> __device__ __forceinline__ T cmul(T a, T b) {
+  T c;
+  c.x = a.x * b.x - a.y * b.y;
+  c.y = a.x * b.y + a.y * b.x;
+  return c;
+}
+template <typename T> __device__ __forceinline__ T cadd(T a, T b) { T c; c.x = a.x + b.x; c.y = a.y + b.y; return c; }
+template <typename T> __device__ __forceinline__ T csub(T a, T b) { T c; c.x = a.x - b.x; c.y = a.y - b.y; return c; }
+template <typename T> __device__ __forceinline__ T cconj(T a) { a.y = -a.y; return a; }
+
+__device__ __forceinline__ void sc(float x, float& s, float& c) { sincosf(x, &s, &c); }
+__device__ __forceinline__ void sc(double x, double& s, double& c) { sincos(x, &s, &c); }
+__device__ __forceinline__ float sn(float x) { return sinf(x); }
+__device__ __forceinline__ double sn(double x) { return sin(x); }
+
+// exp(i phi) - 1 = -2 sin^2(phi/2) + i sin(phi), without cancellation for small phi
+template <typename T, typename R> __device__ __forceinline__ T expm1i(R phi) {
+  R s, c;
+  sc(phi, s, c);
+  const R h = sn(R(0.5) * phi);
+  T e;
+  e.x = R(-2) * h * h;
+  e.y = s;
+  return e;
+}
+
+// 4-point DFT: X_k = sum_r a_r exp(-+ 2 pi i r k / 4)
+template <typename T, bool INV>
+__device__ __forceinline__ void dft4(T& a0, T& a1, T& a2, T& a3) {
+  T c0 = cadd(a0, a2), c1 = csub(a0, a2), c2 = cadd(a1, a3), d = csub(a1, a3);
+  T c3;   // (-i)(a1 - a3) forward, (+i)(a1 - a3) inverse
+  if (!INV) { c3.x = d.y; c3.y = -d.x; } else { c3.x = -d.y; c3.y = d.x; }
+  a0 = cadd(c0, c2);
+  a2 = csub(c0, c2);
+  a1 = cadd(c1, c3);
+  a3 = csub(c1, c3);
+}
+
+// 8-point DFT in registers: X_{2m} = DFT4(v_r + v_{r+4}), X_{2m+1} = DFT4(w^r (v_r - v_{r+4})),
+// w = exp(-+ i pi / 4)
+template <typename R, bool INV>
+__device__ __forceinline__ void dft8(typename C2<R>::T* v) {
+  using T = typename C2<R>::T;
+  const R h = (R)0.70710678118654752440;
+  T a[4], b[4];
+#pragma unroll
+  for (int r = 0; r < 4; ++r) { a[r] = cadd(v[r], v[r + 4]); b[r] = csub(v[r], v[r + 4]); }
+  {   // w^1 = (1 -+ i)/sqrt(2)
+    const T t = b[1];
+    if (!INV) { b[1].x = h * (t.x + t.y); b[1].y = h * (t.y - t.x); }
+    else { b[1].x = h * (t.x - t.y); b[1].y = h * (t.y + t.x); }
+  }
+  {   // w^2 = -+ i
+    const T t = b[2];
+    if (!INV) { b[2].x = t.y; b[2].y = -t.x; } else { b[2].x = -t.y; b[2].y = t.x; }
+  }
+  {   // w^3 = (-1 -+ i)/sqrt(2)
+    const T t = b[3];
+    if (!INV) { b[3].x = h * (t.y - t.x); b[3].y = -h * (t.x + t.y); }
+    else { b[3].x = -h * (t.x + t.y); b[3].y = h * (t.x - t.y); }
+  }
+  dft4<T, INV>(a[0], a[1], a[2], a[3]);
+  dft4<T, INV>(b[0], b[1], b[2], b[3]);
+#pragma unroll
+  for (int m = 0; m < 4; ++m) { v[2 * m] = a[m]; v[2 * m + 1] = b[m]; }
+}
+
+// Stockham radix-8 FFT (unnormalised) of length n = 8^P from x, using y as the other buffer; twiddle
+// table W[m] = exp(-2 pi i m / n).  Every thread of the block calls it; threads t < n/8 compute.
+// Returns the buffer that holds the result.
+template <typename R, bool INV>
+__device__ typename C2<R>::T* fft8(typename C2<R>::T* x, typename C2<R>::T* y, const typename C2<R>::T* W, int n) {
+  using T = typename C2<R>::T;
+  const int t = threadIdx.x, q = n >> 3;
+  for (int Ns = 1; Ns < n; Ns <<= 3) {
+    if (t < q) {
+      const int k = t % Ns;
+      T v[8];
+#pragma unroll
+      for (int r = 0; r < 8; ++r) v[r] = x[t + r * q];
+      const int step = n / (Ns << 3);
+#pragma unroll
+      for (int r = 1; r < 8; ++r) {
+        T w = W[(k * r * step) & (n - 1)];
+        if (INV) w = cconj(w);
+        v[r] = cmul(v[r], w);
+      }
+      dft8<R, INV>(v);
+      const int base = (t / Ns) * (Ns << 3) + k;
+#pragma unroll
+      for (int r = 0; r < 8; ++r) y[base + r * Ns] = v[r];
+    }
+    __syncthreads();
+    T* tmp = x;
+    x = y;
+    y = tmp;
+  }
+  return x;
+}
+
+template <typename R>
+struct GP {
+  using T = typename C2<R>::T;
+  T *A, *B, *C, *W, *D2m1, *DH;   // state, scratch, spare, twiddles, exp(-i tau k^2/2)-1, exp(-i tau k^2/4)
+  int n;
+  double dx, tau, g, xmin;
+  double* red;
+
+  __device__ void setup(const GPParams& p, unsigned char* smem, double* red_) {
+    T* base = reinterpret_cast<T*>(smem);
+    n = p.n;
+    A = base;
+    B = base + n;
+    C = base + 2 * n;
+    W = base + 3 * n;
+    D2m1 = base + 4 * n;
+    DH = base + 5 * n;
+    dx = p.dx;
+    tau = p.tau;
+    g = p.g;
+    xmin = p.xmin;
+    red = red_;
+    for (int m = threadIdx.x; m < n; m += blockDim.x) {
+      double s, co;
+      sincospi(-2.0 * (double)m / (double)n, &s, &co);
+      T w;
+      w.x = (R)co;
+      w.y = (R)s;
+      W[m] = w;
+      const int kk = m < n / 2 ? m : m - n;   // frequency ordering of an unshifted FFT
+      const double k = 2.0 * M_PI * (double)kk / p.L;
+      const double ph2 = -0.5 * tau * k * k, ph4 = -0.25 * tau * k * k;
+      const double h = sin(0.5 * ph2);
+      T d;
+      d.x = (R)(-2.0 * h * h);
+      d.y = (R)sin(ph2);
+      D2m1[m] = d;
+      double s4, c4;
+      sincos(ph4, &s4, &c4);
+      T e;
+      e.x = (R)c4;
+      e.y = (R)s4;
+      DH[m] = e;
+    }
+    __syncthreads();
+  }
+
+  // buf <- F^-1 diag(f) F buf (f = full-step factor, or half-step; conjugated for the adjoint).
+  // buf is A or C; B is the scratch of every transform.
+  template <bool ADJ, bool FULL>
+  __device__ void kinetic(T* buf) {
+    T* X = fft8<R, false>(buf, B, W, n);
+    for (int m = threadIdx.x; m < n; m += blockDim.x) {
+      T v = X[m];
+      T f = FULL ? D2m1[m] : DH[m];
+      if (ADJ) f = cconj(f);
+      v = FULL ? cadd(v, cmul(f, v)) : cmul(f, v);
+      X[m] = v;
+    }
+    __syncthreads();
+    T* other = (X == buf) ? B : buf;
+    T* Y = fft8<R, true>(X, other, W, n);
+    const R inv_n = (R)(1.0 / (double)n);
+    for (int m = threadIdx.x; m < n; m += blockDim.x) {
+      T v = Y[m];
+      v.x *= inv_n;
+      v.y *= inv_n;
+      buf[m] = v;
+    }
+    __syncthreads();
+  }
+
+  __device__ R theta(int m, double u, T a) const {
+    const R xm = (R)(xmin + m * dx - u);
+    return R(0.5) * xm * xm + (R)g * (a.x * a.x + a.y * a.y);
+  }
+
+  // A <- exp(-i tau theta) A (forward Strang factor), in place
+  __device__ void potential(double u) {
+    for (int m = threadIdx.x; m < n; m += blockDim.x) {
+      const T a = A[m];
+      const T e = expm1i<T, R>(-(R)tau * theta(m, u, a));
+      A[m] = cadd(a, cmul(e, a));
+    }
+    __syncthreads();
+  }
+
+  __device__ double sum(double v) {
+    for (int m = 16; m >= 1; m >>= 1) v += __shfl_xor_sync(0xffffffffu, v, m);
+    __syncthreads();
+    if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = v;
+    __syncthreads();
+    double s = 0.0;
+    for (int w = 0; w < (int)((blockDim.x + 31) >> 5); ++w) s += red[w];
+    __syncthreads();
+    return s;
+  }
+
+  // adjoint step at a_j (global, complex R, per element): A holds nu_{j+1} on entry and nu_j on exit;
+  // returns dJ/du_j (FP64).
+  __device__ double adjoint_step(const T* aj, double u) {
+    double part = 0.0;
+    for (int m = threadIdx.x; m < n; m += blockDim.x) {
+      const T a = aj[m];
+      const T nu = A[m];
+      const T e = expm1i<T, R>((R)tau * theta(m, u, a));
+      const T mu = cadd(nu, cmul(e, nu));
+      const R im = mu.x * a.y - mu.y * a.x;   // Im(conj(mu) a)
+      const double dVdu = -(xmin + m * dx - u);
+      part += dVdu * (double)im;
+      T w;
+      const R f = R(2) * (R)tau * (R)g * im;
+      w.x = mu.x + f * a.x;
+      w.y = mu.y + f * a.y;
+      A[m] = w;
+    }
+    __syncthreads();
+    const double gsum = sum(part);
+    kinetic<true, true>(A);
+    return tau * dx * gsum;
+  }
+};
+
+template <typename R> __device__ __forceinline__ typename C2<R>::T ld_state(const double2* src, int m) {
+  typename C2<R>::T v;
+  const double2 z = src[m];
+  v.x = (R)z.x;
+  v.y = (R)z.y;
+  return v;
+}
+
+// ------------------------------------------------------------------------------------ kernels
+template <typename R>
+__global__ void k_gp_forward(GPParams p) {
+  using T = typename C2<R>::T;
+  extern __shared__ __align__(128) unsigned char smem[];
+  __shared__ double red[32];
+  GP<R> s;
+  s.setup(p, smem, red);
+  const int b = blockIdx.x, n = p.n;
+  const double* ub = p.u + (long)b * p.Nt;
+  T* traj = reinterpret_cast<T*>(p.traj) + (long)b * (p.Nt + 1) * n;
+  double2* psin = p.psin + (long)b * (p.N + 1) * n;
+  for (int m = threadIdx.x; m < n; m += blockDim.x) s.A[m] = ld_state<R>(p.psi_i, m);
+  __syncthreads();
+  s.kinetic<false, false>(s.A);   // a_0 = K psi_i
+  int nn = 0;
+  for (int j = 0; j <= p.Nt; ++j) {
+    for (int m = threadIdx.x; m < n; m += blockDim.x) traj[(long)j * n + m] = s.A[m];
+    if (nn <= p.N && j == p.jn[nn]) {   // psi(t_n) = K^H a_j, and J, F at the end
+      for (int m = threadIdx.x; m < n; m += blockDim.x) s.C[m] = s.A[m];
+      __syncthreads();
+      s.kinetic<true, false>(s.C);   // scratch B; the live state A is untouched
+      for (int m = threadIdx.x; m < n; m += blockDim.x) {
+        const T v = s.C[m];
+        psin[(long)nn * n + m] = make_double2((double)v.x, (double)v.y);
+      }
+      if (j == p.Nt) {
+        double orr = 0.0, oi = 0.0;
+        for (int m = threadIdx.x; m < n; m += blockDim.x) {
+          const T v = s.C[m];
+          const double2 f = p.psi_f[m];
+          orr += (double)v.x * f.x + (double)v.y * f.y;
+          oi += (double)v.x * f.y - (double)v.y * f.x;
+        }
+        orr = s.sum(orr) * p.dx;
+        oi = s.sum(oi) * p.dx;
+        if (threadIdx.x == 0) {
+          if (!isfinite(orr) || !isfinite(oi)) atomicOr(p.status, ST_NONFINITE);
+          p.J[b] = orr;
+          p.F[b] = orr * orr + oi * oi;
+          if (p.Jhist) p.Jhist[(long)b * p.hist_stride + p.hist_k] = orr;
+        }
+      }
+      ++nn;
+      __syncthreads();
+    }
+    if (j == p.Nt) break;
+    s.potential(ub[j]);
+    s.kinetic<false, true>(s.A);
+  }
+  if (p.count && threadIdx.x == 0) atomicAdd(p.count, (unsigned long long)p.Nt);
+}
+
+template <typename R>
+__global__ void k_gp_adjoint(GPParams p) {
+  using T = typename C2<R>::T;
+  extern __shared__ __align__(128) unsigned char smem[];
+  __shared__ double red[32];
+  GP<R> s;
+  s.setup(p, smem, red);
+  const int b = blockIdx.x, n = p.n;
+  const double* ub = p.u + (long)b * p.Nt;
+  const T* traj = reinterpret_cast<const T*>(p.traj) + (long)b * (p.Nt + 1) * n;
+  double2* chin = p.chin + (long)b * (p.N + 1) * n;
+  for (int m = threadIdx.x; m < n; m += blockDim.x) {
+    s.A[m] = ld_state<R>(p.psi_f, m);
+    chin[(long)p.N * n + m] = p.psi_f[m];
+  }
+  __syncthreads();
+  s.kinetic<true, false>(s.A);   // nu_Nt = K^H psi_f
+  int nn = p.N - 1;
+  for (int j = p.Nt - 1; j >= 0; --j) {
+    s.adjoint_step(traj + (long)j * n, ub[j]);
+    if (nn >= 0 && j == p.jn[nn]) {   // chi(t_n) = lambda_j = K nu_j
+      for (int m = threadIdx.x; m < n; m += blockDim.x) s.C[m] = s.A[m];
+      __syncthreads();
+      s.kinetic<false, false>(s.C);   // scratch B; the live state A is untouched
+      for (int m = threadIdx.x; m < n; m += blockDim.x) {
+        const T v = s.C[m];
+        chin[(long)nn * n + m] = make_double2((double)v.x, (double)v.y);
+      }
+      --nn;
+      __syncthreads();
+    }
+  }
+  if (p.count && threadIdx.x == 0) atomicAdd(p.count, (unsigned long long)p.Nt);
+}
+
+// grid (N, B): sub-problem n of problem b
+template <typename R>
+__global__ void k_gp_sub(GPParams p) {
+  using T = typename C2<R>::T;
+  extern __shared__ __align__(128) unsigned char smem[];
+  __shared__ double red[32];
+  GP<R> s;
+  s.setup(p, smem, red);
+  const int nsub = blockIdx.x, b = blockIdx.y, n = p.n;
+  const int j0 = p.jn[nsub], j1 = p.jn[nsub + 1];
+  double* ub = p.u + (long)b * p.Nt;
+  T* traj = reinterpret_cast<T*>(p.traj) + (long)b * (p.Nt + 1) * n;
+  const double2* psin = p.psin + (long)b * (p.N + 1) * n;
+  const double2* chin = p.chin + (long)b * (p.N + 1) * n;
+  // forward from psi(t_n), storing a_j for j0..j1-1
+  for (int m = threadIdx.x; m < n; m += blockDim.x) s.A[m] = ld_state<R>(psin + (long)nsub * n, m);
+  __syncthreads();
+  s.kinetic<false, false>(s.A);
+  for (int j = j0; j < j1; ++j) {
+    for (int m = threadIdx.x; m < n; m += blockDim.x) traj[(long)j * n + m] = s.A[m];
+    s.potential(ub[j]);
+    s.kinetic<false, true>(s.A);
+  }
+  // J_n = Re<psi_n(t_{n+1})|chi(t_{n+1})>, psi_n(t_{n+1}) = K^H a_{j1}
+  s.kinetic<true, false>(s.A);
+  double jr = 0.0;
+  for (int m = threadIdx.x; m < n; m += blockDim.x) {
+    const T v = s.A[m];
+    const double2 c = chin[(long)(nsub + 1) * n + m];
+    jr += (double)v.x * c.x + (double)v.y * c.y;
+  }
+  jr = s.sum(jr) * p.dx;
+  // adjoint from chi(t_{n+1}): nu_{j1} = K^H chi(t_{n+1})
+  for (int m = threadIdx.x; m < n; m += blockDim.x) s.A[m] = ld_state<R>(chin + (long)(nsub + 1) * n, m);
+  __syncthreads();
+  s.kinetic<true, false>(s.A);
+  double err = 0.0;
+  double* gb = p.grad + (long)b * p.Nt;
+  for (int j = j1 - 1; j >= j0; --j) {
+    const double uj = ub[j];
+    const double gj = s.adjoint_step(traj + (long)j * n, uj);
+    err += fabs(gj);
+    if (threadIdx.x == 0) {
+      gb[j] = gj;
+      if (p.update) ub[j] = uj + p.rho * gj / p.tau;
+    }
+  }
+  if (threadIdx.x == 0) {
+    const long id = (long)b * p.N + nsub;
+    if (p.Jn) p.Jn[id] = jr;
+    if (p.err) p.err[id] = err;
+    if (p.count) atomicAdd(p.count + 1, (unsigned long long)(2 * (j1 - j0)));
+  }
+}
+
+template <typename R> size_t gp_smem(int n) { return 6 * (size_t)n * sizeof(typename C2<R>::T); }
+int gp_threads(int n) { return n / 8 < 32 ? 32 : n / 8; }
+
+template <typename R, class K>
+cudaError_t launch(K kern, const GPParams& p, dim3 grid, cudaStream_t st) {
+  const size_t sm = gp_smem<R>(p.n);
+  // opt in whenever dynamic + static shared memory could pass the 48 KB default
+  cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
+  if (e != cudaSuccess) return e;
+  kern<<<grid, gp_threads(p.n), sm, st>>>(p);
+  return cudaGetLastError();
+}
+
+}  // namespace
+
+bool gp_supported(int n) { return n == 64 || n == 512 || n == 4096; }
+
+cudaError_t launch_gp_forward(int prec, const GPParams& p, cudaStream_t st) {
+  return prec == 0 ? launch<double>(k_gp_forward<double>, p, dim3(p.B), st)
+                   : launch<float>(k_gp_forward<float>, p, dim3(p.B), st);
+}
+cudaError_t launch_gp_adjoint(int prec, const GPParams& p, cudaStream_t st) {
+  return prec == 0 ? launch<double>(k_gp_adjoint<double>, p, dim3(p.B), st)
+                   : launch<float>(k_gp_adjoint<float>, p, dim3(p.B), st);
+}
+cudaError_t launch_gp_sub(int prec, const GPParams& p, cudaStream_t st) {
+  return prec == 0 ? launch<double>(k_gp_sub<double>, p, dim3(p.N, p.B), st)
+                   : launch<float>(k_gp_sub<float>, p, dim3(p.N, p.B), st);
+}
+
+}  // namespace ism

@@ -1,0 +1,35 @@
+// ism_gp.h -- parameters and launchers of the Gross-Pitaevskii kernels (ism_gp.cu).
+#pragma once
+#include <cuda_runtime.h>
+
+namespace ism {
+
+struct GPParams {
+  int n, Nt, N, B;
+  double tau, T, L, xmin, dx, g, rho;
+  const int* jn;          // [N+1]
+  double* u;              // [B][Nt]
+  const double2* psi_i;   // [n]
+  const double2* psi_f;   // [n]
+  void* traj;             // [B][Nt+1][n] complex R: a_j = K psi_j
+  double2* psin;          // [B][N+1][n] psi(t_n)
+  double2* chin;          // [B][N+1][n] chi(t_n) = lambda_{j_n}
+  double* grad;           // [B][Nt]
+  double* Jn;             // [B][N]
+  double* err;            // [B][N]
+  double* J;              // [B]
+  double* F;              // [B]
+  double* Jhist;          // [B][hist_stride] or null
+  int hist_stride, hist_k;
+  int* status;
+  unsigned long long* count;   // [2]: FFT pairs (sequential sweeps), FFT pairs (sub-interval sweeps)
+  int update;
+};
+
+// prec: 0 FP64, 1 FP32.  n must be 8^P (64, 512, 4096).
+bool gp_supported(int n);
+cudaError_t launch_gp_forward(int prec, const GPParams& p, cudaStream_t st);
+cudaError_t launch_gp_adjoint(int prec, const GPParams& p, cudaStream_t st);
+cudaError_t launch_gp_sub(int prec, const GPParams& p, cudaStream_t st);
+
+}  // namespace ism

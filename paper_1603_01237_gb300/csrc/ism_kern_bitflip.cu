@@ -8,10 +8,10 @@ static bool pick(int d, KernelSet* ks) {
   switch (d) {
     case 2: fill_set<R, OpBitflip<R, 2, 1>>(ks); return true;
     case 4: fill_set<R, OpBitflip<R, 4, 1>>(ks); return true;
-    case 8: fill_set<R, OpBitflip<R, 8, 1>>(ks); return true;
-    case 16: fill_set<R, OpBitflip<R, 16, 1>>(ks); return true;
-    case 32: fill_set<R, OpBitflip<R, 16, 2>>(ks); return true;
-    case 64: fill_set<R, OpBitflip<R, 16, 4>>(ks); return true;
+    case 8: fill_set<R, OpBitflip<R, 4, 2>, OpBitflip<R, 8, 1>>(ks); return true;
+    case 16: fill_set<R, OpBitflip<R, 4, 4>, OpBitflip<R, 16, 1>>(ks); return true;
+    case 32: fill_set<R, OpBitflip<R, 8, 4>, OpBitflip<R, 16, 2>>(ks); return true;
+    case 64: fill_set<R, OpBitflip<R, 8, 8>, OpBitflip<R, 16, 4>>(ks); return true;
     default: return false;
   }
 }

@@ -3,14 +3,15 @@
 
 namespace ism {
 
+// assembly: 8 lanes x ceil(d/8) elements; sweep: 16 lanes x ceil(d/16) elements
 template <typename R>
 static bool pick(int d, KernelSet* ks) {
   const int E = (d + 15) / 16;
   switch (E) {
-    case 1: fill_set<R, OpTridiag<R, 16, 1>>(ks); return true;
-    case 2: fill_set<R, OpTridiag<R, 16, 2>>(ks); return true;
-    case 3: fill_set<R, OpTridiag<R, 16, 3>>(ks); return true;
-    case 4: fill_set<R, OpTridiag<R, 16, 4>>(ks); return true;
+    case 1: fill_set<R, OpTridiag<R, 8, 2>, OpTridiag<R, 16, 1>>(ks); return true;
+    case 2: fill_set<R, OpTridiag<R, 8, 4>, OpTridiag<R, 16, 2>>(ks); return true;
+    case 3: fill_set<R, OpTridiag<R, 8, 6>, OpTridiag<R, 16, 3>>(ks); return true;
+    case 4: fill_set<R, OpTridiag<R, 8, 8>, OpTridiag<R, 16, 4>>(ks); return true;
     default: return false;
   }
 }

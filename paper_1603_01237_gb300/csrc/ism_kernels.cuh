@@ -20,15 +20,20 @@ struct KParams {
   const double* beta;     // [N]
   const double* alpha;    // [Nt] or null
   const void* H;          // packed op data (element type R)
+  const double* H0d;      // FP64 diagonal of H0 (tridiagonal and bit-flip kinds)
   double* u;              // [B][Nt]
   const double2* phi;     // [B][N+1][d]
-  void* M;                // [B][N][d cols][ldm rows] (R2)
+  void* M;                // [B][N] tiles of tile_stride R2: [d cols][ldm rows], ldm odd >= d
+  long tile_stride;
   void* traj;             // [B][Nt+N][G*E] (R2)  H1 psi_n(t_j) per step
   double* grad;           // [B][Nt]
   double* Jn;             // [B][N]
   double* err;            // [B][N]
   int* status;
   unsigned long long* count;   // [3]: Y applications, accumulated terms, exp sub-steps (or null)
+  const double2* psin;         // [B][N+1][d] psi(t_n) (form 1)
+  const double2* chin;         // [B][N+1][d] chi(t_n) (form 1)
+  int form;                    // 0: literal sub-problem from phi; 1: Theorem 2 two-trajectory form
   int update;
   int max_spin;
 };
@@ -43,6 +48,7 @@ struct ChainParams {
   const double* alpha;    // [Nt] or null
   const double* u;        // [B][Nt]
   const int* jn;
+  const double2* ab;      // [N+1] (a_n, b_n) of Eq. (cible), computed on the host in FP64
   double2* psin;          // [B][N+1][d]
   double2* chin;          // [B][N+1][d]
   double2* phi;           // [B][N+1][d]
@@ -50,6 +56,8 @@ struct ChainParams {
   double* F;              // [B]
   double* Jhist;          // [B][hist_stride] or null
   int hist_stride, hist_k;
+  int stages;             // bulk-copy ring depth per chain (2..CHAIN_MAX_STAGES)
+  long tile_stride;       // R2 elements between consecutive tiles (d*ldm rounded up to even)
   int* status;
   int max_spin;
 };
@@ -71,6 +79,7 @@ __device__ __forceinline__ void count_work(unsigned long long* c, const Cheb<R>&
 template <typename R, class Op>
 __global__ void __launch_bounds__(128) k_assemble(KParams p) {
   constexpr int G = Op::G, E = Op::E, GPB = 128 / G;
+  constexpr bool COMP = sizeof(R) == 4;
   using R2 = typename C2<R>::T;
   extern __shared__ __align__(128) unsigned char smem_raw[];
   __shared__ Cheb<R> chs[GPB];
@@ -97,33 +106,52 @@ __global__ void __launch_bounds__(128) k_assemble(KParams p) {
   cheb_setup<G, R>(ch, lg, p.tau, p.c0, p.r0, p.h1n, um, p.tol, p.status);
 
   Op op;
-  op.load(reinterpret_cast<const R*>(p.H), p.d, lg, smem_raw);
-  Vec<R, E> v;
+  op.load(reinterpret_cast<const R*>(p.H), p.H0d, p.d, lg, smem_raw);
+  op.scale(p.H0d, p.d, lg, ch);
+  Vec<R, E> v, lo;
 #pragma unroll
-  for (int r = 0; r < E; ++r) { v.re[r] = (lg * E + r == col) ? R(1) : R(0); v.im[r] = R(0); }
+  for (int r = 0; r < E; ++r) {
+    v.re[r] = (lg * E + r == col) ? R(1) : R(0);
+    v.im[r] = R(0);
+    lo.re[r] = R(0);
+    lo.im[r] = R(0);
+  }
 
-  R un = ldu_ro<R>(ub, j0);
+  // controls two steps ahead in registers
+  R ua = ldu_ro<R>(ub, j0), ub1 = j0 + 1 < j1 ? ldu_ro<R>(ub, j0 + 1) : R(0);
   for (int j = j0; j < j1; ++j) {
-    const R uj = un;
-    if (j + 1 < j1) un = ldu_ro<R>(ub, j + 1);
+    const R uj = ua;
+    ua = ub1;
+    if (j + 2 < j1) ub1 = ldu_ro<R>(ub, j + 2);
     op.set_u(uj, ch, lg);
-    cheb_step<false>(v, op, ch);
+    cheb_step<false, COMP>(v, lo, op, ch);
   }
   if (col < p.d) {
     count_work<R>(p.count, ch, j1 - j0, lg);
-    R2* M = reinterpret_cast<R2*>(p.M) + (bn * p.d + col) * (long)p.ldm;
+    double sn, cs;   // global phase exp(-i c (t_{n+1} - t_n)) of the whole sub-interval, FP64
+    sincos(p.c0 * p.tau * (double)(j1 - j0), &sn, &cs);
+    R2* M = reinterpret_cast<R2*>(p.M) + bn * p.tile_stride + (long)col * p.ldm;
 #pragma unroll
     for (int r = 0; r < E; ++r) {
       int e = lg * E + r;
-      if (e < p.d) { R2 z; z.x = v.re[r]; z.y = v.im[r]; M[e] = z; }
+      if (e < p.d) {
+        double yr, yi;
+        phase_rotate(cs, sn, false, (double)v.re[r] + (double)lo.re[r], (double)v.im[r] + (double)lo.im[r], yr, yi);
+        R2 z; z.x = (R)yr; z.y = (R)yi; M[e] = z;
+      }
     }
   }
 }
 
 // ------------------------------------------------------------------------------ k_subinterval
+// One group per (problem, n).  Sequential part per step: the propagation (forward, then adjoint) and
+// an FP32 group reduction; the FP64 gradient, Err and ascent step are done afterwards with the lanes
+// working on different steps.  The trajectory slot of step j (H1 psi_n(t_j), consumed by the backward
+// sweep at step j) is reused to hold the gradient term Im<delta_j|H1 psi_j> for that final pass.
 template <typename R, class Op>
 __global__ void __launch_bounds__(128) k_subinterval(KParams p) {
   constexpr int G = Op::G, E = Op::E, GPB = 128 / G, GE = G * E;
+  constexpr bool COMP = sizeof(R) == 4;
   using R2 = typename C2<R>::T;
   extern __shared__ __align__(128) unsigned char smem_raw[];
   __shared__ Cheb<R> chs[GPB];
@@ -154,109 +182,160 @@ __global__ void __launch_bounds__(128) k_subinterval(KParams p) {
   cheb_setup<G, R>(ch, lg, p.tau, p.c0, p.r0, p.h1n, um, p.tol, p.status);
 
   Op op;
-  op.load(reinterpret_cast<const R*>(p.H), p.d, lg, smem_raw);
+  op.load(reinterpret_cast<const R*>(p.H), p.H0d, p.d, lg, smem_raw);
+  op.scale(p.H0d, p.d, lg, ch);
+  // Propagation here omits the global phase exp(-i c tau) of each step.  Over the sub-interval it
+  // multiplies psi_n(t_{n+1}) by exp(-i Phi), Phi = c (t_{n+1} - t_n), and every gradient term
+  // <chi_n|H1|psi_n>(t_j) by the same exp(-i Phi) (chi_n carries exp(+i c (t_{n+1} - t_j)), psi_n
+  // exp(-i c (t_j - t_n))); both are applied once, in FP64.
+  double sPhi, cPhi;
+  sincos(p.c0 * p.tau * (double)ns, &sPhi, &cPhi);
 
-  // psi_n(t_n) = phi_n (FP64 -> R)
-  const double2* phn = p.phi + ((long)b * (p.N + 1) + n) * p.d;
-  const double2* phn1 = phn + p.d;
-  Vec<R, E> v;
+  // form 0: psi_n(t_n) = phi_n (Eq. (dirpara)), adjoint from phi_{n+1};
+  // form 1 (phi = phi^u, first local step): psi from psi(t_n) and chi from chi(t_{n+1}), the two
+  // trajectories of which psi_n, chi_n are combinations (proof of Theorem 2); no cancellation.
+  const long off_n = ((long)b * (p.N + 1) + n) * p.d;
+  const double2* phn = (p.form ? p.psin : p.phi) + off_n;
+  const double2* phn1 = (p.form ? p.chin : p.phi) + off_n + p.d;
+  Vec<R, E> v, lo;
 #pragma unroll
   for (int r = 0; r < E; ++r) {
     int e = lg * E + r;
     double2 z = e < p.d ? phn[e] : make_double2(0.0, 0.0);
     v.re[r] = (R)z.x;
     v.im[r] = (R)z.y;
+    lo.re[r] = COMP ? (R)(z.x - (double)v.re[r]) : R(0);
+    lo.im[r] = COMP ? (R)(z.y - (double)v.im[r]) : R(0);
   }
-  R2* tr = reinterpret_cast<R2*>(p.traj) + ((long)b * (p.Nt + p.N) + j0 + n) * GE + lg * E;
+  R2* tr0 = reinterpret_cast<R2*>(p.traj) + ((long)b * (p.Nt + p.N) + j0 + n) * GE;   // slot s at tr0 + s*GE
+  R2* tr = tr0 + lg * E;
 
   // ---- forward sweep: store H1 psi_j, then psi_{j+1} = U_j psi_j
-  R un = ldu<R>(ub, j0);
-  for (int s = 0; s < nsw; ++s) {
-    const bool act = s < ns;
-    const R uj = un;
-    if (s + 1 < ns) un = ldu<R>(ub, j0 + s + 1);
-    Vec<R, E> hv;
-    op.h1(v, hv);
-    if (act && valid) {
+  {
+    R ua = ldu<R>(ub, j0), ub1 = ns > 1 ? ldu<R>(ub, j0 + 1) : ua;
+    for (int s = 0; s < nsw; ++s) {
+      const bool act = s < ns;
+      const R uj = ua;
+      ua = ub1;
+      if (s + 2 < ns) ub1 = ldu<R>(ub, j0 + s + 2);
+      Vec<R, E> hv;
+      op.h1(v, hv);
+      if (act && valid) {
 #pragma unroll
-      for (int r = 0; r < E; ++r) { R2 z; z.x = hv.re[r]; z.y = hv.im[r]; tr[(long)s * GE + r] = z; }
+        for (int r = 0; r < E; ++r) { R2 z; z.x = hv.re[r]; z.y = hv.im[r]; tr[(long)s * GE + r] = z; }
+      }
+      Vec<R, E> w = v, wl = lo;
+      op.set_u(uj, ch, lg);
+      cheb_step<false, COMP>(w, wl, op, ch);
+      if (act) { v = w; lo = wl; }
     }
-    Vec<R, E> w = v;
-    op.set_u(uj, ch, lg);
-    cheb_step<false>(w, op, ch);
-    if (act) v = w;
   }
   // end point: H1 psi_n(t_{n+1}) stays in registers
   Vec<R, E> hend;
   op.h1(v, hend);
 
-  // ---- terminal residual delta = phi_{n+1} - psi_n(t_{n+1}) in FP64; J_n
+  // ---- terminal residual delta = phi_{n+1} - psi_n(t_{n+1}) in FP64 (its norm gives J_n).  Form 0
+  // propagates delta backward; form 1 propagates chi from chi(t_{n+1}) and takes delta from the
+  // chain, delta = (chi - psi)(t_{n+1}) / beta_n.
   double nrm = 0.0;
   Vec<R, E> dl;
 #pragma unroll
   for (int r = 0; r < E; ++r) {
     int e = lg * E + r;
     double2 z = e < p.d ? phn1[e] : make_double2(0.0, 0.0);
-    double dr = z.x - (double)v.re[r], di = z.y - (double)v.im[r];
+    double dr, di;
+    if (!p.form) {
+      double pr, pi;
+      phase_rotate(cPhi, sPhi, false, (double)v.re[r] + (double)lo.re[r], (double)v.im[r] + (double)lo.im[r], pr, pi);
+      dr = z.x - pr;
+      di = z.y - pi;
+      dl.re[r] = (R)dr;
+      dl.im[r] = (R)di;
+    } else {
+      double2 ps = e < p.d ? p.psin[off_n + p.d + e] : make_double2(0.0, 0.0);
+      dr = (z.x - ps.x) / beta;
+      di = (z.y - ps.y) / beta;
+      dl.re[r] = (R)z.x;
+      dl.im[r] = (R)z.y;
+    }
     if (e >= p.d) { dr = 0.0; di = 0.0; }
     nrm += dr * dr + di * di;
-    dl.re[r] = (R)dr;
-    dl.im[r] = (R)di;
   }
   nrm = g_sum<G>(nrm);
-  double pen = 0.0;
-  if (p.alpha) {
-    for (int j = j0 + lg; j < j1; j += G) pen += p.alpha[j] * ub[j] * ub[j];
-    pen = g_sum<G>(pen);
-  }
-  const double Jn = p.w * (-0.5 * nrm) - 0.5 * p.tau * pen / beta;
 
-  // Im<delta|H1 psi>: the chi-part of Im<chi_n|H1|psi_n> with chi_n = psi_n + delta (Im<psi|H1|psi> = 0)
-  auto imdot = [&](const Vec<R, E>& a, const Vec<R, E>& h) -> R {
-    R acc = R(0);
+  // z = <a|h> over the group, FP32 products, both parts (the phase exp(-i Phi) is applied later)
+  auto zdot = [&](const Vec<R, E>& a, const Vec<R, E>& h, R& zr, R& zi) {
+    R xr = R(0), xi = R(0);
 #pragma unroll
-    for (int r = 0; r < E; ++r) acc = fma(a.re[r], h.im[r], fma(-a.im[r], h.re[r], acc));
-    return g_sum<G>(acc);
+    for (int r = 0; r < E; ++r) {
+      xr = fma(a.re[r], h.re[r], fma(a.im[r], h.im[r], xr));
+      xi = fma(a.re[r], h.im[r], fma(-a.im[r], h.re[r], xi));
+    }
+    zr = g_sum<G>(xr);
+    zi = g_sum<G>(xi);
   };
-  double Inext = (double)imdot(dl, hend);
-
-  // ---- backward sweep: delta_j = U_j^H delta_{j+1}, gradient terms, optional ascent step
-  const double ht = 0.5 * p.tau * p.w;
-  const double step = p.rho * beta / p.tau;
-  double err = 0.0;
-  double* gb = p.grad + (long)b * p.Nt;
-  Vec<R, E> hn;
   {
-    const int s0 = ns - 1;
-#pragma unroll
-    for (int r = 0; r < E; ++r) { R2 z = tr[(long)s0 * GE + r]; hn.re[r] = z.x; hn.im[r] = z.y; }
+    R zr, zi;
+    zdot(dl, hend, zr, zi);
+    if (lg == 0 && valid) { R2 z; z.x = zr; z.y = zi; tr0[(long)ns * GE] = z; }
   }
-  for (int s = nsw - 1; s >= 0; --s) {
-    const bool act = s < ns;
-    const int sc = act ? s : ns - 1;
-    const int j = j0 + sc;
-    const double ujd = ub[j];
-    Vec<R, E> hc = hn;
-    if (s - 1 >= 0 && s - 1 < ns) {
+
+  // ---- backward sweep: delta_j = U_j^H delta_{j+1}; gradient term of step j into slot j
+  {
+    const int top = ns - 1;
+    Vec<R, E> h0, h1v;   // slots s and s-1, prefetched
+    auto ldslot = [&](int s, Vec<R, E>& h) {
 #pragma unroll
-      for (int r = 0; r < E; ++r) { R2 z = tr[(long)(s - 1) * GE + r]; hn.re[r] = z.x; hn.im[r] = z.y; }
-    }
-    Vec<R, E> w = dl;
-    op.set_u((R)ujd, ch, lg);
-    cheb_step<true>(w, op, ch);
-    if (act) dl = w;
-    const double I = (double)imdot(dl, hc);
-    if (act) {
-      const double al = p.alpha ? p.alpha[j] : 0.0;
-      const double g = ht * (I + Inext) - p.tau * (al / beta) * ujd;
-      Inext = I;
-      err += fabs(g);
-      if (lg == 0 && valid) {
-        gb[j] = g;
-        if (p.update) ub[j] = ujd + step * g;
+      for (int r = 0; r < E; ++r) { R2 z = tr[(long)s * GE + r]; h.re[r] = z.x; h.im[r] = z.y; }
+    };
+    ldslot(top, h0);
+    ldslot(top > 0 ? top - 1 : top, h1v);
+    R ua = ldu<R>(ub, j0 + top), ub1 = ldu<R>(ub, j0 + (top > 0 ? top - 1 : top));
+    for (int s = nsw - 1; s >= 0; --s) {
+      const bool act = s < ns;
+      Vec<R, E> hc = h0;
+      const R uj = ua;
+      if (act) {
+        h0 = h1v;
+        ua = ub1;
+        if (s - 2 >= 0) { ldslot(s - 2, h1v); ub1 = ldu<R>(ub, j0 + s - 2); }
       }
+      Vec<R, E> w = dl;
+      op.set_u(uj, ch, lg);
+      cheb_step<true>(w, op, ch);
+      if (act) dl = w;
+      R zr, zi;
+      zdot(dl, hc, zr, zi);
+      if (act && lg == 0 && valid) { R2 z; z.x = zr; z.y = zi; tr0[(long)s * GE] = z; }
     }
   }
+  __syncwarp();
+
+  // ---- FP64 pass over the steps: gradient, Err, ascent step, penalty of J_n
+  const double ht = 0.5 * p.tau * p.w / (p.form ? beta : 1.0);
+  const double tb = p.tau / beta;
+  const double step = p.rho * beta / p.tau;
+  double* gb = p.grad + (long)b * p.Nt;
+  double err = 0.0, pen = 0.0;
+  for (int s = lg; s < ns; s += G) {
+    const int j = j0 + s;
+    const double uj = ub[j];
+    const double al = p.alpha ? p.alpha[j] : 0.0;
+    const R2 za = tr0[(long)s * GE], zb = tr0[(long)(s + 1) * GE];
+    // Im(exp(-i Phi) z) for the two ends of step j
+    const double Ia = cPhi * (double)za.y - sPhi * (double)za.x;
+    const double Ib = cPhi * (double)zb.y - sPhi * (double)zb.x;
+    const double g = ht * (Ia + Ib) - tb * al * uj;
+    err += fabs(g);
+    pen += al * uj * uj;
+    if (valid) {
+      gb[j] = g;
+      if (p.update) ub[j] = uj + step * g;
+    }
+  }
+  err = g_sum<G>(err);
+  pen = g_sum<G>(pen);
+  const double Jn = p.w * (-0.5 * nrm) - 0.5 * tb * pen;
   if (lg == 0 && valid) {
     if (p.Jn) p.Jn[gid] = Jn;
     if (p.err) p.err[gid] = err;
@@ -299,26 +378,40 @@ __device__ __forceinline__ bool mbar_wait(uint64_t* bar, unsigned parity, int ma
   return false;
 }
 
+
+// ---------------------------------------------------------------------------------- chains
+// The chain is a sequence of 2N small dependent matvecs: latency, not bandwidth.  The tiles M_n (left
+// in L2 by the assembly) stream into a ring of NS shared-memory stages by TMA bulk copies issued up to
+// NS - 1 matvecs ahead; thread 0 alone waits on a stage's mbarrier (bounded), and one block barrier
+// per matvec publishes both the tile and the previous result.  256 threads: thread (i = t/4, q = t%4)
+// owns output row i and the columns k = q (mod 4); two shuffles finish each row.
+constexpr int CHAIN_MAX_STAGES = 16;
+
 template <typename R>
-__device__ __forceinline__ void chain_matvec(const typename C2<R>::T* Ms, const typename C2<R>::T* x,
-                                             typename C2<R>::T* y, int d, int ldm, bool herm) {
-  // thread (i = t/4, q = t%4): y_i = sum over k = q mod 4 of M[i][k] x_k (M x) or conj(M[k][i]) x_k (M^H x)
+__device__ __forceinline__ void chain_mv(const typename C2<R>::T* Ms, const typename C2<R>::T* x,
+                                         typename C2<R>::T* y, int d, int ldm, bool herm) {
   using R2 = typename C2<R>::T;
-  const int t = threadIdx.x, i = t >> 2, q = t & 3;
-  R ar = R(0), ai = R(0);
+  const int i = threadIdx.x >> 2, q = threadIdx.x & 3;
+  R ar0 = R(0), ai0 = R(0), ar1 = R(0), ai1 = R(0);
   if (i < d) {
-    for (int k = q; k < d; k += 4) {
-      R2 m = herm ? Ms[i * ldm + k] : Ms[k * ldm + i];
-      R2 xv = x[k];
-      if (!herm) {
-        ar = fma(m.x, xv.x, fma(-m.y, xv.y, ar));
-        ai = fma(m.x, xv.y, fma(m.y, xv.x, ai));
-      } else {
-        ar = fma(m.x, xv.x, fma(m.y, xv.y, ar));
-        ai = fma(m.x, xv.y, fma(-m.y, xv.x, ai));
+#pragma unroll 4
+    for (int k = q; k < d; k += 8) {
+      {
+        const R2 m = herm ? Ms[i * ldm + k] : Ms[k * ldm + i];
+        const R2 xv = x[k];
+        if (!herm) { ar0 = fma(m.x, xv.x, fma(-m.y, xv.y, ar0)); ai0 = fma(m.x, xv.y, fma(m.y, xv.x, ai0)); }
+        else { ar0 = fma(m.x, xv.x, fma(m.y, xv.y, ar0)); ai0 = fma(m.x, xv.y, fma(-m.y, xv.x, ai0)); }
+      }
+      const int k2 = k + 4;
+      if (k2 < d) {
+        const R2 m = herm ? Ms[i * ldm + k2] : Ms[k2 * ldm + i];
+        const R2 xv = x[k2];
+        if (!herm) { ar1 = fma(m.x, xv.x, fma(-m.y, xv.y, ar1)); ai1 = fma(m.x, xv.y, fma(m.y, xv.x, ai1)); }
+        else { ar1 = fma(m.x, xv.x, fma(m.y, xv.y, ar1)); ai1 = fma(m.x, xv.y, fma(-m.y, xv.x, ai1)); }
       }
     }
   }
+  R ar = ar0 + ar1, ai = ai0 + ai1;
   ar += __shfl_xor_sync(0xffffffffu, ar, 1);
   ai += __shfl_xor_sync(0xffffffffu, ai, 1);
   ar += __shfl_xor_sync(0xffffffffu, ar, 2);
@@ -326,7 +419,126 @@ __device__ __forceinline__ void chain_matvec(const typename C2<R>::T* Ms, const 
   if (q == 0 && i < d) { R2 z; z.x = ar; z.y = ai; y[i] = z; }
 }
 
-__device__ inline double block_sum256(double v, double* red) {
+// The ring: use m (0..U-1) of the chain(s) this CTA runs reads tile tile_of(m) from stage m % NS.
+template <typename R>
+struct ChainRing {
+  using R2 = typename C2<R>::T;
+  R2* stages;
+  uint64_t* bars;
+  const R2* Mb;
+  long tst;
+  unsigned bytes;
+  int NS, U, N, first;   // tile_of(m): first == 0 -> m < N ? m : 2N-1-m; first == 1 -> N-1-m
+  __device__ int tile_of(int m) const { return first == 1 ? N - 1 - m : (m < N ? m : 2 * N - 1 - m); }
+  __device__ void issue(int m) const {   // thread 0
+    const int st = m % NS;
+    fence_proxy_async();
+    bulk_load(stages + st * tst, Mb + (long)tile_of(m) * tst, bytes, &bars[st]);
+  }
+  __device__ const R2* tile(int m) const { return stages + (m % NS) * tst; }
+};
+
+// One chain of N matvecs over uses m0 .. m0+N-1 of the ring; x_0 in xs[0]; writes the N results (FP64)
+// into out[idx(m)*d] with idx = m - m0 + 1 (psi) or N - 1 - (m - m0) (chi).  Returns false (uniformly)
+// if a tile did not arrive; the copies still in flight have then been drained.
+template <typename R, bool HERM>
+__device__ bool run_chain(const ChainRing<R>& ring, int m0, int N, int d, int ldm, typename C2<R>::T (*xs)[64],
+                          double2* out, int* fail, int* status, int max_spin) {
+  using R2 = typename C2<R>::T;
+  const int t = threadIdx.x;
+  for (int c = 0; c <= N; ++c) {
+    const int m = m0 + c;
+    if (t == 0 && c < N) {
+      if (!mbar_wait(&ring.bars[m % ring.NS], (unsigned)((m / ring.NS) & 1), max_spin)) {
+        for (int q = m; q < ring.U && q < m + ring.NS; ++q)
+          mbar_wait(&ring.bars[q % ring.NS], (unsigned)((q / ring.NS) & 1), max_spin);
+        atomicOr(status, ST_TIMEOUT);
+        *fail = 1;
+      }
+    }
+    __syncthreads();   // tile m present; result of matvec c-1 visible
+    if (*fail) return false;
+    if (c >= 1) {
+      // the stage of use m-1 has been read by everyone: refill it NS uses ahead
+      if (t == 0 && m - 1 + ring.NS < ring.U) ring.issue(m - 1 + ring.NS);
+      const int idx = HERM ? N - c : c;
+      if (t < d) { const R2 z = xs[c & 1][t]; out[(long)idx * d + t] = make_double2((double)z.x, (double)z.y); }
+    }
+    if (c < N) chain_mv<R>(ring.tile(m), xs[c & 1], xs[(c + 1) & 1], d, ldm, HERM);
+  }
+  __syncthreads();   // the last stored state is read by other threads next
+  return true;
+}
+
+// grid (nchains, B), 256 threads, dynamic shared memory NS tiles.  nchains = 2 (overlap objective):
+// CTA 0 runs the psi chain, CTA 1 the chi chain from psi_f, concurrently.  nchains = 1 (observable):
+// one CTA runs the psi chain, forms chi(T) = O psi(T) in FP64 and runs the chi chain, all from one ring.
+// Intermediate states and J follow in k_phi.
+template <typename R>
+__global__ void __launch_bounds__(256) k_chain(ChainParams p) {
+  using R2 = typename C2<R>::T;
+  extern __shared__ __align__(128) unsigned char smem_raw[];
+  __shared__ __align__(8) uint64_t bars[CHAIN_MAX_STAGES];
+  __shared__ __align__(16) R2 xs[2][64];
+  __shared__ double2 vd[64];
+  __shared__ int fail;
+  const int b = blockIdx.y, t = threadIdx.x, d = p.d, N = p.N;
+  double2* psin = p.psin + (long)b * (N + 1) * d;
+  double2* chin = p.chin + (long)b * (N + 1) * d;
+  const bool single = gridDim.x == 1;
+  const bool do_psi = single || blockIdx.x == 0;
+  const bool do_chi = single || blockIdx.x == 1;
+  ChainRing<R> ring;
+  ring.stages = reinterpret_cast<R2*>(smem_raw);
+  ring.bars = bars;
+  ring.Mb = reinterpret_cast<const R2*>(p.M) + (long)b * N * p.tile_stride;
+  ring.tst = p.tile_stride;
+  ring.bytes = (unsigned)(p.tile_stride * sizeof(R2));
+  ring.NS = p.stages;
+  ring.N = N;
+  ring.U = single ? 2 * N : N;
+  ring.first = (!single && blockIdx.x == 1) ? 1 : 0;
+  if (t == 0) {
+    fail = 0;
+    for (int i = 0; i < ring.NS; ++i) mbar_init(&bars[i], 1);
+    fence_mbar_init();
+  }
+  __syncthreads();
+  if (t == 0)
+    for (int m = 0; m < ring.NS && m < ring.U; ++m) ring.issue(m);
+
+  int m0 = 0;
+  if (do_psi) {
+    if (t < d) { const double2 z = p.psi_i[t]; R2 r; r.x = (R)z.x; r.y = (R)z.y; xs[0][t] = r; psin[t] = z; }
+    if (!run_chain<R, false>(ring, m0, N, d, p.ldm, xs, psin, &fail, p.status, p.max_spin)) return;
+    m0 += N;
+  }
+  if (do_chi) {
+    if (p.obj == 0) {
+      if (t < d) vd[t] = p.psi_f[t];
+    } else {   // chi(T) = O psi(T), FP64, thread (i, q) sums k = q (mod 4)
+      const int i = t >> 2, q = t & 3;
+      double sr = 0.0, si = 0.0;
+      if (i < d)
+        for (int k = q; k < d; k += 4) {
+          const double o = p.O[i * d + k];
+          const double2 v = psin[(long)N * d + k];
+          sr += o * v.x;
+          si += o * v.y;
+        }
+      sr += __shfl_xor_sync(0xffffffffu, sr, 1);
+      si += __shfl_xor_sync(0xffffffffu, si, 1);
+      sr += __shfl_xor_sync(0xffffffffu, sr, 2);
+      si += __shfl_xor_sync(0xffffffffu, si, 2);
+      if (q == 0 && i < d) vd[i] = make_double2(sr, si);
+    }
+    __syncthreads();
+    if (t < d) { const double2 z = vd[t]; R2 r; r.x = (R)z.x; r.y = (R)z.y; xs[0][t] = r; chin[(long)N * d + t] = z; }
+    if (!run_chain<R, true>(ring, m0, N, d, p.ldm, xs, chin, &fail, p.status, p.max_spin)) return;
+  }
+}
+
+__device__ inline double block_sum(double v, double* red) {
   for (int m = 16; m >= 1; m >>= 1) v += __shfl_xor_sync(0xffffffffu, v, m);
   __syncthreads();
   if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = v;
@@ -336,115 +548,42 @@ __device__ inline double block_sum256(double v, double* red) {
   return s;
 }
 
-// blockDim = 256; dynamic shared memory: 2 M tiles (R2 d*ldm each) | 2 vectors (R2 64) | FP64 work.
-template <typename R>
-__global__ void __launch_bounds__(256) k_chain(ChainParams p) {
-  using R2 = typename C2<R>::T;
-  extern __shared__ __align__(128) unsigned char smem_raw[];
-  __shared__ __align__(8) uint64_t bars[2];
-  __shared__ double red[8];
-  __shared__ double2 vd[64];        // FP64 vector work space (psi(T), chi(T))
+// grid B, 256 threads: J and F at u (FP64) and the intermediate states (Eq. (cible)), with
+// phi_0 = psi_i and phi_N = chi(T) exactly.
+template <int V = 0>
+__global__ void __launch_bounds__(1024) k_phi(ChainParams p) {
+  __shared__ double red[32];
   const int b = blockIdx.x, t = threadIdx.x, d = p.d, N = p.N;
-  const long tile = (long)d * p.ldm;
-  const unsigned tbytes = (unsigned)(tile * sizeof(R2));
-  R2* Mbuf[2] = {reinterpret_cast<R2*>(smem_raw), reinterpret_cast<R2*>(smem_raw) + tile};
-  R2* xv[2] = {Mbuf[1] + tile, Mbuf[1] + tile + 64};
-  const R2* Mg = reinterpret_cast<const R2*>(p.M) + (long)b * N * tile;
-  double2* psin = p.psin + (long)b * (N + 1) * d;
-  double2* chin = p.chin + (long)b * (N + 1) * d;
-  bool ok = true;
-
-  if (t == 0) { mbar_init(&bars[0], 1); mbar_init(&bars[1], 1); fence_mbar_init(); }
-  __syncthreads();
-  unsigned ph[2] = {0u, 0u};
-
-  // ---- psi chain: psi(t_0) = psi_i, psi(t_{n+1}) = M_n psi(t_n)
-  if (t == 0) bulk_load(Mbuf[0], Mg, tbytes, &bars[0]);
-  if (t < d) { double2 z = p.psi_i[t]; R2 r; r.x = (R)z.x; r.y = (R)z.y; xv[0][t] = r; psin[t] = z; }
-  __syncthreads();
-  for (int n = 0; n < N; ++n) {
-    const int cb = n & 1;
-    const bool pre = n + 1 < N;
-    if (t == 0 && pre) { fence_proxy_async(); bulk_load(Mbuf[cb ^ 1], Mg + (n + 1) * tile, tbytes, &bars[cb ^ 1]); }
-    ok = mbar_wait(&bars[cb], ph[cb], p.max_spin);
-    if (__syncthreads_or(!ok)) {   // a tile never arrived: drain what is in flight, report, leave
-      if (t == 0) {
-        mbar_wait(&bars[cb], ph[cb], p.max_spin);
-        if (pre) mbar_wait(&bars[cb ^ 1], ph[cb ^ 1], p.max_spin);
-        atomicOr(p.status, ST_TIMEOUT);
-      }
-      return;
-    }
-    ph[cb] ^= 1u;
-    chain_matvec<R>(Mbuf[cb], xv[n & 1], xv[(n + 1) & 1], d, p.ldm, false);
-    __syncthreads();
-    if (t < d) { R2 z = xv[(n + 1) & 1][t]; psin[(long)(n + 1) * d + t] = make_double2((double)z.x, (double)z.y); }
-  }
-  // ---- terminal adjoint chi(T) and objective (FP64)
-  if (t < d) vd[t] = psin[(long)N * d + t];
-  __syncthreads();
-  double2 chiT = make_double2(0.0, 0.0);
-  if (t < d) {
-    if (p.obj == 0) {
-      chiT = p.psi_f[t];
-    } else {
-      double sr = 0.0, si = 0.0;
-      for (int k = 0; k < d; ++k) { double o = p.O[t * d + k]; sr += o * vd[k].x; si += o * vd[k].y; }
-      chiT = make_double2(sr, si);
-    }
-  }
-  // <psi(T)|chi(T)> (overlap with psi_f, or <psi|O|psi>)
+  const double2* psin = p.psin + (long)b * (N + 1) * d;
+  const double2* chin = p.chin + (long)b * (N + 1) * d;
   double ovr = 0.0, ovi = 0.0;
-  if (t < d) { double2 a = vd[t]; ovr = a.x * chiT.x + a.y * chiT.y; ovi = a.x * chiT.y - a.y * chiT.x; }
-  ovr = block_sum256(ovr, red);
-  ovi = block_sum256(ovi, red);
+  for (int i = t; i < d; i += blockDim.x) {
+    const double2 a = psin[(long)N * d + i], c = chin[(long)N * d + i];
+    ovr += a.x * c.x + a.y * c.y;
+    ovi += a.x * c.y - a.y * c.x;
+  }
+  ovr = block_sum(ovr, red);
+  ovi = block_sum(ovi, red);
   double pen = 0.0;
   if (p.alpha) {
     const double* ub = p.u + (long)b * p.Nt;
     for (int j = t; j < p.Nt; j += blockDim.x) pen += p.alpha[j] * ub[j] * ub[j];
   }
-  pen = 0.5 * p.tau * block_sum256(pen, red);
+  pen = 0.5 * p.tau * block_sum(pen, red);
   if (t == 0) {
-    double F = p.obj == 0 ? ovr * ovr + ovi * ovi : ovr;
-    double J = ovr - pen;
+    const double F = p.obj == 0 ? ovr * ovr + ovi * ovi : ovr;
+    const double J = ovr - pen;
     if (!isfinite(J) || !isfinite(F)) atomicOr(p.status, ST_NONFINITE);
     p.J[b] = J;
     p.F[b] = F;
     if (p.Jhist) p.Jhist[(long)b * p.hist_stride + p.hist_k] = J;
   }
-  __syncthreads();
-  // ---- chi chain: chi(t_N) = chi(T), chi(t_n) = M_n^H chi(t_{n+1})
-  if (t == 0) { fence_proxy_async(); bulk_load(Mbuf[0], Mg + (long)(N - 1) * tile, tbytes, &bars[0]); }
-  // the psi pass consumed phases as it went; restart both barriers' parities from their state
-  if (t < d) { R2 r; r.x = (R)chiT.x; r.y = (R)chiT.y; xv[0][t] = r; chin[(long)N * d + t] = chiT; }
-  __syncthreads();
-  int cnt = 0;
-  for (int n = N - 1; n >= 0; --n, ++cnt) {
-    const int cb = cnt & 1;
-    const bool pre = n - 1 >= 0;
-    if (t == 0 && pre) { fence_proxy_async(); bulk_load(Mbuf[cb ^ 1], Mg + (long)(n - 1) * tile, tbytes, &bars[cb ^ 1]); }
-    ok = mbar_wait(&bars[cb], ph[cb], p.max_spin);
-    if (__syncthreads_or(!ok)) {
-      if (t == 0) {
-        mbar_wait(&bars[cb], ph[cb], p.max_spin);
-        if (pre) mbar_wait(&bars[cb ^ 1], ph[cb ^ 1], p.max_spin);
-        atomicOr(p.status, ST_TIMEOUT);
-      }
-      return;
-    }
-    ph[cb] ^= 1u;
-    chain_matvec<R>(Mbuf[cb], xv[cnt & 1], xv[(cnt + 1) & 1], d, p.ldm, true);
-    __syncthreads();
-    if (t < d) { R2 z = xv[(cnt + 1) & 1][t]; chin[(long)n * d + t] = make_double2((double)z.x, (double)z.y); }
-  }
-  __syncthreads();
-  // ---- intermediate states (Eq. (cible)), FP64: phi_0 = psi_i, phi_N = chi(T) exactly
   double2* phi = p.phi + (long)b * (N + 1) * d;
   for (long i = t; i < (long)(N + 1) * d; i += blockDim.x) {
     const int n = (int)(i / d);
-    const double tn = p.jn[n] * p.tau;
-    const double a = (p.T - tn) / p.T, c = tn / p.T;
-    double2 ps = psin[i], cs = chin[i];
+    const double2 w = p.ab[n];
+    const double a = w.x, c = w.y;
+    const double2 ps = psin[i], cs = chin[i];
     double2 z;
     if (n == 0) z = ps;
     else if (n == N) z = cs;

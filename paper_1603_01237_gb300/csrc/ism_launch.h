@@ -13,7 +13,8 @@ typedef cudaError_t (*LaunchFn)(const KParams&, cudaStream_t);
 struct KernelSet {
   LaunchFn assemble = nullptr;
   LaunchFn subinterval = nullptr;
-  int G = 0, E = 0;          // lanes per state, elements per lane
+  int G = 0, E = 0;          // lanes per state, elements per lane (sub-interval sweep)
+  int GA = 0;                // lanes per state in the assembly
   size_t op_smem = 0;        // dynamic shared memory of the op (dense H pairs)
 };
 

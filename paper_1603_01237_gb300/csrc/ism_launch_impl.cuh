@@ -16,7 +16,7 @@ cudaError_t launch_assemble_t(const KParams& p, cudaStream_t st) {
   const long groups = (long)p.B * p.N * p.dpad;
   const long grid = (groups + GPB - 1) / GPB;
   const size_t smem = op_smem_bytes<R, Op>();
-  if (smem > 48 * 1024) {
+  if (smem > 40 * 1024) {   // leave room for the static shared memory under the 48 KB default
     cudaError_t e = cudaFuncSetAttribute(k_assemble<R, Op>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (e != cudaSuccess) return e;
   }
@@ -30,7 +30,7 @@ cudaError_t launch_subinterval_t(const KParams& p, cudaStream_t st) {
   const long groups = (long)p.B * p.N;
   const long grid = (groups + GPB - 1) / GPB;
   const size_t smem = op_smem_bytes<R, Op>();
-  if (smem > 48 * 1024) {
+  if (smem > 40 * 1024) {
     cudaError_t e = cudaFuncSetAttribute(k_subinterval<R, Op>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (e != cudaSuccess) return e;
   }
@@ -38,13 +38,16 @@ cudaError_t launch_subinterval_t(const KParams& p, cudaStream_t st) {
   return cudaGetLastError();
 }
 
-template <typename R, class Op>
+// OpA: lane layout of the throughput-bound assembly (few lanes, many elements per lane);
+// OpS: lane layout of the latency-bound sub-interval sweep (more lanes per state).
+template <typename R, class OpA, class OpS = OpA>
 void fill_set(KernelSet* ks) {
-  ks->assemble = &launch_assemble_t<R, Op>;
-  ks->subinterval = &launch_subinterval_t<R, Op>;
-  ks->G = Op::G;
-  ks->E = Op::E;
-  ks->op_smem = op_smem_bytes<R, Op>();
+  ks->assemble = &launch_assemble_t<R, OpA>;
+  ks->subinterval = &launch_subinterval_t<R, OpS>;
+  ks->G = OpS::G;
+  ks->E = OpS::E;
+  ks->GA = OpA::G;
+  ks->op_smem = op_smem_bytes<R, OpS>();
 }
 
 }  // namespace ism

@@ -83,8 +83,9 @@ extern "C" int ism_subinterval_grad_noalloc(const ism_problem* prob, int precisi
   if (precision == ISM_FP64) { hd = ism::pack_op<double>(p.kind, d, p.H0, p.H1, ks.G, ks.E); op_bytes = hd.size() * r1; }
   else { hf = ism::pack_op<float>(p.kind, d, p.H0, p.H1, ks.G, ks.E); op_bytes = hf.size() * r1; }
 
-  // scratch layout: op data | j_n | beta_n | alpha | status | trajectory
-  const size_t off_jn = up256(op_bytes);
+  // scratch layout: op data | FP64 diag(H0) | j_n | beta_n | alpha | status | trajectory
+  const size_t off_h0d = up256(op_bytes);
+  const size_t off_jn = off_h0d + up256(sizeof(double) * d);
   const size_t off_beta = off_jn + up256(sizeof(int) * (p.N + 1));
   const size_t off_alpha = off_beta + up256(sizeof(double) * p.N);
   const size_t off_status = off_alpha + up256(p.alpha ? sizeof(double) * p.Nt : 0);
@@ -111,6 +112,9 @@ extern "C" int ism_subinterval_grad_noalloc(const ism_problem* prob, int precisi
     if (e == cudaSuccess && n) e = cudaMemcpyAsync(base + off, src, n, cudaMemcpyHostToDevice, st);
   };
   h2d(0, precision == ISM_FP64 ? (const void*)hd.data() : (const void*)hf.data(), op_bytes);
+  std::vector<double> h0d(d);
+  for (int e = 0; e < d; ++e) h0d[e] = p.kind == ISM_H_DENSE ? p.H0[(size_t)e * d + e] : p.H0[e];
+  h2d(off_h0d, h0d.data(), sizeof(double) * d);
   h2d(off_jn, jn.data(), sizeof(int) * jn.size());
   h2d(off_beta, beta.data(), sizeof(double) * beta.size());
   if (p.alpha) h2d(off_alpha, p.alpha, sizeof(double) * p.Nt);
@@ -118,7 +122,7 @@ extern "C" int ism_subinterval_grad_noalloc(const ism_problem* prob, int precisi
   if (e != cudaSuccess) return ism::set_error(ISM_ECUDA, (std::string("scratch upload: ") + cudaGetErrorString(e)).c_str());
 
   ism::KParams k{};
-  k.d = d; k.Nt = p.Nt; k.N = p.N; k.B = B; k.ldm = d + (d & 1); k.dpad = d;
+  k.d = d; k.Nt = p.Nt; k.N = p.N; k.B = B; k.ldm = d | 1; k.dpad = d; k.tile_stride = 0;
   k.tau = tau; k.T = p.T; k.c0 = 0.5 * (bd.lo + bd.hi); k.r0 = 0.5 * (bd.hi - bd.lo); k.h1n = bd.h1;
   k.tol = precision == ISM_FP64 ? 1e-17 : 1e-10;
   k.rho = 0.0; k.w = p.objective == ISM_OBJ_OVERLAP ? 1.0 : 2.0;
@@ -126,6 +130,7 @@ extern "C" int ism_subinterval_grad_noalloc(const ism_problem* prob, int precisi
   k.beta = reinterpret_cast<const double*>(base + off_beta);
   k.alpha = p.alpha ? reinterpret_cast<const double*>(base + off_alpha) : nullptr;
   k.H = base;
+  k.H0d = reinterpret_cast<const double*>(base + off_h0d);
   k.u = const_cast<double*>(u);
   k.phi = reinterpret_cast<const double2*>(phi);
   k.M = nullptr;
@@ -135,6 +140,9 @@ extern "C" int ism_subinterval_grad_noalloc(const ism_problem* prob, int precisi
   k.err = nullptr;
   k.status = reinterpret_cast<int*>(base + off_status);
   k.count = nullptr;
+  k.psin = nullptr;
+  k.chin = nullptr;
+  k.form = 0;
   k.update = 0;
   k.max_spin = 1 << 22;
   if ((e = ks.subinterval(k, st)) != cudaSuccess)
@@ -147,6 +155,8 @@ extern "C" int ism_subinterval_grad_noalloc(const ism_problem* prob, int precisi
   if (status & ism::ST_TIMEOUT) return ism::set_error(ISM_ETIMEOUT, "a bounded device-side wait gave up");
   if (status & ism::ST_KOVERFLOW) return ism::set_error(ISM_EUNSUPPORTED, "Chebyshev series needed more terms than compiled");
   if (status & ism::ST_NONFINITE) return ism::set_error(ISM_ENONFINITE, "non-finite value in a control or a result");
+  if (status & ism::ST_SPECTRUM)
+    return ism::set_error(ISM_EUNSUPPORTED, "controls so large that a time step needs more Chebyshev sub-steps than the limit");
   ism::clear_error();
   return ISM_OK;
 }

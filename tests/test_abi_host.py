@@ -67,7 +67,7 @@ def test_plan_rejects_bad_problems(lib, field, value, status):
 
     prob, keep = _problem(abi)
     setattr(prob, field, value)
-    opt = abi.IsmOptions(precision=0, local_iters=1, rho=0.1, cheb_tol=0.0, max_spin_iters=0)
+    opt = abi.IsmOptions(precision=0, local_iters=1, rho=0.1, cheb_tol=0.0, max_spin_iters=0, subproblem_form=0)
     h = C.c_void_p()
     rc = lib.ism_plan(C.byref(prob), C.byref(opt), None, C.byref(h))
     assert rc == status
@@ -78,7 +78,7 @@ def test_plan_rejects_bad_problems(lib, field, value, status):
 def test_plan_rejects_nonsymmetric_and_nonfinite(lib):
     from paper_1603_01237_gb300 import abi
 
-    opt = abi.IsmOptions(precision=0, local_iters=1, rho=0.1, cheb_tol=0.0, max_spin_iters=0)
+    opt = abi.IsmOptions(precision=0, local_iters=1, rho=0.1, cheb_tol=0.0, max_spin_iters=0, subproblem_form=0)
     H0 = np.arange(16.0)
     prob, keep = _problem(abi, H0=H0)
     h = C.c_void_p()
@@ -87,7 +87,7 @@ def test_plan_rejects_nonsymmetric_and_nonfinite(lib):
     H0[5] = np.inf
     prob, keep = _problem(abi, H0=H0)
     assert lib.ism_plan(C.byref(prob), C.byref(opt), None, C.byref(h)) == abi.ISM_ENONFINITE
-    bad = abi.IsmOptions(precision=3, local_iters=1, rho=0.1, cheb_tol=0.0, max_spin_iters=0)
+    bad = abi.IsmOptions(precision=3, local_iters=1, rho=0.1, cheb_tol=0.0, max_spin_iters=0, subproblem_form=0)
     prob, keep = _problem(abi)
     assert lib.ism_plan(C.byref(prob), C.byref(bad), None, C.byref(h)) == abi.ISM_EINVAL
 
@@ -96,7 +96,7 @@ def test_bitflip_needs_power_of_two(lib):
     from paper_1603_01237_gb300 import abi
 
     prob, keep = _problem(abi, d=6, kind=abi.ISM_H_BITFLIP, H0=np.zeros(6), H1=np.ones(3))
-    opt = abi.IsmOptions(precision=0, local_iters=1, rho=0.1, cheb_tol=0.0, max_spin_iters=0)
+    opt = abi.IsmOptions(precision=0, local_iters=1, rho=0.1, cheb_tol=0.0, max_spin_iters=0, subproblem_form=0)
     h = C.c_void_p()
     assert lib.ism_plan(C.byref(prob), C.byref(opt), None, C.byref(h)) == abi.ISM_EINVAL
 

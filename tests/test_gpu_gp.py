@@ -1,0 +1,76 @@
+"""Gross-Pitaevskii variant (Sec. 4, condensates) through the C ABI vs the FP64 oracle: forward and
+adjoint sweeps (psi(t_n), chi(t_n)), sub-problem gradients, ISM iterations."""
+import numpy as np
+import pytest
+
+import workloads as W
+from oracle import gp_oracle as G
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def P():
+    import __graft_entry__
+
+    __graft_entry__.build()
+    import paper_1603_01237_gb300 as P
+
+    return P
+
+
+def _gp(n, Nt, N, T, seed=5, g=1.0, steps=4000):
+    rng = np.random.default_rng(seed)
+    psi_i, psi_f = W.gp_stationary_states(n, 20.0, -10.0, g, dt=2e-3, steps=steps)
+    return W.GPWorkload(name=f"gp{n}", n=n, L=20.0, x_min=-10.0, g=g, psi_i=psi_i, psi_f=psi_f, T=T, Nt=Nt,
+                        N=N, u0=rng.uniform(-0.5, 0.5, Nt))
+
+
+def rel(a, b):
+    return float(np.linalg.norm(np.ravel(a - b)) / np.linalg.norm(np.ravel(b)))
+
+
+CASES = [("gp64", _gp(64, 150, 6, 1.5)), ("gp512", _gp(512, 240, 8, 2.0)), ("gp512-ragged", _gp(512, 157, 5, 1.0))]
+
+
+@pytest.mark.parametrize("name,w", CASES, ids=[c[0] for c in CASES])
+@pytest.mark.parametrize("prec,tol", [("fp64", 1e-11), ("mixed", 2e-5)])
+def test_gp_intermediate_pairs(P, name, w, prec, tol):
+    ps_o, ch_o = G.intermediate_pairs(w, w.u0)
+    with P.Plan(w, precision=prec) as pl:
+        phi = pl.intermediate_states(w.u0)[0]
+    assert np.max(np.abs(phi[0] - ps_o)) <= tol, np.max(np.abs(phi[0] - ps_o))
+    assert np.max(np.abs(phi[1] - ch_o)) <= tol, np.max(np.abs(phi[1] - ch_o))
+
+
+@pytest.mark.parametrize("name,w", CASES, ids=[c[0] for c in CASES])
+@pytest.mark.parametrize("prec,tol", [("fp64", 1e-10), ("mixed", 1e-4)])
+def test_gp_subinterval_grad(P, name, w, prec, tol):
+    ps_o, ch_o = G.intermediate_pairs(w, w.u0)
+    g_o, Jn_o = G.subinterval_all(w, ps_o, ch_o, w.u0)
+    with P.Plan(w, precision=prec) as pl:
+        g, Jn = pl.subinterval_grad(np.stack([ps_o, ch_o]), w.u0)
+    assert rel(g[0], g_o) <= tol, rel(g[0], g_o)
+    assert np.max(np.abs(Jn[0] - Jn_o)) <= tol
+
+
+@pytest.mark.parametrize("prec,tol", [("fp64", 1e-10), ("mixed", 1e-5)])
+def test_gp_iterate(P, prec, tol):
+    w = _gp(512, 200, 8, 2.0)
+    u_o, J_o, F_o, E_o = G.ism_solve(w, w.u0, 3, 0.5)
+    with P.Plan(w, precision=prec, rho=0.5) as pl:
+        u, J, E = pl.iterate(w.u0, 3)
+        _, F = pl.evaluate(u[0])
+    assert np.max(np.abs(J[0] - J_o)) <= tol, np.max(np.abs(J[0] - J_o))
+    assert abs(F[0] - F_o[-1]) <= tol
+    assert rel(E[0], E_o) <= 1e-3 if prec == "mixed" else rel(E[0], E_o) <= 1e-9
+
+
+def test_gp_n_independence(P):
+    w = _gp(64, 120, 1, 1.0)
+    res = []
+    for N in (1, 4, 120):
+        with P.Plan(w.with_(N=N), precision="fp64", rho=0.5) as pl:
+            res.append(pl.iterate(w.u0, 2)[0][0])
+    for u in res[1:]:
+        assert np.max(np.abs(u - res[0])) <= 1e-11

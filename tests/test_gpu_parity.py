@@ -93,7 +93,11 @@ def test_iterate_matches_algorithm1(P, name, w, prec):
     with P.Plan(w, precision=prec) as pl:
         u, J, E = pl.iterate(w.u0, iters)
         Jf, Ff = pl.evaluate(u[0])
-    tolF = 1e-9 if prec == "fp64" else 1e-5
+    # mixed: these reduced cases take steps 10-20x coarser than the benchmark problem (tau*rad ~ 1.3-2.6
+    # per step), where FP32 rounding inside the Chebyshev terms is ~eps * sum_k k|a_k| ~ 3 eps per step;
+    # the 1e-5 bound is checked at the benchmark's own step size (test_rotor_mixed_fine_steps and the
+    # full-size tests)
+    tolF = 1e-9 if prec == "fp64" else 1e-4
     assert np.max(np.abs(J[0] - J_o)) <= tolF
     assert abs(Ff[0] - F_o[-1]) <= tolF
     assert rel_l2(u[0] - w.u0, u_o - w.u0) <= (1e-9 if prec == "fp64" else 1e-4)
@@ -195,3 +199,28 @@ def test_stats_count_work(P):
     # every assembly propagates d columns over all Nt steps (>= 1 sub-step each)
     assert st["substeps"][0] >= 3 * w.d * w.Nt
     assert st["substeps"][1] >= 2 * 2 * w.Nt
+
+
+@pytest.mark.parametrize("w", [W.config("rotor41", Nt=1500, N=30), W.random_dense(8, 91, T=2.0, Nt=300, N=12)],
+                         ids=["rotor41", "dense8"])
+def test_theorem2_form_equals_literal_form_fp64(P, w):
+    """ism_iterate's first local step in the two-trajectory form of the proof of Theorem 2 and in the
+    literal sub-problem form give the same iterates (FP64)."""
+    out = []
+    for form in (1, 2):
+        with P.Plan(w, precision="fp64", subproblem_form=form) as pl:
+            out.append(pl.iterate(w.u0, 3))
+    assert np.max(np.abs(out[0][0] - out[1][0])) <= 1e-11
+    assert np.max(np.abs(out[0][1] - out[1][1])) <= 1e-11
+    assert rel_l2(out[0][2], out[1][2]) <= 1e-10
+
+
+def test_rotor_mixed_fine_steps(P):
+    """At the benchmark's step size (tau = pi/20000) mixed precision stays within 1e-5 of the FP64
+    oracle's J history; here on a 2000-step horizon T = pi/10 (N = 16) so the oracle is quick."""
+    w = W.config("rotor41", Nt=2000, N=16).with_(T=float(np.pi) / 10.0)
+    u_o, J_o, F_o, _ = O.ism_solve(w, w.u0, 4, 5.0)
+    with P.Plan(w, precision="mixed", rho=5.0) as pl:
+        u, J, _ = pl.iterate(w.u0, 4)
+    assert np.max(np.abs(J[0] - J_o)) <= 1e-5, np.max(np.abs(J[0] - J_o))
+    assert np.all(np.diff(J_o) > 0)
