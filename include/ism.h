@@ -60,7 +60,7 @@ typedef enum {
      (H[d+e] couples e and e+1).  d <= 64.                                                        */
   ISM_H_TRIDIAG = 2,
   /* Gross-Pitaevskii condensate (Sec. 4): i d/dt psi = (-1/2 d^2/dx^2 + (x - u)^2/2 + g|psi|^2) psi on a
-     periodic grid of d = 64, 512 or 4096 points x_k = x_min + k L/d, Strang splitting (Eq. (OS)),
+     periodic grid of d = 64 or 512 points x_k = x_min + k L/d, Strang splitting (Eq. (OS)),
      <a|b> = sum conj(a) b L/d.  H0 = {L, x_min, g}; H1 unused (may be NULL); overlap objective only,
      alpha must be NULL.  The sub-problems are the nonlinear variant of Sec. 4: initial states
      psi(t_n) on the forward trajectory, targets chi(t_n) on the adjoint trajectory (the discrete
@@ -173,13 +173,16 @@ int ism_evaluate(ism_plan_t plan, const double* u, double* J, double* F);
  *                       and launches of phase p = 0 assembly, 1 chain, 2 sub-interval.
  *   y_apps[k], terms[k], substeps[k]: for k = 0 assembly, 1 sub-interval sweeps, the number of
  *     applications of the scaled Hamiltonian to one state, of accumulated Chebyshev terms and of
- *     exponential sub-steps -- the algorithmic work from which flop counts follow. */
+ *     exponential sub-steps -- the algorithmic work from which flop counts follow.
+ *   kernels: every kernel the plan launched (the phase kernels and the helpers that check inputs,
+ *     refresh propagator parameters and sum Err). */
 typedef struct {
   double ms[3];
   long long launches[3];
   unsigned long long y_apps[2];
   unsigned long long terms[2];
   unsigned long long substeps[2];
+  long long kernels;
 } ism_stats;
 
 /* ism_set_profiling -- on != 0 records CUDA events around every kernel on the plan's stream. */
@@ -191,7 +194,8 @@ int ism_get_stats(ism_plan_t plan, ism_stats* out, int reset);
 
 /* ism_plan_info -- integer facts about a plan, for tests and benchmarks:
  *   key 0: group lanes per state, 1: state elements per lane, 2: kernel launches per ISM
- *   iteration (L = local_iters), 3: bytes of plan-owned device memory.  Returns -1 for a bad key. */
+ *   iteration (L = local_iters), 3: bytes of plan-owned device memory, 4: bytes of one stored
+ *   sub-interval propagator M_n (0 for the grid kind, which assembles none).  Returns -1 for a bad key. */
 long long ism_plan_info(ism_plan_t plan, int key);
 
 /*

@@ -86,6 +86,10 @@ struct ism_plan_s {
   int* djn = nullptr;
   double* dbeta = nullptr;
   double2* dab = nullptr;   // (a_n, b_n), n = 0..N
+  unsigned char* dcheb = nullptr;   // propagator parameters per (problem, n)
+  unsigned char* dstage = nullptr;  // chain results before FP64 conversion
+  double* dpen = nullptr;           // penalty sums per (problem, n)
+  double* dctab = nullptr;          // Bessel series table
   double* dalpha = nullptr;
   double* dO = nullptr;
   double2* dpsi_i = nullptr;
@@ -95,6 +99,7 @@ struct ism_plan_s {
   double2* dchin = nullptr;
   double2* dphi = nullptr;
   void* dtraj = nullptr;
+  void* dtraj2 = nullptr;
   double* du = nullptr;
   double* dgrad = nullptr;
   double* dJn = nullptr;
@@ -112,6 +117,7 @@ struct ism_plan_s {
   std::vector<cudaEvent_t> pool;
   double ms[3] = {0, 0, 0};
   long long launches[3] = {0, 0, 0};
+  long long kernels = 0;   // every kernel launched, helpers included
   size_t chain_smem = 0;
   int chain_stages = 2;
   size_t bytes = 0;
@@ -155,8 +161,9 @@ cudaEvent_t take_event(ism_plan_s* P) {
 
 // Launch one phase kernel, bracketed by events when profiling is on.
 template <class F>
-cudaError_t timed(ism_plan_s* P, int phase, F&& launch) {
+cudaError_t timed(ism_plan_s* P, int phase, int nkernels, F&& launch) {
   P->launches[phase] += 1;
+  P->kernels += nkernels;
   if (!P->profiling) return launch();
   ism_plan_s::Ev ev{phase, take_event(P), take_event(P)};
   cudaEventRecord(ev.a, P->st);
@@ -258,7 +265,7 @@ int validate_problem(const ism_problem& p, int precision) {
     if (p.objective != ISM_OBJ_OVERLAP) return fail(ISM_EINVAL, "the grid kind supports the overlap objective only");
     if (p.alpha) return fail(ISM_EINVAL, "the grid kind has no control penalty (alpha must be NULL)");
     if (precision != ISM_FP64 && precision != ISM_MIXED) return fail(ISM_EINVAL, "unknown precision");
-    if (!gp_supported(d)) return fail(ISM_EUNSUPPORTED, "the grid kind supports d = 64, 512 or 4096 points");
+    if (!gp_supported(d)) return fail(ISM_EUNSUPPORTED, "the grid kind supports d = 64 or 512 points");
     if (!all_finite(p.H0, 3) || !(p.H0[0] > 0.0)) return fail(ISM_EINVAL, "grid parameters must be finite with L > 0");
     if (!all_finite(p.psi_i, 2L * d) || !all_finite(p.psi_f, 2L * d)) return fail(ISM_ENONFINITE, "non-finite psi_i or psi_f");
     return ISM_OK;
@@ -301,6 +308,15 @@ bool select_kernels(int prec, int kind, int d, KernelSet* ks) {
                                  : kernels_dense(prec, d, ks);
 }
 
+void bessel_table(double* out) {
+  for (int k = 0; k < 32; ++k) {
+    double f = 1.0;
+    for (int i = 2; i <= k; ++i) f /= (double)i;   // 1/k!
+    out[k * 25] = f;
+    for (int m = 1; m <= 24; ++m) out[k * 25 + m] = out[k * 25 + m - 1] / ((double)m * (double)(m + k));
+  }
+}
+
 }  // namespace ism
 
 namespace {
@@ -336,7 +352,8 @@ ism::KParams kparams(ism_plan_s* P, double* u) {
   k.tau = P->tau; k.T = P->T; k.c0 = P->c0; k.r0 = P->r0; k.h1n = P->h1n; k.tol = P->tol;
   k.rho = P->rho; k.w = P->w;
   k.jn = P->djn; k.beta = P->dbeta; k.alpha = P->dalpha; k.H = P->dH; k.H0d = P->dH0d;
-  k.u = u; k.phi = P->dphi; k.M = P->dM; k.traj = P->dtraj;
+  k.cheb = P->dcheb; k.ctab = P->dctab; k.pen = P->dpen;
+  k.u = u; k.phi = P->dphi; k.M = P->dM; k.traj = P->dtraj; k.traj2 = P->dtraj2;
   k.grad = P->dgrad; k.Jn = P->dJn; k.err = P->derr; k.status = P->dstatus;
   k.count = P->dcount;
   k.psin = P->dpsin; k.chin = P->dchin; k.form = 0;
@@ -360,20 +377,24 @@ int run_states(ism_plan_s* P, const double* u, double* Jhist, int hist_stride, i
   if (P->gp) {   // nonlinear: sequential forward sweep (psi(t_n), J) then adjoint sweep (chi(t_n))
     ism::GPParams g = gparams(P, const_cast<double*>(u));
     g.Jhist = Jhist; g.hist_stride = hist_stride; g.hist_k = hist_k;
-    ISM_CUDA_TRY(timed(P, 0, [&] { return ism::launch_gp_forward(P->prec, g, P->st); }));
+    ISM_CUDA_TRY(timed(P, 0, 1, [&] { return ism::launch_gp_forward(P->prec, g, P->st); }));
     g.count = P->dcount + 1;
-    ISM_CUDA_TRY(timed(P, 1, [&] { return ism::launch_gp_adjoint(P->prec, g, P->st); }));
+    ISM_CUDA_TRY(timed(P, 1, 1, [&] { return ism::launch_gp_adjoint(P->prec, g, P->st); }));
     return ISM_OK;
   }
   ism::KParams k = kparams(P, const_cast<double*>(u));
-  ISM_CUDA_TRY(timed(P, 0, [&] { return P->ks.assemble(k, P->st); }));
+  ISM_CUDA_TRY(timed(P, 0, 2, [&] {
+    cudaError_t e = ism::launch_cheb_prep(P->prec, k, P->st);
+    return e != cudaSuccess ? e : P->ks.assemble(k, P->st);
+  }));
   ism::ChainParams c{};
   c.d = P->d; c.Nt = P->Nt; c.N = P->N; c.B = P->B; c.ldm = P->ldm; c.obj = P->obj;
   c.tau = P->tau; c.T = P->T; c.M = P->dM; c.psi_i = P->dpsi_i; c.psi_f = P->dpsi_f; c.O = P->dO;
-  c.alpha = P->dalpha; c.u = u; c.jn = P->djn; c.ab = P->dab; c.psin = P->dpsin; c.chin = P->dchin; c.phi = P->dphi;
+  c.alpha = P->dalpha; c.u = u; c.jn = P->djn; c.ab = P->dab; c.stage = P->dstage;
+  c.pen = P->dalpha ? P->dpen : nullptr; c.psin = P->dpsin; c.chin = P->dchin; c.phi = P->dphi;
   c.J = P->dJ; c.F = P->dF; c.Jhist = Jhist; c.hist_stride = hist_stride; c.hist_k = hist_k;
   c.status = P->dstatus; c.max_spin = P->max_spin; c.stages = P->chain_stages; c.tile_stride = P->tst;
-  ISM_CUDA_TRY(timed(P, 1, [&] { return ism::launch_chain(P->prec, c, P->chain_smem, P->st); }));
+  ISM_CUDA_TRY(timed(P, 1, 2, [&] { return ism::launch_chain(P->prec, c, P->chain_smem, P->st); }));
   return ISM_OK;
 }
 
@@ -385,6 +406,7 @@ int stage_in(ism_plan_s* P, const double* src, long n, double* staging, const do
       int blocks = (int)std::min<long>(1024, (n + 255) / 256);
       if (blocks < 1) blocks = 1;
       k_check_finite<<<blocks, 256, 0, P->st>>>(src, n, P->dstatus);
+      P->kernels += 1;
       ISM_CUDA_TRY(cudaGetLastError());
     }
     *out = src;
@@ -524,6 +546,10 @@ int ism_plan(const ism_problem* prob, const ism_options* opt, void* cuda_stream,
   TRY_ALLOC(P->djn, (size_t)P->N + 1);
   TRY_ALLOC(P->dbeta, (size_t)P->N);
   TRY_ALLOC(P->dab, (size_t)P->N + 1);
+  TRY_ALLOC(P->dcheb, B * P->N * ism::cheb_bytes(P->prec));
+  TRY_ALLOC(P->dstage, B * 2 * ((size_t)P->N + 1) * d * P->r2);
+  TRY_ALLOC(P->dpen, B * P->N);
+  TRY_ALLOC(P->dctab, (size_t)ism::BESSEL_TABLE);
   if (p.alpha) TRY_ALLOC(P->dalpha, (size_t)P->Nt);
   TRY_ALLOC(P->dpsi_i, (size_t)d);
   TRY_ALLOC(P->dpsi_f, (size_t)d);
@@ -537,6 +563,9 @@ int ism_plan(const ism_problem* prob, const ism_options* opt, void* cuda_stream,
   unsigned char* dTb = nullptr;
   TRY_ALLOC(dTb, B * ((size_t)P->Nt + P->N) * GE * P->r2);
   P->dtraj = dTb;
+  unsigned char* dT2 = nullptr;
+  TRY_ALLOC(dT2, B * ((size_t)P->Nt + P->N) * GE * P->r2);
+  P->dtraj2 = dT2;
   TRY_ALLOC(P->du, B * P->Nt);
   TRY_ALLOC(P->dgrad, B * P->Nt);
   TRY_ALLOC(P->dJn, B * P->N);
@@ -558,6 +587,11 @@ int ism_plan(const ism_problem* prob, const ism_options* opt, void* cuda_stream,
     h2d(P->dH0d, h0d.data(), d * sizeof(double));
   }
   h2d(P->djn, jn.data(), jn.size() * sizeof(int));
+  {
+    std::vector<double> tab(ism::BESSEL_TABLE);
+    ism::bessel_table(tab.data());
+    h2d(P->dctab, tab.data(), tab.size() * sizeof(double));
+  }
   h2d(P->dbeta, beta.data(), beta.size() * sizeof(double));
   {
     std::vector<double2> ab(P->N + 1);   // Eq. (cible): a_n = (T - t_n)/T, b_n = t_n/T
@@ -607,6 +641,7 @@ long long ism_plan_info(ism_plan_t P, int key) {
     case 1: return P->ks.E;
     case 2: return 2 + P->L;
     case 3: return (long long)P->bytes;
+    case 4: return P->gp ? 0 : (long long)(P->tst * P->r2);
     default: return -1;
   }
 }
@@ -625,9 +660,11 @@ int ism_get_stats(ism_plan_t P, ism_stats* out, int reset) {
   unsigned long long c[6];
   ISM_CUDA_TRY(cudaMemcpy(c, P->dcount, sizeof(c), cudaMemcpyDeviceToHost));
   for (int i = 0; i < 3; ++i) { out->ms[i] = P->ms[i]; out->launches[i] = P->launches[i]; }
+  out->kernels = P->kernels;
   for (int k = 0; k < 2; ++k) { out->y_apps[k] = c[3 * k]; out->terms[k] = c[3 * k + 1]; out->substeps[k] = c[3 * k + 2]; }
   if (reset) {
     for (int i = 0; i < 3; ++i) { P->ms[i] = 0; P->launches[i] = 0; }
+    P->kernels = 0;
     ISM_CUDA_TRY(cudaMemset(P->dcount, 0, sizeof(c)));
   }
   return ISM_OK;
@@ -666,7 +703,7 @@ int ism_subinterval_grad(ism_plan_t P, const double* phi, const double* u, doubl
                                    cudaMemcpyDefault, P->st));
     ism::GPParams g = gparams(P, const_cast<double*>(ud));
     g.count = P->dcount + 3;
-    ISM_CUDA_TRY(timed(P, 2, [&] { return ism::launch_gp_sub(P->prec, g, P->st); }));
+    ISM_CUDA_TRY(timed(P, 2, 1, [&] { return ism::launch_gp_sub(P->prec, g, P->st); }));
     if ((rc = copy_out(P, grad, P->dgrad, (long)P->B * P->Nt))) return rc;
     if ((rc = copy_out(P, Jn, P->dJn, (long)P->B * P->N))) return rc;
     return finish(P);
@@ -681,7 +718,9 @@ int ism_subinterval_grad(ism_plan_t P, const double* phi, const double* u, doubl
   ism::KParams k = kparams(P, const_cast<double*>(ud));
   k.update = 0;
   k.count = P->dcount + 3;
-  ISM_CUDA_TRY(timed(P, 2, [&] { return P->ks.subinterval(k, P->st); }));
+  ISM_CUDA_TRY(ism::launch_cheb_prep(P->prec, k, P->st));
+  P->kernels += 1;
+  ISM_CUDA_TRY(timed(P, 2, 1, [&] { return P->ks.subinterval(k, P->st); }));
   if ((rc = copy_out(P, grad, P->dgrad, (long)P->B * P->Nt))) return rc;
   if ((rc = copy_out(P, Jn, P->dJn, (long)P->B * P->N))) return rc;
   return finish(P);
@@ -714,7 +753,7 @@ int ism_iterate(ism_plan_t P, int iters, double* u_inout, double* J_hist, double
       g.err = l == 0 ? P->derr : nullptr;
       g.Jn = l == 0 ? P->dJn : nullptr;
       g.count = P->dcount + 3;
-      ISM_CUDA_TRY(timed(P, 2, [&] { return ism::launch_gp_sub(P->prec, g, P->st); }));
+      ISM_CUDA_TRY(timed(P, 2, 1, [&] { return ism::launch_gp_sub(P->prec, g, P->st); }));
     }
     for (int l = 0; l < P->L && !P->gp; ++l) {
       ism::KParams k = kparams(P, ud);
@@ -723,10 +762,16 @@ int ism_iterate(ism_plan_t P, int iters, double* u_inout, double* J_hist, double
       k.err = l == 0 ? P->derr : nullptr;
       k.Jn = l == 0 ? P->dJn : nullptr;
       k.count = P->dcount + 3;
-      ISM_CUDA_TRY(timed(P, 2, [&] { return P->ks.subinterval(k, P->st); }));
+      if (l > 0) {   // controls moved
+        ISM_CUDA_TRY(ism::launch_cheb_prep(P->prec, k, P->st));
+        P->kernels += 1;
+      }
+      if (k.form) ISM_CUDA_TRY(timed(P, 2, 2, [&] { return P->ks.sweeps2(k, P->st); }));
+      else ISM_CUDA_TRY(timed(P, 2, 1, [&] { return P->ks.subinterval(k, P->st); }));
     }
     if (err_hist) {
       k_err_sum<<<P->B, 32, 0, P->st>>>(P->derr, P->N, P->B, P->derrhist, (int)stride, it);
+      P->kernels += 1;
       ISM_CUDA_TRY(cudaGetLastError());
     }
   }

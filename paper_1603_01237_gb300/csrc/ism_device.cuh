@@ -61,20 +61,6 @@ __device__ __forceinline__ int warp_max_i(int v) { return __reduce_max_sync(0xff
 template <typename R, int E> struct Vec { R re[E]; R im[E]; };
 
 // --------------------------------------------------------------- Bessel and Chebyshev set-up
-// J_k(x) from the ascending series sum_m (-1)^m (x/2)^(2m+k) / (m! (m+k)!), 0 <= x <= XMAX.
-__device__ inline double bessel_jk(int k, double x) {
-  const double h = 0.5 * x;
-  double t = 1.0;
-  for (int i = 1; i <= k; ++i) t *= h / (double)i;
-  double s = t;
-  const double h2 = h * h;
-  for (int m = 1; m < 60; ++m) {
-    t *= -h2 / ((double)m * (double)(m + k));
-    s += t;
-    if (fabs(t) <= 1e-18 * fabs(s)) break;
-  }
-  return s;
-}
 
 // Per-group propagator parameters (shared memory).  cf[k] carries a_k with the sign of (-i)^k folded
 // in: even k -> a_k (-1)^(k/2) multiplies the vector itself, odd k -> a_k (-1)^((k-1)/2) multiplies
@@ -87,6 +73,7 @@ template <typename R> struct Cheb {
   R a1h, a1l;       // signed a_1 as hi + lo
   R c, inv_rad;     // spectral centre and 1/rad (FP32 copies)
   double cd, s2d;   // spectral centre and 2/rad in FP64
+  double cph, sph;  // cos, sin of the sub-interval's global phase c * tau * (number of steps)
   int K, S;         // terms, sub-steps per time step
 };
 
@@ -95,53 +82,71 @@ template <typename R> __device__ __forceinline__ void split2(double v, R& hi, R&
   lo = sizeof(R) == 4 ? (R)(v - (double)hi) : R(0);
 }
 
-// Fill `ch` for a group whose controls satisfy |u| <= umax.  All lanes of the warp must call this
-// (K and S are made warp-uniform).  lg = lane in group.
-template <int G, typename R>
-__device__ void cheb_setup(Cheb<R>& ch, int lg, double tau, double c0, double r0, double h1n,
-                          double umax, double tol, int* status) {
-  double rad = (r0 + umax * h1n) * (1.0 + 1e-12) + 1e-12;
-  double x = tau * rad;
+// Chebyshev parameters of one sub-interval, computed by one warp (lane k evaluates J_k).
+// J_k(x) = (x/2)^k sum_m (-x^2/4)^m / (m! (m+k)!) by Horner's rule on the table
+// ctab[k * (BESSEL_M + 1) + m] = 1 / (m! (m+k)!) (FP64, built on the host): no divisions on the device,
+// whose FP64 rate is low.  umax bounds |u| on the sub-interval; nsteps gives the segment phase.
+constexpr int BESSEL_M = 24;
+
+template <typename R>
+__device__ void cheb_params(Cheb<R>& ch, const double* ctab, double tau, double c0, double r0, double h1n,
+                            double umax, double tol, int nsteps, int* status) {
+  const int lane = threadIdx.x & 31;
+  const double rad = (r0 + umax * h1n) * (1.0 + 1e-6) + 1e-12;
+  const double x = tau * rad;
   int S = x < XMAX * SMAX ? (int)ceil(x / XMAX) : SMAX + 1;
   if (S < 1) S = 1;
   if (S > SMAX) {   // |u| beyond what the sub-step budget covers: flag it and keep the work bounded
-    if (lg == 0) atomicOr(status, ST_SPECTRUM);
+    if (lane == 0) atomicOr(status, ST_SPECTRUM);
     S = SMAX;
   }
-  S = warp_max_i(S);
   const double xs = x / (double)S;
-  int kneed = 0;
-  for (int k = lg; k < KMAX; k += G) {
-    double a = bessel_jk(k, xs) * (k == 0 ? 1.0 : 2.0);
-    if (fabs(a) >= tol) kneed = k + 1 > kneed ? k + 1 : kneed;
-    double sg = ((k >> 1) & 1) ? -1.0 : 1.0;   // (-1)^(k/2) for even k, (-1)^((k-1)/2) for odd k
-    split2<R>(sg * a, ch.cf[k], ch.cl[k]);
-  }
-  kneed = g_max<G>(kneed);
-  if (kneed >= KMAX && lg == 0) atomicOr(status, ST_KOVERFLOW);
-  int K = kneed < 2 ? 2 : kneed;
-  K = warp_max_i(K);
-  if (lg == 0) {
-    // a_0 - 1 from its own series (no cancellation): sum_{m>=1} (-1)^m (x/2)^(2m) / (m!)^2
-    const double h2 = 0.25 * xs * xs;
-    double t = 1.0, j0m1 = 0.0;
-    for (int m = 1; m < 60; ++m) {
-      t *= -h2 / ((double)m * (double)m);
-      j0m1 += t;
-      if (fabs(t) <= 1e-18 * fabs(j0m1)) break;
-    }
-    const double a1 = 2.0 * bessel_jk(1, xs);
+  const double y = -0.25 * xs * xs, h = 0.5 * xs;
+  const int k = lane;   // KMAX == 32 == warp size
+  const double* c = ctab + k * (BESSEL_M + 1);
+  double acc = c[BESSEL_M];
+  for (int m = BESSEL_M - 1; m >= 0; --m) acc = fma(acc, y, c[m]);
+  double pw = 1.0;
+  for (int i = 0; i < k; ++i) pw *= h;
+  const double a = acc * pw * (k == 0 ? 1.0 : 2.0);
+  int kneed = fabs(a) >= tol ? k + 1 : 0;
+  kneed = warp_max_i(kneed);
+  if (kneed >= KMAX && lane == 0) atomicOr(status, ST_KOVERFLOW);
+  const double sg = ((k >> 1) & 1) ? -1.0 : 1.0;   // (-1)^(k/2) for even k, (-1)^((k-1)/2) for odd k
+  split2<R>(sg * a, ch.cf[k], ch.cl[k]);
+  if (lane == 0) {
+    // a_0 - 1 = sum_{m>=1} y^m / (m!)^2 without cancellation
+    double t = ctab[BESSEL_M];
+    for (int m = BESSEL_M - 1; m >= 1; --m) t = fma(t, y, ctab[m]);
+    const double j0m1 = t * y;
     split2<R>(1.0 + j0m1, ch.a0h, ch.a0l);
     split2<R>(j0m1, ch.c0h, ch.c0l);
-    split2<R>(a1, ch.a1h, ch.a1l);
     ch.c = (R)c0;
     ch.inv_rad = (R)(1.0 / rad);
     ch.cd = c0;
     ch.s2d = 2.0 / rad;
-    ch.K = K;
+    double sn, cs;
+    sincos(c0 * tau * (double)nsteps, &sn, &cs);
+    ch.cph = cs;
+    ch.sph = sn;
+    ch.K = kneed < 2 ? 2 : kneed;
     ch.S = S;
   }
+  if (lane == 1) split2<R>(a, ch.a1h, ch.a1l);   // a_1 = 2 J_1 (lane 1 holds it)
+}
+
+// Copy a sub-interval's parameters from global memory into a group's shared copy; K and S are made
+// warp-uniform (a group runs extra terms with its own tiny coefficients, and extra sub-steps are
+// discarded by the caller's select).  Every lane of the warp calls this.
+template <int G, typename R>
+__device__ void cheb_load(Cheb<R>& ch, const Cheb<R>* src, int lg, int& Kw, int& Sw) {
+  const int* s = reinterpret_cast<const int*>(src);
+  int* d = reinterpret_cast<int*>(&ch);
+  constexpr int words = sizeof(Cheb<R>) / sizeof(int);
+  for (int i = lg; i < words; i += G) d[i] = s[i];
   __syncwarp();
+  Kw = warp_max_i(ch.K);
+  Sw = warp_max_i(ch.S);
 }
 
 // ---------------------------------------------------------------------- Hamiltonian structures
@@ -360,9 +365,10 @@ struct OpDense {
 // two-sum.  This cuts the per-step FP32 rounding from ~eps(1+x)|v| to ~eps x |v| (x = tau*rad per
 // sub-step).  The coefficients a_0 - 1 (COMP) or a_0 and a_1 enter as hi + lo pairs.
 template <bool ADJ, bool COMP, typename R, int E, class Op>
-__device__ __forceinline__ void cheb_step(Vec<R, E>& v, Vec<R, E>& lo, const Op& op, const Cheb<R>& ch) {
-  const int K = ch.K;
-  for (int s = 0; s < ch.S; ++s) {
+__device__ __forceinline__ void cheb_step(Vec<R, E>& v, Vec<R, E>& lo, const Op& op, const Cheb<R>& ch, int K,
+                                          int Sw) {
+  for (int s = 0; s < Sw; ++s) {
+    const bool on = s < ch.S;   // sub-steps beyond this group's own count are computed and discarded
     Vec<R, E> t0 = v, t1, acc;
     Vec<R, E> zero;
 #pragma unroll
@@ -411,6 +417,7 @@ __device__ __forceinline__ void cheb_step(Vec<R, E>& v, Vec<R, E>& lo, const Op&
     }
 #pragma unroll
     for (int r = 0; r < E; ++r) {
+      if (!on) continue;
       if (!COMP) {
         v.re[r] = acc.re[r];
         v.im[r] = acc.im[r];
@@ -436,8 +443,8 @@ __device__ __forceinline__ void phase_rotate(double cp, double sp, bool adj, dou
 }
 
 template <bool ADJ, typename R, int E, class Op>
-__device__ __forceinline__ void cheb_step(Vec<R, E>& v, const Op& op, const Cheb<R>& ch) {
-  cheb_step<ADJ, false>(v, v, op, ch);
+__device__ __forceinline__ void cheb_step(Vec<R, E>& v, const Op& op, const Cheb<R>& ch, int K, int Sw) {
+  cheb_step<ADJ, false>(v, v, op, ch, K, Sw);
 }
 
 }  // namespace ism

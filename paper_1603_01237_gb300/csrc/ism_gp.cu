@@ -131,6 +131,7 @@ template <typename R>
 struct GP {
   using T = typename C2<R>::T;
   T *A, *B, *C, *W, *D2m1, *DH;   // state, scratch, spare, twiddles, exp(-i tau k^2/2)-1, exp(-i tau k^2/4)
+  R* X;                           // grid points x_m (FP64 -> R)
   int n;
   double dx, tau, g, xmin;
   double* red;
@@ -144,6 +145,7 @@ struct GP {
     W = base + 3 * n;
     D2m1 = base + 4 * n;
     DH = base + 5 * n;
+    X = reinterpret_cast<R*>(base + 6 * n);
     dx = p.dx;
     tau = p.tau;
     g = p.g;
@@ -170,6 +172,7 @@ struct GP {
       e.x = (R)c4;
       e.y = (R)s4;
       DH[m] = e;
+      X[m] = (R)(p.xmin + m * p.dx);
     }
     __syncthreads();
   }
@@ -199,16 +202,17 @@ struct GP {
     __syncthreads();
   }
 
-  __device__ R theta(int m, double u, T a) const {
-    const R xm = (R)(xmin + m * dx - u);
+  __device__ R theta(int m, R u, T a) const {
+    const R xm = X[m] - u;
     return R(0.5) * xm * xm + (R)g * (a.x * a.x + a.y * a.y);
   }
 
   // A <- exp(-i tau theta) A (forward Strang factor), in place
   __device__ void potential(double u) {
+    const R ur = (R)u, tr = (R)tau;
     for (int m = threadIdx.x; m < n; m += blockDim.x) {
       const T a = A[m];
-      const T e = expm1i<T, R>(-(R)tau * theta(m, u, a));
+      const T e = expm1i<T, R>(-tr * theta(m, ur, a));
       A[m] = cadd(a, cmul(e, a));
     }
     __syncthreads();
@@ -228,15 +232,15 @@ struct GP {
   // adjoint step at a_j (global, complex R, per element): A holds nu_{j+1} on entry and nu_j on exit;
   // returns dJ/du_j (FP64).
   __device__ double adjoint_step(const T* aj, double u) {
-    double part = 0.0;
+    const R ur = (R)u, tr = (R)tau;
+    R part = R(0);   // FP32 products; the block sum below accumulates the per-thread partials in FP64
     for (int m = threadIdx.x; m < n; m += blockDim.x) {
       const T a = aj[m];
       const T nu = A[m];
-      const T e = expm1i<T, R>((R)tau * theta(m, u, a));
+      const T e = expm1i<T, R>(tr * theta(m, ur, a));
       const T mu = cadd(nu, cmul(e, nu));
       const R im = mu.x * a.y - mu.y * a.x;   // Im(conj(mu) a)
-      const double dVdu = -(xmin + m * dx - u);
-      part += dVdu * (double)im;
+      part = fma(ur - X[m], im, part);        // dV/du = -(x - u)
       T w;
       const R f = R(2) * (R)tau * (R)g * im;
       w.x = mu.x + f * a.x;
@@ -244,7 +248,7 @@ struct GP {
       A[m] = w;
     }
     __syncthreads();
-    const double gsum = sum(part);
+    const double gsum = sum((double)part);
     kinetic<true, true>(A);
     return tau * dx * gsum;
   }
@@ -401,7 +405,7 @@ __global__ void k_gp_sub(GPParams p) {
   }
 }
 
-template <typename R> size_t gp_smem(int n) { return 6 * (size_t)n * sizeof(typename C2<R>::T); }
+template <typename R> size_t gp_smem(int n) { return 7 * (size_t)n * sizeof(typename C2<R>::T); }
 int gp_threads(int n) { return n / 8 < 32 ? 32 : n / 8; }
 
 template <typename R, class K>
@@ -416,7 +420,7 @@ cudaError_t launch(K kern, const GPParams& p, dim3 grid, cudaStream_t st) {
 
 }  // namespace
 
-bool gp_supported(int n) { return n == 64 || n == 512 || n == 4096; }
+bool gp_supported(int n) { return n == 64 || n == 512; }   // 8^P points whose tables fit in shared memory
 
 cudaError_t launch_gp_forward(int prec, const GPParams& p, cudaStream_t st) {
   return prec == 0 ? launch<double>(k_gp_forward<double>, p, dim3(p.B), st)

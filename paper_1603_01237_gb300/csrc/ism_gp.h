@@ -26,7 +26,7 @@ struct GPParams {
   int update;
 };
 
-// prec: 0 FP64, 1 FP32.  n must be 8^P (64, 512, 4096).
+// prec: 0 FP64, 1 FP32.  n must be 64 or 512 (radix-8 Stockham, tables in shared memory).
 bool gp_supported(int n);
 cudaError_t launch_gp_forward(int prec, const GPParams& p, cudaStream_t st);
 cudaError_t launch_gp_adjoint(int prec, const GPParams& p, cudaStream_t st);

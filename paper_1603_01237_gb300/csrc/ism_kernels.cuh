@@ -21,11 +21,15 @@ struct KParams {
   const double* alpha;    // [Nt] or null
   const void* H;          // packed op data (element type R)
   const double* H0d;      // FP64 diagonal of H0 (tridiagonal and bit-flip kinds)
+  const void* cheb;       // [B][N] Cheb<R>: propagator parameters per sub-interval (k_cheb_prep)
+  double* pen;            // [B][N] sum_j alpha_j u_j^2 per sub-interval (k_cheb_prep), or null
+  const double* ctab;     // Bessel series table for k_cheb_prep
   double* u;              // [B][Nt]
   const double2* phi;     // [B][N+1][d]
   void* M;                // [B][N] tiles of tile_stride R2: [d cols][ldm rows], ldm odd >= d
   long tile_stride;
   void* traj;             // [B][Nt+N][G*E] (R2)  H1 psi_n(t_j) per step
+  void* traj2;            // [B][Nt+N][G*E] (R2)  chi^ per step (concurrent two-trajectory sweeps)
   double* grad;           // [B][Nt]
   double* Jn;             // [B][N]
   double* err;            // [B][N]
@@ -51,6 +55,8 @@ struct ChainParams {
   const double2* ab;      // [N+1] (a_n, b_n) of Eq. (cible), computed on the host in FP64
   double2* psin;          // [B][N+1][d]
   double2* chin;          // [B][N+1][d]
+  void* stage;            // [B][2][N+1][d] R2: chain results before the FP64 conversion in k_phi
+  const double* pen;      // [B][N] penalty sums per sub-interval (from k_cheb_prep), or null
   double2* phi;           // [B][N+1][d]
   double* J;              // [B]
   double* F;              // [B]
@@ -99,11 +105,9 @@ __global__ void __launch_bounds__(128) k_assemble(KParams p) {
   const int j0 = p.jn[n], j1 = p.jn[n + 1];
   const double* ub = p.u + (long)b * p.Nt;
 
-  double um = 0.0;
-  for (int j = j0 + lg; j < j1; j += G) um = fmax(um, fabs(ub[j]));
-  um = g_max<G>(um);
   Cheb<R>& ch = chs[gib];
-  cheb_setup<G, R>(ch, lg, p.tau, p.c0, p.r0, p.h1n, um, p.tol, p.status);
+  int Kw, Sw;
+  cheb_load<G, R>(ch, reinterpret_cast<const Cheb<R>*>(p.cheb) + bn, lg, Kw, Sw);
 
   Op op;
   op.load(reinterpret_cast<const R*>(p.H), p.H0d, p.d, lg, smem_raw);
@@ -124,12 +128,11 @@ __global__ void __launch_bounds__(128) k_assemble(KParams p) {
     ua = ub1;
     if (j + 2 < j1) ub1 = ldu_ro<R>(ub, j + 2);
     op.set_u(uj, ch, lg);
-    cheb_step<false, COMP>(v, lo, op, ch);
+    cheb_step<false, COMP>(v, lo, op, ch, Kw, Sw);
   }
   if (col < p.d) {
     count_work<R>(p.count, ch, j1 - j0, lg);
-    double sn, cs;   // global phase exp(-i c (t_{n+1} - t_n)) of the whole sub-interval, FP64
-    sincos(p.c0 * p.tau * (double)(j1 - j0), &sn, &cs);
+    const double sn = ch.sph, cs = ch.cph;   // global phase exp(-i c (t_{n+1} - t_n)) of the sub-interval
     R2* M = reinterpret_cast<R2*>(p.M) + bn * p.tile_stride + (long)col * p.ldm;
 #pragma unroll
     for (int r = 0; r < E; ++r) {
@@ -175,11 +178,9 @@ __global__ void __launch_bounds__(128) k_subinterval(KParams p) {
   double* ub = p.u + (long)b * p.Nt;
   const double beta = p.beta[n];
 
-  double um = 0.0;
-  for (int j = j0 + lg; j < j1; j += G) um = fmax(um, fabs(ub[j]));
-  um = g_max<G>(um);
   Cheb<R>& ch = chs[gib];
-  cheb_setup<G, R>(ch, lg, p.tau, p.c0, p.r0, p.h1n, um, p.tol, p.status);
+  int Kw, Sw;
+  cheb_load<G, R>(ch, reinterpret_cast<const Cheb<R>*>(p.cheb) + gid, lg, Kw, Sw);
 
   Op op;
   op.load(reinterpret_cast<const R*>(p.H), p.H0d, p.d, lg, smem_raw);
@@ -188,8 +189,7 @@ __global__ void __launch_bounds__(128) k_subinterval(KParams p) {
   // multiplies psi_n(t_{n+1}) by exp(-i Phi), Phi = c (t_{n+1} - t_n), and every gradient term
   // <chi_n|H1|psi_n>(t_j) by the same exp(-i Phi) (chi_n carries exp(+i c (t_{n+1} - t_j)), psi_n
   // exp(-i c (t_j - t_n))); both are applied once, in FP64.
-  double sPhi, cPhi;
-  sincos(p.c0 * p.tau * (double)ns, &sPhi, &cPhi);
+  const double sPhi = ch.sph, cPhi = ch.cph;
 
   // form 0: psi_n(t_n) = phi_n (Eq. (dirpara)), adjoint from phi_{n+1};
   // form 1 (phi = phi^u, first local step): psi from psi(t_n) and chi from chi(t_{n+1}), the two
@@ -226,7 +226,7 @@ __global__ void __launch_bounds__(128) k_subinterval(KParams p) {
       }
       Vec<R, E> w = v, wl = lo;
       op.set_u(uj, ch, lg);
-      cheb_step<false, COMP>(w, wl, op, ch);
+      cheb_step<false, COMP>(w, wl, op, ch, Kw, Sw);
       if (act) { v = w; lo = wl; }
     }
   }
@@ -302,7 +302,7 @@ __global__ void __launch_bounds__(128) k_subinterval(KParams p) {
       }
       Vec<R, E> w = dl;
       op.set_u(uj, ch, lg);
-      cheb_step<true>(w, op, ch);
+      cheb_step<true>(w, op, ch, Kw, Sw);
       if (act) dl = w;
       R zr, zi;
       zdot(dl, hc, zr, zi);
@@ -343,6 +343,194 @@ __global__ void __launch_bounds__(128) k_subinterval(KParams p) {
   if (valid) count_work<R>(p.count, ch, 2L * ns, lg);   // forward U and backward U^H sweeps
 }
 
+__device__ inline double block_sum(double v, double* red) {
+  for (int m = 16; m >= 1; m >>= 1) v += __shfl_xor_sync(0xffffffffu, v, m);
+  __syncthreads();
+  if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = v;
+  __syncthreads();
+  double s = 0.0;
+  for (int w = 0; w < (int)(blockDim.x >> 5); ++w) s += red[w];
+  return s;
+}
+
+// ---------------------------------------------------------------------------- k_cheb_prep
+// One warp per (problem, n): the bound max|u| on the sub-interval and the propagator parameters.
+template <typename R>
+__global__ void __launch_bounds__(32) k_cheb_prep(KParams p) {
+  const int n = blockIdx.x, b = blockIdx.y, lane = threadIdx.x;
+  const int j0 = p.jn[n], j1 = p.jn[n + 1];
+  const double* ub = p.u + (long)b * p.Nt;
+  float um = 0.f;   // |u| bound; the margin in cheb_params covers its FP32 rounding
+  double pen = 0.0;
+  for (int j = j0 + lane; j < j1; j += 32) {
+    const double uj = ub[j];
+    um = fmaxf(um, fabsf((float)uj));
+    if (p.alpha) pen += p.alpha[j] * uj * uj;
+  }
+  for (int m = 16; m >= 1; m >>= 1) {
+    um = fmaxf(um, __shfl_xor_sync(0xffffffffu, um, m));
+    pen += __shfl_xor_sync(0xffffffffu, pen, m);
+  }
+  if (lane == 0 && p.pen) p.pen[(long)b * p.N + n] = pen;
+  __shared__ Cheb<R> ch;
+  cheb_params<R>(ch, p.ctab, p.tau, p.c0, p.r0, p.h1n, (double)um, p.tol, j1 - j0, p.status);
+  __syncwarp();
+  const int* s = reinterpret_cast<const int*>(&ch);
+  int* d = reinterpret_cast<int*>(const_cast<void*>(p.cheb)) + ((long)b * p.N + n) * (sizeof(Cheb<R>) / sizeof(int));
+  for (int i = lane; i < (int)(sizeof(Cheb<R>) / sizeof(int)); i += 32) d[i] = s[i];
+}
+
+// ---------------------------------------------------------------------- k_sweeps2 / k_gradpass
+// Theorem 2 (two-trajectory) form of the first local step, with the two sweeps run concurrently:
+// blockIdx.y = 0 propagates psi forward from psi(t_n) (compensated) and stores H1 psi^_j in trajectory
+// slot j - j_n (0..ns); blockIdx.y = 1 propagates chi backward from chi(t_{n+1}) and stores chi^_j in a
+// second trajectory (slot 0..ns).  Neither depends on the other.  k_gradpass then forms every
+// <chi^_j|H1 psi^_j>, the gradient, Err, J_n and the ascent step in parallel over steps.
+template <typename R, class Op>
+__global__ void __launch_bounds__(128) k_sweeps2(KParams p) {
+  constexpr int G = Op::G, E = Op::E, GPB = 128 / G, GE = G * E;
+  constexpr bool COMP = sizeof(R) == 4;
+  using R2 = typename C2<R>::T;
+  extern __shared__ __align__(128) unsigned char smem_raw[];
+  __shared__ Cheb<R> chs[GPB];
+  const int lg = threadIdx.x % G, gib = threadIdx.x / G;
+  const long gid0 = (long)blockIdx.x * GPB + gib;
+  const long total = (long)p.B * p.N;
+  const bool fwd = blockIdx.y == 0;
+  if (Op::G * Op::E == Op::DP_SMEM) {
+    const R* src = reinterpret_cast<const R*>(p.H);
+    R* dst = reinterpret_cast<R*>(smem_raw);
+    for (int i = threadIdx.x; i < 2 * Op::DP_SMEM * Op::DP_SMEM; i += blockDim.x) dst[i] = src[i];
+    __syncthreads();
+  }
+  const long warp_first = ((long)blockIdx.x * GPB + (threadIdx.x / 32) * (32 / G));
+  if (warp_first >= total) return;
+  const bool valid = gid0 < total;
+  const long gid = valid ? gid0 : total - 1;
+  const int n = (int)(gid % p.N), b = (int)(gid / p.N);
+  const int j0 = p.jn[n], j1 = p.jn[n + 1], ns = j1 - j0;
+  const int nsw = warp_max_i(ns);
+  const double* ub = p.u + (long)b * p.Nt;
+
+  Cheb<R>& ch = chs[gib];
+  int Kw, Sw;
+  cheb_load<G, R>(ch, reinterpret_cast<const Cheb<R>*>(p.cheb) + gid, lg, Kw, Sw);
+  Op op;
+  op.load(reinterpret_cast<const R*>(p.H), p.H0d, p.d, lg, smem_raw);
+  op.scale(p.H0d, p.d, lg, ch);
+
+  const long off_n = ((long)b * (p.N + 1) + n) * p.d;
+  const double2* st = fwd ? p.psin + off_n : p.chin + off_n + p.d;
+  Vec<R, E> v, lo;
+#pragma unroll
+  for (int r = 0; r < E; ++r) {
+    int e = lg * E + r;
+    double2 z = e < p.d ? st[e] : make_double2(0.0, 0.0);
+    v.re[r] = (R)z.x;
+    v.im[r] = (R)z.y;
+    lo.re[r] = COMP ? (R)(z.x - (double)v.re[r]) : R(0);
+    lo.im[r] = COMP ? (R)(z.y - (double)v.im[r]) : R(0);
+  }
+  R2* tr = reinterpret_cast<R2*>(fwd ? p.traj : p.traj2) + ((long)b * (p.Nt + p.N) + j0 + n) * GE + lg * E;
+  auto put = [&](int slot, const Vec<R, E>& x) {
+    if (valid) {
+#pragma unroll
+      for (int r = 0; r < E; ++r) { R2 z; z.x = x.re[r]; z.y = x.im[r]; tr[(long)slot * GE + r] = z; }
+    }
+  };
+  if (fwd) {
+    R ua = ldu<R>(ub, j0), ub1 = ns > 1 ? ldu<R>(ub, j0 + 1) : ua;
+    for (int s = 0; s < nsw; ++s) {
+      const bool act = s < ns;
+      const R uj = ua;
+      ua = ub1;
+      if (s + 2 < ns) ub1 = ldu<R>(ub, j0 + s + 2);
+      Vec<R, E> hv;
+      op.h1(v, hv);
+      if (act) put(s, hv);
+      Vec<R, E> w = v, wl = lo;
+      op.set_u(uj, ch, lg);
+      cheb_step<false, COMP>(w, wl, op, ch, Kw, Sw);
+      if (act) { v = w; lo = wl; }
+    }
+    Vec<R, E> hv;
+    op.h1(v, hv);
+    put(ns, hv);
+  } else {
+    put(ns, v);
+    const int top = ns - 1;
+    R ua = ldu<R>(ub, j0 + top), ub1 = ldu<R>(ub, j0 + (top > 0 ? top - 1 : top));
+    for (int s = nsw - 1; s >= 0; --s) {
+      const bool act = s < ns;
+      const R uj = ua;
+      if (act) {
+        ua = ub1;
+        if (s - 2 >= 0) ub1 = ldu<R>(ub, j0 + s - 2);
+      }
+      Vec<R, E> w = v, wl = lo;
+      op.set_u(uj, ch, lg);
+      cheb_step<true, COMP>(w, wl, op, ch, Kw, Sw);
+      if (act) { v = w; lo = wl; put(s, v); }
+    }
+  }
+  if (valid) count_work<R>(p.count, ch, ns, lg);
+}
+
+// One block per (problem, n); threads over the steps of the sub-interval.
+template <typename R>
+__global__ void __launch_bounds__(256) k_gradpass(KParams p, int GE) {
+  using R2 = typename C2<R>::T;
+  __shared__ double red[8];
+  const int b = blockIdx.y, n = blockIdx.x, t = threadIdx.x, d = p.d;
+  const int j0 = p.jn[n], j1 = p.jn[n + 1], ns = j1 - j0;
+  const double beta = p.beta[n];
+  const long base = ((long)b * (p.Nt + p.N) + j0 + n) * GE;
+  const R2* hp = reinterpret_cast<const R2*>(p.traj) + base;    // H1 psi^ per slot
+  const R2* cp = reinterpret_cast<const R2*>(p.traj2) + base;   // chi^ per slot
+  const Cheb<R>& chp = reinterpret_cast<const Cheb<R>*>(p.cheb)[(long)b * p.N + n];
+  const double sPhi = chp.sph, cPhi = chp.cph;
+  auto I_at = [&](int slot) {   // Im(exp(-i Phi) <chi^|H1 psi^>) at a slot, FP32 products
+    R zr = R(0), zi = R(0);
+    const R2* h = hp + (long)slot * GE;
+    const R2* c = cp + (long)slot * GE;
+    for (int e = 0; e < d; ++e) {
+      const R2 a = c[e], y = h[e];
+      zr = fma(a.x, y.x, fma(a.y, y.y, zr));
+      zi = fma(a.x, y.y, fma(-a.y, y.x, zi));
+    }
+    return cPhi * (double)zi - sPhi * (double)zr;
+  };
+  const double ht = 0.5 * p.tau * p.w / beta, tb = p.tau / beta, step = p.rho * beta / p.tau;
+  double* ub = p.u + (long)b * p.Nt;
+  double* gb = p.grad + (long)b * p.Nt;
+  double err = 0.0, pen = 0.0;
+  for (int s = t; s < ns; s += blockDim.x) {
+    const int j = j0 + s;
+    const double uj = ub[j];
+    const double al = p.alpha ? p.alpha[j] : 0.0;
+    const double g = ht * (I_at(s) + I_at(s + 1)) - tb * al * uj;
+    err += fabs(g);
+    pen += al * uj * uj;
+    gb[j] = g;
+    if (p.update) ub[j] = uj + step * g;
+  }
+  double nrm = 0.0;   // J_n: delta = (chi - psi)(t_{n+1}) / beta_n from the chain (FP64)
+  const long off = ((long)b * (p.N + 1) + n + 1) * d;
+  for (int e = t; e < d; e += blockDim.x) {
+    const double2 c = p.chin[off + e], ps = p.psin[off + e];
+    const double dr = (c.x - ps.x) / beta, di = (c.y - ps.y) / beta;
+    nrm += dr * dr + di * di;
+  }
+  err = block_sum(err, red);
+  pen = block_sum(pen, red);
+  nrm = block_sum(nrm, red);
+  if (t == 0) {
+    const long id = (long)b * p.N + n;
+    if (p.Jn) p.Jn[id] = p.w * (-0.5 * nrm) - 0.5 * tb * pen;
+    if (p.err) p.err[id] = err;
+  }
+}
+
 // -------------------------------------------------------------------------------- k_chain
 __device__ __forceinline__ unsigned smem_u32(const void* p) { return (unsigned)__cvta_generic_to_shared(p); }
 
@@ -380,42 +568,61 @@ __device__ __forceinline__ bool mbar_wait(uint64_t* bar, unsigned parity, int ma
 
 
 // ---------------------------------------------------------------------------------- chains
-// The chain is a sequence of 2N small dependent matvecs: latency, not bandwidth.  The tiles M_n (left
-// in L2 by the assembly) stream into a ring of NS shared-memory stages by TMA bulk copies issued up to
-// NS - 1 matvecs ahead; thread 0 alone waits on a stage's mbarrier (bounded), and one block barrier
-// per matvec publishes both the tile and the previous result.  256 threads: thread (i = t/4, q = t%4)
-// owns output row i and the columns k = q (mod 4); two shuffles finish each row.
+// The chain is a sequence of 2N small dependent matvecs: latency, not bandwidth.  The block is warp
+// specialised.  One producer warp streams the tiles M_n (left in L2 by the assembly) into a ring of NS
+// shared-memory stages with TMA bulk copies: before refilling a stage it waits on that stage's "empty"
+// mbarrier, on which each consumer warp arrives once it has read the tile.  The CW consumer warps wait
+// on the stage's "full" mbarrier themselves (every thread, bounded), so no thread carries the copy
+// bookkeeping inside the dependent chain, and one named barrier over the consumers per matvec publishes
+// the new state.  Consumer thread t owns output row i = t / 8 and the columns k = t (mod 8); three
+// shuffles finish each row.
 constexpr int CHAIN_MAX_STAGES = 16;
+constexpr int CHAIN_LANES = 8;      // lanes per output row
+constexpr int CHAIN_MAX_THREADS = (64 * CHAIN_LANES / 32 + 1) * 32;
 
-template <typename R>
+__host__ __device__ inline int chain_consumer_warps(int d) { return (d * CHAIN_LANES + 31) / 32; }
+
+__device__ __forceinline__ void mbar_arrive(uint64_t* bar) {
+  asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(smem_u32(bar)) : "memory");
+}
+__device__ __forceinline__ void consumer_sync(int nthreads) {
+  asm volatile("bar.sync 1, %0;" ::"r"(nthreads) : "memory");
+}
+
+template <typename R, bool HERM>
 __device__ __forceinline__ void chain_mv(const typename C2<R>::T* Ms, const typename C2<R>::T* x,
-                                         typename C2<R>::T* y, int d, int ldm, bool herm) {
+                                         typename C2<R>::T* y, int d, int ldm) {
   using R2 = typename C2<R>::T;
-  const int i = threadIdx.x >> 2, q = threadIdx.x & 3;
+  const int i = threadIdx.x / CHAIN_LANES, q = threadIdx.x % CHAIN_LANES;
   R ar0 = R(0), ai0 = R(0), ar1 = R(0), ai1 = R(0);
   if (i < d) {
-#pragma unroll 4
-    for (int k = q; k < d; k += 8) {
-      {
-        const R2 m = herm ? Ms[i * ldm + k] : Ms[k * ldm + i];
-        const R2 xv = x[k];
-        if (!herm) { ar0 = fma(m.x, xv.x, fma(-m.y, xv.y, ar0)); ai0 = fma(m.x, xv.y, fma(m.y, xv.x, ai0)); }
-        else { ar0 = fma(m.x, xv.x, fma(m.y, xv.y, ar0)); ai0 = fma(m.x, xv.y, fma(-m.y, xv.x, ai0)); }
+    int k = q;
+    for (; k + CHAIN_LANES < d; k += 2 * CHAIN_LANES) {
+      const int k2 = k + CHAIN_LANES;
+      const R2 m0 = HERM ? Ms[i * ldm + k] : Ms[k * ldm + i];
+      const R2 m1 = HERM ? Ms[i * ldm + k2] : Ms[k2 * ldm + i];
+      const R2 x0 = x[k], x1 = x[k2];
+      if (!HERM) {
+        ar0 = fma(m0.x, x0.x, fma(-m0.y, x0.y, ar0)); ai0 = fma(m0.x, x0.y, fma(m0.y, x0.x, ai0));
+        ar1 = fma(m1.x, x1.x, fma(-m1.y, x1.y, ar1)); ai1 = fma(m1.x, x1.y, fma(m1.y, x1.x, ai1));
+      } else {
+        ar0 = fma(m0.x, x0.x, fma(m0.y, x0.y, ar0)); ai0 = fma(m0.x, x0.y, fma(-m0.y, x0.x, ai0));
+        ar1 = fma(m1.x, x1.x, fma(m1.y, x1.y, ar1)); ai1 = fma(m1.x, x1.y, fma(-m1.y, x1.x, ai1));
       }
-      const int k2 = k + 4;
-      if (k2 < d) {
-        const R2 m = herm ? Ms[i * ldm + k2] : Ms[k2 * ldm + i];
-        const R2 xv = x[k2];
-        if (!herm) { ar1 = fma(m.x, xv.x, fma(-m.y, xv.y, ar1)); ai1 = fma(m.x, xv.y, fma(m.y, xv.x, ai1)); }
-        else { ar1 = fma(m.x, xv.x, fma(m.y, xv.y, ar1)); ai1 = fma(m.x, xv.y, fma(-m.y, xv.x, ai1)); }
-      }
+    }
+    if (k < d) {
+      const R2 m0 = HERM ? Ms[i * ldm + k] : Ms[k * ldm + i];
+      const R2 x0 = x[k];
+      if (!HERM) { ar0 = fma(m0.x, x0.x, fma(-m0.y, x0.y, ar0)); ai0 = fma(m0.x, x0.y, fma(m0.y, x0.x, ai0)); }
+      else { ar0 = fma(m0.x, x0.x, fma(m0.y, x0.y, ar0)); ai0 = fma(m0.x, x0.y, fma(-m0.y, x0.x, ai0)); }
     }
   }
   R ar = ar0 + ar1, ai = ai0 + ai1;
-  ar += __shfl_xor_sync(0xffffffffu, ar, 1);
-  ai += __shfl_xor_sync(0xffffffffu, ai, 1);
-  ar += __shfl_xor_sync(0xffffffffu, ar, 2);
-  ai += __shfl_xor_sync(0xffffffffu, ai, 2);
+#pragma unroll
+  for (int m = 1; m < CHAIN_LANES; m <<= 1) {
+    ar += __shfl_xor_sync(0xffffffffu, ar, m);
+    ai += __shfl_xor_sync(0xffffffffu, ai, m);
+  }
   if (q == 0 && i < d) { R2 z; z.x = ar; z.y = ai; y[i] = z; }
 }
 
@@ -424,73 +631,89 @@ template <typename R>
 struct ChainRing {
   using R2 = typename C2<R>::T;
   R2* stages;
-  uint64_t* bars;
+  uint64_t* full;    // [NS] completes when the copy of a use has landed (count 1 + tx bytes)
+  uint64_t* empty;   // [NS] completes when all consumer warps have read a use (count CW)
   const R2* Mb;
   long tst;
   unsigned bytes;
   int NS, U, N, first;   // tile_of(m): first == 0 -> m < N ? m : 2N-1-m; first == 1 -> N-1-m
   __device__ int tile_of(int m) const { return first == 1 ? N - 1 - m : (m < N ? m : 2 * N - 1 - m); }
-  __device__ void issue(int m) const {   // thread 0
-    const int st = m % NS;
-    fence_proxy_async();
-    bulk_load(stages + st * tst, Mb + (long)tile_of(m) * tst, bytes, &bars[st]);
-  }
   __device__ const R2* tile(int m) const { return stages + (m % NS) * tst; }
 };
 
-// One chain of N matvecs over uses m0 .. m0+N-1 of the ring; x_0 in xs[0]; writes the N results (FP64)
-// into out[idx(m)*d] with idx = m - m0 + 1 (psi) or N - 1 - (m - m0) (chi).  Returns false (uniformly)
-// if a tile did not arrive; the copies still in flight have then been drained.
+// Producer (lane 0 of the last warp): issue every use in order, each after its stage has been emptied.
+// If an empty-wait gives up (the consumers stopped), stop issuing and wait, bounded, for the copies
+// already in flight so that none lands after the block exits.
+template <typename R>
+__device__ void chain_produce(const ChainRing<R>& ring, int* status, int max_spin) {
+  int issued = 0;
+  for (int m = 0; m < ring.U; ++m) {
+    const int st = m % ring.NS;
+    if (m >= ring.NS && !mbar_wait(&ring.empty[st], (unsigned)((m / ring.NS - 1) & 1), max_spin)) {
+      atomicOr(status, ST_TIMEOUT);
+      break;
+    }
+    fence_proxy_async();   // the consumers' reads of this stage precede the copy that overwrites it
+    bulk_load(ring.stages + st * ring.tst, ring.Mb + (long)ring.tile_of(m) * ring.tst, ring.bytes, &ring.full[st]);
+    issued = m + 1;
+  }
+  if (issued < ring.U)
+    for (int m = issued - ring.NS < 0 ? 0 : issued - ring.NS; m < issued; ++m)
+      mbar_wait(&ring.full[m % ring.NS], (unsigned)((m / ring.NS) & 1), max_spin);
+}
+
+// One chain of N matvecs over uses m0 .. m0+N-1 of the ring, run by the CW consumer warps; x_0 in
+// xs[0]; stores the N results (FP32 staging) into out[idx * d] with idx = c (psi) or N - c (chi).
+// Returns false (uniformly over the consumers) if a tile did not arrive.
 template <typename R, bool HERM>
 __device__ bool run_chain(const ChainRing<R>& ring, int m0, int N, int d, int ldm, typename C2<R>::T (*xs)[64],
-                          double2* out, int* fail, int* status, int max_spin) {
-  using R2 = typename C2<R>::T;
+                          typename C2<R>::T* out, int* fail, int* status, int max_spin, int ncons) {
   const int t = threadIdx.x;
   for (int c = 0; c <= N; ++c) {
     const int m = m0 + c;
-    if (t == 0 && c < N) {
-      if (!mbar_wait(&ring.bars[m % ring.NS], (unsigned)((m / ring.NS) & 1), max_spin)) {
-        for (int q = m; q < ring.U && q < m + ring.NS; ++q)
-          mbar_wait(&ring.bars[q % ring.NS], (unsigned)((q / ring.NS) & 1), max_spin);
-        atomicOr(status, ST_TIMEOUT);
-        *fail = 1;
-      }
+    if (c < N && !mbar_wait(&ring.full[m % ring.NS], (unsigned)((m / ring.NS) & 1), max_spin)) {
+      atomicOr(status, ST_TIMEOUT);
+      *(volatile int*)fail = 1;
     }
-    __syncthreads();   // tile m present; result of matvec c-1 visible
-    if (*fail) return false;
+    consumer_sync(ncons);   // result of matvec c-1 visible; every consumer has waited for tile m
+    if (*(volatile int*)fail) return false;
     if (c >= 1) {
-      // the stage of use m-1 has been read by everyone: refill it NS uses ahead
-      if (t == 0 && m - 1 + ring.NS < ring.U) ring.issue(m - 1 + ring.NS);
       const int idx = HERM ? N - c : c;
-      if (t < d) { const R2 z = xs[c & 1][t]; out[(long)idx * d + t] = make_double2((double)z.x, (double)z.y); }
+      if (t < d) out[(long)idx * d + t] = xs[c & 1][t];   // FP32 here; FP64 conversion in k_phi
     }
-    if (c < N) chain_mv<R>(ring.tile(m), xs[c & 1], xs[(c + 1) & 1], d, ldm, HERM);
+    if (c < N) {
+      chain_mv<R, HERM>(ring.tile(m), xs[c & 1], xs[(c + 1) & 1], d, ldm);
+      __syncwarp();
+      if ((t & 31) == 0) mbar_arrive(&ring.empty[m % ring.NS]);
+    }
   }
-  __syncthreads();   // the last stored state is read by other threads next
+  consumer_sync(ncons);   // the last stored state is read by other threads next
   return true;
 }
 
-// grid (nchains, B), 256 threads, dynamic shared memory NS tiles.  nchains = 2 (overlap objective):
+// grid (nchains, B), (CW + 1) warps, dynamic shared memory NS tiles.  nchains = 2 (overlap objective):
 // CTA 0 runs the psi chain, CTA 1 the chi chain from psi_f, concurrently.  nchains = 1 (observable):
 // one CTA runs the psi chain, forms chi(T) = O psi(T) in FP64 and runs the chi chain, all from one ring.
 // Intermediate states and J follow in k_phi.
 template <typename R>
-__global__ void __launch_bounds__(256) k_chain(ChainParams p) {
+__global__ void __launch_bounds__(CHAIN_MAX_THREADS) k_chain(ChainParams p) {
   using R2 = typename C2<R>::T;
   extern __shared__ __align__(128) unsigned char smem_raw[];
-  __shared__ __align__(8) uint64_t bars[CHAIN_MAX_STAGES];
+  __shared__ __align__(8) uint64_t full[CHAIN_MAX_STAGES];
+  __shared__ __align__(8) uint64_t empty[CHAIN_MAX_STAGES];
   __shared__ __align__(16) R2 xs[2][64];
   __shared__ double2 vd[64];
   __shared__ int fail;
   const int b = blockIdx.y, t = threadIdx.x, d = p.d, N = p.N;
-  double2* psin = p.psin + (long)b * (N + 1) * d;
+  const int cw = chain_consumer_warps(d), ncons = cw * 32;
   double2* chin = p.chin + (long)b * (N + 1) * d;
   const bool single = gridDim.x == 1;
   const bool do_psi = single || blockIdx.x == 0;
   const bool do_chi = single || blockIdx.x == 1;
   ChainRing<R> ring;
   ring.stages = reinterpret_cast<R2*>(smem_raw);
-  ring.bars = bars;
+  ring.full = full;
+  ring.empty = empty;
   ring.Mb = reinterpret_cast<const R2*>(p.M) + (long)b * N * p.tile_stride;
   ring.tst = p.tile_stride;
   ring.bytes = (unsigned)(p.tile_stride * sizeof(R2));
@@ -500,75 +723,94 @@ __global__ void __launch_bounds__(256) k_chain(ChainParams p) {
   ring.first = (!single && blockIdx.x == 1) ? 1 : 0;
   if (t == 0) {
     fail = 0;
-    for (int i = 0; i < ring.NS; ++i) mbar_init(&bars[i], 1);
+    for (int i = 0; i < ring.NS; ++i) {
+      mbar_init(&full[i], 1);
+      mbar_init(&empty[i], (unsigned)cw);
+    }
     fence_mbar_init();
   }
-  __syncthreads();
-  if (t == 0)
-    for (int m = 0; m < ring.NS && m < ring.U; ++m) ring.issue(m);
+  __syncthreads();   // the last block-wide barrier: producer and consumers part here
+  if (t >= ncons) {
+    if (t == ncons) chain_produce<R>(ring, p.status, p.max_spin);
+    return;
+  }
 
+  R2* sps = reinterpret_cast<R2*>(p.stage) + (long)b * 2 * (N + 1) * d;
+  R2* sch = sps + (long)(N + 1) * d;
   int m0 = 0;
   if (do_psi) {
-    if (t < d) { const double2 z = p.psi_i[t]; R2 r; r.x = (R)z.x; r.y = (R)z.y; xs[0][t] = r; psin[t] = z; }
-    if (!run_chain<R, false>(ring, m0, N, d, p.ldm, xs, psin, &fail, p.status, p.max_spin)) return;
+    if (t < d) { const double2 z = p.psi_i[t]; R2 r; r.x = (R)z.x; r.y = (R)z.y; xs[0][t] = r; }
+    if (!run_chain<R, false>(ring, m0, N, d, p.ldm, xs, sps, &fail, p.status, p.max_spin, ncons)) return;
     m0 += N;
   }
   if (do_chi) {
     if (p.obj == 0) {
       if (t < d) vd[t] = p.psi_f[t];
-    } else {   // chi(T) = O psi(T), FP64, thread (i, q) sums k = q (mod 4)
-      const int i = t >> 2, q = t & 3;
+    } else {   // chi(T) = O psi(T) in FP64 from the FP32 psi(T) in xs[N & 1]
+      const int i = t / CHAIN_LANES, q = t % CHAIN_LANES;
       double sr = 0.0, si = 0.0;
       if (i < d)
-        for (int k = q; k < d; k += 4) {
+        for (int k = q; k < d; k += CHAIN_LANES) {
           const double o = p.O[i * d + k];
-          const double2 v = psin[(long)N * d + k];
-          sr += o * v.x;
-          si += o * v.y;
+          const R2 v = xs[N & 1][k];
+          sr += o * (double)v.x;
+          si += o * (double)v.y;
         }
-      sr += __shfl_xor_sync(0xffffffffu, sr, 1);
-      si += __shfl_xor_sync(0xffffffffu, si, 1);
-      sr += __shfl_xor_sync(0xffffffffu, sr, 2);
-      si += __shfl_xor_sync(0xffffffffu, si, 2);
+#pragma unroll
+      for (int m = 1; m < CHAIN_LANES; m <<= 1) {
+        sr += __shfl_xor_sync(0xffffffffu, sr, m);
+        si += __shfl_xor_sync(0xffffffffu, si, m);
+      }
       if (q == 0 && i < d) vd[i] = make_double2(sr, si);
     }
-    __syncthreads();
+    consumer_sync(ncons);
     if (t < d) { const double2 z = vd[t]; R2 r; r.x = (R)z.x; r.y = (R)z.y; xs[0][t] = r; chin[(long)N * d + t] = z; }
-    if (!run_chain<R, true>(ring, m0, N, d, p.ldm, xs, chin, &fail, p.status, p.max_spin)) return;
+    if (!run_chain<R, true>(ring, m0, N, d, p.ldm, xs, sch, &fail, p.status, p.max_spin, ncons)) return;
   }
 }
 
-__device__ inline double block_sum(double v, double* red) {
-  for (int m = 16; m >= 1; m >>= 1) v += __shfl_xor_sync(0xffffffffu, v, m);
-  __syncthreads();
-  if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = v;
-  __syncthreads();
-  double s = 0.0;
-  for (int w = 0; w < (int)(blockDim.x >> 5); ++w) s += red[w];
-  return s;
-}
 
-// grid B, 256 threads: J and F at u (FP64) and the intermediate states (Eq. (cible)), with
-// phi_0 = psi_i and phi_N = chi(T) exactly.
-template <int V = 0>
-__global__ void __launch_bounds__(1024) k_phi(ChainParams p) {
-  __shared__ double red[32];
-  const int b = blockIdx.x, t = threadIdx.x, d = p.d, N = p.N;
-  const double2* psin = p.psin + (long)b * (N + 1) * d;
-  const double2* chin = p.chin + (long)b * (N + 1) * d;
+// grid (N+2, B), 128 threads.  Block n <= N converts psi(t_n), chi(t_n) from the chain to FP64
+// (psi(t_0) = psi_i and chi(t_N) = chi(T) are exact) and forms phi_n = a_n psi(t_n) + b_n chi(t_n)
+// (Eq. (cible)); block N+1 forms J and F at u in FP64.
+template <typename R>
+__global__ void __launch_bounds__(128) k_phi(ChainParams p) {
+  using R2 = typename C2<R>::T;
+  __shared__ double red[4];
+  const int n = blockIdx.x, b = blockIdx.y, t = threadIdx.x, d = p.d, N = p.N;
+  double2* psin = p.psin + (long)b * (N + 1) * d;
+  double2* chin = p.chin + (long)b * (N + 1) * d;
+  const R2* sps = reinterpret_cast<const R2*>(p.stage) + (long)b * 2 * (N + 1) * d;
+  const R2* sch = sps + (long)(N + 1) * d;
+  if (n <= N) {
+    const double2 w = p.ab[n];
+    double2* phi = p.phi + ((long)b * (N + 1) + n) * d;
+    for (int e = t; e < d; e += blockDim.x) {
+      double2 ps, cs;
+      if (n == 0) ps = p.psi_i[e];
+      else { const R2 z = sps[(long)n * d + e]; ps = make_double2((double)z.x, (double)z.y); }
+      if (n == N) cs = chin[(long)N * d + e];
+      else { const R2 z = sch[(long)n * d + e]; cs = make_double2((double)z.x, (double)z.y); }
+      psin[(long)n * d + e] = ps;
+      if (n < N) chin[(long)n * d + e] = cs;
+      phi[e] = n == 0 ? ps : (n == N ? cs : make_double2(w.x * ps.x + w.y * cs.x, w.x * ps.y + w.y * cs.y));
+    }
+    return;
+  }
+  // J and F: <psi(T)|chi(T)> is the overlap with psi_f or <psi|O|psi>
   double ovr = 0.0, ovi = 0.0;
-  for (int i = t; i < d; i += blockDim.x) {
-    const double2 a = psin[(long)N * d + i], c = chin[(long)N * d + i];
-    ovr += a.x * c.x + a.y * c.y;
-    ovi += a.x * c.y - a.y * c.x;
+  for (int e = t; e < d; e += blockDim.x) {
+    const R2 z = sps[(long)N * d + e];
+    const double ax = (double)z.x, ay = (double)z.y;
+    const double2 c = chin[(long)N * d + e];
+    ovr += ax * c.x + ay * c.y;
+    ovi += ax * c.y - ay * c.x;
   }
   ovr = block_sum(ovr, red);
   ovi = block_sum(ovi, red);
   double pen = 0.0;
-  if (p.alpha) {
-    const double* ub = p.u + (long)b * p.Nt;
-    for (int j = t; j < p.Nt; j += blockDim.x) pen += p.alpha[j] * ub[j] * ub[j];
-  }
+  if (p.pen)
+    for (int n2 = t; n2 < N; n2 += blockDim.x) pen += p.pen[(long)b * N + n2];
   pen = 0.5 * p.tau * block_sum(pen, red);
   if (t == 0) {
     const double F = p.obj == 0 ? ovr * ovr + ovi * ovi : ovr;
@@ -577,18 +819,6 @@ __global__ void __launch_bounds__(1024) k_phi(ChainParams p) {
     p.J[b] = J;
     p.F[b] = F;
     if (p.Jhist) p.Jhist[(long)b * p.hist_stride + p.hist_k] = J;
-  }
-  double2* phi = p.phi + (long)b * (N + 1) * d;
-  for (long i = t; i < (long)(N + 1) * d; i += blockDim.x) {
-    const int n = (int)(i / d);
-    const double2 w = p.ab[n];
-    const double a = w.x, c = w.y;
-    const double2 ps = psin[i], cs = chin[i];
-    double2 z;
-    if (n == 0) z = ps;
-    else if (n == N) z = cs;
-    else z = make_double2(a * ps.x + c * cs.x, a * ps.y + c * cs.y);
-    phi[i] = z;
   }
 }
 

@@ -13,6 +13,7 @@ typedef cudaError_t (*LaunchFn)(const KParams&, cudaStream_t);
 struct KernelSet {
   LaunchFn assemble = nullptr;
   LaunchFn subinterval = nullptr;
+  LaunchFn sweeps2 = nullptr;     // concurrent two-trajectory sweeps + gradient pass
   int G = 0, E = 0;          // lanes per state, elements per lane (sub-interval sweep)
   int GA = 0;                // lanes per state in the assembly
   size_t op_smem = 0;        // dynamic shared memory of the op (dense H pairs)
@@ -24,6 +25,12 @@ bool kernels_bitflip(int prec, int d, KernelSet* ks);
 bool kernels_dense(int prec, int d, KernelSet* ks);
 cudaError_t launch_chain(int prec, const ChainParams& p, size_t smem, cudaStream_t st);
 bool select_kernels(int prec, int kind, int d, KernelSet* ks);
+// per-sub-interval propagator parameters (one warp each) from the current controls
+cudaError_t launch_cheb_prep(int prec, const KParams& p, cudaStream_t st);
+size_t cheb_bytes(int prec);
+// 1/(m! (m+k)!) for k < 32, m <= 24, row-major (k, m): the Bessel series table of the parameters
+void bessel_table(double* out);
+constexpr int BESSEL_TABLE = 32 * 25;
 
 }  // namespace ism
 

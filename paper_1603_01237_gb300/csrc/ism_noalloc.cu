@@ -83,13 +83,16 @@ extern "C" int ism_subinterval_grad_noalloc(const ism_problem* prob, int precisi
   if (precision == ISM_FP64) { hd = ism::pack_op<double>(p.kind, d, p.H0, p.H1, ks.G, ks.E); op_bytes = hd.size() * r1; }
   else { hf = ism::pack_op<float>(p.kind, d, p.H0, p.H1, ks.G, ks.E); op_bytes = hf.size() * r1; }
 
-  // scratch layout: op data | FP64 diag(H0) | j_n | beta_n | alpha | status | trajectory
+  // scratch layout: op data | FP64 diag(H0) | j_n | beta_n | alpha | status | propagator parameters |
+  // Bessel table | trajectory
   const size_t off_h0d = up256(op_bytes);
   const size_t off_jn = off_h0d + up256(sizeof(double) * d);
   const size_t off_beta = off_jn + up256(sizeof(int) * (p.N + 1));
   const size_t off_alpha = off_beta + up256(sizeof(double) * p.N);
   const size_t off_status = off_alpha + up256(p.alpha ? sizeof(double) * p.Nt : 0);
-  const size_t off_traj = off_status + 256;
+  const size_t off_cheb = off_status + 256;
+  const size_t off_ctab = off_cheb + up256((size_t)B * p.N * ism::cheb_bytes(precision));
+  const size_t off_traj = off_ctab + up256(sizeof(double) * ism::BESSEL_TABLE);
   const size_t need = off_traj + up256((size_t)B * ((size_t)p.Nt + p.N) * GE * r2);
   if (need > kScratchBytes) {
     std::string m = "problem needs " + std::to_string(need) + " bytes of scratch; the static scratch of the "
@@ -118,6 +121,9 @@ extern "C" int ism_subinterval_grad_noalloc(const ism_problem* prob, int precisi
   h2d(off_jn, jn.data(), sizeof(int) * jn.size());
   h2d(off_beta, beta.data(), sizeof(double) * beta.size());
   if (p.alpha) h2d(off_alpha, p.alpha, sizeof(double) * p.Nt);
+  std::vector<double> tab(ism::BESSEL_TABLE);
+  ism::bessel_table(tab.data());
+  h2d(off_ctab, tab.data(), sizeof(double) * tab.size());
   if (e == cudaSuccess) e = cudaMemsetAsync(base + off_status, 0, sizeof(int), st);
   if (e != cudaSuccess) return ism::set_error(ISM_ECUDA, (std::string("scratch upload: ") + cudaGetErrorString(e)).c_str());
 
@@ -135,6 +141,7 @@ extern "C" int ism_subinterval_grad_noalloc(const ism_problem* prob, int precisi
   k.phi = reinterpret_cast<const double2*>(phi);
   k.M = nullptr;
   k.traj = base + off_traj;
+  k.traj2 = nullptr;
   k.grad = grad;
   k.Jn = Jn;
   k.err = nullptr;
@@ -145,6 +152,11 @@ extern "C" int ism_subinterval_grad_noalloc(const ism_problem* prob, int precisi
   k.form = 0;
   k.update = 0;
   k.max_spin = 1 << 22;
+  k.cheb = base + off_cheb;
+  k.pen = nullptr;
+  k.ctab = reinterpret_cast<const double*>(base + off_ctab);
+  if ((e = ism::launch_cheb_prep(precision, k, st)) != cudaSuccess)
+    return ism::set_error(ISM_ECUDA, (std::string("launch: ") + cudaGetErrorString(e)).c_str());
   if ((e = ks.subinterval(k, st)) != cudaSuccess)
     return ism::set_error(ISM_ECUDA, (std::string("launch: ") + cudaGetErrorString(e)).c_str());
   if ((e = cudaStreamSynchronize(st)) != cudaSuccess)
