@@ -29,6 +29,10 @@ import numpy as np  # noqa: E402
 
 METRIC = "ISM gradient iters/s and complex state-steps/s vs plain FP64; p50/p99 solve latency"
 UNIT = "ISM iterations/s"
+DESCR = {"rotor41": "rigid rotor j<=40, maximise <cos theta>(T)",
+         "spin16": "4 spins all-to-all ZZ, X control, |0000> -> |1111>",
+         "ising1024": "10-spin open Ising chain, X control, |0^10> -> |1^10>"}
+SAMPLE_DIV = {"rotor41": 8, "spin16": 1, "ising1024": 64}   # oracle sample = Nt/div steps, N/div sub-intervals
 FP32_LANES_PER_SM = 128
 SMS = 152
 SM_MAX_MHZ = 2070.0
@@ -41,7 +45,7 @@ def parse():
     ap.add_argument("--warmup", type=int, default=5)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--config", default="rotor41")
-    ap.add_argument("--N", type=int, default=128)
+    ap.add_argument("--N", type=int, default=None, help="sub-intervals (default: the workload's own)")
     ap.add_argument("--batch", type=int, default=1)
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-fp64", action="store_true")
@@ -143,8 +147,9 @@ def oracle_sample(cfg: str, N_full: int):
     from oracle import ism_oracle as O
 
     full = W.config(cfg, N=N_full)
-    Nt_s = full.Nt // 8
-    N_s = max(1, N_full // 8)
+    div = SAMPLE_DIV.get(cfg, 8)
+    Nt_s = max(1, full.Nt // div)
+    N_s = max(1, full.N // div)
     w = W.config(cfg, N=N_s, Nt=Nt_s)
     t0 = time.perf_counter()
     O.ism_iteration(w, w.u0, w.rho, w.local_iters)
@@ -243,8 +248,10 @@ def run_ours(args):
     state_steps = 5 * w.Nt                     # useful state-steps per ISM iteration (2 sweeps + 3 sub-interval)
 
     # roofline of the dominant phase (largest share of device time); one launch of a phase per iteration
-    names = ["k_assemble", "k_chain", "k_sweeps2"]
-    kernels = ["k_cheb_prep + k_assemble", "k_chain + k_phi", "k_sweeps2 + k_gradpass"]
+    large = plan.ks_large
+    names = ["k_lsweep", "k_phi", "k_lsub"] if large else ["k_assemble", "k_chain", "k_sweeps2"]
+    kernels = (["k_cheb_prep + k_lsweep", "k_phi", "k_lsub"] if large
+               else ["k_cheb_prep + k_assemble", "k_chain + k_phi", "k_sweeps2 + k_gradpass"])
     dom = int(np.argmax(st["ms"]))
     ms_launch = st["ms"][dom] / args.steps
     peaks = measured_peaks()
@@ -308,8 +315,8 @@ def run_ours(args):
         "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": tot_ms / args.steps, "higher_is_better": True, "scaling": "weak",
         "vs_baseline": None, "dtype": "f32 propagation, f64 states/overlaps/update", "data": "synthetic",
-        "config": {"workload": f"{args.config}: rigid rotor j<=40 (d={w.d}), <cos theta>(T), T=pi, Nt={w.Nt}, "
-                               f"N={w.N}, batch={B} per GPU", "d": w.d, "Nt": w.Nt, "N": w.N, "batch": B,
+        "config": {"workload": f"{args.config}: {DESCR.get(args.config, args.config)} (d={w.d}), T={w.T:g}, "
+                               f"Nt={w.Nt}, N={w.N}, batch={B} per GPU", "d": w.d, "Nt": w.Nt, "N": w.N, "batch": B,
                    "precision": "mixed", "l2": "flushed between steps (512 MB write, outside the timed events)"},
         "state_steps_per_s": value * state_steps,
         "step_ms_p50": statistics.median(step_ms), "step_ms_p99": float(np.percentile(step_ms, 99)),

@@ -195,7 +195,9 @@ int ism_get_stats(ism_plan_t plan, ism_stats* out, int reset);
 /* ism_plan_info -- integer facts about a plan, for tests and benchmarks:
  *   key 0: group lanes per state, 1: state elements per lane, 2: kernel launches per ISM
  *   iteration (L = local_iters), 3: bytes of plan-owned device memory, 4: bytes of one stored
- *   sub-interval propagator M_n (0 for the grid kind, which assembles none).  Returns -1 for a bad key. */
+ *   sub-interval propagator M_n (0 when none is assembled), 5: 1 when the plan propagates the global
+ *   trajectories directly (bit-flip d >= 128, one state per CTA) instead of assembling M_n.
+ *   Returns -1 for a bad key. */
 long long ism_plan_info(ism_plan_t plan, int key);
 
 /*

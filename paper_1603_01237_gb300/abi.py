@@ -234,6 +234,11 @@ class Plan:
     def info(self, key: int) -> int:
         return int(load().ism_plan_info(self.handle, key))
 
+    @property
+    def ks_large(self) -> bool:
+        """True when the global trajectories are propagated directly (d >= 128) instead of assembled."""
+        return self.info(5) == 1
+
     # ---------------------------------------------------------------- numpy conveniences
     def _u(self, u):
         u = np.ascontiguousarray(np.asarray(u, dtype=np.float64))

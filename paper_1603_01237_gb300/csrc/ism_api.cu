@@ -100,6 +100,7 @@ struct ism_plan_s {
   double2* dphi = nullptr;
   void* dtraj = nullptr;
   void* dtraj2 = nullptr;
+  void* dzp = nullptr;              // large d: per-step, per-warp overlap partials
   double* du = nullptr;
   double* dgrad = nullptr;
   double* dJn = nullptr;
@@ -275,11 +276,13 @@ int validate_problem(const ism_problem& p, int precision) {
   if (p.objective == ISM_OBJ_OVERLAP && !p.psi_f) return fail(ISM_EINVAL, "psi_f is required for the overlap objective");
   if (p.objective == ISM_OBJ_OBSERVABLE && !p.O) return fail(ISM_EINVAL, "O is required for the observable objective");
   if (precision != ISM_FP64 && precision != ISM_MIXED) return fail(ISM_EINVAL, "unknown precision");
-  if (d > 64) return fail(ISM_EUNSUPPORTED, "this build supports d <= 64");
   int q = 0;
   if (p.kind == ISM_H_BITFLIP) {
     while ((1 << q) < d) ++q;
     if ((1 << q) != d || d < 2) return fail(ISM_EINVAL, "bit-flip kind needs d = 2^q >= 2");
+    if (d > 1024) return fail(ISM_EUNSUPPORTED, "this build supports bit-flip d <= 1024");
+  } else if (d > 64) {
+    return fail(ISM_EUNSUPPORTED, "this build supports tridiagonal and dense d <= 64");
   }
   const long nH = p.kind == ISM_H_DENSE ? (long)d * d : p.kind == ISM_H_TRIDIAG ? 2L * d - 1 : d;
   const long nH1 = p.kind == ISM_H_DENSE ? (long)d * d : p.kind == ISM_H_TRIDIAG ? 2L * d - 1 : q;
@@ -304,7 +307,7 @@ int validate_problem(const ism_problem& p, int precision) {
 
 bool select_kernels(int prec, int kind, int d, KernelSet* ks) {
   return kind == ISM_H_TRIDIAG   ? kernels_tridiag(prec, d, ks)
-         : kind == ISM_H_BITFLIP ? kernels_bitflip(prec, d, ks)
+         : kind == ISM_H_BITFLIP ? (d > 64 ? kernels_large_bitflip(prec, d, ks) : kernels_bitflip(prec, d, ks))
                                  : kernels_dense(prec, d, ks);
 }
 
@@ -358,6 +361,8 @@ ism::KParams kparams(ism_plan_s* P, double* u) {
   k.count = P->dcount;
   k.psin = P->dpsin; k.chin = P->dchin; k.form = 0;
   k.update = 0; k.max_spin = P->max_spin;
+  k.psi_i = P->dpsi_i; k.psi_f = P->dpsi_f; k.O = P->dO; k.obj = P->obj;
+  k.psin_w = P->dpsin; k.chin_w = P->dchin; k.zp = P->dzp;
   return k;
 }
 
@@ -383,10 +388,17 @@ int run_states(ism_plan_s* P, const double* u, double* Jhist, int hist_stride, i
     return ISM_OK;
   }
   ism::KParams k = kparams(P, const_cast<double*>(u));
-  ISM_CUDA_TRY(timed(P, 0, 2, [&] {
-    cudaError_t e = ism::launch_cheb_prep(P->prec, k, P->st);
-    return e != cudaSuccess ? e : P->ks.assemble(k, P->st);
-  }));
+  if (P->ks.large) {   // direct sweeps: psi(t_n), chi(t_n) in FP64
+    ISM_CUDA_TRY(timed(P, 0, 2, [&] {
+      cudaError_t e = ism::launch_cheb_prep(P->prec, k, P->st);
+      return e != cudaSuccess ? e : P->ks.lsweep(k, P->st);
+    }));
+  } else {
+    ISM_CUDA_TRY(timed(P, 0, 2, [&] {
+      cudaError_t e = ism::launch_cheb_prep(P->prec, k, P->st);
+      return e != cudaSuccess ? e : P->ks.assemble(k, P->st);
+    }));
+  }
   ism::ChainParams c{};
   c.d = P->d; c.Nt = P->Nt; c.N = P->N; c.B = P->B; c.ldm = P->ldm; c.obj = P->obj;
   c.tau = P->tau; c.T = P->T; c.M = P->dM; c.psi_i = P->dpsi_i; c.psi_f = P->dpsi_f; c.O = P->dO;
@@ -394,7 +406,12 @@ int run_states(ism_plan_s* P, const double* u, double* Jhist, int hist_stride, i
   c.pen = P->dalpha ? P->dpen : nullptr; c.psin = P->dpsin; c.chin = P->dchin; c.phi = P->dphi;
   c.J = P->dJ; c.F = P->dF; c.Jhist = Jhist; c.hist_stride = hist_stride; c.hist_k = hist_k;
   c.status = P->dstatus; c.max_spin = P->max_spin; c.stages = P->chain_stages; c.tile_stride = P->tst;
-  ISM_CUDA_TRY(timed(P, 1, 2, [&] { return ism::launch_chain(P->prec, c, P->chain_smem, P->st); }));
+  if (P->ks.large) {
+    c.src64 = 1;
+    ISM_CUDA_TRY(timed(P, 1, 1, [&] { return ism::launch_phi(P->prec, c, P->st); }));
+  } else {
+    ISM_CUDA_TRY(timed(P, 1, 2, [&] { return ism::launch_chain(P->prec, c, P->chain_smem, P->st); }));
+  }
   return ISM_OK;
 }
 
@@ -513,7 +530,7 @@ int ism_plan(const ism_problem* prob, const ism_options* opt, void* cuda_stream,
 
   bool ok = ism::select_kernels(P->prec, p.kind, d, &P->ks);
   if (!ok) { delete P; return fail(ISM_EUNSUPPORTED, "no compiled kernel for this kind and d"); }
-  const int gpw = 32 / P->ks.GA;
+  const int gpw = P->ks.large ? 1 : 32 / P->ks.GA;
   P->dpad = (d + gpw - 1) / gpw * gpw;
   P->ldm = d | 1;                                   // odd column stride
   P->tst = ((long)d * P->ldm + 1) / 2 * 2;          // even tile stride: tiles are multiples of 16 bytes
@@ -547,25 +564,33 @@ int ism_plan(const ism_problem* prob, const ism_options* opt, void* cuda_stream,
   TRY_ALLOC(P->dbeta, (size_t)P->N);
   TRY_ALLOC(P->dab, (size_t)P->N + 1);
   TRY_ALLOC(P->dcheb, B * P->N * ism::cheb_bytes(P->prec));
-  TRY_ALLOC(P->dstage, B * 2 * ((size_t)P->N + 1) * d * P->r2);
+  if (!P->ks.large) TRY_ALLOC(P->dstage, B * 2 * ((size_t)P->N + 1) * d * P->r2);
   TRY_ALLOC(P->dpen, B * P->N);
   TRY_ALLOC(P->dctab, (size_t)ism::BESSEL_TABLE);
   if (p.alpha) TRY_ALLOC(P->dalpha, (size_t)P->Nt);
   TRY_ALLOC(P->dpsi_i, (size_t)d);
   TRY_ALLOC(P->dpsi_f, (size_t)d);
   if (p.objective == ISM_OBJ_OBSERVABLE) TRY_ALLOC(P->dO, (size_t)d * d);
-  unsigned char* dMb = nullptr;
-  TRY_ALLOC(dMb, B * P->N * (size_t)P->tst * P->r2);
-  P->dM = dMb;
+  if (!P->ks.large) {   // sub-interval propagators M_n (assembly + chain)
+    unsigned char* dMb = nullptr;
+    TRY_ALLOC(dMb, B * P->N * (size_t)P->tst * P->r2);
+    P->dM = dMb;
+  }
   TRY_ALLOC(P->dpsin, B * (P->N + 1) * (size_t)d);
   TRY_ALLOC(P->dchin, B * (P->N + 1) * (size_t)d);
   TRY_ALLOC(P->dphi, B * (P->N + 1) * (size_t)d);
   unsigned char* dTb = nullptr;
   TRY_ALLOC(dTb, B * ((size_t)P->Nt + P->N) * GE * P->r2);
   P->dtraj = dTb;
-  unsigned char* dT2 = nullptr;
-  TRY_ALLOC(dT2, B * ((size_t)P->Nt + P->N) * GE * P->r2);
-  P->dtraj2 = dT2;
+  if (!P->ks.large) {   // second trajectory of the concurrent two-trajectory sweeps
+    unsigned char* dT2 = nullptr;
+    TRY_ALLOC(dT2, B * ((size_t)P->Nt + P->N) * GE * P->r2);
+    P->dtraj2 = dT2;
+  } else {
+    unsigned char* dZ = nullptr;
+    TRY_ALLOC(dZ, B * ((size_t)P->Nt + P->N) * P->ks.W * P->r2);
+    P->dzp = dZ;
+  }
   TRY_ALLOC(P->du, B * P->Nt);
   TRY_ALLOC(P->dgrad, B * P->Nt);
   TRY_ALLOC(P->dJn, B * P->N);
@@ -641,7 +666,8 @@ long long ism_plan_info(ism_plan_t P, int key) {
     case 1: return P->ks.E;
     case 2: return 2 + P->L;
     case 3: return (long long)P->bytes;
-    case 4: return P->gp ? 0 : (long long)(P->tst * P->r2);
+    case 4: return (P->gp || P->ks.large) ? 0 : (long long)(P->tst * P->r2);
+    case 5: return P->ks.large ? 1 : 0;
     default: return -1;
   }
 }
@@ -766,7 +792,7 @@ int ism_iterate(ism_plan_t P, int iters, double* u_inout, double* J_hist, double
         ISM_CUDA_TRY(ism::launch_cheb_prep(P->prec, k, P->st));
         P->kernels += 1;
       }
-      if (k.form) ISM_CUDA_TRY(timed(P, 2, 2, [&] { return P->ks.sweeps2(k, P->st); }));
+      if (k.form && !P->ks.large) ISM_CUDA_TRY(timed(P, 2, 2, [&] { return P->ks.sweeps2(k, P->st); }));
       else ISM_CUDA_TRY(timed(P, 2, 1, [&] { return P->ks.subinterval(k, P->st); }));
     }
     if (err_hist) {

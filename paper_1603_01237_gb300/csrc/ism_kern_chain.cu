@@ -3,21 +3,40 @@
 
 namespace ism {
 
-cudaError_t launch_chain(int prec, const ChainParams& p, size_t smem, cudaStream_t st) {
+template <typename R, int JC>
+static cudaError_t chain_t(const ChainParams& p, size_t smem, cudaStream_t st) {
   dim3 grid(p.obj == 0 ? 2 : 1, p.B);
   const int threads = (chain_consumer_warps(p.d) + 1) * 32;   // consumer warps + one producer warp
-  cudaError_t e;
-  if (prec == 0) {
-    e = cudaFuncSetAttribute(k_chain<double>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-    if (e != cudaSuccess) return e;
-    k_chain<double><<<grid, threads, smem, st>>>(p);
-  } else {
-    e = cudaFuncSetAttribute(k_chain<float>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-    if (e != cudaSuccess) return e;
-    k_chain<float><<<grid, threads, smem, st>>>(p);
-  }
-  e = cudaGetLastError();
+  cudaError_t e = cudaFuncSetAttribute(k_chain<R, JC>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
   if (e != cudaSuccess) return e;
+  k_chain<R, JC><<<grid, threads, smem, st>>>(p);
+  return cudaGetLastError();
+}
+
+template <typename R>
+static cudaError_t chain_d(const ChainParams& p, size_t smem, cudaStream_t st) {
+  switch ((p.d + CHAIN_LANES - 1) / CHAIN_LANES) {   // columns per consumer thread
+    case 1: return chain_t<R, 1>(p, smem, st);
+    case 2: return chain_t<R, 2>(p, smem, st);
+    case 3: return chain_t<R, 3>(p, smem, st);
+    case 4: return chain_t<R, 4>(p, smem, st);
+    case 5: return chain_t<R, 5>(p, smem, st);
+    case 6: return chain_t<R, 6>(p, smem, st);
+    case 7: return chain_t<R, 7>(p, smem, st);
+    case 8: return chain_t<R, 8>(p, smem, st);
+    default: return cudaErrorInvalidValue;
+  }
+}
+
+cudaError_t launch_chain(int prec, const ChainParams& p, size_t smem, cudaStream_t st) {
+  cudaError_t e = prec == 0 ? chain_d<double>(p, smem, st) : chain_d<float>(p, smem, st);
+  if (e != cudaSuccess) return e;
+  if (prec == 0) k_phi<double><<<dim3(p.N + 2, p.B), 128, 0, st>>>(p);
+  else k_phi<float><<<dim3(p.N + 2, p.B), 128, 0, st>>>(p);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_phi(int prec, const ChainParams& p, cudaStream_t st) {
   if (prec == 0) k_phi<double><<<dim3(p.N + 2, p.B), 128, 0, st>>>(p);
   else k_phi<float><<<dim3(p.N + 2, p.B), 128, 0, st>>>(p);
   return cudaGetLastError();

@@ -1,0 +1,45 @@
+// Spin chains of 7 to 10 sites (d = 128 .. 1024): diagonal H0, bit-flip H1, one state per CTA.
+#include "ism_large.cuh"
+#include "ism_launch.h"
+
+namespace ism {
+
+template <typename R, class Op>
+cudaError_t launch_lsweep_t(const KParams& p, cudaStream_t st) {
+  k_lsweep<R, Op><<<dim3(p.obj == 0 ? 2 : 1, p.B), Op::NT, 0, st>>>(p);
+  return cudaGetLastError();
+}
+
+template <typename R, class Op>
+cudaError_t launch_lsub_t(const KParams& p, cudaStream_t st) {
+  k_lsub<R, Op><<<dim3(p.N, p.B), Op::NT, 0, st>>>(p);
+  return cudaGetLastError();
+}
+
+template <typename R, int W>
+static void fill_large(KernelSet* ks) {
+  using Op = OpBitflipCTA<R, W, 4>;
+  ks->large = true;
+  ks->lsweep = &launch_lsweep_t<R, Op>;
+  ks->subinterval = &launch_lsub_t<R, Op>;
+  ks->G = Op::NT;
+  ks->E = Op::E;
+  ks->W = W;
+}
+
+template <typename R>
+static bool pick(int d, KernelSet* ks) {
+  switch (d) {
+    case 128: fill_large<R, 1>(ks); return true;
+    case 256: fill_large<R, 2>(ks); return true;
+    case 512: fill_large<R, 4>(ks); return true;
+    case 1024: fill_large<R, 8>(ks); return true;
+    default: return false;
+  }
+}
+
+bool kernels_large_bitflip(int prec, int d, KernelSet* ks) {
+  return prec == 0 ? pick<double>(d, ks) : pick<float>(d, ks);
+}
+
+}  // namespace ism

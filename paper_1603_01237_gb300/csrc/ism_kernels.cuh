@@ -40,6 +40,14 @@ struct KParams {
   int form;                    // 0: literal sub-problem from phi; 1: Theorem 2 two-trajectory form
   int update;
   int max_spin;
+  // direct global sweeps (large d): inputs and FP64 outputs, per-warp overlap partials
+  const double2* psi_i;        // [d]
+  const double2* psi_f;        // [d]
+  const double* O;             // [d][d] (observable objective)
+  int obj;
+  double2* psin_w;             // [B][N+1][d] psi(t_n)
+  double2* chin_w;             // [B][N+1][d] chi(t_n)
+  void* zp;                    // [B][Nt+N][W] (R2)
 };
 
 struct ChainParams {
@@ -66,6 +74,7 @@ struct ChainParams {
   long tile_stride;       // R2 elements between consecutive tiles (d*ldm rounded up to even)
   int* status;
   int max_spin;
+  int src64;              // k_phi: psi(t_n), chi(t_n) are already FP64 in psin, chin (direct sweeps)
 };
 
 template <typename R> __device__ __forceinline__ R ldu_ro(const double* u, long i) { return (R)__ldg(u + i); }
@@ -589,32 +598,42 @@ __device__ __forceinline__ void consumer_sync(int nthreads) {
   asm volatile("bar.sync 1, %0;" ::"r"(nthreads) : "memory");
 }
 
-template <typename R, bool HERM>
+// Per-thread shared-memory offsets of the tile elements a consumer thread reads, computed once:
+// thread (i = t / 8, q = t % 8) reads columns k = q + 8 j, j < JC = ceil(d / 8), of row i.
+template <int JC>
+struct ChainIdx {
+  int off[JC];    // element offset in a tile: (k, i) of M (HERM = false) or (i, k) (HERM = true)
+  int xk[JC];     // k
+  unsigned on;    // bit j: k < d and i < d
+  __device__ void init(int d, int ldm, bool herm) {
+    const int i = threadIdx.x / CHAIN_LANES, q = threadIdx.x % CHAIN_LANES;
+    on = 0u;
+#pragma unroll
+    for (int j = 0; j < JC; ++j) {
+      const int k = q + CHAIN_LANES * j;
+      const bool ok = k < d && i < d;
+      off[j] = ok ? (herm ? i * ldm + k : k * ldm + i) : 0;
+      xk[j] = ok ? k : 0;
+      on |= ok ? (1u << j) : 0u;
+    }
+  }
+};
+
+template <typename R, bool HERM, int JC>
 __device__ __forceinline__ void chain_mv(const typename C2<R>::T* Ms, const typename C2<R>::T* x,
-                                         typename C2<R>::T* y, int d, int ldm) {
+                                         typename C2<R>::T* y, const ChainIdx<JC>& ix, int d) {
   using R2 = typename C2<R>::T;
   const int i = threadIdx.x / CHAIN_LANES, q = threadIdx.x % CHAIN_LANES;
   R ar0 = R(0), ai0 = R(0), ar1 = R(0), ai1 = R(0);
-  if (i < d) {
-    int k = q;
-    for (; k + CHAIN_LANES < d; k += 2 * CHAIN_LANES) {
-      const int k2 = k + CHAIN_LANES;
-      const R2 m0 = HERM ? Ms[i * ldm + k] : Ms[k * ldm + i];
-      const R2 m1 = HERM ? Ms[i * ldm + k2] : Ms[k2 * ldm + i];
-      const R2 x0 = x[k], x1 = x[k2];
-      if (!HERM) {
-        ar0 = fma(m0.x, x0.x, fma(-m0.y, x0.y, ar0)); ai0 = fma(m0.x, x0.y, fma(m0.y, x0.x, ai0));
-        ar1 = fma(m1.x, x1.x, fma(-m1.y, x1.y, ar1)); ai1 = fma(m1.x, x1.y, fma(m1.y, x1.x, ai1));
-      } else {
-        ar0 = fma(m0.x, x0.x, fma(m0.y, x0.y, ar0)); ai0 = fma(m0.x, x0.y, fma(-m0.y, x0.x, ai0));
-        ar1 = fma(m1.x, x1.x, fma(m1.y, x1.y, ar1)); ai1 = fma(m1.x, x1.y, fma(-m1.y, x1.x, ai1));
-      }
-    }
-    if (k < d) {
-      const R2 m0 = HERM ? Ms[i * ldm + k] : Ms[k * ldm + i];
-      const R2 x0 = x[k];
-      if (!HERM) { ar0 = fma(m0.x, x0.x, fma(-m0.y, x0.y, ar0)); ai0 = fma(m0.x, x0.y, fma(m0.y, x0.x, ai0)); }
-      else { ar0 = fma(m0.x, x0.x, fma(m0.y, x0.y, ar0)); ai0 = fma(m0.x, x0.y, fma(-m0.y, x0.x, ai0)); }
+#pragma unroll
+  for (int j = 0; j < JC; ++j) {
+    if (ix.on & (1u << j)) {
+      const R2 m = Ms[ix.off[j]];
+      const R2 xv = x[ix.xk[j]];
+      R& ar = (j & 1) ? ar1 : ar0;
+      R& ai = (j & 1) ? ai1 : ai0;
+      if (!HERM) { ar = fma(m.x, xv.x, fma(-m.y, xv.y, ar)); ai = fma(m.x, xv.y, fma(m.y, xv.x, ai)); }
+      else { ar = fma(m.x, xv.x, fma(m.y, xv.y, ar)); ai = fma(m.x, xv.y, fma(-m.y, xv.x, ai)); }
     }
   }
   R ar = ar0 + ar1, ai = ai0 + ai1;
@@ -665,10 +684,12 @@ __device__ void chain_produce(const ChainRing<R>& ring, int* status, int max_spi
 // One chain of N matvecs over uses m0 .. m0+N-1 of the ring, run by the CW consumer warps; x_0 in
 // xs[0]; stores the N results (FP32 staging) into out[idx * d] with idx = c (psi) or N - c (chi).
 // Returns false (uniformly over the consumers) if a tile did not arrive.
-template <typename R, bool HERM>
+template <typename R, bool HERM, int JC>
 __device__ bool run_chain(const ChainRing<R>& ring, int m0, int N, int d, int ldm, typename C2<R>::T (*xs)[64],
                           typename C2<R>::T* out, int* fail, int* status, int max_spin, int ncons) {
   const int t = threadIdx.x;
+  ChainIdx<JC> ix;
+  ix.init(d, ldm, HERM);
   for (int c = 0; c <= N; ++c) {
     const int m = m0 + c;
     if (c < N && !mbar_wait(&ring.full[m % ring.NS], (unsigned)((m / ring.NS) & 1), max_spin)) {
@@ -682,7 +703,7 @@ __device__ bool run_chain(const ChainRing<R>& ring, int m0, int N, int d, int ld
       if (t < d) out[(long)idx * d + t] = xs[c & 1][t];   // FP32 here; FP64 conversion in k_phi
     }
     if (c < N) {
-      chain_mv<R, HERM>(ring.tile(m), xs[c & 1], xs[(c + 1) & 1], d, ldm);
+      chain_mv<R, HERM, JC>(ring.tile(m), xs[c & 1], xs[(c + 1) & 1], ix, d);
       __syncwarp();
       if ((t & 31) == 0) mbar_arrive(&ring.empty[m % ring.NS]);
     }
@@ -695,7 +716,7 @@ __device__ bool run_chain(const ChainRing<R>& ring, int m0, int N, int d, int ld
 // CTA 0 runs the psi chain, CTA 1 the chi chain from psi_f, concurrently.  nchains = 1 (observable):
 // one CTA runs the psi chain, forms chi(T) = O psi(T) in FP64 and runs the chi chain, all from one ring.
 // Intermediate states and J follow in k_phi.
-template <typename R>
+template <typename R, int JC>
 __global__ void __launch_bounds__(CHAIN_MAX_THREADS) k_chain(ChainParams p) {
   using R2 = typename C2<R>::T;
   extern __shared__ __align__(128) unsigned char smem_raw[];
@@ -740,7 +761,7 @@ __global__ void __launch_bounds__(CHAIN_MAX_THREADS) k_chain(ChainParams p) {
   int m0 = 0;
   if (do_psi) {
     if (t < d) { const double2 z = p.psi_i[t]; R2 r; r.x = (R)z.x; r.y = (R)z.y; xs[0][t] = r; }
-    if (!run_chain<R, false>(ring, m0, N, d, p.ldm, xs, sps, &fail, p.status, p.max_spin, ncons)) return;
+    if (!run_chain<R, false, JC>(ring, m0, N, d, p.ldm, xs, sps, &fail, p.status, p.max_spin, ncons)) return;
     m0 += N;
   }
   if (do_chi) {
@@ -765,7 +786,7 @@ __global__ void __launch_bounds__(CHAIN_MAX_THREADS) k_chain(ChainParams p) {
     }
     consumer_sync(ncons);
     if (t < d) { const double2 z = vd[t]; R2 r; r.x = (R)z.x; r.y = (R)z.y; xs[0][t] = r; chin[(long)N * d + t] = z; }
-    if (!run_chain<R, true>(ring, m0, N, d, p.ldm, xs, sch, &fail, p.status, p.max_spin, ncons)) return;
+    if (!run_chain<R, true, JC>(ring, m0, N, d, p.ldm, xs, sch, &fail, p.status, p.max_spin, ncons)) return;
   }
 }
 
@@ -788,11 +809,14 @@ __global__ void __launch_bounds__(128) k_phi(ChainParams p) {
     for (int e = t; e < d; e += blockDim.x) {
       double2 ps, cs;
       if (n == 0) ps = p.psi_i[e];
+      else if (p.src64) ps = psin[(long)n * d + e];
       else { const R2 z = sps[(long)n * d + e]; ps = make_double2((double)z.x, (double)z.y); }
-      if (n == N) cs = chin[(long)N * d + e];
+      if (n == N || p.src64) cs = chin[(long)n * d + e];
       else { const R2 z = sch[(long)n * d + e]; cs = make_double2((double)z.x, (double)z.y); }
-      psin[(long)n * d + e] = ps;
-      if (n < N) chin[(long)n * d + e] = cs;
+      if (!p.src64) {
+        psin[(long)n * d + e] = ps;
+        if (n < N) chin[(long)n * d + e] = cs;
+      }
       phi[e] = n == 0 ? ps : (n == N ? cs : make_double2(w.x * ps.x + w.y * cs.x, w.x * ps.y + w.y * cs.y));
     }
     return;
@@ -800,8 +824,9 @@ __global__ void __launch_bounds__(128) k_phi(ChainParams p) {
   // J and F: <psi(T)|chi(T)> is the overlap with psi_f or <psi|O|psi>
   double ovr = 0.0, ovi = 0.0;
   for (int e = t; e < d; e += blockDim.x) {
-    const R2 z = sps[(long)N * d + e];
-    const double ax = (double)z.x, ay = (double)z.y;
+    double ax, ay;
+    if (p.src64) { const double2 z = psin[(long)N * d + e]; ax = z.x; ay = z.y; }
+    else { const R2 z = sps[(long)N * d + e]; ax = (double)z.x; ay = (double)z.y; }
     const double2 c = chin[(long)N * d + e];
     ovr += ax * c.x + ay * c.y;
     ovi += ax * c.y - ay * c.x;

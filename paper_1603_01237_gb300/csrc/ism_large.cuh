@@ -1,0 +1,381 @@
+// ism_large.cuh -- the ISM path for state dimensions too large for one warp (spin chains of 7 to 11
+// sites, d = 2^q = 128 .. 2048) with diagonal H0 and bit-flip H1 = sum_i h_i X_i.
+//
+// One state is spread over a whole CTA of W warps, E contiguous elements per thread (element
+// e = t * E + r, t = threadIdx.x): the bits of e below log2(E) live in one thread, the next five in
+// the lanes of a warp (shuffles), the rest across warps (shared memory, one block barrier per
+// application of H).  Assembling the sub-interval propagators M_n (Sec. 3) would cost d state
+// propagations per sub-interval and d^2 storage each, so the global trajectories of Algorithm 1
+// steps (a)-(b) are propagated directly: one CTA runs psi forward over all Nt steps, another chi
+// backward (Sec. 2: Step 1 is the sequential part of the method), storing psi(t_n), chi(t_n) in FP64.
+//
+//   k_lsweep  steps (a)-(b): psi(t_n) and chi(t_n), n = 0..N, by direct propagation.
+//   k_lsub    step (c): one CTA per (problem, n), the same computation as k_subinterval.
+#pragma once
+#include "ism_kernels.cuh"
+
+namespace ism {
+
+template <typename R, int W_, int E_>
+struct OpBitflipCTA {
+  static constexpr int W = W_, E = E_, NT = 32 * W_;
+  static constexpr int LE = Log2<E_>::v, LW = Log2<W_>::v, Q = LE + 5 + LW;
+  static constexpr int D = 1 << Q;
+  using R2 = typename C2<R>::T;
+  R ah[E], al[E];   // 2(H0_ee - c)/rad as hi + lo
+  R h[Q], yh[Q];
+  R2* buf;          // [2][D] exchange buffers in shared memory
+  mutable int par;
+
+  __device__ void load(const R* H, R2* sbuf) {
+#pragma unroll
+    for (int i = 0; i < Q; ++i) h[i] = H[D + i];
+    buf = sbuf;
+    par = 0;
+  }
+  __device__ void scale(const double* H0d, const Cheb<R>& ch) {
+#pragma unroll
+    for (int r = 0; r < E; ++r) split2<R>((H0d[threadIdx.x * E + r] - ch.cd) * ch.s2d, ah[r], al[r]);
+  }
+  __device__ __forceinline__ void set_u(R u, const Cheb<R>& ch, int) {
+    const R s2 = R(2) * ch.inv_rad;
+#pragma unroll
+    for (int i = 0; i < Q; ++i) yh[i] = u * h[i] * s2;
+  }
+  // acc += sum_i w_i X_i in.  Called by every thread of the CTA in the same order.
+  template <class V>
+  __device__ __forceinline__ void flips(const V& in, V& acc, const R* w) const {
+#pragma unroll
+    for (int i = 0; i < LE; ++i)
+#pragma unroll
+      for (int r = 0; r < E; ++r) {
+        acc.re[r] = fma(w[i], in.re[r ^ (1 << i)], acc.re[r]);
+        acc.im[r] = fma(w[i], in.im[r ^ (1 << i)], acc.im[r]);
+      }
+#pragma unroll
+    for (int i = 0; i < 5; ++i)
+#pragma unroll
+      for (int r = 0; r < E; ++r) {
+        const R xr = __shfl_xor_sync(0xffffffffu, in.re[r], 1 << i);
+        const R xi = __shfl_xor_sync(0xffffffffu, in.im[r], 1 << i);
+        acc.re[r] = fma(w[LE + i], xr, acc.re[r]);
+        acc.im[r] = fma(w[LE + i], xi, acc.im[r]);
+      }
+    if (LW > 0) {
+      // Double-buffered: a buffer is rewritten two exchanges later, after every thread has passed
+      // the barrier of the exchange in between, so one barrier per exchange suffices.
+      R2* b = buf + par * D;
+      par ^= 1;
+      const int e0 = threadIdx.x * E;
+#pragma unroll
+      for (int r = 0; r < E; ++r) { R2 z; z.x = in.re[r]; z.y = in.im[r]; b[e0 + r] = z; }
+      __syncthreads();
+#pragma unroll
+      for (int i = 0; i < LW; ++i)
+#pragma unroll
+        for (int r = 0; r < E; ++r) {
+          const R2 z = b[(e0 + r) ^ (1 << (LE + 5 + i))];
+          acc.re[r] = fma(w[LE + 5 + i], z.x, acc.re[r]);
+          acc.im[r] = fma(w[LE + 5 + i], z.y, acc.im[r]);
+        }
+    }
+  }
+  template <class V>
+  __device__ __forceinline__ void rec(const V& in, const V& sub, V& out) const {
+    V t;
+#pragma unroll
+    for (int r = 0; r < E; ++r) {
+      R xr = -sub.re[r], xi = -sub.im[r];
+      if (sizeof(R) == 4) { xr = fma(al[r], in.re[r], xr); xi = fma(al[r], in.im[r], xi); }
+      t.re[r] = fma(ah[r], in.re[r], xr);
+      t.im[r] = fma(ah[r], in.im[r], xi);
+    }
+    flips(in, t, yh);
+    out = t;
+  }
+  template <class V>
+  __device__ __forceinline__ void h1(const V& in, V& out) const {
+#pragma unroll
+    for (int r = 0; r < E; ++r) { out.re[r] = R(0); out.im[r] = R(0); }
+    flips(in, out, h);
+  }
+};
+
+// CTA-wide sum (every thread gets it); red holds >= 32 doubles.
+__device__ inline double cta_sum(double v, double* red) {
+  for (int m = 16; m >= 1; m >>= 1) v += __shfl_xor_sync(0xffffffffu, v, m);
+  __syncthreads();
+  if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = v;
+  __syncthreads();
+  double s = 0.0;
+  for (int w = 0; w < (int)(blockDim.x >> 5); ++w) s += red[w];
+  __syncthreads();
+  return s;
+}
+
+// The parameters of sub-interval (b, n) into the CTA's shared copy.
+template <typename R>
+__device__ __forceinline__ void cheb_load_cta(Cheb<R>& ch, const void* cheb, long idx) {
+  const int* s = reinterpret_cast<const int*>(reinterpret_cast<const Cheb<R>*>(cheb) + idx);
+  int* d = reinterpret_cast<int*>(&ch);
+  constexpr int words = sizeof(Cheb<R>) / sizeof(int);
+  __syncthreads();   // the previous parameters are no longer read
+  for (int i = threadIdx.x; i < words; i += blockDim.x) d[i] = s[i];
+  __syncthreads();
+}
+
+template <typename R, int E>
+__device__ __forceinline__ void load_state(Vec<R, E>& v, Vec<R, E>& lo, const double2* src) {
+#pragma unroll
+  for (int r = 0; r < E; ++r) {
+    const double2 z = src[threadIdx.x * E + r];
+    v.re[r] = (R)z.x;
+    v.im[r] = (R)z.y;
+    lo.re[r] = sizeof(R) == 4 ? (R)(z.x - (double)v.re[r]) : R(0);
+    lo.im[r] = sizeof(R) == 4 ? (R)(z.y - (double)v.im[r]) : R(0);
+  }
+}
+
+// Apply the segment phase in FP64, store the FP64 state, and continue from its hi + lo split.
+template <typename R, int E>
+__device__ __forceinline__ void phase_store(Vec<R, E>& v, Vec<R, E>& lo, const Cheb<R>& ch, bool adj, double2* dst) {
+#pragma unroll
+  for (int r = 0; r < E; ++r) {
+    double yr, yi;
+    phase_rotate(ch.cph, ch.sph, adj, (double)v.re[r] + (double)lo.re[r], (double)v.im[r] + (double)lo.im[r], yr, yi);
+    dst[threadIdx.x * E + r] = make_double2(yr, yi);
+    v.re[r] = (R)yr;
+    v.im[r] = (R)yi;
+    lo.re[r] = sizeof(R) == 4 ? (R)(yr - (double)v.re[r]) : R(0);
+    lo.im[r] = sizeof(R) == 4 ? (R)(yi - (double)v.im[r]) : R(0);
+  }
+}
+
+// ------------------------------------------------------------------------------- k_lsweep
+// grid (nchains, B), Op::NT threads.  nchains = 2 (overlap objective): CTA 0 propagates psi forward
+// from psi_i, CTA 1 chi backward from psi_f, concurrently.  nchains = 1 (observable): one CTA runs
+// psi, forms chi(T) = O psi(T) in FP64 and runs chi.  Both trajectories are compensated (hi + lo)
+// in FP32 and rounded through FP64 at every sub-interval end, where the segment phase is applied.
+template <typename R, class Op>
+__global__ void __launch_bounds__(Op::NT) k_lsweep(KParams p) {
+  constexpr int E = Op::E, D = Op::D;
+  constexpr bool COMP = sizeof(R) == 4;
+  using R2 = typename C2<R>::T;
+  __shared__ __align__(16) R2 sbuf[2 * D];
+  __shared__ Cheb<R> ch;
+  __shared__ double red[32];
+  const int b = blockIdx.y, N = p.N;
+  const bool single = gridDim.x == 1;
+  const double* ub = p.u + (long)b * p.Nt;
+  double2* psin = p.psin_w + (long)b * (N + 1) * D;
+  double2* chin = p.chin_w + (long)b * (N + 1) * D;
+  Op op;
+  op.load(reinterpret_cast<const R*>(p.H), sbuf);
+  Vec<R, E> v, lo;
+  if (single || blockIdx.x == 0) {
+    load_state<R, E>(v, lo, p.psi_i);
+#pragma unroll
+    for (int r = 0; r < E; ++r) psin[threadIdx.x * E + r] = p.psi_i[threadIdx.x * E + r];
+    for (int n = 0; n < N; ++n) {
+      cheb_load_cta<R>(ch, p.cheb, (long)b * N + n);
+      op.scale(p.H0d, ch);
+      const int j0 = p.jn[n], j1 = p.jn[n + 1];
+      R un = ldu_ro<R>(ub, j0);
+      for (int j = j0; j < j1; ++j) {
+        const R uj = un;
+        if (j + 1 < j1) un = ldu_ro<R>(ub, j + 1);
+        op.set_u(uj, ch, 0);
+        cheb_step<false, COMP>(v, lo, op, ch, ch.K, ch.S);
+      }
+      phase_store<R, E>(v, lo, ch, false, psin + (long)(n + 1) * D);
+      if (p.count && threadIdx.x == 0) count_work<R>(p.count, ch, j1 - j0, 0);
+    }
+  }
+  if (single || blockIdx.x == 1) {
+    double2* chT = chin + (long)N * D;
+    if (p.obj == 0) {
+#pragma unroll
+      for (int r = 0; r < E; ++r) chT[threadIdx.x * E + r] = p.psi_f[threadIdx.x * E + r];
+    } else {   // chi(T) = O psi(T), FP64; psi(T) was written by this CTA
+      __syncthreads();
+      const double2* psT = psin + (long)N * D;
+#pragma unroll 1
+      for (int r = 0; r < E; ++r) {
+        const int e = threadIdx.x * E + r;
+        double sr = 0.0, si = 0.0;
+        for (int f = 0; f < D; ++f) {
+          const double o = p.O[(long)e * D + f];
+          const double2 z = psT[f];
+          sr = fma(o, z.x, sr);
+          si = fma(o, z.y, si);
+        }
+        chT[e] = make_double2(sr, si);
+      }
+      __syncthreads();
+    }
+    load_state<R, E>(v, lo, chT);
+    for (int n = N - 1; n >= 0; --n) {
+      cheb_load_cta<R>(ch, p.cheb, (long)b * N + n);
+      op.scale(p.H0d, ch);
+      const int j0 = p.jn[n], j1 = p.jn[n + 1];
+      R un = ldu_ro<R>(ub, j1 - 1);
+      for (int j = j1 - 1; j >= j0; --j) {
+        const R uj = un;
+        if (j - 1 >= j0) un = ldu_ro<R>(ub, j - 1);
+        op.set_u(uj, ch, 0);
+        cheb_step<true, COMP>(v, lo, op, ch, ch.K, ch.S);
+      }
+      phase_store<R, E>(v, lo, ch, true, chin + (long)n * D);
+      if (p.count && threadIdx.x == 0) count_work<R>(p.count, ch, j1 - j0, 0);
+    }
+  }
+}
+
+// -------------------------------------------------------------------------------- k_lsub
+// grid (N, B), Op::NT threads: sub-problem n of problem b, as k_subinterval (forms 0 and 1), with
+// the state over the CTA.  Per step each warp stores its partial <delta|H1 psi> in zp (slot s, warp w);
+// the FP64 pass sums the W partials.
+template <typename R, class Op>
+__global__ void __launch_bounds__(Op::NT) k_lsub(KParams p) {
+  constexpr int E = Op::E, D = Op::D, W = Op::W;
+  constexpr bool COMP = sizeof(R) == 4;
+  using R2 = typename C2<R>::T;
+  __shared__ __align__(16) R2 sbuf[2 * D];
+  __shared__ Cheb<R> ch;
+  __shared__ double red[32];
+  const int n = blockIdx.x, b = blockIdx.y, t = threadIdx.x, lane = t & 31, wid = t >> 5;
+  const int j0 = p.jn[n], j1 = p.jn[n + 1], ns = j1 - j0;
+  double* ub = p.u + (long)b * p.Nt;
+  const double beta = p.beta[n];
+  cheb_load_cta<R>(ch, p.cheb, (long)b * p.N + n);
+  Op op;
+  op.load(reinterpret_cast<const R*>(p.H), sbuf);
+  op.scale(p.H0d, ch);
+  const int K = ch.K, S = ch.S;
+  const double sPhi = ch.sph, cPhi = ch.cph;
+
+  const long off_n = ((long)b * (p.N + 1) + n) * D;
+  const double2* phn = (p.form ? p.psin : p.phi) + off_n;
+  const double2* phn1 = (p.form ? p.chin : p.phi) + off_n + D;
+  Vec<R, E> v, lo;
+  load_state<R, E>(v, lo, phn);
+  const long slot0 = (long)b * (p.Nt + p.N) + j0 + n;
+  R2* tr0 = reinterpret_cast<R2*>(p.traj) + slot0 * D;   // slot s: H1 psi_n(t_{j0+s}) at tr0 + s*D
+  R2* zp0 = reinterpret_cast<R2*>(p.zp) + slot0 * W;      // slot s: W warp partials
+  R2* tr = tr0 + t * E;
+
+  // ---- forward sweep: store H1 psi_j, then psi_{j+1} = U_j psi_j
+  {
+    R un = ldu<R>(ub, j0);
+    for (int s = 0; s < ns; ++s) {
+      const R uj = un;
+      if (s + 1 < ns) un = ldu<R>(ub, j0 + s + 1);
+      Vec<R, E> hv;
+      op.h1(v, hv);
+#pragma unroll
+      for (int r = 0; r < E; ++r) { R2 z; z.x = hv.re[r]; z.y = hv.im[r]; tr[(long)s * D + r] = z; }
+      op.set_u(uj, ch, 0);
+      cheb_step<false, COMP>(v, lo, op, ch, K, S);
+    }
+  }
+  Vec<R, E> hend;
+  op.h1(v, hend);
+
+  // ---- terminal residual (see k_subinterval)
+  double nrm = 0.0;
+  Vec<R, E> dl;
+#pragma unroll
+  for (int r = 0; r < E; ++r) {
+    const int e = t * E + r;
+    const double2 z = phn1[e];
+    double dr, di;
+    if (!p.form) {
+      double pr, pi;
+      phase_rotate(cPhi, sPhi, false, (double)v.re[r] + (double)lo.re[r], (double)v.im[r] + (double)lo.im[r], pr, pi);
+      dr = z.x - pr;
+      di = z.y - pi;
+      dl.re[r] = (R)dr;
+      dl.im[r] = (R)di;
+    } else {
+      const double2 ps = p.psin[off_n + D + e];
+      dr = (z.x - ps.x) / beta;
+      di = (z.y - ps.y) / beta;
+      dl.re[r] = (R)z.x;
+      dl.im[r] = (R)z.y;
+    }
+    nrm += dr * dr + di * di;
+  }
+  nrm = cta_sum(nrm, red);
+
+  // per-warp partial of <a|h>, FP32 products
+  auto zdot = [&](const Vec<R, E>& a, const Vec<R, E>& h, R2* dst) {
+    R xr = R(0), xi = R(0);
+#pragma unroll
+    for (int r = 0; r < E; ++r) {
+      xr = fma(a.re[r], h.re[r], fma(a.im[r], h.im[r], xr));
+      xi = fma(a.re[r], h.im[r], fma(-a.im[r], h.re[r], xi));
+    }
+    for (int m = 16; m >= 1; m >>= 1) {
+      xr += __shfl_xor_sync(0xffffffffu, xr, m);
+      xi += __shfl_xor_sync(0xffffffffu, xi, m);
+    }
+    if (lane == 0) { R2 z; z.x = xr; z.y = xi; dst[wid] = z; }
+  };
+  zdot(dl, hend, zp0 + (long)ns * W);
+
+  // ---- backward sweep: delta_j = U_j^H delta_{j+1}; partials of step j into zp slot j
+  {
+    auto ldslot = [&](int s, Vec<R, E>& h) {
+#pragma unroll
+      for (int r = 0; r < E; ++r) { const R2 z = tr[(long)s * D + r]; h.re[r] = z.x; h.im[r] = z.y; }
+    };
+    Vec<R, E> hn;
+    ldslot(ns - 1, hn);
+    R un = ldu<R>(ub, j1 - 1);
+    for (int s = ns - 1; s >= 0; --s) {
+      const Vec<R, E> hc = hn;
+      const R uj = un;
+      if (s >= 1) { ldslot(s - 1, hn); un = ldu<R>(ub, j0 + s - 1); }
+      op.set_u(uj, ch, 0);
+      cheb_step<true>(dl, op, ch, K, S);
+      zdot(dl, hc, zp0 + (long)s * W);
+    }
+  }
+  __syncthreads();   // every warp's partials are written
+
+  // ---- FP64 pass over the steps: gradient, Err, ascent step, penalty of J_n
+  const double ht = 0.5 * p.tau * p.w / (p.form ? beta : 1.0);
+  const double tb = p.tau / beta;
+  const double step = p.rho * beta / p.tau;
+  double* gb = p.grad + (long)b * p.Nt;
+  double err = 0.0, pen = 0.0;
+  for (int s = t; s < ns; s += blockDim.x) {
+    const int j = j0 + s;
+    const double uj = ub[j];
+    const double al = p.alpha ? p.alpha[j] : 0.0;
+    double zar = 0.0, zai = 0.0, zbr = 0.0, zbi = 0.0;
+#pragma unroll
+    for (int w = 0; w < W; ++w) {
+      const R2 za = zp0[(long)s * W + w], zb = zp0[(long)(s + 1) * W + w];
+      zar += (double)za.x; zai += (double)za.y;
+      zbr += (double)zb.x; zbi += (double)zb.y;
+    }
+    const double Ia = cPhi * zai - sPhi * zar;
+    const double Ib = cPhi * zbi - sPhi * zbr;
+    const double g = ht * (Ia + Ib) - tb * al * uj;
+    err += fabs(g);
+    pen += al * uj * uj;
+    gb[j] = g;
+    if (p.update) ub[j] = uj + step * g;
+  }
+  err = cta_sum(err, red);
+  pen = cta_sum(pen, red);
+  if (t == 0) {
+    const long gid = (long)b * p.N + n;
+    if (p.Jn) p.Jn[gid] = p.w * (-0.5 * nrm) - 0.5 * tb * pen;
+    if (p.err) p.err[gid] = err;
+  }
+  if (t == 0) count_work<R>(p.count, ch, 2L * ns, 0);   // forward U and backward U^H sweeps
+}
+
+}  // namespace ism

@@ -17,13 +17,19 @@ struct KernelSet {
   int G = 0, E = 0;          // lanes per state, elements per lane (sub-interval sweep)
   int GA = 0;                // lanes per state in the assembly
   size_t op_smem = 0;        // dynamic shared memory of the op (dense H pairs)
+  // large d (one state per CTA): direct global sweeps instead of assembly + chain
+  bool large = false;
+  LaunchFn lsweep = nullptr;
+  int W = 0;                 // warps per state
 };
 
 // prec: 0 = FP64, 1 = FP32 propagation.  Return false when d is outside the compiled range.
 bool kernels_tridiag(int prec, int d, KernelSet* ks);
 bool kernels_bitflip(int prec, int d, KernelSet* ks);
 bool kernels_dense(int prec, int d, KernelSet* ks);
-cudaError_t launch_chain(int prec, const ChainParams& p, size_t smem, cudaStream_t st);
+bool kernels_large_bitflip(int prec, int d, KernelSet* ks);   // d = 128, 256, 512, 1024
+cudaError_t launch_chain(int prec, const ChainParams& p, size_t smem, cudaStream_t st);   // k_chain + k_phi
+cudaError_t launch_phi(int prec, const ChainParams& p, cudaStream_t st);                   // k_phi alone
 bool select_kernels(int prec, int kind, int d, KernelSet* ks);
 // per-sub-interval propagator parameters (one warp each) from the current controls
 cudaError_t launch_cheb_prep(int prec, const KParams& p, cudaStream_t st);

@@ -73,6 +73,7 @@ extern "C" int ism_subinterval_grad_noalloc(const ism_problem* prob, int precisi
     return ism::set_error(ISM_EINVAL, "phi, u, grad and Jn must be device memory for the allocation-free entry point");
   ism::KernelSet ks;
   if (!ism::select_kernels(precision, p.kind, p.d, &ks)) return ism::set_error(ISM_EUNSUPPORTED, "no compiled kernel for this kind and d");
+  if (ks.large) return ism::set_error(ISM_EUNSUPPORTED, "the allocation-free entry point covers d <= 64");
 
   const int d = p.d, B = p.batch < 1 ? 1 : p.batch, GE = ks.G * ks.E;
   const size_t r1 = precision == ISM_FP64 ? sizeof(double) : sizeof(float);
