@@ -305,8 +305,8 @@ int validate_problem(const ism_problem& p, int precision) {
   return ISM_OK;
 }
 
-bool select_kernels(int prec, int kind, int d, KernelSet* ks) {
-  return kind == ISM_H_TRIDIAG   ? kernels_tridiag(prec, d, ks)
+bool select_kernels(int prec, int kind, int d, KernelSet* ks, bool h1diag) {
+  return kind == ISM_H_TRIDIAG   ? kernels_tridiag(prec, d, h1diag, ks)
          : kind == ISM_H_BITFLIP ? (d > 64 ? kernels_large_bitflip(prec, d, ks) : kernels_bitflip(prec, d, ks))
                                  : kernels_dense(prec, d, ks);
 }
@@ -528,7 +528,12 @@ int ism_plan(const ism_problem* prob, const ism_options* opt, void* cuda_stream,
     return ISM_OK;
   }
 
-  bool ok = ism::select_kernels(P->prec, p.kind, d, &P->ks);
+  bool h1diag = true;
+  if (p.kind == ISM_H_TRIDIAG) {
+    h1diag = false;
+    for (int e = 0; e < d; ++e) h1diag |= p.H1[e] != 0.0;
+  }
+  bool ok = ism::select_kernels(P->prec, p.kind, d, &P->ks, h1diag);
   if (!ok) { delete P; return fail(ISM_EUNSUPPORTED, "no compiled kernel for this kind and d"); }
   const int gpw = P->ks.large ? 1 : 32 / P->ks.GA;
   P->dpad = (d + gpw - 1) / gpw * gpw;

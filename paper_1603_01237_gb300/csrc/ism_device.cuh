@@ -159,28 +159,35 @@ __device__ void cheb_load(Cheb<R>& ch, const Cheb<R>* src, int lg, int& Kw, int&
 //   Bitflip: [d0 (d) | h (q)], H1 = sum_i h_i X_i, d = 2^q = G*E.
 //   Dense:   [(G E) x (G E) pairs {H0_ef, H1_ef}] zero padded, row-major, staged in shared memory.
 
-template <typename R, int G_, int E_>
+// HB: H1 has a non-zero diagonal (otherwise its diagonal is neither stored nor applied).  The
+// off-diagonals o0 (H0) and o1 (H1) are read from global memory (L1-resident) once per step, not held
+// in registers, to keep the register count of the many-lane assembly low.
+template <typename R, int G_, int E_, bool HB = true>
 struct OpTridiag {
   static constexpr int G = G_, E = E_, DP_SMEM = 0;
-  R d1[E], o0[E], o1[E];
-  R ah[E], al[E];        // 2(H0_ee - c)/rad as hi + lo (FP64 set-up)
-  R yb[E], yo[E], yom;   // 2u H1_ee/rad, 2Y off-diagonal (e, e+1), 2Y off-diagonal (e0-1, e0)
+  static constexpr int EB = HB ? E_ : 1;
+  const R* o0p;           // H0 off-diagonal of this lane's rows
+  const R* o1p;           // H1 off-diagonal of this lane's rows
+  R o1[E];                // H1 off-diagonal (h1 applications)
+  R d1[EB];               // H1 diagonal
+  R ah[E], al[E];         // 2(H0_ee - c)/rad as hi + lo (FP64 set-up)
+  R yb[EB], yo[E], yom;   // 2u H1_ee/rad, 2Y off-diagonal (e, e+1), 2Y off-diagonal (e0-1, e0)
   R h1m;                  // H1 off-diagonal (e0-1, e0)
-  bool hasb;              // H1 has a diagonal
+  int dd, e0;
 
   // H: packed op data in R; H0d: FP64 diagonal of H0
   __device__ void load(const R* H, const double* H0d, int d, int lg, void*) {
-    bool any = false;
+    dd = d;
+    e0 = lg * E;
+    o0p = H + d;
+    o1p = H + 3 * d;
 #pragma unroll
     for (int r = 0; r < E; ++r) {
-      int e = lg * E + r;
+      int e = e0 + r;
       bool in = e < d;
-      o0[r] = in ? H[d + e] : R(0);
-      d1[r] = in ? H[2 * d + e] : R(0);
       o1[r] = in ? H[3 * d + e] : R(0);
-      any |= d1[r] != R(0);
+      if (HB) d1[r] = in ? H[2 * d + e] : R(0);
     }
-    hasb = __any_sync(0xffffffffu, any);
     R t = g_up<G>(o1[E - 1]);
     h1m = lg == 0 ? R(0) : t;
   }
@@ -195,8 +202,11 @@ struct OpTridiag {
     const R s2 = R(2) * ch.inv_rad;
 #pragma unroll
     for (int r = 0; r < E; ++r) {
-      yb[r] = u * d1[r] * s2;
-      yo[r] = (o0[r] + u * o1[r]) * s2;
+      const int e = e0 + r;
+      const R a = e < dd ? __ldg(o0p + e) : R(0);
+      const R b = e < dd ? __ldg(o1p + e) : R(0);
+      if (HB) yb[r] = u * d1[r] * s2;
+      yo[r] = (a + u * b) * s2;
     }
     R t = g_up<G>(yo[E - 1]);
     yom = lg == 0 ? R(0) : t;
@@ -213,7 +223,7 @@ struct OpTridiag {
       R xr = fma(ym, mre, fma(yo[r], pre, -sub.re[r]));
       R xi = fma(ym, mim, fma(yo[r], pim, -sub.im[r]));
       if (sizeof(R) == 4) { xr = fma(al[r], in.re[r], xr); xi = fma(al[r], in.im[r], xi); }
-      if (hasb) { xr = fma(yb[r], in.re[r], xr); xi = fma(yb[r], in.im[r], xi); }
+      if (HB) { xr = fma(yb[r], in.re[r], xr); xi = fma(yb[r], in.im[r], xi); }
       out.re[r] = fma(ah[r], in.re[r], xr);
       out.im[r] = fma(ah[r], in.im[r], xi);
     }
@@ -227,8 +237,10 @@ struct OpTridiag {
       R mre = r == 0 ? lre : in.re[r - 1], mim = r == 0 ? lim : in.im[r - 1];
       R pre = r == E - 1 ? rre : in.re[r + 1], pim = r == E - 1 ? rim : in.im[r + 1];
       R om = r == 0 ? h1m : o1[r - 1];
-      out.re[r] = fma(d1[r], in.re[r], fma(om, mre, o1[r] * pre));
-      out.im[r] = fma(d1[r], in.im[r], fma(om, mim, o1[r] * pim));
+      R xr = fma(om, mre, o1[r] * pre), xi = fma(om, mim, o1[r] * pim);
+      if (HB) { xr = fma(d1[r], in.re[r], xr); xi = fma(d1[r], in.im[r], xi); }
+      out.re[r] = xr;
+      out.im[r] = xi;
     }
   }
 };

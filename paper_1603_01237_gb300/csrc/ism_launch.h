@@ -24,13 +24,13 @@ struct KernelSet {
 };
 
 // prec: 0 = FP64, 1 = FP32 propagation.  Return false when d is outside the compiled range.
-bool kernels_tridiag(int prec, int d, KernelSet* ks);
+bool kernels_tridiag(int prec, int d, bool h1diag, KernelSet* ks);   // h1diag: H1 has a diagonal
 bool kernels_bitflip(int prec, int d, KernelSet* ks);
 bool kernels_dense(int prec, int d, KernelSet* ks);
 bool kernels_large_bitflip(int prec, int d, KernelSet* ks);   // d = 128, 256, 512, 1024
 cudaError_t launch_chain(int prec, const ChainParams& p, size_t smem, cudaStream_t st);   // k_chain + k_phi
 cudaError_t launch_phi(int prec, const ChainParams& p, cudaStream_t st);                   // k_phi alone
-bool select_kernels(int prec, int kind, int d, KernelSet* ks);
+bool select_kernels(int prec, int kind, int d, KernelSet* ks, bool h1diag = true);
 // per-sub-interval propagator parameters (one warp each) from the current controls
 cudaError_t launch_cheb_prep(int prec, const KParams& p, cudaStream_t st);
 size_t cheb_bytes(int prec);
