@@ -54,7 +54,10 @@ typedef enum {
   /* H0 and H1 are d x d real symmetric, row-major, d <= 64.                                    */
   ISM_H_DENSE = 0,
   /* d = 2^q spins.  H0 is diagonal: H0[0..d-1] = diag(H0).  H1 = sum_i h_i X_i (bit flips of
-     basis index s, spin i <-> bit i): H1[0..q-1] = h_i.  d <= 64.                                */
+     basis index s, spin i <-> bit i): H1[0..q-1] = h_i.  d <= 1024.  For d <= 64 a state lives in
+     part of a warp and the global trajectories go through the assembled sub-interval propagators
+     (Sec. 3); for d = 128 .. 1024 a state spans a whole CTA and the global trajectories of
+     Algorithm 1 (a)-(b) are propagated directly, step by step.                                   */
   ISM_H_BITFLIP = 1,
   /* H0, H1 symmetric tridiagonal: H[0..d-1] = diagonal, H[d..2d-2] = first off-diagonal
      (H[d+e] couples e and e+1).  d <= 64.                                                        */
