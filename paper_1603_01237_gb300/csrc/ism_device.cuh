@@ -60,6 +60,17 @@ __device__ __forceinline__ int warp_max_i(int v) { return __reduce_max_sync(0xff
 
 template <typename R, int E> struct Vec { R re[E]; R im[E]; };
 
+// Packed FP32 complex state: (re, im) of an element in one 64-bit register pair.  Every Hamiltonian
+// here is real, so both halves of an element meet the same real coefficient and one packed FMA
+// (fma.rn.f32x2, sm_100 and later) updates both: half the instructions of the split layout at the
+// same FP32 rate.
+template <int E> struct VecP { float2 z[E]; };
+__device__ __forceinline__ float2 bc2(float a) { return make_float2(a, a); }
+__device__ __forceinline__ float2 neg2(float2 a) { return make_float2(-a.x, -a.y); }
+__device__ __forceinline__ float2 fma2(float2 a, float2 b, float2 c) { return __ffma2_rn(a, b, c); }
+__device__ __forceinline__ float2 add2(float2 a, float2 b) { return __fadd2_rn(a, b); }
+__device__ __forceinline__ float2 mul2(float2 a, float2 b) { return __fmul2_rn(a, b); }
+
 // --------------------------------------------------------------- Bessel and Chebyshev set-up
 
 // Per-group propagator parameters (shared memory).  cf[k] carries a_k with the sign of (-i)^k folded
@@ -165,6 +176,9 @@ __device__ void cheb_load(Cheb<R>& ch, const Cheb<R>* src, int lg, int& Kw, int&
 template <typename R, int G_, int E_, bool HB = true>
 struct OpTridiag {
   static constexpr int G = G_, E = E_, DP_SMEM = 0;
+  static constexpr bool PACKED = true;   // offers rec_p / h1_p on packed FP32 states
+  // resident assembly CTAs per SM to aim for (caps registers at 128 where that costs no spills)
+  static constexpr int ASM_MINB = (E_ <= 6 && !HB) ? 4 : 1;
   static constexpr int EB = HB ? E_ : 1;
   const R* o0p;           // H0 off-diagonal of this lane's rows
   const R* o1p;           // H1 off-diagonal of this lane's rows
@@ -243,6 +257,40 @@ struct OpTridiag {
       out.im[r] = xi;
     }
   }
+  // packed FP32 forms of rec and h1 (R = float)
+  __device__ __forceinline__ void rec_p(const VecP<E>& in, const VecP<E>& sub, VecP<E>& out) const {
+    float2 l, q;
+    l.x = g_up<G>(in.z[E - 1].x);
+    l.y = g_up<G>(in.z[E - 1].y);
+    q.x = g_down<G>(in.z[0].x);
+    q.y = g_down<G>(in.z[0].y);
+#pragma unroll
+    for (int r = 0; r < E; ++r) {
+      const float2 m = r == 0 ? l : in.z[r - 1];
+      const float2 pn = r == E - 1 ? q : in.z[r + 1];
+      const float ym = r == 0 ? (float)yom : (float)yo[r - 1];
+      float2 x = fma2(bc2(ym), m, fma2(bc2((float)yo[r]), pn, neg2(sub.z[r])));
+      x = fma2(bc2((float)al[r]), in.z[r], x);
+      if (HB) x = fma2(bc2((float)yb[r]), in.z[r], x);
+      out.z[r] = fma2(bc2((float)ah[r]), in.z[r], x);
+    }
+  }
+  __device__ __forceinline__ void h1_p(const VecP<E>& in, VecP<E>& out) const {
+    float2 l, q;
+    l.x = g_up<G>(in.z[E - 1].x);
+    l.y = g_up<G>(in.z[E - 1].y);
+    q.x = g_down<G>(in.z[0].x);
+    q.y = g_down<G>(in.z[0].y);
+#pragma unroll
+    for (int r = 0; r < E; ++r) {
+      const float2 m = r == 0 ? l : in.z[r - 1];
+      const float2 pn = r == E - 1 ? q : in.z[r + 1];
+      const float om = r == 0 ? (float)h1m : (float)o1[r - 1];
+      float2 x = fma2(bc2(om), m, mul2(bc2((float)o1[r]), pn));
+      if (HB) x = fma2(bc2((float)d1[r]), in.z[r], x);
+      out.z[r] = x;
+    }
+  }
 };
 
 template <int E> struct Log2 { static constexpr int v = E <= 1 ? 0 : 1 + Log2<E / 2>::v; };
@@ -251,6 +299,8 @@ template <> struct Log2<1> { static constexpr int v = 0; };
 template <typename R, int G_, int E_>
 struct OpBitflip {
   static constexpr int G = G_, E = E_, DP_SMEM = 0;
+  static constexpr bool PACKED = false;
+  static constexpr int ASM_MINB = 1;
   static constexpr int LE = Log2<E>::v, LG = Log2<G>::v, Q = LE + LG;
   R ah[E], al[E];        // 2(H0_ee - c)/rad as hi + lo
   R h[Q > 0 ? Q : 1];
@@ -316,6 +366,8 @@ struct OpBitflip {
 template <typename R, int G_, int E_>
 struct OpDense {
   static constexpr int G = G_, E = E_, DP = G_ * E_, DP_SMEM = G_ * E_;
+  static constexpr bool PACKED = false;
+  static constexpr int ASM_MINB = 1;
   using R2 = typename C2<R>::T;
   const R2* Hs;   // shared memory
   int lg;
@@ -457,6 +509,63 @@ __device__ __forceinline__ void phase_rotate(double cp, double sp, bool adj, dou
 template <bool ADJ, typename R, int E, class Op>
 __device__ __forceinline__ void cheb_step(Vec<R, E>& v, const Op& op, const Cheb<R>& ch, int K, int Sw) {
   cheb_step<ADJ, false>(v, v, op, ch, K, Sw);
+}
+
+// cheb_step on packed FP32 states (the same series, sub-steps and compensation).  Odd terms multiply
+// (-i)^k (forward) or (+i)^k (adjoint): they are summed into a separate packed accumulator o with
+// their signed real coefficients and folded in once per sub-step, acc += (o.im, -o.re), so the
+// inner loop has no re/im swaps.
+template <bool ADJ, bool COMP, int E, class Op>
+__device__ __forceinline__ void cheb_step_p(VecP<E>& v, VecP<E>& lo, const Op& op, const Cheb<float>& ch, int K,
+                                            int Sw) {
+  for (int s = 0; s < Sw; ++s) {
+    const bool on = s < ch.S;
+    VecP<E> t0 = v, t1, acc, o, zero;
+#pragma unroll
+    for (int r = 0; r < E; ++r) zero.z[r] = make_float2(0.f, 0.f);
+    op.rec_p(t0, zero, t1);   // t1 = 2 Y t0
+#pragma unroll
+    for (int r = 0; r < E; ++r) t1.z[r] = mul2(t1.z[r], bc2(0.5f));
+    const float sg = ADJ ? -1.f : 1.f;
+    const float b0h = COMP ? ch.c0h : ch.a0h, b0l = COMP ? ch.c0l : ch.a0l;
+#pragma unroll
+    for (int r = 0; r < E; ++r) {
+      acc.z[r] = fma2(bc2(b0h), t0.z[r], mul2(bc2(b0l), t0.z[r]));
+      o.z[r] = fma2(bc2(sg * ch.a1h), t1.z[r], mul2(bc2(sg * ch.a1l), t1.z[r]));
+    }
+    for (int k = 2; k < K; k += 2) {
+      op.rec_p(t1, t0, t0);   // t0 <- T_k
+      const float2 ce = bc2(ch.cf[k]), cel = bc2(ch.cl[k]);
+#pragma unroll
+      for (int r = 0; r < E; ++r) acc.z[r] = fma2(ce, t0.z[r], fma2(cel, t0.z[r], acc.z[r]));
+      if (k + 1 < K) {
+        op.rec_p(t0, t1, t1);   // t1 <- T_{k+1}
+        const float2 co = bc2(sg * ch.cf[k + 1]), col = bc2(sg * ch.cl[k + 1]);
+#pragma unroll
+        for (int r = 0; r < E; ++r) o.z[r] = fma2(co, t1.z[r], fma2(col, t1.z[r], o.z[r]));
+      }
+    }
+#pragma unroll
+    for (int r = 0; r < E; ++r) {
+      acc.z[r].x += o.z[r].y;
+      acc.z[r].y -= o.z[r].x;
+    }
+    if (!on) continue;
+#pragma unroll
+    for (int r = 0; r < E; ++r) {
+      if (!COMP) {
+        v.z[r] = acc.z[r];
+      } else {
+        // (hi, lo) <- two_sum(hi, acc + lo)
+        const float2 x = v.z[r];
+        const float2 t = add2(acc.z[r], lo.z[r]);
+        const float2 sm = add2(x, t);
+        const float2 bb = add2(sm, neg2(x));
+        lo.z[r] = add2(add2(x, neg2(add2(sm, neg2(bb)))), add2(t, neg2(bb)));
+        v.z[r] = sm;
+      }
+    }
+  }
 }
 
 }  // namespace ism

@@ -92,7 +92,7 @@ __device__ __forceinline__ void count_work(unsigned long long* c, const Cheb<R>&
 
 // ------------------------------------------------------------------------------ k_assemble
 template <typename R, class Op>
-__global__ void __launch_bounds__(128) k_assemble(KParams p) {
+__global__ void __launch_bounds__(128, Op::ASM_MINB) k_assemble(KParams p) {
   constexpr int G = Op::G, E = Op::E, GPB = 128 / G;
   constexpr bool COMP = sizeof(R) == 4;
   using R2 = typename C2<R>::T;
@@ -122,22 +122,44 @@ __global__ void __launch_bounds__(128) k_assemble(KParams p) {
   op.load(reinterpret_cast<const R*>(p.H), p.H0d, p.d, lg, smem_raw);
   op.scale(p.H0d, p.d, lg, ch);
   Vec<R, E> v, lo;
+  if constexpr (sizeof(R) == 4 && Op::PACKED) {   // packed FP32: both halves per instruction
+    VecP<E> pv, pl;
 #pragma unroll
-  for (int r = 0; r < E; ++r) {
-    v.re[r] = (lg * E + r == col) ? R(1) : R(0);
-    v.im[r] = R(0);
-    lo.re[r] = R(0);
-    lo.im[r] = R(0);
-  }
+    for (int r = 0; r < E; ++r) {
+      pv.z[r] = make_float2((lg * E + r == col) ? 1.f : 0.f, 0.f);
+      pl.z[r] = make_float2(0.f, 0.f);
+    }
+    float ua = ldu_ro<float>(ub, j0), ub1 = j0 + 1 < j1 ? ldu_ro<float>(ub, j0 + 1) : 0.f;
+    for (int j = j0; j < j1; ++j) {
+      const float uj = ua;
+      ua = ub1;
+      if (j + 2 < j1) ub1 = ldu_ro<float>(ub, j + 2);
+      op.set_u(uj, ch, lg);
+      cheb_step_p<false, true>(pv, pl, op, ch, Kw, Sw);
+    }
+#pragma unroll
+    for (int r = 0; r < E; ++r) {
+      v.re[r] = pv.z[r].x; v.im[r] = pv.z[r].y;
+      lo.re[r] = pl.z[r].x; lo.im[r] = pl.z[r].y;
+    }
+  } else {
+#pragma unroll
+    for (int r = 0; r < E; ++r) {
+      v.re[r] = (lg * E + r == col) ? R(1) : R(0);
+      v.im[r] = R(0);
+      lo.re[r] = R(0);
+      lo.im[r] = R(0);
+    }
 
-  // controls two steps ahead in registers
-  R ua = ldu_ro<R>(ub, j0), ub1 = j0 + 1 < j1 ? ldu_ro<R>(ub, j0 + 1) : R(0);
-  for (int j = j0; j < j1; ++j) {
-    const R uj = ua;
-    ua = ub1;
-    if (j + 2 < j1) ub1 = ldu_ro<R>(ub, j + 2);
-    op.set_u(uj, ch, lg);
-    cheb_step<false, COMP>(v, lo, op, ch, Kw, Sw);
+    // controls two steps ahead in registers
+    R ua = ldu_ro<R>(ub, j0), ub1 = j0 + 1 < j1 ? ldu_ro<R>(ub, j0 + 1) : R(0);
+    for (int j = j0; j < j1; ++j) {
+      const R uj = ua;
+      ua = ub1;
+      if (j + 2 < j1) ub1 = ldu_ro<R>(ub, j + 2);
+      op.set_u(uj, ch, lg);
+      cheb_step<false, COMP>(v, lo, op, ch, Kw, Sw);
+    }
   }
   if (col < p.d) {
     count_work<R>(p.count, ch, j1 - j0, lg);
@@ -441,45 +463,96 @@ __global__ void __launch_bounds__(128) k_sweeps2(KParams p) {
     lo.im[r] = COMP ? (R)(z.y - (double)v.im[r]) : R(0);
   }
   R2* tr = reinterpret_cast<R2*>(fwd ? p.traj : p.traj2) + ((long)b * (p.Nt + p.N) + j0 + n) * GE + lg * E;
-  auto put = [&](int slot, const Vec<R, E>& x) {
-    if (valid) {
+  if constexpr (sizeof(R) == 4 && Op::PACKED) {   // packed FP32: both halves per instruction
+    VecP<E> pv, pl;
 #pragma unroll
-      for (int r = 0; r < E; ++r) { R2 z; z.x = x.re[r]; z.y = x.im[r]; tr[(long)slot * GE + r] = z; }
+    for (int r = 0; r < E; ++r) {
+      pv.z[r] = make_float2(v.re[r], v.im[r]);
+      pl.z[r] = make_float2(lo.re[r], lo.im[r]);
     }
-  };
-  if (fwd) {
-    R ua = ldu<R>(ub, j0), ub1 = ns > 1 ? ldu<R>(ub, j0 + 1) : ua;
-    for (int s = 0; s < nsw; ++s) {
-      const bool act = s < ns;
-      const R uj = ua;
-      ua = ub1;
-      if (s + 2 < ns) ub1 = ldu<R>(ub, j0 + s + 2);
+    float2* trp = reinterpret_cast<float2*>(tr);
+    auto putp = [&](int slot, const VecP<E>& x) {
+      if (valid) {
+#pragma unroll
+        for (int r = 0; r < E; ++r) trp[(long)slot * GE + r] = x.z[r];
+      }
+    };
+    if (fwd) {
+      float ua = ldu<float>(ub, j0), ub1 = ns > 1 ? ldu<float>(ub, j0 + 1) : ua;
+      for (int s = 0; s < nsw; ++s) {
+        const bool act = s < ns;
+        const float uj = ua;
+        ua = ub1;
+        if (s + 2 < ns) ub1 = ldu<float>(ub, j0 + s + 2);
+        VecP<E> hv;
+        op.h1_p(pv, hv);
+        if (act) putp(s, hv);
+        VecP<E> w = pv, wl = pl;
+        op.set_u(uj, ch, lg);
+        cheb_step_p<false, true>(w, wl, op, ch, Kw, Sw);
+        if (act) { pv = w; pl = wl; }
+      }
+      VecP<E> hv;
+      op.h1_p(pv, hv);
+      putp(ns, hv);
+    } else {
+      putp(ns, pv);
+      const int top = ns - 1;
+      float ua = ldu<float>(ub, j0 + top), ub1 = ldu<float>(ub, j0 + (top > 0 ? top - 1 : top));
+      for (int s = nsw - 1; s >= 0; --s) {
+        const bool act = s < ns;
+        const float uj = ua;
+        if (act) {
+          ua = ub1;
+          if (s - 2 >= 0) ub1 = ldu<float>(ub, j0 + s - 2);
+        }
+        VecP<E> w = pv, wl = pl;
+        op.set_u(uj, ch, lg);
+        cheb_step_p<true, true>(w, wl, op, ch, Kw, Sw);
+        if (act) { pv = w; pl = wl; putp(s, pv); }
+      }
+    }
+  } else {
+    auto put = [&](int slot, const Vec<R, E>& x) {
+      if (valid) {
+  #pragma unroll
+        for (int r = 0; r < E; ++r) { R2 z; z.x = x.re[r]; z.y = x.im[r]; tr[(long)slot * GE + r] = z; }
+      }
+    };
+    if (fwd) {
+      R ua = ldu<R>(ub, j0), ub1 = ns > 1 ? ldu<R>(ub, j0 + 1) : ua;
+      for (int s = 0; s < nsw; ++s) {
+        const bool act = s < ns;
+        const R uj = ua;
+        ua = ub1;
+        if (s + 2 < ns) ub1 = ldu<R>(ub, j0 + s + 2);
+        Vec<R, E> hv;
+        op.h1(v, hv);
+        if (act) put(s, hv);
+        Vec<R, E> w = v, wl = lo;
+        op.set_u(uj, ch, lg);
+        cheb_step<false, COMP>(w, wl, op, ch, Kw, Sw);
+        if (act) { v = w; lo = wl; }
+      }
       Vec<R, E> hv;
       op.h1(v, hv);
-      if (act) put(s, hv);
-      Vec<R, E> w = v, wl = lo;
-      op.set_u(uj, ch, lg);
-      cheb_step<false, COMP>(w, wl, op, ch, Kw, Sw);
-      if (act) { v = w; lo = wl; }
-    }
-    Vec<R, E> hv;
-    op.h1(v, hv);
-    put(ns, hv);
-  } else {
-    put(ns, v);
-    const int top = ns - 1;
-    R ua = ldu<R>(ub, j0 + top), ub1 = ldu<R>(ub, j0 + (top > 0 ? top - 1 : top));
-    for (int s = nsw - 1; s >= 0; --s) {
-      const bool act = s < ns;
-      const R uj = ua;
-      if (act) {
-        ua = ub1;
-        if (s - 2 >= 0) ub1 = ldu<R>(ub, j0 + s - 2);
+      put(ns, hv);
+    } else {
+      put(ns, v);
+      const int top = ns - 1;
+      R ua = ldu<R>(ub, j0 + top), ub1 = ldu<R>(ub, j0 + (top > 0 ? top - 1 : top));
+      for (int s = nsw - 1; s >= 0; --s) {
+        const bool act = s < ns;
+        const R uj = ua;
+        if (act) {
+          ua = ub1;
+          if (s - 2 >= 0) ub1 = ldu<R>(ub, j0 + s - 2);
+        }
+        Vec<R, E> w = v, wl = lo;
+        op.set_u(uj, ch, lg);
+        cheb_step<true, COMP>(w, wl, op, ch, Kw, Sw);
+        if (act) { v = w; lo = wl; put(s, v); }
       }
-      Vec<R, E> w = v, wl = lo;
-      op.set_u(uj, ch, lg);
-      cheb_step<true, COMP>(w, wl, op, ch, Kw, Sw);
-      if (act) { v = w; lo = wl; put(s, v); }
     }
   }
   if (valid) count_work<R>(p.count, ch, ns, lg);
