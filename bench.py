@@ -36,10 +36,11 @@ METRIC = "ISM gradient iters/s and complex state-steps/s vs plain FP64; p50/p99 
 UNIT = "ISM iterations/s"
 DESCR = {"rotor41": "rigid rotor j<=40, maximise <cos theta>(T)",
          "spin16": "4 spins all-to-all ZZ, X control, |0000> -> |1111>",
-         "ising1024": "10-spin open Ising chain, X control, |0^10> -> |1^10>"}
-SAMPLE_DIV = {"rotor41": 8, "spin16": 1, "ising1024": 64}
-BATCH_DEFAULT = {"rotor41": 64, "spin16": 64, "ising1024": 8}   # independent solves per launch
-SOLVE_ITERS = {"rotor41": 50, "spin16": 20, "ising1024": 20}   # oracle sample = Nt/div steps, N/div sub-intervals
+         "ising1024": "10-spin open Ising chain, X control, |0^10> -> |1^10>",
+         "gp512": "1D Gross-Pitaevskii condensate, 512-point grid, trap centre control, ground -> odd state"}
+SAMPLE_DIV = {"rotor41": 8, "spin16": 1, "ising1024": 64, "gp512": 8}
+BATCH_DEFAULT = {"rotor41": 2048, "spin16": 2048, "ising1024": 8, "gp512": 8}   # independent solves per launch
+SOLVE_ITERS = {"rotor41": 50, "spin16": 20, "ising1024": 20, "gp512": 20}   # oracle sample = Nt/div steps, N/div sub-intervals
 FP32_LANES_PER_SM = 128
 SMS = 152
 SM_MAX_MHZ = 2070.0
@@ -56,6 +57,7 @@ def parse():
     ap.add_argument("--batch", type=int, default=None, help="problems per launch (default: per workload)")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-fp64", action="store_true")
+    ap.add_argument("--no-serving", action="store_true")
     return ap.parse_args()
 
 
@@ -142,22 +144,46 @@ def measured_peaks() -> dict:
         return {"hbm_gbs": 6800.0, "bf16_tflops": 1900.0, "source": "fallback"}
 
 
+def gp_pair_flops(n: int) -> float:
+    """Algorithmic flops of one split step of the grid model: an FFT pair (2 x 5 n log2 n) and two
+    pointwise complex products (2 x 6n)."""
+    return 10.0 * n * np.log2(n) + 12.0 * n
+
+
 def fp32_peak_tflops() -> float:
     return SMS * FP32_LANES_PER_SM * 2 * SM_MAX_MHZ * 1e6 / 1e12
 
 
 # ------------------------------------------------------------------------------ CPU oracle
-def oracle_sample(cfg: str, N_full: int):
-    """One ISM iteration of the oracle on a time-truncated sample of the workload: Nt/8 steps with
-    N/8 sub-intervals (same steps per sub-interval, same d).  Returns (seconds, scale to full)."""
-    import workloads as W
-    from oracle import ism_oracle as O
+_GP_STATES = {}
 
-    full = W.config(cfg, N=N_full)
+
+def load_workload(cfg: str, N=None, Nt=None):
+    """The named synthetic workload (workloads/): the linear configurations or the 512-point grid."""
+    import workloads as W
+
+    if cfg == "gp512":
+        w = W.gp_bec(Nt=Nt or 10000, N=N or 64, states=_GP_STATES.get("gp512"))
+        _GP_STATES["gp512"] = (w.psi_i, w.psi_f)
+        return w
+    return W.config(cfg, N=N, Nt=Nt)
+
+
+def dim_of(w) -> int:
+    return int(w.n) if getattr(w, "kind", "") == "gp" else int(w.d)
+
+
+def oracle_sample(cfg: str, N_full: int):
+    """One ISM iteration of the oracle on a time-truncated sample of the workload: Nt/div steps with
+    N/div sub-intervals (same d and steps per sub-interval).  Returns (seconds, scale to full)."""
+    from oracle import gp_oracle, ism_oracle
+
+    full = load_workload(cfg, N=N_full)
     div = SAMPLE_DIV.get(cfg, 8)
     Nt_s = max(1, full.Nt // div)
     N_s = max(1, full.N // div)
-    w = W.config(cfg, N=N_s, Nt=Nt_s)
+    w = load_workload(cfg, N=N_s, Nt=Nt_s)
+    O = gp_oracle if cfg == "gp512" else ism_oracle
     t0 = time.perf_counter()
     O.ism_iteration(w, w.u0, w.rho, w.local_iters)
     dt = time.perf_counter() - t0
@@ -172,7 +198,7 @@ def run_reference(args):
         return 0
     import workloads as W
 
-    full = W.config(args.config, N=args.N)
+    full = load_workload(args.config, N=args.N)
     times = []
     sample = ""
     scale = 1.0
@@ -194,6 +220,47 @@ def run_reference(args):
     return 0
 
 
+# ------------------------------------------------------------------------------ serving mix
+def serving_mix(P, W, seed: int, n_req: int = 48, rate: float = 200.0, slots: int = 8):
+    """Continuous-batching server (ism_server_*) on a request mix shaped like the serving workload:
+    spin systems of d in {16, 64, 256, 1024} (4 all-to-all spins; open chains of 6, 8, 10 sites),
+    N in {8, 32, 128}, 20 iterations each, mixed precision, Poisson arrivals at `rate`/s; step counts
+    Nt ~ U{1000..5000} (the serving workload draws up to 50000; reduced to bound the run).  Reports
+    requests/s over the makespan and p50/p99 latency, against the same requests run one at a time."""
+    rng = np.random.default_rng(seed)
+    reqs = []
+    for k in range(n_req):
+        d = int(rng.choice([16, 64, 256, 1024]))
+        Nt = int(rng.integers(1000, 5001))
+        N = int(min(rng.choice([8, 32, 128]), Nt))
+        if d == 16:
+            w = W.spin_all_to_all(4, 5000 + k, T=10.0 * Nt / 1000, Nt=Nt, N=N)
+        else:
+            q = int(round(np.log2(d)))
+            w = W.spin_chain(q, 5000 + k, T=2e-4 * Nt * 5, Nt=Nt, N=N)
+        reqs.append(W.with_random_target(w, 6000 + k).with_(rho=0.2))
+    gaps = rng.exponential(1.0 / rate, n_req)
+    with P.Server(slots=slots, hbm_budget_bytes=32 << 30) as srv:
+        for w in reqs[:2]:                      # warm-up: module load, first plans
+            srv.result(srv.submit(w, iters=1, precision="mixed"))
+        t0 = time.perf_counter()
+        ids = []
+        for w, g in zip(reqs, gaps):
+            time.sleep(g)
+            ids.append(srv.submit(w, iters=20, precision="mixed"))
+        lat = [srv.result(i)[2][2] for i in ids]
+        makespan = time.perf_counter() - t0
+    t1 = time.perf_counter()
+    for w in reqs:
+        with P.Plan(w, precision="mixed") as pl:
+            pl.iterate(w.u0, 20)
+    serial = time.perf_counter() - t1
+    return {"requests": n_req, "arrival_rate_per_s": rate, "slots": slots, "iterations": 20,
+            "requests_per_s": n_req / makespan, "latency_p50_ms": float(np.percentile(lat, 50)),
+            "latency_p99_ms": float(np.percentile(lat, 99)), "one_at_a_time_requests_per_s": n_req / serial,
+            "mix": "d in {16,64,256,1024}, Nt ~ U{1000..5000}, N in {8,32,128}, mixed precision"}
+
+
 # ------------------------------------------------------------------------------ our arm
 def run_ours(args):
     import torch
@@ -210,12 +277,14 @@ def run_ours(args):
     import paper_1603_01237_gb300 as P
     import workloads as W
 
-    w = W.config(args.config, N=args.N)
+    w = load_workload(args.config, N=args.N)
+    d = dim_of(w)
     B = args.batch or BATCH_DEFAULT.get(args.config, 1)
     stream = torch.cuda.Stream()
     plan = P.Plan(w, precision="mixed", batch=B, stream=stream)
     rng = np.random.default_rng(2000 + rank)
-    U0 = np.stack([w.u0] + [rng.uniform(-1, 1, w.Nt) for _ in range(B - 1)])
+    amp = float(np.max(np.abs(w.u0)))   # further problems: controls of the same amplitude as u0
+    U0 = np.stack([w.u0] + [rng.uniform(-amp, amp, w.Nt) for _ in range(B - 1)])
     u_dev = torch.tensor(U0, dtype=torch.float64, device="cuda").contiguous()
     flush = torch.empty(512 * 1024 * 1024 // 4, dtype=torch.float32, device="cuda")   # 512 MB > L2
 
@@ -252,29 +321,43 @@ def run_ours(args):
         tot_ms = float(t.item())
     iters_total = B * args.steps * world
     value = iters_total / (tot_ms / 1e3)
-    state_steps = 5 * w.Nt                     # useful state-steps per ISM iteration (2 sweeps + 3 sub-interval)
+    # useful state-steps per ISM iteration: 2 global sweeps + forward, recompute and adjoint per
+    # sub-interval (the grid model stores its forward states: 2 + 2)
+    state_steps = (4 if plan.gp else 5) * w.Nt
 
     # roofline of the dominant phase (largest share of device time); one launch of a phase per iteration
     large = plan.ks_large
-    names = ["k_lsweep", "k_phi", "k_lsub"] if large else ["k_assemble", "k_chain", "k_sweeps2"]
-    kernels = (["k_cheb_prep + k_lsweep", "k_phi", "k_lsub"] if large
-               else ["k_cheb_prep + k_assemble", "k_chain + k_phi", "k_sweeps2 + k_gradpass"])
+    if plan.gp:
+        names = ["k_gp_forward", "k_gp_adjoint", "k_gp_sub"]
+        kernels = names
+    elif large:
+        names = ["k_lsweep", "k_phi", "k_lsub"]
+        kernels = ["k_cheb_prep + k_lsweep", "k_phi", "k_lsub"]
+    else:
+        names = ["k_assemble", "k_chain", "k_sweeps2"]
+        kernels = ["k_cheb_prep + k_assemble", "k_chain + k_phi", "k_sweeps2 + k_gradpass"]
     dom = int(np.argmax(st["ms"]))
     ms_launch = st["ms"][dom] / args.steps
     peaks = measured_peaks()
-    if dom in (0, 2):
-        k = 0 if dom == 0 else 1
-        flops = cheb_flops(plan.kind, w.d, st["y_apps"][k], st["terms"][k], st["substeps"][k]) / args.steps
+    alu_src = "derived: 152 SMs x 128 FP32 lanes x 2 flop x 2070 MHz (no measured FP32 peak)"
+    if plan.gp or dom in (0, 2) or large:
+        if plan.gp:   # FFT pairs counted by the kernels: forward, adjoint, sub-interval
+            pairs = [st["y_apps"][0], st["terms"][0], st["terms"][1]][dom]
+            flops = pairs * gp_pair_flops(d) / args.steps
+        elif dom == 1:   # k_phi
+            flops = 8.0 * B * (w.N + 1) * d
+        else:
+            k = 0 if dom == 0 else 1
+            flops = cheb_flops(plan.kind, d, st["y_apps"][k], st["terms"][k], st["substeps"][k]) / args.steps
         achieved = flops / (ms_launch / 1e3) / 1e12
         peak = fp32_peak_tflops()
         roof = {"kernel": names[dom], "kernels_timed": kernels[dom], "bound": "alu", "achieved": achieved,
                 "peak": peak, "unit": "TFLOP/s", "frac": achieved / peak, "traffic": None,
-                "peak_source": "derived: 152 SMs x 128 FP32 lanes x 2 flop x 2070 MHz (no measured FP32 peak)",
-                "flops_per_launch": flops, "ms_per_launch": ms_launch}
+                "peak_source": alu_src, "flops_per_launch": flops, "ms_per_launch": ms_launch}
     else:
         # algorithmic bytes: every stored propagator tile read once per chain, both staged state chains written
         tile = plan.info(4)
-        nbytes = B * (2 * w.N * tile + 2 * (w.N + 1) * w.d * 8)
+        nbytes = B * (2 * w.N * tile + 2 * (w.N + 1) * d * 8)
         achieved = nbytes / (ms_launch / 1e3) / 1e9
         roof = {"kernel": names[dom], "kernels_timed": kernels[dom], "bound": "hbm", "achieved": achieved,
                 "peak": peaks["hbm_gbs"], "unit": "GB/s", "frac": achieved / peaks["hbm_gbs"], "traffic": None,
@@ -319,7 +402,7 @@ def run_ours(args):
     u1 = torch.tensor(w.u0, dtype=torch.float64, device="cuda").reshape(1, -1).contiguous()
     u1_0 = u1.clone()
     p1.ism_iterate(it_solve, u1, None, None)
-    n_solves = 10 if w.d <= 64 else 2
+    n_solves = 10 if d <= 64 else 2
     sol_ms = []
     with torch.cuda.stream(stream):
         for _ in range(n_solves):
@@ -333,6 +416,8 @@ def run_ours(args):
     p1.close()
     solve = {"batch": 1, "iterations": it_solve, "solves": n_solves, "p50_ms": float(np.percentile(sol_ms, 50)),
              "p99_ms": float(np.percentile(sol_ms, 99)), "ms_per_iteration": float(np.median(sol_ms)) / it_solve}
+
+    serving = None if args.no_serving else serving_mix(P, W, seed=3000 + rank)
 
     cpu = None
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
@@ -349,12 +434,13 @@ def run_ours(args):
         "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": tot_ms / args.steps, "higher_is_better": True, "scaling": "weak",
         "vs_baseline": None, "dtype": "f32 propagation, f64 states/overlaps/update", "data": "synthetic",
-        "config": {"workload": f"{args.config}: {DESCR.get(args.config, args.config)} (d={w.d}), T={w.T:g}, "
-                               f"Nt={w.Nt}, N={w.N}, batch={B} per GPU", "d": w.d, "Nt": w.Nt, "N": w.N, "batch": B,
+        "config": {"workload": f"{args.config}: {DESCR.get(args.config, args.config)} (d={d}), T={w.T:g}, "
+                               f"Nt={w.Nt}, N={w.N}, batch={B} per GPU", "d": d, "Nt": w.Nt, "N": w.N, "batch": B,
                    "precision": "mixed", "l2": "flushed between steps (512 MB write, outside the timed events)"},
         "state_steps_per_s": value * state_steps,
         "step_ms_p50": statistics.median(step_ms), "step_ms_p99": float(np.percentile(step_ms, 99)),
         "solve_latency": solve,
+        "serving": serving,
         "fp64_plain": fp64,
         "phase_share": phase_share,
         "roofline": roof,

@@ -30,6 +30,8 @@
 #ifndef ISM_H_
 #define ISM_H_
 
+#include <stddef.h>
+
 #ifdef __cplusplus
 extern "C" {
 #endif
@@ -109,6 +111,12 @@ typedef struct {
                                   phi_{n+1} - psi_n(t_{n+1}) that FP32 propagation cannot resolve;
                               0 = default: 2 in ISM_MIXED, 1 in ISM_FP64.  Later local steps
                               (L > 1) and ism_subinterval_grad always use the literal form.      */
+  int step1;               /* how Algorithm 1 (a)-(b) obtains psi(t_n), chi(t_n) for d <= 64:
+                              1 = propagator assembly and chain (Sec. 3): d Nt state-steps per
+                                  problem, parallel over sub-intervals -- lowest latency;
+                              2 = direct sweeps: 2 Nt state-steps per problem, sequential in time --
+                                  least work, for many problems per plan;
+                              0 = default: 2 when batch >= 96, else 1.  Larger d always sweeps. */
 } ism_options;
 
 typedef struct ism_plan_s* ism_plan_t;
@@ -171,6 +179,18 @@ int ism_iterate(ism_plan_t plan, int iters, double* u_inout, double* J_hist, dou
  */
 int ism_evaluate(ism_plan_t plan, const double* u, double* J, double* F);
 
+/*
+ * ism_gradient -- gradient of the full objective J[u] at u (Eq. (gradJ) in its discrete trapezoid
+ *   form, penalty included) for every problem of the plan, and J.  By Theorem 2 it is the
+ *   concatenation over n of beta_n times the sub-problem gradients at phi = phi^u; the library
+ *   evaluates it with the two-trajectory form of the theorem's proof (psi from psi(t_n), chi from
+ *   chi(t_{n+1})): one pass of Algorithm 1 (a)-(b) and one parallel sub-interval pass, u unchanged.
+ *   For the grid kind it is the reverse-mode gradient of the discrete split-step map.  This is the
+ *   backward pass of an automatic-differentiation wrapper around ism_evaluate.
+ *   u: [batch][Nt] (host or device); grad: [batch][Nt] output (host or device); J: [batch] or NULL.
+ */
+int ism_gradient(ism_plan_t plan, const double* u, double* grad, double* J);
+
 /* Work and time accounting of a plan, accumulated over calls until reset.
  *   ms[p], launches[p]: device time (CUDA events around each kernel, only while profiling is on)
  *                       and launches of phase p = 0 assembly, 1 chain, 2 sub-interval.
@@ -195,11 +215,17 @@ int ism_set_profiling(ism_plan_t plan, int on);
  *   reset != 0 zeroes it afterwards. */
 int ism_get_stats(ism_plan_t plan, ism_stats* out, int reset);
 
+/* ism_plan_footprint -- device bytes ism_plan would allocate for (prob, opt), without allocating or
+ *   touching a GPU (admission control).  The J/Err history buffers that ism_iterate adds on demand
+ *   (16 bytes x batch x (iters + 1)) are not included.  Same validation and errors as ism_plan. */
+int ism_plan_footprint(const ism_problem* prob, const ism_options* opt, size_t* bytes);
+
 /* ism_plan_info -- integer facts about a plan, for tests and benchmarks:
  *   key 0: group lanes per state, 1: state elements per lane, 2: kernel launches per ISM
  *   iteration (L = local_iters), 3: bytes of plan-owned device memory, 4: bytes of one stored
  *   sub-interval propagator M_n (0 when none is assembled), 5: 1 when the plan propagates the global
- *   trajectories directly (bit-flip d >= 128, one state per CTA) instead of assembling M_n.
+ *   trajectories directly (bit-flip d >= 128, one state per CTA) instead of assembling M_n,
+ *   6: how Algorithm 1 (a)-(b) runs (ism_options.step1 after the default is resolved: 1 or 2).
  *   Returns -1 for a bad key. */
 long long ism_plan_info(ism_plan_t plan, int key);
 
@@ -231,6 +257,48 @@ const char* ism_last_error(void);
 
 /* Library version string. */
 const char* ism_version(void);
+
+/*
+ * Serving loop (no counterpart in the paper, which solves one problem at a time): a server queues
+ * submitted solves -- each its own problem, options, initial controls and iteration count, so the
+ * Hilbert dimensions, step counts and N of concurrent requests may all differ -- and runs them on
+ * `slots` worker threads, one CUDA stream each.  A queued request is admitted, in arrival order, as
+ * soon as a slot is free and its plan's device footprint (ism_plan_footprint plus its history
+ * buffers) fits in the remaining budget; its plan stays resident on the device for the whole solve
+ * and is released when it ends.  Solves of different slots overlap on the GPU, and a request's
+ * result does not depend on the other requests.
+ */
+typedef struct ism_server_s* ism_server_t;
+
+typedef struct {
+  int slots;                 /* concurrent solves (worker threads and CUDA streams), 1..64           */
+  size_t hbm_budget_bytes;   /* device memory the admitted plans may hold together                   */
+} ism_server_options;
+
+enum { ISM_REQ_QUEUED = 0, ISM_REQ_RUNNING = 1, ISM_REQ_DONE = 2, ISM_REQ_FAILED = 3 };
+
+/* ism_server_create -- start the workers on the current CUDA device.  ISM_EINVAL for bad options. */
+int ism_server_create(const ism_server_options* opt, ism_server_t* out);
+
+/* ism_server_submit -- queue a solve: ism_iterate(iters) from u0 ([batch][Nt]) on a plan for (prob,
+ *   opt).  Every array of prob and u0 is copied before the call returns.  *id receives the request
+ *   id.  Errors: those of ism_plan_footprint; ISM_ENOMEM if the request alone exceeds the budget. */
+int ism_server_submit(ism_server_t srv, const ism_problem* prob, const ism_options* opt, const double* u0,
+                      int iters, long long* id);
+
+/* ism_server_poll -- state of a request (ISM_REQ_*); wait != 0 blocks until it is done or failed.
+ *   When done, copies the final controls into u_out ([batch][Nt]) and the objective history into
+ *   J_hist ([batch][iters+1]) if they are non-NULL; times_ms (3 doubles, may be NULL) receives the
+ *   queueing time, the run time and the total latency (-1 while unknown).  Returns the request's
+ *   error status if it failed, ISM_EINVAL for an unknown id. */
+int ism_server_poll(ism_server_t srv, long long id, int wait, int* state, double* u_out, double* J_hist,
+                    double* times_ms);
+
+/* ism_server_release -- forget a finished request (its host copies are freed). */
+int ism_server_release(ism_server_t srv, long long id);
+
+/* ism_server_destroy -- finish the running solves, fail the queued ones, stop the workers. */
+int ism_server_destroy(ism_server_t srv);
 
 #ifdef __cplusplus
 }

@@ -23,7 +23,9 @@ STATUS_NAMES = {0: "ISM_OK", 1: "ISM_EINVAL", 2: "ISM_ENOMEM", 3: "ISM_ECUDA", 4
                 5: "ISM_ETIMEOUT", 6: "ISM_EUNSUPPORTED"}
 
 EXPORTS = ("ism_plan", "ism_plan_destroy", "ism_intermediate_states", "ism_subinterval_grad",
-           "ism_iterate", "ism_evaluate", "ism_set_profiling", "ism_get_stats", "ism_plan_info",
+           "ism_iterate", "ism_evaluate", "ism_gradient", "ism_set_profiling", "ism_get_stats", "ism_plan_info",
+           "ism_plan_footprint", "ism_server_create", "ism_server_submit", "ism_server_poll",
+           "ism_server_release", "ism_server_destroy",
            "ism_subinterval_grad_noalloc", "ism_last_error", "ism_version")
 
 
@@ -35,12 +37,20 @@ class IsmProblem(C.Structure):
 
 class IsmOptions(C.Structure):
     _fields_ = [("precision", C.c_int), ("local_iters", C.c_int), ("rho", C.c_double),
-                ("cheb_tol", C.c_double), ("max_spin_iters", C.c_int), ("subproblem_form", C.c_int)]
+                ("cheb_tol", C.c_double), ("max_spin_iters", C.c_int), ("subproblem_form", C.c_int),
+                ("step1", C.c_int)]
 
 
 class IsmStats(C.Structure):
     _fields_ = [("ms", C.c_double * 3), ("launches", C.c_longlong * 3), ("y_apps", C.c_ulonglong * 2),
                 ("terms", C.c_ulonglong * 2), ("substeps", C.c_ulonglong * 2), ("kernels", C.c_longlong)]
+
+
+class IsmServerOptions(C.Structure):
+    _fields_ = [("slots", C.c_int), ("hbm_budget_bytes", C.c_size_t)]
+
+
+ISM_REQ_QUEUED, ISM_REQ_RUNNING, ISM_REQ_DONE, ISM_REQ_FAILED = 0, 1, 2, 3
 
 
 class IsmError(RuntimeError):
@@ -72,12 +82,27 @@ def load(path: str | None = None):
     lib.ism_iterate.restype = i
     lib.ism_evaluate.argtypes = [vp, vp, vp, vp]
     lib.ism_evaluate.restype = i
+    lib.ism_gradient.argtypes = [vp, vp, vp, vp]
+    lib.ism_gradient.restype = i
     lib.ism_set_profiling.argtypes = [vp, i]
     lib.ism_set_profiling.restype = i
     lib.ism_get_stats.argtypes = [vp, C.POINTER(IsmStats), i]
     lib.ism_get_stats.restype = i
     lib.ism_plan_info.argtypes = [vp, i]
     lib.ism_plan_info.restype = C.c_longlong
+    lib.ism_plan_footprint.argtypes = [C.POINTER(IsmProblem), C.POINTER(IsmOptions), C.POINTER(C.c_size_t)]
+    lib.ism_plan_footprint.restype = i
+    lib.ism_server_create.argtypes = [C.POINTER(IsmServerOptions), C.POINTER(vp)]
+    lib.ism_server_create.restype = i
+    lib.ism_server_submit.argtypes = [vp, C.POINTER(IsmProblem), C.POINTER(IsmOptions), vp, i,
+                                      C.POINTER(C.c_longlong)]
+    lib.ism_server_submit.restype = i
+    lib.ism_server_poll.argtypes = [vp, C.c_longlong, i, C.POINTER(i), vp, vp, vp]
+    lib.ism_server_poll.restype = i
+    lib.ism_server_release.argtypes = [vp, C.c_longlong]
+    lib.ism_server_release.restype = i
+    lib.ism_server_destroy.argtypes = [vp]
+    lib.ism_server_destroy.restype = i
     lib.ism_subinterval_grad_noalloc.argtypes = [C.POINTER(IsmProblem), i, vp, vp, vp, vp, vp]
     lib.ism_subinterval_grad_noalloc.restype = i
     lib.ism_last_error.argtypes = []
@@ -171,12 +196,47 @@ def subinterval_grad_noalloc(w, precision: str, phi, u, grad, Jn=None, *, batch:
                                             _ptr(phi), _ptr(u), _ptr(grad), _ptr(Jn), st))
 
 
+def problem_and_options(w, *, precision=None, batch=1, local_iters=None, rho=None, kind=None, cheb_tol=0.0,
+                        subproblem_form=0, step1=0):
+    """(ism_problem, ism_options, arrays to keep alive) for a workload object."""
+    kind = kind or w.kind
+    gp = kind == "gp"
+    d = int(w.n) if gp else int(w.d)
+    prec = precision or w.precision
+    if gp:   # grid kind: H0 = {L, x_min, g}
+        H0p, H1p = np.array([w.L, w.x_min, w.g], dtype=np.float64), None
+    else:
+        H0p, H1p = pack_hamiltonian(kind, w.H0, w.H1)
+    psi_i = _c128_interleaved(w.psi_i)
+    psi_f = _c128_interleaved(w.psi_f) if w.objective == "overlap" else None
+    O = np.ascontiguousarray(w.O, dtype=np.float64) if w.objective == "observable" else None
+    alpha = None if w.alpha is None else np.ascontiguousarray(w.alpha, dtype=np.float64)
+    keep = [H0p, H1p, psi_i, psi_f, O, alpha]
+    prob = IsmProblem(d=d, kind=_KIND[kind], H0=_ptr(H0p), H1=_ptr(H1p), psi_i=_ptr(psi_i),
+                      objective=ISM_OBJ_OVERLAP if w.objective == "overlap" else ISM_OBJ_OBSERVABLE,
+                      psi_f=_ptr(psi_f), O=_ptr(O), T=float(w.T), Nt=int(w.Nt), N=int(w.N), alpha=_ptr(alpha),
+                      batch=int(batch))
+    opt = IsmOptions(precision=ISM_FP64 if prec == "fp64" else ISM_MIXED,
+                     local_iters=int(local_iters or w.local_iters), rho=float(w.rho if rho is None else rho),
+                     cheb_tol=float(cheb_tol), max_spin_iters=0, subproblem_form=int(subproblem_form),
+                     step1=int(step1))
+    return prob, opt, keep
+
+
+def footprint(w, **kw) -> int:
+    """Device bytes a plan for workload w would allocate (ism_plan_footprint; no GPU needed)."""
+    prob, opt, keep = problem_and_options(w, **kw)
+    n = C.c_size_t()
+    _check(load().ism_plan_footprint(C.byref(prob), C.byref(opt), C.byref(n)))
+    return int(n.value)
+
+
 class Plan:
     """An ism_plan over one workload (any object with the fields of workloads.Workload)."""
 
     def __init__(self, w, *, precision: str | None = None, batch: int = 1, stream=None,
                  local_iters: int | None = None, rho: float | None = None, kind: str | None = None,
-                 cheb_tol: float = 0.0, subproblem_form: int = 0):
+                 cheb_tol: float = 0.0, subproblem_form: int = 0, step1: int = 0):
         lib = load()
         self.w = w
         self.kind = kind or w.kind
@@ -184,24 +244,10 @@ class Plan:
         self.gp = self.kind == "gp"
         self.d = int(w.n) if self.gp else int(w.d)
         self.Nt, self.N = int(w.Nt), int(w.N)
-        prec = precision or w.precision
-        self.precision = prec
-        if self.gp:   # grid kind: H0 = {L, x_min, g}
-            H0p, H1p = np.array([w.L, w.x_min, w.g], dtype=np.float64), None
-        else:
-            H0p, H1p = pack_hamiltonian(self.kind, w.H0, w.H1)
-        self._keep = [H0p, H1p, _c128_interleaved(w.psi_i)]
-        psi_f = _c128_interleaved(w.psi_f) if w.objective == "overlap" else None
-        O = np.ascontiguousarray(w.O, dtype=np.float64) if w.objective == "observable" else None
-        alpha = None if w.alpha is None else np.ascontiguousarray(w.alpha, dtype=np.float64)
-        self._keep += [psi_f, O, alpha]
-        prob = IsmProblem(d=self.d, kind=_KIND[self.kind], H0=_ptr(H0p), H1=_ptr(H1p), psi_i=_ptr(self._keep[2]),
-                          objective=ISM_OBJ_OVERLAP if w.objective == "overlap" else ISM_OBJ_OBSERVABLE,
-                          psi_f=_ptr(psi_f), O=_ptr(O), T=float(w.T), Nt=self.Nt, N=self.N, alpha=_ptr(alpha),
-                          batch=self.batch)
-        opt = IsmOptions(precision=ISM_FP64 if prec == "fp64" else ISM_MIXED,
-                         local_iters=int(local_iters or w.local_iters), rho=float(w.rho if rho is None else rho),
-                         cheb_tol=float(cheb_tol), max_spin_iters=0, subproblem_form=int(subproblem_form))
+        self.precision = precision or w.precision
+        prob, opt, self._keep = problem_and_options(w, precision=precision, batch=batch, local_iters=local_iters,
+                                                    rho=rho, kind=kind, cheb_tol=cheb_tol,
+                                                    subproblem_form=subproblem_form, step1=step1)
         h = C.c_void_p()
         st = None
         if stream is not None:
@@ -221,6 +267,9 @@ class Plan:
 
     def ism_evaluate(self, u, J=None, F=None):
         _check(load().ism_evaluate(self.handle, _ptr(u), _ptr(J), _ptr(F)))
+
+    def ism_gradient(self, u, grad, J=None):
+        _check(load().ism_gradient(self.handle, _ptr(u), _ptr(grad), _ptr(J)))
 
     def ism_set_profiling(self, on: bool):
         _check(load().ism_set_profiling(self.handle, int(bool(on))))
@@ -273,6 +322,13 @@ class Plan:
         self.ism_evaluate(self._u(u), J, F)
         return J, F
 
+    def gradient(self, u):
+        """(dJ/du (batch, Nt), J (batch,)) at u."""
+        grad = np.empty((self.batch, self.Nt))
+        J = np.empty(self.batch)
+        self.ism_gradient(self._u(u), grad, J)
+        return grad, J
+
     def close(self):
         if getattr(self, "handle", None) is not None and self.handle.value:
             load().ism_plan_destroy(self.handle)
@@ -289,3 +345,62 @@ class Plan:
 
     def __exit__(self, *a):
         self.close()
+
+
+class Server:
+    """Serving loop of the C ABI (ism_server_*): concurrent solves of different problems on one GPU,
+    admitted by device footprint.  submit() returns a request id; result() waits for it."""
+
+    def __init__(self, slots: int = 4, hbm_budget_bytes: int = 16 << 30):
+        self.handle = C.c_void_p()
+        opt = IsmServerOptions(slots=int(slots), hbm_budget_bytes=int(hbm_budget_bytes))
+        rc = load().ism_server_create(C.byref(opt), C.byref(self.handle))
+        if rc != ISM_OK:
+            raise IsmError(rc, "ism_server_create")
+        self._shape = {}
+
+    def submit(self, w, u0=None, iters=None, batch: int = 1, **plan_kw) -> int:
+        prob, opt, keep = problem_and_options(w, batch=batch, **plan_kw)
+        Nt = int(w.Nt)
+        u = np.ascontiguousarray(np.broadcast_to(np.asarray(w.u0 if u0 is None else u0, dtype=np.float64),
+                                                 (batch, Nt))).copy()
+        it = int(w.iters if iters is None else iters)
+        rid = C.c_longlong()
+        _check(load().ism_server_submit(self.handle, C.byref(prob), C.byref(opt), _ptr(u), it, C.byref(rid)))
+        self._shape[rid.value] = (batch, Nt, it)
+        return rid.value
+
+    def poll(self, rid: int, wait: bool = False):
+        """(state, u (batch, Nt) or None, J_hist (batch, iters+1) or None, times_ms (3,))."""
+        B, Nt, it = self._shape[rid]
+        st = C.c_int()
+        u = np.empty((B, Nt))
+        J = np.empty((B, it + 1))
+        t = np.empty(3)
+        _check(load().ism_server_poll(self.handle, C.c_longlong(rid), int(bool(wait)), C.byref(st), _ptr(u), _ptr(J),
+                                      _ptr(t)))
+        done = st.value == ISM_REQ_DONE
+        return st.value, (u if done else None), (J if done else None), t
+
+    def result(self, rid: int):
+        st, u, J, t = self.poll(rid, wait=True)
+        load().ism_server_release(self.handle, C.c_longlong(rid))
+        self._shape.pop(rid, None)
+        return u, J, t
+
+    def close(self):
+        if getattr(self, "handle", None) is not None and self.handle.value:
+            load().ism_server_destroy(self.handle)
+            self.handle = C.c_void_p()
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *exc):
+        self.close()
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass

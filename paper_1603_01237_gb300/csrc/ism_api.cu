@@ -123,6 +123,8 @@ struct ism_plan_s {
   int chain_stages = 2;
   size_t bytes = 0;
   std::vector<void*> allocs;
+  bool dry = false;   // plan_build for the footprint only: nothing is allocated or uploaded
+  bool direct = false;   // d <= 64: global trajectories by direct sweeps instead of assembly + chain
 };
 
 namespace {
@@ -132,20 +134,27 @@ int dalloc(ism_plan_s* P, T** out, size_t count) {
   void* p = nullptr;
   size_t bytes = count * sizeof(T);
   if (bytes == 0) bytes = 16;
-  cudaError_t e = cudaMalloc(&p, bytes);
+  if (P->dry) {   // footprint only: count what would be allocated (cudaMalloc granularity)
+    P->bytes += (bytes + 511) / 512 * 512;
+    *out = nullptr;
+    return ISM_OK;
+  }
+  // stream-ordered: allocation and release do not synchronise the device, so plans created and
+  // destroyed while other plans' kernels run (a serving loop) do not stall them
+  cudaError_t e = cudaMallocAsync(&p, bytes, P->st);
   if (e != cudaSuccess) {
     cudaGetLastError();
     return fail(e == cudaErrorMemoryAllocation ? ISM_ENOMEM : ISM_ECUDA,
                 std::string("cudaMalloc of ") + std::to_string(bytes) + " bytes: " + cudaGetErrorString(e));
   }
   P->allocs.push_back(p);
-  P->bytes += bytes;
+  P->bytes += (bytes + 511) / 512 * 512;   // the same count as the footprint
   *out = reinterpret_cast<T*>(p);
   return ISM_OK;
 }
 
 void free_all(ism_plan_s* P) {
-  for (void* p : P->allocs) cudaFree(p);
+  for (void* p : P->allocs) cudaFreeAsync(p, P->st);
   P->allocs.clear();
   for (auto& e : P->pending) { cudaEventDestroy(e.a); cudaEventDestroy(e.b); }
   P->pending.clear();
@@ -333,7 +342,8 @@ int finish(ism_plan_s* P) {
   if (e != cudaSuccess) return fail(ISM_ECUDA, std::string("stream: ") + cudaGetErrorString(e));
   collect_events(P);
   int st = 0;
-  ISM_CUDA_TRY(cudaMemcpy(&st, P->dstatus, sizeof(int), cudaMemcpyDeviceToHost));
+  ISM_CUDA_TRY(cudaMemcpyAsync(&st, P->dstatus, sizeof(int), cudaMemcpyDeviceToHost, P->st));
+  ISM_CUDA_TRY(cudaStreamSynchronize(P->st));
   if (st & ism::ST_TIMEOUT) return fail(ISM_ETIMEOUT, "a bounded device-side wait gave up");
   if (st & ism::ST_KOVERFLOW) return fail(ISM_EUNSUPPORTED, "Chebyshev series needed more terms than compiled");
   if (st & ism::ST_NONFINITE) return fail(ISM_ENONFINITE, "non-finite value in a control or a result");
@@ -388,10 +398,11 @@ int run_states(ism_plan_s* P, const double* u, double* Jhist, int hist_stride, i
     return ISM_OK;
   }
   ism::KParams k = kparams(P, const_cast<double*>(u));
-  if (P->ks.large) {   // direct sweeps: psi(t_n), chi(t_n) in FP64
+  if (P->ks.large || P->direct) {   // direct sweeps: psi(t_n), chi(t_n) in FP64
+    ism::LaunchFn sweep = P->ks.large ? P->ks.lsweep : P->ks.gsweep;
     ISM_CUDA_TRY(timed(P, 0, 2, [&] {
       cudaError_t e = ism::launch_cheb_prep(P->prec, k, P->st);
-      return e != cudaSuccess ? e : P->ks.lsweep(k, P->st);
+      return e != cudaSuccess ? e : sweep(k, P->st);
     }));
   } else {
     ISM_CUDA_TRY(timed(P, 0, 2, [&] {
@@ -406,7 +417,7 @@ int run_states(ism_plan_s* P, const double* u, double* Jhist, int hist_stride, i
   c.pen = P->dalpha ? P->dpen : nullptr; c.psin = P->dpsin; c.chin = P->dchin; c.phi = P->dphi;
   c.J = P->dJ; c.F = P->dF; c.Jhist = Jhist; c.hist_stride = hist_stride; c.hist_k = hist_k;
   c.status = P->dstatus; c.max_spin = P->max_spin; c.stages = P->chain_stages; c.tile_stride = P->tst;
-  if (P->ks.large) {
+  if (P->ks.large || P->direct) {
     c.src64 = 1;
     ISM_CUDA_TRY(timed(P, 1, 1, [&] { return ism::launch_phi(P->prec, c, P->st); }));
   } else {
@@ -460,8 +471,14 @@ const char* ism_last_error(void) { return g_err.c_str(); }
 
 const char* ism_version(void) { return "ism-gb300 0.1 (sm_103a)"; }
 
-int ism_plan(const ism_problem* prob, const ism_options* opt, void* cuda_stream, ism_plan_t* out) {
-  if (!prob || !opt || !out) return fail(ISM_EINVAL, "null problem, options or output handle");
+}  // extern "C"
+
+namespace {
+
+// Validate, size and (unless dry) allocate and upload a plan.  dry: only *bytes is produced.
+int plan_build(const ism_problem* prob, const ism_options* opt, void* cuda_stream, ism_plan_t* out, bool dry,
+               size_t* bytes_out) {
+  if (!prob || !opt || (!out && !dry)) return fail(ISM_EINVAL, "null problem, options or output handle");
   const ism_problem& p = *prob;
   const int d = p.d;
   {
@@ -472,9 +489,11 @@ int ism_plan(const ism_problem* prob, const ism_options* opt, void* cuda_stream,
   if (!(opt->rho >= 0.0) || !std::isfinite(opt->rho)) return fail(ISM_EINVAL, "rho must be finite and >= 0");
   if (opt->cheb_tol < 0.0) return fail(ISM_EINVAL, "cheb_tol must be >= 0");
   if (opt->subproblem_form < 0 || opt->subproblem_form > 2) return fail(ISM_EINVAL, "subproblem_form must be 0, 1 or 2");
+  if (opt->step1 < 0 || opt->step1 > 2) return fail(ISM_EINVAL, "step1 must be 0, 1 or 2");
 
   ism_plan_s* P = new (std::nothrow) ism_plan_s();
   if (!P) return fail(ISM_ENOMEM, "host allocation");
+  P->dry = dry;
   P->d = d; P->kind = p.kind; P->obj = p.objective; P->Nt = p.Nt; P->N = p.N; P->B = p.batch < 1 ? 1 : p.batch;
   P->prec = opt->precision; P->L = opt->local_iters < 1 ? 1 : opt->local_iters;
   P->T = p.T; P->tau = p.T / p.Nt; P->rho = opt->rho;
@@ -513,11 +532,17 @@ int ism_plan(const ism_problem* prob, const ism_options* opt, void* cuda_stream,
     TRY_GP(P->dstatus, 1);
     TRY_GP(P->dcount, 6);
 #undef TRY_GP
-    cudaError_t e = cudaMemcpy(P->djn, jn.data(), jn.size() * sizeof(int), cudaMemcpyHostToDevice);
-    if (e == cudaSuccess) e = cudaMemcpy(P->dpsi_i, p.psi_i, 2 * sizeof(double) * d, cudaMemcpyHostToDevice);
-    if (e == cudaSuccess) e = cudaMemcpy(P->dpsi_f, p.psi_f, 2 * sizeof(double) * d, cudaMemcpyHostToDevice);
-    if (e == cudaSuccess) e = cudaMemset(P->dstatus, 0, sizeof(int));
-    if (e == cudaSuccess) e = cudaMemset(P->dcount, 0, 6 * sizeof(unsigned long long));
+    if (dry) {
+      *bytes_out = P->bytes;
+      delete P;
+      return ISM_OK;
+    }
+    cudaError_t e = cudaMemcpyAsync(P->djn, jn.data(), jn.size() * sizeof(int), cudaMemcpyHostToDevice, P->st);
+    if (e == cudaSuccess) e = cudaMemcpyAsync(P->dpsi_i, p.psi_i, 2 * sizeof(double) * d, cudaMemcpyHostToDevice, P->st);
+    if (e == cudaSuccess) e = cudaMemcpyAsync(P->dpsi_f, p.psi_f, 2 * sizeof(double) * d, cudaMemcpyHostToDevice, P->st);
+    if (e == cudaSuccess) e = cudaMemsetAsync(P->dstatus, 0, sizeof(int), P->st);
+    if (e == cudaSuccess) e = cudaMemsetAsync(P->dcount, 0, 6 * sizeof(unsigned long long), P->st);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(P->st);   // the host arrays above are local
     if (e != cudaSuccess) {
       free_all(P);
       delete P;
@@ -535,6 +560,7 @@ int ism_plan(const ism_problem* prob, const ism_options* opt, void* cuda_stream,
   }
   bool ok = ism::select_kernels(P->prec, p.kind, d, &P->ks, h1diag);
   if (!ok) { delete P; return fail(ISM_EUNSUPPORTED, "no compiled kernel for this kind and d"); }
+  P->direct = !P->ks.large && (opt->step1 == 2 || (opt->step1 == 0 && P->B >= 96));
   const int gpw = P->ks.large ? 1 : 32 / P->ks.GA;
   P->dpad = (d + gpw - 1) / gpw * gpw;
   P->ldm = d | 1;                                   // odd column stride
@@ -569,14 +595,14 @@ int ism_plan(const ism_problem* prob, const ism_options* opt, void* cuda_stream,
   TRY_ALLOC(P->dbeta, (size_t)P->N);
   TRY_ALLOC(P->dab, (size_t)P->N + 1);
   TRY_ALLOC(P->dcheb, B * P->N * ism::cheb_bytes(P->prec));
-  if (!P->ks.large) TRY_ALLOC(P->dstage, B * 2 * ((size_t)P->N + 1) * d * P->r2);
+  if (!P->ks.large && !P->direct) TRY_ALLOC(P->dstage, B * 2 * ((size_t)P->N + 1) * d * P->r2);
   TRY_ALLOC(P->dpen, B * P->N);
   TRY_ALLOC(P->dctab, (size_t)ism::BESSEL_TABLE);
   if (p.alpha) TRY_ALLOC(P->dalpha, (size_t)P->Nt);
   TRY_ALLOC(P->dpsi_i, (size_t)d);
   TRY_ALLOC(P->dpsi_f, (size_t)d);
   if (p.objective == ISM_OBJ_OBSERVABLE) TRY_ALLOC(P->dO, (size_t)d * d);
-  if (!P->ks.large) {   // sub-interval propagators M_n (assembly + chain)
+  if (!P->ks.large && !P->direct) {   // sub-interval propagators M_n (assembly + chain)
     unsigned char* dMb = nullptr;
     TRY_ALLOC(dMb, B * P->N * (size_t)P->tst * P->r2);
     P->dM = dMb;
@@ -605,10 +631,15 @@ int ism_plan(const ism_problem* prob, const ism_options* opt, void* cuda_stream,
   TRY_ALLOC(P->dstatus, 1);
   TRY_ALLOC(P->dcount, 6);
 #undef TRY_ALLOC
+  if (dry) {
+    *bytes_out = P->bytes;
+    delete P;
+    return ISM_OK;
+  }
 
   cudaError_t e = cudaSuccess;
   auto h2d = [&](void* dst, const void* src, size_t n) {
-    if (e == cudaSuccess) e = cudaMemcpy(dst, src, n, cudaMemcpyHostToDevice);
+    if (e == cudaSuccess) e = cudaMemcpyAsync(dst, src, n, cudaMemcpyHostToDevice, P->st);
   };
   h2d(P->dH, P->prec == ISM_FP64 ? (const void*)hd.data() : (const void*)hf.data(), hbytes);
   {
@@ -634,10 +665,11 @@ int ism_plan(const ism_problem* prob, const ism_options* opt, void* cuda_stream,
   if (p.alpha) h2d(P->dalpha, p.alpha, P->Nt * sizeof(double));
   h2d(P->dpsi_i, p.psi_i, 2 * sizeof(double) * d);
   if (p.objective == ISM_OBJ_OVERLAP) h2d(P->dpsi_f, p.psi_f, 2 * sizeof(double) * d);
-  else if (e == cudaSuccess) e = cudaMemset(P->dpsi_f, 0, 2 * sizeof(double) * d);
+  else if (e == cudaSuccess) e = cudaMemsetAsync(P->dpsi_f, 0, 2 * sizeof(double) * d, P->st);
   if (p.objective == ISM_OBJ_OBSERVABLE) h2d(P->dO, p.O, sizeof(double) * d * d);
-  if (e == cudaSuccess) e = cudaMemset(P->dstatus, 0, sizeof(int));
-  if (e == cudaSuccess) e = cudaMemset(P->dcount, 0, 6 * sizeof(unsigned long long));
+  if (e == cudaSuccess) e = cudaMemsetAsync(P->dstatus, 0, sizeof(int), P->st);
+  if (e == cudaSuccess) e = cudaMemsetAsync(P->dcount, 0, 6 * sizeof(unsigned long long), P->st);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(P->st);   // the host arrays uploaded above are local
   if (e != cudaSuccess) {
     free_all(P);
     delete P;
@@ -653,6 +685,22 @@ int ism_plan(const ism_problem* prob, const ism_options* opt, void* cuda_stream,
   *out = P;
   g_err.clear();
   return ISM_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
+int ism_plan(const ism_problem* prob, const ism_options* opt, void* cuda_stream, ism_plan_t* out) {
+  return plan_build(prob, opt, cuda_stream, out, false, nullptr);
+}
+
+int ism_plan_footprint(const ism_problem* prob, const ism_options* opt, size_t* bytes) {
+  if (!bytes) return fail(ISM_EINVAL, "null output");
+  *bytes = 0;
+  int rc = plan_build(prob, opt, nullptr, nullptr, true, bytes);
+  if (rc == ISM_OK) g_err.clear();
+  return rc;
 }
 
 int ism_plan_destroy(ism_plan_t P) {
@@ -671,8 +719,9 @@ long long ism_plan_info(ism_plan_t P, int key) {
     case 1: return P->ks.E;
     case 2: return 2 + P->L;
     case 3: return (long long)P->bytes;
-    case 4: return (P->gp || P->ks.large) ? 0 : (long long)(P->tst * P->r2);
+    case 4: return (P->gp || P->ks.large || P->direct) ? 0 : (long long)(P->tst * P->r2);
     case 5: return P->ks.large ? 1 : 0;
+    case 6: return (P->ks.large || P->direct) ? 2 : 1;
     default: return -1;
   }
 }
@@ -816,6 +865,32 @@ int ism_iterate(ism_plan_t P, int iters, double* u_inout, double* J_hist, double
   if ((rc = finish(P))) return rc;
   if (!dev_u && !all_finite(u_inout, nu)) return fail(ISM_ENONFINITE, "controls became non-finite");
   return ISM_OK;
+}
+
+int ism_gradient(ism_plan_t P, const double* u, double* grad, double* J) {
+  if (!P || !u || !grad) return fail(ISM_EINVAL, "null argument");
+  int rc = begin(P);
+  if (rc) return rc;
+  const double* ud = nullptr;
+  if ((rc = stage_in(P, u, (long)P->B * P->Nt, P->du, &ud, true))) return rc;
+  if ((rc = run_states(P, ud, nullptr, 0, 0))) return rc;
+  if (P->gp) {   // the sub-problem gradients at the adjoint targets are the global gradient
+    ism::GPParams g = gparams(P, const_cast<double*>(ud));
+    g.update = 0;
+    g.count = P->dcount + 3;
+    ISM_CUDA_TRY(timed(P, 2, 1, [&] { return ism::launch_gp_sub(P->prec, g, P->st); }));
+  } else {       // Theorem 2 two-trajectory form, scaled by beta_n
+    ism::KParams k = kparams(P, const_cast<double*>(ud));
+    k.update = 0;
+    k.form = 1;
+    k.global = 1;
+    k.count = P->dcount + 3;
+    if (P->ks.large) ISM_CUDA_TRY(timed(P, 2, 1, [&] { return P->ks.subinterval(k, P->st); }));
+    else ISM_CUDA_TRY(timed(P, 2, 2, [&] { return P->ks.sweeps2(k, P->st); }));
+  }
+  if ((rc = copy_out(P, grad, P->dgrad, (long)P->B * P->Nt))) return rc;
+  if ((rc = copy_out(P, J, P->dJ, P->B))) return rc;
+  return finish(P);
 }
 
 int ism_evaluate(ism_plan_t P, const double* u, double* J, double* F) {

@@ -36,6 +36,14 @@ template <typename T> __device__ __forceinline__ T cmul(T a, T b) {
 template <typename T> __device__ __forceinline__ T cadd(T a, T b) { T c; c.x = a.x + b.x; c.y = a.y + b.y; return c; }
 template <typename T> __device__ __forceinline__ T csub(T a, T b) { T c; c.x = a.x - b.x; c.y = a.y - b.y; return c; }
 template <typename T> __device__ __forceinline__ T cconj(T a) { a.y = -a.y; return a; }
+// a * (bh + bl) for a factor b held as hi + lo: every transform applies the same rounded twiddles and
+// kinetic factors at every step, so their FP32 rounding would add up over the steps like a bias.
+template <typename T> __device__ __forceinline__ T cmul_hl(T a, T bh, T bl) {
+  T c;
+  c.x = fma(a.x, bh.x, fma(-a.y, bh.y, fma(a.x, bl.x, -a.y * bl.y)));
+  c.y = fma(a.x, bh.y, fma(a.y, bh.x, fma(a.x, bl.y, a.y * bl.x)));
+  return c;
+}
 
 __device__ __forceinline__ void sc(float x, float& s, float& c) { sincosf(x, &s, &c); }
 __device__ __forceinline__ void sc(double x, double& s, double& c) { sincos(x, &s, &c); }
@@ -70,14 +78,16 @@ __device__ __forceinline__ void dft4(T& a0, T& a1, T& a2, T& a3) {
 template <typename R, bool INV>
 __device__ __forceinline__ void dft8(typename C2<R>::T* v) {
   using T = typename C2<R>::T;
-  const R h = (R)0.70710678118654752440;
+  constexpr double hd = 0.70710678118654752440;
+  const R h = (R)hd, hl = (R)(hd - (double)(R)hd);   // 1/sqrt(2) as hi + lo (lo = 0 in FP64)
   T a[4], b[4];
 #pragma unroll
   for (int r = 0; r < 4; ++r) { a[r] = cadd(v[r], v[r + 4]); b[r] = csub(v[r], v[r + 4]); }
   {   // w^1 = (1 -+ i)/sqrt(2)
     const T t = b[1];
-    if (!INV) { b[1].x = h * (t.x + t.y); b[1].y = h * (t.y - t.x); }
-    else { b[1].x = h * (t.x - t.y); b[1].y = h * (t.y + t.x); }
+    const R p = t.x + t.y, m = t.y - t.x, q = t.x - t.y;
+    if (!INV) { b[1].x = fma(h, p, hl * p); b[1].y = fma(h, m, hl * m); }
+    else { b[1].x = fma(h, q, hl * q); b[1].y = fma(h, p, hl * p); }
   }
   {   // w^2 = -+ i
     const T t = b[2];
@@ -85,8 +95,9 @@ __device__ __forceinline__ void dft8(typename C2<R>::T* v) {
   }
   {   // w^3 = (-1 -+ i)/sqrt(2)
     const T t = b[3];
-    if (!INV) { b[3].x = h * (t.y - t.x); b[3].y = -h * (t.x + t.y); }
-    else { b[3].x = -h * (t.x + t.y); b[3].y = h * (t.x - t.y); }
+    const R p = t.x + t.y, m = t.y - t.x, q = t.x - t.y;
+    if (!INV) { b[3].x = fma(h, m, hl * m); b[3].y = -fma(h, p, hl * p); }
+    else { b[3].x = -fma(h, p, hl * p); b[3].y = fma(h, q, hl * q); }
   }
   dft4<T, INV>(a[0], a[1], a[2], a[3]);
   dft4<T, INV>(b[0], b[1], b[2], b[3]);
@@ -94,11 +105,20 @@ __device__ __forceinline__ void dft8(typename C2<R>::T* v) {
   for (int m = 0; m < 4; ++m) { v[2 * m] = a[m]; v[2 * m + 1] = b[m]; }
 }
 
+struct Ident {
+  template <class T> __device__ __forceinline__ T operator()(int, T v) const { return v; }
+};
+
 // Stockham radix-8 FFT (unnormalised) of length n = 8^P from x, using y as the other buffer; twiddle
-// table W[m] = exp(-2 pi i m / n).  Every thread of the block calls it; threads t < n/8 compute.
+// table W[m] + Wl[m] = exp(-2 pi i m / n) (hi + lo).  Every thread of the block calls it; threads
+// t < n/8 compute.
+// pre(m, v) is applied to every input element as the first pass loads it, post(m, v) to every output
+// element as the last pass stores it, so pointwise factors cost no pass and no barrier of their own.
 // Returns the buffer that holds the result.
-template <typename R, bool INV>
-__device__ typename C2<R>::T* fft8(typename C2<R>::T* x, typename C2<R>::T* y, const typename C2<R>::T* W, int n) {
+template <typename R, bool INV, class Pre = Ident, class Post = Ident>
+__device__ typename C2<R>::T* fft8(typename C2<R>::T* x, typename C2<R>::T* y, const typename C2<R>::T* W,
+                                   const typename C2<R>::T* Wl, int n, const Pre& pre = Pre(),
+                                   const Post& post = Post()) {
   using T = typename C2<R>::T;
   const int t = threadIdx.x, q = n >> 3;
   for (int Ns = 1; Ns < n; Ns <<= 3) {
@@ -106,18 +126,26 @@ __device__ typename C2<R>::T* fft8(typename C2<R>::T* x, typename C2<R>::T* y, c
       const int k = t % Ns;
       T v[8];
 #pragma unroll
-      for (int r = 0; r < 8; ++r) v[r] = x[t + r * q];
+      for (int r = 0; r < 8; ++r) {
+        const int m = t + r * q;
+        v[r] = Ns == 1 ? pre(m, x[m]) : x[m];
+      }
       const int step = n / (Ns << 3);
 #pragma unroll
       for (int r = 1; r < 8; ++r) {
-        T w = W[(k * r * step) & (n - 1)];
-        if (INV) w = cconj(w);
-        v[r] = cmul(v[r], w);
+        const int i = (k * r * step) & (n - 1);
+        T w = W[i], wl = Wl[i];
+        if (INV) { w = cconj(w); wl = cconj(wl); }
+        v[r] = cmul_hl(v[r], w, wl);
       }
       dft8<R, INV>(v);
       const int base = (t / Ns) * (Ns << 3) + k;
+      const bool last = (Ns << 3) == n;
 #pragma unroll
-      for (int r = 0; r < 8; ++r) y[base + r * Ns] = v[r];
+      for (int r = 0; r < 8; ++r) {
+        const int m = base + r * Ns;
+        y[m] = last ? post(m, v[r]) : v[r];
+      }
     }
     __syncthreads();
     T* tmp = x;
@@ -131,7 +159,8 @@ template <typename R>
 struct GP {
   using T = typename C2<R>::T;
   T *A, *B, *C, *W, *D2m1, *DH;   // state, scratch, spare, twiddles, exp(-i tau k^2/2)-1, exp(-i tau k^2/4)
-  R* X;                           // grid points x_m (FP64 -> R)
+  T *Wl, *D2l, *DHl;              // low parts of the three tables (zero in FP64)
+  R *X, *Xl;                      // grid points x_m as hi + lo
   int n;
   double dx, tau, g, xmin;
   double* red;
@@ -145,7 +174,11 @@ struct GP {
     W = base + 3 * n;
     D2m1 = base + 4 * n;
     DH = base + 5 * n;
-    X = reinterpret_cast<R*>(base + 6 * n);
+    Wl = base + 6 * n;
+    D2l = base + 7 * n;
+    DHl = base + 8 * n;
+    X = reinterpret_cast<R*>(base + 9 * n);
+    Xl = X + n;
     dx = p.dx;
     tau = p.tau;
     g = p.g;
@@ -154,68 +187,81 @@ struct GP {
     for (int m = threadIdx.x; m < n; m += blockDim.x) {
       double s, co;
       sincospi(-2.0 * (double)m / (double)n, &s, &co);
-      T w;
+      T w, wl;
       w.x = (R)co;
       w.y = (R)s;
+      wl.x = (R)(co - (double)w.x);
+      wl.y = (R)(s - (double)w.y);
       W[m] = w;
+      Wl[m] = wl;
       const int kk = m < n / 2 ? m : m - n;   // frequency ordering of an unshifted FFT
       const double k = 2.0 * M_PI * (double)kk / p.L;
       const double ph2 = -0.5 * tau * k * k, ph4 = -0.25 * tau * k * k;
       const double h = sin(0.5 * ph2);
-      T d;
-      d.x = (R)(-2.0 * h * h);
-      d.y = (R)sin(ph2);
+      T d, dl;
+      const double dx_ = -2.0 * h * h, dy_ = sin(ph2);
+      d.x = (R)dx_;
+      d.y = (R)dy_;
+      dl.x = (R)(dx_ - (double)d.x);
+      dl.y = (R)(dy_ - (double)d.y);
       D2m1[m] = d;
+      D2l[m] = dl;
       double s4, c4;
       sincos(ph4, &s4, &c4);
-      T e;
+      T e, el;
       e.x = (R)c4;
       e.y = (R)s4;
+      el.x = (R)(c4 - (double)e.x);
+      el.y = (R)(s4 - (double)e.y);
       DH[m] = e;
-      X[m] = (R)(p.xmin + m * p.dx);
+      DHl[m] = el;
+      const double xm = p.xmin + m * p.dx;
+      X[m] = (R)xm;
+      Xl[m] = (R)(xm - (double)X[m]);
     }
     __syncthreads();
   }
 
-  // buf <- F^-1 diag(f) F buf (f = full-step factor, or half-step; conjugated for the adjoint).
-  // buf is A or C; B is the scratch of every transform.
-  template <bool ADJ, bool FULL>
-  __device__ void kinetic(T* buf) {
-    T* X = fft8<R, false>(buf, B, W, n);
-    for (int m = threadIdx.x; m < n; m += blockDim.x) {
-      T v = X[m];
-      T f = FULL ? D2m1[m] : DH[m];
-      if (ADJ) f = cconj(f);
-      v = FULL ? cadd(v, cmul(f, v)) : cmul(f, v);
-      X[m] = v;
-    }
-    __syncthreads();
+  // buf <- F^-1 diag(f) F pre(buf) (f = full-step factor, or half-step; conjugated for the adjoint).
+  // buf is A or C; B is the scratch of every transform.  The forward transform applies pre on load
+  // and f on store, the inverse the 1/n normalisation on store; with 2 log_8(n) passes in all (an
+  // even number) the result lands back in buf.
+  template <bool ADJ, bool FULL, class Pre = Ident>
+  __device__ void kinetic(T* buf, const Pre& pre = Pre()) {
+    const T* fh = FULL ? D2m1 : DH;
+    const T* fl = FULL ? D2l : DHl;
+    auto factor = [fh, fl](int m, T v) {
+      T f = fh[m], g = fl[m];
+      if (ADJ) { f = cconj(f); g = cconj(g); }
+      return FULL ? cadd(v, cmul_hl(v, f, g)) : cmul_hl(v, f, g);
+    };
+    T* X = fft8<R, false>(buf, B, W, Wl, n, pre, factor);
     T* other = (X == buf) ? B : buf;
-    T* Y = fft8<R, true>(X, other, W, n);
     const R inv_n = (R)(1.0 / (double)n);
-    for (int m = threadIdx.x; m < n; m += blockDim.x) {
-      T v = Y[m];
+    auto scale = [inv_n](int, T v) {
       v.x *= inv_n;
       v.y *= inv_n;
-      buf[m] = v;
-    }
-    __syncthreads();
+      return v;
+    };
+    fft8<R, true>(X, other, W, Wl, n, Ident(), scale);
   }
 
   __device__ R theta(int m, R u, T a) const {
-    const R xm = X[m] - u;
+    const R xm = (X[m] - u) + Xl[m];
     return R(0.5) * xm * xm + (R)g * (a.x * a.x + a.y * a.y);
   }
 
-  // A <- exp(-i tau theta) A (forward Strang factor), in place
-  __device__ void potential(double u) {
+  // One forward Strang step on a = A (a_{j+1} = F^-1 e^{-i tau k^2/2} F e^{-i tau theta} a_j), with
+  // the potential factor applied as the first FFT pass loads each element; `keep`, if not null,
+  // receives a_j on the way.
+  __device__ void step(double u, T* keep) {
     const R ur = (R)u, tr = (R)tau;
-    for (int m = threadIdx.x; m < n; m += blockDim.x) {
-      const T a = A[m];
-      const T e = expm1i<T, R>(-tr * theta(m, ur, a));
-      A[m] = cadd(a, cmul(e, a));
-    }
-    __syncthreads();
+    const GP* self = this;
+    kinetic<false, true>(A, [self, ur, tr, keep](int m, T a) {
+      if (keep) keep[m] = a;
+      const T e = expm1i<T, R>(-tr * self->theta(m, ur, a));
+      return cadd(a, cmul(e, a));
+    });
   }
 
   __device__ double sum(double v) {
@@ -230,27 +276,27 @@ struct GP {
   }
 
   // adjoint step at a_j (global, complex R, per element): A holds nu_{j+1} on entry and nu_j on exit;
-  // returns dJ/du_j (FP64).
+  // the pointwise part runs as the first FFT pass loads each element.  GRAD: also return dJ/du_j
+  // (FP64 block sum of FP32 per-thread partials); the global adjoint sweep needs only the states.
+  template <bool GRAD>
   __device__ double adjoint_step(const T* aj, double u) {
-    const R ur = (R)u, tr = (R)tau;
-    R part = R(0);   // FP32 products; the block sum below accumulates the per-thread partials in FP64
-    for (int m = threadIdx.x; m < n; m += blockDim.x) {
+    const R ur = (R)u, tr = (R)tau, f2 = R(2) * (R)tau * (R)g;
+    R part = R(0);
+    const GP* self = this;
+    kinetic<true, true>(A, [self, aj, ur, tr, f2, &part](int m, T nu) {
       const T a = aj[m];
-      const T nu = A[m];
-      const T e = expm1i<T, R>(tr * theta(m, ur, a));
+      const T e = expm1i<T, R>(tr * self->theta(m, ur, a));
       const T mu = cadd(nu, cmul(e, nu));
       const R im = mu.x * a.y - mu.y * a.x;   // Im(conj(mu) a)
-      part = fma(ur - X[m], im, part);        // dV/du = -(x - u)
+      if (GRAD) part = fma((ur - self->X[m]) - self->Xl[m], im, part);   // dV/du = -(x - u)
       T w;
-      const R f = R(2) * (R)tau * (R)g * im;
+      const R f = f2 * im;
       w.x = mu.x + f * a.x;
       w.y = mu.y + f * a.y;
-      A[m] = w;
-    }
-    __syncthreads();
-    const double gsum = sum((double)part);
-    kinetic<true, true>(A);
-    return tau * dx * gsum;
+      return w;
+    });
+    if (!GRAD) return 0.0;
+    return tau * dx * sum((double)part);
   }
 };
 
@@ -279,7 +325,6 @@ __global__ void k_gp_forward(GPParams p) {
   s.kinetic<false, false>(s.A);   // a_0 = K psi_i
   int nn = 0;
   for (int j = 0; j <= p.Nt; ++j) {
-    for (int m = threadIdx.x; m < n; m += blockDim.x) traj[(long)j * n + m] = s.A[m];
     if (nn <= p.N && j == p.jn[nn]) {   // psi(t_n) = K^H a_j, and J, F at the end
       for (int m = threadIdx.x; m < n; m += blockDim.x) s.C[m] = s.A[m];
       __syncthreads();
@@ -309,8 +354,7 @@ __global__ void k_gp_forward(GPParams p) {
       __syncthreads();
     }
     if (j == p.Nt) break;
-    s.potential(ub[j]);
-    s.kinetic<false, true>(s.A);
+    s.step(ub[j], traj + (long)j * n);   // stores a_j as it goes
   }
   if (p.count && threadIdx.x == 0) atomicAdd(p.count, (unsigned long long)p.Nt);
 }
@@ -334,7 +378,7 @@ __global__ void k_gp_adjoint(GPParams p) {
   s.kinetic<true, false>(s.A);   // nu_Nt = K^H psi_f
   int nn = p.N - 1;
   for (int j = p.Nt - 1; j >= 0; --j) {
-    s.adjoint_step(traj + (long)j * n, ub[j]);
+    s.template adjoint_step<false>(traj + (long)j * n, ub[j]);
     if (nn >= 0 && j == p.jn[nn]) {   // chi(t_n) = lambda_j = K nu_j
       for (int m = threadIdx.x; m < n; m += blockDim.x) s.C[m] = s.A[m];
       __syncthreads();
@@ -368,11 +412,7 @@ __global__ void k_gp_sub(GPParams p) {
   for (int m = threadIdx.x; m < n; m += blockDim.x) s.A[m] = ld_state<R>(psin + (long)nsub * n, m);
   __syncthreads();
   s.kinetic<false, false>(s.A);
-  for (int j = j0; j < j1; ++j) {
-    for (int m = threadIdx.x; m < n; m += blockDim.x) traj[(long)j * n + m] = s.A[m];
-    s.potential(ub[j]);
-    s.kinetic<false, true>(s.A);
-  }
+  for (int j = j0; j < j1; ++j) s.step(ub[j], traj + (long)j * n);
   // J_n = Re<psi_n(t_{n+1})|chi(t_{n+1})>, psi_n(t_{n+1}) = K^H a_{j1}
   s.kinetic<true, false>(s.A);
   double jr = 0.0;
@@ -390,7 +430,7 @@ __global__ void k_gp_sub(GPParams p) {
   double* gb = p.grad + (long)b * p.Nt;
   for (int j = j1 - 1; j >= j0; --j) {
     const double uj = ub[j];
-    const double gj = s.adjoint_step(traj + (long)j * n, uj);
+    const double gj = s.template adjoint_step<true>(traj + (long)j * n, uj);
     err += fabs(gj);
     if (threadIdx.x == 0) {
       gb[j] = gj;
@@ -405,7 +445,7 @@ __global__ void k_gp_sub(GPParams p) {
   }
 }
 
-template <typename R> size_t gp_smem(int n) { return 7 * (size_t)n * sizeof(typename C2<R>::T); }
+template <typename R> size_t gp_smem(int n) { return 10 * (size_t)n * sizeof(typename C2<R>::T); }
 int gp_threads(int n) { return n / 8 < 32 ? 32 : n / 8; }
 
 template <typename R, class K>

@@ -16,24 +16,32 @@ cudaError_t launch_lsub_t(const KParams& p, cudaStream_t st) {
   return cudaGetLastError();
 }
 
-template <typename R, int W>
+// Sweep layout (WS warps x ES elements per thread) and sub-interval layout (W warps x 4 elements)
+// are chosen separately: the sweep is one CTA per SM on a sequential chain, the sub-interval kernel
+// N CTAs sharing the GPU.
+template <typename R, int WS, int ES, int W>
 static void fill_large(KernelSet* ks) {
+  using OpS = OpBitflipCTA<R, WS, ES>;
   using Op = OpBitflipCTA<R, W, 4>;
+  static_assert(OpS::D == Op::D, "both layouts cover the same dimension");
   ks->large = true;
-  ks->lsweep = &launch_lsweep_t<R, Op>;
+  ks->lsweep = &launch_lsweep_t<R, OpS>;
   ks->subinterval = &launch_lsub_t<R, Op>;
   ks->G = Op::NT;
   ks->E = Op::E;
   ks->W = W;
 }
 
+// Measured at d = 1024 (FP32): 4 elements per thread over 8 warps, ~640 ns per application of H;
+// 16 elements over 2 warps, 2.2x slower (two of four SM sub-partitions idle, longer per-thread
+// chains).  The exchanges, not the arithmetic, set the pace, so both kernels use the 4-element layout.
 template <typename R>
 static bool pick(int d, KernelSet* ks) {
   switch (d) {
-    case 128: fill_large<R, 1>(ks); return true;
-    case 256: fill_large<R, 2>(ks); return true;
-    case 512: fill_large<R, 4>(ks); return true;
-    case 1024: fill_large<R, 8>(ks); return true;
+    case 128: fill_large<R, 1, 4, 1>(ks); return true;
+    case 256: fill_large<R, 2, 4, 2>(ks); return true;
+    case 512: fill_large<R, 4, 4, 4>(ks); return true;
+    case 1024: fill_large<R, 8, 4, 8>(ks); return true;
     default: return false;
   }
 }

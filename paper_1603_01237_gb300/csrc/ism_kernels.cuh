@@ -9,6 +9,8 @@
 //                 (Eq. (dirpara)), then the backward adjoint and the per-step gradient of J_n
 //                 (proof of Theorem 2), and optionally the ascent step of Eq. (gradStep).
 #pragma once
+#include <type_traits>
+
 #include "ism_device.cuh"
 
 namespace ism {
@@ -38,6 +40,7 @@ struct KParams {
   const double2* psin;         // [B][N+1][d] psi(t_n) (form 1)
   const double2* chin;         // [B][N+1][d] chi(t_n) (form 1)
   int form;                    // 0: literal sub-problem from phi; 1: Theorem 2 two-trajectory form
+  int global;                  // form 1 only: scale the gradient to the full objective (beta_n g_n)
   int update;
   int max_spin;
   // direct global sweeps (large d): inputs and FP64 outputs, per-warp overlap partials
@@ -558,6 +561,135 @@ __global__ void __launch_bounds__(128) k_sweeps2(KParams p) {
   if (valid) count_work<R>(p.count, ch, ns, lg);
 }
 
+// ------------------------------------------------------------------------------ k_gsweep
+// Algorithm 1 steps (a)-(b) by direct propagation, one group per trajectory: psi forward over all Nt
+// steps from psi_i and chi backward from chi(T), psi(t_n) and chi(t_n) stored in FP64 with each
+// sub-interval's phase applied in FP64 there (the states continue from their FP64 values).  Work
+// 2 Nt state-steps per problem instead of the assembly's d Nt, but Nt sequential steps: the choice
+// for many problems per launch, where the groups of different problems fill the GPU.
+// grid (ceil(B / groups per CTA), nch): blockIdx.y is the direction, so every warp runs one
+// direction (the group shuffles and warp barriers need the whole warp on the same path).  Direction 1
+// (chi) exists only for the overlap objective; the observable objective runs chi after psi in the
+// same group (chi(T) = O psi(T) needs psi(T)).
+template <typename R, class Op>
+__global__ void __launch_bounds__(128) k_gsweep(KParams p) {
+  constexpr int G = Op::G, E = Op::E, GPB = 128 / G;
+  constexpr bool COMP = sizeof(R) == 4;
+  constexpr bool PK = sizeof(R) == 4 && Op::PACKED;
+  extern __shared__ __align__(128) unsigned char smem_raw[];
+  __shared__ Cheb<R> chs[GPB];
+  const int lg = threadIdx.x % G, gib = threadIdx.x / G;
+  const int nch = gridDim.y;
+  const long gid0 = (long)blockIdx.x * GPB + gib;
+  const long total = (long)p.B;
+  if (Op::G * Op::E == Op::DP_SMEM) {
+    const R* src = reinterpret_cast<const R*>(p.H);
+    R* dst = reinterpret_cast<R*>(smem_raw);
+    for (int i = threadIdx.x; i < 2 * Op::DP_SMEM * Op::DP_SMEM; i += blockDim.x) dst[i] = src[i];
+    __syncthreads();
+  }
+  const long warp_first = ((long)blockIdx.x * GPB + (threadIdx.x / 32) * (32 / G));
+  if (warp_first >= total) return;
+  const bool valid = gid0 < total;
+  const long gid = valid ? gid0 : total - 1;
+  const int b = (int)gid, dir = (int)blockIdx.y;
+  const int d = p.d, N = p.N;
+  const double* ub = p.u + (long)b * p.Nt;
+  double2* psin = p.psin_w + (long)b * (N + 1) * d;
+  double2* chin = p.chin_w + (long)b * (N + 1) * d;
+  Cheb<R>& ch = chs[gib];
+  Op op;
+  op.load(reinterpret_cast<const R*>(p.H), p.H0d, d, lg, smem_raw);
+  Vec<R, E> v, lo;
+  auto load64 = [&](const double2* src) {
+#pragma unroll
+    for (int r = 0; r < E; ++r) {
+      const int e = lg * E + r;
+      const double2 z = e < d ? src[e] : make_double2(0.0, 0.0);
+      v.re[r] = (R)z.x;
+      v.im[r] = (R)z.y;
+      lo.re[r] = COMP ? (R)(z.x - (double)v.re[r]) : R(0);
+      lo.im[r] = COMP ? (R)(z.y - (double)v.im[r]) : R(0);
+    }
+  };
+  auto store64 = [&](bool adj, double2* dst) {   // segment phase in FP64, store, continue from it
+#pragma unroll
+    for (int r = 0; r < E; ++r) {
+      const int e = lg * E + r;
+      double yr, yi;
+      phase_rotate(ch.cph, ch.sph, adj, (double)v.re[r] + (double)lo.re[r], (double)v.im[r] + (double)lo.im[r], yr, yi);
+      if (e < d && valid) dst[e] = make_double2(yr, yi);
+      v.re[r] = (R)yr;
+      v.im[r] = (R)yi;
+      lo.re[r] = COMP ? (R)(yr - (double)v.re[r]) : R(0);
+      lo.im[r] = COMP ? (R)(yi - (double)v.im[r]) : R(0);
+    }
+  };
+  // propagate over sub-interval n forward (ADJ = false) or backward (ADJ = true)
+  auto segment = [&](int n, auto adj_tag) {
+    constexpr bool ADJ = decltype(adj_tag)::value;
+    int Kw, Sw;
+    __syncwarp();
+    cheb_load<G, R>(ch, reinterpret_cast<const Cheb<R>*>(p.cheb) + (long)b * N + n, lg, Kw, Sw);
+    op.scale(p.H0d, d, lg, ch);
+    const int j0 = p.jn[n], j1 = p.jn[n + 1];
+    if constexpr (PK) {
+      VecP<E> pv, pl;
+#pragma unroll
+      for (int r = 0; r < E; ++r) { pv.z[r] = make_float2(v.re[r], v.im[r]); pl.z[r] = make_float2(lo.re[r], lo.im[r]); }
+      for (int s = 0; s < j1 - j0; ++s) {
+        const int j = ADJ ? j1 - 1 - s : j0 + s;
+        op.set_u(ldu_ro<float>(ub, j), ch, lg);
+        cheb_step_p<ADJ, true>(pv, pl, op, ch, Kw, Sw);
+      }
+#pragma unroll
+      for (int r = 0; r < E; ++r) { v.re[r] = pv.z[r].x; v.im[r] = pv.z[r].y; lo.re[r] = pl.z[r].x; lo.im[r] = pl.z[r].y; }
+    } else {
+      for (int s = 0; s < j1 - j0; ++s) {
+        const int j = ADJ ? j1 - 1 - s : j0 + s;
+        op.set_u(ldu_ro<R>(ub, j), ch, lg);
+        cheb_step<ADJ, COMP>(v, lo, op, ch, Kw, Sw);
+      }
+    }
+    if (valid) count_work<R>(p.count, ch, j1 - j0, lg);
+  };
+  if (dir == 0) {
+    load64(p.psi_i);
+    if (valid)
+      for (int e = lg; e < d; e += G) psin[e] = p.psi_i[e];
+    for (int n = 0; n < N; ++n) {
+      segment(n, std::false_type());
+      store64(false, psin + (long)(n + 1) * d);
+    }
+  }
+  if (dir == 1 || nch == 1) {
+    double2* chT = chin + (long)N * d;
+    if (p.obj == 0) {
+      if (valid)
+        for (int e = lg; e < d; e += G) chT[e] = p.psi_f[e];
+    } else {   // chi(T) = O psi(T) in FP64; psi(T) was stored by this group
+      __syncwarp();
+      const double2* psT = psin + (long)N * d;
+      for (int e = lg; e < d; e += G) {
+        double sr = 0.0, si = 0.0;
+        for (int f = 0; f < d; ++f) {
+          const double o = p.O[(long)e * d + f];
+          const double2 z = psT[f];
+          sr = fma(o, z.x, sr);
+          si = fma(o, z.y, si);
+        }
+        if (valid) chT[e] = make_double2(sr, si);
+      }
+    }
+    __syncwarp();
+    load64(chT);
+    for (int n = N - 1; n >= 0; --n) {
+      segment(n, std::true_type());
+      store64(true, chin + (long)n * d);
+    }
+  }
+}
+
 // One block per (problem, n); threads over the steps of the sub-interval.
 template <typename R>
 __global__ void __launch_bounds__(256) k_gradpass(KParams p, int GE) {
@@ -582,7 +714,8 @@ __global__ void __launch_bounds__(256) k_gradpass(KParams p, int GE) {
     }
     return cPhi * (double)zi - sPhi * (double)zr;
   };
-  const double ht = 0.5 * p.tau * p.w / beta, tb = p.tau / beta, step = p.rho * beta / p.tau;
+  const double bs = p.global ? 1.0 : beta;   // Theorem 2: beta_n g_n is the gradient of J
+  const double ht = 0.5 * p.tau * p.w / bs, tb = p.tau / bs, step = p.rho * beta / p.tau;
   double* ub = p.u + (long)b * p.Nt;
   double* gb = p.grad + (long)b * p.Nt;
   double err = 0.0, pen = 0.0;

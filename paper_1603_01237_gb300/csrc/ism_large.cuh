@@ -344,8 +344,8 @@ __global__ void __launch_bounds__(Op::NT) k_lsub(KParams p) {
   __syncthreads();   // every warp's partials are written
 
   // ---- FP64 pass over the steps: gradient, Err, ascent step, penalty of J_n
-  const double ht = 0.5 * p.tau * p.w / (p.form ? beta : 1.0);
-  const double tb = p.tau / beta;
+  const double ht = 0.5 * p.tau * p.w / ((p.form && !p.global) ? beta : 1.0);
+  const double tb = p.tau / (p.global ? 1.0 : beta);   // Theorem 2: beta_n g_n is the gradient of J
   const double step = p.rho * beta / p.tau;
   double* gb = p.grad + (long)b * p.Nt;
   double err = 0.0, pen = 0.0;

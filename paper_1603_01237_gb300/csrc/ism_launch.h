@@ -14,6 +14,7 @@ struct KernelSet {
   LaunchFn assemble = nullptr;
   LaunchFn subinterval = nullptr;
   LaunchFn sweeps2 = nullptr;     // concurrent two-trajectory sweeps + gradient pass
+  LaunchFn gsweep = nullptr;      // direct global sweeps (Algorithm 1 (a)-(b) without assembly)
   int G = 0, E = 0;          // lanes per state, elements per lane (sub-interval sweep)
   int GA = 0;                // lanes per state in the assembly
   size_t op_smem = 0;        // dynamic shared memory of the op (dense H pairs)

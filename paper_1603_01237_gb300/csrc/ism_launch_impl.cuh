@@ -55,6 +55,19 @@ cudaError_t launch_sweeps2_t(const KParams& p, cudaStream_t st) {
   return cudaGetLastError();
 }
 
+template <typename R, class Op>
+cudaError_t launch_gsweep_t(const KParams& p, cudaStream_t st) {
+  constexpr int GPB = 128 / Op::G;
+  const long grid = ((long)p.B + GPB - 1) / GPB;
+  const size_t smem = op_smem_bytes<R, Op>();
+  if (smem > 40 * 1024) {
+    cudaError_t e = cudaFuncSetAttribute(k_gsweep<R, Op>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    if (e != cudaSuccess) return e;
+  }
+  k_gsweep<R, Op><<<dim3((unsigned)grid, p.obj == 0 ? 2 : 1), 128, smem, st>>>(p);
+  return cudaGetLastError();
+}
+
 // OpA: lane layout of the throughput-bound assembly (few lanes, many elements per lane);
 // OpS: lane layout of the latency-bound sub-interval sweep (more lanes per state).
 template <typename R, class OpA, class OpS = OpA>
@@ -62,6 +75,7 @@ void fill_set(KernelSet* ks) {
   ks->assemble = &launch_assemble_t<R, OpA>;
   ks->subinterval = &launch_subinterval_t<R, OpS>;
   ks->sweeps2 = &launch_sweeps2_t<R, OpS>;
+  ks->gsweep = &launch_gsweep_t<R, OpS>;
   ks->G = OpS::G;
   ks->E = OpS::E;
   ks->GA = OpA::G;

@@ -127,3 +127,22 @@ def test_pack_hamiltonian_checks_structure():
     assert np.allclose(h, 1.0) and np.allclose(d0, np.diag(s.H0))
     with pytest.raises(ValueError):
         abi.pack_hamiltonian("tridiag", s.H0, s.H1)
+
+
+def test_footprint_needs_no_gpu_and_scales_with_the_problem(lib):
+    """ism_plan_footprint sizes a plan on the host: it grows linearly with the batch and with Nt,
+    and rejects what ism_plan rejects."""
+    import workloads as W
+    from paper_1603_01237_gb300 import abi
+
+    w = W.config("rotor41", Nt=2000, N=16)
+    f1 = abi.footprint(w, batch=1)
+    f2 = abi.footprint(w, batch=2)
+    f4 = abi.footprint(w, batch=4)
+    assert 0 < f1 < f2 < f4
+    assert abs((f4 - f2) - 2 * (f2 - f1)) <= 8 * 512   # per-problem part, up to allocation rounding
+    assert abi.footprint(W.config("rotor41", Nt=4000, N=16)) > f1
+    assert abi.footprint(W.config("ising1024", Nt=2000, N=16)) > 2000 * 1024 * 8   # per-step trajectory
+    with pytest.raises(abi.IsmError) as ei:
+        abi.footprint(W.config("rotor41", Nt=100, N=200))
+    assert ei.value.status == 1

@@ -1,5 +1,7 @@
 """Full-size parity against stored oracle values (tests/golden/*.json, written by make_golden.py,
-which calls only the oracle): the rotor benchmark problem, d=41, Nt=20000, N=128, 50 iterations."""
+which calls only the oracles): the rotor benchmark problem (d=41, Nt=20000, N=128, 50 iterations),
+the condensate problem (512-point grid, Nt=10000, N=64, 20 iterations) and the 10-spin chain
+(d=1024, Nt=50000, N=256, 2 iterations)."""
 import json
 import os
 
@@ -28,13 +30,14 @@ def _load(name):
 
 
 @pytest.mark.parametrize("prec,tolJ,tolu", [("fp64", 1e-9, 1e-9), ("mixed", 1e-5, 1e-4)])
-@pytest.mark.parametrize("N", [16, 128])
-def test_rotor41_50_iterations(P, prec, tolJ, tolu, N):
+@pytest.mark.parametrize("N,step1", [(16, 1), (128, 1), (128, 2)])
+def test_rotor41_50_iterations(P, prec, tolJ, tolu, N, step1):
     """J[u^(k)] for k = 0..50 and sampled final controls; with one local step the iterates do not depend
-    on N (Theorem 2), so one oracle history serves N = 16 and 128."""
+    on N (Theorem 2), so one oracle history serves N = 16 and 128; step1 = 2 takes the global
+    trajectories by direct sweeps instead of assembly."""
     g = _load("rotor41.json")
     w = W.config("rotor41", N=N)
-    with P.Plan(w, precision=prec) as pl:
+    with P.Plan(w, precision=prec, step1=step1) as pl:
         u, J, E = pl.iterate(w.u0, g["iters"])
         _, F = pl.evaluate(u[0])
     J_o = np.array(g["J_hist"])
@@ -60,3 +63,68 @@ def test_rotor41_first_subinterval_gradient(P, prec, tol):
     ref = np.array(g["grad"])
     assert np.linalg.norm(grad[0][idx] - ref) <= tol * np.linalg.norm(ref)
     assert abs(np.linalg.norm(grad[0]) - g["grad_l2"]) <= tol * g["grad_l2"]
+
+
+# ---------------------------------------------------------------- condensate, 512-point grid
+@pytest.mark.parametrize("prec,tolJ,tolu", [("fp64", 1e-9, 1e-8), ("mixed", 1e-5, 1e-3)])
+def test_gp512_20_iterations(P, prec, tolJ, tolu):
+    """The condensate benchmark problem (Nt=10000, N=64): J[u^(k)] for k = 0..20 and sampled final
+    controls against the stored oracle history."""
+    g = _load("gp512.json")
+    w = W.gp_bec()
+    with P.Plan(w, precision=prec, rho=g["rho"]) as pl:
+        u, J, E = pl.iterate(w.u0, g["iters"])
+    J_o = np.array(g["J_hist"])
+    assert np.max(np.abs(J[0] - J_o)) <= tolJ, np.max(np.abs(J[0] - J_o))
+    idx = np.array(g["u_final_idx"])
+    du = u[0][idx] - np.array(g["u_final"])
+    assert np.linalg.norm(du) <= tolu * np.linalg.norm(np.array(g["u_final"]) - w.u0[idx])
+
+
+@pytest.mark.parametrize("prec,tol", [("fp64", 1e-9), ("mixed", 1e-4)])
+def test_gp512_first_gradient(P, prec, tol):
+    """All sub-problem gradients at u0 (from the plan's own psi(t_n), chi(t_n)) equal the global
+    gradient of the full problem (nonlinear reading of Sec. 4)."""
+    g = _load("gp512.json")
+    w = W.gp_bec()
+    with P.Plan(w, precision="fp64") as pl:
+        pairs = pl.intermediate_states(w.u0)[0]
+    with P.Plan(w, precision=prec) as pl:
+        grad, _ = pl.subinterval_grad(pairs, w.u0)
+    idx = np.array(g["grad0_idx"])
+    ref = np.array(g["grad0"])
+    assert np.linalg.norm(grad[0][idx] - ref) <= tol * np.linalg.norm(ref)
+    assert abs(np.linalg.norm(grad[0]) - g["grad0_l2"]) <= tol * g["grad0_l2"]
+
+
+# ---------------------------------------------------------------- 10-spin chain, d = 1024
+def _ising():
+    return W.with_random_target(W.config("ising1024"), 1103)
+
+
+@pytest.mark.parametrize("prec,tolJ,tolu", [("fp64", 1e-9, 1e-8), ("mixed", 1e-5, 1e-4)])
+def test_ising1024_two_iterations(P, prec, tolJ, tolu):
+    """d=1024, Nt=50000, N=256 (random unit target, seed 1103): two ISM iterations against the oracle."""
+    g = _load("ising1024.json")
+    w = _ising()
+    with P.Plan(w, precision=prec, rho=g["rho"]) as pl:
+        u, J, E = pl.iterate(w.u0, g["iters"])
+    J_o = np.array(g["J_hist"])
+    assert np.max(np.abs(J[0] - J_o)) <= tolJ, np.max(np.abs(J[0] - J_o))
+    idx = np.array(g["u_final_idx"])
+    du = u[0][idx] - np.array(g["u_final"])
+    assert np.linalg.norm(du) <= tolu * np.linalg.norm(np.array(g["u_final"]) - w.u0[idx])
+
+
+@pytest.mark.parametrize("prec,tol", [("fp64", 1e-9), ("mixed", 1e-4)])
+def test_ising1024_first_subinterval_gradient(P, prec, tol):
+    g = _load("ising1024.json")
+    w = _ising()
+    with P.Plan(w, precision="fp64") as pl:
+        phi = pl.intermediate_states(w.u0)
+    with P.Plan(w, precision=prec) as pl:
+        grad, Jn = pl.subinterval_grad(phi, w.u0)
+    idx = np.array(g["grad_idx"])
+    ref = np.array(g["grad"])
+    assert np.linalg.norm(grad[0][idx] - ref) <= tol * np.linalg.norm(ref)
+    assert np.max(np.abs(Jn[0] - np.array(g["Jn"]))) <= (1e-10 if prec == "fp64" else 1e-6)

@@ -234,3 +234,45 @@ def test_rotor_mixed_fine_steps(P):
         u, J, _ = pl.iterate(w.u0, 4)
     assert np.max(np.abs(J[0] - J_o)) <= 1e-5, np.max(np.abs(J[0] - J_o))
     assert np.all(np.diff(J_o) > 0)
+
+
+# ---------------------------------------------------------------- Algorithm 1 (a)-(b) by direct sweeps
+DIRECT = [c for c in CASES if c[0] in ("spin16-ragged", "rotor41-fp64", "rotor41-mixed", "dense41-obs-fp64",
+                                        "dense16-mixed", "bitflip32-mixed", "tridiag41-h1diag-mixed")]
+
+
+@pytest.mark.parametrize("name,w,prec", DIRECT, ids=[c[0] for c in DIRECT])
+def test_direct_sweeps_match_oracle(P, name, w, prec):
+    """step1 = 2: psi(t_n), chi(t_n) by direct propagation (2 Nt state-steps) instead of assembly."""
+    phi_o = O.intermediate_states(w, w.u0)
+    Jo, Fo = O.objective(w, w.u0)
+    with P.Plan(w, precision=prec, step1=2) as pl:
+        assert pl.info(6) == 2
+        phi = pl.intermediate_states(w.u0)[0]
+        J, F = pl.evaluate(w.u0)
+    tol = FP64_PHI if prec == "fp64" else MIX_PHI
+    assert np.max(np.abs(phi - phi_o)) <= tol, np.max(np.abs(phi - phi_o))
+    assert np.array_equal(phi[0], phi_o[0])
+    assert abs(J[0] - Jo) <= (1e-11 if prec == "fp64" else 2e-5)
+    assert abs(F[0] - Fo) <= (1e-11 if prec == "fp64" else 2e-5)
+
+
+@pytest.mark.parametrize("name,w,prec", DIRECT[:3], ids=[c[0] for c in DIRECT[:3]])
+def test_direct_iterate_matches_algorithm1(P, name, w, prec):
+    iters = 3
+    u_o, J_o, F_o, E_o = O.ism_solve(w, w.u0, iters, w.rho)
+    with P.Plan(w, precision=prec, step1=2) as pl:
+        u, J, E = pl.iterate(w.u0, iters)
+    tol = 1e-9 if prec == "fp64" else 1e-4
+    assert np.max(np.abs(J[0] - J_o)) <= tol
+    assert rel_l2(u[0] - w.u0, u_o - w.u0) <= tol
+
+
+def test_step1_default_follows_the_batch(P):
+    w = W.config("rotor41", Nt=400, N=8)
+    with P.Plan(w, precision="mixed", batch=95) as pl:
+        assert pl.info(6) == 1
+    with P.Plan(w, precision="mixed", batch=96) as pl:
+        assert pl.info(6) == 2
+    with P.Plan(w, precision="mixed", batch=96, step1=1) as pl:
+        assert pl.info(6) == 1

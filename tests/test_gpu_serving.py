@@ -1,0 +1,80 @@
+"""Serving loop (ism_server_*): requests of different dimensions, step counts and N, submitted while
+others run, each give exactly the result of the same solve run alone; admission by device footprint."""
+import time
+
+import numpy as np
+import pytest
+
+import workloads as W
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def P():
+    import __graft_entry__
+
+    __graft_entry__.build()
+    import paper_1603_01237_gb300 as P
+
+    return P
+
+
+def _gp(n=64, Nt=200, N=8, T=1.5, seed=9):
+    rng = np.random.default_rng(seed)
+    psi_i, psi_f = W.gp_stationary_states(n, 20.0, -10.0, 1.0, dt=2e-3, steps=4000)
+    return W.GPWorkload(name="gp", n=n, L=20.0, x_min=-10.0, g=1.0, psi_i=psi_i, psi_f=psi_f, T=T, Nt=Nt, N=N,
+                        u0=rng.uniform(-0.5, 0.5, Nt), rho=0.5)
+
+
+def _mix():
+    return [
+        (W.config("spin16", Nt=400, N=4), "fp64", 6),
+        (W.config("rotor41", Nt=1200, N=16), "mixed", 5),
+        (W.with_random_target(W.spin_chain(7, 51, T=1.0, Nt=300, N=8, u_amp=1.0), 52), "mixed", 3),
+        (W.random_dense(16, 53, T=2.0, Nt=250, N=5), "fp64", 4),
+        (_gp(), "mixed", 3),
+        (W.config("rotor41", Nt=3000, N=64), "mixed", 4),
+        (W.with_random_target(W.spin_chain(9, 54, T=1.0, Nt=200, N=4, u_amp=1.0), 55), "mixed", 2),
+        (W.config("spin16", Nt=1000, N=8), "mixed", 5),
+    ]
+
+
+def test_results_in_the_mix_equal_results_alone(P):
+    mix = _mix()
+    rng = np.random.default_rng(1)
+    with P.Server(slots=3, hbm_budget_bytes=8 << 30) as srv:
+        ids = []
+        for w, prec, iters in mix:
+            ids.append(srv.submit(w, iters=iters, precision=prec))
+            time.sleep(rng.exponential(0.005))   # arrivals while earlier requests run
+        got = [srv.result(i) for i in ids]
+    for (w, prec, iters), (u, J, t) in zip(mix, got):
+        with P.Plan(w, precision=prec) as pl:
+            ua, Ja, _ = pl.iterate(w.u0, iters)
+        assert np.array_equal(u, ua), w.name
+        assert np.array_equal(J, Ja), w.name
+        assert t[2] >= t[1] >= 0.0
+
+
+def test_admission_by_footprint(P):
+    """A budget that holds one plan at a time still completes every request (one after another);
+    a request larger than the whole budget is refused at submission."""
+    w = W.config("rotor41", Nt=1500, N=16)
+    one = P.footprint(w) + 16 * 4 + (1 << 20)
+    with P.Server(slots=4, hbm_budget_bytes=int(one * 1.5)) as srv:
+        ids = [srv.submit(w, iters=3, precision="mixed") for _ in range(3)]
+        res = [srv.result(i) for i in ids]
+        for u, J, t in res[1:]:
+            assert np.array_equal(u, res[0][0])
+        starts = sorted(t[0] for _, _, t in res)
+        assert starts[2] > starts[0]   # queued behind the budget
+        with pytest.raises(P.IsmError) as ei:
+            srv.submit(W.config("rotor41", Nt=20000, N=128), iters=1, batch=64)
+        assert ei.value.status == 2
+
+
+def test_footprint_matches_plan_bytes(P):
+    for w in (W.config("rotor41", Nt=2000, N=16), W.config("ising1024", Nt=500, N=8), _gp()):
+        with P.Plan(w, precision="mixed") as pl:
+            assert pl.info(3) == P.footprint(w, precision="mixed")

@@ -216,6 +216,14 @@ def rabi(delta: float, u: float, *, T: float, Nt: int, N: int = 1) -> Workload:
 # ----------------------------------------------------------------------------------------------
 # The named benchmark configurations.  Seed = 1000 + configuration index.
 # ----------------------------------------------------------------------------------------------
+def with_random_target(w: Workload, seed: int) -> Workload:
+    """The same problem with a seeded random unit target (standard normal real and imaginary parts,
+    normalised), so that overlaps and gradients are O(1) from any start."""
+    rng = np.random.default_rng(seed)
+    v = rng.standard_normal(w.d) + 1j * rng.standard_normal(w.d)
+    return w.with_(psi_f=v / np.linalg.norm(v))
+
+
 CONFIG_NAMES = ("spin16", "rotor41", "gp512", "ising1024")
 
 
@@ -325,11 +333,12 @@ def gp_stationary_states(n: int, L: float, x_min: float, g: float, *, dt: float 
 
 
 def gp_bec(n: int = 512, seed: int = 1002, *, T: float = 8.0, Nt: int = 10000, N: int = 64, g: float = 1.0,
-           u_amp: float = 0.1, steps: int = 40000, name: str = "gp512") -> GPWorkload:
+           u_amp: float = 0.1, steps: int = 40000, name: str = "gp512", states=None) -> GPWorkload:
     """Grid of n points on [-10, 10) (periodic), g = 1, T = 8, ground state -> lowest odd state,
-    u0 ~ U[-u_amp, u_amp] (the only random draw)."""
+    u0 ~ U[-u_amp, u_amp] (the only random draw).  `states` = (psi_i, psi_f) reuses stationary states
+    already computed for the same (n, g, steps)."""
     rng = np.random.default_rng(seed)
     u0 = rng.uniform(-u_amp, u_amp, size=Nt)
     L, x_min = 20.0, -10.0
-    psi_i, psi_f = gp_stationary_states(n, L, x_min, g, steps=steps)
+    psi_i, psi_f = states if states is not None else gp_stationary_states(n, L, x_min, g, steps=steps)
     return GPWorkload(name=name, n=n, L=L, x_min=x_min, g=g, psi_i=psi_i, psi_f=psi_f, T=T, Nt=Nt, N=N, u0=u0)
