@@ -133,6 +133,35 @@ def cheb_flops(kind: str, d: int, y_apps: int, terms: int, substeps: int) -> flo
     return float(y_apps) * (4 * nnz_of(kind, d) + 2 * d) + float(terms) * 4 * d + float(substeps) * 6 * d
 
 
+def kernel_source_hash() -> str:
+    """Hash of the CUDA sources and headers the kernels are built from (a captured DRAM traffic is
+    reported only while the kernels are the ones it was captured on)."""
+    import hashlib
+
+    h = hashlib.sha256()
+    csrc = os.path.join(ROOT, "paper_1603_01237_gb300", "csrc")
+    for name in sorted(os.listdir(csrc)):
+        if name.endswith((".cu", ".cuh", ".h")):
+            with open(os.path.join(csrc, name), "rb") as f:
+                h.update(name.encode() + b"\0" + f.read())
+    with open(os.path.join(ROOT, "include", "ism.h"), "rb") as f:
+        h.update(f.read())
+    return h.hexdigest()[:16]
+
+
+# DRAM bytes (dram__bytes_read.sum + dram__bytes_write.sum) per problem per launch of a kernel, from
+# one ncu capture of a smaller batch of the same workload (traffic grows with the problems a launch
+# processes), keyed by (kernel, workload) with the kernel source hash at capture time; see profiles/.
+TRAFFIC_PER_PROBLEM = {}
+
+
+def traffic_of(kernel: str, workload: str, batch: int):
+    rec = TRAFFIC_PER_PROBLEM.get((kernel, workload))
+    if rec is None or rec["source_hash"] != kernel_source_hash():
+        return None
+    return rec["bytes_per_problem"] * batch
+
+
 def measured_peaks() -> dict:
     """HBM copy bandwidth and bf16 GEMM rate measured on this GPU model, else the stated fallback."""
     path = os.path.join(os.path.dirname(os.path.abspath(__file__)), "MEASURED_PEAKS.json")
@@ -327,9 +356,13 @@ def run_ours(args):
 
     # roofline of the dominant phase (largest share of device time); one launch of a phase per iteration
     large = plan.ks_large
+    direct = plan.info(6) == 2   # Algorithm 1 (a)-(b) by direct sweeps
     if plan.gp:
         names = ["k_gp_forward", "k_gp_adjoint", "k_gp_sub"]
         kernels = names
+    elif direct and not large:
+        names = ["k_gsweep", "k_phi", "k_subinterval"]
+        kernels = ["k_cheb_prep + k_gsweep", "k_phi", "k_subinterval"]
     elif large:
         names = ["k_lsweep", "k_phi", "k_lsub"]
         kernels = ["k_cheb_prep + k_lsweep", "k_phi", "k_lsub"]
@@ -340,7 +373,7 @@ def run_ours(args):
     ms_launch = st["ms"][dom] / args.steps
     peaks = measured_peaks()
     alu_src = "derived: 152 SMs x 128 FP32 lanes x 2 flop x 2070 MHz (no measured FP32 peak)"
-    if plan.gp or dom in (0, 2) or large:
+    if plan.gp or dom in (0, 2) or large or direct:
         if plan.gp:   # FFT pairs counted by the kernels: forward, adjoint, sub-interval
             pairs = [st["y_apps"][0], st["terms"][0], st["terms"][1]][dom]
             flops = pairs * gp_pair_flops(d) / args.steps
@@ -352,7 +385,8 @@ def run_ours(args):
         achieved = flops / (ms_launch / 1e3) / 1e12
         peak = fp32_peak_tflops()
         roof = {"kernel": names[dom], "kernels_timed": kernels[dom], "bound": "alu", "achieved": achieved,
-                "peak": peak, "unit": "TFLOP/s", "frac": achieved / peak, "traffic": None,
+                "peak": peak, "unit": "TFLOP/s", "frac": achieved / peak,
+                "traffic": traffic_of(names[dom], args.config, B),
                 "peak_source": alu_src, "flops_per_launch": flops, "ms_per_launch": ms_launch}
     else:
         # algorithmic bytes: every stored propagator tile read once per chain, both staged state chains written
@@ -360,7 +394,8 @@ def run_ours(args):
         nbytes = B * (2 * w.N * tile + 2 * (w.N + 1) * d * 8)
         achieved = nbytes / (ms_launch / 1e3) / 1e9
         roof = {"kernel": names[dom], "kernels_timed": kernels[dom], "bound": "hbm", "achieved": achieved,
-                "peak": peaks["hbm_gbs"], "unit": "GB/s", "frac": achieved / peaks["hbm_gbs"], "traffic": None,
+                "peak": peaks["hbm_gbs"], "unit": "GB/s", "frac": achieved / peaks["hbm_gbs"],
+                "traffic": traffic_of(names[dom], args.config, B),
                 "peak_source": peaks["source"], "bytes_per_launch": nbytes, "ms_per_launch": ms_launch}
     phase_share = {n: st["ms"][i] / max(1e-12, sum(st["ms"])) for i, n in enumerate(names)}
 

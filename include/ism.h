@@ -115,7 +115,9 @@ typedef struct {
                               1 = propagator assembly and chain (Sec. 3): d Nt state-steps per
                                   problem, parallel over sub-intervals -- lowest latency;
                               2 = direct sweeps: 2 Nt state-steps per problem, sequential in time --
-                                  least work, for many problems per plan;
+                                  least work, for many problems per plan (the sub-problems then
+                                  run the forward and adjoint sweeps of a sub-interval in one
+                                  lane group, for throughput, rather than in two concurrent ones);
                               0 = default: 2 when batch >= 96, else 1.  Larger d always sweeps. */
 } ism_options;
 

@@ -613,11 +613,11 @@ int plan_build(const ism_problem* prob, const ism_options* opt, void* cuda_strea
   unsigned char* dTb = nullptr;
   TRY_ALLOC(dTb, B * ((size_t)P->Nt + P->N) * GE * P->r2);
   P->dtraj = dTb;
-  if (!P->ks.large) {   // second trajectory of the concurrent two-trajectory sweeps
+  if (!P->ks.large && !P->direct) {   // second trajectory of the concurrent two-trajectory sweeps
     unsigned char* dT2 = nullptr;
     TRY_ALLOC(dT2, B * ((size_t)P->Nt + P->N) * GE * P->r2);
     P->dtraj2 = dT2;
-  } else {
+  } else if (P->ks.large) {
     unsigned char* dZ = nullptr;
     TRY_ALLOC(dZ, B * ((size_t)P->Nt + P->N) * P->ks.W * P->r2);
     P->dzp = dZ;
@@ -846,7 +846,7 @@ int ism_iterate(ism_plan_t P, int iters, double* u_inout, double* J_hist, double
         ISM_CUDA_TRY(ism::launch_cheb_prep(P->prec, k, P->st));
         P->kernels += 1;
       }
-      if (k.form && !P->ks.large) ISM_CUDA_TRY(timed(P, 2, 2, [&] { return P->ks.sweeps2(k, P->st); }));
+      if (k.form && !P->ks.large && !P->direct) ISM_CUDA_TRY(timed(P, 2, 2, [&] { return P->ks.sweeps2(k, P->st); }));
       else ISM_CUDA_TRY(timed(P, 2, 1, [&] { return P->ks.subinterval(k, P->st); }));
     }
     if (err_hist) {
@@ -885,7 +885,7 @@ int ism_gradient(ism_plan_t P, const double* u, double* grad, double* J) {
     k.form = 1;
     k.global = 1;
     k.count = P->dcount + 3;
-    if (P->ks.large) ISM_CUDA_TRY(timed(P, 2, 1, [&] { return P->ks.subinterval(k, P->st); }));
+    if (P->ks.large || P->direct) ISM_CUDA_TRY(timed(P, 2, 1, [&] { return P->ks.subinterval(k, P->st); }));
     else ISM_CUDA_TRY(timed(P, 2, 2, [&] { return P->ks.sweeps2(k, P->st); }));
   }
   if ((rc = copy_out(P, grad, P->dgrad, (long)P->B * P->Nt))) return rc;

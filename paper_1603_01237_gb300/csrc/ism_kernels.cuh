@@ -245,7 +245,38 @@ __global__ void __launch_bounds__(128) k_subinterval(KParams p) {
   R2* tr = tr0 + lg * E;
 
   // ---- forward sweep: store H1 psi_j, then psi_{j+1} = U_j psi_j
-  {
+  constexpr bool PK = sizeof(R) == 4 && Op::PACKED;
+  Vec<R, E> hend;   // end point: H1 psi_n(t_{n+1}) stays in registers
+  if constexpr (PK) {   // packed FP32: both halves per instruction
+    VecP<E> pv, pl;
+#pragma unroll
+    for (int r = 0; r < E; ++r) { pv.z[r] = make_float2(v.re[r], v.im[r]); pl.z[r] = make_float2(lo.re[r], lo.im[r]); }
+    float2* trp = reinterpret_cast<float2*>(tr);
+    float ua = ldu<float>(ub, j0), ub1 = ns > 1 ? ldu<float>(ub, j0 + 1) : ua;
+    for (int s = 0; s < nsw; ++s) {
+      const bool act = s < ns;
+      const float uj = ua;
+      ua = ub1;
+      if (s + 2 < ns) ub1 = ldu<float>(ub, j0 + s + 2);
+      VecP<E> hv;
+      op.h1_p(pv, hv);
+      if (act && valid) {
+#pragma unroll
+        for (int r = 0; r < E; ++r) trp[(long)s * GE + r] = hv.z[r];
+      }
+      VecP<E> w = pv, wl = pl;
+      op.set_u(uj, ch, lg);
+      cheb_step_p<false, true>(w, wl, op, ch, Kw, Sw);
+      if (act) { pv = w; pl = wl; }
+    }
+    VecP<E> he;
+    op.h1_p(pv, he);
+#pragma unroll
+    for (int r = 0; r < E; ++r) {
+      v.re[r] = pv.z[r].x; v.im[r] = pv.z[r].y; lo.re[r] = pl.z[r].x; lo.im[r] = pl.z[r].y;
+      hend.re[r] = he.z[r].x; hend.im[r] = he.z[r].y;
+    }
+  } else {
     R ua = ldu<R>(ub, j0), ub1 = ns > 1 ? ldu<R>(ub, j0 + 1) : ua;
     for (int s = 0; s < nsw; ++s) {
       const bool act = s < ns;
@@ -263,10 +294,8 @@ __global__ void __launch_bounds__(128) k_subinterval(KParams p) {
       cheb_step<false, COMP>(w, wl, op, ch, Kw, Sw);
       if (act) { v = w; lo = wl; }
     }
+    op.h1(v, hend);
   }
-  // end point: H1 psi_n(t_{n+1}) stays in registers
-  Vec<R, E> hend;
-  op.h1(v, hend);
 
   // ---- terminal residual delta = phi_{n+1} - psi_n(t_{n+1}) in FP64 (its norm gives J_n).  Form 0
   // propagates delta backward; form 1 propagates chi from chi(t_{n+1}) and takes delta from the
@@ -315,7 +344,48 @@ __global__ void __launch_bounds__(128) k_subinterval(KParams p) {
   }
 
   // ---- backward sweep: delta_j = U_j^H delta_{j+1}; gradient term of step j into slot j
-  {
+  if constexpr (PK) {
+    const int top = ns - 1;
+    const float2* trp = reinterpret_cast<const float2*>(tr);
+    VecP<E> pd, h0, h1v, dummy;
+#pragma unroll
+    for (int r = 0; r < E; ++r) pd.z[r] = make_float2(dl.re[r], dl.im[r]);
+    auto ldslot = [&](int s, VecP<E>& h) {
+#pragma unroll
+      for (int r = 0; r < E; ++r) h.z[r] = trp[(long)s * GE + r];
+    };
+    // <a|h> over the group from packed products: (re re, im im) and (re im, -im re) pair sums
+    auto zdotp = [&](const VecP<E>& a, const VecP<E>& h, float& zr, float& zi) {
+      float2 s1 = make_float2(0.f, 0.f), s2 = make_float2(0.f, 0.f);
+#pragma unroll
+      for (int r = 0; r < E; ++r) {
+        s1 = fma2(a.z[r], h.z[r], s1);
+        s2 = fma2(a.z[r], make_float2(h.z[r].y, -h.z[r].x), s2);
+      }
+      zr = g_sum<G>(s1.x + s1.y);
+      zi = g_sum<G>(s2.x + s2.y);
+    };
+    ldslot(top, h0);
+    ldslot(top > 0 ? top - 1 : top, h1v);
+    float ua = ldu<float>(ub, j0 + top), ub1 = ldu<float>(ub, j0 + (top > 0 ? top - 1 : top));
+    for (int s = nsw - 1; s >= 0; --s) {
+      const bool act = s < ns;
+      VecP<E> hc = h0;
+      const float uj = ua;
+      if (act) {
+        h0 = h1v;
+        ua = ub1;
+        if (s - 2 >= 0) { ldslot(s - 2, h1v); ub1 = ldu<float>(ub, j0 + s - 2); }
+      }
+      VecP<E> w = pd;
+      op.set_u(uj, ch, lg);
+      cheb_step_p<true, false>(w, dummy, op, ch, Kw, Sw);
+      if (act) pd = w;
+      float zr, zi;
+      zdotp(pd, hc, zr, zi);
+      if (act && lg == 0 && valid) { R2 z; z.x = zr; z.y = zi; tr0[(long)s * GE] = z; }
+    }
+  } else {
     const int top = ns - 1;
     Vec<R, E> h0, h1v;   // slots s and s-1, prefetched
     auto ldslot = [&](int s, Vec<R, E>& h) {
@@ -346,8 +416,8 @@ __global__ void __launch_bounds__(128) k_subinterval(KParams p) {
   __syncwarp();
 
   // ---- FP64 pass over the steps: gradient, Err, ascent step, penalty of J_n
-  const double ht = 0.5 * p.tau * p.w / (p.form ? beta : 1.0);
-  const double tb = p.tau / beta;
+  const double ht = 0.5 * p.tau * p.w / ((p.form && !p.global) ? beta : 1.0);
+  const double tb = p.tau / (p.global ? 1.0 : beta);   // Theorem 2: beta_n g_n is the gradient of J
   const double step = p.rho * beta / p.tau;
   double* gb = p.grad + (long)b * p.Nt;
   double err = 0.0, pen = 0.0;
