@@ -39,7 +39,7 @@ DESCR = {"rotor41": "rigid rotor j<=40, maximise <cos theta>(T)",
          "ising1024": "10-spin open Ising chain, X control, |0^10> -> |1^10>",
          "gp512": "1D Gross-Pitaevskii condensate, 512-point grid, trap centre control, ground -> odd state"}
 SAMPLE_DIV = {"rotor41": 8, "spin16": 1, "ising1024": 64, "gp512": 8}
-BATCH_DEFAULT = {"rotor41": 2048, "spin16": 2048, "ising1024": 8, "gp512": 8}   # independent solves per launch
+BATCH_DEFAULT = {"rotor41": 2048, "spin16": 2048, "ising1024": 64, "gp512": 256}   # independent solves per launch
 SOLVE_ITERS = {"rotor41": 50, "spin16": 20, "ising1024": 20, "gp512": 20}   # oracle sample = Nt/div steps, N/div sub-intervals
 FP32_LANES_PER_SM = 128
 SMS = 152

@@ -102,6 +102,7 @@ struct ism_plan_s {
   void* dtraj2 = nullptr;
   void* dzp = nullptr;              // large d: per-step, per-warp overlap partials
   double* du = nullptr;
+  float* duf = nullptr;             // FP32 copy of the controls (FP32 propagation)
   double* dgrad = nullptr;
   double* dJn = nullptr;
   double* derr = nullptr;
@@ -371,7 +372,7 @@ ism::KParams kparams(ism_plan_s* P, double* u) {
   k.count = P->dcount;
   k.psin = P->dpsin; k.chin = P->dchin; k.form = 0;
   k.update = 0; k.max_spin = P->max_spin;
-  k.psi_i = P->dpsi_i; k.psi_f = P->dpsi_f; k.O = P->dO; k.obj = P->obj;
+  k.psi_i = P->dpsi_i; k.psi_f = P->dpsi_f; k.O = P->dO; k.obj = P->obj; k.uf = P->duf;
   k.psin_w = P->dpsin; k.chin_w = P->dchin; k.zp = P->dzp;
   return k;
 }
@@ -440,8 +441,16 @@ int stage_in(ism_plan_s* P, const double* src, long n, double* staging, const do
     *out = src;
     return ISM_OK;
   }
-  if (check && !all_finite(src, n)) return fail(ISM_ENONFINITE, "non-finite value in an input array");
+  // host data: copy, then check on the device (a host pass over a large batch of controls would
+  // cost more than the copy); a non-finite value surfaces as ISM_ENONFINITE when the call finishes
   ISM_CUDA_TRY(cudaMemcpyAsync(staging, src, n * sizeof(double), cudaMemcpyHostToDevice, P->st));
+  if (check) {
+    int blocks = (int)std::min<long>(1024, (n + 255) / 256);
+    if (blocks < 1) blocks = 1;
+    k_check_finite<<<blocks, 256, 0, P->st>>>(staging, n, P->dstatus);
+    P->kernels += 1;
+    ISM_CUDA_TRY(cudaGetLastError());
+  }
   *out = staging;
   return ISM_OK;
 }
@@ -623,6 +632,7 @@ int plan_build(const ism_problem* prob, const ism_options* opt, void* cuda_strea
     P->dzp = dZ;
   }
   TRY_ALLOC(P->du, B * P->Nt);
+  TRY_ALLOC(P->duf, B * P->Nt);
   TRY_ALLOC(P->dgrad, B * P->Nt);
   TRY_ALLOC(P->dJn, B * P->N);
   TRY_ALLOC(P->derr, B * P->N);
@@ -856,14 +866,20 @@ int ism_iterate(ism_plan_t P, int iters, double* u_inout, double* J_hist, double
     }
   }
   if (J_hist && (rc = run_states(P, ud, P->dJhist, (int)stride, iters))) return rc;
-  if (!dev_u) ISM_CUDA_TRY(cudaMemcpyAsync(u_inout, ud, nu * sizeof(double), cudaMemcpyDeviceToHost, P->st));
+  if (!dev_u) {   // the updated controls: checked on the device, then copied back
+    int blocks = (int)std::min<long>(1024, (nu + 255) / 256);
+    if (blocks < 1) blocks = 1;
+    k_check_finite<<<blocks, 256, 0, P->st>>>(ud, nu, P->dstatus);
+    P->kernels += 1;
+    ISM_CUDA_TRY(cudaGetLastError());
+    ISM_CUDA_TRY(cudaMemcpyAsync(u_inout, ud, nu * sizeof(double), cudaMemcpyDeviceToHost, P->st));
+  }
   // J_hist is [B][iters+1]; err_hist is [B][iters] (packed from the stride-(iters+1) device rows)
   if (J_hist) ISM_CUDA_TRY(cudaMemcpyAsync(J_hist, P->dJhist, (size_t)P->B * stride * sizeof(double), cudaMemcpyDefault, P->st));
   if (err_hist && iters > 0)
     ISM_CUDA_TRY(cudaMemcpy2DAsync(err_hist, iters * sizeof(double), P->derrhist, stride * sizeof(double),
                                    iters * sizeof(double), P->B, cudaMemcpyDefault, P->st));
   if ((rc = finish(P))) return rc;
-  if (!dev_u && !all_finite(u_inout, nu)) return fail(ISM_ENONFINITE, "controls became non-finite");
   return ISM_OK;
 }
 

@@ -43,6 +43,7 @@ struct KParams {
   int global;                  // form 1 only: scale the gradient to the full objective (beta_n g_n)
   int update;
   int max_spin;
+  float* uf;                   // [B][Nt] FP32 copy of u (written by k_cheb_prep)
   // direct global sweeps (large d): inputs and FP64 outputs, per-warp overlap partials
   const double2* psi_i;        // [d]
   const double2* psi_f;        // [d]
@@ -82,6 +83,12 @@ struct ChainParams {
 
 template <typename R> __device__ __forceinline__ R ldu_ro(const double* u, long i) { return (R)__ldg(u + i); }
 template <typename R> __device__ __forceinline__ R ldu(const double* u, long i) { return (R)u[i]; }
+// A control in the propagation precision: FP32 sweeps read the FP32 copy that k_cheb_prep writes
+// (a conversion from FP64 would run on the FP64 pipe at every step).
+template <typename R> __device__ __forceinline__ R uval(const double* u, const float* uf, long i) {
+  if constexpr (sizeof(R) == 4) return __ldg(uf + i);
+  else return __ldg(u + i);
+}
 
 // Work accounting: one group adds its applications of Y, accumulated series terms and exp sub-steps.
 template <typename R>
@@ -116,6 +123,7 @@ __global__ void __launch_bounds__(128, Op::ASM_MINB) k_assemble(KParams p) {
   const int n = (int)(bn % p.N), b = (int)(bn / p.N);
   const int j0 = p.jn[n], j1 = p.jn[n + 1];
   const double* ub = p.u + (long)b * p.Nt;
+  const float* ufb = p.uf + (long)b * p.Nt;
 
   Cheb<R>& ch = chs[gib];
   int Kw, Sw;
@@ -132,11 +140,11 @@ __global__ void __launch_bounds__(128, Op::ASM_MINB) k_assemble(KParams p) {
       pv.z[r] = make_float2((lg * E + r == col) ? 1.f : 0.f, 0.f);
       pl.z[r] = make_float2(0.f, 0.f);
     }
-    float ua = ldu_ro<float>(ub, j0), ub1 = j0 + 1 < j1 ? ldu_ro<float>(ub, j0 + 1) : 0.f;
+    float ua = __ldg(ufb + (j0)), ub1 = j0 + 1 < j1 ? __ldg(ufb + (j0 + 1)) : 0.f;
     for (int j = j0; j < j1; ++j) {
       const float uj = ua;
       ua = ub1;
-      if (j + 2 < j1) ub1 = ldu_ro<float>(ub, j + 2);
+      if (j + 2 < j1) ub1 = __ldg(ufb + (j + 2));
       op.set_u(uj, ch, lg);
       cheb_step_p<false, true>(pv, pl, op, ch, Kw, Sw);
     }
@@ -155,11 +163,11 @@ __global__ void __launch_bounds__(128, Op::ASM_MINB) k_assemble(KParams p) {
     }
 
     // controls two steps ahead in registers
-    R ua = ldu_ro<R>(ub, j0), ub1 = j0 + 1 < j1 ? ldu_ro<R>(ub, j0 + 1) : R(0);
+    R ua = uval<R>(ub, ufb, j0), ub1 = j0 + 1 < j1 ? uval<R>(ub, ufb, j0 + 1) : R(0);
     for (int j = j0; j < j1; ++j) {
       const R uj = ua;
       ua = ub1;
-      if (j + 2 < j1) ub1 = ldu_ro<R>(ub, j + 2);
+      if (j + 2 < j1) ub1 = uval<R>(ub, ufb, j + 2);
       op.set_u(uj, ch, lg);
       cheb_step<false, COMP>(v, lo, op, ch, Kw, Sw);
     }
@@ -210,6 +218,7 @@ __global__ void __launch_bounds__(128) k_subinterval(KParams p) {
   const int j0 = p.jn[n], j1 = p.jn[n + 1], ns = j1 - j0;
   const int nsw = warp_max_i(ns);
   double* ub = p.u + (long)b * p.Nt;
+  const float* ufb = p.uf + (long)b * p.Nt;
   const double beta = p.beta[n];
 
   Cheb<R>& ch = chs[gib];
@@ -252,12 +261,12 @@ __global__ void __launch_bounds__(128) k_subinterval(KParams p) {
 #pragma unroll
     for (int r = 0; r < E; ++r) { pv.z[r] = make_float2(v.re[r], v.im[r]); pl.z[r] = make_float2(lo.re[r], lo.im[r]); }
     float2* trp = reinterpret_cast<float2*>(tr);
-    float ua = ldu<float>(ub, j0), ub1 = ns > 1 ? ldu<float>(ub, j0 + 1) : ua;
+    float ua = ufb[j0], ub1 = ns > 1 ? ufb[j0 + 1] : ua;
     for (int s = 0; s < nsw; ++s) {
       const bool act = s < ns;
       const float uj = ua;
       ua = ub1;
-      if (s + 2 < ns) ub1 = ldu<float>(ub, j0 + s + 2);
+      if (s + 2 < ns) ub1 = ufb[j0 + s + 2];
       VecP<E> hv;
       op.h1_p(pv, hv);
       if (act && valid) {
@@ -277,12 +286,12 @@ __global__ void __launch_bounds__(128) k_subinterval(KParams p) {
       hend.re[r] = he.z[r].x; hend.im[r] = he.z[r].y;
     }
   } else {
-    R ua = ldu<R>(ub, j0), ub1 = ns > 1 ? ldu<R>(ub, j0 + 1) : ua;
+    R ua = uval<R>(ub, ufb, j0), ub1 = ns > 1 ? uval<R>(ub, ufb, j0 + 1) : ua;
     for (int s = 0; s < nsw; ++s) {
       const bool act = s < ns;
       const R uj = ua;
       ua = ub1;
-      if (s + 2 < ns) ub1 = ldu<R>(ub, j0 + s + 2);
+      if (s + 2 < ns) ub1 = uval<R>(ub, ufb, j0 + s + 2);
       Vec<R, E> hv;
       op.h1(v, hv);
       if (act && valid) {
@@ -367,7 +376,7 @@ __global__ void __launch_bounds__(128) k_subinterval(KParams p) {
     };
     ldslot(top, h0);
     ldslot(top > 0 ? top - 1 : top, h1v);
-    float ua = ldu<float>(ub, j0 + top), ub1 = ldu<float>(ub, j0 + (top > 0 ? top - 1 : top));
+    float ua = ufb[j0 + top], ub1 = ufb[j0 + (top > 0 ? top - 1 : top)];
     for (int s = nsw - 1; s >= 0; --s) {
       const bool act = s < ns;
       VecP<E> hc = h0;
@@ -375,7 +384,7 @@ __global__ void __launch_bounds__(128) k_subinterval(KParams p) {
       if (act) {
         h0 = h1v;
         ua = ub1;
-        if (s - 2 >= 0) { ldslot(s - 2, h1v); ub1 = ldu<float>(ub, j0 + s - 2); }
+        if (s - 2 >= 0) { ldslot(s - 2, h1v); ub1 = ufb[j0 + s - 2]; }
       }
       VecP<E> w = pd;
       op.set_u(uj, ch, lg);
@@ -394,7 +403,7 @@ __global__ void __launch_bounds__(128) k_subinterval(KParams p) {
     };
     ldslot(top, h0);
     ldslot(top > 0 ? top - 1 : top, h1v);
-    R ua = ldu<R>(ub, j0 + top), ub1 = ldu<R>(ub, j0 + (top > 0 ? top - 1 : top));
+    R ua = uval<R>(ub, ufb, j0 + top), ub1 = uval<R>(ub, ufb, j0 + (top > 0 ? top - 1 : top));
     for (int s = nsw - 1; s >= 0; --s) {
       const bool act = s < ns;
       Vec<R, E> hc = h0;
@@ -402,7 +411,7 @@ __global__ void __launch_bounds__(128) k_subinterval(KParams p) {
       if (act) {
         h0 = h1v;
         ua = ub1;
-        if (s - 2 >= 0) { ldslot(s - 2, h1v); ub1 = ldu<R>(ub, j0 + s - 2); }
+        if (s - 2 >= 0) { ldslot(s - 2, h1v); ub1 = uval<R>(ub, ufb, j0 + s - 2); }
       }
       Vec<R, E> w = dl;
       op.set_u(uj, ch, lg);
@@ -466,8 +475,10 @@ __global__ void __launch_bounds__(32) k_cheb_prep(KParams p) {
   const double* ub = p.u + (long)b * p.Nt;
   float um = 0.f;   // |u| bound; the margin in cheb_params covers its FP32 rounding
   double pen = 0.0;
+  float* ufb = p.uf ? p.uf + (long)b * p.Nt : nullptr;
   for (int j = j0 + lane; j < j1; j += 32) {
     const double uj = ub[j];
+    if (ufb) ufb[j] = (float)uj;
     um = fmaxf(um, fabsf((float)uj));
     if (p.alpha) pen += p.alpha[j] * uj * uj;
   }
@@ -515,6 +526,7 @@ __global__ void __launch_bounds__(128) k_sweeps2(KParams p) {
   const int j0 = p.jn[n], j1 = p.jn[n + 1], ns = j1 - j0;
   const int nsw = warp_max_i(ns);
   const double* ub = p.u + (long)b * p.Nt;
+  const float* ufb = p.uf + (long)b * p.Nt;
 
   Cheb<R>& ch = chs[gib];
   int Kw, Sw;
@@ -551,12 +563,12 @@ __global__ void __launch_bounds__(128) k_sweeps2(KParams p) {
       }
     };
     if (fwd) {
-      float ua = ldu<float>(ub, j0), ub1 = ns > 1 ? ldu<float>(ub, j0 + 1) : ua;
+      float ua = ufb[j0], ub1 = ns > 1 ? ufb[j0 + 1] : ua;
       for (int s = 0; s < nsw; ++s) {
         const bool act = s < ns;
         const float uj = ua;
         ua = ub1;
-        if (s + 2 < ns) ub1 = ldu<float>(ub, j0 + s + 2);
+        if (s + 2 < ns) ub1 = ufb[j0 + s + 2];
         VecP<E> hv;
         op.h1_p(pv, hv);
         if (act) putp(s, hv);
@@ -571,13 +583,13 @@ __global__ void __launch_bounds__(128) k_sweeps2(KParams p) {
     } else {
       putp(ns, pv);
       const int top = ns - 1;
-      float ua = ldu<float>(ub, j0 + top), ub1 = ldu<float>(ub, j0 + (top > 0 ? top - 1 : top));
+      float ua = ufb[j0 + top], ub1 = ufb[j0 + (top > 0 ? top - 1 : top)];
       for (int s = nsw - 1; s >= 0; --s) {
         const bool act = s < ns;
         const float uj = ua;
         if (act) {
           ua = ub1;
-          if (s - 2 >= 0) ub1 = ldu<float>(ub, j0 + s - 2);
+          if (s - 2 >= 0) ub1 = ufb[j0 + s - 2];
         }
         VecP<E> w = pv, wl = pl;
         op.set_u(uj, ch, lg);
@@ -593,12 +605,12 @@ __global__ void __launch_bounds__(128) k_sweeps2(KParams p) {
       }
     };
     if (fwd) {
-      R ua = ldu<R>(ub, j0), ub1 = ns > 1 ? ldu<R>(ub, j0 + 1) : ua;
+      R ua = uval<R>(ub, ufb, j0), ub1 = ns > 1 ? uval<R>(ub, ufb, j0 + 1) : ua;
       for (int s = 0; s < nsw; ++s) {
         const bool act = s < ns;
         const R uj = ua;
         ua = ub1;
-        if (s + 2 < ns) ub1 = ldu<R>(ub, j0 + s + 2);
+        if (s + 2 < ns) ub1 = uval<R>(ub, ufb, j0 + s + 2);
         Vec<R, E> hv;
         op.h1(v, hv);
         if (act) put(s, hv);
@@ -613,13 +625,13 @@ __global__ void __launch_bounds__(128) k_sweeps2(KParams p) {
     } else {
       put(ns, v);
       const int top = ns - 1;
-      R ua = ldu<R>(ub, j0 + top), ub1 = ldu<R>(ub, j0 + (top > 0 ? top - 1 : top));
+      R ua = uval<R>(ub, ufb, j0 + top), ub1 = uval<R>(ub, ufb, j0 + (top > 0 ? top - 1 : top));
       for (int s = nsw - 1; s >= 0; --s) {
         const bool act = s < ns;
         const R uj = ua;
         if (act) {
           ua = ub1;
-          if (s - 2 >= 0) ub1 = ldu<R>(ub, j0 + s - 2);
+          if (s - 2 >= 0) ub1 = uval<R>(ub, ufb, j0 + s - 2);
         }
         Vec<R, E> w = v, wl = lo;
         op.set_u(uj, ch, lg);
@@ -665,6 +677,7 @@ __global__ void __launch_bounds__(128) k_gsweep(KParams p) {
   const int b = (int)gid, dir = (int)blockIdx.y;
   const int d = p.d, N = p.N;
   const double* ub = p.u + (long)b * p.Nt;
+  const float* ufb = p.uf + (long)b * p.Nt;
   double2* psin = p.psin_w + (long)b * (N + 1) * d;
   double2* chin = p.chin_w + (long)b * (N + 1) * d;
   Cheb<R>& ch = chs[gib];
@@ -707,17 +720,28 @@ __global__ void __launch_bounds__(128) k_gsweep(KParams p) {
       VecP<E> pv, pl;
 #pragma unroll
       for (int r = 0; r < E; ++r) { pv.z[r] = make_float2(v.re[r], v.im[r]); pl.z[r] = make_float2(lo.re[r], lo.im[r]); }
-      for (int s = 0; s < j1 - j0; ++s) {
-        const int j = ADJ ? j1 - 1 - s : j0 + s;
-        op.set_u(ldu_ro<float>(ub, j), ch, lg);
+      // controls two steps ahead in registers: the sweep's steps are its critical path
+      const int ns = j1 - j0;
+      auto jof = [&](int s) { return ADJ ? j1 - 1 - s : j0 + s; };
+      float ua = __ldg(ufb + jof(0)), ub1 = ns > 1 ? __ldg(ufb + jof(1)) : 0.f;
+      for (int s = 0; s < ns; ++s) {
+        const float uj = ua;
+        ua = ub1;
+        if (s + 2 < ns) ub1 = __ldg(ufb + jof(s + 2));
+        op.set_u(uj, ch, lg);
         cheb_step_p<ADJ, true>(pv, pl, op, ch, Kw, Sw);
       }
 #pragma unroll
       for (int r = 0; r < E; ++r) { v.re[r] = pv.z[r].x; v.im[r] = pv.z[r].y; lo.re[r] = pl.z[r].x; lo.im[r] = pl.z[r].y; }
     } else {
-      for (int s = 0; s < j1 - j0; ++s) {
-        const int j = ADJ ? j1 - 1 - s : j0 + s;
-        op.set_u(ldu_ro<R>(ub, j), ch, lg);
+      const int ns = j1 - j0;
+      auto jof = [&](int s) { return ADJ ? j1 - 1 - s : j0 + s; };
+      R ua = uval<R>(ub, ufb, jof(0)), ub1 = ns > 1 ? uval<R>(ub, ufb, jof(1)) : R(0);
+      for (int s = 0; s < ns; ++s) {
+        const R uj = ua;
+        ua = ub1;
+        if (s + 2 < ns) ub1 = uval<R>(ub, ufb, jof(s + 2));
+        op.set_u(uj, ch, lg);
         cheb_step<ADJ, COMP>(v, lo, op, ch, Kw, Sw);
       }
     }

@@ -167,6 +167,7 @@ __global__ void __launch_bounds__(Op::NT) k_lsweep(KParams p) {
   const int b = blockIdx.y, N = p.N;
   const bool single = gridDim.x == 1;
   const double* ub = p.u + (long)b * p.Nt;
+  const float* ufb = p.uf + (long)b * p.Nt;
   double2* psin = p.psin_w + (long)b * (N + 1) * D;
   double2* chin = p.chin_w + (long)b * (N + 1) * D;
   Op op;
@@ -180,10 +181,10 @@ __global__ void __launch_bounds__(Op::NT) k_lsweep(KParams p) {
       cheb_load_cta<R>(ch, p.cheb, (long)b * N + n);
       op.scale(p.H0d, ch);
       const int j0 = p.jn[n], j1 = p.jn[n + 1];
-      R un = ldu_ro<R>(ub, j0);
+      R un = uval<R>(ub, ufb, j0);
       for (int j = j0; j < j1; ++j) {
         const R uj = un;
-        if (j + 1 < j1) un = ldu_ro<R>(ub, j + 1);
+        if (j + 1 < j1) un = uval<R>(ub, ufb, j + 1);
         op.set_u(uj, ch, 0);
         cheb_step<false, COMP>(v, lo, op, ch, ch.K, ch.S);
       }
@@ -218,10 +219,10 @@ __global__ void __launch_bounds__(Op::NT) k_lsweep(KParams p) {
       cheb_load_cta<R>(ch, p.cheb, (long)b * N + n);
       op.scale(p.H0d, ch);
       const int j0 = p.jn[n], j1 = p.jn[n + 1];
-      R un = ldu_ro<R>(ub, j1 - 1);
+      R un = uval<R>(ub, ufb, j1 - 1);
       for (int j = j1 - 1; j >= j0; --j) {
         const R uj = un;
-        if (j - 1 >= j0) un = ldu_ro<R>(ub, j - 1);
+        if (j - 1 >= j0) un = uval<R>(ub, ufb, j - 1);
         op.set_u(uj, ch, 0);
         cheb_step<true, COMP>(v, lo, op, ch, ch.K, ch.S);
       }
@@ -246,6 +247,7 @@ __global__ void __launch_bounds__(Op::NT) k_lsub(KParams p) {
   const int n = blockIdx.x, b = blockIdx.y, t = threadIdx.x, lane = t & 31, wid = t >> 5;
   const int j0 = p.jn[n], j1 = p.jn[n + 1], ns = j1 - j0;
   double* ub = p.u + (long)b * p.Nt;
+  const float* ufb = p.uf + (long)b * p.Nt;
   const double beta = p.beta[n];
   cheb_load_cta<R>(ch, p.cheb, (long)b * p.N + n);
   Op op;
@@ -266,10 +268,10 @@ __global__ void __launch_bounds__(Op::NT) k_lsub(KParams p) {
 
   // ---- forward sweep: store H1 psi_j, then psi_{j+1} = U_j psi_j
   {
-    R un = ldu<R>(ub, j0);
+    R un = uval<R>(ub, ufb, j0);
     for (int s = 0; s < ns; ++s) {
       const R uj = un;
-      if (s + 1 < ns) un = ldu<R>(ub, j0 + s + 1);
+      if (s + 1 < ns) un = uval<R>(ub, ufb, j0 + s + 1);
       Vec<R, E> hv;
       op.h1(v, hv);
 #pragma unroll
@@ -331,11 +333,11 @@ __global__ void __launch_bounds__(Op::NT) k_lsub(KParams p) {
     };
     Vec<R, E> hn;
     ldslot(ns - 1, hn);
-    R un = ldu<R>(ub, j1 - 1);
+    R un = uval<R>(ub, ufb, j1 - 1);
     for (int s = ns - 1; s >= 0; --s) {
       const Vec<R, E> hc = hn;
       const R uj = un;
-      if (s >= 1) { ldslot(s - 1, hn); un = ldu<R>(ub, j0 + s - 1); }
+      if (s >= 1) { ldslot(s - 1, hn); un = uval<R>(ub, ufb, j0 + s - 1); }
       op.set_u(uj, ch, 0);
       cheb_step<true>(dl, op, ch, K, S);
       zdot(dl, hc, zp0 + (long)s * W);

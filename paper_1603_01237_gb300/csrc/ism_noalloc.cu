@@ -85,7 +85,7 @@ extern "C" int ism_subinterval_grad_noalloc(const ism_problem* prob, int precisi
   else { hf = ism::pack_op<float>(p.kind, d, p.H0, p.H1, ks.G, ks.E); op_bytes = hf.size() * r1; }
 
   // scratch layout: op data | FP64 diag(H0) | j_n | beta_n | alpha | status | propagator parameters |
-  // Bessel table | trajectory
+  // Bessel table | FP32 controls | trajectory
   const size_t off_h0d = up256(op_bytes);
   const size_t off_jn = off_h0d + up256(sizeof(double) * d);
   const size_t off_beta = off_jn + up256(sizeof(int) * (p.N + 1));
@@ -93,7 +93,8 @@ extern "C" int ism_subinterval_grad_noalloc(const ism_problem* prob, int precisi
   const size_t off_status = off_alpha + up256(p.alpha ? sizeof(double) * p.Nt : 0);
   const size_t off_cheb = off_status + 256;
   const size_t off_ctab = off_cheb + up256((size_t)B * p.N * ism::cheb_bytes(precision));
-  const size_t off_traj = off_ctab + up256(sizeof(double) * ism::BESSEL_TABLE);
+  const size_t off_uf = off_ctab + up256(sizeof(double) * ism::BESSEL_TABLE);
+  const size_t off_traj = off_uf + up256(sizeof(float) * (size_t)B * p.Nt);
   const size_t need = off_traj + up256((size_t)B * ((size_t)p.Nt + p.N) * GE * r2);
   if (need > kScratchBytes) {
     std::string m = "problem needs " + std::to_string(need) + " bytes of scratch; the static scratch of the "
@@ -155,6 +156,7 @@ extern "C" int ism_subinterval_grad_noalloc(const ism_problem* prob, int precisi
   k.max_spin = 1 << 22;
   k.cheb = base + off_cheb;
   k.pen = nullptr;
+  k.uf = reinterpret_cast<float*>(base + off_uf);
   k.ctab = reinterpret_cast<const double*>(base + off_ctab);
   if ((e = ism::launch_cheb_prep(precision, k, st)) != cudaSuccess)
     return ism::set_error(ISM_ECUDA, (std::string("launch: ") + cudaGetErrorString(e)).c_str());
