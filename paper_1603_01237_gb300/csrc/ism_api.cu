@@ -86,6 +86,7 @@ struct ism_plan_s {
   int* djn = nullptr;
   double* dbeta = nullptr;
   double2* dab = nullptr;   // (a_n, b_n), n = 0..N
+  double2* dphase = nullptr;   // (cos, sin) of c0 tau (steps of sub-interval n)
   unsigned char* dcheb = nullptr;   // propagator parameters per (problem, n)
   unsigned char* dstage = nullptr;  // chain results before FP64 conversion
   double* dpen = nullptr;           // penalty sums per (problem, n)
@@ -366,7 +367,7 @@ ism::KParams kparams(ism_plan_s* P, double* u) {
   k.tau = P->tau; k.T = P->T; k.c0 = P->c0; k.r0 = P->r0; k.h1n = P->h1n; k.tol = P->tol;
   k.rho = P->rho; k.w = P->w;
   k.jn = P->djn; k.beta = P->dbeta; k.alpha = P->dalpha; k.H = P->dH; k.H0d = P->dH0d;
-  k.cheb = P->dcheb; k.ctab = P->dctab; k.pen = P->dpen;
+  k.cheb = P->dcheb; k.ctab = P->dctab; k.pen = P->dpen; k.phase = P->dphase;
   k.u = u; k.phi = P->dphi; k.M = P->dM; k.traj = P->dtraj; k.traj2 = P->dtraj2;
   k.grad = P->dgrad; k.Jn = P->dJn; k.err = P->derr; k.status = P->dstatus;
   k.count = P->dcount;
@@ -603,6 +604,7 @@ int plan_build(const ism_problem* prob, const ism_options* opt, void* cuda_strea
   TRY_ALLOC(P->djn, (size_t)P->N + 1);
   TRY_ALLOC(P->dbeta, (size_t)P->N);
   TRY_ALLOC(P->dab, (size_t)P->N + 1);
+  TRY_ALLOC(P->dphase, (size_t)P->N);
   TRY_ALLOC(P->dcheb, B * P->N * ism::cheb_bytes(P->prec));
   if (!P->ks.large && !P->direct) TRY_ALLOC(P->dstage, B * 2 * ((size_t)P->N + 1) * d * P->r2);
   TRY_ALLOC(P->dpen, B * P->N);
@@ -664,6 +666,12 @@ int plan_build(const ism_problem* prob, const ism_options* opt, void* cuda_strea
     h2d(P->dctab, tab.data(), tab.size() * sizeof(double));
   }
   h2d(P->dbeta, beta.data(), beta.size() * sizeof(double));
+  std::vector<double2> phase(P->N);   // the global phase of each segment, once per plan
+  for (int n = 0; n < P->N; ++n) {
+    const double ph = P->c0 * P->tau * (double)(jn[n + 1] - jn[n]);
+    phase[n] = make_double2(std::cos(ph), std::sin(ph));
+  }
+  h2d(P->dphase, phase.data(), phase.size() * sizeof(double2));
   {
     std::vector<double2> ab(P->N + 1);   // Eq. (cible): a_n = (T - t_n)/T, b_n = t_n/T
     for (int n = 0; n <= P->N; ++n) {

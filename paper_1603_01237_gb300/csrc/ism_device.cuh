@@ -96,12 +96,13 @@ template <typename R> __device__ __forceinline__ void split2(double v, R& hi, R&
 // Chebyshev parameters of one sub-interval, computed by one warp (lane k evaluates J_k).
 // J_k(x) = (x/2)^k sum_m (-x^2/4)^m / (m! (m+k)!) by Horner's rule on the table
 // ctab[k * (BESSEL_M + 1) + m] = 1 / (m! (m+k)!) (FP64, built on the host): no divisions on the device,
-// whose FP64 rate is low.  umax bounds |u| on the sub-interval; nsteps gives the segment phase.
+// whose FP64 rate is low.  umax bounds |u| on the sub-interval; phase = (cos, sin) of the segment's
+// global phase c0 tau (steps), computed on the host.
 constexpr int BESSEL_M = 24;
 
 template <typename R>
 __device__ void cheb_params(Cheb<R>& ch, const double* ctab, double tau, double c0, double r0, double h1n,
-                            double umax, double tol, int nsteps, int* status) {
+                            double umax, double tol, double2 phase, int* status) {
   const int lane = threadIdx.x & 31;
   const double rad = (r0 + umax * h1n) * (1.0 + 1e-6) + 1e-12;
   const double x = tau * rad;
@@ -113,12 +114,27 @@ __device__ void cheb_params(Cheb<R>& ch, const double* ctab, double tau, double 
   }
   const double xs = x / (double)S;
   const double y = -0.25 * xs * xs, h = 0.5 * xs;
+  // terms of the series needed: |y|^m / (m!)^2 (the k = 0 ratio, the slowest) below 1e-19; FP64
+  // work is scarce on this GPU, and small steps need only a few terms (x = 0.13: 6 of 24)
+  int M = 1;
+  {
+    const float ay = (float)fabs(y);
+    float t = 1.f;
+    while (M < BESSEL_M) {
+      t *= ay / (float)(M * M);
+      if (t < 1e-19f) break;
+      ++M;
+    }
+  }
   const int k = lane;   // KMAX == 32 == warp size
   const double* c = ctab + k * (BESSEL_M + 1);
-  double acc = c[BESSEL_M];
-  for (int m = BESSEL_M - 1; m >= 0; --m) acc = fma(acc, y, c[m]);
-  double pw = 1.0;
-  for (int i = 0; i < k; ++i) pw *= h;
+  double acc = c[M];
+  for (int m = M - 1; m >= 0; --m) acc = fma(acc, y, c[m]);
+  double pw = 1.0, base = h;   // h^k by squaring
+  for (int e = k; e; e >>= 1) {
+    if (e & 1) pw *= base;
+    base *= base;
+  }
   const double a = acc * pw * (k == 0 ? 1.0 : 2.0);
   int kneed = fabs(a) >= tol ? k + 1 : 0;
   kneed = warp_max_i(kneed);
@@ -127,8 +143,8 @@ __device__ void cheb_params(Cheb<R>& ch, const double* ctab, double tau, double 
   split2<R>(sg * a, ch.cf[k], ch.cl[k]);
   if (lane == 0) {
     // a_0 - 1 = sum_{m>=1} y^m / (m!)^2 without cancellation
-    double t = ctab[BESSEL_M];
-    for (int m = BESSEL_M - 1; m >= 1; --m) t = fma(t, y, ctab[m]);
+    double t = ctab[M];
+    for (int m = M - 1; m >= 1; --m) t = fma(t, y, ctab[m]);
     const double j0m1 = t * y;
     split2<R>(1.0 + j0m1, ch.a0h, ch.a0l);
     split2<R>(j0m1, ch.c0h, ch.c0l);
@@ -136,10 +152,8 @@ __device__ void cheb_params(Cheb<R>& ch, const double* ctab, double tau, double 
     ch.inv_rad = (R)(1.0 / rad);
     ch.cd = c0;
     ch.s2d = 2.0 / rad;
-    double sn, cs;
-    sincos(c0 * tau * (double)nsteps, &sn, &cs);
-    ch.cph = cs;
-    ch.sph = sn;
+    ch.cph = phase.x;   // cos, sin of c0 * tau * (steps of the sub-interval), from the host
+    ch.sph = phase.y;
     ch.K = kneed < 2 ? 2 : kneed;
     ch.S = S;
   }

@@ -106,14 +106,16 @@ __device__ __forceinline__ void dft8(typename C2<R>::T* v) {
 }
 
 struct Ident {
+  template <class T> __device__ __forceinline__ T operator()(int, int, T v) const { return v; }
   template <class T> __device__ __forceinline__ T operator()(int, T v) const { return v; }
 };
 
 // Stockham radix-8 FFT (unnormalised) of length n = 8^P from x, using y as the other buffer; twiddle
 // table W[m] + Wl[m] = exp(-2 pi i m / n) (hi + lo).  Every thread of the block calls it; threads
 // t < n/8 compute.
-// pre(m, v) is applied to every input element as the first pass loads it, post(m, v) to every output
-// element as the last pass stores it, so pointwise factors cost no pass and no barrier of their own.
+// pre(m, r, v) is applied to every input element as the first pass loads it (thread t loads elements
+// m = t + r n/8, r = 0..7), post(m, v) to every output element as the last pass stores it, so
+// pointwise factors cost no pass and no barrier of their own.
 // Returns the buffer that holds the result.
 template <typename R, bool INV, class Pre = Ident, class Post = Ident>
 __device__ typename C2<R>::T* fft8(typename C2<R>::T* x, typename C2<R>::T* y, const typename C2<R>::T* W,
@@ -128,7 +130,7 @@ __device__ typename C2<R>::T* fft8(typename C2<R>::T* x, typename C2<R>::T* y, c
 #pragma unroll
       for (int r = 0; r < 8; ++r) {
         const int m = t + r * q;
-        v[r] = Ns == 1 ? pre(m, x[m]) : x[m];
+        v[r] = Ns == 1 ? pre(m, r, x[m]) : x[m];
       }
       const int step = n / (Ns << 3);
 #pragma unroll
@@ -257,7 +259,7 @@ struct GP {
   __device__ void step(double u, T* keep) {
     const R ur = (R)u, tr = (R)tau;
     const GP* self = this;
-    kinetic<false, true>(A, [self, ur, tr, keep](int m, T a) {
+    kinetic<false, true>(A, [self, ur, tr, keep](int m, int, T a) {
       if (keep) keep[m] = a;
       const T e = expm1i<T, R>(-tr * self->theta(m, ur, a));
       return cadd(a, cmul(e, a));
@@ -278,13 +280,15 @@ struct GP {
   // adjoint step at a_j (global, complex R, per element): A holds nu_{j+1} on entry and nu_j on exit;
   // the pointwise part runs as the first FFT pass loads each element.  GRAD: also return dJ/du_j
   // (FP64 block sum of FP32 per-thread partials); the global adjoint sweep needs only the states.
+  // aj[r] = a_j at element t + r n/8 (this thread's elements of the first FFT pass), loaded by the
+  // caller one step ahead so that the global-memory latency is off the step's critical path.
   template <bool GRAD>
-  __device__ double adjoint_step(const T* aj, double u) {
+  __device__ double adjoint_step(const T (&aj)[8], double u) {
     const R ur = (R)u, tr = (R)tau, f2 = R(2) * (R)tau * (R)g;
     R part = R(0);
     const GP* self = this;
-    kinetic<true, true>(A, [self, aj, ur, tr, f2, &part](int m, T nu) {
-      const T a = aj[m];
+    kinetic<true, true>(A, [self, &aj, ur, tr, f2, &part](int m, int r, T nu) {
+      const T a = aj[r];
       const T e = expm1i<T, R>(tr * self->theta(m, ur, a));
       const T mu = cadd(nu, cmul(e, nu));
       const R im = mu.x * a.y - mu.y * a.x;   // Im(conj(mu) a)
@@ -299,6 +303,15 @@ struct GP {
     return tau * dx * sum((double)part);
   }
 };
+
+// This thread's 8 first-pass elements of a stored row (threads beyond n/8 load nothing).
+template <typename T> __device__ __forceinline__ void ld_row8(T (&a)[8], const T* row, int n) {
+  const int t = threadIdx.x, q = n >> 3;
+  if (t < q) {
+#pragma unroll
+    for (int r = 0; r < 8; ++r) a[r] = row[t + r * q];
+  }
+}
 
 template <typename R> __device__ __forceinline__ typename C2<R>::T ld_state(const double2* src, int m) {
   typename C2<R>::T v;
@@ -377,8 +390,13 @@ __global__ void k_gp_adjoint(GPParams p) {
   __syncthreads();
   s.kinetic<true, false>(s.A);   // nu_Nt = K^H psi_f
   int nn = p.N - 1;
+  T acur[8], anext[8];
+  ld_row8(acur, traj + (long)(p.Nt - 1) * n, n);
   for (int j = p.Nt - 1; j >= 0; --j) {
-    s.template adjoint_step<false>(traj + (long)j * n, ub[j]);
+    if (j > 0) ld_row8(anext, traj + (long)(j - 1) * n, n);
+    s.template adjoint_step<false>(acur, ub[j]);
+#pragma unroll
+    for (int r = 0; r < 8; ++r) acur[r] = anext[r];
     if (nn >= 0 && j == p.jn[nn]) {   // chi(t_n) = lambda_j = K nu_j
       for (int m = threadIdx.x; m < n; m += blockDim.x) s.C[m] = s.A[m];
       __syncthreads();
@@ -428,9 +446,14 @@ __global__ void k_gp_sub(GPParams p) {
   s.kinetic<true, false>(s.A);
   double err = 0.0;
   double* gb = p.grad + (long)b * p.Nt;
+  T acur[8], anext[8];
+  ld_row8(acur, traj + (long)(j1 - 1) * n, n);
   for (int j = j1 - 1; j >= j0; --j) {
     const double uj = ub[j];
-    const double gj = s.template adjoint_step<true>(traj + (long)j * n, uj);
+    if (j > j0) ld_row8(anext, traj + (long)(j - 1) * n, n);
+    const double gj = s.template adjoint_step<true>(acur, uj);
+#pragma unroll
+    for (int r = 0; r < 8; ++r) acur[r] = anext[r];
     err += fabs(gj);
     if (threadIdx.x == 0) {
       gb[j] = gj;

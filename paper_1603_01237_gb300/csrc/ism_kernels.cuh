@@ -26,6 +26,7 @@ struct KParams {
   const void* cheb;       // [B][N] Cheb<R>: propagator parameters per sub-interval (k_cheb_prep)
   double* pen;            // [B][N] sum_j alpha_j u_j^2 per sub-interval (k_cheb_prep), or null
   const double* ctab;     // Bessel series table for k_cheb_prep
+  const double2* phase;   // [N] (cos, sin) of c0 tau (j_{n+1} - j_n), the segment phases
   double* u;              // [B][Nt]
   const double2* phi;     // [B][N+1][d]
   void* M;                // [B][N] tiles of tile_stride R2: [d cols][ldm rows], ldm odd >= d
@@ -488,7 +489,7 @@ __global__ void __launch_bounds__(32) k_cheb_prep(KParams p) {
   }
   if (lane == 0 && p.pen) p.pen[(long)b * p.N + n] = pen;
   __shared__ Cheb<R> ch;
-  cheb_params<R>(ch, p.ctab, p.tau, p.c0, p.r0, p.h1n, (double)um, p.tol, j1 - j0, p.status);
+  cheb_params<R>(ch, p.ctab, p.tau, p.c0, p.r0, p.h1n, (double)um, p.tol, p.phase[n], p.status);
   __syncwarp();
   const int* s = reinterpret_cast<const int*>(&ch);
   int* d = reinterpret_cast<int*>(const_cast<void*>(p.cheb)) + ((long)b * p.N + n) * (sizeof(Cheb<R>) / sizeof(int));

@@ -14,6 +14,7 @@
 // start at zero (the status word) is cleared at the start of every call, everything else is written
 // before it is read.  Two calls whose work overlaps on the GPU (different streams, or different host
 // threads on one device) race on the array.
+#include <cmath>
 #include <cstring>
 #include <mutex>
 #include <string>
@@ -85,7 +86,7 @@ extern "C" int ism_subinterval_grad_noalloc(const ism_problem* prob, int precisi
   else { hf = ism::pack_op<float>(p.kind, d, p.H0, p.H1, ks.G, ks.E); op_bytes = hf.size() * r1; }
 
   // scratch layout: op data | FP64 diag(H0) | j_n | beta_n | alpha | status | propagator parameters |
-  // Bessel table | FP32 controls | trajectory
+  // Bessel table | segment phases | FP32 controls | trajectory
   const size_t off_h0d = up256(op_bytes);
   const size_t off_jn = off_h0d + up256(sizeof(double) * d);
   const size_t off_beta = off_jn + up256(sizeof(int) * (p.N + 1));
@@ -93,7 +94,8 @@ extern "C" int ism_subinterval_grad_noalloc(const ism_problem* prob, int precisi
   const size_t off_status = off_alpha + up256(p.alpha ? sizeof(double) * p.Nt : 0);
   const size_t off_cheb = off_status + 256;
   const size_t off_ctab = off_cheb + up256((size_t)B * p.N * ism::cheb_bytes(precision));
-  const size_t off_uf = off_ctab + up256(sizeof(double) * ism::BESSEL_TABLE);
+  const size_t off_phase = off_ctab + up256(sizeof(double) * ism::BESSEL_TABLE);
+  const size_t off_uf = off_phase + up256(sizeof(double2) * p.N);
   const size_t off_traj = off_uf + up256(sizeof(float) * (size_t)B * p.Nt);
   const size_t need = off_traj + up256((size_t)B * ((size_t)p.Nt + p.N) * GE * r2);
   if (need > kScratchBytes) {
@@ -126,6 +128,13 @@ extern "C" int ism_subinterval_grad_noalloc(const ism_problem* prob, int precisi
   std::vector<double> tab(ism::BESSEL_TABLE);
   ism::bessel_table(tab.data());
   h2d(off_ctab, tab.data(), sizeof(double) * tab.size());
+  const double c0 = 0.5 * (bd.lo + bd.hi);
+  std::vector<double2> phase(p.N);
+  for (int n = 0; n < p.N; ++n) {
+    const double ph = c0 * tau * (double)(jn[n + 1] - jn[n]);
+    phase[n] = make_double2(std::cos(ph), std::sin(ph));
+  }
+  h2d(off_phase, phase.data(), sizeof(double2) * phase.size());
   if (e == cudaSuccess) e = cudaMemsetAsync(base + off_status, 0, sizeof(int), st);
   if (e != cudaSuccess) return ism::set_error(ISM_ECUDA, (std::string("scratch upload: ") + cudaGetErrorString(e)).c_str());
 
@@ -157,6 +166,7 @@ extern "C" int ism_subinterval_grad_noalloc(const ism_problem* prob, int precisi
   k.cheb = base + off_cheb;
   k.pen = nullptr;
   k.uf = reinterpret_cast<float*>(base + off_uf);
+  k.phase = reinterpret_cast<const double2*>(base + off_phase);
   k.ctab = reinterpret_cast<const double*>(base + off_ctab);
   if ((e = ism::launch_cheb_prep(precision, k, st)) != cudaSuccess)
     return ism::set_error(ISM_ECUDA, (std::string("launch: ") + cudaGetErrorString(e)).c_str());
