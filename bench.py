@@ -249,6 +249,24 @@ def run_reference(args):
     return 0
 
 
+# ------------------------------------------------------------------------------ multi-rank timing
+def slowest_rank_ms(ms: float, world: int, device: str) -> float:
+    """The job's time: the maximum over ranks of each rank's timed region (a no-op for one rank)."""
+    if world <= 1:
+        return ms
+    import torch
+    import torch.distributed as dist
+
+    t = torch.tensor([ms], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def job_throughput(batch: int, steps: int, world: int, ms: float) -> float:
+    """ISM iterations per second of the whole job: every rank solves its own batch (weak scaling)."""
+    return batch * steps * world / (ms / 1e3)
+
+
 # ------------------------------------------------------------------------------ serving mix
 def serving_mix(P, W, seed: int, n_req: int = 48, rate: float = 200.0, slots: int = 8):
     """Continuous-batching server (ism_server_*) on a request mix shaped like the serving workload:
@@ -344,12 +362,8 @@ def run_ours(args):
     tot_ms = sum(step_ms)
     st = plan.ism_get_stats(reset=True)
     plan.ism_set_profiling(False)
-    if world > 1:
-        t = torch.tensor([tot_ms], device="cuda")
-        torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
-        tot_ms = float(t.item())
-    iters_total = B * args.steps * world
-    value = iters_total / (tot_ms / 1e3)
+    tot_ms = slowest_rank_ms(tot_ms, world, "cuda")
+    value = job_throughput(B, args.steps, world, tot_ms)
     # useful state-steps per ISM iteration: 2 global sweeps + forward, recompute and adjoint per
     # sub-interval (the grid model stores its forward states: 2 + 2)
     state_steps = (4 if plan.gp else 5) * w.Nt
