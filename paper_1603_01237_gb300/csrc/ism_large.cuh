@@ -43,8 +43,55 @@ struct OpBitflipCTA {
     for (int i = 0; i < Q; ++i) yh[i] = u * h[i] * s2;
   }
   // acc += sum_i w_i X_i in.  Called by every thread of the CTA in the same order.
+  // With 4 elements per thread every bit above the thread's own two goes through shared memory: the
+  // thread stores its 4 elements as two 16-byte halves (element pairs (0,1) and (2,3) of every
+  // thread in separate arrays, so a warp's 16-byte loads hit distinct banks), and for bit i reads
+  // the partner thread's 4 elements with two 16-byte loads, one barrier per application (double
+  // buffered).  Lane shuffles would move the same bytes in four times as many instructions.
   template <class V>
   __device__ __forceinline__ void flips(const V& in, V& acc, const R* w) const {
+    if constexpr (E == 4) {
+#pragma unroll
+      for (int i = 0; i < 2; ++i)
+#pragma unroll
+        for (int r = 0; r < 4; ++r) {
+          acc.re[r] = fma(w[i], in.re[r ^ (1 << i)], acc.re[r]);
+          acc.im[r] = fma(w[i], in.im[r ^ (1 << i)], acc.im[r]);
+        }
+      R2* b = buf + par * D;   // [0, D/2): pairs (0,1) of every thread; [D/2, D): pairs (2,3)
+      par ^= 1;
+      const int t = threadIdx.x;
+      if constexpr (sizeof(R) == 4) {   // one 16-byte store / load per element pair
+        float4* b4 = reinterpret_cast<float4*>(b);
+        b4[t] = make_float4(in.re[0], in.im[0], in.re[1], in.im[1]);
+        b4[D / 4 + t] = make_float4(in.re[2], in.im[2], in.re[3], in.im[3]);
+      } else {
+        R2 z0, z1, z2, z3;
+        z0.x = in.re[0]; z0.y = in.im[0]; z1.x = in.re[1]; z1.y = in.im[1];
+        z2.x = in.re[2]; z2.y = in.im[2]; z3.x = in.re[3]; z3.y = in.im[3];
+        b[2 * t] = z0; b[2 * t + 1] = z1;
+        b[D / 2 + 2 * t] = z2; b[D / 2 + 2 * t + 1] = z3;
+      }
+      __syncthreads();
+#pragma unroll
+      for (int i = 2; i < Q; ++i) {
+        const int tp = t ^ (1 << (i - 2));
+        R2 p0, p1, p2, p3;
+        if constexpr (sizeof(R) == 4) {
+          const float4* b4 = reinterpret_cast<const float4*>(b);
+          const float4 lo4 = b4[tp], hi4 = b4[D / 4 + tp];
+          p0.x = lo4.x; p0.y = lo4.y; p1.x = lo4.z; p1.y = lo4.w;
+          p2.x = hi4.x; p2.y = hi4.y; p3.x = hi4.z; p3.y = hi4.w;
+        } else {
+          p0 = b[2 * tp]; p1 = b[2 * tp + 1]; p2 = b[D / 2 + 2 * tp]; p3 = b[D / 2 + 2 * tp + 1];
+        }
+        acc.re[0] = fma(w[i], p0.x, acc.re[0]); acc.im[0] = fma(w[i], p0.y, acc.im[0]);
+        acc.re[1] = fma(w[i], p1.x, acc.re[1]); acc.im[1] = fma(w[i], p1.y, acc.im[1]);
+        acc.re[2] = fma(w[i], p2.x, acc.re[2]); acc.im[2] = fma(w[i], p2.y, acc.im[2]);
+        acc.re[3] = fma(w[i], p3.x, acc.re[3]); acc.im[3] = fma(w[i], p3.y, acc.im[3]);
+      }
+      return;
+    }
 #pragma unroll
     for (int i = 0; i < LE; ++i)
 #pragma unroll
