@@ -227,7 +227,8 @@ int ism_plan_footprint(const ism_problem* prob, const ism_options* opt, size_t* 
  *   iteration (L = local_iters), 3: bytes of plan-owned device memory, 4: bytes of one stored
  *   sub-interval propagator M_n (0 when none is assembled), 5: 1 when the plan propagates the global
  *   trajectories directly (bit-flip d >= 128, one state per CTA) instead of assembling M_n,
- *   6: how Algorithm 1 (a)-(b) runs (ism_options.step1 after the default is resolved: 1 or 2).
+ *   6: how Algorithm 1 (a)-(b) runs (ism_options.step1 after the default is resolved: 1 or 2),
+ *   7: tiles per block of the blocked chain (1 = plain chain).
  *   Returns -1 for a bad key. */
 long long ism_plan_info(ism_plan_t plan, int key);
 

@@ -127,6 +127,8 @@ struct ism_plan_s {
   std::vector<void*> allocs;
   bool dry = false;   // plan_build for the footprint only: nothing is allocated or uploaded
   bool direct = false;   // d <= 64: global trajectories by direct sweeps instead of assembly + chain
+  int sblk = 1, Nc = 0;  // blocked chain: products of sblk consecutive tiles, Nc of them (0: plain)
+  void* dMc = nullptr;
 };
 
 namespace {
@@ -419,11 +421,12 @@ int run_states(ism_plan_s* P, const double* u, double* Jhist, int hist_stride, i
   c.pen = P->dalpha ? P->dpen : nullptr; c.psin = P->dpsin; c.chin = P->dchin; c.phi = P->dphi;
   c.J = P->dJ; c.F = P->dF; c.Jhist = Jhist; c.hist_stride = hist_stride; c.hist_k = hist_k;
   c.status = P->dstatus; c.max_spin = P->max_spin; c.stages = P->chain_stages; c.tile_stride = P->tst;
+  c.Mc = P->dMc; c.Nc = P->Nc; c.sblk = P->sblk;
   if (P->ks.large || P->direct) {
     c.src64 = 1;
     ISM_CUDA_TRY(timed(P, 1, 1, [&] { return ism::launch_phi(P->prec, c, P->st); }));
   } else {
-    ISM_CUDA_TRY(timed(P, 1, 2, [&] { return ism::launch_chain(P->prec, c, P->chain_smem, P->st); }));
+    ISM_CUDA_TRY(timed(P, 1, P->Nc ? 4 : 2, [&] { return ism::launch_chain(P->prec, c, P->chain_smem, P->st); }));
   }
   return ISM_OK;
 }
@@ -617,6 +620,17 @@ int plan_build(const ism_problem* prob, const ism_options* opt, void* cuda_strea
     unsigned char* dMb = nullptr;
     TRY_ALLOC(dMb, B * P->N * (size_t)P->tst * P->r2);
     P->dM = dMb;
+    // blocked chain from N = 32: blocks of ~sqrt(N) tiles, as many as fit in shared memory
+    const size_t tile = (size_t)P->tst * P->r2;
+    int sb = (int)std::lround(std::sqrt((double)P->N));
+    while (sb > 1 && (sb * tile > 200 * 1024 || 3 * tile > 200 * 1024)) --sb;
+    if (P->N >= 32 && sb >= 2) {
+      P->sblk = sb;
+      P->Nc = (P->N + sb - 1) / sb;
+      unsigned char* dMc = nullptr;
+      TRY_ALLOC(dMc, B * (size_t)P->Nc * tile);
+      P->dMc = dMc;
+    }
   }
   TRY_ALLOC(P->dpsin, B * (P->N + 1) * (size_t)d);
   TRY_ALLOC(P->dchin, B * (P->N + 1) * (size_t)d);
@@ -740,6 +754,7 @@ long long ism_plan_info(ism_plan_t P, int key) {
     case 4: return (P->gp || P->ks.large || P->direct) ? 0 : (long long)(P->tst * P->r2);
     case 5: return P->ks.large ? 1 : 0;
     case 6: return (P->ks.large || P->direct) ? 2 : 1;
+    case 7: return P->Nc ? P->sblk : 1;
     default: return -1;
   }
 }

@@ -28,9 +28,53 @@ static cudaError_t chain_d(const ChainParams& p, size_t smem, cudaStream_t st) {
   }
 }
 
-cudaError_t launch_chain(int prec, const ChainParams& p, size_t smem, cudaStream_t st) {
-  cudaError_t e = prec == 0 ? chain_d<double>(p, smem, st) : chain_d<float>(p, smem, st);
+template <typename R, int JC>
+static cudaError_t fill_t(const ChainParams& p, cudaStream_t st) {
+  using R2 = typename C2<R>::T;
+  const size_t sm = (size_t)p.sblk * p.tile_stride * sizeof(R2);
+  cudaError_t e = cudaFuncSetAttribute(k_fill<R, JC>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
   if (e != cudaSuccess) return e;
+  k_fill<R, JC><<<dim3(p.Nc, p.B, 2), chain_consumer_warps(p.d) * 32, sm, st>>>(p);
+  return cudaGetLastError();
+}
+
+template <typename R>
+static cudaError_t fill_d(const ChainParams& p, cudaStream_t st) {
+  switch ((p.d + CHAIN_LANES - 1) / CHAIN_LANES) {
+    case 1: return fill_t<R, 1>(p, st);
+    case 2: return fill_t<R, 2>(p, st);
+    case 3: return fill_t<R, 3>(p, st);
+    case 4: return fill_t<R, 4>(p, st);
+    case 5: return fill_t<R, 5>(p, st);
+    case 6: return fill_t<R, 6>(p, st);
+    case 7: return fill_t<R, 7>(p, st);
+    case 8: return fill_t<R, 8>(p, st);
+    default: return cudaErrorInvalidValue;
+  }
+}
+
+template <typename R>
+static cudaError_t blockprod_t(const ChainParams& p, cudaStream_t st) {
+  using R2 = typename C2<R>::T;
+  const size_t sm = 3 * p.tile_stride * sizeof(R2);
+  cudaError_t e = cudaFuncSetAttribute(k_blockprod<R>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
+  if (e != cudaSuccess) return e;
+  k_blockprod<R><<<dim3(p.Nc, p.B), 256, sm, st>>>(p);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_chain(int prec, const ChainParams& p, size_t smem, cudaStream_t st) {
+  cudaError_t e;
+  if (p.Nc) {   // blocked: products of consecutive tiles first
+    e = prec == 0 ? blockprod_t<double>(p, st) : blockprod_t<float>(p, st);
+    if (e != cudaSuccess) return e;
+  }
+  e = prec == 0 ? chain_d<double>(p, smem, st) : chain_d<float>(p, smem, st);
+  if (e != cudaSuccess) return e;
+  if (p.Nc) {   // states inside the blocks
+    e = prec == 0 ? fill_d<double>(p, st) : fill_d<float>(p, st);
+    if (e != cudaSuccess) return e;
+  }
   if (prec == 0) k_phi<double><<<dim3(p.N + 2, p.B), 128, 0, st>>>(p);
   else k_phi<float><<<dim3(p.N + 2, p.B), 128, 0, st>>>(p);
   return cudaGetLastError();

@@ -80,6 +80,9 @@ struct ChainParams {
   int* status;
   int max_spin;
   int src64;              // k_phi: psi(t_n), chi(t_n) are already FP64 in psin, chin (direct sweeps)
+  // blocked chain: Nc coarse steps over the products of sblk consecutive tiles (0: plain chain)
+  void* Mc;               // [B][Nc] tiles: P_k = M_{k sblk + len_k - 1} ... M_{k sblk}
+  int Nc, sblk;
 };
 
 template <typename R> __device__ __forceinline__ R ldu_ro(const double* u, long i) { return (R)__ldg(u + i); }
@@ -985,9 +988,11 @@ __device__ void chain_produce(const ChainRing<R>& ring, int* status, int max_spi
 // One chain of N matvecs over uses m0 .. m0+N-1 of the ring, run by the CW consumer warps; x_0 in
 // xs[0]; stores the N results (FP32 staging) into out[idx * d] with idx = c (psi) or N - c (chi).
 // Returns false (uniformly over the consumers) if a tile did not arrive.
+// A coarse chain (blocked, sblk > 1) stores its result c at index min(c sblk, Nfull).
 template <typename R, bool HERM, int JC>
 __device__ bool run_chain(const ChainRing<R>& ring, int m0, int N, int d, int ldm, typename C2<R>::T (*xs)[64],
-                          typename C2<R>::T* out, int* fail, int* status, int max_spin, int ncons) {
+                          typename C2<R>::T* out, int* fail, int* status, int max_spin, int ncons, int sblk,
+                          int Nfull) {
   const int t = threadIdx.x;
   ChainIdx<JC> ix;
   ix.init(d, ldm, HERM);
@@ -1000,7 +1005,8 @@ __device__ bool run_chain(const ChainRing<R>& ring, int m0, int N, int d, int ld
     consumer_sync(ncons);   // result of matvec c-1 visible; every consumer has waited for tile m
     if (*(volatile int*)fail) return false;
     if (c >= 1) {
-      const int idx = HERM ? N - c : c;
+      const int ic = (HERM ? N - c : c) * sblk;
+      const int idx = ic < Nfull ? ic : Nfull;
       if (t < d) out[(long)idx * d + t] = xs[c & 1][t];   // FP32 here; FP64 conversion in k_phi
     }
     if (c < N) {
@@ -1027,6 +1033,7 @@ __global__ void __launch_bounds__(CHAIN_MAX_THREADS) k_chain(ChainParams p) {
   __shared__ double2 vd[64];
   __shared__ int fail;
   const int b = blockIdx.y, t = threadIdx.x, d = p.d, N = p.N;
+  const int Nn = p.Nc ? p.Nc : N, sb = p.Nc ? p.sblk : 1;   // coarse chain over block products, or plain
   const int cw = chain_consumer_warps(d), ncons = cw * 32;
   double2* chin = p.chin + (long)b * (N + 1) * d;
   const bool single = gridDim.x == 1;
@@ -1036,12 +1043,12 @@ __global__ void __launch_bounds__(CHAIN_MAX_THREADS) k_chain(ChainParams p) {
   ring.stages = reinterpret_cast<R2*>(smem_raw);
   ring.full = full;
   ring.empty = empty;
-  ring.Mb = reinterpret_cast<const R2*>(p.M) + (long)b * N * p.tile_stride;
+  ring.Mb = reinterpret_cast<const R2*>(p.Nc ? p.Mc : p.M) + (long)b * Nn * p.tile_stride;
   ring.tst = p.tile_stride;
   ring.bytes = (unsigned)(p.tile_stride * sizeof(R2));
   ring.NS = p.stages;
-  ring.N = N;
-  ring.U = single ? 2 * N : N;
+  ring.N = Nn;
+  ring.U = single ? 2 * Nn : Nn;
   ring.first = (!single && blockIdx.x == 1) ? 1 : 0;
   if (t == 0) {
     fail = 0;
@@ -1062,8 +1069,8 @@ __global__ void __launch_bounds__(CHAIN_MAX_THREADS) k_chain(ChainParams p) {
   int m0 = 0;
   if (do_psi) {
     if (t < d) { const double2 z = p.psi_i[t]; R2 r; r.x = (R)z.x; r.y = (R)z.y; xs[0][t] = r; }
-    if (!run_chain<R, false, JC>(ring, m0, N, d, p.ldm, xs, sps, &fail, p.status, p.max_spin, ncons)) return;
-    m0 += N;
+    if (!run_chain<R, false, JC>(ring, m0, Nn, d, p.ldm, xs, sps, &fail, p.status, p.max_spin, ncons, sb, N)) return;
+    m0 += Nn;
   }
   if (do_chi) {
     if (p.obj == 0) {
@@ -1074,7 +1081,7 @@ __global__ void __launch_bounds__(CHAIN_MAX_THREADS) k_chain(ChainParams p) {
       if (i < d)
         for (int k = q; k < d; k += CHAIN_LANES) {
           const double o = p.O[i * d + k];
-          const R2 v = xs[N & 1][k];
+          const R2 v = xs[Nn & 1][k];
           sr += o * (double)v.x;
           si += o * (double)v.y;
         }
@@ -1087,10 +1094,96 @@ __global__ void __launch_bounds__(CHAIN_MAX_THREADS) k_chain(ChainParams p) {
     }
     consumer_sync(ncons);
     if (t < d) { const double2 z = vd[t]; R2 r; r.x = (R)z.x; r.y = (R)z.y; xs[0][t] = r; chin[(long)N * d + t] = z; }
-    if (!run_chain<R, true, JC>(ring, m0, N, d, p.ldm, xs, sch, &fail, p.status, p.max_spin, ncons)) return;
+    if (!run_chain<R, true, JC>(ring, m0, Nn, d, p.ldm, xs, sch, &fail, p.status, p.max_spin, ncons, sb, N)) return;
   }
 }
 
+
+// ------------------------------------------------------------------------ blocked chain
+// The chain's 2N dependent matvecs take ~0.4-0.5 us each on one SM.  With N large the chain is
+// shortened by products of consecutive propagators (Sec. 3: M_n are products of step propagators
+// too): k_blockprod forms P_k = M_{k s + len - 1} ... M_{k s} for all blocks k in parallel, the
+// chain runs over the P_k (psi(t_{ks}), chi(t_{ks})), and k_fill recovers the states inside every
+// block from its first (psi) or last (chi) state, all blocks at once.
+
+// grid (Nc, B), 256 threads, dynamic shared memory 3 tiles.  Q = T P column-major (X(i, j) at
+// X[j ldm + i]), thread t computing outputs o = t, t + 256, ...
+template <typename R>
+__global__ void __launch_bounds__(256) k_blockprod(ChainParams p) {
+  using R2 = typename C2<R>::T;
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  const int k = blockIdx.x, b = blockIdx.y, d = p.d, ldm = p.ldm, N = p.N, s = p.sblk;
+  const long tst = p.tile_stride;
+  R2* P = reinterpret_cast<R2*>(smem_raw);
+  R2* T = P + tst;
+  R2* Q = T + tst;
+  const R2* Mb = reinterpret_cast<const R2*>(p.M) + ((long)b * N + (long)k * s) * tst;
+  const int len = min(s, N - k * s);
+  for (long i = threadIdx.x; i < tst; i += blockDim.x) P[i] = Mb[i];
+  for (int r = 1; r < len; ++r) {
+    for (long i = threadIdx.x; i < tst; i += blockDim.x) T[i] = Mb[(long)r * tst + i];
+    __syncthreads();
+    for (int o = threadIdx.x; o < d * d; o += blockDim.x) {
+      const int i = o % d, j = o / d;
+      R zr = R(0), zi = R(0);
+      for (int q = 0; q < d; ++q) {
+        const R2 a = T[q * ldm + i], c = P[j * ldm + q];
+        zr = fma(a.x, c.x, fma(-a.y, c.y, zr));
+        zi = fma(a.x, c.y, fma(a.y, c.x, zi));
+      }
+      R2 z;
+      z.x = zr;
+      z.y = zi;
+      Q[j * ldm + i] = z;
+    }
+    __syncthreads();
+    R2* tmp = P;
+    P = Q;
+    Q = tmp;
+  }
+  R2* dst = reinterpret_cast<R2*>(p.Mc) + ((long)b * p.Nc + k) * tst;
+  for (long i = threadIdx.x; i < tst; i += blockDim.x) dst[i] = P[i];
+}
+
+// grid (Nc, B, 2), consumer-layout threads, dynamic shared memory: the block's tiles.  z = 0: psi
+// forward from psi(t_{ks}) (psi_i for k = 0), z = 1: chi backward from chi(t_{ks + len}) (chi(T) in
+// FP64 for the last block); both write the FP32 staging the chain writes.
+template <typename R, int JC>
+__global__ void __launch_bounds__(CHAIN_MAX_THREADS) k_fill(ChainParams p) {
+  using R2 = typename C2<R>::T;
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  __shared__ __align__(16) R2 xs[2][64];
+  const int k = blockIdx.x, b = blockIdx.y, herm = blockIdx.z, t = threadIdx.x;
+  const int d = p.d, N = p.N, s = p.sblk;
+  const long tst = p.tile_stride;
+  const int j0 = k * s, len = min(s, N - j0);
+  R2* tiles = reinterpret_cast<R2*>(smem_raw);
+  const R2* Mb = reinterpret_cast<const R2*>(p.M) + ((long)b * N + j0) * tst;
+  for (long i = t; i < (long)len * tst; i += blockDim.x) tiles[i] = Mb[i];
+  R2* sps = reinterpret_cast<R2*>(p.stage) + (long)b * 2 * (N + 1) * d;
+  R2* sch = sps + (long)(N + 1) * d;
+  const double2* chin = p.chin + (long)b * (N + 1) * d;
+  if (t < d) {
+    R2 z;
+    if (!herm) {
+      if (j0 == 0) { z.x = (R)p.psi_i[t].x; z.y = (R)p.psi_i[t].y; }
+      else z = sps[(long)j0 * d + t];
+    } else {
+      if (j0 + len == N) { z.x = (R)chin[(long)N * d + t].x; z.y = (R)chin[(long)N * d + t].y; }
+      else z = sch[(long)(j0 + len) * d + t];
+    }
+    xs[0][t] = z;
+  }
+  __syncthreads();
+  ChainIdx<JC> ix;
+  ix.init(d, p.ldm, herm != 0);
+  for (int c = 1; c < len; ++c) {   // results at j0 + c (psi) or j0 + len - c (chi)
+    if (!herm) chain_mv<R, false, JC>(tiles + (long)(c - 1) * tst, xs[(c - 1) & 1], xs[c & 1], ix, d);
+    else chain_mv<R, true, JC>(tiles + (long)(len - c) * tst, xs[(c - 1) & 1], xs[c & 1], ix, d);
+    __syncthreads();
+    if (t < d) (herm ? sch : sps)[(long)(herm ? j0 + len - c : j0 + c) * d + t] = xs[c & 1][t];
+  }
+}
 
 // grid (N+2, B), 128 threads.  Block n <= N converts psi(t_n), chi(t_n) from the chain to FP64
 // (psi(t_0) = psi_i and chi(t_N) = chi(T) are exact) and forms phi_n = a_n psi(t_n) + b_n chi(t_n)

@@ -276,3 +276,28 @@ def test_step1_default_follows_the_batch(P):
         assert pl.info(6) == 2
     with P.Plan(w, precision="mixed", batch=96, step1=1) as pl:
         assert pl.info(6) == 1
+
+
+# ---------------------------------------------------------------- blocked chain (N >= 32)
+BLOCKED = [
+    ("rotor41-N40-fp64", W.config("rotor41", Nt=1000, N=40), "fp64"),         # observable, ragged blocks
+    ("rotor41-N40-mixed", W.config("rotor41", Nt=2000, N=40).with_(T=2000 * np.pi / 20000), "mixed"),
+    ("dense16-N37-fp64", W.random_dense(16, 65, T=2.0, Nt=370, N=37), "fp64"),  # overlap: two chains
+    ("bitflip32-N64-mixed", _random_target(W.spin_chain(5, 69, T=4.0, Nt=640, N=64, u_amp=1.0), 4), "mixed"),
+]
+
+
+@pytest.mark.parametrize("name,w,prec", BLOCKED, ids=[c[0] for c in BLOCKED])
+def test_blocked_chain_matches_oracle(P, name, w, prec):
+    """From N = 32 the chain runs over products of ~sqrt(N) consecutive propagators and fills the
+    states inside each block in parallel; the intermediate states and J are unchanged."""
+    phi_o = O.intermediate_states(w, w.u0)
+    Jo, Fo = O.objective(w, w.u0)
+    with P.Plan(w, precision=prec) as pl:
+        assert pl.info(7) > 1
+        phi = pl.intermediate_states(w.u0)[0]
+        J, F = pl.evaluate(w.u0)
+    tol = FP64_PHI if prec == "fp64" else MIX_PHI
+    assert np.max(np.abs(phi - phi_o)) <= tol, np.max(np.abs(phi - phi_o))
+    assert abs(J[0] - Jo) <= (1e-11 if prec == "fp64" else 2e-5)
+    assert abs(F[0] - Fo) <= (1e-11 if prec == "fp64" else 2e-5)
