@@ -1107,7 +1107,7 @@ __global__ void __launch_bounds__(CHAIN_MAX_THREADS) k_chain(ChainParams p) {
 // block from its first (psi) or last (chi) state, all blocks at once.
 
 // grid (Nc, B), 256 threads, dynamic shared memory 3 tiles.  Q = T P column-major (X(i, j) at
-// X[j ldm + i]), thread t computing outputs o = t, t + 256, ...
+// X[j ldm + i]).
 template <typename R>
 __global__ void __launch_bounds__(256) k_blockprod(ChainParams p) {
   using R2 = typename C2<R>::T;
@@ -1123,18 +1123,45 @@ __global__ void __launch_bounds__(256) k_blockprod(ChainParams p) {
   for (int r = 1; r < len; ++r) {
     for (long i = threadIdx.x; i < tst; i += blockDim.x) T[i] = Mb[(long)r * tst + i];
     __syncthreads();
-    for (int o = threadIdx.x; o < d * d; o += blockDim.x) {
-      const int i = o % d, j = o / d;
-      R zr = R(0), zi = R(0);
+    // register tiles of 2 rows x 4 columns: 6 shared loads per 8 complex multiply-adds
+    const int nbi = (d + 1) / 2, nbj = (d + 3) / 4;
+    for (int tb = threadIdx.x; tb < nbi * nbj; tb += blockDim.x) {
+      const int i0 = (tb % nbi) * 2, j0 = (tb / nbi) * 4;
+      R zr[2][4], zi[2][4];
+#pragma unroll
+      for (int a = 0; a < 2; ++a)
+#pragma unroll
+        for (int c = 0; c < 4; ++c) { zr[a][c] = R(0); zi[a][c] = R(0); }
       for (int q = 0; q < d; ++q) {
-        const R2 a = T[q * ldm + i], c = P[j * ldm + q];
-        zr = fma(a.x, c.x, fma(-a.y, c.y, zr));
-        zi = fma(a.x, c.y, fma(a.y, c.x, zi));
+        R2 ta[2], pc[4];
+#pragma unroll
+        for (int a = 0; a < 2; ++a) {
+          const int i = i0 + a < d ? i0 + a : d - 1;   // padded rows/columns compute a copy, not stored
+          ta[a] = T[q * ldm + i];
+        }
+#pragma unroll
+        for (int c = 0; c < 4; ++c) {
+          const int j = j0 + c < d ? j0 + c : d - 1;
+          pc[c] = P[j * ldm + q];
+        }
+#pragma unroll
+        for (int a = 0; a < 2; ++a)
+#pragma unroll
+          for (int c = 0; c < 4; ++c) {
+            zr[a][c] = fma(ta[a].x, pc[c].x, fma(-ta[a].y, pc[c].y, zr[a][c]));
+            zi[a][c] = fma(ta[a].x, pc[c].y, fma(ta[a].y, pc[c].x, zi[a][c]));
+          }
       }
-      R2 z;
-      z.x = zr;
-      z.y = zi;
-      Q[j * ldm + i] = z;
+#pragma unroll
+      for (int a = 0; a < 2; ++a)
+#pragma unroll
+        for (int c = 0; c < 4; ++c)
+          if (i0 + a < d && j0 + c < d) {
+            R2 z;
+            z.x = zr[a][c];
+            z.y = zi[a][c];
+            Q[(j0 + c) * ldm + i0 + a] = z;
+          }
     }
     __syncthreads();
     R2* tmp = P;
