@@ -241,7 +241,8 @@ def run_reference(args):
         "impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": args.gpus,
         "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 / value, "higher_is_better": True,
         "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
-        "config": {"workload": f"{args.config} d={full.d} Nt={full.Nt} N={args.N}", "precision": "fp64 (oracle)"},
+        "config": {"workload": f"{args.config}: {DESCR.get(args.config, args.config)} (d={dim_of(full)}), "
+                               f"T={full.T:g}, Nt={full.Nt}, N={full.N}, one problem", "precision": "fp64 (oracle)"},
         "cpu_baseline": {"value": value, "unit": UNIT, "cores": 1, "kind": "oracle", "sample": sample},
         "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
     }

@@ -197,7 +197,7 @@ def subinterval_grad_noalloc(w, precision: str, phi, u, grad, Jn=None, *, batch:
 
 
 def problem_and_options(w, *, precision=None, batch=1, local_iters=None, rho=None, kind=None, cheb_tol=0.0,
-                        subproblem_form=0, step1=0):
+                        subproblem_form=0, step1=0, max_spin_iters=0):
     """(ism_problem, ism_options, arrays to keep alive) for a workload object."""
     kind = kind or w.kind
     gp = kind == "gp"
@@ -218,8 +218,8 @@ def problem_and_options(w, *, precision=None, batch=1, local_iters=None, rho=Non
                       batch=int(batch))
     opt = IsmOptions(precision=ISM_FP64 if prec == "fp64" else ISM_MIXED,
                      local_iters=int(local_iters or w.local_iters), rho=float(w.rho if rho is None else rho),
-                     cheb_tol=float(cheb_tol), max_spin_iters=0, subproblem_form=int(subproblem_form),
-                     step1=int(step1))
+                     cheb_tol=float(cheb_tol), max_spin_iters=int(max_spin_iters),
+                     subproblem_form=int(subproblem_form), step1=int(step1))
     return prob, opt, keep
 
 
@@ -236,7 +236,7 @@ class Plan:
 
     def __init__(self, w, *, precision: str | None = None, batch: int = 1, stream=None,
                  local_iters: int | None = None, rho: float | None = None, kind: str | None = None,
-                 cheb_tol: float = 0.0, subproblem_form: int = 0, step1: int = 0):
+                 cheb_tol: float = 0.0, subproblem_form: int = 0, step1: int = 0, max_spin_iters: int = 0):
         lib = load()
         self.w = w
         self.kind = kind or w.kind
@@ -247,7 +247,8 @@ class Plan:
         self.precision = precision or w.precision
         prob, opt, self._keep = problem_and_options(w, precision=precision, batch=batch, local_iters=local_iters,
                                                     rho=rho, kind=kind, cheb_tol=cheb_tol,
-                                                    subproblem_form=subproblem_form, step1=step1)
+                                                    subproblem_form=subproblem_form, step1=step1,
+                                                    max_spin_iters=max_spin_iters)
         h = C.c_void_p()
         st = None
         if stream is not None:

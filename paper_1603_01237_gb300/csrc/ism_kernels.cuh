@@ -890,6 +890,7 @@ __device__ __forceinline__ bool mbar_wait(uint64_t* bar, unsigned parity, int ma
 // the new state.  Consumer thread t owns output row i = t / 8 and the columns k = t (mod 8); three
 // shuffles finish each row.
 constexpr int CHAIN_MAX_STAGES = 16;
+constexpr int CHAIN_DRAIN_SPIN = 1 << 22;   // bounded wait for copies in flight (~0.3 s at most)
 constexpr int CHAIN_LANES = 8;      // lanes per output row
 constexpr int CHAIN_MAX_THREADS = (64 * CHAIN_LANES / 32 + 1) * 32;
 
@@ -980,9 +981,11 @@ __device__ void chain_produce(const ChainRing<R>& ring, int* status, int max_spi
     bulk_load(ring.stages + st * ring.tst, ring.Mb + (long)ring.tile_of(m) * ring.tst, ring.bytes, &ring.full[st]);
     issued = m + 1;
   }
+  // the drain has its own bound, independent of the caller's wait cap: copies in flight complete
+  // within microseconds, and none may land after the block exits
   if (issued < ring.U)
     for (int m = issued - ring.NS < 0 ? 0 : issued - ring.NS; m < issued; ++m)
-      mbar_wait(&ring.full[m % ring.NS], (unsigned)((m / ring.NS) & 1), max_spin);
+      mbar_wait(&ring.full[m % ring.NS], (unsigned)((m / ring.NS) & 1), CHAIN_DRAIN_SPIN);
 }
 
 // One chain of N matvecs over uses m0 .. m0+N-1 of the ring, run by the CW consumer warps; x_0 in

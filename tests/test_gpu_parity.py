@@ -301,3 +301,23 @@ def test_blocked_chain_matches_oracle(P, name, w, prec):
     assert np.max(np.abs(phi - phi_o)) <= tol, np.max(np.abs(phi - phi_o))
     assert abs(J[0] - Jo) <= (1e-11 if prec == "fp64" else 2e-5)
     assert abs(F[0] - Fo) <= (1e-11 if prec == "fp64" else 2e-5)
+
+
+def test_bounded_wait_gives_up_cleanly(P):
+    """A cap of one try on device-side waits makes the chain's first mbarrier wait give up before its
+    propagator tile has landed: the call returns ISM_ETIMEOUT (the block first waits, with its own
+    bound, for the copies it has in flight), and the context stays usable."""
+    w = W.config("rotor41", Nt=2000, N=16)
+    seen = 0
+    for _ in range(4):
+        with P.Plan(w, precision="mixed", max_spin_iters=1) as pl:
+            try:
+                pl.evaluate(w.u0)
+            except P.IsmError as e:
+                assert e.status == 5, e
+                seen += 1
+    assert seen >= 1
+    Jo, _ = O.objective(w, w.u0)
+    with P.Plan(w, precision="mixed") as pl:
+        J, _ = pl.evaluate(w.u0)
+    assert abs(J[0] - Jo) <= 2e-5
