@@ -79,6 +79,19 @@ typedef enum {
   ISM_OBJ_OBSERVABLE = 1   /* J = <psi(T)|O|psi(T)>, chi(T) = O psi(T), weight 2 on Im-terms      */
 } ism_objective;
 
+typedef enum {
+  /* exp(-i tau H(u_j)) by the Chebyshev (Jacobi-Anger) series to the truncation threshold cheb_tol:
+     the exact piecewise-constant propagator of Eq. (dir) up to rounding; every kind, both precisions */
+  ISM_SCHEME_CHEBYSHEV = 0,
+  /* the Crank-Nicolson step of Sec. 3: (I + i tau H_j/2) psi_{j+1} = (I - i tau H_j/2) psi_j, the
+     linear system solved by Jacobi iterations to cheb_tol (K per step with
+     (tau/2)(max off-diagonal row sum of H0 + max|u| that of H1) = rho, rho^K <= cheb_tol; a plan
+     whose controls make rho >= 1/2 fails with ISM_EUNSUPPORTED).  The gradients are the exact
+     derivatives of this discrete scheme, w (tau/2) Im<xi_j|H1|psi_j + psi_{j+1}> with
+     xi_j = (I - i tau H_j/2)^{-1} chi_{j+1}.  ISM_H_TRIDIAG and ISM_FP64 only.                     */
+  ISM_SCHEME_CRANK_NICOLSON = 1
+} ism_scheme;
+
 /* The control problem (Sec. 2).  All pointers are HOST pointers read only during ism_plan. */
 typedef struct {
   int d;                   /* Hilbert-space dimension                                            */
@@ -119,6 +132,7 @@ typedef struct {
                                   run the forward and adjoint sweeps of a sub-interval in one
                                   lane group, for throughput, rather than in two concurrent ones);
                               0 = default: 2 when batch >= 96, else 1.  Larger d always sweeps. */
+  int scheme;              /* ism_scheme: time step of the piecewise-constant propagation          */
 } ism_options;
 
 typedef struct ism_plan_s* ism_plan_t;
@@ -228,7 +242,8 @@ int ism_plan_footprint(const ism_problem* prob, const ism_options* opt, size_t* 
  *   sub-interval propagator M_n (0 when none is assembled), 5: 1 when the plan propagates the global
  *   trajectories directly (bit-flip d >= 128, one state per CTA) instead of assembling M_n,
  *   6: how Algorithm 1 (a)-(b) runs (ism_options.step1 after the default is resolved: 1 or 2),
- *   7: tiles per block of the blocked chain (1 = plain chain).
+ *   7: tiles per block of the blocked chain (1 = plain chain),
+ *   8: the plan's time-step scheme (ism_scheme).
  *   Returns -1 for a bad key. */
 long long ism_plan_info(ism_plan_t plan, int key);
 

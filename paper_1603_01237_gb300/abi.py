@@ -18,6 +18,8 @@ ISM_OK, ISM_EINVAL, ISM_ENOMEM, ISM_ECUDA, ISM_ENONFINITE, ISM_ETIMEOUT, ISM_EUN
 ISM_FP64, ISM_MIXED = 0, 1
 ISM_H_DENSE, ISM_H_BITFLIP, ISM_H_TRIDIAG, ISM_H_GRID_GP = 0, 1, 2, 3
 ISM_OBJ_OVERLAP, ISM_OBJ_OBSERVABLE = 0, 1
+ISM_SCHEME_CHEBYSHEV, ISM_SCHEME_CRANK_NICOLSON = 0, 1
+_SCHEME = {"chebyshev": ISM_SCHEME_CHEBYSHEV, "crank_nicolson": ISM_SCHEME_CRANK_NICOLSON}
 
 STATUS_NAMES = {0: "ISM_OK", 1: "ISM_EINVAL", 2: "ISM_ENOMEM", 3: "ISM_ECUDA", 4: "ISM_ENONFINITE",
                 5: "ISM_ETIMEOUT", 6: "ISM_EUNSUPPORTED"}
@@ -38,7 +40,7 @@ class IsmProblem(C.Structure):
 class IsmOptions(C.Structure):
     _fields_ = [("precision", C.c_int), ("local_iters", C.c_int), ("rho", C.c_double),
                 ("cheb_tol", C.c_double), ("max_spin_iters", C.c_int), ("subproblem_form", C.c_int),
-                ("step1", C.c_int)]
+                ("step1", C.c_int), ("scheme", C.c_int)]
 
 
 class IsmStats(C.Structure):
@@ -197,8 +199,9 @@ def subinterval_grad_noalloc(w, precision: str, phi, u, grad, Jn=None, *, batch:
 
 
 def problem_and_options(w, *, precision=None, batch=1, local_iters=None, rho=None, kind=None, cheb_tol=0.0,
-                        subproblem_form=0, step1=0, max_spin_iters=0):
-    """(ism_problem, ism_options, arrays to keep alive) for a workload object."""
+                        subproblem_form=0, step1=0, max_spin_iters=0, scheme="chebyshev"):
+    """(ism_problem, ism_options, arrays to keep alive) for a workload object.  scheme: "chebyshev"
+    (exact step) or "crank_nicolson" (the Sec. 3 step; tridiagonal kind, FP64)."""
     kind = kind or w.kind
     gp = kind == "gp"
     d = int(w.n) if gp else int(w.d)
@@ -219,7 +222,7 @@ def problem_and_options(w, *, precision=None, batch=1, local_iters=None, rho=Non
     opt = IsmOptions(precision=ISM_FP64 if prec == "fp64" else ISM_MIXED,
                      local_iters=int(local_iters or w.local_iters), rho=float(w.rho if rho is None else rho),
                      cheb_tol=float(cheb_tol), max_spin_iters=int(max_spin_iters),
-                     subproblem_form=int(subproblem_form), step1=int(step1))
+                     subproblem_form=int(subproblem_form), step1=int(step1), scheme=_SCHEME[scheme])
     return prob, opt, keep
 
 
@@ -236,7 +239,8 @@ class Plan:
 
     def __init__(self, w, *, precision: str | None = None, batch: int = 1, stream=None,
                  local_iters: int | None = None, rho: float | None = None, kind: str | None = None,
-                 cheb_tol: float = 0.0, subproblem_form: int = 0, step1: int = 0, max_spin_iters: int = 0):
+                 cheb_tol: float = 0.0, subproblem_form: int = 0, step1: int = 0, max_spin_iters: int = 0,
+                 scheme: str = "chebyshev"):
         lib = load()
         self.w = w
         self.kind = kind or w.kind
@@ -248,7 +252,7 @@ class Plan:
         prob, opt, self._keep = problem_and_options(w, precision=precision, batch=batch, local_iters=local_iters,
                                                     rho=rho, kind=kind, cheb_tol=cheb_tol,
                                                     subproblem_form=subproblem_form, step1=step1,
-                                                    max_spin_iters=max_spin_iters)
+                                                    max_spin_iters=max_spin_iters, scheme=scheme)
         h = C.c_void_p()
         st = None
         if stream is not None:

@@ -72,6 +72,7 @@ struct ism_plan_s {
   double T = 0, tau = 0, rho = 0, tol = 0, w = 1;
   int max_spin = 0;
   int form = 1;   // sub-problem form in ism_iterate: 1 literal, 2 Theorem 2 (first local step)
+  int scheme = ISM_SCHEME_CHEBYSHEV;
   bool gp = false;                       // grid (Gross-Pitaevskii) kind
   double gpL = 0, gpxmin = 0, gpg = 0;   // its grid length, origin and nonlinearity
   double c0 = 0, r0 = 0, h1n = 0;
@@ -349,10 +350,13 @@ int finish(ism_plan_s* P) {
   ISM_CUDA_TRY(cudaMemcpyAsync(&st, P->dstatus, sizeof(int), cudaMemcpyDeviceToHost, P->st));
   ISM_CUDA_TRY(cudaStreamSynchronize(P->st));
   if (st & ism::ST_TIMEOUT) return fail(ISM_ETIMEOUT, "a bounded device-side wait gave up");
+  const bool cn = P->scheme == ISM_SCHEME_CRANK_NICOLSON;
   if (st & ism::ST_KOVERFLOW) return fail(ISM_EUNSUPPORTED, "Chebyshev series needed more terms than compiled");
   if (st & ism::ST_NONFINITE) return fail(ISM_ENONFINITE, "non-finite value in a control or a result");
   if (st & ism::ST_SPECTRUM)
-    return fail(ISM_EUNSUPPORTED, "controls so large that a time step needs more Chebyshev sub-steps than the limit");
+    return fail(ISM_EUNSUPPORTED, cn ? "controls so large that tau/2 times the off-diagonal row sum of H reaches 1/2 "
+                                       "(the Jacobi solve of the Crank-Nicolson step)"
+                                     : "controls so large that a time step needs more Chebyshev sub-steps than the limit");
   g_err.clear();
   return ISM_OK;
 }
@@ -377,6 +381,7 @@ ism::KParams kparams(ism_plan_s* P, double* u) {
   k.update = 0; k.max_spin = P->max_spin;
   k.psi_i = P->dpsi_i; k.psi_f = P->dpsi_f; k.O = P->dO; k.obj = P->obj; k.uf = P->duf;
   k.psin_w = P->dpsin; k.chin_w = P->dchin; k.zp = P->dzp;
+  k.scheme = P->scheme == ISM_SCHEME_CRANK_NICOLSON ? 1 : 0;
   return k;
 }
 
@@ -503,6 +508,10 @@ int plan_build(const ism_problem* prob, const ism_options* opt, void* cuda_strea
   if (opt->cheb_tol < 0.0) return fail(ISM_EINVAL, "cheb_tol must be >= 0");
   if (opt->subproblem_form < 0 || opt->subproblem_form > 2) return fail(ISM_EINVAL, "subproblem_form must be 0, 1 or 2");
   if (opt->step1 < 0 || opt->step1 > 2) return fail(ISM_EINVAL, "step1 must be 0, 1 or 2");
+  if (opt->scheme != ISM_SCHEME_CHEBYSHEV && opt->scheme != ISM_SCHEME_CRANK_NICOLSON)
+    return fail(ISM_EINVAL, "scheme must be ISM_SCHEME_CHEBYSHEV or ISM_SCHEME_CRANK_NICOLSON");
+  if (opt->scheme == ISM_SCHEME_CRANK_NICOLSON && (p.kind != ISM_H_TRIDIAG || opt->precision != ISM_FP64))
+    return fail(ISM_EUNSUPPORTED, "the Crank-Nicolson scheme is built for the tridiagonal kind in FP64");
 
   ism_plan_s* P = new (std::nothrow) ism_plan_s();
   if (!P) return fail(ISM_ENOMEM, "host allocation");
@@ -514,6 +523,7 @@ int plan_build(const ism_problem* prob, const ism_options* opt, void* cuda_strea
   P->w = p.objective == ISM_OBJ_OVERLAP ? 1.0 : 2.0;
   P->max_spin = opt->max_spin_iters > 0 ? opt->max_spin_iters : (1 << 22);
   P->form = opt->subproblem_form != 0 ? opt->subproblem_form : (P->prec == ISM_MIXED ? 2 : 1);
+  P->scheme = opt->scheme;
   P->st = reinterpret_cast<cudaStream_t>(cuda_stream);
   cudaGetDevice(&P->dev);
 
@@ -571,7 +581,8 @@ int plan_build(const ism_problem* prob, const ism_options* opt, void* cuda_strea
     h1diag = false;
     for (int e = 0; e < d; ++e) h1diag |= p.H1[e] != 0.0;
   }
-  bool ok = ism::select_kernels(P->prec, p.kind, d, &P->ks, h1diag);
+  bool ok = P->scheme == ISM_SCHEME_CRANK_NICOLSON ? ism::kernels_tridiag_cn(P->prec, d, h1diag, &P->ks)
+                                                    : ism::select_kernels(P->prec, p.kind, d, &P->ks, h1diag);
   if (!ok) { delete P; return fail(ISM_EUNSUPPORTED, "no compiled kernel for this kind and d"); }
   P->direct = !P->ks.large && (opt->step1 == 2 || (opt->step1 == 0 && P->B >= 96));
   const int gpw = P->ks.large ? 1 : 32 / P->ks.GA;
@@ -580,10 +591,23 @@ int plan_build(const ism_problem* prob, const ism_options* opt, void* cuda_strea
   P->tst = ((long)d * P->ldm + 1) / 2 * 2;          // even tile stride: tiles are multiples of 16 bytes
   P->r2 = P->prec == ISM_FP64 ? sizeof(double2) : sizeof(float2);
 
-  Bounds bd = bounds_of(p.kind, d, p.H0, p.H1);
-  P->c0 = 0.5 * (bd.lo + bd.hi);
-  P->r0 = 0.5 * (bd.hi - bd.lo);
-  P->h1n = bd.h1;
+  if (P->scheme == ISM_SCHEME_CRANK_NICOLSON) {
+    // no centring (c0 = 0: no segment phase); r0, h1n = largest off-diagonal absolute row sums of H0,
+    // H1, which bound the contraction of the Jacobi solve
+    P->c0 = 0.0;
+    P->r0 = P->h1n = 0.0;
+    for (int e = 0; e < d; ++e) {
+      const double l0 = e > 0 ? std::fabs(p.H0[d + e - 1]) : 0.0, r0 = e < d - 1 ? std::fabs(p.H0[d + e]) : 0.0;
+      const double l1 = e > 0 ? std::fabs(p.H1[d + e - 1]) : 0.0, r1 = e < d - 1 ? std::fabs(p.H1[d + e]) : 0.0;
+      P->r0 = std::fmax(P->r0, l0 + r0);
+      P->h1n = std::fmax(P->h1n, l1 + r1);
+    }
+  } else {
+    Bounds bd = bounds_of(p.kind, d, p.H0, p.H1);
+    P->c0 = 0.5 * (bd.lo + bd.hi);
+    P->r0 = 0.5 * (bd.hi - bd.lo);
+    P->h1n = bd.h1;
+  }
 
   // partition (Sec. 2): j_n = floor(n Nt / N), t_n = j_n tau, beta_n = T / (t_{n+1} - t_n)
   std::vector<int> jn(P->N + 1);
@@ -638,7 +662,7 @@ int plan_build(const ism_problem* prob, const ism_options* opt, void* cuda_strea
   unsigned char* dTb = nullptr;
   TRY_ALLOC(dTb, B * ((size_t)P->Nt + P->N) * GE * P->r2);
   P->dtraj = dTb;
-  if (!P->ks.large && !P->direct) {   // second trajectory of the concurrent two-trajectory sweeps
+  if (!P->ks.large && !P->direct && P->ks.sweeps2) {   // second trajectory of the concurrent sweeps
     unsigned char* dT2 = nullptr;
     TRY_ALLOC(dT2, B * ((size_t)P->Nt + P->N) * GE * P->r2);
     P->dtraj2 = dT2;
@@ -755,6 +779,7 @@ long long ism_plan_info(ism_plan_t P, int key) {
     case 5: return P->ks.large ? 1 : 0;
     case 6: return (P->ks.large || P->direct) ? 2 : 1;
     case 7: return P->Nc ? P->sblk : 1;
+    case 8: return P->scheme;
     default: return -1;
   }
 }
@@ -879,7 +904,8 @@ int ism_iterate(ism_plan_t P, int iters, double* u_inout, double* J_hist, double
         ISM_CUDA_TRY(ism::launch_cheb_prep(P->prec, k, P->st));
         P->kernels += 1;
       }
-      if (k.form && !P->ks.large && !P->direct) ISM_CUDA_TRY(timed(P, 2, 2, [&] { return P->ks.sweeps2(k, P->st); }));
+      if (k.form && !P->ks.large && !P->direct && P->ks.sweeps2)
+        ISM_CUDA_TRY(timed(P, 2, 2, [&] { return P->ks.sweeps2(k, P->st); }));
       else ISM_CUDA_TRY(timed(P, 2, 1, [&] { return P->ks.subinterval(k, P->st); }));
     }
     if (err_hist) {
@@ -924,7 +950,7 @@ int ism_gradient(ism_plan_t P, const double* u, double* grad, double* J) {
     k.form = 1;
     k.global = 1;
     k.count = P->dcount + 3;
-    if (P->ks.large || P->direct) ISM_CUDA_TRY(timed(P, 2, 1, [&] { return P->ks.subinterval(k, P->st); }));
+    if (P->ks.large || P->direct || !P->ks.sweeps2) ISM_CUDA_TRY(timed(P, 2, 1, [&] { return P->ks.subinterval(k, P->st); }));
     else ISM_CUDA_TRY(timed(P, 2, 2, [&] { return P->ks.sweeps2(k, P->st); }));
   }
   if ((rc = copy_out(P, grad, P->dgrad, (long)P->B * P->Nt))) return rc;

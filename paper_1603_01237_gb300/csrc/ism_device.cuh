@@ -26,6 +26,7 @@ namespace ism {
 constexpr int KMAX = 32;        // Chebyshev terms held per group
 constexpr double XMAX = 4.0;    // largest tau*rad per sub-step (more -> sub-steps)
 constexpr int SMAX = 64;        // sub-steps per time step before a plan reports ST_SPECTRUM
+constexpr int CN_KMAX = 64;     // Jacobi iterations per Crank-Nicolson solve (rho < 1/2, tol >= 1e-19)
 
 enum StatusBits : int {
   ST_TIMEOUT = 1,      // a bounded mbarrier wait gave up
@@ -85,7 +86,8 @@ template <typename R> struct Cheb {
   R c, inv_rad;     // spectral centre and 1/rad (FP32 copies)
   double cd, s2d;   // spectral centre and 2/rad in FP64
   double cph, sph;  // cos, sin of the sub-interval's global phase c * tau * (number of steps)
-  int K, S;         // terms, sub-steps per time step
+  int K, S;         // terms, sub-steps per time step (Crank-Nicolson: Jacobi iterations, 1)
+  R h;              // Crank-Nicolson only: tau / 2
 };
 
 template <typename R> __device__ __forceinline__ void split2(double v, R& hi, R& lo) {
@@ -160,6 +162,33 @@ __device__ void cheb_params(Cheb<R>& ch, const double* ctab, double tau, double 
   if (lane == 1) split2<R>(a, ch.a1h, ch.a1l);   // a_1 = 2 J_1 (lane 1 holds it)
 }
 
+// Crank-Nicolson parameters of one sub-interval (one thread): K Jacobi iterations per linear solve,
+// with rho = (tau/2)(off0 + umax off1) (off0, off1: largest off-diagonal absolute row sums of H0 and
+// H1) the contraction of each iteration, so that rho^K <= tol (at most CN_KMAX).  rho >= 1/2 is flagged
+// ST_SPECTRUM.
+template <typename R>
+__device__ void cn_params(Cheb<R>& ch, double tau, double off0, double off1, double umax, double tol, int* status) {
+  for (int k = 0; k < KMAX; ++k) { ch.cf[k] = R(0); ch.cl[k] = R(0); }
+  ch.a0h = ch.a0l = ch.c0h = ch.c0l = ch.a1h = ch.a1l = R(0);
+  ch.c = R(0);
+  ch.inv_rad = R(0);
+  ch.cd = 0.0;
+  ch.s2d = 0.0;
+  ch.cph = 1.0;   // no global phase is split off
+  ch.sph = 0.0;
+  ch.S = 1;
+  ch.h = (R)(0.5 * tau);
+  const double rho = 0.5 * tau * (off0 + umax * off1) * (1.0 + 1e-6);
+  int K = 1;
+  if (rho >= 0.5) {   // flagged; one iteration keeps the (discarded) results bounded
+    atomicOr(status, ST_SPECTRUM);
+  } else if (rho > 0.0) {
+    K = (int)ceil(log(tol) / log(rho));
+    K = K < 1 ? 1 : (K > CN_KMAX ? CN_KMAX : K);
+  }
+  ch.K = K;
+}
+
 // Copy a sub-interval's parameters from global memory into a group's shared copy; K and S are made
 // warp-uniform (a group runs extra terms with its own tiny coefficients, and extra sub-steps are
 // discarded by the caller's select).  Every lane of the warp calls this.
@@ -191,6 +220,7 @@ template <typename R, int G_, int E_, bool HB = true>
 struct OpTridiag {
   static constexpr int G = G_, E = E_, DP_SMEM = 0;
   static constexpr bool PACKED = true;   // offers rec_p / h1_p on packed FP32 states
+  static constexpr bool CN = false;      // time step: Chebyshev series (OpTridiagCN: Crank-Nicolson)
   // resident assembly CTAs per SM to aim for (caps registers at 128 where that costs no spills)
   static constexpr int ASM_MINB = (E_ <= 6 && !HB) ? 4 : 1;
   static constexpr int EB = HB ? E_ : 1;
@@ -314,6 +344,7 @@ template <typename R, int G_, int E_>
 struct OpBitflip {
   static constexpr int G = G_, E = E_, DP_SMEM = 0;
   static constexpr bool PACKED = false;
+  static constexpr bool CN = false;
   static constexpr int ASM_MINB = 1;
   static constexpr int LE = Log2<E>::v, LG = Log2<G>::v, Q = LE + LG;
   R ah[E], al[E];        // 2(H0_ee - c)/rad as hi + lo
@@ -381,6 +412,7 @@ template <typename R, int G_, int E_>
 struct OpDense {
   static constexpr int G = G_, E = E_, DP = G_ * E_, DP_SMEM = G_ * E_;
   static constexpr bool PACKED = false;
+  static constexpr bool CN = false;
   static constexpr int ASM_MINB = 1;
   using R2 = typename C2<R>::T;
   const R2* Hs;   // shared memory
@@ -523,6 +555,133 @@ __device__ __forceinline__ void phase_rotate(double cp, double sp, bool adj, dou
 template <bool ADJ, typename R, int E, class Op>
 __device__ __forceinline__ void cheb_step(Vec<R, E>& v, const Op& op, const Cheb<R>& ch, int K, int Sw) {
   cheb_step<ADJ, false>(v, v, op, ch, K, Sw);
+}
+
+// ------------------------------------------------------------- Crank-Nicolson step (Sec. 3)
+// x = (I + i sg h H)^{-1} r (sg = +1: A = I + i tau H/2, sg = -1: B = I - i tau H/2, h = tau/2) by
+// Jacobi iterations on the split diag(1 + i sg h H_ee) + off-diagonal: each iteration shrinks the
+// error by at most rho = h max_e(|H_{e,e-1}| + |H_{e,e+1}|) (the diagonal has modulus >= 1); the
+// caller's K iterations reach rho^K below the working precision (k_cheb_prep).
+template <typename R, int E, class Op>
+__device__ __forceinline__ void cn_solve(Vec<R, E>& x, const Vec<R, E>& r, const Op& op, R h, R sg, int K) {
+  // D^{-1} = (1 - i sg h d_e) / (1 + (h d_e)^2) = dr_e - i sg di_e (op.dr, op.di)
+#pragma unroll
+  for (int e = 0; e < E; ++e) {
+    const R di = sg * op.di[e];
+    x.re[e] = fma(op.dr[e], r.re[e], di * r.im[e]);
+    x.im[e] = fma(op.dr[e], r.im[e], -di * r.re[e]);
+  }
+  for (int k = 1; k < K; ++k) {
+    Vec<R, E> o;
+    op.template cn_apply<false>(x, o);
+#pragma unroll
+    for (int e = 0; e < E; ++e) {   // y = r - i sg h (off x), then x = D^{-1} y
+      const R yr = fma(sg * h, o.im[e], r.re[e]);
+      const R yi = fma(-sg * h, o.re[e], r.im[e]);
+      const R di = sg * op.di[e];
+      x.re[e] = fma(op.dr[e], yr, di * yi);
+      x.im[e] = fma(op.dr[e], yi, -di * yr);
+    }
+  }
+}
+
+// ADJ = false: v <- A^{-1} B v.  ADJ = true: xi <- B^{-1} v, then v <- A xi (= U^H v).
+template <bool ADJ, typename R, int E, class Op>
+__device__ __forceinline__ void cn_step(Vec<R, E>& v, Vec<R, E>& xi, const Op& op, R h, int K) {
+  Vec<R, E> t;
+  if (!ADJ) {
+    op.template cn_apply<true>(v, t);
+    Vec<R, E> r;
+#pragma unroll
+    for (int e = 0; e < E; ++e) {   // r = v - i h H v
+      r.re[e] = fma(h, t.im[e], v.re[e]);
+      r.im[e] = fma(-h, t.re[e], v.im[e]);
+    }
+    cn_solve(v, r, op, h, R(1), K);
+  } else {
+    cn_solve(xi, v, op, h, R(-1), K);
+    op.template cn_apply<true>(xi, t);
+#pragma unroll
+    for (int e = 0; e < E; ++e) {   // v = xi + i h H xi
+      v.re[e] = fma(-h, t.im[e], xi.re[e]);
+      v.im[e] = fma(h, t.re[e], xi.im[e]);
+    }
+  }
+}
+
+// Tridiagonal H with the Crank-Nicolson step of Sec. 3 in place of the Chebyshev series: the same lane
+// layout and packed data, but H = H0 + u H1 itself (no centring or scaling).  ah[] holds the H0
+// diagonal (scale), cdg/cof the diagonal and the (e, e+1) couplings of H at the current control.
+template <typename R, int G_, int E_, bool HB = true>
+struct OpTridiagCN : OpTridiag<R, G_, E_, HB> {
+  using Base = OpTridiag<R, G_, E_, HB>;
+  static constexpr bool CN = true;
+  static constexpr bool PACKED = false;
+  static constexpr int E = E_, G = G_;
+  R cdg[E_], cof[E_], cofm;
+  R dr[E_], di[E_];   // inverse of the Jacobi diagonal 1 + i h H_ee: dr - i di (A), dr + i di (B)
+  R hh;               // tau / 2
+  __device__ __forceinline__ void diag_inverse() {
+#pragma unroll
+    for (int r = 0; r < E_; ++r) {
+      const R t = hh * cdg[r];
+      dr[r] = R(1) / fma(t, t, R(1));
+      di[r] = t * dr[r];
+    }
+  }
+  __device__ void scale(const double* H0d, int d, int lg, const Cheb<R>& ch) {
+    hh = ch.h;
+#pragma unroll
+    for (int r = 0; r < E_; ++r) {
+      const int e = lg * E_ + r;
+      this->ah[r] = e < d ? (R)H0d[e] : R(0);
+      cdg[r] = this->ah[r];
+    }
+    if constexpr (!HB) diag_inverse();   // the diagonal does not depend on u
+  }
+  __device__ __forceinline__ void set_u(R u, const Cheb<R>&, int lg) {
+#pragma unroll
+    for (int r = 0; r < E_; ++r) {
+      const int e = this->e0 + r;
+      const bool in = e < this->dd;
+      const R a = in ? __ldg(this->o0p + e) : R(0);
+      const R b = in ? __ldg(this->o1p + e) : R(0);
+      cof[r] = a + u * b;
+      if constexpr (HB) cdg[r] = fma(u, this->d1[r], this->ah[r]);
+    }
+    const R t = g_up<G_>(cof[E_ - 1]);
+    cofm = lg == 0 ? R(0) : t;
+    if constexpr (HB) diag_inverse();
+  }
+  // out = H in (FULL) or its off-diagonal part alone
+  template <bool FULL, class V>
+  __device__ __forceinline__ void cn_apply(const V& in, V& out) const {
+    R lre = g_up<G_>(in.re[E_ - 1]), lim = g_up<G_>(in.im[E_ - 1]);
+    R rre = g_down<G_>(in.re[0]), rim = g_down<G_>(in.im[0]);
+#pragma unroll
+    for (int r = 0; r < E_; ++r) {
+      R mre = r == 0 ? lre : in.re[r - 1], mim = r == 0 ? lim : in.im[r - 1];
+      R pre = r == E_ - 1 ? rre : in.re[r + 1], pim = r == E_ - 1 ? rim : in.im[r + 1];
+      R om = r == 0 ? cofm : cof[r - 1];
+      R xr = fma(om, mre, cof[r] * pre), xi = fma(om, mim, cof[r] * pim);
+      if (FULL) { xr = fma(cdg[r], in.re[r], xr); xi = fma(cdg[r], in.im[r], xi); }
+      out.re[r] = xr;
+      out.im[r] = xi;
+    }
+  }
+};
+
+// One time step of the op's scheme on a state (v, lo): the Chebyshev series (compensated when COMP),
+// or the Crank-Nicolson step (FP64, lo unused).
+template <bool ADJ, bool COMP, typename R, int E, class Op>
+__device__ __forceinline__ void prop_step(Vec<R, E>& v, Vec<R, E>& lo, const Op& op, const Cheb<R>& ch, int Kw,
+                                          int Sw) {
+  if constexpr (Op::CN) {
+    Vec<R, E> xi;
+    cn_step<ADJ>(v, xi, op, ch.h, Kw);
+  } else {
+    cheb_step<ADJ, COMP>(v, lo, op, ch, Kw, Sw);
+  }
 }
 
 // cheb_step on packed FP32 states (the same series, sub-steps and compensation).  Odd terms multiply

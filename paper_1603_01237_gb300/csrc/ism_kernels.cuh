@@ -45,6 +45,8 @@ struct KParams {
   int update;
   int max_spin;
   float* uf;                   // [B][Nt] FP32 copy of u (written by k_cheb_prep)
+  int scheme;                  // 0: Chebyshev series; 1: Crank-Nicolson (r0, h1n: off-diagonal row-sum
+                               //    bounds of H0 and H1)
   // direct global sweeps (large d): inputs and FP64 outputs, per-warp overlap partials
   const double2* psi_i;        // [d]
   const double2* psi_f;        // [d]
@@ -173,7 +175,7 @@ __global__ void __launch_bounds__(128, Op::ASM_MINB) k_assemble(KParams p) {
       ua = ub1;
       if (j + 2 < j1) ub1 = uval<R>(ub, ufb, j + 2);
       op.set_u(uj, ch, lg);
-      cheb_step<false, COMP>(v, lo, op, ch, Kw, Sw);
+      prop_step<false, COMP>(v, lo, op, ch, Kw, Sw);
     }
   }
   if (col < p.d) {
@@ -304,7 +306,7 @@ __global__ void __launch_bounds__(128) k_subinterval(KParams p) {
       }
       Vec<R, E> w = v, wl = lo;
       op.set_u(uj, ch, lg);
-      cheb_step<false, COMP>(w, wl, op, ch, Kw, Sw);
+      prop_step<false, COMP>(w, wl, op, ch, Kw, Sw);
       if (act) { v = w; lo = wl; }
     }
     op.h1(v, hend);
@@ -398,6 +400,41 @@ __global__ void __launch_bounds__(128) k_subinterval(KParams p) {
       zdotp(pd, hc, zr, zi);
       if (act && lg == 0 && valid) { R2 z; z.x = zr; z.y = zi; tr0[(long)s * GE] = z; }
     }
+  } else if constexpr (Op::CN) {
+    // Crank-Nicolson (Sec. 3): lambda_j = A_j xi_j, xi_j = B_j^{-1} lambda_{j+1}; the exact gradient of
+    // the discrete J_n pairs xi_j with H1 (psi_j + psi_{j+1}), so slot j receives
+    // <xi_j|H1 psi_j + H1 psi_{j+1}> (H1 psi_{j+1} is the previous slot's, kept in registers).
+    const int top = ns - 1;
+    Vec<R, E> h0, h1v, hn = hend;
+    auto ldslot = [&](int s, Vec<R, E>& h) {
+#pragma unroll
+      for (int r = 0; r < E; ++r) { R2 z = tr[(long)s * GE + r]; h.re[r] = z.x; h.im[r] = z.y; }
+    };
+    ldslot(top, h0);
+    ldslot(top > 0 ? top - 1 : top, h1v);
+    R ua = uval<R>(ub, ufb, j0 + top), ub1 = uval<R>(ub, ufb, j0 + (top > 0 ? top - 1 : top));
+    for (int s = nsw - 1; s >= 0; --s) {
+      const bool act = s < ns;
+      Vec<R, E> hc = h0;
+      const R uj = ua;
+      if (act) {
+        h0 = h1v;
+        ua = ub1;
+        if (s - 2 >= 0) { ldslot(s - 2, h1v); ub1 = uval<R>(ub, ufb, j0 + s - 2); }
+      }
+      Vec<R, E> w = dl, xi, hs;
+      op.set_u(uj, ch, lg);
+      cn_step<true>(w, xi, op, ch.h, Kw);
+#pragma unroll
+      for (int r = 0; r < E; ++r) { hs.re[r] = hc.re[r] + hn.re[r]; hs.im[r] = hc.im[r] + hn.im[r]; }
+      R zr, zi;
+      zdot(xi, hs, zr, zi);
+      if (act) {
+        dl = w;
+        hn = hc;
+        if (lg == 0 && valid) { R2 z; z.x = zr; z.y = zi; tr0[(long)s * GE] = z; }
+      }
+    }
   } else {
     const int top = ns - 1;
     Vec<R, E> h0, h1v;   // slots s and s-1, prefetched
@@ -439,9 +476,9 @@ __global__ void __launch_bounds__(128) k_subinterval(KParams p) {
     const double uj = ub[j];
     const double al = p.alpha ? p.alpha[j] : 0.0;
     const R2 za = tr0[(long)s * GE], zb = tr0[(long)(s + 1) * GE];
-    // Im(exp(-i Phi) z) for the two ends of step j
+    // Im(exp(-i Phi) z) for the two ends of step j (Crank-Nicolson: slot j holds both ends, Phi = 0)
     const double Ia = cPhi * (double)za.y - sPhi * (double)za.x;
-    const double Ib = cPhi * (double)zb.y - sPhi * (double)zb.x;
+    const double Ib = Op::CN ? 0.0 : cPhi * (double)zb.y - sPhi * (double)zb.x;
     const double g = ht * (Ia + Ib) - tb * al * uj;
     err += fabs(g);
     pen += al * uj * uj;
@@ -492,7 +529,11 @@ __global__ void __launch_bounds__(32) k_cheb_prep(KParams p) {
   }
   if (lane == 0 && p.pen) p.pen[(long)b * p.N + n] = pen;
   __shared__ Cheb<R> ch;
-  cheb_params<R>(ch, p.ctab, p.tau, p.c0, p.r0, p.h1n, (double)um, p.tol, p.phase[n], p.status);
+  if (p.scheme == 1) {
+    if (lane == 0) cn_params<R>(ch, p.tau, p.r0, p.h1n, (double)um, p.tol, p.status);
+  } else {
+    cheb_params<R>(ch, p.ctab, p.tau, p.c0, p.r0, p.h1n, (double)um, p.tol, p.phase[n], p.status);
+  }
   __syncwarp();
   const int* s = reinterpret_cast<const int*>(&ch);
   int* d = reinterpret_cast<int*>(const_cast<void*>(p.cheb)) + ((long)b * p.N + n) * (sizeof(Cheb<R>) / sizeof(int));
@@ -746,7 +787,7 @@ __global__ void __launch_bounds__(128) k_gsweep(KParams p) {
         ua = ub1;
         if (s + 2 < ns) ub1 = uval<R>(ub, ufb, jof(s + 2));
         op.set_u(uj, ch, lg);
-        cheb_step<ADJ, COMP>(v, lo, op, ch, Kw, Sw);
+        prop_step<ADJ, COMP>(v, lo, op, ch, Kw, Sw);
       }
     }
     if (valid) count_work<R>(p.count, ch, j1 - j0, lg);

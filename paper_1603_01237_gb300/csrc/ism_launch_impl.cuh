@@ -70,11 +70,14 @@ cudaError_t launch_gsweep_t(const KParams& p, cudaStream_t st) {
 
 // OpA: lane layout of the throughput-bound assembly (few lanes, many elements per lane);
 // OpS: lane layout of the latency-bound sub-interval sweep (more lanes per state).
-template <typename R, class OpA, class OpS = OpA>
+// SWEEPS2: also build the concurrent two-trajectory sweeps (otherwise the sub-problems of the
+// two-trajectory form run in k_subinterval).
+template <typename R, class OpA, class OpS = OpA, bool SWEEPS2 = true>
 void fill_set(KernelSet* ks) {
   ks->assemble = &launch_assemble_t<R, OpA>;
   ks->subinterval = &launch_subinterval_t<R, OpS>;
-  ks->sweeps2 = &launch_sweeps2_t<R, OpS>;
+  if constexpr (SWEEPS2) ks->sweeps2 = &launch_sweeps2_t<R, OpS>;
+  else ks->sweeps2 = nullptr;
   ks->gsweep = &launch_gsweep_t<R, OpS>;
   ks->G = OpS::G;
   ks->E = OpS::E;

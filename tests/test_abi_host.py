@@ -146,3 +146,26 @@ def test_footprint_needs_no_gpu_and_scales_with_the_problem(lib):
     with pytest.raises(abi.IsmError) as ei:
         abi.footprint(W.config("rotor41", Nt=100, N=200))
     assert ei.value.status == 1
+
+
+def test_crank_nicolson_option_validated_on_the_host(lib):
+    """The Crank-Nicolson scheme is accepted for the tridiagonal kind in FP64 only; its plans hold no
+    second trajectory (the sub-problems run in one group)."""
+    import workloads as W
+    from paper_1603_01237_gb300 import abi
+
+    w = W.config("rotor41", Nt=2000, N=16)
+    f_cn = abi.footprint(w, precision="fp64", scheme="crank_nicolson", step1=1)
+    f_ch = abi.footprint(w, precision="fp64", step1=1)
+    assert 0 < f_cn < f_ch
+    for kw in ({"precision": "mixed"},):
+        with pytest.raises(abi.IsmError) as ei:
+            abi.footprint(w, scheme="crank_nicolson", **kw)
+        assert ei.value.status == abi.ISM_EUNSUPPORTED
+    with pytest.raises(abi.IsmError) as ei:
+        abi.footprint(W.random_dense(5, 3, T=1.0, Nt=50, N=2), scheme="crank_nicolson")
+    assert ei.value.status == abi.ISM_EUNSUPPORTED
+    prob, opt, keep = abi.problem_and_options(w, precision="fp64")
+    opt.scheme = 7
+    n = abi.C.c_size_t()
+    assert lib.ism_plan_footprint(abi.C.byref(prob), abi.C.byref(opt), abi.C.byref(n)) == abi.ISM_EINVAL
