@@ -3,10 +3,11 @@
 
 A step is one pass of Algorithm 1 (propagator assembly, chain and intermediate states, sub-interval
 forward/adjoint/gradient sweeps, control update) over a batch of independent rigid-rotor problems
-(d = 41, Nt = 20000, N = 128, mixed precision, 64 problems per launch by default).  The value is
+(d = 41, Nt = 20000, N = 128, mixed precision, 2048 problems per launch by default).  The value is
 ISM iterations per second summed over the batch; the line also carries the one-problem solve
-latency (p50/p99 of complete 50-iteration solves), the plain FP64 one-problem path, the end-to-end
-rate through host buffers, the roofline of the dominant kernel and the oracle on the host cores.
+latency (p50/p99 of complete 50-iteration solves), the plain FP64 one-problem path, the paper's
+Crank-Nicolson scheme in FP64 (batched and one problem), a serving mix, the end-to-end rate through
+host buffers, the roofline of the dominant kernel and the oracle on the host cores.
 Prints one JSON line.
 
     python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference] [--config NAME]
@@ -58,6 +59,7 @@ def parse():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-fp64", action="store_true")
     ap.add_argument("--no-serving", action="store_true")
+    ap.add_argument("--no-cn", action="store_true", help="skip the Crank-Nicolson (Sec. 3 scheme) leg")
     return ap.parse_args()
 
 
@@ -310,6 +312,103 @@ def serving_mix(P, W, seed: int, n_req: int = 48, rate: float = 200.0, slots: in
 
 
 # ------------------------------------------------------------------------------ our arm
+# ------------------------------------------------------------------------------ Crank-Nicolson leg
+CN_BATCH = 1024   # saturates the FP64 pipe (256 problems per launch take the same time per launch)
+FP64_PEAK_TFLOPS = SMS * 2 * 2 * SM_MAX_MHZ * 1e6 / 1e12
+FP64_SRC = "derived: 152 SMs x 2 FP64 FMA/clk x 2 flop x 2070 MHz (no measured FP64 peak)"
+
+
+def cn_jacobi_iterations(w, tol: float = 1e-17) -> int:
+    """Jacobi iterations per Crank-Nicolson solve, as the parameter kernel chooses them:
+    rho = (tau/2)(off0 + max|u| off1), rho^K <= tol."""
+    off = lambda A: float(np.max(np.abs(A - np.diag(np.diag(A))).sum(axis=1)))
+    rho = 0.5 * w.T / w.Nt * (off(w.H0) + float(np.max(np.abs(w.u0))) * off(w.H1)) * (1 + 1e-6)
+    return 1 if rho <= 0 else max(1, int(np.ceil(np.log(tol) / np.log(rho))))
+
+
+def cn_flops_per_state_step(d: int, K: int) -> float:
+    """FP64 flops of one Crank-Nicolson step of one state with tridiagonal H (per complex element:
+    H v 12, right-hand side 4, first Jacobi iteration 6, each further one 16 -- off-diagonal part
+    of H 6, update 4, diagonal inverse 6)."""
+    return d * (22.0 + 16.0 * (K - 1))
+
+
+def crank_nicolson_leg(P, w, stream, steps: int, cpu: bool):
+    """The Sec. 3 scheme in FP64 on the same rotor problem: batched direct sweeps (CN_BATCH problems
+    per launch; inputs larger than L2), one-problem latency by the assembly path, the FP64 ALU
+    roofline of the dominant kernel and the Crank-Nicolson oracle on a bounded sample."""
+    import torch
+
+    K = cn_jacobi_iterations(w)
+    B = CN_BATCH
+    rng = np.random.default_rng(4000)
+    amp = float(np.max(np.abs(w.u0)))
+    U0 = np.stack([w.u0] + [rng.uniform(-amp, amp, w.Nt) for _ in range(B - 1)])
+    plan = P.Plan(w, precision="fp64", batch=B, stream=stream, scheme="crank_nicolson", step1=2)
+    u = torch.tensor(U0, dtype=torch.float64, device="cuda").contiguous()
+    plan.ism_iterate(1, u, None, None)
+    n = max(2, steps // 10)
+    plan.ism_set_profiling(True)
+    plan.ism_get_stats(reset=True)
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    torch.cuda.synchronize()
+    with torch.cuda.stream(stream):
+        e0.record(stream)
+        plan.ism_iterate(n, u, None, None)
+        e1.record(stream)
+    torch.cuda.synchronize()
+    ms = e0.elapsed_time(e1) / n
+    st = plan.ism_get_stats(reset=True)
+    plan.close()
+    names = ["k_gsweep", "k_phi", "k_subinterval"]
+    dom = 0 if st["ms"][0] >= st["ms"][2] else 2
+    ms_launch = st["ms"][dom] / n
+    flops = 2.0 * w.Nt * B * cn_flops_per_state_step(int(w.d), K)   # two sweeps per launch
+    achieved = flops / (ms_launch / 1e3) / 1e12
+    roof = {"kernel": names[dom], "bound": "alu", "achieved": achieved, "peak": FP64_PEAK_TFLOPS,
+            "unit": "TFLOP/s", "frac": achieved / FP64_PEAK_TFLOPS, "traffic": None, "peak_source": FP64_SRC,
+            "flops_per_launch": flops, "ms_per_launch": ms_launch}
+    p1 = P.Plan(w, precision="fp64", batch=1, stream=stream, scheme="crank_nicolson")
+    u1 = torch.tensor(w.u0, dtype=torch.float64, device="cuda").reshape(1, -1).contiguous()
+    p1.ism_iterate(1, u1, None, None)
+    torch.cuda.synchronize()
+    with torch.cuda.stream(stream):
+        e0.record(stream)
+        p1.ism_iterate(3, u1, None, None)
+        e1.record(stream)
+    torch.cuda.synchronize()
+    ms1 = e0.elapsed_time(e1) / 3
+    p1.close()
+    out = {"value": B / (ms / 1e3), "unit": UNIT, "batch": B, "ms_per_iteration": ms, "jacobi_iterations": K,
+           "precision": "fp64", "l2": "inputs larger than L2 (trajectory slots 15.8 GB)",
+           "latency_ms_per_iteration_batch1": ms1, "phase_share": {nm: st["ms"][i] / max(1e-12, sum(st["ms"]))
+                                                                  for i, nm in enumerate(names)},
+           "roofline": roof}
+    if cpu:
+        from oracle import cn_oracle
+
+        div = SAMPLE_DIV.get("rotor41", 8)
+        ws = W_config(w, Nt=w.Nt // div, N=max(1, w.N // div))
+        tot, n_s = 0.0, 0
+        while tot < 10.0 and n_s < 20:
+            t0 = time.perf_counter()
+            cn_oracle.ism_iteration(ws, ws.u0, ws.rho, ws.local_iters)
+            tot += time.perf_counter() - t0
+            n_s += 1
+        out["cpu_baseline"] = {"value": n_s * (ws.Nt / w.Nt) / tot, "unit": UNIT, "cores": 1, "kind": "oracle",
+                               "sample": f"one Crank-Nicolson oracle ISM iteration on rotor41 truncated to "
+                                         f"Nt={ws.Nt}, N={ws.N}, scaled by {ws.Nt / w.Nt:g}; {n_s} repetitions, "
+                                         f"{tot:.1f} s"}
+    return out
+
+
+def W_config(w, Nt: int, N: int):
+    """The same named workload at another Nt, N (same seed: u0 drawn at the new length)."""
+    import workloads as W
+
+    return W.config(w.name, Nt=Nt, N=N)
+
+
 def run_ours(args):
     import torch
 
@@ -468,6 +567,9 @@ def run_ours(args):
              "p99_ms": float(np.percentile(sol_ms, 99)), "ms_per_iteration": float(np.median(sol_ms)) / it_solve}
 
     serving = None if args.no_serving else serving_mix(P, W, seed=3000 + rank)
+    cn = None
+    if not args.no_cn and getattr(w, "kind", "") == "tridiag":
+        cn = crank_nicolson_leg(P, w, stream, args.steps, cpu=(rank == 0 and world == 1 and not args.no_cpu_baseline))
 
     cpu = None
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
@@ -492,6 +594,7 @@ def run_ours(args):
         "solve_latency": solve,
         "serving": serving,
         "fp64_plain": fp64,
+        "crank_nicolson": cn,
         "phase_share": phase_share,
         "roofline": roof,
         "cpu_baseline": cpu,
