@@ -3,7 +3,7 @@
 
 A step is one pass of Algorithm 1 (propagator assembly, chain and intermediate states, sub-interval
 forward/adjoint/gradient sweeps, control update) over a batch of independent rigid-rotor problems
-(d = 41, Nt = 20000, N = 128, mixed precision, 2048 problems per launch by default).  The value is
+(d = 41, Nt = 20000, N = 128, mixed precision, 2432 = 16 x 152 problems per launch by default).  The value is
 ISM iterations per second summed over the batch; the line also carries the one-problem solve
 latency (p50/p99 of complete 50-iteration solves), the plain FP64 one-problem path, the paper's
 Crank-Nicolson scheme in FP64 (batched and one problem), a serving mix, the end-to-end rate through
@@ -11,7 +11,7 @@ host buffers, the roofline of the dominant kernel and the oracle on the host cor
 Prints one JSON line.
 
     python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference] [--config NAME]
-                    [--batch B] [--N N]
+                    [--batch B] [--N N] [--Nt NT]
 """
 from __future__ import annotations
 
@@ -40,7 +40,9 @@ DESCR = {"rotor41": "rigid rotor j<=40, maximise <cos theta>(T)",
          "ising1024": "10-spin open Ising chain, X control, |0^10> -> |1^10>",
          "gp512": "1D Gross-Pitaevskii condensate, 512-point grid, trap centre control, ground -> odd state"}
 SAMPLE_DIV = {"rotor41": 8, "spin16": 1, "ising1024": 64, "gp512": 8}
-BATCH_DEFAULT = {"rotor41": 2048, "spin16": 2048, "ising1024": 64, "gp512": 256}   # independent solves per launch
+# independent solves per launch: multiples of the 152 SMs (16 problems per SM for the lane-group
+# sweeps, one CTA per SM and direction for ising1024, two 304-CTA waves for the grid model)
+BATCH_DEFAULT = {"rotor41": 2432, "spin16": 2432, "ising1024": 76, "gp512": 304}
 SOLVE_ITERS = {"rotor41": 50, "spin16": 20, "ising1024": 20, "gp512": 20}   # oracle sample = Nt/div steps, N/div sub-intervals
 FP32_LANES_PER_SM = 128
 SMS = 152
@@ -55,6 +57,8 @@ def parse():
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--config", default="rotor41")
     ap.add_argument("--N", type=int, default=None, help="sub-intervals (default: the workload's own)")
+    ap.add_argument("--Nt", type=int, default=None,
+                    help="time steps (default: the workload's own; smaller for profiler captures)")
     ap.add_argument("--batch", type=int, default=None, help="problems per launch (default: per workload)")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-fp64", action="store_true")
@@ -424,7 +428,7 @@ def run_ours(args):
     import paper_1603_01237_gb300 as P
     import workloads as W
 
-    w = load_workload(args.config, N=args.N)
+    w = load_workload(args.config, N=args.N, Nt=args.Nt)
     d = dim_of(w)
     B = args.batch or BATCH_DEFAULT.get(args.config, 1)
     stream = torch.cuda.Stream()

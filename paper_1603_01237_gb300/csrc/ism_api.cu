@@ -510,8 +510,10 @@ int plan_build(const ism_problem* prob, const ism_options* opt, void* cuda_strea
   if (opt->step1 < 0 || opt->step1 > 2) return fail(ISM_EINVAL, "step1 must be 0, 1 or 2");
   if (opt->scheme != ISM_SCHEME_CHEBYSHEV && opt->scheme != ISM_SCHEME_CRANK_NICOLSON)
     return fail(ISM_EINVAL, "scheme must be ISM_SCHEME_CHEBYSHEV or ISM_SCHEME_CRANK_NICOLSON");
-  if (opt->scheme == ISM_SCHEME_CRANK_NICOLSON && (p.kind != ISM_H_TRIDIAG || opt->precision != ISM_FP64))
-    return fail(ISM_EUNSUPPORTED, "the Crank-Nicolson scheme is built for the tridiagonal kind in FP64");
+  if (opt->scheme == ISM_SCHEME_CRANK_NICOLSON &&
+      (p.kind == ISM_H_GRID_GP || p.d > 64 || opt->precision != ISM_FP64))
+    return fail(ISM_EUNSUPPORTED, "the Crank-Nicolson scheme is built in FP64 for the tridiagonal, dense and bit-flip kinds "
+                                  "with d <= 64");
 
   ism_plan_s* P = new (std::nothrow) ism_plan_s();
   if (!P) return fail(ISM_ENOMEM, "host allocation");
@@ -581,7 +583,7 @@ int plan_build(const ism_problem* prob, const ism_options* opt, void* cuda_strea
     h1diag = false;
     for (int e = 0; e < d; ++e) h1diag |= p.H1[e] != 0.0;
   }
-  bool ok = P->scheme == ISM_SCHEME_CRANK_NICOLSON ? ism::kernels_tridiag_cn(P->prec, d, h1diag, &P->ks)
+  bool ok = P->scheme == ISM_SCHEME_CRANK_NICOLSON ? ism::kernels_cn(P->prec, p.kind, d, h1diag, &P->ks)
                                                     : ism::select_kernels(P->prec, p.kind, d, &P->ks, h1diag);
   if (!ok) { delete P; return fail(ISM_EUNSUPPORTED, "no compiled kernel for this kind and d"); }
   P->direct = !P->ks.large && (opt->step1 == 2 || (opt->step1 == 0 && P->B >= 96));
@@ -596,11 +598,25 @@ int plan_build(const ism_problem* prob, const ism_options* opt, void* cuda_strea
     // H1, which bound the contraction of the Jacobi solve
     P->c0 = 0.0;
     P->r0 = P->h1n = 0.0;
-    for (int e = 0; e < d; ++e) {
-      const double l0 = e > 0 ? std::fabs(p.H0[d + e - 1]) : 0.0, r0 = e < d - 1 ? std::fabs(p.H0[d + e]) : 0.0;
-      const double l1 = e > 0 ? std::fabs(p.H1[d + e - 1]) : 0.0, r1 = e < d - 1 ? std::fabs(p.H1[d + e]) : 0.0;
-      P->r0 = std::fmax(P->r0, l0 + r0);
-      P->h1n = std::fmax(P->h1n, l1 + r1);
+    if (p.kind == ISM_H_TRIDIAG) {
+      for (int e = 0; e < d; ++e) {
+        const double l0 = e > 0 ? std::fabs(p.H0[d + e - 1]) : 0.0, r0 = e < d - 1 ? std::fabs(p.H0[d + e]) : 0.0;
+        const double l1 = e > 0 ? std::fabs(p.H1[d + e - 1]) : 0.0, r1 = e < d - 1 ? std::fabs(p.H1[d + e]) : 0.0;
+        P->r0 = std::fmax(P->r0, l0 + r0);
+        P->h1n = std::fmax(P->h1n, l1 + r1);
+      }
+    } else if (p.kind == ISM_H_BITFLIP) {   // H0 diagonal; every row of H1 holds |h_i| once per flip
+      int q = 0;
+      while ((1 << q) < d) ++q;
+      for (int i = 0; i < q; ++i) P->h1n += std::fabs(p.H1[i]);
+    } else {   // dense
+      for (int e = 0; e < d; ++e) {
+        double s0 = 0.0, s1 = 0.0;
+        for (int f = 0; f < d; ++f)
+          if (f != e) { s0 += std::fabs(p.H0[(size_t)e * d + f]); s1 += std::fabs(p.H1[(size_t)e * d + f]); }
+        P->r0 = std::fmax(P->r0, s0);
+        P->h1n = std::fmax(P->h1n, s1);
+      }
     }
   } else {
     Bounds bd = bounds_of(p.kind, d, p.H0, p.H1);

@@ -671,6 +671,75 @@ struct OpTridiagCN : OpTridiag<R, G_, E_, HB> {
   }
 };
 
+// Bit-flip H with the Crank-Nicolson step: diagonal H0 (the Jacobi diagonal, independent of u) and
+// off-diagonal u H1 = u sum_i h_i X_i.
+template <typename R, int G_, int E_>
+struct OpBitflipCN : OpBitflip<R, G_, E_> {
+  using Base = OpBitflip<R, G_, E_>;
+  static constexpr bool CN = true;
+  static constexpr int E = E_, G = G_, Q = Base::Q;
+  R cdg[E_], dr[E_], di[E_], hh;
+  __device__ void scale(const double* H0d, int d, int lg, const Cheb<R>& ch) {
+    hh = ch.h;
+#pragma unroll
+    for (int r = 0; r < E_; ++r) {
+      cdg[r] = (R)H0d[lg * E_ + r];
+      const R t = hh * cdg[r];
+      dr[r] = R(1) / fma(t, t, R(1));
+      di[r] = t * dr[r];
+    }
+  }
+  __device__ __forceinline__ void set_u(R u, const Cheb<R>&, int) {
+#pragma unroll
+    for (int i = 0; i < Q; ++i) this->yh[i] = u * this->h[i];
+  }
+  template <bool FULL, class V>
+  __device__ __forceinline__ void cn_apply(const V& in, V& out) const {
+    V t;
+#pragma unroll
+    for (int r = 0; r < E_; ++r) {
+      t.re[r] = FULL ? cdg[r] * in.re[r] : R(0);
+      t.im[r] = FULL ? cdg[r] * in.im[r] : R(0);
+    }
+    this->flips(in, t, this->yh);
+    out = t;
+  }
+};
+
+// Dense H with the Crank-Nicolson step: H = H0 + u H1 from the shared-memory pairs; the Jacobi
+// diagonal H0_ee + u H1_ee is read from the same pairs.
+template <typename R, int G_, int E_>
+struct OpDenseCN : OpDense<R, G_, E_> {
+  using Base = OpDense<R, G_, E_>;
+  static constexpr bool CN = true;
+  static constexpr int E = E_, G = G_, DP = Base::DP;
+  R cdg[E_], dr[E_], di[E_], hh;
+  __device__ void scale(const double*, int, int, const Cheb<R>& ch) { hh = ch.h; }
+  __device__ __forceinline__ void set_u(R u, const Cheb<R>&, int) {
+    this->u2 = u;   // mv<true> forms H0_ef + u H1_ef with s2 = 1
+#pragma unroll
+    for (int r = 0; r < E_; ++r) {
+      const int e = this->lg * E_ + r;
+      const typename Base::R2 p = this->Hs[e * DP + e];
+      cdg[r] = fma(u, p.y, p.x);
+      const R t = hh * cdg[r];
+      dr[r] = R(1) / fma(t, t, R(1));
+      di[r] = t * dr[r];
+    }
+  }
+  template <bool FULL, class V>
+  __device__ __forceinline__ void cn_apply(const V& in, V& out) const {
+    this->template mv<true>(in, out, R(1));
+    if (!FULL) {
+#pragma unroll
+      for (int r = 0; r < E_; ++r) {
+        out.re[r] = fma(-cdg[r], in.re[r], out.re[r]);
+        out.im[r] = fma(-cdg[r], in.im[r], out.im[r]);
+      }
+    }
+  }
+};
+
 // One time step of the op's scheme on a state (v, lo): the Chebyshev series (compensated when COMP),
 // or the Crank-Nicolson step (FP64, lo unused).
 template <bool ADJ, bool COMP, typename R, int E, class Op>

@@ -1,5 +1,7 @@
-// Tridiagonal Hamiltonians with the Crank-Nicolson time step of Sec. 3 (FP64, d <= 64): the
-// lane layouts of the Chebyshev build; the sub-problems always run the one-group sweep (k_subinterval).
+// The Crank-Nicolson time step of Sec. 3 (FP64, d <= 64) for the tridiagonal, bit-flip and dense
+// kinds: the lane layouts of the Chebyshev builds; the sub-problems always run the one-group sweep
+// (k_subinterval).
+#include "ism.h"
 #include "ism_launch_impl.cuh"
 
 namespace ism {
@@ -17,9 +19,38 @@ static bool pick_cn(int d, KernelSet* ks) {
   }
 }
 
-bool kernels_tridiag_cn(int prec, int d, bool h1diag, KernelSet* ks) {
+static bool pick_bitflip_cn(int d, KernelSet* ks) {
+  using R = double;
+  switch (d) {
+    case 2: fill_set<R, OpBitflipCN<R, 2, 1>, OpBitflipCN<R, 2, 1>, false>(ks); return true;
+    case 4: fill_set<R, OpBitflipCN<R, 4, 1>, OpBitflipCN<R, 4, 1>, false>(ks); return true;
+    case 8: fill_set<R, OpBitflipCN<R, 4, 2>, OpBitflipCN<R, 8, 1>, false>(ks); return true;
+    case 16: fill_set<R, OpBitflipCN<R, 4, 4>, OpBitflipCN<R, 16, 1>, false>(ks); return true;
+    case 32: fill_set<R, OpBitflipCN<R, 8, 4>, OpBitflipCN<R, 16, 2>, false>(ks); return true;
+    case 64: fill_set<R, OpBitflipCN<R, 8, 8>, OpBitflipCN<R, 16, 4>, false>(ks); return true;
+    default: return false;
+  }
+}
+
+static bool pick_dense_cn(int d, KernelSet* ks) {
+  using R = double;
+  switch ((d + 15) / 16) {
+    case 1: fill_set<R, OpDenseCN<R, 16, 1>, OpDenseCN<R, 16, 1>, false>(ks); return true;
+    case 2: fill_set<R, OpDenseCN<R, 16, 2>, OpDenseCN<R, 16, 2>, false>(ks); return true;
+    case 3: fill_set<R, OpDenseCN<R, 16, 3>, OpDenseCN<R, 16, 3>, false>(ks); return true;
+    case 4: fill_set<R, OpDenseCN<R, 16, 4>, OpDenseCN<R, 16, 4>, false>(ks); return true;
+    default: return false;
+  }
+}
+
+bool kernels_cn(int prec, int kind, int d, bool h1diag, KernelSet* ks) {
   if (prec != 0 || d < 1 || d > 64) return false;
-  return h1diag ? pick_cn<true>(d, ks) : pick_cn<false>(d, ks);
+  switch (kind) {
+    case ISM_H_TRIDIAG: return h1diag ? pick_cn<true>(d, ks) : pick_cn<false>(d, ks);
+    case ISM_H_BITFLIP: return pick_bitflip_cn(d, ks);
+    case ISM_H_DENSE: return pick_dense_cn(d, ks);
+    default: return false;
+  }
 }
 
 }  // namespace ism

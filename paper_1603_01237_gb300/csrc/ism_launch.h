@@ -29,7 +29,8 @@ bool kernels_tridiag(int prec, int d, bool h1diag, KernelSet* ks);   // h1diag: 
 bool kernels_bitflip(int prec, int d, KernelSet* ks);
 bool kernels_dense(int prec, int d, KernelSet* ks);
 bool kernels_large_bitflip(int prec, int d, KernelSet* ks);   // d = 128, 256, 512, 1024
-bool kernels_tridiag_cn(int prec, int d, bool h1diag, KernelSet* ks);   // Crank-Nicolson step, FP64 only
+// Crank-Nicolson step (FP64 only): tridiagonal, bit-flip (d <= 64) and dense kinds
+bool kernels_cn(int prec, int kind, int d, bool h1diag, KernelSet* ks);
 cudaError_t launch_chain(int prec, const ChainParams& p, size_t smem, cudaStream_t st);   // k_chain + k_phi
 cudaError_t launch_phi(int prec, const ChainParams& p, cudaStream_t st);                   // k_phi alone
 bool select_kernels(int prec, int kind, int d, KernelSet* ks, bool h1diag = true);

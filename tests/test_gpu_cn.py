@@ -1,5 +1,6 @@
 """Crank-Nicolson plans (the time step of Sec. 3) through the C ABI vs the Crank-Nicolson oracle on
-identical seeded inputs, FP64: intermediate states by both step-1 paths (assembly + chain, plain and
+identical seeded inputs, FP64, for the tridiagonal, bit-flip and dense kinds: intermediate states
+by both step-1 paths (assembly + chain, plain and
 blocked; direct sweeps), sub-problem gradients and J_n, Algorithm 1 iterations, the global gradient
 (Theorem 2 form), and the plan's errors for controls beyond the Jacobi solve's range.
 
@@ -60,6 +61,13 @@ CASES = [
     ("strong12", _strong(12, 71, T=2.0, Nt=120, N=7)),
     ("strong33-h1diag-obs", _strong(33, 72, T=2.0, Nt=150, N=9, objective="observable", h1diag=True)),
     ("tridiag2", W.rabi(0.7, 0.3, T=3.0, Nt=64, N=8).with_(kind="tridiag")),
+    # the bit-flip and dense kinds (spin models, generic H)
+    ("spin16", W.config("spin16", Nt=400, N=4)),
+    ("bitflip64-ragged", W.with_random_target(W.spin_chain(6, 67, T=2.0, Nt=201, N=7, u_amp=1.5), 3)),
+    ("bitflip2", W.with_random_target(W.spin_all_to_all(1, 5, T=3.0, Nt=64, N=4, u_amp=1.5), 1)),
+    ("dense5", W.random_dense(5, 61, T=2.0, Nt=203, N=6)),
+    ("dense41-obs", W.random_dense(41, 62, T=2.0, Nt=150, N=9, objective="observable")),
+    ("dense64", W.random_dense(64, 63, T=2.0, Nt=120, N=5)),
 ]
 IDS = [c[0] for c in CASES]
 
@@ -90,8 +98,11 @@ def test_cn_subinterval_grad(P, name, w):
     assert np.max(np.abs(Jn[0] - Jn_o)) <= 1e-12 * max(1.0, np.abs(Jn_o).max())
 
 
+ITER = [CASES[i] for i in (0, 1, 2, 3, 6, 9)]
+
+
 @pytest.mark.parametrize("step1", [1, 2])
-@pytest.mark.parametrize("name,w", CASES[:4], ids=IDS[:4])
+@pytest.mark.parametrize("name,w", ITER, ids=[c[0] for c in ITER])
 def test_cn_iterate_matches_algorithm1(P, name, w, step1):
     iters = 3
     u_o, J_o, F_o, E_o = C.ism_solve(w, w.u0, iters, w.rho)
