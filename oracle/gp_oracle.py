@@ -5,7 +5,12 @@ reference legs may import this module.  It shares no code with the CUDA path.
 
 Model (Sec. 4, condensates, with the readings listed in the design notes): on a periodic grid
 x_k = x_min + k dx, k = 0..n-1, the state obeys i d/dt psi = (-1/2 d^2/dx^2 + V(x, u) + g |psi|^2) psi
-with V(x, u) = (x - u)^2 / 2; <a|b> = sum_k conj(a_k) b_k dx; J = Re<psi(T)|psi_f> (alpha = 0).
+with <a|b> = sum_k conj(a_k) b_k dx and J = Re<psi(T)|psi_f> (alpha = 0).  Two potentials:
+  harmonic trap with a control-shifted centre, V(x, u) = (x - u)^2 / 2;
+  the double well of Sec. 4 (radio-frequency splitting, control lambda = u, separation d > 0):
+      V(x, u) = (|x| - u d/2)^2 / 2          for |x| > u d/4,
+      V(x, u) = ((u d)^2 / 8 - x^2) / 2      otherwise,
+  whose derivative is dV/du = -(d/2)(|x| - u d/2), resp. u d^2 / 8.
 
 Time step (Strang splitting, Eq. (OS), written for -1/2 d^2 so the half kinetic factor in Fourier
 space is exp(-i tau k^2 / 4)):  a = K psi_j with K = F^-1 diag(exp(-i tau k^2/4)) F,
@@ -16,7 +21,7 @@ Adjoint (reverse mode of the discrete map, Wirtinger calculus): with dJ = Re<lam
 lambda_Nt = psi_f and, for one step at w = a_j,
     mu = exp(+i tau theta) K^H lambda_{j+1},
     lambda_j = K^H [ mu + 2 tau g Im(conj(mu) w) w ],
-    dJ/du_j = tau sum_k dV/du(x_k) Im(conj(mu_k) w_k) dx,   dV/du = -(x - u_j).
+    dJ/du_j = tau sum_k dV/du(x_k) Im(conj(mu_k) w_k) dx.
 Nonlinear ISM (Sec. 4): initial states psi(t_n) on the forward trajectory, targets chi(t_n) on the
 adjoint trajectory, J_n = Re<psi_n(t_{n+1})|chi(t_{n+1})>; chi(t_n) is read as the discrete adjoint
 lambda_{j_n} of the full problem.
@@ -27,7 +32,7 @@ import numpy as np
 
 from .ism_oracle import partition
 
-__all__ = ["strang_step", "forward", "objective", "adjoint_sweep", "global_gradient", "intermediate_pairs",
+__all__ = ["potential", "potential_du", "strang_step", "forward", "objective", "adjoint_sweep", "global_gradient", "intermediate_pairs",
            "subinterval", "subinterval_all", "ism_iteration", "ism_solve", "gradient_method"]
 
 
@@ -43,8 +48,28 @@ def _KH(w, v):
     return np.fft.ifft(np.conj(_half_kinetic(w)) * np.fft.fft(v))
 
 
+def potential(w, x, u_j):
+    """V(x, u_j) for the workload's potential (module docstring)."""
+    x = np.asarray(x, dtype=np.float64)
+    if getattr(w, "potential", "harmonic") == "harmonic":
+        return 0.5 * (x - u_j) ** 2
+    d = w.dw
+    ax = np.abs(x)
+    return np.where(ax > u_j * d / 4.0, 0.5 * (ax - u_j * d / 2.0) ** 2, 0.5 * ((u_j * d) ** 2 / 8.0 - x ** 2))
+
+
+def potential_du(w, x, u_j):
+    """dV/du at (x, u_j)."""
+    x = np.asarray(x, dtype=np.float64)
+    if getattr(w, "potential", "harmonic") == "harmonic":
+        return -(x - u_j)
+    d = w.dw
+    ax = np.abs(x)
+    return np.where(ax > u_j * d / 4.0, -(d / 2.0) * (ax - u_j * d / 2.0), u_j * d * d / 8.0 + 0.0 * x)
+
+
 def _theta(w, a, u_j):
-    return 0.5 * (w.x - u_j) ** 2 + w.g * np.abs(a) ** 2
+    return potential(w, w.x, u_j) + w.g * np.abs(a) ** 2
 
 
 def strang_step(w, psi, u_j):
@@ -80,8 +105,7 @@ def _adjoint_step(w, lam_next, psi_j, u_j):
     th = _theta(w, a, u_j)
     mu = np.exp(1j * w.tau * th) * _KH(w, lam_next)
     lam = _KH(w, mu + 2.0 * w.tau * w.g * np.imag(np.conj(mu) * a) * a)
-    dVdu = -(w.x - u_j)
-    g = w.tau * np.sum(dVdu * np.imag(np.conj(mu) * a)) * w.dx
+    g = w.tau * np.sum(potential_du(w, w.x, u_j) * np.imag(np.conj(mu) * a)) * w.dx
     return lam, float(g)
 
 

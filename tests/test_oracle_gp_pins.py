@@ -81,3 +81,86 @@ def test_gp_rho_increases_J():
     w = _small(g=1.0, Nt=40, N=4, T=2.0)
     _, J, _, _ = G.ism_solve(w, w.u0, 4, 0.1)
     assert np.all(np.diff(J) > 0)
+
+
+# ------------------------------------------------------------------ double-well potential (Sec. 4)
+def _dw_small(g=1.0, n=32, Nt=20, N=4, T=0.8, seed=4, dw=4.0):
+    """Even initial state (harmonic ground state); the target is a random state, since the double
+    well conserves parity and an odd target would have zero overlap for every control."""
+    rng = np.random.default_rng(seed)
+    psi_i, _ = W.gp_stationary_states(n, 20.0, -10.0, g, dt=2e-3, steps=3000)
+    psi_f = rng.standard_normal(n) + 1j * rng.standard_normal(n)
+    psi_f = psi_f / np.sqrt(np.sum(np.abs(psi_f) ** 2) * (20.0 / n))
+    return W.GPWorkload(name="dw-small", n=n, L=20.0, x_min=-10.0, g=g, psi_i=psi_i, psi_f=psi_f, T=T, Nt=Nt,
+                        N=N, u0=rng.uniform(0.2, 1.2, Nt), potential="double_well", dw=dw)
+
+
+def test_double_well_potential_is_c1_and_its_derivative_matches_differences():
+    """The two branches meet with equal value and slope at |x| = u d/4 (a dropped factor in either
+    branch breaks this), and dV/du equals central differences of V in u away from that point."""
+    w = _dw_small()
+    for u in (0.3, 1.0, 1.7):
+        xb = u * w.dw / 4.0
+        for x0 in (xb, -xb):
+            lo = G.potential(w, np.array([x0 * (1 - 1e-10)]), u)[0]
+            hi = G.potential(w, np.array([x0 * (1 + 1e-10)]), u)[0]
+            assert abs(lo - hi) < 1e-9
+            dlo = G.potential_du(w, np.array([x0 * (1 - 1e-10)]), u)[0]
+            dhi = G.potential_du(w, np.array([x0 * (1 + 1e-10)]), u)[0]
+            assert abs(dlo - dhi) < 1e-8
+    x = np.linspace(-9.7, 9.7, 97)
+    for u in (-0.4, 0.3, 1.0, 1.7):
+        h = 1e-5
+        fd = (G.potential(w, x, u + h) - G.potential(w, x, u - h)) / (2 * h)
+        far = np.abs(np.abs(x) - u * w.dw / 4.0) > 1e-3
+        assert np.max(np.abs(fd - G.potential_du(w, x, u))[far]) < 1e-8
+
+
+def test_double_well_at_zero_control_is_the_harmonic_trap():
+    """V(x, 0) = x^2/2 = the harmonic trap at u = 0: identical trajectories."""
+    w = _dw_small(Nt=40)
+    h = w.with_(potential="harmonic", dw=0.0)
+    zero = np.zeros(w.Nt)
+    a = G.forward(w, zero, w.psi_i, 0, w.Nt)
+    b = G.forward(h, zero, h.psi_i, 0, h.Nt)
+    assert np.max(np.abs(a - b)) < 1e-14
+
+
+def test_double_well_conserves_parity():
+    """V(-x, u) = V(x, u): an even state stays even under any control (grid symmetric about 0)."""
+    w = _dw_small(Nt=60)
+    psi = G.forward(w, w.u0, w.psi_i, 0, w.Nt)[-1]
+    mirror = psi[(-np.arange(w.n)) % w.n]
+    assert np.max(np.abs(psi - mirror)) < 1e-12
+    assert np.max(np.abs(w.psi_i - w.psi_i[(-np.arange(w.n)) % w.n])) < 1e-12
+
+
+@pytest.mark.parametrize("g", [0.0, 1.0])
+def test_double_well_gradient_matches_finite_differences(g):
+    w = _dw_small(g=g)
+    grad = G.global_gradient(w, w.u0)
+    h = 1e-4
+    fd = np.empty(w.Nt)
+    for j in range(w.Nt):
+        def J_at(s):
+            v = w.u0.copy()
+            v[j] += s
+            return G.objective(w, v)[0]
+        fd[j] = (8 * (J_at(h) - J_at(-h)) - (J_at(2 * h) - J_at(-2 * h))) / (12 * h)
+    assert np.linalg.norm(grad - fd) <= 1e-8 * np.linalg.norm(fd)
+
+
+def test_double_well_ism_iterates_do_not_depend_on_N():
+    w = _dw_small(Nt=24, N=1)
+    u1, J1, _, _ = G.ism_solve(w, w.u0, 3, 0.05)
+    for N in (3, 8):
+        uN, JN, _, _ = G.ism_solve(w.with_(N=N), w.u0, 3, 0.05)
+        assert np.max(np.abs(uN - u1)) < 1e-12 and np.max(np.abs(JN - J1)) < 1e-12
+
+
+def test_double_well_rho_increases_J():
+    """The step size of the double-well problem (rho = 0.05) increases J monotonically over 5
+    gradient iterations on a 128-point version of the benchmark set-up."""
+    w = W.gp_double_well(n=128, Nt=1000, N=8, steps=20000)
+    _, J = G.gradient_method(w, w.u0, 5, 0.05)
+    assert np.all(np.diff(J) > 0)

@@ -258,7 +258,8 @@ def config(name: str, *, N: Optional[int] = None, Nt: Optional[int] = None, iter
 @dataclass
 class GPWorkload:
     """1D GP problem: i d/dt psi = (-1/2 d^2/dx^2 + V(x, u) + g |psi|^2) psi on a periodic grid,
-    V(x, u) = (x - u)^2 / 2, maximise J = Re<psi(T)|psi_f> with <a|b> = sum conj(a) b dx."""
+    V(x, u) = (x - u)^2 / 2 (harmonic) or the double well of separation dw (potential =
+    "double_well"), maximise J = Re<psi(T)|psi_f> with <a|b> = sum conj(a) b dx."""
 
     name: str
     n: int              # grid points
@@ -278,6 +279,8 @@ class GPWorkload:
     kind: str = "gp"
     objective: str = "overlap"
     alpha: Optional[np.ndarray] = None
+    potential: str = "harmonic"   # "harmonic": (x - u)^2/2; "double_well": the split trap, separation dw
+    dw: float = 0.0
 
     @property
     def dx(self) -> float:
@@ -342,3 +345,46 @@ def gp_bec(n: int = 512, seed: int = 1002, *, T: float = 8.0, Nt: int = 10000, N
     L, x_min = 20.0, -10.0
     psi_i, psi_f = states if states is not None else gp_stationary_states(n, L, x_min, g, steps=steps)
     return GPWorkload(name=name, n=n, L=L, x_min=x_min, g=g, psi_i=psi_i, psi_f=psi_f, T=T, Nt=Nt, N=N, u0=u0)
+
+
+def double_well_values(x: np.ndarray, lam: float, dw: float) -> np.ndarray:
+    """The double-well potential on a grid at control lam (model set-up for the stationary states)."""
+    ax = np.abs(x)
+    return np.where(ax > lam * dw / 4.0, 0.5 * (ax - lam * dw / 2.0) ** 2, 0.5 * ((lam * dw) ** 2 / 8.0 - x ** 2))
+
+
+def gp_ground_state(n: int, L: float, x_min: float, g: float, V: np.ndarray, *, dt: float = 1e-3,
+                    steps: int = 40000) -> np.ndarray:
+    """Ground state of -1/2 d^2 + V + g|psi|^2 on the periodic grid by imaginary-time split steps with
+    renormalisation, started from a Gaussian.  Model set-up only."""
+    x = x_min + np.arange(n) * (L / n)
+    dx = L / n
+    kk = 2.0 * np.pi * np.fft.fftfreq(n, d=dx)
+    half = np.exp(-0.25 * dt * kk ** 2)
+    v = np.exp(-0.5 * x ** 2).astype(np.complex128)
+    v = v / np.sqrt(np.sum(np.abs(v) ** 2) * dx)
+    for _ in range(steps):
+        v = np.fft.ifft(half * np.fft.fft(v))
+        v = v * np.exp(-dt * (V + g * np.abs(v) ** 2))
+        v = np.fft.ifft(half * np.fft.fft(v))
+        v = v / np.sqrt(np.sum(np.abs(v) ** 2) * dx)
+    return v
+
+
+def gp_double_well(n: int = 512, seed: int = 1005, *, T: float = 8.0, Nt: int = 10000, N: int = 64,
+                   g: float = 1.0, dw: float = 4.0, u_amp: float = 0.05, steps: int = 20000,
+                   name: str = "gp512dw", states=None) -> GPWorkload:
+    """Condensate splitting in the double well of Sec. 4 on the grid of gp_bec: psi_i = ground state
+    of V(x, 0) (the harmonic trap), psi_f = ground state of V(x, 1) (two wells at +-dw/2), control
+    lambda(t), initial guess the ramp t/T plus U[-u_amp, u_amp] (the only random draw)."""
+    rng = np.random.default_rng(seed)
+    tm = (np.arange(Nt) + 0.5) * (T / Nt)
+    u0 = tm / T + rng.uniform(-u_amp, u_amp, size=Nt)
+    L, x_min = 20.0, -10.0
+    if states is None:
+        x = x_min + np.arange(n) * (L / n)
+        states = (gp_ground_state(n, L, x_min, g, double_well_values(x, 0.0, dw), steps=steps),
+                  gp_ground_state(n, L, x_min, g, double_well_values(x, 1.0, dw), steps=steps))
+    psi_i, psi_f = states
+    return GPWorkload(name=name, n=n, L=L, x_min=x_min, g=g, psi_i=psi_i, psi_f=psi_f, T=T, Nt=Nt, N=N, u0=u0,
+                      potential="double_well", dw=dw)
