@@ -38,12 +38,14 @@ UNIT = "ISM iterations/s"
 DESCR = {"rotor41": "rigid rotor j<=40, maximise <cos theta>(T)",
          "spin16": "4 spins all-to-all ZZ, X control, |0000> -> |1111>",
          "ising1024": "10-spin open Ising chain, X control, |0^10> -> |1^10>",
-         "gp512": "1D Gross-Pitaevskii condensate, 512-point grid, trap centre control, ground -> odd state"}
-SAMPLE_DIV = {"rotor41": 8, "spin16": 1, "ising1024": 64, "gp512": 8}
+         "gp512": "1D Gross-Pitaevskii condensate, 512-point grid, trap centre control, ground -> odd state",
+         "gp512dw": "1D Gross-Pitaevskii condensate, 512-point grid, double-well splitting control, "
+                    "harmonic ground state -> split-trap ground state"}
+SAMPLE_DIV = {"rotor41": 8, "spin16": 1, "ising1024": 64, "gp512": 8, "gp512dw": 8}
 # independent solves per launch: multiples of the 152 SMs (16 problems per SM for the lane-group
 # sweeps, one CTA per SM and direction for ising1024, two 304-CTA waves for the grid model)
-BATCH_DEFAULT = {"rotor41": 2432, "spin16": 2432, "ising1024": 76, "gp512": 304}
-SOLVE_ITERS = {"rotor41": 50, "spin16": 20, "ising1024": 20, "gp512": 20}   # oracle sample = Nt/div steps, N/div sub-intervals
+BATCH_DEFAULT = {"rotor41": 2432, "spin16": 2432, "ising1024": 76, "gp512": 304, "gp512dw": 304}
+SOLVE_ITERS = {"rotor41": 50, "spin16": 20, "ising1024": 20, "gp512": 20, "gp512dw": 20}   # oracle sample = Nt/div steps, N/div sub-intervals
 FP32_LANES_PER_SM = 128
 SMS = 152
 SM_MAX_MHZ = 2070.0
@@ -201,6 +203,10 @@ def load_workload(cfg: str, N=None, Nt=None):
         w = W.gp_bec(Nt=Nt or 10000, N=N or 64, states=_GP_STATES.get("gp512"))
         _GP_STATES["gp512"] = (w.psi_i, w.psi_f)
         return w
+    if cfg == "gp512dw":
+        w = W.gp_double_well(Nt=Nt or 10000, N=N or 64, states=_GP_STATES.get("gp512dw"))
+        _GP_STATES["gp512dw"] = (w.psi_i, w.psi_f)
+        return w.with_(rho=0.05)
     return W.config(cfg, N=N, Nt=Nt)
 
 
@@ -218,7 +224,7 @@ def oracle_sample(cfg: str, N_full: int):
     Nt_s = max(1, full.Nt // div)
     N_s = max(1, full.N // div)
     w = load_workload(cfg, N=N_s, Nt=Nt_s)
-    O = gp_oracle if cfg == "gp512" else ism_oracle
+    O = gp_oracle if cfg.startswith("gp512") else ism_oracle
     t0 = time.perf_counter()
     O.ism_iteration(w, w.u0, w.rho, w.local_iters)
     dt = time.perf_counter() - t0

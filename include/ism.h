@@ -71,7 +71,11 @@ typedef enum {
      psi(t_n) on the forward trajectory, targets chi(t_n) on the adjoint trajectory (the discrete
      adjoint of the full problem), J_n = Re<psi_n(t_{n+1})|chi(t_{n+1})>, ascent u += rho grad/tau.
      phi arrays of the entry points hold both sets: [batch][2][N+1][2d] = psi(t_n), then chi(t_n). */
-  ISM_H_GRID_GP = 3
+  ISM_H_GRID_GP = 3,
+  /* The same condensate in the double well of Sec. 4, control lambda = u, separation D > 0:
+     V(x, u) = (|x| - u D/2)^2/2 for |x| > u D/4, ((u D)^2/8 - x^2)/2 otherwise (V(x, 0) = x^2/2).
+     H0 = {L, x_min, g, D}; everything else as ISM_H_GRID_GP.                                       */
+  ISM_H_GRID_GP_DOUBLE_WELL = 4
 } ism_hkind;
 
 typedef enum {

@@ -16,7 +16,7 @@ LIB_PATH = os.path.join(os.path.dirname(os.path.abspath(__file__)), "libism.so")
 
 ISM_OK, ISM_EINVAL, ISM_ENOMEM, ISM_ECUDA, ISM_ENONFINITE, ISM_ETIMEOUT, ISM_EUNSUPPORTED = range(7)
 ISM_FP64, ISM_MIXED = 0, 1
-ISM_H_DENSE, ISM_H_BITFLIP, ISM_H_TRIDIAG, ISM_H_GRID_GP = 0, 1, 2, 3
+ISM_H_DENSE, ISM_H_BITFLIP, ISM_H_TRIDIAG, ISM_H_GRID_GP, ISM_H_GRID_GP_DOUBLE_WELL = 0, 1, 2, 3, 4
 ISM_OBJ_OVERLAP, ISM_OBJ_OBSERVABLE = 0, 1
 ISM_SCHEME_CHEBYSHEV, ISM_SCHEME_CRANK_NICOLSON = 0, 1
 _SCHEME = {"chebyshev": ISM_SCHEME_CHEBYSHEV, "crank_nicolson": ISM_SCHEME_CRANK_NICOLSON}
@@ -201,13 +201,15 @@ def subinterval_grad_noalloc(w, precision: str, phi, u, grad, Jn=None, *, batch:
 def problem_and_options(w, *, precision=None, batch=1, local_iters=None, rho=None, kind=None, cheb_tol=0.0,
                         subproblem_form=0, step1=0, max_spin_iters=0, scheme="chebyshev"):
     """(ism_problem, ism_options, arrays to keep alive) for a workload object.  scheme: "chebyshev"
-    (exact step) or "crank_nicolson" (the Sec. 3 step; tridiagonal kind, FP64)."""
+    (exact step) or "crank_nicolson" (the Sec. 3 step; FP64, d <= 64, not the grid kinds)."""
     kind = kind or w.kind
     gp = kind == "gp"
     d = int(w.n) if gp else int(w.d)
     prec = precision or w.precision
-    if gp:   # grid kind: H0 = {L, x_min, g}
-        H0p, H1p = np.array([w.L, w.x_min, w.g], dtype=np.float64), None
+    dwell = gp and getattr(w, "potential", "harmonic") == "double_well"
+    if gp:   # grid kinds: H0 = {L, x_min, g} (harmonic trap) or {L, x_min, g, D} (double well)
+        H0p = np.array([w.L, w.x_min, w.g] + ([w.dw] if dwell else []), dtype=np.float64)
+        H1p = None
     else:
         H0p, H1p = pack_hamiltonian(kind, w.H0, w.H1)
     psi_i = _c128_interleaved(w.psi_i)
@@ -215,8 +217,8 @@ def problem_and_options(w, *, precision=None, batch=1, local_iters=None, rho=Non
     O = np.ascontiguousarray(w.O, dtype=np.float64) if w.objective == "observable" else None
     alpha = None if w.alpha is None else np.ascontiguousarray(w.alpha, dtype=np.float64)
     keep = [H0p, H1p, psi_i, psi_f, O, alpha]
-    prob = IsmProblem(d=d, kind=_KIND[kind], H0=_ptr(H0p), H1=_ptr(H1p), psi_i=_ptr(psi_i),
-                      objective=ISM_OBJ_OVERLAP if w.objective == "overlap" else ISM_OBJ_OBSERVABLE,
+    prob = IsmProblem(d=d, kind=ISM_H_GRID_GP_DOUBLE_WELL if dwell else _KIND[kind], H0=_ptr(H0p), H1=_ptr(H1p),
+                      psi_i=_ptr(psi_i), objective=ISM_OBJ_OVERLAP if w.objective == "overlap" else ISM_OBJ_OBSERVABLE,
                       psi_f=_ptr(psi_f), O=_ptr(O), T=float(w.T), Nt=int(w.Nt), N=int(w.N), alpha=_ptr(alpha),
                       batch=int(batch))
     opt = IsmOptions(precision=ISM_FP64 if prec == "fp64" else ISM_MIXED,

@@ -75,6 +75,8 @@ struct ism_plan_s {
   int scheme = ISM_SCHEME_CHEBYSHEV;
   bool gp = false;                       // grid (Gross-Pitaevskii) kind
   double gpL = 0, gpxmin = 0, gpg = 0;   // its grid length, origin and nonlinearity
+  int gppot = 0;                         // potential: 0 harmonic (x - u)^2/2, 1 double well
+  double gpdw = 0;                       // double-well separation D
   double c0 = 0, r0 = 0, h1n = 0;
   ism::KernelSet ks;
   int ldm = 0, dpad = 0;
@@ -274,14 +276,17 @@ int validate_problem(const ism_problem& p, int precision) {
   if (p.N < 1 || p.N > p.Nt) return fail(ISM_EINVAL, "need 1 <= N <= Nt");
   if (!(p.T > 0.0) || !std::isfinite(p.T)) return fail(ISM_EINVAL, "T must be finite and > 0");
   if (p.batch < 0) return fail(ISM_EINVAL, "batch must be >= 0");
-  if (p.kind < ISM_H_DENSE || p.kind > ISM_H_GRID_GP) return fail(ISM_EINVAL, "unknown Hamiltonian kind");
-  if (p.kind == ISM_H_GRID_GP) {
-    if (!p.H0 || !p.psi_i || !p.psi_f) return fail(ISM_EINVAL, "the grid kind needs H0 = {L, x_min, g}, psi_i and psi_f");
+  if (p.kind < ISM_H_DENSE || p.kind > ISM_H_GRID_GP_DOUBLE_WELL) return fail(ISM_EINVAL, "unknown Hamiltonian kind");
+  if (p.kind == ISM_H_GRID_GP || p.kind == ISM_H_GRID_GP_DOUBLE_WELL) {
+    const bool dw = p.kind == ISM_H_GRID_GP_DOUBLE_WELL;
+    if (!p.H0 || !p.psi_i || !p.psi_f)
+      return fail(ISM_EINVAL, "the grid kinds need H0 = {L, x_min, g} (+ D for the double well), psi_i and psi_f");
     if (p.objective != ISM_OBJ_OVERLAP) return fail(ISM_EINVAL, "the grid kind supports the overlap objective only");
     if (p.alpha) return fail(ISM_EINVAL, "the grid kind has no control penalty (alpha must be NULL)");
     if (precision != ISM_FP64 && precision != ISM_MIXED) return fail(ISM_EINVAL, "unknown precision");
     if (!gp_supported(d)) return fail(ISM_EUNSUPPORTED, "the grid kind supports d = 64 or 512 points");
-    if (!all_finite(p.H0, 3) || !(p.H0[0] > 0.0)) return fail(ISM_EINVAL, "grid parameters must be finite with L > 0");
+    if (!all_finite(p.H0, dw ? 4 : 3) || !(p.H0[0] > 0.0) || (dw && !(p.H0[3] > 0.0)))
+      return fail(ISM_EINVAL, "grid parameters must be finite with L > 0 (and D > 0)");
     if (!all_finite(p.psi_i, 2L * d) || !all_finite(p.psi_f, 2L * d)) return fail(ISM_ENONFINITE, "non-finite psi_i or psi_f");
     return ISM_OK;
   }
@@ -389,6 +394,7 @@ ism::GPParams gparams(ism_plan_s* P, double* u) {
   ism::GPParams g{};
   g.n = P->d; g.Nt = P->Nt; g.N = P->N; g.B = P->B;
   g.tau = P->tau; g.T = P->T; g.L = P->gpL; g.xmin = P->gpxmin; g.dx = P->gpL / P->d; g.g = P->gpg; g.rho = P->rho;
+  g.pot = P->gppot; g.dw = P->gpdw;
   g.jn = P->djn; g.u = u; g.psi_i = P->dpsi_i; g.psi_f = P->dpsi_f; g.traj = P->dtraj;
   g.psin = P->dpsin; g.chin = P->dchin; g.grad = P->dgrad; g.Jn = P->dJn; g.err = P->derr;
   g.J = P->dJ; g.F = P->dF; g.Jhist = nullptr; g.hist_stride = 0; g.hist_k = 0;
@@ -511,7 +517,7 @@ int plan_build(const ism_problem* prob, const ism_options* opt, void* cuda_strea
   if (opt->scheme != ISM_SCHEME_CHEBYSHEV && opt->scheme != ISM_SCHEME_CRANK_NICOLSON)
     return fail(ISM_EINVAL, "scheme must be ISM_SCHEME_CHEBYSHEV or ISM_SCHEME_CRANK_NICOLSON");
   if (opt->scheme == ISM_SCHEME_CRANK_NICOLSON &&
-      (p.kind == ISM_H_GRID_GP || p.d > 64 || opt->precision != ISM_FP64))
+      (p.kind == ISM_H_GRID_GP || p.kind == ISM_H_GRID_GP_DOUBLE_WELL || p.d > 64 || opt->precision != ISM_FP64))
     return fail(ISM_EUNSUPPORTED, "the Crank-Nicolson scheme is built in FP64 for the tridiagonal, dense and bit-flip kinds "
                                   "with d <= 64");
 
@@ -529,11 +535,13 @@ int plan_build(const ism_problem* prob, const ism_options* opt, void* cuda_strea
   P->st = reinterpret_cast<cudaStream_t>(cuda_stream);
   cudaGetDevice(&P->dev);
 
-  if (p.kind == ISM_H_GRID_GP) {
+  if (p.kind == ISM_H_GRID_GP || p.kind == ISM_H_GRID_GP_DOUBLE_WELL) {
     P->gp = true;
     P->gpL = p.H0[0];
     P->gpxmin = p.H0[1];
     P->gpg = p.H0[2];
+    P->gppot = p.kind == ISM_H_GRID_GP_DOUBLE_WELL ? 1 : 0;
+    P->gpdw = P->gppot ? p.H0[3] : 0.0;
     P->r2 = P->prec == ISM_FP64 ? sizeof(double2) : sizeof(float2);
     std::vector<int> jn(P->N + 1);
     for (int n = 0; n <= P->N; ++n) jn[n] = (int)(((long long)n * P->Nt) / P->N);

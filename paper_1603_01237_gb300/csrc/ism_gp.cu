@@ -1,7 +1,9 @@
 // ism_gp.cu -- the Gross-Pitaevskii (condensate) variant of the ISM hot path (Sec. 4, condensates).
 //
 // Model: i d/dt psi = (-1/2 d^2/dx^2 + V(x, u) + g |psi|^2) psi on a periodic grid of n points,
-// V = (x - u)^2 / 2, J = Re<psi(T)|psi_f>, <a|b> = sum conj(a) b dx.  Time step (Strang, Eq. (OS)):
+// V = (x - u)^2 / 2 (harmonic trap, control-shifted centre) or the double well of Sec. 4 (control
+// lambda = u, separation D: V = (|x| - u D/2)^2/2 for |x| > u D/4, ((u D)^2/8 - x^2)/2 otherwise),
+// J = Re<psi(T)|psi_f>, <a|b> = sum conj(a) b dx.  Time step (Strang, Eq. (OS)):
 // psi_{j+1} = K exp(-i tau theta_j) K psi_j with K = F^-1 diag(exp(-i tau k^2/4)) F and
 // theta_j = V(x, u_j) + g |K psi_j|^2.
 //
@@ -165,6 +167,8 @@ struct GP {
   R *X, *Xl;                      // grid points x_m as hi + lo
   int n;
   double dx, tau, g, xmin;
+  int pot;            // 0 harmonic, 1 double well
+  R dh, dq, d28;      // D/2, D/4, D^2/8 (double well)
   double* red;
 
   __device__ void setup(const GPParams& p, unsigned char* smem, double* red_) {
@@ -185,6 +189,10 @@ struct GP {
     tau = p.tau;
     g = p.g;
     xmin = p.xmin;
+    pot = p.pot;
+    dh = (R)(0.5 * p.dw);
+    dq = (R)(0.25 * p.dw);
+    d28 = (R)(0.125 * p.dw * p.dw);
     red = red_;
     for (int m = threadIdx.x; m < n; m += blockDim.x) {
       double s, co;
@@ -248,10 +256,28 @@ struct GP {
     fft8<R, true>(X, other, W, Wl, n, Ident(), scale);
   }
 
-  __device__ R theta(int m, R u, T a) const {
-    const R xm = (X[m] - u) + Xl[m];
-    return R(0.5) * xm * xm + (R)g * (a.x * a.x + a.y * a.y);
+  // V(x_m, u) and dV/du(x_m, u); x_m = X + Xl (hi + lo)
+  __device__ __forceinline__ R pot_v(int m, R u) const {
+    if (!pot) {
+      const R xm = (X[m] - u) + Xl[m];
+      return R(0.5) * xm * xm;
+    }
+    const R xh = X[m], xl = Xl[m];
+    const R axh = fabs(xh), axl = xh < R(0) ? -xl : xl;
+    if (axh + axl > u * dq) {
+      const R t = (axh - u * dh) + axl;
+      return R(0.5) * t * t;
+    }
+    return R(0.5) * (u * u * d28 - fma(xh, xh, R(2) * xh * xl));
   }
+  __device__ __forceinline__ R pot_du(int m, R u) const {
+    if (!pot) return (u - X[m]) - Xl[m];
+    const R xh = X[m], xl = Xl[m];
+    const R axh = fabs(xh), axl = xh < R(0) ? -xl : xl;
+    if (axh + axl > u * dq) return -dh * ((axh - u * dh) + axl);
+    return u * d28;
+  }
+  __device__ R theta(int m, R u, T a) const { return pot_v(m, u) + (R)g * (a.x * a.x + a.y * a.y); }
 
   // One forward Strang step on a = A (a_{j+1} = F^-1 e^{-i tau k^2/2} F e^{-i tau theta} a_j), with
   // the potential factor applied as the first FFT pass loads each element; `keep`, if not null,
@@ -292,7 +318,7 @@ struct GP {
       const T e = expm1i<T, R>(tr * self->theta(m, ur, a));
       const T mu = cadd(nu, cmul(e, nu));
       const R im = mu.x * a.y - mu.y * a.x;   // Im(conj(mu) a)
-      if (GRAD) part = fma((ur - self->X[m]) - self->Xl[m], im, part);   // dV/du = -(x - u)
+      if (GRAD) part = fma(self->pot_du(m, ur), im, part);
       T w;
       const R f = f2 * im;
       w.x = mu.x + f * a.x;

@@ -7,6 +7,8 @@ namespace ism {
 struct GPParams {
   int n, Nt, N, B;
   double tau, T, L, xmin, dx, g, rho;
+  int pot;                // 0: V = (x - u)^2/2; 1: the double well of separation dw
+  double dw;
   const int* jn;          // [N+1]
   double* u;              // [B][Nt]
   const double2* psi_i;   // [n]

@@ -129,10 +129,10 @@ int ism_server_submit(ism_server_t S, const ism_problem* prob, const ism_options
   auto r = std::make_unique<Request>();
   const ism_problem& p = *prob;
   const int d = p.d;
-  const bool gp = p.kind == ISM_H_GRID_GP;
+  const bool gp = p.kind == ISM_H_GRID_GP || p.kind == ISM_H_GRID_GP_DOUBLE_WELL;
   int q = 0;
   while ((1 << q) < d) ++q;
-  const size_t nH0 = gp ? 3 : p.kind == ISM_H_DENSE ? (size_t)d * d : p.kind == ISM_H_TRIDIAG ? 2 * (size_t)d - 1 : (size_t)d;
+  const size_t nH0 = gp ? (p.kind == ISM_H_GRID_GP_DOUBLE_WELL ? 4 : 3) : p.kind == ISM_H_DENSE ? (size_t)d * d : p.kind == ISM_H_TRIDIAG ? 2 * (size_t)d - 1 : (size_t)d;
   const size_t nH1 = gp ? 0 : p.kind == ISM_H_DENSE ? (size_t)d * d : p.kind == ISM_H_TRIDIAG ? 2 * (size_t)d - 1 : (size_t)q;
   r->H0 = copy_of(p.H0, nH0);
   r->H1 = copy_of(p.H1, nH1);

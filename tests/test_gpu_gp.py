@@ -1,5 +1,6 @@
-"""Gross-Pitaevskii variant (Sec. 4, condensates) through the C ABI vs the FP64 oracle: forward and
-adjoint sweeps (psi(t_n), chi(t_n)), sub-problem gradients, ISM iterations."""
+"""Gross-Pitaevskii variant (Sec. 4, condensates; harmonic trap with shifted centre and the double well)
+through the C ABI vs the FP64 oracle: forward and adjoint sweeps (psi(t_n), chi(t_n)), sub-problem
+gradients, ISM iterations."""
 import numpy as np
 import pytest
 
@@ -30,7 +31,13 @@ def rel(a, b):
     return float(np.linalg.norm(np.ravel(a - b)) / np.linalg.norm(np.ravel(b)))
 
 
-CASES = [("gp64", _gp(64, 150, 6, 1.5)), ("gp512", _gp(512, 240, 8, 2.0)), ("gp512-ragged", _gp(512, 157, 5, 1.0))]
+def _dw(n, Nt, N, T, seed=6, steps=4000):
+    """Double well (Sec. 4): harmonic ground state -> ground state of the split trap, ramp + noise."""
+    return W.gp_double_well(n=n, seed=seed, T=T, Nt=Nt, N=N, steps=steps, u_amp=0.3)
+
+
+CASES = [("gp64", _gp(64, 150, 6, 1.5)), ("gp512", _gp(512, 240, 8, 2.0)), ("gp512-ragged", _gp(512, 157, 5, 1.0)),
+         ("dw64", _dw(64, 150, 6, 1.5)), ("dw512", _dw(512, 240, 8, 2.0)), ("dw512-ragged", _dw(512, 157, 5, 1.0))]
 
 
 @pytest.mark.parametrize("name,w", CASES, ids=[c[0] for c in CASES])
@@ -74,3 +81,29 @@ def test_gp_n_independence(P):
             res.append(pl.iterate(w.u0, 2)[0][0])
     for u in res[1:]:
         assert np.max(np.abs(u - res[0])) <= 1e-11
+
+
+@pytest.mark.parametrize("prec,tol", [("fp64", 1e-10), ("mixed", 1e-5)])
+def test_double_well_iterate(P, prec, tol):
+    w = _dw(512, 200, 8, 2.0)
+    u_o, J_o, F_o, E_o = G.ism_solve(w, w.u0, 3, 0.05)
+    with P.Plan(w, precision=prec, rho=0.05) as pl:
+        u, J, E = pl.iterate(w.u0, 3)
+        _, F = pl.evaluate(u[0])
+    assert np.max(np.abs(J[0] - J_o)) <= tol, np.max(np.abs(J[0] - J_o))
+    assert abs(F[0] - F_o[-1]) <= tol
+    assert rel(E[0], E_o) <= 1e-3 if prec == "mixed" else rel(E[0], E_o) <= 1e-9
+
+
+def test_double_well_full_size_mixed(P):
+    """The double-well problem at the condensate benchmark's size (512 points, Nt = 10000, N = 64),
+    mixed precision, two ISM iterations and the global gradient against the FP64 oracle."""
+    w = W.gp_double_well(n=512, Nt=10000, N=64, steps=20000)
+    u_o, J_o, F_o, _ = G.ism_solve(w, w.u0, 2, 0.05)
+    g_o = G.global_gradient(w, w.u0)
+    with P.Plan(w, precision="mixed", rho=0.05) as pl:
+        u, J, _ = pl.iterate(w.u0, 2)
+        g, Jg = pl.gradient(w.u0)
+    assert np.max(np.abs(J[0] - J_o)) <= 1e-5, np.max(np.abs(J[0] - J_o))
+    assert rel(g[0], g_o) <= 1e-4, rel(g[0], g_o)
+    assert np.max(np.abs(u[0] - u_o)) <= 1e-4 * np.max(np.abs(u_o))
