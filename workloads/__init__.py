@@ -39,6 +39,11 @@ __all__ = [
     "GPWorkload",
     "gp_bec",
     "gp_stationary_states",
+    "gp_double_well",
+    "gp_ground_state",
+    "MCWorkload",
+    "random_pauli",
+    "spin5_liouville",
 ]
 
 
@@ -388,3 +393,110 @@ def gp_double_well(n: int = 512, seed: int = 1005, *, T: float = 8.0, Nt: int = 
     psi_i, psi_f = states
     return GPWorkload(name=name, n=n, L=L, x_min=x_min, g=g, psi_i=psi_i, psi_f=psi_f, T=T, Nt=Nt, N=N, u0=u0,
                       potential="double_well", dw=dw)
+
+
+# ----------------------------------------------------------------------------------------------
+# Several controls on a Pauli structure (the five-spin example of Sec. 4)
+# ----------------------------------------------------------------------------------------------
+@dataclass
+class MCWorkload:
+    """A control problem with m controls: H(t) = diag(H0d) + sum_c u_c(t) H_c, H_c = sum_b
+    (ax[c, b] X_b + ay[c, b] Y_b) on d = 2^q basis states (bit b of the index <-> X_b, Y_b; Pauli
+    Y = [[0, -i], [i, 0]]), maximise J = Re<psi(T)|psi_f>.  u0 is (Nt, m)."""
+
+    name: str
+    q: int
+    H0d: np.ndarray      # (d,) float64
+    ax: np.ndarray       # (m, q) float64
+    ay: np.ndarray       # (m, q) float64
+    psi_i: np.ndarray    # (d,) complex128
+    psi_f: np.ndarray    # (d,) complex128
+    T: float
+    Nt: int
+    N: int
+    u0: np.ndarray       # (Nt, m) float64
+    iters: int = 20
+    rho: float = 0.1
+    local_iters: int = 1
+    precision: str = "mixed"
+    kind: str = "pauli"
+    objective: str = "overlap"
+    alpha: Optional[np.ndarray] = None
+    meta: dict = field(default_factory=dict)
+
+    @property
+    def d(self) -> int:
+        return 1 << self.q
+
+    @property
+    def m(self) -> int:
+        return int(self.ax.shape[0])
+
+    @property
+    def tau(self) -> float:
+        return self.T / self.Nt
+
+    def with_(self, **kw) -> "MCWorkload":
+        import dataclasses
+
+        return dataclasses.replace(self, **kw)
+
+
+def random_pauli(q: int, m: int, seed: int, *, T: float, Nt: int, N: int, u_amp: float = 1.0,
+                 h0_scale: float = 2.0, name: str = "pauli") -> MCWorkload:
+    """Random multi-control problem for parity tests.  Draws, in order: H0d ~ U[-h0_scale, h0_scale]
+    (d), ax ~ U[-1, 1] (m x q), ay ~ U[-1, 1] (m x q), psi_i and psi_f (complex Gaussian, normalised),
+    u0 ~ U[-u_amp, u_amp] (Nt x m)."""
+    rng = np.random.default_rng(seed)
+    d = 1 << q
+    H0d = rng.uniform(-h0_scale, h0_scale, d)
+    ax = rng.uniform(-1.0, 1.0, (m, q))
+    ay = rng.uniform(-1.0, 1.0, (m, q))
+    v = rng.standard_normal(d) + 1j * rng.standard_normal(d)
+    f = rng.standard_normal(d) + 1j * rng.standard_normal(d)
+    u0 = rng.uniform(-u_amp, u_amp, (Nt, m))
+    return MCWorkload(name=name, q=q, H0d=H0d, ax=ax, ay=ay, psi_i=v / np.linalg.norm(v), psi_f=f / np.linalg.norm(f),
+                      T=T, Nt=Nt, N=N, u0=u0)
+
+
+SPIN5_COUPLINGS = ((1, 2), (1, 3), (2, 3), (2, 5), (3, 4))
+
+
+def spin5_liouville(seed: int = 1006, *, Nt: int = 32768, N: int = 128, Jp: float = 140.0,
+                    T: Optional[float] = None, u_amp: Optional[float] = None, name: str = "spin5") -> MCWorkload:
+    """The five-spin example of Sec. 4 in the density-matrix formalism, written as a state of the
+    Liouville space: rho (32 x 32) <-> v[s + 32 s'] = rho[s, s'] (row index s on bits 0-4, column
+    index s' on bits 5-9), i d rho/dt = [H, rho] <-> i dv/dt = (I (x) H - H^T (x) I) v.
+
+    H = H0 + sum_k (u_x^k I_x^(k) + u_y^k I_y^(k)), I_a = sigma_a / 2 on spin k (spin k <-> bit k-1),
+    H0 = 2 pi Jp sum_{(k,l)} I_z^(k) I_z^(l) over SPIN5_COUPLINGS (diagonal), so in Liouville space
+    H0 -> E(s) - E(s') and the controls c = 0..4 (u_x^k) and 5..9 (u_y^k) act as
+    u_x^k: (X on bit k-1 - X on bit k+4)/2,  u_y^k: (Y on bit k-1 + Y on bit k+4)/2
+    (-H^T acts on the column index; X^T = X, Y^T = -Y).  rho(0) = I_x^(1), target I_x^(5), both
+    normalised in the Frobenius norm, J = Re Tr(rho_f rho(T)).  T = 10/Jp (the paper prints "Jp/10";
+    read as ten coupling periods), steps T/2^15; u0 ~ U[-u_amp, u_amp], u_amp = 2 pi Jp by default
+    (the only random draw).  meta holds the Hilbert-space description for the density-matrix oracle."""
+    rng = np.random.default_rng(seed)
+    T = 10.0 / Jp if T is None else T
+    u_amp = 2.0 * np.pi * Jp if u_amp is None else u_amp
+    ns, q, m = 5, 10, 10
+    s = np.arange(32)
+    z = 1.0 - 2.0 * ((s[:, None] >> np.arange(ns)[None, :]) & 1)   # (32, 5): eigenvalues of sigma_z
+    E = 2.0 * np.pi * Jp * sum(0.25 * z[:, k - 1] * z[:, l - 1] for k, l in SPIN5_COUPLINGS)
+    e = np.arange(1024)
+    row, col = e & 31, e >> 5
+    H0d = E[row] - E[col]
+    ax = np.zeros((m, q))
+    ay = np.zeros((m, q))
+    for k in range(1, ns + 1):
+        ax[k - 1, k - 1], ax[k - 1, k + 4] = 0.5, -0.5
+        ay[5 + k - 1, k - 1], ay[5 + k - 1, k + 4] = 0.5, 0.5
+    rho0 = np.zeros(1024, dtype=np.complex128)
+    rhof = np.zeros(1024, dtype=np.complex128)
+    rho0[(row ^ 1) == col] = 0.5          # I_x^(1)[s, s'] = 1/2 for s' = s ^ bit 0
+    rhof[(row ^ 16) == col] = 0.5         # I_x^(5): bit 4
+    rho0 /= np.linalg.norm(rho0)
+    rhof /= np.linalg.norm(rhof)
+    u0 = rng.uniform(-u_amp, u_amp, (Nt, m))
+    return MCWorkload(name=name, q=q, H0d=H0d, ax=ax, ay=ay, psi_i=rho0, psi_f=rhof, T=T, Nt=Nt, N=N, u0=u0,
+                      meta={"spins": ns, "couplings": SPIN5_COUPLINGS, "Jp": Jp, "initial": ("x", 1), "target": ("x", 5)})
