@@ -75,7 +75,14 @@ typedef enum {
   /* The same condensate in the double well of Sec. 4, control lambda = u, separation D > 0:
      V(x, u) = (|x| - u D/2)^2/2 for |x| > u D/4, ((u D)^2/8 - x^2)/2 otherwise (V(x, 0) = x^2/2).
      H0 = {L, x_min, g, D}; everything else as ISM_H_GRID_GP.                                       */
-  ISM_H_GRID_GP_DOUBLE_WELL = 4
+  ISM_H_GRID_GP_DOUBLE_WELL = 4,
+  /* Several controls (the five-spin example of Sec. 4, in Liouville space): d = 2^q = 128 .. 1024,
+     H(t) = diag(H0) + sum_{c < m} u_c(t) H_c, H_c = sum_b (ax[c][b] X_b + ay[c][b] Y_b) (bit b of the
+     basis index; Pauli Y = [[0, -i], [i, 0]]).  H0[0..d-1] = diagonal; H1[(c q + b) 2 + {0, 1}] =
+     ax[c][b], ay[c][b] (m = ism_problem.controls, 1..32).  Controls, gradients and the ascent are
+     per step and control: every u or grad array of the entry points is [batch][Nt][m].  Overlap
+     objective only; alpha must be NULL.                                                           */
+  ISM_H_PAULI = 5
 } ism_hkind;
 
 typedef enum {
@@ -112,6 +119,7 @@ typedef struct {
   int N;                   /* number of sub-intervals, 1 <= N <= Nt                               */
   const double* alpha;     /* Nt penalty weights alpha_j = alpha(t at step midpoint), or NULL (0)  */
   int batch;               /* independent control problems in the plan, >= 1 (0 is read as 1)    */
+  int controls;            /* number of controls m (ISM_H_PAULI; 0 is read as 1, others must be 1) */
 } ism_problem;
 
 typedef struct {

@@ -224,10 +224,22 @@ def dm_operators(meta):
     return H0, Hc, r0 / np.linalg.norm(r0), rf / np.linalg.norm(rf)
 
 
-def _dm_unitary(H0, Hc, tau, u_j):
-    H = H0 + sum(float(u_j[c]) * Hc[c] for c in range(len(Hc)))
-    lam, V = np.linalg.eigh(H)
-    return (V * np.exp(-1j * tau * lam)[None, :]) @ V.conj().T
+def _dm_unitaries(H0, Hc, tau, u, j0, j1):
+    """U_j = exp(-i tau H_j), H_j = H0 + sum_c u_{j,c} H_c, for j in [j0, j1): numpy.linalg.eigh of
+    each Hermitian H_j, U_j = V_j diag(exp(-i tau lambda_j)) V_j^H."""
+    uu = np.asarray(u[j0:j1], dtype=np.float64)
+    Hs = np.asarray(Hc)
+    d = H0.shape[0]
+    H = H0[None] + (uu.astype(np.complex128) @ Hs.reshape(len(Hs), -1)).reshape(-1, d, d)
+    out = []
+    for k in range(j1 - j0):
+        lam, V = np.linalg.eigh(H[k])
+        out.append((V * np.exp(-1j * tau * lam)[None, :]) @ V.conj().T)
+    return out
+
+
+def _dm_chunks(Nt, size=2048):
+    return [(a, min(Nt, a + size)) for a in range(0, Nt, size)]
 
 
 def dm_forward(w, u):
@@ -235,9 +247,10 @@ def dm_forward(w, u):
     H0, Hc, r0, _ = dm_operators(w.meta)
     out = np.empty((w.Nt + 1,) + r0.shape, dtype=np.complex128)
     out[0] = r0
-    for j in range(w.Nt):
-        U = _dm_unitary(H0, Hc, w.tau, u[j])
-        out[j + 1] = U @ out[j] @ U.conj().T
+    for a, b in _dm_chunks(w.Nt):
+        U = _dm_unitaries(H0, Hc, w.tau, u, a, b)
+        for k in range(b - a):
+            out[a + k + 1] = U[k] @ out[a + k] @ U[k].conj().T
     return out
 
 
@@ -246,9 +259,10 @@ def dm_backward(w, u):
     H0, Hc, _, rf = dm_operators(w.meta)
     out = np.empty((w.Nt + 1,) + rf.shape, dtype=np.complex128)
     out[-1] = rf
-    for j in reversed(range(w.Nt)):
-        U = _dm_unitary(H0, Hc, w.tau, u[j])
-        out[j] = U.conj().T @ out[j + 1] @ U
+    for a, b in reversed(_dm_chunks(w.Nt)):
+        U = _dm_unitaries(H0, Hc, w.tau, u, a, b)
+        for k in reversed(range(b - a)):
+            out[a + k] = U[k].conj().T @ out[a + k + 1] @ U[k]
     return out
 
 
@@ -258,12 +272,15 @@ def dm_objective(w, u) -> float:
 
 
 def dm_gradient(w, u) -> np.ndarray:
-    """(Nt, m) trapezoid gradient with Im Tr(chi^H [H_c, rho])."""
+    """(Nt, m) trapezoid gradient with Im Tr(chi^H [H_c, rho]) = Im Tr(H_c C), C = rho chi^H - chi^H rho
+    (cyclic trace): Tr(H_c C) = sum_ab H_c[a, b] C[b, a]."""
     _, Hc, _, _ = dm_operators(w.meta)
     rho = dm_forward(w, u)
     chi = dm_backward(w, u)
-    im = np.empty((w.Nt + 1, len(Hc)))
-    for c, H in enumerate(Hc):
-        comm = np.einsum("ab,jbc->jac", H, rho) - np.einsum("jab,bc->jac", rho, H)
-        im[:, c] = np.imag(np.einsum("jab,jab->j", chi.conj(), comm))
+    d = rho.shape[1]
+    CT = np.empty((rho.shape[0], d * d), dtype=np.complex128)
+    for j in range(rho.shape[0]):
+        cH = chi[j].conj().T
+        CT[j] = (rho[j] @ cH - cH @ rho[j]).T.reshape(-1)
+    im = np.imag(CT @ np.asarray(Hc).reshape(len(Hc), -1).T)
     return 0.5 * w.tau * (im[1:] + im[:-1])

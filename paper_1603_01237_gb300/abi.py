@@ -16,7 +16,7 @@ LIB_PATH = os.path.join(os.path.dirname(os.path.abspath(__file__)), "libism.so")
 
 ISM_OK, ISM_EINVAL, ISM_ENOMEM, ISM_ECUDA, ISM_ENONFINITE, ISM_ETIMEOUT, ISM_EUNSUPPORTED = range(7)
 ISM_FP64, ISM_MIXED = 0, 1
-ISM_H_DENSE, ISM_H_BITFLIP, ISM_H_TRIDIAG, ISM_H_GRID_GP, ISM_H_GRID_GP_DOUBLE_WELL = 0, 1, 2, 3, 4
+ISM_H_DENSE, ISM_H_BITFLIP, ISM_H_TRIDIAG, ISM_H_GRID_GP, ISM_H_GRID_GP_DOUBLE_WELL, ISM_H_PAULI = 0, 1, 2, 3, 4, 5
 ISM_OBJ_OVERLAP, ISM_OBJ_OBSERVABLE = 0, 1
 ISM_SCHEME_CHEBYSHEV, ISM_SCHEME_CRANK_NICOLSON = 0, 1
 _SCHEME = {"chebyshev": ISM_SCHEME_CHEBYSHEV, "crank_nicolson": ISM_SCHEME_CRANK_NICOLSON}
@@ -34,7 +34,8 @@ EXPORTS = ("ism_plan", "ism_plan_destroy", "ism_intermediate_states", "ism_subin
 class IsmProblem(C.Structure):
     _fields_ = [("d", C.c_int), ("kind", C.c_int), ("H0", C.c_void_p), ("H1", C.c_void_p),
                 ("psi_i", C.c_void_p), ("objective", C.c_int), ("psi_f", C.c_void_p), ("O", C.c_void_p),
-                ("T", C.c_double), ("Nt", C.c_int), ("N", C.c_int), ("alpha", C.c_void_p), ("batch", C.c_int)]
+                ("T", C.c_double), ("Nt", C.c_int), ("N", C.c_int), ("alpha", C.c_void_p), ("batch", C.c_int),
+                ("controls", C.c_int)]
 
 
 class IsmOptions(C.Structure):
@@ -143,7 +144,8 @@ def _c128_interleaved(v) -> np.ndarray:
     return v.view(np.float64).copy()
 
 
-_KIND = {"dense": ISM_H_DENSE, "bitflip": ISM_H_BITFLIP, "tridiag": ISM_H_TRIDIAG, "gp": ISM_H_GRID_GP}
+_KIND = {"dense": ISM_H_DENSE, "bitflip": ISM_H_BITFLIP, "tridiag": ISM_H_TRIDIAG, "gp": ISM_H_GRID_GP,
+         "pauli": ISM_H_PAULI}
 
 
 def pack_hamiltonian(kind: str, H0: np.ndarray, H1: np.ndarray):
@@ -207,9 +209,14 @@ def problem_and_options(w, *, precision=None, batch=1, local_iters=None, rho=Non
     d = int(w.n) if gp else int(w.d)
     prec = precision or w.precision
     dwell = gp and getattr(w, "potential", "harmonic") == "double_well"
+    m = 1
     if gp:   # grid kinds: H0 = {L, x_min, g} (harmonic trap) or {L, x_min, g, D} (double well)
         H0p = np.array([w.L, w.x_min, w.g] + ([w.dw] if dwell else []), dtype=np.float64)
         H1p = None
+    elif kind == "pauli":   # diagonal H0; H1 = [m][q][2] weights (ax, ay)
+        m = int(w.m)
+        H0p = np.ascontiguousarray(w.H0d, dtype=np.float64)
+        H1p = np.ascontiguousarray(np.stack([w.ax, w.ay], axis=-1), dtype=np.float64).reshape(-1)
     else:
         H0p, H1p = pack_hamiltonian(kind, w.H0, w.H1)
     psi_i = _c128_interleaved(w.psi_i)
@@ -220,7 +227,7 @@ def problem_and_options(w, *, precision=None, batch=1, local_iters=None, rho=Non
     prob = IsmProblem(d=d, kind=ISM_H_GRID_GP_DOUBLE_WELL if dwell else _KIND[kind], H0=_ptr(H0p), H1=_ptr(H1p),
                       psi_i=_ptr(psi_i), objective=ISM_OBJ_OVERLAP if w.objective == "overlap" else ISM_OBJ_OBSERVABLE,
                       psi_f=_ptr(psi_f), O=_ptr(O), T=float(w.T), Nt=int(w.Nt), N=int(w.N), alpha=_ptr(alpha),
-                      batch=int(batch))
+                      batch=int(batch), controls=m)
     opt = IsmOptions(precision=ISM_FP64 if prec == "fp64" else ISM_MIXED,
                      local_iters=int(local_iters or w.local_iters), rho=float(w.rho if rho is None else rho),
                      cheb_tol=float(cheb_tol), max_spin_iters=int(max_spin_iters),
@@ -248,6 +255,7 @@ class Plan:
         self.kind = kind or w.kind
         self.batch = int(batch)
         self.gp = self.kind == "gp"
+        self.m = int(w.m) if self.kind == "pauli" else 1
         self.d = int(w.n) if self.gp else int(w.d)
         self.Nt, self.N = int(w.Nt), int(w.N)
         self.precision = precision or w.precision
@@ -298,7 +306,11 @@ class Plan:
     # ---------------------------------------------------------------- numpy conveniences
     def _u(self, u):
         u = np.ascontiguousarray(np.asarray(u, dtype=np.float64))
-        return np.ascontiguousarray(np.broadcast_to(u, (self.batch, self.Nt))).copy()
+        return np.ascontiguousarray(np.broadcast_to(u, self._ushape())).copy()
+
+    def _ushape(self):
+        """(batch, Nt), or (batch, Nt, m) for several controls."""
+        return (self.batch, self.Nt) if self.m == 1 else (self.batch, self.Nt, self.m)
 
     def _phi_shape(self):
         return (self.batch, 2, self.N + 1, self.d) if self.gp else (self.batch, self.N + 1, self.d)
@@ -311,7 +323,7 @@ class Plan:
 
     def subinterval_grad(self, phi, u):
         phi = np.ascontiguousarray(np.broadcast_to(np.asarray(phi, dtype=np.complex128), self._phi_shape()))
-        grad = np.empty((self.batch, self.Nt))
+        grad = np.empty(self._ushape())
         Jn = np.empty((self.batch, self.N))
         self.ism_subinterval_grad(phi.view(np.float64), self._u(u), grad, Jn)
         return grad, Jn
@@ -330,8 +342,8 @@ class Plan:
         return J, F
 
     def gradient(self, u):
-        """(dJ/du (batch, Nt), J (batch,)) at u."""
-        grad = np.empty((self.batch, self.Nt))
+        """(dJ/du (batch, Nt) or (batch, Nt, m), J (batch,)) at u."""
+        grad = np.empty(self._ushape())
         J = np.empty(self.batch)
         self.ism_gradient(self._u(u), grad, J)
         return grad, J
@@ -369,20 +381,21 @@ class Server:
     def submit(self, w, u0=None, iters=None, batch: int = 1, **plan_kw) -> int:
         prob, opt, keep = problem_and_options(w, batch=batch, **plan_kw)
         Nt = int(w.Nt)
+        ushape = (batch, Nt, int(w.m)) if getattr(w, "kind", "") == "pauli" else (batch, Nt)
         u = np.ascontiguousarray(np.broadcast_to(np.asarray(w.u0 if u0 is None else u0, dtype=np.float64),
-                                                 (batch, Nt))).copy()
+                                                 ushape)).copy()
         it = int(w.iters if iters is None else iters)
         rid = C.c_longlong()
         _check(load().ism_server_submit(self.handle, C.byref(prob), C.byref(opt), _ptr(u), it, C.byref(rid)))
-        self._shape[rid.value] = (batch, Nt, it)
+        self._shape[rid.value] = (ushape, it)
         return rid.value
 
     def poll(self, rid: int, wait: bool = False):
-        """(state, u (batch, Nt) or None, J_hist (batch, iters+1) or None, times_ms (3,))."""
-        B, Nt, it = self._shape[rid]
+        """(state, u (batch, Nt[, m]) or None, J_hist (batch, iters+1) or None, times_ms (3,))."""
+        ushape, it = self._shape[rid]
         st = C.c_int()
-        u = np.empty((B, Nt))
-        J = np.empty((B, it + 1))
+        u = np.empty(ushape)
+        J = np.empty((ushape[0], it + 1))
         t = np.empty(3)
         _check(load().ism_server_poll(self.handle, C.c_longlong(rid), int(bool(wait)), C.byref(st), _ptr(u), _ptr(J),
                                       _ptr(t)))

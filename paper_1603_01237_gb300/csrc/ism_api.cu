@@ -76,6 +76,10 @@ struct ism_plan_s {
   bool gp = false;                       // grid (Gross-Pitaevskii) kind
   double gpL = 0, gpxmin = 0, gpg = 0;   // its grid length, origin and nonlinearity
   int gppot = 0;                         // potential: 0 harmonic (x - u)^2/2, 1 double well
+  int m = 1, q = 0;                      // controls per step; bits of d (Pauli kind)
+  bool pauli = false;
+  double* dwts = nullptr;                // Pauli kind: [m][q][2] control weights
+  void* dcxy = nullptr;                  // Pauli kind: [B][Nt][2q] step coefficients (R)
   double gpdw = 0;                       // double-well separation D
   double c0 = 0, r0 = 0, h1n = 0;
   ism::KernelSet ks;
@@ -222,6 +226,9 @@ Bounds bounds_of(int kind, int d, const double* H0, const double* H1) {
     while ((1 << q) < d) ++q;
     for (int e = 0; e < d; ++e) { b.lo = std::fmin(b.lo, H0[e]); b.hi = std::fmax(b.hi, H0[e]); }
     for (int i = 0; i < q; ++i) b.h1 += std::fabs(H1[i]);
+  } else if (kind == ISM_H_PAULI) {   // the controls' bound is taken per sub-interval on the device
+    for (int e = 0; e < d; ++e) { b.lo = std::fmin(b.lo, H0[e]); b.hi = std::fmax(b.hi, H0[e]); }
+    b.h1 = 1.0;
   } else {
     for (int e = 0; e < d; ++e) {
       double r0 = 0.0, r1 = 0.0;
@@ -248,6 +255,9 @@ std::vector<R> pack_op(int kind, int d, const double* H0, const double* H1, int 
       out[2 * d + e] = (R)H1[e];
       if (e < d - 1) { out[d + e] = (R)H0[d + e]; out[3 * d + e] = (R)H1[d + e]; }
     }
+  } else if (kind == ISM_H_PAULI) {   // the kernels read the FP64 diagonal and the step coefficients
+    out.assign((size_t)d, R(0));
+    for (int e = 0; e < d; ++e) out[e] = (R)H0[e];
   } else if (kind == ISM_H_BITFLIP) {
     int q = 0;
     while ((1 << q) < d) ++q;
@@ -276,7 +286,24 @@ int validate_problem(const ism_problem& p, int precision) {
   if (p.N < 1 || p.N > p.Nt) return fail(ISM_EINVAL, "need 1 <= N <= Nt");
   if (!(p.T > 0.0) || !std::isfinite(p.T)) return fail(ISM_EINVAL, "T must be finite and > 0");
   if (p.batch < 0) return fail(ISM_EINVAL, "batch must be >= 0");
-  if (p.kind < ISM_H_DENSE || p.kind > ISM_H_GRID_GP_DOUBLE_WELL) return fail(ISM_EINVAL, "unknown Hamiltonian kind");
+  if (p.kind < ISM_H_DENSE || p.kind > ISM_H_PAULI) return fail(ISM_EINVAL, "unknown Hamiltonian kind");
+  if (p.controls < 0 || p.controls > 32 || (p.kind != ISM_H_PAULI && p.controls > 1))
+    return fail(ISM_EINVAL, "controls must be 1..32, and 1 unless the kind is ISM_H_PAULI");
+  if (p.kind == ISM_H_PAULI) {
+    const int m = p.controls < 1 ? 1 : p.controls;
+    int q = 0;
+    while ((1 << q) < d) ++q;
+    if ((1 << q) != d) return fail(ISM_EINVAL, "the Pauli kind needs d = 2^q");
+    if (d < 128 || d > 1024) return fail(ISM_EUNSUPPORTED, "this build supports the Pauli kind for d = 128 .. 1024");
+    if (!p.H0 || !p.H1 || !p.psi_i || !p.psi_f) return fail(ISM_EINVAL, "H0, H1, psi_i and psi_f are required");
+    if (p.objective != ISM_OBJ_OVERLAP) return fail(ISM_EINVAL, "the Pauli kind supports the overlap objective only");
+    if (p.alpha) return fail(ISM_EINVAL, "the Pauli kind has no control penalty (alpha must be NULL)");
+    if (precision != ISM_FP64 && precision != ISM_MIXED) return fail(ISM_EINVAL, "unknown precision");
+    if (!all_finite(p.H0, d) || !all_finite(p.H1, 2L * m * q) || !all_finite(p.psi_i, 2L * d) ||
+        !all_finite(p.psi_f, 2L * d))
+      return fail(ISM_ENONFINITE, "non-finite value in H0, H1, psi_i or psi_f");
+    return ISM_OK;
+  }
   if (p.kind == ISM_H_GRID_GP || p.kind == ISM_H_GRID_GP_DOUBLE_WELL) {
     const bool dw = p.kind == ISM_H_GRID_GP_DOUBLE_WELL;
     if (!p.H0 || !p.psi_i || !p.psi_f)
@@ -325,6 +352,7 @@ int validate_problem(const ism_problem& p, int precision) {
 }
 
 bool select_kernels(int prec, int kind, int d, KernelSet* ks, bool h1diag) {
+  if (kind == ISM_H_PAULI) return kernels_pauli(prec, d, ks);
   return kind == ISM_H_TRIDIAG   ? kernels_tridiag(prec, d, h1diag, ks)
          : kind == ISM_H_BITFLIP ? (d > 64 ? kernels_large_bitflip(prec, d, ks) : kernels_bitflip(prec, d, ks))
                                  : kernels_dense(prec, d, ks);
@@ -387,7 +415,13 @@ ism::KParams kparams(ism_plan_s* P, double* u) {
   k.psi_i = P->dpsi_i; k.psi_f = P->dpsi_f; k.O = P->dO; k.obj = P->obj; k.uf = P->duf;
   k.psin_w = P->dpsin; k.chin_w = P->dchin; k.zp = P->dzp;
   k.scheme = P->scheme == ISM_SCHEME_CRANK_NICOLSON ? 1 : 0;
+  k.m = P->m; k.q = P->q; k.wts = P->dwts; k.cxy = P->dcxy; k.zq = P->dzp;
   return k;
+}
+
+// The per-sub-interval parameters of the plan's kernels at the controls of k.
+cudaError_t prep_params(ism_plan_s* P, const ism::KParams& k) {
+  return P->ks.prep ? P->ks.prep(k, P->st) : ism::launch_cheb_prep(P->prec, k, P->st);
 }
 
 ism::GPParams gparams(ism_plan_s* P, double* u) {
@@ -416,12 +450,12 @@ int run_states(ism_plan_s* P, const double* u, double* Jhist, int hist_stride, i
   if (P->ks.large || P->direct) {   // direct sweeps: psi(t_n), chi(t_n) in FP64
     ism::LaunchFn sweep = P->ks.large ? P->ks.lsweep : P->ks.gsweep;
     ISM_CUDA_TRY(timed(P, 0, 2, [&] {
-      cudaError_t e = ism::launch_cheb_prep(P->prec, k, P->st);
+      cudaError_t e = prep_params(P, k);
       return e != cudaSuccess ? e : sweep(k, P->st);
     }));
   } else {
     ISM_CUDA_TRY(timed(P, 0, 2, [&] {
-      cudaError_t e = ism::launch_cheb_prep(P->prec, k, P->st);
+      cudaError_t e = prep_params(P, k);
       return e != cudaSuccess ? e : P->ks.assemble(k, P->st);
     }));
   }
@@ -586,6 +620,11 @@ int plan_build(const ism_problem* prob, const ism_options* opt, void* cuda_strea
     return ISM_OK;
   }
 
+  if (p.kind == ISM_H_PAULI) {
+    P->pauli = true;
+    P->m = p.controls < 1 ? 1 : p.controls;
+    while ((1 << P->q) < d) ++P->q;
+  }
   bool h1diag = true;
   if (p.kind == ISM_H_TRIDIAG) {
     h1diag = false;
@@ -690,14 +729,20 @@ int plan_build(const ism_problem* prob, const ism_options* opt, void* cuda_strea
     unsigned char* dT2 = nullptr;
     TRY_ALLOC(dT2, B * ((size_t)P->Nt + P->N) * GE * P->r2);
     P->dtraj2 = dT2;
-  } else if (P->ks.large) {
+  } else if (P->ks.large) {   // per-slot overlap partials: W warps, or the 2q bit overlaps (Pauli kind)
     unsigned char* dZ = nullptr;
-    TRY_ALLOC(dZ, B * ((size_t)P->Nt + P->N) * P->ks.W * P->r2);
+    TRY_ALLOC(dZ, B * ((size_t)P->Nt + P->N) * (P->pauli ? 2 * P->q : P->ks.W) * P->r2);
     P->dzp = dZ;
   }
-  TRY_ALLOC(P->du, B * P->Nt);
+  if (P->pauli) {
+    unsigned char* dC = nullptr;
+    TRY_ALLOC(dC, B * (size_t)P->Nt * 2 * P->q * (P->r2 / 2));
+    P->dcxy = dC;
+    TRY_ALLOC(P->dwts, (size_t)P->m * P->q * 2);
+  }
+  TRY_ALLOC(P->du, B * P->Nt * P->m);
   TRY_ALLOC(P->duf, B * P->Nt);
-  TRY_ALLOC(P->dgrad, B * P->Nt);
+  TRY_ALLOC(P->dgrad, B * P->Nt * P->m);
   TRY_ALLOC(P->dJn, B * P->N);
   TRY_ALLOC(P->derr, B * P->N);
   TRY_ALLOC(P->dJ, B);
@@ -743,6 +788,7 @@ int plan_build(const ism_problem* prob, const ism_options* opt, void* cuda_strea
     h2d(P->dab, ab.data(), ab.size() * sizeof(double2));
   }
   if (p.alpha) h2d(P->dalpha, p.alpha, P->Nt * sizeof(double));
+  if (P->pauli) h2d(P->dwts, p.H1, (size_t)P->m * P->q * 2 * sizeof(double));
   h2d(P->dpsi_i, p.psi_i, 2 * sizeof(double) * d);
   if (p.objective == ISM_OBJ_OVERLAP) h2d(P->dpsi_f, p.psi_f, 2 * sizeof(double) * d);
   else if (e == cudaSuccess) e = cudaMemsetAsync(P->dpsi_f, 0, 2 * sizeof(double) * d, P->st);
@@ -837,7 +883,7 @@ int ism_intermediate_states(ism_plan_t P, const double* u, double* phi) {
   int rc = begin(P);
   if (rc) return rc;
   const double* ud = nullptr;
-  if ((rc = stage_in(P, u, (long)P->B * P->Nt, P->du, &ud, true))) return rc;
+  if ((rc = stage_in(P, u, (long)P->B * P->Nt * P->m, P->du, &ud, true))) return rc;
   if ((rc = run_states(P, ud, nullptr, 0, 0))) return rc;
   if (P->gp) {
     const size_t blk = 2 * sizeof(double) * (size_t)(P->N + 1) * P->d;   // one set of N+1 states
@@ -855,7 +901,7 @@ int ism_subinterval_grad(ism_plan_t P, const double* phi, const double* u, doubl
   int rc = begin(P);
   if (rc) return rc;
   const double* ud = nullptr;
-  if ((rc = stage_in(P, u, (long)P->B * P->Nt, P->du, &ud, true))) return rc;
+  if ((rc = stage_in(P, u, (long)P->B * P->Nt * P->m, P->du, &ud, true))) return rc;
   if (P->gp) {
     const size_t blk = 2 * sizeof(double) * (size_t)(P->N + 1) * P->d;
     if (!is_device_ptr(phi) && !all_finite(phi, 4L * P->B * (P->N + 1) * P->d))
@@ -866,7 +912,7 @@ int ism_subinterval_grad(ism_plan_t P, const double* phi, const double* u, doubl
     ism::GPParams g = gparams(P, const_cast<double*>(ud));
     g.count = P->dcount + 3;
     ISM_CUDA_TRY(timed(P, 2, 1, [&] { return ism::launch_gp_sub(P->prec, g, P->st); }));
-    if ((rc = copy_out(P, grad, P->dgrad, (long)P->B * P->Nt))) return rc;
+    if ((rc = copy_out(P, grad, P->dgrad, (long)P->B * P->Nt * P->m))) return rc;
     if ((rc = copy_out(P, Jn, P->dJn, (long)P->B * P->N))) return rc;
     return finish(P);
   }
@@ -880,10 +926,10 @@ int ism_subinterval_grad(ism_plan_t P, const double* phi, const double* u, doubl
   ism::KParams k = kparams(P, const_cast<double*>(ud));
   k.update = 0;
   k.count = P->dcount + 3;
-  ISM_CUDA_TRY(ism::launch_cheb_prep(P->prec, k, P->st));
+  ISM_CUDA_TRY(prep_params(P, k));
   P->kernels += 1;
   ISM_CUDA_TRY(timed(P, 2, 1, [&] { return P->ks.subinterval(k, P->st); }));
-  if ((rc = copy_out(P, grad, P->dgrad, (long)P->B * P->Nt))) return rc;
+  if ((rc = copy_out(P, grad, P->dgrad, (long)P->B * P->Nt * P->m))) return rc;
   if ((rc = copy_out(P, Jn, P->dJn, (long)P->B * P->N))) return rc;
   return finish(P);
 }
@@ -893,7 +939,7 @@ int ism_iterate(ism_plan_t P, int iters, double* u_inout, double* J_hist, double
   if (iters < 0) return fail(ISM_EINVAL, "iters must be >= 0");
   int rc = begin(P);
   if (rc) return rc;
-  const long nu = (long)P->B * P->Nt;
+  const long nu = (long)P->B * P->Nt * P->m;
   const bool dev_u = is_device_ptr(u_inout);
   double* ud = nullptr;
   if (dev_u) {
@@ -925,7 +971,7 @@ int ism_iterate(ism_plan_t P, int iters, double* u_inout, double* J_hist, double
       k.Jn = l == 0 ? P->dJn : nullptr;
       k.count = P->dcount + 3;
       if (l > 0) {   // controls moved
-        ISM_CUDA_TRY(ism::launch_cheb_prep(P->prec, k, P->st));
+        ISM_CUDA_TRY(prep_params(P, k));
         P->kernels += 1;
       }
       if (k.form && !P->ks.large && !P->direct && P->ks.sweeps2)
@@ -961,7 +1007,7 @@ int ism_gradient(ism_plan_t P, const double* u, double* grad, double* J) {
   int rc = begin(P);
   if (rc) return rc;
   const double* ud = nullptr;
-  if ((rc = stage_in(P, u, (long)P->B * P->Nt, P->du, &ud, true))) return rc;
+  if ((rc = stage_in(P, u, (long)P->B * P->Nt * P->m, P->du, &ud, true))) return rc;
   if ((rc = run_states(P, ud, nullptr, 0, 0))) return rc;
   if (P->gp) {   // the sub-problem gradients at the adjoint targets are the global gradient
     ism::GPParams g = gparams(P, const_cast<double*>(ud));
@@ -977,7 +1023,7 @@ int ism_gradient(ism_plan_t P, const double* u, double* grad, double* J) {
     if (P->ks.large || P->direct || !P->ks.sweeps2) ISM_CUDA_TRY(timed(P, 2, 1, [&] { return P->ks.subinterval(k, P->st); }));
     else ISM_CUDA_TRY(timed(P, 2, 2, [&] { return P->ks.sweeps2(k, P->st); }));
   }
-  if ((rc = copy_out(P, grad, P->dgrad, (long)P->B * P->Nt))) return rc;
+  if ((rc = copy_out(P, grad, P->dgrad, (long)P->B * P->Nt * P->m))) return rc;
   if ((rc = copy_out(P, J, P->dJ, P->B))) return rc;
   return finish(P);
 }
@@ -987,7 +1033,7 @@ int ism_evaluate(ism_plan_t P, const double* u, double* J, double* F) {
   int rc = begin(P);
   if (rc) return rc;
   const double* ud = nullptr;
-  if ((rc = stage_in(P, u, (long)P->B * P->Nt, P->du, &ud, true))) return rc;
+  if ((rc = stage_in(P, u, (long)P->B * P->Nt * P->m, P->du, &ud, true))) return rc;
   if ((rc = run_states(P, ud, nullptr, 0, 0))) return rc;
   if ((rc = copy_out(P, J, P->dJ, P->B))) return rc;
   if ((rc = copy_out(P, F, P->dF, P->B))) return rc;

@@ -47,6 +47,11 @@ struct KParams {
   float* uf;                   // [B][Nt] FP32 copy of u (written by k_cheb_prep)
   int scheme;                  // 0: Chebyshev series; 1: Crank-Nicolson (r0, h1n: off-diagonal row-sum
                                //    bounds of H0 and H1)
+  // several controls (Pauli structure): u and grad are [B][Nt][m]
+  int m, q;
+  const double* wts;           // [m][q][2] weights (ax, ay) of X_b, Y_b in control c
+  void* cxy;                   // [B][Nt][2q] (R) step coefficients cx_b, cy_b (k_pauli_prep)
+  void* zq;                    // [B][Nt+N][2q] (R2) per-slot overlaps <delta|X_b psi>, <delta|Y_b psi>
   // direct global sweeps (large d): inputs and FP64 outputs, per-warp overlap partials
   const double2* psi_i;        // [d]
   const double2* psi_f;        // [d]

@@ -15,6 +15,7 @@ struct KernelSet {
   LaunchFn subinterval = nullptr;
   LaunchFn sweeps2 = nullptr;     // concurrent two-trajectory sweeps + gradient pass
   LaunchFn gsweep = nullptr;      // direct global sweeps (Algorithm 1 (a)-(b) without assembly)
+  LaunchFn prep = nullptr;        // per-sub-interval parameters, when not k_cheb_prep (several controls)
   int G = 0, E = 0;          // lanes per state, elements per lane (sub-interval sweep)
   int GA = 0;                // lanes per state in the assembly
   size_t op_smem = 0;        // dynamic shared memory of the op (dense H pairs)
@@ -29,6 +30,7 @@ bool kernels_tridiag(int prec, int d, bool h1diag, KernelSet* ks);   // h1diag: 
 bool kernels_bitflip(int prec, int d, KernelSet* ks);
 bool kernels_dense(int prec, int d, KernelSet* ks);
 bool kernels_large_bitflip(int prec, int d, KernelSet* ks);   // d = 128, 256, 512, 1024
+bool kernels_pauli(int prec, int d, KernelSet* ks);   // several controls, Pauli structure, d = 128..1024
 // Crank-Nicolson step (FP64 only): tridiagonal, bit-flip (d <= 64) and dense kinds
 bool kernels_cn(int prec, int kind, int d, bool h1diag, KernelSet* ks);
 cudaError_t launch_chain(int prec, const ChainParams& p, size_t smem, cudaStream_t st);   // k_chain + k_phi

@@ -133,7 +133,12 @@ int ism_server_submit(ism_server_t S, const ism_problem* prob, const ism_options
   int q = 0;
   while ((1 << q) < d) ++q;
   const size_t nH0 = gp ? (p.kind == ISM_H_GRID_GP_DOUBLE_WELL ? 4 : 3) : p.kind == ISM_H_DENSE ? (size_t)d * d : p.kind == ISM_H_TRIDIAG ? 2 * (size_t)d - 1 : (size_t)d;
-  const size_t nH1 = gp ? 0 : p.kind == ISM_H_DENSE ? (size_t)d * d : p.kind == ISM_H_TRIDIAG ? 2 * (size_t)d - 1 : (size_t)q;
+  const size_t m = p.kind == ISM_H_PAULI && p.controls > 1 ? (size_t)p.controls : 1;
+  const size_t nH1 = gp ? 0
+                     : p.kind == ISM_H_DENSE   ? (size_t)d * d
+                     : p.kind == ISM_H_TRIDIAG ? 2 * (size_t)d - 1
+                     : p.kind == ISM_H_PAULI   ? 2 * m * q
+                                               : (size_t)q;
   r->H0 = copy_of(p.H0, nH0);
   r->H1 = copy_of(p.H1, nH1);
   r->psi_i = copy_of(p.psi_i, 2 * (size_t)d);
@@ -148,7 +153,7 @@ int ism_server_submit(ism_server_t S, const ism_problem* prob, const ism_options
   r->prob.O = r->O.empty() ? nullptr : r->O.data();
   r->prob.alpha = r->alpha.empty() ? nullptr : r->alpha.data();
   r->opt = *opt;
-  r->u.assign(u0, u0 + (size_t)B * p.Nt);
+  r->u.assign(u0, u0 + (size_t)B * p.Nt * m);
   r->J.assign((size_t)B * ((size_t)iters + 1), 0.0);
   r->iters = iters;
   r->bytes = bytes;
