@@ -40,12 +40,14 @@ DESCR = {"rotor41": "rigid rotor j<=40, maximise <cos theta>(T)",
          "ising1024": "10-spin open Ising chain, X control, |0^10> -> |1^10>",
          "gp512": "1D Gross-Pitaevskii condensate, 512-point grid, trap centre control, ground -> odd state",
          "gp512dw": "1D Gross-Pitaevskii condensate, 512-point grid, double-well splitting control, "
-                    "harmonic ground state -> split-trap ground state"}
-SAMPLE_DIV = {"rotor41": 8, "spin16": 1, "ising1024": 64, "gp512": 8, "gp512dw": 8}
+                    "harmonic ground state -> split-trap ground state",
+         "spin5": "5 coupled spins, 10 controls (u_x, u_y per spin), density matrix in Liouville space, "
+                  "I_x(1) -> I_x(5)"}
+SAMPLE_DIV = {"rotor41": 8, "spin16": 1, "ising1024": 64, "gp512": 8, "gp512dw": 8, "spin5": 256}
 # independent solves per launch: multiples of the 152 SMs (16 problems per SM for the lane-group
 # sweeps, one CTA per SM and direction for ising1024, two 304-CTA waves for the grid model)
-BATCH_DEFAULT = {"rotor41": 2432, "spin16": 2432, "ising1024": 76, "gp512": 304, "gp512dw": 304}
-SOLVE_ITERS = {"rotor41": 50, "spin16": 20, "ising1024": 20, "gp512": 20, "gp512dw": 20}   # oracle sample = Nt/div steps, N/div sub-intervals
+BATCH_DEFAULT = {"rotor41": 2432, "spin16": 2432, "ising1024": 76, "gp512": 304, "gp512dw": 304, "spin5": 76}
+SOLVE_ITERS = {"rotor41": 50, "spin16": 20, "ising1024": 20, "gp512": 20, "gp512dw": 20, "spin5": 20}   # oracle sample = Nt/div steps, N/div sub-intervals
 FP32_LANES_PER_SM = 128
 SMS = 152
 SM_MAX_MHZ = 2070.0
@@ -131,6 +133,8 @@ def nnz_of(kind: str, d: int) -> int:
         return 3 * d - 2
     if kind == "bitflip":
         return d * (1 + int(round(np.log2(d))))
+    if kind == "pauli":   # diagonal + an X and a Y flip per bit (the Y flips count as complex x real too)
+        return d * (1 + 2 * int(round(np.log2(d))))
     return d * d
 
 
@@ -207,6 +211,8 @@ def load_workload(cfg: str, N=None, Nt=None):
         w = W.gp_double_well(Nt=Nt or 10000, N=N or 64, states=_GP_STATES.get("gp512dw"))
         _GP_STATES["gp512dw"] = (w.psi_i, w.psi_f)
         return w.with_(rho=0.05)
+    if cfg == "spin5":
+        return W.spin5_liouville(Nt=Nt or 32768, N=N or 128).with_(rho=100.0, iters=20)
     return W.config(cfg, N=N, Nt=Nt)
 
 
@@ -224,7 +230,9 @@ def oracle_sample(cfg: str, N_full: int):
     Nt_s = max(1, full.Nt // div)
     N_s = max(1, full.N // div)
     w = load_workload(cfg, N=N_s, Nt=Nt_s)
-    O = gp_oracle if cfg.startswith("gp512") else ism_oracle
+    from oracle import mc_oracle
+
+    O = gp_oracle if cfg.startswith("gp512") else mc_oracle if cfg == "spin5" else ism_oracle
     t0 = time.perf_counter()
     O.ism_iteration(w, w.u0, w.rho, w.local_iters)
     dt = time.perf_counter() - t0
@@ -441,7 +449,7 @@ def run_ours(args):
     plan = P.Plan(w, precision="mixed", batch=B, stream=stream)
     rng = np.random.default_rng(2000 + rank)
     amp = float(np.max(np.abs(w.u0)))   # further problems: controls of the same amplitude as u0
-    U0 = np.stack([w.u0] + [rng.uniform(-amp, amp, w.Nt) for _ in range(B - 1)])
+    U0 = np.stack([w.u0] + [rng.uniform(-amp, amp, w.u0.shape) for _ in range(B - 1)])
     u_dev = torch.tensor(U0, dtype=torch.float64, device="cuda").contiguous()
     flush = torch.empty(512 * 1024 * 1024 // 4, dtype=torch.float32, device="cuda")   # 512 MB > L2
 
@@ -487,6 +495,9 @@ def run_ours(args):
     elif direct and not large:
         names = ["k_gsweep", "k_phi", "k_subinterval"]
         kernels = ["k_cheb_prep + k_gsweep", "k_phi", "k_subinterval"]
+    elif plan.kind == "pauli":
+        names = ["k_pauli_sweep", "k_phi", "k_pauli_sub"]
+        kernels = ["k_pauli_prep + k_pauli_sweep", "k_phi", "k_pauli_sub"]
     elif large:
         names = ["k_lsweep", "k_phi", "k_lsub"]
         kernels = ["k_cheb_prep + k_lsweep", "k_phi", "k_lsub"]
