@@ -753,6 +753,80 @@ __device__ __forceinline__ void prop_step(Vec<R, E>& v, Vec<R, E>& lo, const Op&
   }
 }
 
+// Series coefficients of one sub-interval as packed register pairs (c, c), with the sign of the odd
+// terms of the adjoint folded in: the packed step then reads no shared memory and builds no pairs
+// inside its term loop.  Valid when the warp's term count is at most KR.
+template <int KR>
+struct CoefP {
+  float2 c[KR], l[KR];   // signed a_k as hi, lo (k >= 2)
+  float2 b0h, b0l;       // a_0 (or a_0 - 1 when compensated) as hi, lo
+  float2 a1h, a1l;       // signed a_1 as hi, lo
+};
+template <int KR, bool ADJ, bool COMP>
+__device__ __forceinline__ void load_coef(CoefP<KR>& cp, const Cheb<float>& ch) {
+  const float sg = ADJ ? -1.f : 1.f;
+#pragma unroll
+  for (int k = 2; k < KR; ++k) {
+    const float s = (k & 1) ? sg : 1.f;
+    cp.c[k] = bc2(s * ch.cf[k]);
+    cp.l[k] = bc2(s * ch.cl[k]);
+  }
+  cp.b0h = bc2(COMP ? ch.c0h : ch.a0h);
+  cp.b0l = bc2(COMP ? ch.c0l : ch.a0l);
+  cp.a1h = bc2(sg * ch.a1h);
+  cp.a1l = bc2(sg * ch.a1l);
+}
+
+// cheb_step_p with the coefficients in registers (K <= KR terms, warp-uniform).
+template <bool COMP, int KR, int E, class Op>
+__device__ __forceinline__ void cheb_step_pr(VecP<E>& v, VecP<E>& lo, const Op& op, const CoefP<KR>& cp, int K,
+                                             int Sw, int S) {
+  for (int s = 0; s < Sw; ++s) {
+    const bool on = s < S;
+    VecP<E> t0 = v, t1, acc, o, zero;
+#pragma unroll
+    for (int r = 0; r < E; ++r) zero.z[r] = make_float2(0.f, 0.f);
+    op.rec_p(t0, zero, t1);   // t1 = 2 Y t0
+#pragma unroll
+    for (int r = 0; r < E; ++r) {
+      t1.z[r] = mul2(t1.z[r], bc2(0.5f));
+      acc.z[r] = fma2(cp.b0h, t0.z[r], mul2(cp.b0l, t0.z[r]));
+      o.z[r] = fma2(cp.a1h, t1.z[r], mul2(cp.a1l, t1.z[r]));
+    }
+#pragma unroll
+    for (int k = 2; k < KR; k += 2) {
+      if (k >= K) break;
+      op.rec_p(t1, t0, t0);   // t0 <- T_k
+#pragma unroll
+      for (int r = 0; r < E; ++r) acc.z[r] = fma2(cp.c[k], t0.z[r], fma2(cp.l[k], t0.z[r], acc.z[r]));
+      if (k + 1 < K && k + 1 < KR) {
+        op.rec_p(t0, t1, t1);   // t1 <- T_{k+1}
+#pragma unroll
+        for (int r = 0; r < E; ++r) o.z[r] = fma2(cp.c[k + 1], t1.z[r], fma2(cp.l[k + 1], t1.z[r], o.z[r]));
+      }
+    }
+#pragma unroll
+    for (int r = 0; r < E; ++r) {
+      acc.z[r].x += o.z[r].y;
+      acc.z[r].y -= o.z[r].x;
+    }
+    if (!on) continue;
+#pragma unroll
+    for (int r = 0; r < E; ++r) {
+      if (!COMP) {
+        v.z[r] = acc.z[r];
+      } else {
+        const float2 x = v.z[r];
+        const float2 t = add2(acc.z[r], lo.z[r]);
+        const float2 sm = add2(x, t);
+        const float2 bb = add2(sm, neg2(x));
+        lo.z[r] = add2(add2(x, neg2(add2(sm, neg2(bb)))), add2(t, neg2(bb)));
+        v.z[r] = sm;
+      }
+    }
+  }
+}
+
 // cheb_step on packed FP32 states (the same series, sub-steps and compensation).  Odd terms multiply
 // (-i)^k (forward) or (+i)^k (adjoint): they are summed into a separate packed accumulator o with
 // their signed real coefficients and folded in once per sub-step, acc += (o.im, -o.re), so the

@@ -703,6 +703,8 @@ __global__ void __launch_bounds__(128) k_sweeps2(KParams p) {
 // direction (the group shuffles and warp barriers need the whole warp on the same path).  Direction 1
 // (chi) exists only for the overlap objective; the observable objective runs chi after psi in the
 // same group (chi(T) = O psi(T) needs psi(T)).
+constexpr int GSWEEP_KR = 10;   // series terms held in registers by the packed direct sweeps
+
 template <typename R, class Op>
 __global__ void __launch_bounds__(128) k_gsweep(KParams p) {
   constexpr int G = Op::G, E = Op::E, GPB = 128 / G;
@@ -774,12 +776,25 @@ __global__ void __launch_bounds__(128) k_gsweep(KParams p) {
       const int ns = j1 - j0;
       auto jof = [&](int s) { return ADJ ? j1 - 1 - s : j0 + s; };
       float ua = __ldg(ufb + jof(0)), ub1 = ns > 1 ? __ldg(ufb + jof(1)) : 0.f;
-      for (int s = 0; s < ns; ++s) {
-        const float uj = ua;
-        ua = ub1;
-        if (s + 2 < ns) ub1 = __ldg(ufb + jof(s + 2));
-        op.set_u(uj, ch, lg);
-        cheb_step_p<ADJ, true>(pv, pl, op, ch, Kw, Sw);
+      if (Kw <= GSWEEP_KR) {   // coefficients in registers
+        CoefP<GSWEEP_KR> cp;
+        load_coef<GSWEEP_KR, ADJ, true>(cp, ch);
+        const int S = ch.S;
+        for (int s = 0; s < ns; ++s) {
+          const float uj = ua;
+          ua = ub1;
+          if (s + 2 < ns) ub1 = __ldg(ufb + jof(s + 2));
+          op.set_u(uj, ch, lg);
+          cheb_step_pr<true>(pv, pl, op, cp, Kw, Sw, S);
+        }
+      } else {
+        for (int s = 0; s < ns; ++s) {
+          const float uj = ua;
+          ua = ub1;
+          if (s + 2 < ns) ub1 = __ldg(ufb + jof(s + 2));
+          op.set_u(uj, ch, lg);
+          cheb_step_p<ADJ, true>(pv, pl, op, ch, Kw, Sw);
+        }
       }
 #pragma unroll
       for (int r = 0; r < E; ++r) { v.re[r] = pv.z[r].x; v.im[r] = pv.z[r].y; lo.re[r] = pl.z[r].x; lo.im[r] = pl.z[r].y; }
