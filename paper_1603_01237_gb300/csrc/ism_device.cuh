@@ -232,6 +232,8 @@ struct OpTridiag {
   R yb[EB], yo[E], yom;   // 2u H1_ee/rad, 2Y off-diagonal (e, e+1), 2Y off-diagonal (e0-1, e0)
   R h1m;                  // H1 off-diagonal (e0-1, e0)
   int dd, e0;
+  // packed (c, c) copies of the recurrence coefficients for rec_p (R = float), formed once per step
+  float2 ah2[E], al2[E], yo2[E], yb2[EB], yom2;
 
   // H: packed op data in R; H0d: FP64 diagonal of H0
   __device__ void load(const R* H, const double* H0d, int d, int lg, void*) {
@@ -254,6 +256,10 @@ struct OpTridiag {
     for (int r = 0; r < E; ++r) {
       int e = lg * E + r;
       split2<R>(e < d ? (H0d[e] - ch.cd) * ch.s2d : 0.0, ah[r], al[r]);
+      if constexpr (sizeof(R) == 4) {
+        ah2[r] = bc2((float)ah[r]);
+        al2[r] = bc2((float)al[r]);
+      }
     }
   }
   __device__ __forceinline__ void set_u(R u, const Cheb<R>& ch, int lg) {
@@ -268,6 +274,14 @@ struct OpTridiag {
     }
     R t = g_up<G>(yo[E - 1]);
     yom = lg == 0 ? R(0) : t;
+    if constexpr (sizeof(R) == 4) {
+#pragma unroll
+      for (int r = 0; r < E; ++r) {
+        yo2[r] = bc2((float)yo[r]);
+        if (HB) yb2[r] = bc2((float)yb[r]);
+      }
+      yom2 = bc2((float)yom);
+    }
   }
   template <class V>
   __device__ __forceinline__ void rec(const V& in, const V& sub, V& out) const {
@@ -312,11 +326,11 @@ struct OpTridiag {
     for (int r = 0; r < E; ++r) {
       const float2 m = r == 0 ? l : in.z[r - 1];
       const float2 pn = r == E - 1 ? q : in.z[r + 1];
-      const float ym = r == 0 ? (float)yom : (float)yo[r - 1];
-      float2 x = fma2(bc2(ym), m, fma2(bc2((float)yo[r]), pn, neg2(sub.z[r])));
-      x = fma2(bc2((float)al[r]), in.z[r], x);
-      if (HB) x = fma2(bc2((float)yb[r]), in.z[r], x);
-      out.z[r] = fma2(bc2((float)ah[r]), in.z[r], x);
+      const float2 ym = r == 0 ? yom2 : yo2[r - 1];
+      float2 x = fma2(ym, m, fma2(yo2[r], pn, neg2(sub.z[r])));
+      x = fma2(al2[r], in.z[r], x);
+      if (HB) x = fma2(yb2[r], in.z[r], x);
+      out.z[r] = fma2(ah2[r], in.z[r], x);
     }
   }
   __device__ __forceinline__ void h1_p(const VecP<E>& in, VecP<E>& out) const {
