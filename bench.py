@@ -161,10 +161,13 @@ def kernel_source_hash() -> str:
     return h.hexdigest()[:16]
 
 
-# DRAM bytes (dram__bytes_read.sum + dram__bytes_write.sum) per problem per launch of a kernel, from
-# one ncu capture of a smaller batch of the same workload (traffic grows with the problems a launch
-# processes), keyed by (kernel, workload) with the kernel source hash at capture time; see profiles/.
-TRAFFIC_PER_PROBLEM = {}
+# DRAM bytes (dram__bytes_read.sum + dram__bytes_write.sum) of one full-size launch divided by its
+# problems, from a one-pass ncu capture of the default step (2432 rotor problems); reported only while
+# the kernel sources hash to the captured build.
+TRAFFIC_PER_PROBLEM = {
+    ("k_gsweep", "rotor41"): {"bytes_per_problem": (563161088 + 374609408) / 2432, "source_hash": "56d6ab1a1a96f328"},
+    ("k_subinterval", "rotor41"): {"bytes_per_problem": (20624017664 + 20791980288) / 2432, "source_hash": "56d6ab1a1a96f328"},
+}
 
 
 def traffic_of(kernel: str, workload: str, batch: int):
