@@ -172,3 +172,40 @@ def test_crank_nicolson_option_validated_on_the_host(lib):
     opt.scheme = 7
     n = abi.C.c_size_t()
     assert lib.ism_plan_footprint(abi.C.byref(prob), abi.C.byref(opt), abi.C.byref(n)) == abi.ISM_EINVAL
+
+
+def test_several_controls_validated_on_the_host(lib):
+    """The Pauli kind (several controls): sized per control, d = 128..1024 only, overlap objective, no
+    penalty; the controls field is refused on the other kinds."""
+    import workloads as W
+    from paper_1603_01237_gb300 import abi
+
+    w = W.random_pauli(8, 3, 7, T=1.0, Nt=100, N=4)
+    f3 = abi.footprint(w, precision="mixed")
+    f1 = abi.footprint(w.with_(ax=w.ax[:1], ay=w.ay[:1], u0=w.u0[:, :1]), precision="mixed")
+    assert f3 > f1 > 0   # controls, gradients per control
+    with pytest.raises(abi.IsmError) as ei:
+        abi.footprint(W.random_pauli(6, 2, 7, T=1.0, Nt=50, N=2))
+    assert ei.value.status == abi.ISM_EUNSUPPORTED   # d = 64: the Pauli kind needs d >= 128
+    prob, opt, keep = abi.problem_and_options(w, precision="fp64")
+    n = abi.C.c_size_t()
+    prob.controls = 33
+    assert lib.ism_plan_footprint(abi.C.byref(prob), abi.C.byref(opt), abi.C.byref(n)) == abi.ISM_EINVAL
+    s = W.config("spin16", Nt=100)
+    prob, opt, keep = abi.problem_and_options(s, precision="fp64")
+    prob.controls = 2
+    assert lib.ism_plan_footprint(abi.C.byref(prob), abi.C.byref(opt), abi.C.byref(n)) == abi.ISM_EINVAL
+    with pytest.raises(abi.IsmError) as ei:
+        abi.footprint(w, precision="fp64", scheme="crank_nicolson")
+    assert ei.value.status == abi.ISM_EUNSUPPORTED
+
+
+def test_double_well_kind_validated_on_the_host(lib):
+    import workloads as W
+    from paper_1603_01237_gb300 import abi
+
+    w = W.gp_double_well(n=64, Nt=50, N=2, steps=10)
+    assert abi.footprint(w) > 0
+    with pytest.raises(abi.IsmError) as ei:
+        abi.footprint(w.with_(dw=-1.0))
+    assert ei.value.status == abi.ISM_EINVAL
