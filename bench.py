@@ -3,7 +3,7 @@
 
 A step is one pass of Algorithm 1 (propagator assembly, chain and intermediate states, sub-interval
 forward/adjoint/gradient sweeps, control update) over a batch of independent rigid-rotor problems
-(d = 41, Nt = 20000, N = 128, mixed precision, 2432 = 16 x 152 problems per launch by default).  The value is
+(d = 41, Nt = 20000, N = 128, mixed precision, 4864 = 32 x 152 problems per launch by default).  The value is
 ISM iterations per second summed over the batch; the line also carries the one-problem solve
 latency (p50/p99 of complete 50-iteration solves), the plain FP64 one-problem path, the paper's
 Crank-Nicolson scheme in FP64 (batched and one problem), a serving mix, the end-to-end rate through
@@ -44,9 +44,10 @@ DESCR = {"rotor41": "rigid rotor j<=40, maximise <cos theta>(T)",
          "spin5": "5 coupled spins, 10 controls (u_x, u_y per spin), density matrix in Liouville space, "
                   "I_x(1) -> I_x(5)"}
 SAMPLE_DIV = {"rotor41": 8, "spin16": 1, "ising1024": 64, "gp512": 8, "gp512dw": 8, "spin5": 256}
-# independent solves per launch: multiples of the 152 SMs (16 problems per SM for the lane-group
-# sweeps, one CTA per SM and direction for ising1024, two 304-CTA waves for the grid model)
-BATCH_DEFAULT = {"rotor41": 2432, "spin16": 2432, "ising1024": 76, "gp512": 304, "gp512dw": 304, "spin5": 76}
+# independent solves per launch: multiples of the 152 SMs (rotor41: two CTAs of 16 problems per SM in
+# the wide lane layout of the direct sweeps; spin16: two CTAs of 8; one CTA per SM and direction for
+# the CTA-wide kinds; two 152-CTA waves for the grid model)
+BATCH_DEFAULT = {"rotor41": 4864, "spin16": 2432, "ising1024": 76, "gp512": 304, "gp512dw": 304, "spin5": 76}
 SOLVE_ITERS = {"rotor41": 50, "spin16": 20, "ising1024": 20, "gp512": 20, "gp512dw": 20, "spin5": 20}   # oracle sample = Nt/div steps, N/div sub-intervals
 FP32_LANES_PER_SM = 128
 SMS = 152

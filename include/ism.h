@@ -256,7 +256,9 @@ int ism_plan_footprint(const ism_problem* prob, const ism_options* opt, size_t* 
  *   trajectories directly (bit-flip d >= 128, one state per CTA) instead of assembling M_n,
  *   6: how Algorithm 1 (a)-(b) runs (ism_options.step1 after the default is resolved: 1 or 2),
  *   7: tiles per block of the blocked chain (1 = plain chain),
- *   8: the plan's time-step scheme (ism_scheme).
+ *   8: the plan's time-step scheme (ism_scheme),
+ *   9: lanes per state of the direct sweeps (0 when the plan assembles; fewer lanes with more
+ *      elements each once the batch gives every SM two CTAs of that layout).
  *   Returns -1 for a bad key. */
 long long ism_plan_info(ism_plan_t plan, int key);
 

@@ -78,6 +78,7 @@ struct ism_plan_s {
   int gppot = 0;                         // potential: 0 harmonic (x - u)^2/2, 1 double well
   int m = 1, q = 0;                      // controls per step; bits of d (Pauli kind)
   bool pauli = false;
+  bool wide = false;                     // direct sweeps in the wide lane layout
   double* dwts = nullptr;                // Pauli kind: [m][q][2] control weights
   void* dcxy = nullptr;                  // Pauli kind: [B][Nt][2q] step coefficients (R)
   double gpdw = 0;                       // double-well separation D
@@ -448,7 +449,7 @@ int run_states(ism_plan_s* P, const double* u, double* Jhist, int hist_stride, i
   }
   ism::KParams k = kparams(P, const_cast<double*>(u));
   if (P->ks.large || P->direct) {   // direct sweeps: psi(t_n), chi(t_n) in FP64
-    ism::LaunchFn sweep = P->ks.large ? P->ks.lsweep : P->ks.gsweep;
+    ism::LaunchFn sweep = P->ks.large ? P->ks.lsweep : P->wide ? P->ks.gsweep_wide : P->ks.gsweep;
     ISM_CUDA_TRY(timed(P, 0, 2, [&] {
       cudaError_t e = prep_params(P, k);
       return e != cudaSuccess ? e : sweep(k, P->st);
@@ -634,6 +635,15 @@ int plan_build(const ism_problem* prob, const ism_options* opt, void* cuda_strea
                                                     : ism::select_kernels(P->prec, p.kind, d, &P->ks, h1diag);
   if (!ok) { delete P; return fail(ISM_EUNSUPPORTED, "no compiled kernel for this kind and d"); }
   P->direct = !P->ks.large && (opt->step1 == 2 || (opt->step1 == 0 && P->B >= 96));
+  if (P->direct && P->ks.gsweep_wide) {
+    // the wide layout holds 128 / GW problems per CTA; it pays once every SM gets two of its CTAs
+    int nsm = 0;
+    if (cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, P->dev) != cudaSuccess || nsm < 1) {
+      cudaGetLastError();
+      nsm = 152;
+    }
+    P->wide = (long)P->B >= 2L * nsm * (128 / P->ks.GW);
+  }
   const int gpw = P->ks.large ? 1 : 32 / P->ks.GA;
   P->dpad = (d + gpw - 1) / gpw * gpw;
   P->ldm = d | 1;                                   // odd column stride
@@ -850,6 +860,7 @@ long long ism_plan_info(ism_plan_t P, int key) {
     case 6: return (P->ks.large || P->direct) ? 2 : 1;
     case 7: return P->Nc ? P->sblk : 1;
     case 8: return P->scheme;
+    case 9: return P->wide ? P->ks.GW : (P->direct ? P->ks.G : 0);
     default: return -1;
   }
 }

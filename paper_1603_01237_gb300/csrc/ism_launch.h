@@ -15,6 +15,10 @@ struct KernelSet {
   LaunchFn subinterval = nullptr;
   LaunchFn sweeps2 = nullptr;     // concurrent two-trajectory sweeps + gradient pass
   LaunchFn gsweep = nullptr;      // direct global sweeps (Algorithm 1 (a)-(b) without assembly)
+  // the same sweeps in the assembly's lane layout (fewer lanes, more elements per lane): fewer
+  // shuffles per element, for batches that give every SM two CTAs of it (FP32 packed path only)
+  LaunchFn gsweep_wide = nullptr;
+  int GW = 0;                     // lanes per state of gsweep_wide
   LaunchFn prep = nullptr;        // per-sub-interval parameters, when not k_cheb_prep (several controls)
   int G = 0, E = 0;          // lanes per state, elements per lane (sub-interval sweep)
   int GA = 0;                // lanes per state in the assembly

@@ -79,6 +79,9 @@ void fill_set(KernelSet* ks) {
   if constexpr (SWEEPS2) ks->sweeps2 = &launch_sweeps2_t<R, OpS>;
   else ks->sweeps2 = nullptr;
   ks->gsweep = &launch_gsweep_t<R, OpS>;
+  if constexpr (sizeof(R) == 4 && OpA::PACKED && OpA::G != OpS::G) ks->gsweep_wide = &launch_gsweep_t<R, OpA>;
+  else ks->gsweep_wide = nullptr;
+  ks->GW = OpA::G;
   ks->G = OpS::G;
   ks->E = OpS::E;
   ks->GA = OpA::G;

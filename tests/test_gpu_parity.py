@@ -321,3 +321,27 @@ def test_bounded_wait_gives_up_cleanly(P):
     with P.Plan(w, precision="mixed") as pl:
         J, _ = pl.evaluate(w.u0)
     assert abs(J[0] - Jo) <= 2e-5
+
+
+def test_direct_sweeps_wide_layout_for_large_batches(P):
+    """From 2 x 152 x 16 problems per plan the direct sweeps switch to the assembly's lane layout
+    (8 lanes x 6 elements for d = 41): the same results as the 16-lane layout of a small batch, and
+    the oracle's within the mixed tolerance."""
+    r = W.config("rotor41", Nt=2000, N=16).with_(T=float(np.pi) / 10.0)
+    rng = np.random.default_rng(9)
+    rows = np.stack([r.u0] + [rng.uniform(-1, 1, r.Nt) for _ in range(2)])
+    B = 4864
+    U = np.tile(rows, (B // 3 + 1, 1))[:B]
+    with P.Plan(r, precision="mixed", batch=B) as pl:
+        assert pl.info(6) == 2 and pl.info(9) == 8
+        Jw, Fw = pl.evaluate(U)
+        gw, _ = pl.gradient(U)
+    with P.Plan(r, precision="mixed", batch=3, step1=2) as pl:
+        assert pl.info(9) == 16
+        Jn, Fn = pl.evaluate(rows)
+        gn, _ = pl.gradient(rows)
+    for b in range(3):
+        for k in (b, b + 3 * 700, B - 3 + ((b - B) % 3)):
+            assert abs(Jw[k] - Jn[b]) <= 1e-12 and rel_l2(gw[k], gn[b]) <= 1e-10
+        Jo, Fo = O.objective(r, rows[b])
+        assert abs(Jn[b] - Jo) <= 1e-5
