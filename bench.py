@@ -146,17 +146,20 @@ def cheb_flops(kind: str, d: int, y_apps: int, terms: int, substeps: int) -> flo
     return float(y_apps) * (4 * nnz_of(kind, d) + 2 * d) + float(terms) * 4 * d + float(substeps) * 6 * d
 
 
-def kernel_source_hash() -> str:
-    """Hash of the CUDA sources and headers the kernels are built from (a captured DRAM traffic is
-    reported only while the kernels are the ones it was captured on)."""
+KERNEL_SOURCES = ("ism_device.cuh", "ism_kernels.cuh", "ism_launch_impl.cuh", "ism_launch.h", "ism_kern_tridiag.cu")
+
+
+def kernel_source_hash(files=KERNEL_SOURCES) -> str:
+    """Hash of the sources the small-d Chebyshev kernels (k_cheb_prep, k_gsweep, k_subinterval, ...)
+    are built from: a captured DRAM traffic is reported only while those kernels are the ones it was
+    captured on."""
     import hashlib
 
     h = hashlib.sha256()
     csrc = os.path.join(ROOT, "paper_1603_01237_gb300", "csrc")
-    for name in sorted(os.listdir(csrc)):
-        if name.endswith((".cu", ".cuh", ".h")):
-            with open(os.path.join(csrc, name), "rb") as f:
-                h.update(name.encode() + b"\0" + f.read())
+    for name in files:
+        with open(os.path.join(csrc, name), "rb") as f:
+            h.update(name.encode() + b"\0" + f.read())
     with open(os.path.join(ROOT, "include", "ism.h"), "rb") as f:
         h.update(f.read())
     return h.hexdigest()[:16]
