@@ -166,11 +166,11 @@ def kernel_source_hash(files=KERNEL_SOURCES) -> str:
 
 
 # DRAM bytes (dram__bytes_read.sum + dram__bytes_write.sum) of one full-size launch divided by its
-# problems, from a one-pass ncu capture of the default step (2432 rotor problems); reported only while
-# the kernel sources hash to the captured build.
+# problems, from a one-pass ncu capture of the default step (4864 rotor problems: k_gsweep in the wide
+# lane layout); reported only while the kernel sources hash to the captured build.
 TRAFFIC_PER_PROBLEM = {
-    ("k_gsweep", "rotor41"): {"bytes_per_problem": (563161088 + 374609408) / 2432, "source_hash": "56d6ab1a1a96f328"},
-    ("k_subinterval", "rotor41"): {"bytes_per_problem": (20624017664 + 20791980288) / 2432, "source_hash": "56d6ab1a1a96f328"},
+    ("k_gsweep", "rotor41"): {"bytes_per_problem": (1169409536 + 789165568) / 4864, "source_hash": "b76aad182f545798"},
+    ("k_subinterval", "rotor41"): {"bytes_per_problem": (41560729344 + 41613115648) / 4864, "source_hash": "b76aad182f545798"},
 }
 
 

@@ -25,6 +25,7 @@
 
 #include "ism_device.cuh"
 #include "ism_gp.h"
+#include "ism_launch.h"
 
 namespace ism {
 namespace {
@@ -500,8 +501,7 @@ int gp_threads(int n) { return n / 8 < 32 ? 32 : n / 8; }
 template <typename R, class K>
 cudaError_t launch(K kern, const GPParams& p, dim3 grid, cudaStream_t st) {
   const size_t sm = gp_smem<R>(p.n);
-  // opt in whenever dynamic + static shared memory could pass the 48 KB default
-  cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
+  cudaError_t e = raise_smem_cap(reinterpret_cast<const void*>(kern));
   if (e != cudaSuccess) return e;
   kern<<<grid, gp_threads(p.n), sm, st>>>(p);
   return cudaGetLastError();

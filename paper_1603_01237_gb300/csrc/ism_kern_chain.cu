@@ -1,4 +1,8 @@
 // The chains over sub-interval propagators (FP32 or FP64 tiles) and the intermediate states.
+#include <mutex>
+#include <set>
+#include <utility>
+
 #include "ism_launch_impl.cuh"
 
 namespace ism {
@@ -7,7 +11,7 @@ template <typename R, int JC>
 static cudaError_t chain_t(const ChainParams& p, size_t smem, cudaStream_t st) {
   dim3 grid(p.obj == 0 ? 2 : 1, p.B);
   const int threads = (chain_consumer_warps(p.d) + 1) * 32;   // consumer warps + one producer warp
-  cudaError_t e = cudaFuncSetAttribute(k_chain<R, JC>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+  cudaError_t e = raise_smem_cap(reinterpret_cast<const void*>(k_chain<R, JC>));
   if (e != cudaSuccess) return e;
   k_chain<R, JC><<<grid, threads, smem, st>>>(p);
   return cudaGetLastError();
@@ -32,7 +36,7 @@ template <typename R, int JC>
 static cudaError_t fill_t(const ChainParams& p, cudaStream_t st) {
   using R2 = typename C2<R>::T;
   const size_t sm = (size_t)p.sblk * p.tile_stride * sizeof(R2);
-  cudaError_t e = cudaFuncSetAttribute(k_fill<R, JC>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
+  cudaError_t e = raise_smem_cap(reinterpret_cast<const void*>(k_fill<R, JC>));
   if (e != cudaSuccess) return e;
   k_fill<R, JC><<<dim3(p.Nc, p.B, 2), chain_consumer_warps(p.d) * 32, sm, st>>>(p);
   return cudaGetLastError();
@@ -57,7 +61,7 @@ template <typename R>
 static cudaError_t blockprod_t(const ChainParams& p, cudaStream_t st) {
   using R2 = typename C2<R>::T;
   const size_t sm = 3 * p.tile_stride * sizeof(R2);
-  cudaError_t e = cudaFuncSetAttribute(k_blockprod<R>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
+  cudaError_t e = raise_smem_cap(reinterpret_cast<const void*>(k_blockprod<R>));
   if (e != cudaSuccess) return e;
   k_blockprod<R><<<dim3(p.Nc, p.B), 256, sm, st>>>(p);
   return cudaGetLastError();
@@ -93,5 +97,24 @@ cudaError_t launch_cheb_prep(int prec, const KParams& p, cudaStream_t st) {
 }
 
 size_t cheb_bytes(int prec) { return prec == 0 ? sizeof(Cheb<double>) : sizeof(Cheb<float>); }
+
+cudaError_t raise_smem_cap(const void* kernel) {
+  static std::mutex mu;
+  static std::set<std::pair<const void*, int>> done;
+  int dev = 0;
+  cudaError_t e = cudaGetDevice(&dev);
+  if (e != cudaSuccess) return e;
+  std::lock_guard<std::mutex> lk(mu);
+  if (done.count({kernel, dev})) return cudaSuccess;
+  int optin = 0;
+  e = cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev);
+  if (e != cudaSuccess) return e;
+  cudaFuncAttributes a;
+  e = cudaFuncGetAttributes(&a, kernel);
+  if (e != cudaSuccess) return e;
+  e = cudaFuncSetAttribute(kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, optin - (int)a.sharedSizeBytes);
+  if (e == cudaSuccess) done.insert({kernel, dev});
+  return e;
+}
 
 }  // namespace ism

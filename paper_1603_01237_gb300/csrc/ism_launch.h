@@ -8,6 +8,12 @@ namespace ism {
 struct KParams;
 struct ChainParams;
 
+// Raise a kernel's dynamic shared-memory cap, once per kernel and device, to all the device allows
+// beside the kernel's static shared memory.  Launches then pass their own (smaller) sizes; plans on
+// other host threads (the serving loop) cannot lower the cap under a launch in flight, which a
+// per-launch cudaFuncSetAttribute with differing sizes would.
+cudaError_t raise_smem_cap(const void* kernel);
+
 typedef cudaError_t (*LaunchFn)(const KParams&, cudaStream_t);
 
 struct KernelSet {

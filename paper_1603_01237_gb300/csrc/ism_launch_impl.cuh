@@ -17,7 +17,7 @@ cudaError_t launch_assemble_t(const KParams& p, cudaStream_t st) {
   const long grid = (groups + GPB - 1) / GPB;
   const size_t smem = op_smem_bytes<R, Op>();
   if (smem > 40 * 1024) {   // leave room for the static shared memory under the 48 KB default
-    cudaError_t e = cudaFuncSetAttribute(k_assemble<R, Op>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    cudaError_t e = raise_smem_cap(reinterpret_cast<const void*>(k_assemble<R, Op>));
     if (e != cudaSuccess) return e;
   }
   k_assemble<R, Op><<<(unsigned)grid, 128, smem, st>>>(p);
@@ -31,7 +31,7 @@ cudaError_t launch_subinterval_t(const KParams& p, cudaStream_t st) {
   const long grid = (groups + GPB - 1) / GPB;
   const size_t smem = op_smem_bytes<R, Op>();
   if (smem > 40 * 1024) {
-    cudaError_t e = cudaFuncSetAttribute(k_subinterval<R, Op>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    cudaError_t e = raise_smem_cap(reinterpret_cast<const void*>(k_subinterval<R, Op>));
     if (e != cudaSuccess) return e;
   }
   k_subinterval<R, Op><<<(unsigned)grid, 128, smem, st>>>(p);
@@ -45,7 +45,7 @@ cudaError_t launch_sweeps2_t(const KParams& p, cudaStream_t st) {
   const long grid = (groups + GPB - 1) / GPB;
   const size_t smem = op_smem_bytes<R, Op>();
   if (smem > 40 * 1024) {
-    cudaError_t e = cudaFuncSetAttribute(k_sweeps2<R, Op>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    cudaError_t e = raise_smem_cap(reinterpret_cast<const void*>(k_sweeps2<R, Op>));
     if (e != cudaSuccess) return e;
   }
   k_sweeps2<R, Op><<<dim3((unsigned)grid, 2), 128, smem, st>>>(p);
@@ -61,7 +61,7 @@ cudaError_t launch_gsweep_t(const KParams& p, cudaStream_t st) {
   const long grid = ((long)p.B + GPB - 1) / GPB;
   const size_t smem = op_smem_bytes<R, Op>();
   if (smem > 40 * 1024) {
-    cudaError_t e = cudaFuncSetAttribute(k_gsweep<R, Op>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    cudaError_t e = raise_smem_cap(reinterpret_cast<const void*>(k_gsweep<R, Op>));
     if (e != cudaSuccess) return e;
   }
   k_gsweep<R, Op><<<dim3((unsigned)grid, p.obj == 0 ? 2 : 1), 128, smem, st>>>(p);

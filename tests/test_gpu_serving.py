@@ -78,3 +78,27 @@ def test_footprint_matches_plan_bytes(P):
     for w in (W.config("rotor41", Nt=2000, N=16), W.config("ising1024", Nt=500, N=8), _gp()):
         with P.Plan(w, precision="mixed") as pl:
             assert pl.info(3) == P.footprint(w, precision="mixed")
+
+
+def test_concurrent_blocked_chains_of_different_sizes(P):
+    """Plans whose chain kernels need different shared-memory sizes (blocked chains of d = 16, 41 and
+    64 at N = 64 and 128) run concurrently on 6 slots, many times over: every request completes and
+    equals its solve alone (the kernels' shared-memory caps are raised once, not per launch)."""
+    base = [
+        (W.config("spin16", Nt=640, N=64), "mixed", 2),
+        (W.config("rotor41", Nt=1280, N=128), "mixed", 2),
+        (W.random_dense(64, 56, T=1.0, Nt=256, N=64), "mixed", 2),
+        (W.random_dense(57, 57, T=1.0, Nt=256, N=64), "fp64", 2),
+    ]
+    mix = base * 6
+    with P.Server(slots=6, hbm_budget_bytes=16 << 30) as srv:
+        ids = [srv.submit(w, iters=it, precision=prec) for w, prec, it in mix]
+        got = [srv.result(i) for i in ids]
+    alone = []
+    for w, prec, it in base:
+        with P.Plan(w, precision=prec) as pl:
+            assert pl.info(7) > 1   # blocked chain
+            alone.append(pl.iterate(w.u0, it)[:2])
+    for k, (u, J, t) in enumerate(got):
+        ua, Ja = alone[k % len(base)]
+        assert np.array_equal(u, ua) and np.array_equal(J, Ja)
