@@ -315,7 +315,9 @@ struct OpTridiag {
       out.im[r] = xi;
     }
   }
-  // packed FP32 forms of rec and h1 (R = float)
+  // packed FP32 forms of rec and h1 (R = float).  DL = false leaves out the low part of the diagonal
+  // (for sweeps over one sub-interval, where its rounding does not accumulate).
+  template <bool DL = true>
   __device__ __forceinline__ void rec_p(const VecP<E>& in, const VecP<E>& sub, VecP<E>& out) const {
     float2 l, q;
     l.x = g_up<G>(in.z[E - 1].x);
@@ -328,7 +330,7 @@ struct OpTridiag {
       const float2 pn = r == E - 1 ? q : in.z[r + 1];
       const float2 ym = r == 0 ? yom2 : yo2[r - 1];
       float2 x = fma2(ym, m, fma2(yo2[r], pn, neg2(sub.z[r])));
-      x = fma2(al2[r], in.z[r], x);
+      if (DL) x = fma2(al2[r], in.z[r], x);
       if (HB) x = fma2(yb2[r], in.z[r], x);
       out.z[r] = fma2(ah2[r], in.z[r], x);
     }
@@ -841,11 +843,14 @@ __device__ __forceinline__ void cheb_step_pr(VecP<E>& v, VecP<E>& lo, const Op& 
   }
 }
 
-// cheb_step on packed FP32 states (the same series, sub-steps and compensation).  Odd terms multiply
+// cheb_step on packed FP32 states (the same series, sub-steps and compensation).  LOC = false drops
+// the low parts of a_k for k >= 2 and DL = false that of the diagonal: both roundings repeat at every
+// step, so the global sweeps (tens of thousands of steps) keep them, while the sweeps over one
+// sub-interval (the sub-problems: ~10^2 steps) may leave them out at ~10^-8 relative cost.  Odd terms multiply
 // (-i)^k (forward) or (+i)^k (adjoint): they are summed into a separate packed accumulator o with
 // their signed real coefficients and folded in once per sub-step, acc += (o.im, -o.re), so the
 // inner loop has no re/im swaps.
-template <bool ADJ, bool COMP, int E, class Op>
+template <bool ADJ, bool COMP, bool LOC = true, bool DL = true, int E, class Op>
 __device__ __forceinline__ void cheb_step_p(VecP<E>& v, VecP<E>& lo, const Op& op, const Cheb<float>& ch, int K,
                                             int Sw) {
   for (int s = 0; s < Sw; ++s) {
@@ -853,7 +858,7 @@ __device__ __forceinline__ void cheb_step_p(VecP<E>& v, VecP<E>& lo, const Op& o
     VecP<E> t0 = v, t1, acc, o, zero;
 #pragma unroll
     for (int r = 0; r < E; ++r) zero.z[r] = make_float2(0.f, 0.f);
-    op.rec_p(t0, zero, t1);   // t1 = 2 Y t0
+    op.template rec_p<DL>(t0, zero, t1);   // t1 = 2 Y t0
 #pragma unroll
     for (int r = 0; r < E; ++r) t1.z[r] = mul2(t1.z[r], bc2(0.5f));
     const float sg = ADJ ? -1.f : 1.f;
@@ -864,15 +869,15 @@ __device__ __forceinline__ void cheb_step_p(VecP<E>& v, VecP<E>& lo, const Op& o
       o.z[r] = fma2(bc2(sg * ch.a1h), t1.z[r], mul2(bc2(sg * ch.a1l), t1.z[r]));
     }
     for (int k = 2; k < K; k += 2) {
-      op.rec_p(t1, t0, t0);   // t0 <- T_k
+      op.template rec_p<DL>(t1, t0, t0);   // t0 <- T_k
       const float2 ce = bc2(ch.cf[k]), cel = bc2(ch.cl[k]);
 #pragma unroll
-      for (int r = 0; r < E; ++r) acc.z[r] = fma2(ce, t0.z[r], fma2(cel, t0.z[r], acc.z[r]));
+      for (int r = 0; r < E; ++r) acc.z[r] = fma2(ce, t0.z[r], LOC ? fma2(cel, t0.z[r], acc.z[r]) : acc.z[r]);
       if (k + 1 < K) {
-        op.rec_p(t0, t1, t1);   // t1 <- T_{k+1}
+        op.template rec_p<DL>(t0, t1, t1);   // t1 <- T_{k+1}
         const float2 co = bc2(sg * ch.cf[k + 1]), col = bc2(sg * ch.cl[k + 1]);
 #pragma unroll
-        for (int r = 0; r < E; ++r) o.z[r] = fma2(co, t1.z[r], fma2(col, t1.z[r], o.z[r]));
+        for (int r = 0; r < E; ++r) o.z[r] = fma2(co, t1.z[r], LOC ? fma2(col, t1.z[r], o.z[r]) : o.z[r]);
       }
     }
 #pragma unroll

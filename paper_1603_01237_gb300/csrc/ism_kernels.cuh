@@ -286,7 +286,7 @@ __global__ void __launch_bounds__(128) k_subinterval(KParams p) {
       }
       VecP<E> w = pv, wl = pl;
       op.set_u(uj, ch, lg);
-      cheb_step_p<false, true>(w, wl, op, ch, Kw, Sw);
+      cheb_step_p<false, true, false, true>(w, wl, op, ch, Kw, Sw);
       if (act) { pv = w; pl = wl; }
     }
     VecP<E> he;
@@ -399,7 +399,7 @@ __global__ void __launch_bounds__(128) k_subinterval(KParams p) {
       }
       VecP<E> w = pd;
       op.set_u(uj, ch, lg);
-      cheb_step_p<true, false>(w, dummy, op, ch, Kw, Sw);
+      cheb_step_p<true, false, false, false>(w, dummy, op, ch, Kw, Sw);
       if (act) pd = w;
       float zr, zi;
       zdotp(pd, hc, zr, zi);
@@ -624,7 +624,7 @@ __global__ void __launch_bounds__(128) k_sweeps2(KParams p) {
         if (act) putp(s, hv);
         VecP<E> w = pv, wl = pl;
         op.set_u(uj, ch, lg);
-        cheb_step_p<false, true>(w, wl, op, ch, Kw, Sw);
+        cheb_step_p<false, true, false, true>(w, wl, op, ch, Kw, Sw);
         if (act) { pv = w; pl = wl; }
       }
       VecP<E> hv;
@@ -643,7 +643,7 @@ __global__ void __launch_bounds__(128) k_sweeps2(KParams p) {
         }
         VecP<E> w = pv, wl = pl;
         op.set_u(uj, ch, lg);
-        cheb_step_p<true, true>(w, wl, op, ch, Kw, Sw);
+        cheb_step_p<true, true, false, false>(w, wl, op, ch, Kw, Sw);
         if (act) { pv = w; pl = wl; putp(s, pv); }
       }
     }
