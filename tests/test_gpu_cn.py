@@ -186,3 +186,20 @@ def test_cn_controls_beyond_the_solve_are_rejected(P):
         assert ei.value.status == 6
         J, _ = pl.evaluate(w.u0)
     assert abs(J[0] - C.objective(w, w.u0)[0]) <= 1e-12
+
+
+@pytest.mark.parametrize("step1", [1, 2])
+@pytest.mark.parametrize("N", [1, 24])
+def test_cn_degenerate_partitions(P, N, step1):
+    """N = 1 (no decomposition) and N = Nt (one step per sub-interval)."""
+    w = _strong(12, 73, T=0.5, Nt=24, N=N)
+    phi_o = C.intermediate_states(w, w.u0)
+    g_o, Jn_o = C.subinterval_all(w, phi_o, w.u0)
+    u_o, J_o, _, _ = C.ism_solve(w, w.u0, 2, 0.3)
+    with P.Plan(w, precision="fp64", scheme="crank_nicolson", step1=step1, rho=0.3) as pl:
+        phi = pl.intermediate_states(w.u0)[0]
+        g, Jn = pl.subinterval_grad(phi_o, w.u0)
+        u, J, _ = pl.iterate(w.u0, 2)
+    assert np.max(np.abs(phi - phi_o)) <= PHI
+    assert rel_l2(g[0], g_o) <= GRAD and np.max(np.abs(Jn[0] - Jn_o)) <= 1e-12
+    assert np.max(np.abs(J[0] - J_o)) <= 1e-9 and rel_l2(u[0] - w.u0, u_o - w.u0) <= 1e-9

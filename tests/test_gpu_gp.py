@@ -107,3 +107,16 @@ def test_double_well_full_size_mixed(P):
     assert np.max(np.abs(J[0] - J_o)) <= 1e-5, np.max(np.abs(J[0] - J_o))
     assert rel(g[0], g_o) <= 1e-4, rel(g[0], g_o)
     assert np.max(np.abs(u[0] - u_o)) <= 1e-4 * np.max(np.abs(u_o))
+
+
+@pytest.mark.parametrize("N", [1, 40])
+def test_double_well_degenerate_partitions(P, N):
+    """N = 1 and N = Nt for the double well (FP64)."""
+    w = _dw(64, 40, N, 0.5)
+    ps_o, ch_o = G.intermediate_pairs(w, w.u0)
+    u_o, J_o, _, _ = G.ism_solve(w, w.u0, 2, 0.05)
+    with P.Plan(w, precision="fp64", rho=0.05) as pl:
+        phi = pl.intermediate_states(w.u0)[0]
+        u, J, _ = pl.iterate(w.u0, 2)
+    assert np.max(np.abs(phi[0] - ps_o)) <= 1e-11 and np.max(np.abs(phi[1] - ch_o)) <= 1e-11
+    assert np.max(np.abs(J[0] - J_o)) <= 1e-10 and np.max(np.abs(u[0] - u_o)) <= 1e-10

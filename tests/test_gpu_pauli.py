@@ -102,3 +102,20 @@ def test_spin5_at_the_paper_size_against_the_density_matrix_oracle(P):
     u1_o = w.u0 + rho * g_o / w.tau
     assert rel(u1[0] - w.u0, u1_o - w.u0) <= 1e-4
     assert abs(Jh[0, 1] - M.dm_objective(w, u1_o)) <= 1e-5
+
+
+@pytest.mark.parametrize("prec", ["fp64", "mixed"])
+def test_pauli_most_controls_and_one_step_sub_intervals(P, prec):
+    """32 controls (the most a plan takes) on d = 128, N = Nt (one step per sub-interval)."""
+    w = W.random_pauli(7, 32, 34, T=0.3, Nt=20, N=20, u_amp=0.3)
+    phi_o = M.intermediate_states(w, w.u0)
+    g_o, _ = M.subinterval_all(w, phi_o, w.u0)
+    u_o, J_o, _, _ = M.ism_solve(w, w.u0, 2, 0.3)
+    with P.Plan(w, precision=prec, rho=0.3) as pl:
+        phi = pl.intermediate_states(w.u0)[0]
+        g, _ = pl.subinterval_grad(phi_o, w.u0)
+        u, J, _ = pl.iterate(w.u0, 2)
+    assert np.max(np.abs(phi - phi_o)) <= TOL[prec][0]
+    assert rel(g[0], g_o) <= TOL[prec][1]
+    assert np.max(np.abs(J[0] - J_o)) <= (1e-9 if prec == "fp64" else 1e-5)
+    assert rel(u[0] - w.u0, u_o - w.u0) <= (1e-9 if prec == "fp64" else 1e-4)
