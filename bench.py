@@ -169,8 +169,8 @@ def kernel_source_hash(files=KERNEL_SOURCES) -> str:
 # problems, from a one-pass ncu capture of the default step (4864 rotor problems: k_gsweep in the wide
 # lane layout); reported only while the kernel sources hash to the captured build.
 TRAFFIC_PER_PROBLEM = {
-    ("k_gsweep", "rotor41"): {"bytes_per_problem": (1169409536 + 789165568) / 4864, "source_hash": "b76aad182f545798"},
-    ("k_subinterval", "rotor41"): {"bytes_per_problem": (41560729344 + 41613115648) / 4864, "source_hash": "b76aad182f545798"},
+    ("k_gsweep", "rotor41"): {"bytes_per_problem": (1169261312 + 789064960) / 4864, "source_hash": "6437dec4c97039bf"},
+    ("k_subinterval", "rotor41"): {"bytes_per_problem": (42362061824 + 41639220224) / 4864, "source_hash": "6437dec4c97039bf"},
 }
 
 
