@@ -552,8 +552,8 @@ int plan_build(const ism_problem* prob, const ism_options* opt, void* cuda_strea
   if (opt->scheme != ISM_SCHEME_CHEBYSHEV && opt->scheme != ISM_SCHEME_CRANK_NICOLSON)
     return fail(ISM_EINVAL, "scheme must be ISM_SCHEME_CHEBYSHEV or ISM_SCHEME_CRANK_NICOLSON");
   if (opt->scheme == ISM_SCHEME_CRANK_NICOLSON &&
-      (p.kind == ISM_H_GRID_GP || p.kind == ISM_H_GRID_GP_DOUBLE_WELL || p.d > 64 || opt->precision != ISM_FP64))
-    return fail(ISM_EUNSUPPORTED, "the Crank-Nicolson scheme is built in FP64 for the tridiagonal, dense and bit-flip kinds "
+      (p.kind == ISM_H_GRID_GP || p.kind == ISM_H_GRID_GP_DOUBLE_WELL || p.kind == ISM_H_PAULI || p.d > 64))
+    return fail(ISM_EUNSUPPORTED, "the Crank-Nicolson scheme is built for the tridiagonal, dense and bit-flip kinds "
                                   "with d <= 64");
 
   ism_plan_s* P = new (std::nothrow) ism_plan_s();

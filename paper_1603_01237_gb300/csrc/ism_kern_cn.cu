@@ -1,14 +1,15 @@
-// The Crank-Nicolson time step of Sec. 3 (FP64, d <= 64) for the tridiagonal, bit-flip and dense
-// kinds: the lane layouts of the Chebyshev builds; the sub-problems always run the one-group sweep
-// (k_subinterval).
+// The Crank-Nicolson time step of Sec. 3 (d <= 64) for the tridiagonal, bit-flip and dense kinds, in
+// FP64 and in FP32 propagation (mixed mode: the Cayley step is unitary by construction, so its FP32
+// rounding does not build up a norm or phase drift the way a truncated series would; states at the
+// partition, overlaps and the update stay FP64): the lane layouts of the Chebyshev builds; the
+// sub-problems always run the one-group sweep (k_subinterval).
 #include "ism.h"
 #include "ism_launch_impl.cuh"
 
 namespace ism {
 
-template <bool HB>
+template <typename R, bool HB>
 static bool pick_cn(int d, KernelSet* ks) {
-  using R = double;
   const int E = (d + 15) / 16;
   switch (E) {
     case 1: fill_set<R, OpTridiagCN<R, 8, 2, HB>, OpTridiagCN<R, 16, 1, HB>, false>(ks); return true;
@@ -19,8 +20,8 @@ static bool pick_cn(int d, KernelSet* ks) {
   }
 }
 
+template <typename R>
 static bool pick_bitflip_cn(int d, KernelSet* ks) {
-  using R = double;
   switch (d) {
     case 2: fill_set<R, OpBitflipCN<R, 2, 1>, OpBitflipCN<R, 2, 1>, false>(ks); return true;
     case 4: fill_set<R, OpBitflipCN<R, 4, 1>, OpBitflipCN<R, 4, 1>, false>(ks); return true;
@@ -32,8 +33,8 @@ static bool pick_bitflip_cn(int d, KernelSet* ks) {
   }
 }
 
+template <typename R>
 static bool pick_dense_cn(int d, KernelSet* ks) {
-  using R = double;
   switch ((d + 15) / 16) {
     case 1: fill_set<R, OpDenseCN<R, 16, 1>, OpDenseCN<R, 16, 1>, false>(ks); return true;
     case 2: fill_set<R, OpDenseCN<R, 16, 2>, OpDenseCN<R, 16, 2>, false>(ks); return true;
@@ -43,14 +44,19 @@ static bool pick_dense_cn(int d, KernelSet* ks) {
   }
 }
 
-bool kernels_cn(int prec, int kind, int d, bool h1diag, KernelSet* ks) {
-  if (prec != 0 || d < 1 || d > 64) return false;
+template <typename R>
+static bool pick_kind(int kind, int d, bool h1diag, KernelSet* ks) {
   switch (kind) {
-    case ISM_H_TRIDIAG: return h1diag ? pick_cn<true>(d, ks) : pick_cn<false>(d, ks);
-    case ISM_H_BITFLIP: return pick_bitflip_cn(d, ks);
-    case ISM_H_DENSE: return pick_dense_cn(d, ks);
+    case ISM_H_TRIDIAG: return h1diag ? pick_cn<R, true>(d, ks) : pick_cn<R, false>(d, ks);
+    case ISM_H_BITFLIP: return pick_bitflip_cn<R>(d, ks);
+    case ISM_H_DENSE: return pick_dense_cn<R>(d, ks);
     default: return false;
   }
+}
+
+bool kernels_cn(int prec, int kind, int d, bool h1diag, KernelSet* ks) {
+  if (d < 1 || d > 64) return false;
+  return prec == 0 ? pick_kind<double>(kind, d, h1diag, ks) : pick_kind<float>(kind, d, h1diag, ks);
 }
 
 }  // namespace ism

@@ -41,7 +41,7 @@ bool kernels_bitflip(int prec, int d, KernelSet* ks);
 bool kernels_dense(int prec, int d, KernelSet* ks);
 bool kernels_large_bitflip(int prec, int d, KernelSet* ks);   // d = 128, 256, 512, 1024
 bool kernels_pauli(int prec, int d, KernelSet* ks);   // several controls, Pauli structure, d = 128..1024
-// Crank-Nicolson step (FP64 only): tridiagonal, bit-flip (d <= 64) and dense kinds
+// Crank-Nicolson step (FP64 or FP32 propagation): tridiagonal, bit-flip (d <= 64) and dense kinds
 bool kernels_cn(int prec, int kind, int d, bool h1diag, KernelSet* ks);
 cudaError_t launch_chain(int prec, const ChainParams& p, size_t smem, cudaStream_t st);   // k_chain + k_phi
 cudaError_t launch_phi(int prec, const ChainParams& p, cudaStream_t st);                   // k_phi alone

@@ -203,3 +203,46 @@ def test_cn_degenerate_partitions(P, N, step1):
     assert np.max(np.abs(phi - phi_o)) <= PHI
     assert rel_l2(g[0], g_o) <= GRAD and np.max(np.abs(Jn[0] - Jn_o)) <= 1e-12
     assert np.max(np.abs(J[0] - J_o)) <= 1e-9 and rel_l2(u[0] - w.u0, u_o - w.u0) <= 1e-9
+
+
+# ---------------------------------------------------------------- mixed precision (FP32 propagation)
+MIXED = [
+    ("rotor41", W.config("rotor41", Nt=1000, N=16, precision="fp64")),
+    ("strong12", _strong(12, 71, T=2.0, Nt=120, N=7)),
+    ("strong33-h1diag-obs", _strong(33, 72, T=2.0, Nt=150, N=9, objective="observable", h1diag=True)),
+    ("spin16", W.config("spin16", Nt=400, N=4)),
+    ("dense41-obs", W.random_dense(41, 62, T=2.0, Nt=150, N=9, objective="observable")),
+]
+
+
+@pytest.mark.parametrize("step1", [1, 2])
+@pytest.mark.parametrize("name,w", MIXED, ids=[c[0] for c in MIXED])
+def test_cn_mixed_states_gradient_iterate(P, name, w, step1):
+    """FP32 propagation with FP64 states at the partition, overlaps and update: the mixed tolerances
+    (states 2e-5, gradient relative 1e-4, J 1e-5)."""
+    phi_o = C.intermediate_states(w, w.u0)
+    g_o = C.global_gradient(w, w.u0)
+    u_o, J_o, _, _ = C.ism_solve(w, w.u0, 2, w.rho)
+    with P.Plan(w, precision="mixed", scheme="crank_nicolson", step1=step1) as pl:
+        assert pl.info(8) == 1
+        phi = pl.intermediate_states(w.u0)[0]
+        g, _ = pl.gradient(w.u0)
+        u, J, _ = pl.iterate(w.u0, 2)
+    assert np.max(np.abs(phi - phi_o)) <= 2e-5, np.max(np.abs(phi - phi_o))
+    assert rel_l2(g[0], g_o) <= 1e-4, rel_l2(g[0], g_o)
+    assert np.max(np.abs(J[0] - J_o)) <= 1e-5, np.max(np.abs(J[0] - J_o))
+    assert rel_l2(u[0] - w.u0, u_o - w.u0) <= 1e-4
+
+
+def test_cn_mixed_rotor_full_size(P):
+    """The rotor at the benchmark's size (Nt = 20000, N = 128) with the FP32 Crank-Nicolson step: J and
+    the gradient at u0 against the FP64 Crank-Nicolson oracle, batched direct sweeps and one problem."""
+    w = W.config("rotor41", precision="fp64")
+    J_o, F_o = C.objective(w, w.u0)
+    g_o = C.global_gradient(w, w.u0)
+    for batch in (1, 96):
+        with P.Plan(w, precision="mixed", scheme="crank_nicolson", batch=batch) as pl:
+            J, F = pl.evaluate(np.broadcast_to(w.u0, (batch, w.Nt)))
+            g, _ = pl.gradient(np.broadcast_to(w.u0, (batch, w.Nt)))
+        assert np.max(np.abs(J - J_o)) <= 1e-5 and np.max(np.abs(F - F_o)) <= 1e-5
+        assert max(rel_l2(g[b], g_o) for b in range(batch)) <= 1e-4
