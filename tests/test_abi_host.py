@@ -149,8 +149,8 @@ def test_footprint_needs_no_gpu_and_scales_with_the_problem(lib):
 
 
 def test_crank_nicolson_option_validated_on_the_host(lib):
-    """The Crank-Nicolson scheme is accepted in FP64 for the tridiagonal, dense and bit-flip kinds with
-    d <= 64; its plans hold no second trajectory (the sub-problems run in one group)."""
+    """The Crank-Nicolson scheme is accepted in both precisions for the tridiagonal, dense and bit-flip
+    kinds with d <= 64; its plans hold no second trajectory (the sub-problems run in one group)."""
     import workloads as W
     from paper_1603_01237_gb300 import abi
 
@@ -158,10 +158,7 @@ def test_crank_nicolson_option_validated_on_the_host(lib):
     f_cn = abi.footprint(w, precision="fp64", scheme="crank_nicolson", step1=1)
     f_ch = abi.footprint(w, precision="fp64", step1=1)
     assert 0 < f_cn < f_ch
-    for kw in ({"precision": "mixed"},):
-        with pytest.raises(abi.IsmError) as ei:
-            abi.footprint(w, scheme="crank_nicolson", **kw)
-        assert ei.value.status == abi.ISM_EUNSUPPORTED
+    assert abi.footprint(w, precision="mixed", scheme="crank_nicolson") > 0   # FP32 Cayley steps
     assert abi.footprint(W.random_dense(5, 3, T=1.0, Nt=50, N=2), scheme="crank_nicolson") > 0
     assert abi.footprint(W.config("spin16", Nt=100), scheme="crank_nicolson") > 0
     for big in (W.config("ising1024", Nt=200, N=4), W.gp_bec(n=64, Nt=20, N=2, steps=10)):
