@@ -46,7 +46,8 @@ class IsmOptions(C.Structure):
 
 class IsmStats(C.Structure):
     _fields_ = [("ms", C.c_double * 3), ("launches", C.c_longlong * 3), ("y_apps", C.c_ulonglong * 2),
-                ("terms", C.c_ulonglong * 2), ("substeps", C.c_ulonglong * 2), ("kernels", C.c_longlong)]
+                ("terms", C.c_ulonglong * 2), ("substeps", C.c_ulonglong * 2), ("kernels", C.c_longlong),
+                ("norm_drift", C.c_double)]
 
 
 class IsmServerOptions(C.Structure):
@@ -293,7 +294,8 @@ class Plan:
         st = IsmStats()
         _check(load().ism_get_stats(self.handle, C.byref(st), int(bool(reset))))
         return {"ms": list(st.ms), "launches": list(st.launches), "y_apps": list(st.y_apps),
-                "terms": list(st.terms), "substeps": list(st.substeps), "kernels": int(st.kernels)}
+                "terms": list(st.terms), "substeps": list(st.substeps), "kernels": int(st.kernels),
+                "norm_drift": float(st.norm_drift)}
 
     def info(self, key: int) -> int:
         return int(load().ism_plan_info(self.handle, key))

@@ -121,7 +121,7 @@ struct ism_plan_s {
   double* derrhist = nullptr;
   long hist_cap = 0;
   int* dstatus = nullptr;
-  unsigned long long* dcount = nullptr;   // [6]: assembly (3), sub-interval (3)
+  unsigned long long* dcount = nullptr;   // [7]: assembly (3), sub-interval (3), norm drift (double bits)
   bool profiling = false;
   struct Ev { int phase; cudaEvent_t a, b; };
   std::vector<Ev> pending;                // events recorded in the current call
@@ -468,6 +468,7 @@ int run_states(ism_plan_s* P, const double* u, double* Jhist, int hist_stride, i
   c.J = P->dJ; c.F = P->dF; c.Jhist = Jhist; c.hist_stride = hist_stride; c.hist_k = hist_k;
   c.status = P->dstatus; c.max_spin = P->max_spin; c.stages = P->chain_stages; c.tile_stride = P->tst;
   c.Mc = P->dMc; c.Nc = P->Nc; c.sblk = P->sblk;
+  c.drift = P->dcount + 6;
   if (P->ks.large || P->direct) {
     c.src64 = 1;
     ISM_CUDA_TRY(timed(P, 1, 1, [&] { return ism::launch_phi(P->prec, c, P->st); }));
@@ -598,7 +599,7 @@ int plan_build(const ism_problem* prob, const ism_options* opt, void* cuda_strea
     TRY_GP(P->dJ, B);
     TRY_GP(P->dF, B);
     TRY_GP(P->dstatus, 1);
-    TRY_GP(P->dcount, 6);
+    TRY_GP(P->dcount, 7);
 #undef TRY_GP
     if (dry) {
       *bytes_out = P->bytes;
@@ -609,7 +610,7 @@ int plan_build(const ism_problem* prob, const ism_options* opt, void* cuda_strea
     if (e == cudaSuccess) e = cudaMemcpyAsync(P->dpsi_i, p.psi_i, 2 * sizeof(double) * d, cudaMemcpyHostToDevice, P->st);
     if (e == cudaSuccess) e = cudaMemcpyAsync(P->dpsi_f, p.psi_f, 2 * sizeof(double) * d, cudaMemcpyHostToDevice, P->st);
     if (e == cudaSuccess) e = cudaMemsetAsync(P->dstatus, 0, sizeof(int), P->st);
-    if (e == cudaSuccess) e = cudaMemsetAsync(P->dcount, 0, 6 * sizeof(unsigned long long), P->st);
+    if (e == cudaSuccess) e = cudaMemsetAsync(P->dcount, 0, 7 * sizeof(unsigned long long), P->st);
     if (e == cudaSuccess) e = cudaStreamSynchronize(P->st);   // the host arrays above are local
     if (e != cudaSuccess) {
       free_all(P);
@@ -758,7 +759,7 @@ int plan_build(const ism_problem* prob, const ism_options* opt, void* cuda_strea
   TRY_ALLOC(P->dJ, B);
   TRY_ALLOC(P->dF, B);
   TRY_ALLOC(P->dstatus, 1);
-  TRY_ALLOC(P->dcount, 6);
+  TRY_ALLOC(P->dcount, 7);
 #undef TRY_ALLOC
   if (dry) {
     *bytes_out = P->bytes;
@@ -804,7 +805,7 @@ int plan_build(const ism_problem* prob, const ism_options* opt, void* cuda_strea
   else if (e == cudaSuccess) e = cudaMemsetAsync(P->dpsi_f, 0, 2 * sizeof(double) * d, P->st);
   if (p.objective == ISM_OBJ_OBSERVABLE) h2d(P->dO, p.O, sizeof(double) * d * d);
   if (e == cudaSuccess) e = cudaMemsetAsync(P->dstatus, 0, sizeof(int), P->st);
-  if (e == cudaSuccess) e = cudaMemsetAsync(P->dcount, 0, 6 * sizeof(unsigned long long), P->st);
+  if (e == cudaSuccess) e = cudaMemsetAsync(P->dcount, 0, 7 * sizeof(unsigned long long), P->st);
   if (e == cudaSuccess) e = cudaStreamSynchronize(P->st);   // the host arrays uploaded above are local
   if (e != cudaSuccess) {
     free_all(P);
@@ -876,11 +877,12 @@ int ism_get_stats(ism_plan_t P, ism_stats* out, int reset) {
   ISM_CUDA_TRY(cudaSetDevice(P->dev));
   ISM_CUDA_TRY(cudaStreamSynchronize(P->st));
   collect_events(P);
-  unsigned long long c[6];
+  unsigned long long c[7];   // work counters of two phases, then the norm drift's bits
   ISM_CUDA_TRY(cudaMemcpy(c, P->dcount, sizeof(c), cudaMemcpyDeviceToHost));
   for (int i = 0; i < 3; ++i) { out->ms[i] = P->ms[i]; out->launches[i] = P->launches[i]; }
   out->kernels = P->kernels;
   for (int k = 0; k < 2; ++k) { out->y_apps[k] = c[3 * k]; out->terms[k] = c[3 * k + 1]; out->substeps[k] = c[3 * k + 2]; }
+  std::memcpy(&out->norm_drift, &c[6], sizeof(double));
   if (reset) {
     for (int i = 0; i < 3; ++i) { P->ms[i] = 0; P->launches[i] = 0; }
     P->kernels = 0;

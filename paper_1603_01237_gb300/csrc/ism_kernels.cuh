@@ -90,6 +90,7 @@ struct ChainParams {
   // blocked chain: Nc coarse steps over the products of sblk consecutive tiles (0: plain chain)
   void* Mc;               // [B][Nc] tiles: P_k = M_{k sblk + len_k - 1} ... M_{k sblk}
   int Nc, sblk;
+  unsigned long long* drift;   // largest relative norm drift seen by k_phi (double bits), or null
 };
 
 template <typename R> __device__ __forceinline__ R ldu_ro(const double* u, long i) { return (R)__ldg(u + i); }
@@ -1288,36 +1289,84 @@ __global__ void __launch_bounds__(128) k_phi(ChainParams p) {
   double2* chin = p.chin + (long)b * (N + 1) * d;
   const R2* sps = reinterpret_cast<const R2*>(p.stage) + (long)b * 2 * (N + 1) * d;
   const R2* sch = sps + (long)(N + 1) * d;
+  auto load_ps = [&](int m, int e) -> double2 {
+    if (m == 0) return p.psi_i[e];
+    if (p.src64) return psin[(long)m * d + e];
+    const R2 z = sps[(long)m * d + e];
+    return make_double2((double)z.x, (double)z.y);
+  };
+  auto load_cs = [&](int m, int e) -> double2 {
+    if (m == N || p.src64) return chin[(long)m * d + e];
+    const R2 z = sch[(long)m * d + e];
+    return make_double2((double)z.x, (double)z.y);
+  };
+  // Norm renormalisation in FP64: the propagation is unitary, so psi(t_n) keeps the norm of psi_i and
+  // chi(t_n) that of chi(T); rescaling them back removes the norm drift of FP32 propagation (a no-op
+  // in exact arithmetic) and the largest relative drift is recorded.
+  auto norms = [&](int m, double& sp, double& sc) {
+    double a = 0.0, a0 = 0.0, c = 0.0, cT = 0.0;
+    for (int e = t; e < d; e += blockDim.x) {
+      const double2 x = load_ps(m, e), x0 = p.psi_i[e], y = load_cs(m, e), yT = chin[(long)N * d + e];
+      a = fma(x.x, x.x, fma(x.y, x.y, a));
+      a0 = fma(x0.x, x0.x, fma(x0.y, x0.y, a0));
+      c = fma(y.x, y.x, fma(y.y, y.y, c));
+      cT = fma(yT.x, yT.x, fma(yT.y, yT.y, cT));
+    }
+    a = block_sum(a, red);
+    a0 = block_sum(a0, red);
+    c = block_sum(c, red);
+    cT = block_sum(cT, red);
+    sp = (a > 0.0 && a0 > 0.0) ? sqrt(a0 / a) : 1.0;
+    sc = (c > 0.0 && cT > 0.0) ? sqrt(cT / c) : 1.0;
+    if (t == 0 && p.drift && a0 > 0.0 && cT > 0.0) {
+      const double dr = fmax(fabs(a / a0 - 1.0), fabs(c / cT - 1.0));
+      if (dr >= 0.0) atomicMax(p.drift, __double_as_longlong(dr));   // ordered as integers when >= 0
+    }
+  };
   if (n <= N) {
     const double2 w = p.ab[n];
     double2* phi = p.phi + ((long)b * (N + 1) + n) * d;
+    double sp, sc;
+    norms(n, sp, sc);
+    if (n == 0) sp = 1.0;   // psi_i and chi(T) are the references
+    if (n == N) sc = 1.0;
     for (int e = t; e < d; e += blockDim.x) {
-      double2 ps, cs;
-      if (n == 0) ps = p.psi_i[e];
-      else if (p.src64) ps = psin[(long)n * d + e];
-      else { const R2 z = sps[(long)n * d + e]; ps = make_double2((double)z.x, (double)z.y); }
-      if (n == N || p.src64) cs = chin[(long)n * d + e];
-      else { const R2 z = sch[(long)n * d + e]; cs = make_double2((double)z.x, (double)z.y); }
-      if (!p.src64) {
-        psin[(long)n * d + e] = ps;
-        if (n < N) chin[(long)n * d + e] = cs;
-      }
+      double2 ps = load_ps(n, e), cs = load_cs(n, e);
+      ps.x *= sp; ps.y *= sp;
+      cs.x *= sc; cs.y *= sc;
+      if (n > 0) psin[(long)n * d + e] = ps;
+      if (n < N) chin[(long)n * d + e] = cs;
       phi[e] = n == 0 ? ps : (n == N ? cs : make_double2(w.x * ps.x + w.y * cs.x, w.x * ps.y + w.y * cs.y));
     }
     return;
   }
-  // J and F: <psi(T)|chi(T)> is the overlap with psi_f or <psi|O|psi>
+  // J and F: <psi(T)|chi(T)> is the overlap with psi_f or <psi|O|psi>, with psi(T) renormalised as
+  // block N renormalises it (the scale is applied to the sum: block N may be rewriting psi(T))
   double ovr = 0.0, ovi = 0.0;
   for (int e = t; e < d; e += blockDim.x) {
-    double ax, ay;
-    if (p.src64) { const double2 z = psin[(long)N * d + e]; ax = z.x; ay = z.y; }
-    else { const R2 z = sps[(long)N * d + e]; ax = (double)z.x; ay = (double)z.y; }
+    const double2 z = load_ps(N, e);
     const double2 c = chin[(long)N * d + e];
-    ovr += ax * c.x + ay * c.y;
-    ovi += ax * c.y - ay * c.x;
+    ovr += z.x * c.x + z.y * c.y;
+    ovi += z.x * c.y - z.y * c.x;
   }
   ovr = block_sum(ovr, red);
   ovi = block_sum(ovi, red);
+  {
+    double a = 0.0, a0 = 0.0;
+    for (int e = t; e < d; e += blockDim.x) {
+      const double2 x = load_ps(N, e), x0 = p.psi_i[e];
+      a = fma(x.x, x.x, fma(x.y, x.y, a));
+      a0 = fma(x0.x, x0.x, fma(x0.y, x0.y, a0));
+    }
+    a = block_sum(a, red);
+    a0 = block_sum(a0, red);
+    // overlap objective: chi(T) = psi_f, linear in psi(T); observable: chi(T) = O psi(T) was formed from
+    // the unscaled psi(T), so <psi|O|psi> takes the scale twice
+    const double s = (a > 0.0 && a0 > 0.0) ? sqrt(a0 / a) : 1.0;
+    const double sj = p.obj == 0 ? s : s * s;
+    ovr *= sj;
+    ovi *= sj;
+  }
   double pen = 0.0;
   if (p.pen)
     for (int n2 = t; n2 < N; n2 += blockDim.x) pen += p.pen[(long)b * N + n2];
