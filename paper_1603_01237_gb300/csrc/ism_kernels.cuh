@@ -1329,19 +1329,21 @@ __global__ void __launch_bounds__(128) k_phi(ChainParams p) {
     double sp, sc;
     norms(n, sp, sc);
     if (n == 0) sp = 1.0;   // psi_i and chi(T) are the references
-    if (n == N) sc = 1.0;
+    // psi(T) stays as propagated in psin (the J block below reads it concurrently and applies the
+    // scale to its sums instead; chi(T) = O psi(T) was formed from it)
+    if (n == N) { sc = 1.0; sp = 1.0; }
     for (int e = t; e < d; e += blockDim.x) {
       double2 ps = load_ps(n, e), cs = load_cs(n, e);
       ps.x *= sp; ps.y *= sp;
       cs.x *= sc; cs.y *= sc;
-      if (n > 0) psin[(long)n * d + e] = ps;
+      psin[(long)n * d + e] = ps;   // psi(t_0) = psi_i too: the chain path has not written it
       if (n < N) chin[(long)n * d + e] = cs;
       phi[e] = n == 0 ? ps : (n == N ? cs : make_double2(w.x * ps.x + w.y * cs.x, w.x * ps.y + w.y * cs.y));
     }
     return;
   }
-  // J and F: <psi(T)|chi(T)> is the overlap with psi_f or <psi|O|psi>, with psi(T) renormalised as
-  // block N renormalises it (the scale is applied to the sum: block N may be rewriting psi(T))
+  // J and F: <psi(T)|chi(T)> is the overlap with psi_f or <psi|O|psi>, with psi(T) renormalised (the
+  // scale is applied to the sums)
   double ovr = 0.0, ovi = 0.0;
   for (int e = t; e < d; e += blockDim.x) {
     const double2 z = load_ps(N, e);

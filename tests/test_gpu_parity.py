@@ -350,10 +350,11 @@ def test_direct_sweeps_wide_layout_for_large_batches(P):
 def test_norm_drift_is_recorded_and_removed(P):
     """psi(t_n), chi(t_n) are renormalised in FP64 to the norms of psi_i and chi(T) (a no-op in exact
     arithmetic); the largest drift found is reported: rounding-level in FP64, small but nonzero for
-    FP32 propagation.  The renormalised states give J within the usual bounds."""
+    FP32 propagation (~1e-5 in norm^2 after the FP32 chain of 16 assembled propagators, less for
+    the compensated direct sweeps).  The renormalised states give J within the usual bounds."""
     w = W.config("rotor41", Nt=2000, N=16)
     J_o, _ = O.objective(w, w.u0)
-    for prec, lo, hi, tj in (("fp64", 0.0, 1e-12, 1e-9), ("mixed", 1e-12, 1e-5, 1e-5)):
+    for prec, lo, hi, tj in (("fp64", 0.0, 1e-12, 1e-9), ("mixed", 1e-12, 1e-4, 1e-5)):
         for step1 in (1, 2):
             with P.Plan(w, precision=prec, step1=step1) as pl:
                 pl.ism_get_stats(reset=True)
