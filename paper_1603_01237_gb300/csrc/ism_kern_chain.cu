@@ -79,14 +79,14 @@ cudaError_t launch_chain(int prec, const ChainParams& p, size_t smem, cudaStream
     e = prec == 0 ? fill_d<double>(p, st) : fill_d<float>(p, st);
     if (e != cudaSuccess) return e;
   }
-  if (prec == 0) k_phi<double><<<dim3(p.N + 2, p.B), 128, 0, st>>>(p);
-  else k_phi<float><<<dim3(p.N + 2, p.B), 128, 0, st>>>(p);
+  if (prec == 0) k_phi<double><<<dim3((p.N + 2 + 3) / 4, p.B), 128, 0, st>>>(p);
+  else k_phi<float><<<dim3((p.N + 2 + 3) / 4, p.B), 128, 0, st>>>(p);
   return cudaGetLastError();
 }
 
 cudaError_t launch_phi(int prec, const ChainParams& p, cudaStream_t st) {
-  if (prec == 0) k_phi<double><<<dim3(p.N + 2, p.B), 128, 0, st>>>(p);
-  else k_phi<float><<<dim3(p.N + 2, p.B), 128, 0, st>>>(p);
+  if (prec == 0) k_phi<double><<<dim3((p.N + 2 + 3) / 4, p.B), 128, 0, st>>>(p);
+  else k_phi<float><<<dim3((p.N + 2 + 3) / 4, p.B), 128, 0, st>>>(p);
   return cudaGetLastError();
 }
 

@@ -1277,14 +1277,21 @@ __global__ void __launch_bounds__(CHAIN_MAX_THREADS) k_fill(ChainParams p) {
   }
 }
 
-// grid (N+2, B), 128 threads.  Block n <= N converts psi(t_n), chi(t_n) from the chain to FP64
-// (psi(t_0) = psi_i and chi(t_N) = chi(T) are exact) and forms phi_n = a_n psi(t_n) + b_n chi(t_n)
-// (Eq. (cible)); block N+1 forms J and F at u in FP64.
+// grid (ceil((N+2)/4), B), 128 threads: warp w of block x handles index n = 4x + w.  For n <= N it
+// converts psi(t_n), chi(t_n) from the chain to FP64 (psi(t_0) = psi_i and chi(t_N) = chi(T) are
+// exact), renormalises them in FP64 and forms phi_n = a_n psi(t_n) + b_n chi(t_n) (Eq. (cible));
+// n = N+1 forms J and F at u in FP64.  Warp-level sums only: no block barrier.
+__device__ __forceinline__ double warp_sum_d(double v) {
+  for (int m = 16; m >= 1; m >>= 1) v += __shfl_xor_sync(0xffffffffu, v, m);
+  return v;
+}
+
 template <typename R>
 __global__ void __launch_bounds__(128) k_phi(ChainParams p) {
   using R2 = typename C2<R>::T;
-  __shared__ double red[4];
-  const int n = blockIdx.x, b = blockIdx.y, t = threadIdx.x, d = p.d, N = p.N;
+  const int lane = threadIdx.x & 31, b = blockIdx.y, d = p.d, N = p.N;
+  const int n = blockIdx.x * 4 + (threadIdx.x >> 5);
+  if (n > N + 1) return;   // whole warps leave
   double2* psin = p.psin + (long)b * (N + 1) * d;
   double2* chin = p.chin + (long)b * (N + 1) * d;
   const R2* sps = reinterpret_cast<const R2*>(p.stage) + (long)b * 2 * (N + 1) * d;
@@ -1300,39 +1307,36 @@ __global__ void __launch_bounds__(128) k_phi(ChainParams p) {
     const R2 z = sch[(long)m * d + e];
     return make_double2((double)z.x, (double)z.y);
   };
-  // Norm renormalisation in FP64: the propagation is unitary, so psi(t_n) keeps the norm of psi_i and
-  // chi(t_n) that of chi(T); rescaling them back removes the norm drift of FP32 propagation (a no-op
-  // in exact arithmetic) and the largest relative drift is recorded.
-  auto norms = [&](int m, double& sp, double& sc) {
-    double a = 0.0, a0 = 0.0, c = 0.0, cT = 0.0;
-    for (int e = t; e < d; e += blockDim.x) {
-      const double2 x = load_ps(m, e), x0 = p.psi_i[e], y = load_cs(m, e), yT = chin[(long)N * d + e];
-      a = fma(x.x, x.x, fma(x.y, x.y, a));
-      a0 = fma(x0.x, x0.x, fma(x0.y, x0.y, a0));
-      c = fma(y.x, y.x, fma(y.y, y.y, c));
-      cT = fma(yT.x, yT.x, fma(yT.y, yT.y, cT));
-    }
-    a = block_sum(a, red);
-    a0 = block_sum(a0, red);
-    c = block_sum(c, red);
-    cT = block_sum(cT, red);
-    sp = (a > 0.0 && a0 > 0.0) ? sqrt(a0 / a) : 1.0;
-    sc = (c > 0.0 && cT > 0.0) ? sqrt(cT / c) : 1.0;
-    if (t == 0 && p.drift && a0 > 0.0 && cT > 0.0) {
-      const double dr = fmax(fabs(a / a0 - 1.0), fabs(c / cT - 1.0));
-      if (dr >= 0.0) atomicMax(p.drift, __double_as_longlong(dr));   // ordered as integers when >= 0
-    }
-  };
+  // Norm renormalisation in FP64: the propagation is unitary, so psi(t_n) keeps the norm of psi_i
+  // and chi(t_n) that of chi(T); rescaling them back removes the norm drift of FP32 propagation (a
+  // no-op in exact arithmetic) and the largest relative drift is recorded.
+  double a = 0.0, a0 = 0.0, c = 0.0, cT = 0.0;
+  const int m = n <= N ? n : N;
+  for (int e = lane; e < d; e += 32) {
+    const double2 x = load_ps(m, e), x0 = p.psi_i[e], y = load_cs(m, e), yT = chin[(long)N * d + e];
+    a = fma(x.x, x.x, fma(x.y, x.y, a));
+    a0 = fma(x0.x, x0.x, fma(x0.y, x0.y, a0));
+    c = fma(y.x, y.x, fma(y.y, y.y, c));
+    cT = fma(yT.x, yT.x, fma(yT.y, yT.y, cT));
+  }
+  a = warp_sum_d(a);
+  a0 = warp_sum_d(a0);
+  c = warp_sum_d(c);
+  cT = warp_sum_d(cT);
+  const double s_psi = (a > 0.0 && a0 > 0.0) ? sqrt(a0 / a) : 1.0;
+  const double s_chi = (c > 0.0 && cT > 0.0) ? sqrt(cT / c) : 1.0;
   if (n <= N) {
+    if (lane == 0 && p.drift && a0 > 0.0 && cT > 0.0) {
+      const double dr = fmax(fabs(a / a0 - 1.0), fabs(c / cT - 1.0));
+      if (dr >= 0.0) atomicMax(p.drift, (unsigned long long)__double_as_longlong(dr));   // ordered as integers
+    }
+    // psi_i and chi(T) are the references; psi(T) stays as propagated in psin (the J warp reads it
+    // concurrently and applies the scale to its sums; chi(T) = O psi(T) was formed from it)
+    const double sp = (n == 0 || n == N) ? 1.0 : s_psi;
+    const double sc = n == N ? 1.0 : s_chi;
     const double2 w = p.ab[n];
     double2* phi = p.phi + ((long)b * (N + 1) + n) * d;
-    double sp, sc;
-    norms(n, sp, sc);
-    if (n == 0) sp = 1.0;   // psi_i and chi(T) are the references
-    // psi(T) stays as propagated in psin (the J block below reads it concurrently and applies the
-    // scale to its sums instead; chi(T) = O psi(T) was formed from it)
-    if (n == N) { sc = 1.0; sp = 1.0; }
-    for (int e = t; e < d; e += blockDim.x) {
+    for (int e = lane; e < d; e += 32) {
       double2 ps = load_ps(n, e), cs = load_cs(n, e);
       ps.x *= sp; ps.y *= sp;
       cs.x *= sc; cs.y *= sc;
@@ -1343,37 +1347,25 @@ __global__ void __launch_bounds__(128) k_phi(ChainParams p) {
     return;
   }
   // J and F: <psi(T)|chi(T)> is the overlap with psi_f or <psi|O|psi>, with psi(T) renormalised (the
-  // scale is applied to the sums)
+  // scale is applied to the sums).  Overlap objective: chi(T) = psi_f, linear in psi(T); observable:
+  // chi(T) = O psi(T) was formed from the unscaled psi(T), so <psi|O|psi> takes the scale twice.
   double ovr = 0.0, ovi = 0.0;
-  for (int e = t; e < d; e += blockDim.x) {
+  for (int e = lane; e < d; e += 32) {
     const double2 z = load_ps(N, e);
-    const double2 c = chin[(long)N * d + e];
-    ovr += z.x * c.x + z.y * c.y;
-    ovi += z.x * c.y - z.y * c.x;
+    const double2 y = chin[(long)N * d + e];
+    ovr += z.x * y.x + z.y * y.y;
+    ovi += z.x * y.y - z.y * y.x;
   }
-  ovr = block_sum(ovr, red);
-  ovi = block_sum(ovi, red);
-  {
-    double a = 0.0, a0 = 0.0;
-    for (int e = t; e < d; e += blockDim.x) {
-      const double2 x = load_ps(N, e), x0 = p.psi_i[e];
-      a = fma(x.x, x.x, fma(x.y, x.y, a));
-      a0 = fma(x0.x, x0.x, fma(x0.y, x0.y, a0));
-    }
-    a = block_sum(a, red);
-    a0 = block_sum(a0, red);
-    // overlap objective: chi(T) = psi_f, linear in psi(T); observable: chi(T) = O psi(T) was formed from
-    // the unscaled psi(T), so <psi|O|psi> takes the scale twice
-    const double s = (a > 0.0 && a0 > 0.0) ? sqrt(a0 / a) : 1.0;
-    const double sj = p.obj == 0 ? s : s * s;
-    ovr *= sj;
-    ovi *= sj;
-  }
+  ovr = warp_sum_d(ovr);
+  ovi = warp_sum_d(ovi);
+  const double sj = p.obj == 0 ? s_psi : s_psi * s_psi;
+  ovr *= sj;
+  ovi *= sj;
   double pen = 0.0;
   if (p.pen)
-    for (int n2 = t; n2 < N; n2 += blockDim.x) pen += p.pen[(long)b * N + n2];
-  pen = 0.5 * p.tau * block_sum(pen, red);
-  if (t == 0) {
+    for (int n2 = lane; n2 < N; n2 += 32) pen += p.pen[(long)b * N + n2];
+  pen = 0.5 * p.tau * warp_sum_d(pen);
+  if (lane == 0) {
     const double F = p.obj == 0 ? ovr * ovr + ovi * ovi : ovr;
     const double J = ovr - pen;
     if (!isfinite(J) || !isfinite(F)) atomicOr(p.status, ST_NONFINITE);
