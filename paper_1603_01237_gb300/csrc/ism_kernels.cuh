@@ -1328,7 +1328,10 @@ __global__ void __launch_bounds__(128) k_phi(ChainParams p) {
   if (n <= N) {
     if (lane == 0 && p.drift && a0 > 0.0 && cT > 0.0) {
       const double dr = fmax(fabs(a / a0 - 1.0), fabs(c / cT - 1.0));
-      if (dr >= 0.0) atomicMax(p.drift, (unsigned long long)__double_as_longlong(dr));   // ordered as integers
+      // non-negative doubles order as their bit patterns; read first, so that the hundreds of
+      // thousands of warps of a batched launch do not all queue atomics on one address
+      const unsigned long long bits = (unsigned long long)__double_as_longlong(dr);
+      if (dr >= 0.0 && bits > *reinterpret_cast<volatile unsigned long long*>(p.drift)) atomicMax(p.drift, bits);
     }
     // psi_i and chi(T) are the references; psi(T) stays as propagated in psin (the J warp reads it
     // concurrently and applies the scale to its sums; chi(T) = O psi(T) was formed from it)
