@@ -79,6 +79,7 @@ struct ism_plan_s {
   int m = 1, q = 0;                      // controls per step; bits of d (Pauli kind)
   bool pauli = false;
   bool wide = false;                     // direct sweeps in the wide lane layout
+  double nrm_psi_i = 0, nrm_psi_f = 0;   // |psi_i|^2, |psi_f|^2 (references of the renormalisation)
   double* dwts = nullptr;                // Pauli kind: [m][q][2] control weights
   void* dcxy = nullptr;                  // Pauli kind: [B][Nt][2q] step coefficients (R)
   double gpdw = 0;                       // double-well separation D
@@ -469,6 +470,9 @@ int run_states(ism_plan_s* P, const double* u, double* Jhist, int hist_stride, i
   c.status = P->dstatus; c.max_spin = P->max_spin; c.stages = P->chain_stages; c.tile_stride = P->tst;
   c.Mc = P->dMc; c.Nc = P->Nc; c.sblk = P->sblk;
   c.drift = P->dcount + 6;
+  c.nrm_psi_i = P->nrm_psi_i;
+  c.inv_nrm_psi_i = P->nrm_psi_i > 0.0 ? 1.0 / P->nrm_psi_i : 0.0;
+  c.nrm_chi_T = P->obj == ISM_OBJ_OVERLAP ? P->nrm_psi_f : -1.0;
   if (P->ks.large || P->direct) {
     c.src64 = 1;
     ISM_CUDA_TRY(timed(P, 1, 1, [&] { return ism::launch_phi(P->prec, c, P->st); }));
@@ -622,6 +626,11 @@ int plan_build(const ism_problem* prob, const ism_options* opt, void* cuda_strea
     return ISM_OK;
   }
 
+  for (int e = 0; e < d; ++e) {
+    P->nrm_psi_i += p.psi_i[2 * e] * p.psi_i[2 * e] + p.psi_i[2 * e + 1] * p.psi_i[2 * e + 1];
+    if (p.objective == ISM_OBJ_OVERLAP && p.psi_f)
+      P->nrm_psi_f += p.psi_f[2 * e] * p.psi_f[2 * e] + p.psi_f[2 * e + 1] * p.psi_f[2 * e + 1];
+  }
   if (p.kind == ISM_H_PAULI) {
     P->pauli = true;
     P->m = p.controls < 1 ? 1 : p.controls;

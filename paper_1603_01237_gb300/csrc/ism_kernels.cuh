@@ -91,6 +91,8 @@ struct ChainParams {
   void* Mc;               // [B][Nc] tiles: P_k = M_{k sblk + len_k - 1} ... M_{k sblk}
   int Nc, sblk;
   unsigned long long* drift;   // largest relative norm drift seen by k_phi (double bits), or null
+  double nrm_psi_i, inv_nrm_psi_i;   // |psi_i|^2 and its inverse
+  double nrm_chi_T;                  // |psi_f|^2 (overlap objective), or -1: summed per problem
 };
 
 template <typename R> __device__ __forceinline__ R ldu_ro(const double* u, long i) { return (R)__ldg(u + i); }
@@ -1310,24 +1312,32 @@ __global__ void __launch_bounds__(128) k_phi(ChainParams p) {
   // Norm renormalisation in FP64: the propagation is unitary, so psi(t_n) keeps the norm of psi_i
   // and chi(t_n) that of chi(T); rescaling them back removes the norm drift of FP32 propagation (a
   // no-op in exact arithmetic) and the largest relative drift is recorded.
-  double a = 0.0, a0 = 0.0, c = 0.0, cT = 0.0;
+  // reference norms: |psi_i|^2 and, for the overlap objective, |chi(T)|^2 = |psi_f|^2 come from the host;
+  // the observable's chi(T) = O psi(T) differs per problem and is summed here (FP64 is scarce on this
+  // GPU: no divisions, one reciprocal square root per state)
+  double a = 0.0, c = 0.0, cT = p.nrm_chi_T;
   const int m = n <= N ? n : N;
   for (int e = lane; e < d; e += 32) {
-    const double2 x = load_ps(m, e), x0 = p.psi_i[e], y = load_cs(m, e), yT = chin[(long)N * d + e];
+    const double2 x = load_ps(m, e), y = load_cs(m, e);
     a = fma(x.x, x.x, fma(x.y, x.y, a));
-    a0 = fma(x0.x, x0.x, fma(x0.y, x0.y, a0));
     c = fma(y.x, y.x, fma(y.y, y.y, c));
-    cT = fma(yT.x, yT.x, fma(yT.y, yT.y, cT));
   }
   a = warp_sum_d(a);
-  a0 = warp_sum_d(a0);
   c = warp_sum_d(c);
-  cT = warp_sum_d(cT);
-  const double s_psi = (a > 0.0 && a0 > 0.0) ? sqrt(a0 / a) : 1.0;
-  const double s_chi = (c > 0.0 && cT > 0.0) ? sqrt(cT / c) : 1.0;
+  if (cT < 0.0) {
+    double t = 0.0;
+    for (int e = lane; e < d; e += 32) {
+      const double2 yT = chin[(long)N * d + e];
+      t = fma(yT.x, yT.x, fma(yT.y, yT.y, t));
+    }
+    cT = warp_sum_d(t);
+  }
+  const double a0 = p.nrm_psi_i;
+  const double s_psi = (a > 0.0 && a0 > 0.0) ? sqrt(a0) * rsqrt(a) : 1.0;
+  const double s_chi = (c > 0.0 && cT > 0.0) ? sqrt(cT) * rsqrt(c) : 1.0;
   if (n <= N) {
     if (lane == 0 && p.drift && a0 > 0.0 && cT > 0.0) {
-      const double dr = fmax(fabs(a / a0 - 1.0), fabs(c / cT - 1.0));
+      const double dr = fmax(fabs(a * p.inv_nrm_psi_i - 1.0), fabs(c - cT) / cT);
       // non-negative doubles order as their bit patterns; read first, so that the hundreds of
       // thousands of warps of a batched launch do not all queue atomics on one address
       const unsigned long long bits = (unsigned long long)__double_as_longlong(dr);
