@@ -80,6 +80,7 @@ struct ism_plan_s {
   bool pauli = false;
   bool wide = false;                     // direct sweeps in the wide lane layout
   double nrm_psi_i = 0, nrm_psi_f = 0;   // |psi_i|^2, |psi_f|^2 (references of the renormalisation)
+  double* dnrm = nullptr;                // [B][N+1][2] squared norms of psi(t_n), chi(t_n) (direct sweeps)
   double* dwts = nullptr;                // Pauli kind: [m][q][2] control weights
   void* dcxy = nullptr;                  // Pauli kind: [B][Nt][2q] step coefficients (R)
   double gpdw = 0;                       // double-well separation D
@@ -418,6 +419,7 @@ ism::KParams kparams(ism_plan_s* P, double* u) {
   k.psin_w = P->dpsin; k.chin_w = P->dchin; k.zp = P->dzp;
   k.scheme = P->scheme == ISM_SCHEME_CRANK_NICOLSON ? 1 : 0;
   k.m = P->m; k.q = P->q; k.wts = P->dwts; k.cxy = P->dcxy; k.zq = P->dzp;
+  k.nrm_w = P->dnrm;
   return k;
 }
 
@@ -473,6 +475,7 @@ int run_states(ism_plan_s* P, const double* u, double* Jhist, int hist_stride, i
   c.nrm_psi_i = P->nrm_psi_i;
   c.inv_nrm_psi_i = P->nrm_psi_i > 0.0 ? 1.0 / P->nrm_psi_i : 0.0;
   c.nrm_chi_T = P->obj == ISM_OBJ_OVERLAP ? P->nrm_psi_f : -1.0;
+  c.nrm = (P->direct && !P->ks.large) ? P->dnrm : nullptr;   // k_gsweep leaves the squared norms
   if (P->ks.large || P->direct) {
     c.src64 = 1;
     ISM_CUDA_TRY(timed(P, 1, 1, [&] { return ism::launch_phi(P->prec, c, P->st); }));
@@ -742,6 +745,7 @@ int plan_build(const ism_problem* prob, const ism_options* opt, void* cuda_strea
   TRY_ALLOC(P->dpsin, B * (P->N + 1) * (size_t)d);
   TRY_ALLOC(P->dchin, B * (P->N + 1) * (size_t)d);
   TRY_ALLOC(P->dphi, B * (P->N + 1) * (size_t)d);
+  if (P->direct && !P->ks.large) TRY_ALLOC(P->dnrm, B * (P->N + 1) * 2);
   unsigned char* dTb = nullptr;
   TRY_ALLOC(dTb, B * ((size_t)P->Nt + P->N) * GE * P->r2);
   P->dtraj = dTb;

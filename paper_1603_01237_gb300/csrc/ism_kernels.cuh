@@ -52,6 +52,7 @@ struct KParams {
   const double* wts;           // [m][q][2] weights (ax, ay) of X_b, Y_b in control c
   void* cxy;                   // [B][Nt][2q] (R) step coefficients cx_b, cy_b (k_pauli_prep)
   void* zq;                    // [B][Nt+N][2q] (R2) per-slot overlaps <delta|X_b psi>, <delta|Y_b psi>
+  double* nrm_w;               // [B][N+1][2] |psi(t_n)|^2, |chi(t_n)|^2 from k_gsweep (FP64), or null
   // direct global sweeps (large d): inputs and FP64 outputs, per-warp overlap partials
   const double2* psi_i;        // [d]
   const double2* psi_f;        // [d]
@@ -93,6 +94,7 @@ struct ChainParams {
   unsigned long long* drift;   // largest relative norm drift seen by k_phi (double bits), or null
   double nrm_psi_i, inv_nrm_psi_i;   // |psi_i|^2 and its inverse
   double nrm_chi_T;                  // |psi_f|^2 (overlap objective), or -1: summed per problem
+  const double* nrm;                 // [B][N+1][2] squared norms from the direct sweeps, or null
 };
 
 template <typename R> __device__ __forceinline__ R ldu_ro(const double* u, long i) { return (R)__ldg(u + i); }
@@ -750,19 +752,28 @@ __global__ void __launch_bounds__(128) k_gsweep(KParams p) {
       lo.im[r] = COMP ? (R)(z.y - (double)v.im[r]) : R(0);
     }
   };
-  auto store64 = [&](bool adj, double2* dst) {   // segment phase in FP64, store, continue from it
+  // segment phase in FP64, store, continue from it; the FP64 squared norm goes to nslot (for the
+  // renormalisation in k_phi, which then reads one number instead of summing the state again)
+  auto store64 = [&](bool adj, double2* dst, double* nslot) {
+    double sq = 0.0;
 #pragma unroll
     for (int r = 0; r < E; ++r) {
       const int e = lg * E + r;
       double yr, yi;
       phase_rotate(ch.cph, ch.sph, adj, (double)v.re[r] + (double)lo.re[r], (double)v.im[r] + (double)lo.im[r], yr, yi);
-      if (e < d && valid) dst[e] = make_double2(yr, yi);
+      if (e < d) {
+        if (valid) dst[e] = make_double2(yr, yi);
+        sq = fma(yr, yr, fma(yi, yi, sq));
+      }
       v.re[r] = (R)yr;
       v.im[r] = (R)yi;
       lo.re[r] = COMP ? (R)(yr - (double)v.re[r]) : R(0);
       lo.im[r] = COMP ? (R)(yi - (double)v.im[r]) : R(0);
     }
+    sq = g_sum<G>(sq);
+    if (nslot && valid && lg == 0) *nslot = sq;
   };
+  double* nrm = p.nrm_w ? p.nrm_w + (long)b * (N + 1) * 2 : nullptr;   // [N+1][2]: |psi(t_n)|^2, |chi(t_n)|^2
   // propagate over sub-interval n forward (ADJ = false) or backward (ADJ = true)
   auto segment = [&](int n, auto adj_tag) {
     constexpr bool ADJ = decltype(adj_tag)::value;
@@ -821,7 +832,7 @@ __global__ void __launch_bounds__(128) k_gsweep(KParams p) {
       for (int e = lg; e < d; e += G) psin[e] = p.psi_i[e];
     for (int n = 0; n < N; ++n) {
       segment(n, std::false_type());
-      store64(false, psin + (long)(n + 1) * d);
+      store64(false, psin + (long)(n + 1) * d, nrm ? nrm + 2 * (n + 1) : nullptr);
     }
   }
   if (dir == 1 || nch == 1) {
@@ -842,12 +853,20 @@ __global__ void __launch_bounds__(128) k_gsweep(KParams p) {
         }
         if (valid) chT[e] = make_double2(sr, si);
       }
+      __syncwarp();
+      double sq = 0.0;
+      for (int e = lg; e < d; e += G) {
+        const double2 z = chT[e];
+        sq = fma(z.x, z.x, fma(z.y, z.y, sq));
+      }
+      sq = g_sum<G>(sq);
+      if (nrm && valid && lg == 0) nrm[2 * N + 1] = sq;
     }
     __syncwarp();
     load64(chT);
     for (int n = N - 1; n >= 0; --n) {
       segment(n, std::true_type());
-      store64(true, chin + (long)n * d);
+      store64(true, chin + (long)n * d, nrm ? nrm + 2 * n + 1 : nullptr);
     }
   }
 }
@@ -1317,13 +1336,20 @@ __global__ void __launch_bounds__(128) k_phi(ChainParams p) {
   // GPU: no divisions, one reciprocal square root per state)
   double a = 0.0, c = 0.0, cT = p.nrm_chi_T;
   const int m = n <= N ? n : N;
-  for (int e = lane; e < d; e += 32) {
-    const double2 x = load_ps(m, e), y = load_cs(m, e);
-    a = fma(x.x, x.x, fma(x.y, x.y, a));
-    c = fma(y.x, y.x, fma(y.y, y.y, c));
+  const double* nb = p.nrm ? p.nrm + (long)b * (N + 1) * 2 : nullptr;
+  if (nb) {   // squared norms left by the direct sweeps (psi(t_0) = psi_i and chi(T) are the references)
+    a = m == 0 ? p.nrm_psi_i : nb[2 * m];
+    if (cT < 0.0) cT = nb[2 * N + 1];
+    c = m == N ? cT : nb[2 * m + 1];
+  } else {
+    for (int e = lane; e < d; e += 32) {
+      const double2 x = load_ps(m, e), y = load_cs(m, e);
+      a = fma(x.x, x.x, fma(x.y, x.y, a));
+      c = fma(y.x, y.x, fma(y.y, y.y, c));
+    }
+    a = warp_sum_d(a);
+    c = warp_sum_d(c);
   }
-  a = warp_sum_d(a);
-  c = warp_sum_d(c);
   if (cT < 0.0) {
     double t = 0.0;
     for (int e = lane; e < d; e += 32) {
