@@ -1358,12 +1358,21 @@ __global__ void __launch_bounds__(128) k_phi(ChainParams p) {
     }
     cT = warp_sum_d(t);
   }
+  // relative drifts of the squared norms and the scales (1 + delta)^(-1/2), by the series
+  // 1 - delta/2 + 3 delta^2/8 (truncation below 4e-13 for |delta| < 1e-4; rsqrt beyond): FP64 square
+  // roots and divisions for each of the ~10^5-10^6 states of a batched step would cost more than
+  // the rest of this kernel.  The drift of chi needs |psi_f|^2 or |chi(T)|^2 inverted only to FP32
+  // accuracy (it multiplies a drift of ~1e-6).
   const double a0 = p.nrm_psi_i;
-  const double s_psi = (a > 0.0 && a0 > 0.0) ? sqrt(a0) * rsqrt(a) : 1.0;
-  const double s_chi = (c > 0.0 && cT > 0.0) ? sqrt(cT) * rsqrt(c) : 1.0;
+  const bool okp = a > 0.0 && a0 > 0.0, okc = c > 0.0 && cT > 0.0;
+  const double dp = okp ? fma(a, p.inv_nrm_psi_i, -1.0) : 0.0;
+  const double dc = okc ? (c - cT) * (double)(1.0f / (float)cT) : 0.0;
+  auto inv_sqrt1p = [](double dl) { return fabs(dl) < 1e-4 ? fma(fma(0.375, dl, -0.5), dl, 1.0) : rsqrt(1.0 + dl); };
+  const double s_psi = inv_sqrt1p(dp);
+  const double s_chi = inv_sqrt1p(dc);
   if (n <= N) {
-    if (lane == 0 && p.drift && a0 > 0.0 && cT > 0.0) {
-      const double dr = fmax(fabs(a * p.inv_nrm_psi_i - 1.0), fabs(c - cT) / cT);
+    if (lane == 0 && p.drift && okp && okc) {
+      const double dr = fmax(fabs(dp), fabs(dc));
       // non-negative doubles order as their bit patterns; read first, so that the hundreds of
       // thousands of warps of a batched launch do not all queue atomics on one address
       const unsigned long long bits = (unsigned long long)__double_as_longlong(dr);
