@@ -236,8 +236,9 @@ typedef struct {
   unsigned long long terms[2];
   unsigned long long substeps[2];
   long long kernels;
-  double norm_drift;        /* largest |norm^2 / reference - 1| of psi(t_n), chi(t_n) before their FP64
-                               renormalisation (d <= 1024 kinds; 0 for the grid kinds)               */
+  double norm_drift;        /* largest |norm^2 / reference - 1| of psi(T) and chi(t_0) (the ends of the
+                               global trajectories, where it is largest) before the FP64
+                               renormalisation of psi(t_n), chi(t_n) (0 for the grid kinds)          */
 } ism_stats;
 
 /* ism_set_profiling -- on != 0 records CUDA events around every kernel on the plan's stream. */

@@ -1371,8 +1371,10 @@ __global__ void __launch_bounds__(128) k_phi(ChainParams p) {
   const double s_psi = inv_sqrt1p(dp);
   const double s_chi = inv_sqrt1p(dc);
   if (n <= N) {
-    if (lane == 0 && p.drift && okp && okc) {
-      const double dr = fmax(fabs(dp), fabs(dc));
+    // the drift is recorded where the propagation is longest, psi(T) and chi(t_0) (block-uniform
+    // reads of one address by every state of a batch would cost more than the states themselves)
+    if (lane == 0 && p.drift && okp && okc && (n == N || n == 0)) {
+      const double dr = n == N ? fabs(dp) : fabs(dc);
       // non-negative doubles order as their bit patterns; read first, so that the hundreds of
       // thousands of warps of a batched launch do not all queue atomics on one address
       const unsigned long long bits = (unsigned long long)__double_as_longlong(dr);
