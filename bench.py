@@ -167,8 +167,8 @@ def kernel_source_hash(files=KERNEL_SOURCES) -> str:
 # problems, from a one-pass ncu capture of the default step (4864 rotor problems: k_gsweep in the wide
 # lane layout); reported only while the kernel sources hash to the captured build.
 TRAFFIC_PER_PROBLEM = {
-    ("k_gsweep", "rotor41"): {"bytes_per_problem": (1169261312 + 789064960) / 4864, "source_hash": "d90065f281acb93a"},
-    ("k_subinterval", "rotor41"): {"bytes_per_problem": (42362061824 + 41639220224) / 4864, "source_hash": "d90065f281acb93a"},
+    ("k_gsweep", "rotor41"): {"bytes_per_problem": (1183849984 + 806942208) / 4864, "source_hash": "948b803a362d0bfc"},
+    ("k_subinterval", "rotor41"): {"bytes_per_problem": (42478998272 + 41642060032) / 4864, "source_hash": "948b803a362d0bfc"},
 }
 
 
