@@ -167,8 +167,8 @@ def kernel_source_hash(files=KERNEL_SOURCES) -> str:
 # problems, from a one-pass ncu capture of the default step (4864 rotor problems: k_gsweep in the wide
 # lane layout); reported only while the kernel sources hash to the captured build.
 TRAFFIC_PER_PROBLEM = {
-    ("k_gsweep", "rotor41"): {"bytes_per_problem": (1183849984 + 806942208) / 4864, "source_hash": "948b803a362d0bfc"},
-    ("k_subinterval", "rotor41"): {"bytes_per_problem": (42478998272 + 41642060032) / 4864, "source_hash": "948b803a362d0bfc"},
+    ("k_gsweep", "rotor41"): {"bytes_per_problem": (1196194816 + 807960320) / 4864, "source_hash": "41fa2a11e09cc429"},
+    ("k_subinterval", "rotor41"): {"bytes_per_problem": (42514150912 + 41645251584) / 4864, "source_hash": "41fa2a11e09cc429"},
 }
 
 

@@ -88,6 +88,7 @@ template <typename R> struct Cheb {
   double cph, sph;  // cos, sin of the sub-interval's global phase c * tau * (number of steps)
   int K, S;         // terms, sub-steps per time step (Crank-Nicolson: Jacobi iterations, 1)
   R h;              // Crank-Nicolson only: tau / 2
+  double hd;        // Crank-Nicolson only: tau / 2 in FP64 (hi/lo diagonal coefficients of FP32 steps)
 };
 
 template <typename R> __device__ __forceinline__ void split2(double v, R& hi, R& lo) {
@@ -178,6 +179,7 @@ __device__ void cn_params(Cheb<R>& ch, double tau, double off0, double off1, dou
   ch.sph = 0.0;
   ch.S = 1;
   ch.h = (R)(0.5 * tau);
+  ch.hd = 0.5 * tau;
   const double rho = 0.5 * tau * (off0 + umax * off1) * (1.0 + 1e-6);
   int K = 1;
   if (rho >= 0.5) {   // flagged; one iteration keeps the (discarded) results bounded
@@ -578,49 +580,78 @@ __device__ __forceinline__ void cheb_step(Vec<R, E>& v, const Op& op, const Cheb
 // Jacobi iterations on the split diag(1 + i sg h H_ee) + off-diagonal: each iteration shrinks the
 // error by at most rho = h max_e(|H_{e,e-1}| + |H_{e,e+1}|) (the diagonal has modulus >= 1); the
 // caller's K iterations reach rho^K below the working precision (k_cheb_prep).
+// FP32 steps (LO): the diagonal quantities repeat at every step, so their FP32 rounding would add up
+// over the global trajectories like a small change of tau (a phase drift of ~1e-4 rad over 2 x 10^4
+// rotor steps).  Ops with a u-independent diagonal carry t = h H_ee, dr and di as hi + lo pairs
+// (th/tl, dr/drl, di/dil, formed in FP64; Op::CN_LO); the others have none.
+template <typename R, int E, class Op>
+__device__ __forceinline__ void cn_dinv(Vec<R, E>& x, R xr_in[E], R xi_in[E], const Op& op, R sg) {
+#pragma unroll
+  for (int e = 0; e < E; ++e) {   // x = (dr - i sg di) y
+    const R yr = xr_in[e], yi = xi_in[e];
+    const R di = sg * op.di[e];
+    R xr = di * yi, xi = -di * yr;
+    if constexpr (Op::CN_LO) {
+      const R dl = sg * op.dil[e];
+      xr = fma(op.drl[e], yr, fma(dl, yi, xr));
+      xi = fma(op.drl[e], yi, fma(-dl, yr, xi));
+    }
+    x.re[e] = fma(op.dr[e], yr, xr);
+    x.im[e] = fma(op.dr[e], yi, xi);
+  }
+}
+
 template <typename R, int E, class Op>
 __device__ __forceinline__ void cn_solve(Vec<R, E>& x, const Vec<R, E>& r, const Op& op, R h, R sg, int K) {
   // D^{-1} = (1 - i sg h d_e) / (1 + (h d_e)^2) = dr_e - i sg di_e (op.dr, op.di)
+  {
+    R yr[E], yi[E];
 #pragma unroll
-  for (int e = 0; e < E; ++e) {
-    const R di = sg * op.di[e];
-    x.re[e] = fma(op.dr[e], r.re[e], di * r.im[e]);
-    x.im[e] = fma(op.dr[e], r.im[e], -di * r.re[e]);
+    for (int e = 0; e < E; ++e) { yr[e] = r.re[e]; yi[e] = r.im[e]; }
+    cn_dinv(x, yr, yi, op, sg);
   }
   for (int k = 1; k < K; ++k) {
     Vec<R, E> o;
     op.template cn_apply<false>(x, o);
+    R yr[E], yi[E];
 #pragma unroll
     for (int e = 0; e < E; ++e) {   // y = r - i sg h (off x), then x = D^{-1} y
-      const R yr = fma(sg * h, o.im[e], r.re[e]);
-      const R yi = fma(-sg * h, o.re[e], r.im[e]);
-      const R di = sg * op.di[e];
-      x.re[e] = fma(op.dr[e], yr, di * yi);
-      x.im[e] = fma(op.dr[e], yi, -di * yr);
+      yr[e] = fma(sg * h, o.im[e], r.re[e]);
+      yi[e] = fma(-sg * h, o.re[e], r.im[e]);
     }
+    cn_dinv(x, yr, yi, op, sg);
   }
 }
 
-// ADJ = false: v <- A^{-1} B v.  ADJ = true: xi <- B^{-1} v, then v <- A xi (= U^H v).
+// ADJ = false: v <- A^{-1} B v.  ADJ = true: xi <- B^{-1} v, then v <- A xi (= U^H v).  Where
+// Op::CN_LO, h H v is formed as (th + tl) v + h (off v); else as h (H v).
 template <bool ADJ, typename R, int E, class Op>
 __device__ __forceinline__ void cn_step(Vec<R, E>& v, Vec<R, E>& xi, const Op& op, R h, int K) {
-  Vec<R, E> t;
+  Vec<R, E> o;
   if (!ADJ) {
-    op.template cn_apply<true>(v, t);
+    op.template cn_apply<!Op::CN_LO>(v, o);
     Vec<R, E> r;
 #pragma unroll
     for (int e = 0; e < E; ++e) {   // r = v - i h H v
-      r.re[e] = fma(h, t.im[e], v.re[e]);
-      r.im[e] = fma(-h, t.re[e], v.im[e]);
+      r.re[e] = fma(h, o.im[e], v.re[e]);
+      r.im[e] = fma(-h, o.re[e], v.im[e]);
+      if constexpr (Op::CN_LO) {
+        r.re[e] = fma(op.th[e], v.im[e], fma(op.tl[e], v.im[e], r.re[e]));
+        r.im[e] = fma(-op.th[e], v.re[e], fma(-op.tl[e], v.re[e], r.im[e]));
+      }
     }
     cn_solve(v, r, op, h, R(1), K);
   } else {
     cn_solve(xi, v, op, h, R(-1), K);
-    op.template cn_apply<true>(xi, t);
+    op.template cn_apply<!Op::CN_LO>(xi, o);
 #pragma unroll
     for (int e = 0; e < E; ++e) {   // v = xi + i h H xi
-      v.re[e] = fma(-h, t.im[e], xi.re[e]);
-      v.im[e] = fma(h, t.re[e], xi.im[e]);
+      v.re[e] = fma(-h, o.im[e], xi.re[e]);
+      v.im[e] = fma(h, o.re[e], xi.im[e]);
+      if constexpr (Op::CN_LO) {
+        v.re[e] = fma(-op.th[e], xi.im[e], fma(-op.tl[e], xi.im[e], v.re[e]));
+        v.im[e] = fma(op.th[e], xi.re[e], fma(op.tl[e], xi.re[e], v.im[e]));
+      }
     }
   }
 }
@@ -636,6 +667,9 @@ struct OpTridiagCN : OpTridiag<R, G_, E_, HB> {
   static constexpr int E = E_, G = G_;
   R cdg[E_], cof[E_], cofm;
   R dr[E_], di[E_];   // inverse of the Jacobi diagonal 1 + i h H_ee: dr - i di (A), dr + i di (B)
+  R drl[E_], dil[E_]; // their low parts (CN_LO: u-independent diagonal, FP32 steps)
+  R th[E_], tl[E_];   // t = h H_ee as hi + lo (CN_LO)
+  static constexpr bool CN_LO = !HB && sizeof(R) == 4;
   R hh;               // tau / 2
   __device__ __forceinline__ void diag_inverse() {
 #pragma unroll
@@ -652,8 +686,14 @@ struct OpTridiagCN : OpTridiag<R, G_, E_, HB> {
       const int e = lg * E_ + r;
       this->ah[r] = e < d ? (R)H0d[e] : R(0);
       cdg[r] = this->ah[r];
+      if constexpr (!HB) {   // the diagonal does not depend on u: coefficients in FP64, as hi + lo
+        const double t = e < d ? ch.hd * H0d[e] : 0.0;
+        const double den = 1.0 / fma(t, t, 1.0);
+        split2<R>(t, th[r], tl[r]);
+        split2<R>(den, dr[r], drl[r]);
+        split2<R>(t * den, di[r], dil[r]);
+      }
     }
-    if constexpr (!HB) diag_inverse();   // the diagonal does not depend on u
   }
   __device__ __forceinline__ void set_u(R u, const Cheb<R>&, int lg) {
 #pragma unroll
@@ -694,15 +734,18 @@ struct OpBitflipCN : OpBitflip<R, G_, E_> {
   using Base = OpBitflip<R, G_, E_>;
   static constexpr bool CN = true;
   static constexpr int E = E_, G = G_, Q = Base::Q;
-  R cdg[E_], dr[E_], di[E_], hh;
+  R cdg[E_], dr[E_], di[E_], drl[E_], dil[E_], th[E_], tl[E_], hh;
+  static constexpr bool CN_LO = sizeof(R) == 4;
   __device__ void scale(const double* H0d, int d, int lg, const Cheb<R>& ch) {
     hh = ch.h;
 #pragma unroll
-    for (int r = 0; r < E_; ++r) {
+    for (int r = 0; r < E_; ++r) {   // u-independent diagonal: coefficients in FP64, as hi + lo
       cdg[r] = (R)H0d[lg * E_ + r];
-      const R t = hh * cdg[r];
-      dr[r] = R(1) / fma(t, t, R(1));
-      di[r] = t * dr[r];
+      const double t = ch.hd * H0d[lg * E_ + r];
+      const double den = 1.0 / fma(t, t, 1.0);
+      split2<R>(t, th[r], tl[r]);
+      split2<R>(den, dr[r], drl[r]);
+      split2<R>(t * den, di[r], dil[r]);
     }
   }
   __device__ __forceinline__ void set_u(R u, const Cheb<R>&, int) {
@@ -730,6 +773,7 @@ struct OpDenseCN : OpDense<R, G_, E_> {
   static constexpr bool CN = true;
   static constexpr int E = E_, G = G_, DP = Base::DP;
   R cdg[E_], dr[E_], di[E_], hh;
+  static constexpr bool CN_LO = false;   // the diagonal depends on u
   __device__ void scale(const double*, int, int, const Cheb<R>& ch) { hh = ch.h; }
   __device__ __forceinline__ void set_u(R u, const Cheb<R>&, int) {
     this->u2 = u;   // mv<true> forms H0_ef + u H1_ef with s2 = 1

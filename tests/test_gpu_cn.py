@@ -237,10 +237,9 @@ def test_cn_mixed_states_gradient_iterate(P, name, w, step1):
 def test_cn_mixed_rotor_full_size(P):
     """The rotor at the benchmark's size (Nt = 20000, N = 128) with the FP32 Crank-Nicolson step: J and
     the gradient at u0 against the FP64 Crank-Nicolson oracle, batched direct sweeps and one problem.
-    J meets the mixed bar (1e-5); the gradient reaches 3e-4 relative, not 1e-4: the FP32 roundings of
-    tau H_ee / 2 and of the diagonal inverse repeat at every one of the 2 x 20000 global steps (the
-    Chebyshev path carries its diagonal and coefficients as hi + lo pairs and reaches 1e-5 here), so
-    this bound is the one pinned for the FP32 Cayley step."""
+    J meets the mixed bar (1e-5) and the gradient the 1e-4 relative one: tau H_ee / 2 and the Jacobi
+    diagonal inverse are formed in FP64 and carried as hi + lo pairs, since their FP32 roundings would
+    repeat at every one of the 2 x 20000 global steps (plain FP32 coefficients leave 3e-4 here)."""
     w = W.config("rotor41", precision="fp64")
     J_o, F_o = C.objective(w, w.u0)
     g_o = C.global_gradient(w, w.u0)
@@ -249,4 +248,5 @@ def test_cn_mixed_rotor_full_size(P):
             J, F = pl.evaluate(np.broadcast_to(w.u0, (batch, w.Nt)))
             g, _ = pl.gradient(np.broadcast_to(w.u0, (batch, w.Nt)))
         assert np.max(np.abs(J - J_o)) <= 1e-5 and np.max(np.abs(F - F_o)) <= 1e-5
-        assert max(rel_l2(g[b], g_o) for b in range(batch)) <= 5e-4
+        err = max(rel_l2(g[b], g_o) for b in range(batch))
+        assert err <= 1e-4, err
