@@ -99,8 +99,9 @@ typedef enum {
      (tau/2)(max off-diagonal row sum of H0 + max|u| that of H1) = rho, rho^K <= cheb_tol; a plan
      whose controls make rho >= 1/2 fails with ISM_EUNSUPPORTED).  The gradients are the exact
      derivatives of this discrete scheme, w (tau/2) Im<xi_j|H1|psi_j + psi_{j+1}> with
-     xi_j = (I - i tau H_j/2)^{-1} chi_{j+1}.  Both precisions (ISM_MIXED propagates in FP32: the
-     Cayley step is unitary by construction); the tridiagonal, dense and bit-flip kinds with
+     xi_j = (I - i tau H_j/2)^{-1} chi_{j+1}.  Both precisions (ISM_MIXED propagates in FP32, the
+     Cayley step being unitary by construction; a u-independent diagonal enters it through FP64
+     coefficients split into FP32 hi + lo pairs); the tridiagonal, dense and bit-flip kinds with
      d <= 64 (ISM_EUNSUPPORTED otherwise).                                                         */
   ISM_SCHEME_CRANK_NICOLSON = 1
 } ism_scheme;
