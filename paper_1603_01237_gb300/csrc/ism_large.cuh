@@ -1,5 +1,6 @@
-// ism_large.cuh -- the ISM path for state dimensions too large for one warp (spin chains of 7 to 11
-// sites, d = 2^q = 128 .. 2048) with diagonal H0 and bit-flip H1 = sum_i h_i X_i.
+// ism_large.cuh -- the ISM path for state dimensions too large for one warp (spin chains of 7 to 10
+// sites, d = 2^q = 128 .. 1024, the dimensions instantiated and accepted by ism_plan) with diagonal
+// H0 and bit-flip H1 = sum_i h_i X_i.
 //
 // One state is spread over a whole CTA of W warps, E contiguous elements per thread (element
 // e = t * E + r, t = threadIdx.x): the bits of e below log2(E) live in one thread, the next five in
