@@ -315,12 +315,15 @@ typedef struct {
 
 enum { ISM_REQ_QUEUED = 0, ISM_REQ_RUNNING = 1, ISM_REQ_DONE = 2, ISM_REQ_FAILED = 3 };
 
-/* ism_server_create -- start the workers on the current CUDA device.  ISM_EINVAL for bad options. */
+/* ism_server_create -- start the workers on the current CUDA device.  ISM_EINVAL for bad options,
+ *   ISM_ENOMEM if the server or its worker threads cannot be created (none is left running). */
 int ism_server_create(const ism_server_options* opt, ism_server_t* out);
 
 /* ism_server_submit -- queue a solve: ism_iterate(iters) from u0 ([batch][Nt]) on a plan for (prob,
  *   opt).  Every array of prob and u0 is copied before the call returns.  *id receives the request
- *   id.  Errors: those of ism_plan_footprint; ISM_ENOMEM if the request alone exceeds the budget. */
+ *   id.  Errors: those of ism_plan_footprint; ISM_ENOMEM if the request alone exceeds the budget or
+ *   its host copy cannot be allocated.  A plan or solve that fails later, in a worker, is reported by
+ *   ism_server_poll with the failing call's status and message. */
 int ism_server_submit(ism_server_t srv, const ism_problem* prob, const ism_options* opt, const double* u0,
                       int iters, long long* id);
 
@@ -332,7 +335,8 @@ int ism_server_submit(ism_server_t srv, const ism_problem* prob, const ism_optio
 int ism_server_poll(ism_server_t srv, long long id, int wait, int* state, double* u_out, double* J_hist,
                     double* times_ms);
 
-/* ism_server_release -- forget a finished request (its host copies are freed). */
+/* ism_server_release -- forget a finished request (its host copies are freed).  ISM_EINVAL for an
+ *   unknown id or a request that is still queued or running. */
 int ism_server_release(ism_server_t srv, long long id);
 
 /* ism_server_destroy -- finish the running solves, fail the queued ones, stop the workers. */

@@ -16,6 +16,7 @@
 #include <deque>
 #include <memory>
 #include <mutex>
+#include <new>
 #include <string>
 #include <thread>
 #include <unordered_map>
@@ -101,34 +102,15 @@ struct ism_server_s {
   }
 };
 
-extern "C" {
+namespace {
 
-int ism_server_create(const ism_server_options* opt, ism_server_t* out) {
-  if (!opt || !out) return ism::set_error(ISM_EINVAL, "null argument");
-  if (opt->slots < 1 || opt->slots > 64 || opt->hbm_budget_bytes == 0)
-    return ism::set_error(ISM_EINVAL, "slots must be 1..64 and the budget > 0");
-  auto* S = new (std::nothrow) ism_server_s();
-  if (!S) return ISM_ENOMEM;
-  S->o = *opt;
-  cudaGetDevice(&S->dev);
-  for (int i = 0; i < opt->slots; ++i) S->workers.emplace_back([S] { S->work(); });
-  *out = S;
-  return ISM_OK;
-}
-
-int ism_server_submit(ism_server_t S, const ism_problem* prob, const ism_options* opt, const double* u0, int iters,
-                      long long* id) {
-  if (!S || !prob || !opt || !u0 || !id || iters < 0) return ism::set_error(ISM_EINVAL, "null argument or iters < 0");
-  size_t bytes = 0;
-  int rc = ism_plan_footprint(prob, opt, &bytes);
-  if (rc != ISM_OK) return rc;
-  const int B = prob->batch < 1 ? 1 : prob->batch;
-  bytes += 16 * (size_t)B * ((size_t)iters + 1) + (1u << 20);   // history buffers and slack
-  if (bytes > S->o.hbm_budget_bytes)
-    return ism::set_error(ISM_ENOMEM, "the request's device footprint exceeds the server's whole budget");
+// Copies the request's problem, options and controls and queues it; returns its id.  Host
+// allocations here may throw std::bad_alloc, which the extern "C" caller turns into ISM_ENOMEM.
+long long enqueue_copy(ism_server_s* S, const ism_problem& p, const ism_options& opt, const double* u0, int iters,
+                       size_t bytes) {
   auto r = std::make_unique<Request>();
-  const ism_problem& p = *prob;
   const int d = p.d;
+  const int B = p.batch < 1 ? 1 : p.batch;
   const bool gp = p.kind == ISM_H_GRID_GP || p.kind == ISM_H_GRID_GP_DOUBLE_WELL;
   int q = 0;
   while ((1 << q) < d) ++q;
@@ -152,18 +134,71 @@ int ism_server_submit(ism_server_t S, const ism_problem* prob, const ism_options
   r->prob.psi_f = r->psi_f.empty() ? nullptr : r->psi_f.data();
   r->prob.O = r->O.empty() ? nullptr : r->O.data();
   r->prob.alpha = r->alpha.empty() ? nullptr : r->alpha.data();
-  r->opt = *opt;
+  r->opt = opt;
   r->u.assign(u0, u0 + (size_t)B * p.Nt * m);
   r->J.assign((size_t)B * ((size_t)iters + 1), 0.0);
   r->iters = iters;
   r->bytes = bytes;
   r->t_submit = now_ms();
-  {
-    std::lock_guard<std::mutex> lk(S->mu);
-    r->id = S->next_id++;
-    *id = r->id;
-    S->queue.push_back(r.get());
-    S->all.emplace(r->id, std::move(r));
+  std::lock_guard<std::mutex> lk(S->mu);
+  const long long rid = S->next_id++;
+  r->id = rid;
+  Request* raw = r.get();
+  S->all.emplace(rid, std::move(r));
+  try {
+    S->queue.push_back(raw);
+  } catch (...) {
+    S->all.erase(rid);
+    throw;
+  }
+  return rid;
+}
+
+}  // namespace
+
+extern "C" {
+
+int ism_server_create(const ism_server_options* opt, ism_server_t* out) {
+  if (!opt || !out) return ism::set_error(ISM_EINVAL, "null argument");
+  if (opt->slots < 1 || opt->slots > 64 || opt->hbm_budget_bytes == 0)
+    return ism::set_error(ISM_EINVAL, "slots must be 1..64 and the budget > 0");
+  auto* S = new (std::nothrow) ism_server_s();
+  if (!S) return ism::set_error(ISM_ENOMEM, "host memory for the server");
+  S->o = *opt;
+  cudaGetDevice(&S->dev);
+  try {
+    for (int i = 0; i < opt->slots; ++i) S->workers.emplace_back([S] { S->work(); });
+  } catch (...) {
+    // a worker thread could not be started: stop the ones that did and report it
+    {
+      std::lock_guard<std::mutex> lk(S->mu);
+      S->stop = true;
+    }
+    S->cv.notify_all();
+    for (auto& t : S->workers) t.join();
+    delete S;
+    return ism::set_error(ISM_ENOMEM, "could not start the server's worker threads");
+  }
+  *out = S;
+  return ISM_OK;
+}
+
+int ism_server_submit(ism_server_t S, const ism_problem* prob, const ism_options* opt, const double* u0, int iters,
+                      long long* id) {
+  if (!S || !prob || !opt || !u0 || !id || iters < 0) return ism::set_error(ISM_EINVAL, "null argument or iters < 0");
+  size_t bytes = 0;
+  int rc = ism_plan_footprint(prob, opt, &bytes);
+  if (rc != ISM_OK) return rc;
+  const int B = prob->batch < 1 ? 1 : prob->batch;
+  bytes += 16 * (size_t)B * ((size_t)iters + 1) + (1u << 20);   // history buffers and slack
+  if (bytes > S->o.hbm_budget_bytes)
+    return ism::set_error(ISM_ENOMEM, "the request's device footprint exceeds the server's whole budget");
+  try {
+    *id = enqueue_copy(S, *prob, *opt, u0, iters, bytes);
+  } catch (const std::bad_alloc&) {
+    return ism::set_error(ISM_ENOMEM, "host memory for the request's copy of its problem");
+  } catch (...) {
+    return ism::set_error(ISM_EINVAL, "the request could not be queued");
   }
   S->cv.notify_all();
   return ISM_OK;
@@ -171,7 +206,7 @@ int ism_server_submit(ism_server_t S, const ism_problem* prob, const ism_options
 
 int ism_server_poll(ism_server_t S, long long id, int wait, int* state, double* u_out, double* J_hist,
                     double* times_ms) {
-  if (!S || !state) return ISM_EINVAL;
+  if (!S || !state) return ism::set_error(ISM_EINVAL, "null argument");
   std::unique_lock<std::mutex> lk(S->mu);
   auto it = S->all.find(id);
   if (it == S->all.end()) return ism::set_error(ISM_EINVAL, "unknown request id");
@@ -192,12 +227,12 @@ int ism_server_poll(ism_server_t S, long long id, int wait, int* state, double* 
 }
 
 int ism_server_release(ism_server_t S, long long id) {
-  if (!S) return ISM_EINVAL;
+  if (!S) return ism::set_error(ISM_EINVAL, "null argument");
   std::lock_guard<std::mutex> lk(S->mu);
   auto it = S->all.find(id);
-  if (it == S->all.end()) return ISM_EINVAL;
+  if (it == S->all.end()) return ism::set_error(ISM_EINVAL, "unknown request id");
   const int st = it->second->state;
-  if (st != ISM_REQ_DONE && st != ISM_REQ_FAILED) return ISM_EINVAL;
+  if (st != ISM_REQ_DONE && st != ISM_REQ_FAILED) return ism::set_error(ISM_EINVAL, "the request has not finished");
   S->all.erase(it);
   return ISM_OK;
 }

@@ -206,3 +206,44 @@ def test_double_well_kind_validated_on_the_host(lib):
     with pytest.raises(abi.IsmError) as ei:
         abi.footprint(w.with_(dw=-1.0))
     assert ei.value.status == abi.ISM_EINVAL
+
+
+def test_server_validates_options_requests_and_ids_on_the_host(lib):
+    """The serving loop's host-side checks (ism_server_*): bad options, a request larger than the
+    whole budget, unknown request ids; nothing here reaches the device."""
+    import workloads as W
+    from paper_1603_01237_gb300 import abi
+
+    for slots, budget in ((0, 1 << 30), (65, 1 << 30), (2, 0)):
+        with pytest.raises(abi.IsmError) as ei:
+            abi.Server(slots=slots, hbm_budget_bytes=budget)
+        assert ei.value.status == abi.ISM_EINVAL
+    with abi.Server(slots=2, hbm_budget_bytes=1 << 20) as srv:
+        with pytest.raises(abi.IsmError) as ei:      # footprint + history + slack > 1 MiB
+            srv.submit(W.config("rotor41", Nt=2000, N=16), iters=2)
+        assert ei.value.status == abi.ISM_ENOMEM and "budget" in str(ei.value)
+        st = C.c_int()
+        assert lib.ism_server_poll(srv.handle, C.c_longlong(12345), 0, C.byref(st), None, None, None) == abi.ISM_EINVAL
+        assert b"unknown request id" in lib.ism_last_error()
+        assert lib.ism_server_release(srv.handle, C.c_longlong(12345)) == abi.ISM_EINVAL
+
+
+def test_server_reports_a_failed_request_without_a_gpu(lib):
+    """With no CUDA device the request is admitted, its plan fails in the worker, and poll() returns
+    the plan's error: the failure travels back through the queue instead of hanging or aborting."""
+    import torch
+
+    import workloads as W
+    from paper_1603_01237_gb300 import abi
+
+    if torch.cuda.is_available():
+        pytest.skip("a CUDA device is present: the request would run (covered by the GPU serving tests)")
+    with abi.Server(slots=2, hbm_budget_bytes=1 << 30) as srv:
+        rid = srv.submit(W.config("spin16", Nt=100, N=4), iters=1)
+        with pytest.raises(abi.IsmError) as ei:
+            srv.poll(rid, wait=True)
+        assert ei.value.status == abi.ISM_ECUDA
+        state = C.c_int()
+        lib.ism_server_poll(srv.handle, C.c_longlong(rid), 0, C.byref(state), None, None, None)
+        assert state.value == abi.ISM_REQ_FAILED
+        assert lib.ism_server_release(srv.handle, C.c_longlong(rid)) == abi.ISM_OK
