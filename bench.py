@@ -264,10 +264,13 @@ def run_reference(args):
     value = len(times) * scale / tot * 1.0    # full-size ISM iterations per second
     line = {
         "impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": args.gpus,
-        "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 / value, "higher_is_better": True,
-        "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+        # ms_per_step is the measured wall time of one timed step (one sample iteration); value scales
+        # the sample's rate to full-size iterations, so value != 1000 / ms_per_step here
+        "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * tot / len(times),
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
         "config": {"workload": f"{args.config}: {DESCR.get(args.config, args.config)} (d={dim_of(full)}), "
-                               f"T={full.T:g}, Nt={full.Nt}, N={full.N}, one problem", "precision": "fp64 (oracle)"},
+                               f"T={full.T:g}, Nt={full.Nt}, N={full.N}, one problem", "precision": "fp64 (oracle)",
+                   "step": sample},
         "cpu_baseline": {"value": value, "unit": UNIT, "cores": 1, "kind": "oracle", "sample": sample},
         "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
     }
