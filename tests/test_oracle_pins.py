@@ -233,6 +233,19 @@ def test_err_is_l1_of_subgradients():
     assert np.isclose(err, np.abs(g).sum(), rtol=1e-14)
 
 
+@pytest.mark.parametrize("L", [1, 3])
+def test_err_is_taken_at_the_first_local_step(L):
+    """Err (Algorithm 1 (e), read as the sub-gradients at u^(k)) does not depend on the number of
+    local steps, and by Theorem 2 equals sum_j |g_j| / beta_n(j) with g the full-interval gradient
+    (an uneven partition, so that the beta_n differ)."""
+    w = W.random_dense(4, 55, T=2.0, Nt=31, N=4)
+    j, _, _, _, beta = O.interval_weights(w.T, w.Nt, w.N)
+    g_full = O.global_gradient(w, w.u0)
+    expected = sum(np.abs(g_full[j[n]:j[n + 1]]).sum() / beta[n] for n in range(w.N))
+    _, err, _ = O.ism_iteration(w, w.u0, 0.2, L=L)
+    assert np.isclose(err, expected, rtol=1e-11)
+
+
 # --------------------------------------------------------------------- benchmark configurations
 def test_spin16_step_size_is_monotone():
     w = W.config("spin16", iters=6)
