@@ -226,7 +226,7 @@ Bounds bounds_of(int kind, int d, const double* H0, const double* H1) {
     }
   } else if (kind == ISM_H_BITFLIP) {
     int q = 0;
-    while ((1 << q) < d) ++q;
+    while (q < 30 && (1 << q) < d) ++q;
     for (int e = 0; e < d; ++e) { b.lo = std::fmin(b.lo, H0[e]); b.hi = std::fmax(b.hi, H0[e]); }
     for (int i = 0; i < q; ++i) b.h1 += std::fabs(H1[i]);
   } else if (kind == ISM_H_PAULI) {   // the controls' bound is taken per sub-interval on the device
@@ -263,7 +263,7 @@ std::vector<R> pack_op(int kind, int d, const double* H0, const double* H1, int 
     for (int e = 0; e < d; ++e) out[e] = (R)H0[e];
   } else if (kind == ISM_H_BITFLIP) {
     int q = 0;
-    while ((1 << q) < d) ++q;
+    while (q < 30 && (1 << q) < d) ++q;
     out.assign((size_t)d + q, R(0));
     for (int e = 0; e < d; ++e) out[e] = (R)H0[e];
     for (int i = 0; i < q; ++i) out[d + i] = (R)H1[i];
@@ -295,7 +295,7 @@ int validate_problem(const ism_problem& p, int precision) {
   if (p.kind == ISM_H_PAULI) {
     const int m = p.controls < 1 ? 1 : p.controls;
     int q = 0;
-    while ((1 << q) < d) ++q;
+    while (q < 30 && (1 << q) < d) ++q;
     if ((1 << q) != d) return fail(ISM_EINVAL, "the Pauli kind needs d = 2^q");
     if (d < 128 || d > 1024) return fail(ISM_EUNSUPPORTED, "this build supports the Pauli kind for d = 128 .. 1024");
     if (!p.H0 || !p.H1 || !p.psi_i || !p.psi_f) return fail(ISM_EINVAL, "H0, H1, psi_i and psi_f are required");
@@ -327,7 +327,7 @@ int validate_problem(const ism_problem& p, int precision) {
   if (precision != ISM_FP64 && precision != ISM_MIXED) return fail(ISM_EINVAL, "unknown precision");
   int q = 0;
   if (p.kind == ISM_H_BITFLIP) {
-    while ((1 << q) < d) ++q;
+    while (q < 30 && (1 << q) < d) ++q;
     if ((1 << q) != d || d < 2) return fail(ISM_EINVAL, "bit-flip kind needs d = 2^q >= 2");
     if (d > 1024) return fail(ISM_EUNSUPPORTED, "this build supports bit-flip d <= 1024");
   } else if (d > 64) {
@@ -637,7 +637,7 @@ int plan_build(const ism_problem* prob, const ism_options* opt, void* cuda_strea
   if (p.kind == ISM_H_PAULI) {
     P->pauli = true;
     P->m = p.controls < 1 ? 1 : p.controls;
-    while ((1 << P->q) < d) ++P->q;
+    while (P->q < 30 && (1 << P->q) < d) ++P->q;
   }
   bool h1diag = true;
   if (p.kind == ISM_H_TRIDIAG) {
@@ -677,7 +677,7 @@ int plan_build(const ism_problem* prob, const ism_options* opt, void* cuda_strea
       }
     } else if (p.kind == ISM_H_BITFLIP) {   // H0 diagonal; every row of H1 holds |h_i| once per flip
       int q = 0;
-      while ((1 << q) < d) ++q;
+      while (q < 30 && (1 << q) < d) ++q;
       for (int i = 0; i < q; ++i) P->h1n += std::fabs(p.H1[i]);
     } else {   // dense
       for (int e = 0; e < d; ++e) {

@@ -113,7 +113,7 @@ long long enqueue_copy(ism_server_s* S, const ism_problem& p, const ism_options&
   const int B = p.batch < 1 ? 1 : p.batch;
   const bool gp = p.kind == ISM_H_GRID_GP || p.kind == ISM_H_GRID_GP_DOUBLE_WELL;
   int q = 0;
-  while ((1 << q) < d) ++q;
+  while (q < 30 && (1 << q) < d) ++q;
   const size_t nH0 = gp ? (p.kind == ISM_H_GRID_GP_DOUBLE_WELL ? 4 : 3) : p.kind == ISM_H_DENSE ? (size_t)d * d : p.kind == ISM_H_TRIDIAG ? 2 * (size_t)d - 1 : (size_t)d;
   const size_t m = p.kind == ISM_H_PAULI && p.controls > 1 ? (size_t)p.controls : 1;
   const size_t nH1 = gp ? 0

@@ -101,6 +101,22 @@ def test_bitflip_needs_power_of_two(lib):
     assert lib.ism_plan(C.byref(prob), C.byref(opt), None, C.byref(h)) == abi.ISM_EINVAL
 
 
+@pytest.mark.parametrize("kind_name", ["ISM_H_BITFLIP", "ISM_H_PAULI"])
+@pytest.mark.parametrize("d,status", [(2 ** 31 - 1, 1), (2 ** 30 + 1, 1), (2 ** 30, 6), (2048, 6)])
+def test_power_of_two_kinds_reject_huge_d(lib, kind_name, d, status):
+    """The kinds with d = 2^q take q from d on the host; a d near the int range must give an error
+    (not a power of two: ISM_EINVAL; a power of two above 1024: ISM_EUNSUPPORTED), before any array
+    of that size is read."""
+    from paper_1603_01237_gb300 import abi
+
+    prob, keep = _problem(abi, kind=getattr(abi, kind_name))
+    prob.d = d
+    opt = abi.IsmOptions(precision=0, local_iters=1, rho=0.1, cheb_tol=0.0, max_spin_iters=0, subproblem_form=0)
+    n = C.c_size_t()
+    assert lib.ism_plan_footprint(C.byref(prob), C.byref(opt), C.byref(n)) == status
+    assert len(lib.ism_last_error()) > 0
+
+
 def test_null_arguments(lib):
     from paper_1603_01237_gb300 import abi
 
