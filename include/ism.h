@@ -284,7 +284,8 @@ long long ism_plan_info(ism_plan_t plan, int key);
  *   it keeps the last call's contents (the status word is cleared on entry); calls whose work
  *   overlaps on the GPU race on it.  A problem needing more scratch than the array holds is rejected
  *   with ISM_EINVAL and a message giving both sizes; host pointers for phi, u, grad or Jn give
- *   ISM_EINVAL.  Other errors as ism_subinterval_grad.
+ *   ISM_EINVAL.  Covers the dense, tridiagonal and bit-flip kinds with d <= 64 (the Chebyshev step);
+ *   other kinds and larger d give ISM_EUNSUPPORTED.  Other errors as ism_subinterval_grad.
  */
 #define ISM_NOALLOC_SCRATCH_BYTES (32u << 20)
 int ism_subinterval_grad_noalloc(const ism_problem* prob, int precision, const double* phi, const double* u,

@@ -70,6 +70,10 @@ extern "C" int ism_subinterval_grad_noalloc(const ism_problem* prob, int precisi
   const ism_problem& p = *prob;
   int rc = ism::validate_problem(p, precision);
   if (rc != ISM_OK) return rc;
+  // the kernels below read a packed H0/H1 of the dense, tridiagonal or bit-flip layout: the grid kinds
+  // (H0 = a few grid parameters, H1 unused) and the Pauli kind have other layouts and other sweeps
+  if (p.kind != ISM_H_DENSE && p.kind != ISM_H_TRIDIAG && p.kind != ISM_H_BITFLIP)
+    return ism::set_error(ISM_EUNSUPPORTED, "the allocation-free entry point covers the dense, tridiagonal and bit-flip kinds");
   if (!is_device_ptr(phi) || !is_device_ptr(u) || !is_device_ptr(grad) || (Jn && !is_device_ptr(Jn)))
     return ism::set_error(ISM_EINVAL, "phi, u, grad and Jn must be device memory for the allocation-free entry point");
   ism::KernelSet ks;

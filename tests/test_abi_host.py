@@ -117,6 +117,24 @@ def test_power_of_two_kinds_reject_huge_d(lib, kind_name, d, status):
     assert len(lib.ism_last_error()) > 0
 
 
+def test_noalloc_entry_point_refuses_other_kinds_on_the_host(lib):
+    """The allocation-free entry point runs the Chebyshev sweep of the dense, tridiagonal and bit-flip
+    layouts: a grid problem (H0 = three grid parameters, no H1) or a Pauli problem is refused before
+    any array is read or any device memory is touched."""
+    import workloads as W
+    from paper_1603_01237_gb300 import abi
+
+    gp = W.gp_bec(n=64, Nt=40, N=4, steps=50)
+    pauli = W.random_pauli(7, 2, 5, T=1.0, Nt=40, N=4)
+    dummy = np.zeros(2 * 2 * 5 * 128)
+    for w in (gp, pauli):
+        prob, opt, keep = abi.problem_and_options(w, precision="fp64")
+        rc = lib.ism_subinterval_grad_noalloc(C.byref(prob), 0, dummy.ctypes.data, dummy.ctypes.data,
+                                              dummy.ctypes.data, None, None)
+        assert rc == abi.ISM_EUNSUPPORTED
+        assert "dense, tridiagonal and bit-flip" in lib.ism_last_error().decode()
+
+
 def test_null_arguments(lib):
     from paper_1603_01237_gb300 import abi
 
