@@ -340,7 +340,10 @@ int ism_server_poll(ism_server_t srv, long long id, int wait, int* state, double
  *   unknown id or a request that is still queued or running. */
 int ism_server_release(ism_server_t srv, long long id);
 
-/* ism_server_destroy -- finish the running solves, fail the queued ones, stop the workers. */
+/* ism_server_destroy -- finish the running solves, fail the queued ones, stop the workers and free
+ *   the server.  The caller must make sure that no other call on srv is in progress (in particular
+ *   no thread blocked in ism_server_poll with wait != 0) and that none starts afterwards: srv is
+ *   freed on return. */
 int ism_server_destroy(ism_server_t srv);
 
 #ifdef __cplusplus
