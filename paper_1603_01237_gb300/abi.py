@@ -123,8 +123,13 @@ def _check(rc: int):
         raise IsmError(rc, msg)
 
 
+_ARRAY_DTYPES = ("float64", "complex128")   # every array of the C ABI is double (complex: interleaved pairs)
+
+
 def _ptr(x):
-    """Address of a numpy array / torch tensor (host or device), or None."""
+    """Address of a numpy array / torch tensor (host or device), or None.  Only float64 and complex128
+    data are accepted: the library reads every array as doubles, so a narrower type would be read past
+    its end."""
     if x is None:
         return None
     if isinstance(x, int):
@@ -132,10 +137,14 @@ def _ptr(x):
     if isinstance(x, np.ndarray):
         if not x.flags["C_CONTIGUOUS"]:
             raise ValueError("arrays must be C-contiguous")
+        if x.dtype.name not in _ARRAY_DTYPES:
+            raise TypeError(f"arrays must be float64 or complex128, not {x.dtype.name}")
         return x.ctypes.data
     if hasattr(x, "data_ptr"):
         if not x.is_contiguous():
             raise ValueError("tensors must be contiguous")
+        if str(x.dtype).replace("torch.", "") not in _ARRAY_DTYPES:
+            raise TypeError(f"tensors must be float64 or complex128, not {x.dtype}")
         return x.data_ptr()
     raise TypeError(f"unsupported array type {type(x)}")
 

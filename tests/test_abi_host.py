@@ -135,6 +135,28 @@ def test_noalloc_entry_point_refuses_other_kinds_on_the_host(lib):
         assert "dense, tridiagonal and bit-flip" in lib.ism_last_error().decode()
 
 
+def test_binding_accepts_only_double_arrays():
+    """The C ABI reads every array as doubles: the binding refuses narrower element types (which the
+    library would read past their end) and non-contiguous data, host or torch."""
+    import torch
+
+    from paper_1603_01237_gb300 import abi
+
+    assert abi._ptr(None) is None
+    assert abi._ptr(np.zeros(4)) > 0
+    assert abi._ptr(np.zeros(4, dtype=np.complex128)) > 0
+    assert abi._ptr(torch.zeros(4, dtype=torch.float64)) > 0
+    assert abi._ptr(torch.zeros(4, dtype=torch.complex128)) > 0
+    for bad in (np.zeros(4, dtype=np.float32), np.zeros(4, dtype=np.int64), np.zeros(4, dtype=np.complex64),
+                torch.zeros(4, dtype=torch.float32), torch.zeros(4, dtype=torch.int32)):
+        with pytest.raises(TypeError):
+            abi._ptr(bad)
+    with pytest.raises(ValueError):
+        abi._ptr(np.zeros((4, 4))[:, 0])
+    with pytest.raises(ValueError):
+        abi._ptr(torch.zeros(4, 4, dtype=torch.float64).t())
+
+
 def test_null_arguments(lib):
     from paper_1603_01237_gb300 import abi
 
