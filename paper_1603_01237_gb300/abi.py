@@ -149,6 +149,19 @@ def _ptr(x):
     raise TypeError(f"unsupported array type {type(x)}")
 
 
+def _doubles(x) -> int:
+    """Number of doubles an array or tensor holds (a complex128 element is two)."""
+    if isinstance(x, np.ndarray):
+        return int(x.size) * (2 if x.dtype.name == "complex128" else 1)
+    return int(x.numel()) * (2 if str(x.dtype).endswith("complex128") else 1)
+
+
+def _need(x, n: int, name: str):
+    """Refuse an array shorter than the n doubles the library will read or write through it."""
+    if x is not None and not isinstance(x, int) and _doubles(x) < n:
+        raise ValueError(f"{name} holds {_doubles(x)} doubles; this plan needs {n}")
+
+
 def _c128_interleaved(v) -> np.ndarray:
     v = np.ascontiguousarray(np.asarray(v, dtype=np.complex128))
     return v.view(np.float64).copy()
@@ -281,19 +294,41 @@ class Plan:
         self.handle = h
 
     # ---------------------------------------------------------------- raw entry points (same names)
+    # Each checks that its arrays hold at least the doubles the call reads or writes (layouts of ism.h).
+    def _n_u(self) -> int:
+        return self.batch * self.Nt * self.m
+
+    def _n_phi(self) -> int:
+        return self.batch * (2 if self.gp else 1) * (self.N + 1) * 2 * self.d
+
     def ism_intermediate_states(self, u, phi):
+        _need(u, self._n_u(), "u")
+        _need(phi, self._n_phi(), "phi")
         _check(load().ism_intermediate_states(self.handle, _ptr(u), _ptr(phi)))
 
     def ism_subinterval_grad(self, phi, u, grad, Jn=None):
+        _need(phi, self._n_phi(), "phi")
+        _need(u, self._n_u(), "u")
+        _need(grad, self._n_u(), "grad")
+        _need(Jn, self.batch * self.N, "Jn")
         _check(load().ism_subinterval_grad(self.handle, _ptr(phi), _ptr(u), _ptr(grad), _ptr(Jn)))
 
     def ism_iterate(self, iters, u_inout, J_hist=None, err_hist=None):
+        _need(u_inout, self._n_u(), "u_inout")
+        _need(J_hist, self.batch * (int(iters) + 1), "J_hist")
+        _need(err_hist, self.batch * int(iters), "err_hist")
         _check(load().ism_iterate(self.handle, int(iters), _ptr(u_inout), _ptr(J_hist), _ptr(err_hist)))
 
     def ism_evaluate(self, u, J=None, F=None):
+        _need(u, self._n_u(), "u")
+        _need(J, self.batch, "J")
+        _need(F, self.batch, "F")
         _check(load().ism_evaluate(self.handle, _ptr(u), _ptr(J), _ptr(F)))
 
     def ism_gradient(self, u, grad, J=None):
+        _need(u, self._n_u(), "u")
+        _need(grad, self._n_u(), "grad")
+        _need(J, self.batch, "J")
         _check(load().ism_gradient(self.handle, _ptr(u), _ptr(grad), _ptr(J)))
 
     def ism_set_profiling(self, on: bool):

@@ -157,6 +157,39 @@ def test_binding_accepts_only_double_arrays():
         abi._ptr(torch.zeros(4, 4, dtype=torch.float64).t())
 
 
+@pytest.mark.parametrize("gp,m", [(False, 1), (True, 1), (False, 3)])
+def test_plan_methods_refuse_short_arrays(lib, gp, m):
+    """The raw Plan methods pass bare pointers, so each first checks that every array holds the doubles
+    ism.h's layout gives it ([batch][Nt](*m) controls and gradients, [batch](*2)*(N+1)*2d states,
+    [batch][iters+1] and [batch][iters] histories); a short array is refused before the library is
+    called (no plan is needed for that: this one has no handle)."""
+    from paper_1603_01237_gb300 import abi
+
+    pl = object.__new__(abi.Plan)
+    pl.handle, pl.batch, pl.Nt, pl.N, pl.d, pl.gp, pl.m = None, 3, 20, 4, 8, gp, m
+    nu, nphi = 3 * 20 * m, 3 * (2 if gp else 1) * 5 * 2 * 8
+    u, g, phi = np.zeros(nu), np.zeros(nu), np.zeros(nphi)
+    short = lambda n: np.zeros(n - 1)   # noqa: E731
+    cases = [
+        lambda: pl.ism_intermediate_states(short(nu), phi),
+        lambda: pl.ism_intermediate_states(u, short(nphi)),
+        lambda: pl.ism_intermediate_states(u, np.zeros(nphi // 2 - 1, dtype=np.complex128)),
+        lambda: pl.ism_subinterval_grad(phi, u, short(nu)),
+        lambda: pl.ism_subinterval_grad(phi, u, g, short(3 * 4)),
+        lambda: pl.ism_iterate(5, short(nu)),
+        lambda: pl.ism_iterate(5, u, short(3 * 6)),
+        lambda: pl.ism_iterate(5, u, None, short(3 * 5)),
+        lambda: pl.ism_evaluate(u, short(3)),
+        lambda: pl.ism_gradient(u, short(nu)),
+    ]
+    for call in cases:
+        with pytest.raises(ValueError):
+            call()
+    # arrays of the right size reach the library, which refuses the missing plan
+    with pytest.raises(abi.IsmError):
+        pl.ism_subinterval_grad(np.zeros(nphi // 2, dtype=np.complex128), u, g, np.zeros(3 * 4))
+
+
 def test_null_arguments(lib):
     from paper_1603_01237_gb300 import abi
 
