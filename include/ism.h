@@ -133,8 +133,9 @@ typedef struct {
   int max_spin_iters;      /* iteration cap for device-side waits; 0 = default                    */
   int subproblem_form;     /* gradient of the first local step in ism_iterate:
                               1 = literal sub-problem (psi_n from phi_n, chi_n from phi_{n+1});
-                              2 = the two-trajectory form of the proof of Theorem 2 (psi from psi(t_n),
-                                  chi from chi(t_{n+1}), scaled by 1/beta_n): identical at phi = phi^u
+                              2 = the two-trajectory form of the proof of Theorem 2 (psi from psi(t_n)
+                                  and chi from chi(t_n), both propagated forward, scaled by 1/beta_n;
+                                  nothing per step is stored but one overlap): identical at phi = phi^u
                                   in exact arithmetic, and free of the O(1/N) cancellation of
                                   phi_{n+1} - psi_n(t_{n+1}) that FP32 propagation cannot resolve;
                               0 = default: 2 in ISM_MIXED, 1 in ISM_FP64.  Later local steps
@@ -148,6 +149,14 @@ typedef struct {
                                   lane group, for throughput, rather than in two concurrent ones);
                               0 = default: 2 when batch >= 96, else 1.  Larger d always sweeps. */
   int scheme;              /* ism_scheme: time step of the piecewise-constant propagation          */
+  int ckpt_stride;         /* literal sub-problems (d <= 64): the forward sweep of sub-interval n
+                              stores psi_n every ckpt_stride steps and the adjoint sweep recomputes
+                              each segment of ckpt_stride steps from its stored state, so a
+                              sub-problem holds ceil(n_steps / S) states and S vectors H1 psi_n
+                              instead of its whole trajectory (the first local step of the
+                              two-trajectory form stores no states at all: it recomputes each
+                              segment from psi(t_n), chi(t_n)).  0 = default, ceil(sqrt(longest
+                              sub-interval)); values above the longest sub-interval are clamped.  */
 } ism_options;
 
 typedef struct ism_plan_s* ism_plan_t;
@@ -272,20 +281,24 @@ long long ism_plan_info(ism_plan_t plan, int key);
  *   allocate device memory (code inside another framework's memory pool, allocation-free real-time
  *   loops, processes with a device-memory budget fixed up front).  The paper has no counterpart: it
  *   is an addition of this library.  Needs no plan and calls no cudaMalloc, cudaFree or allocating
- *   library routine: all scratch (packed Hamiltonian, partition, penalty weights, status word and the
- *   per-step H1 psi trajectory) lives in one static device array of ISM_NOALLOC_SCRATCH_BYTES that
- *   every GPU loading the library holds until the process exits.
+ *   library routine: all scratch (packed Hamiltonian, partition, penalty weights, status word, the
+ *   per-step overlaps and the checkpoints and segment buffer of the literal sub-problem) lives in one
+ *   static device array of ISM_NOALLOC_SCRATCH_BYTES that every GPU loading the library holds until
+ *   the process exits.  It launches the same kernels as ism_subinterval_grad on a plan of the same
+ *   problem and precision, with the default checkpoint stride, and gives the same results bit for bit.
  *   prob:      the problem (host struct and host arrays, as for ism_plan); precision: ism_precision.
- *   phi, u:    [batch][N+1][2d] and [batch][Nt] inputs, DEVICE memory.
- *   grad, Jn:  [batch][Nt] and [batch][N] (Jn may be NULL) outputs, DEVICE memory.
- *   cuda_stream: the stream the work is ordered on; the call returns after it has finished.
+ *   phi, u:    [batch][N+1][2d] and [batch][Nt] inputs, DEVICE memory of the current GPU.
+ *   grad, Jn:  [batch][Nt] and [batch][N] (Jn may be NULL) outputs, DEVICE memory of the current GPU.
+ *   cuda_stream: the stream the work is ordered on.  The call synchronises that stream and reads the
+ *   status word back before it returns, so it must not be called while the stream is being captured.
  *   The first call on a device looks up the array's device address (cudaGetSymbolAddress) with that
- *   device current; make that first call before any stream capture.  All calls share the array and
- *   it keeps the last call's contents (the status word is cleared on entry); calls whose work
- *   overlaps on the GPU race on it.  A problem needing more scratch than the array holds is rejected
- *   with ISM_EINVAL and a message giving both sizes; host pointers for phi, u, grad or Jn give
- *   ISM_EINVAL.  Covers the dense, tridiagonal and bit-flip kinds with d <= 64 (the Chebyshev step);
- *   other kinds and larger d give ISM_EUNSUPPORTED.  Other errors as ism_subinterval_grad.
+ *   device current.  All calls share the array and it keeps the last call's contents (the status word
+ *   is cleared on entry); calls whose work overlaps on the GPU race on it.  A problem needing more
+ *   scratch than the array holds is rejected with ISM_EINVAL and a message giving both sizes; host
+ *   pointers, or device memory of another GPU, for phi, u, grad or Jn give ISM_EINVAL; NaN or Inf in
+ *   u or phi gives ISM_ENONFINITE.  Covers the dense, tridiagonal and bit-flip kinds with d <= 64
+ *   (the Chebyshev step); other kinds and larger d give ISM_EUNSUPPORTED.  Other errors as
+ *   ism_subinterval_grad.
  */
 #define ISM_NOALLOC_SCRATCH_BYTES (32u << 20)
 int ism_subinterval_grad_noalloc(const ism_problem* prob, int precision, const double* phi, const double* u,

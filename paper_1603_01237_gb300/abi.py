@@ -41,7 +41,7 @@ class IsmProblem(C.Structure):
 class IsmOptions(C.Structure):
     _fields_ = [("precision", C.c_int), ("local_iters", C.c_int), ("rho", C.c_double),
                 ("cheb_tol", C.c_double), ("max_spin_iters", C.c_int), ("subproblem_form", C.c_int),
-                ("step1", C.c_int), ("scheme", C.c_int)]
+                ("step1", C.c_int), ("scheme", C.c_int), ("ckpt_stride", C.c_int)]
 
 
 class IsmStats(C.Structure):
@@ -207,6 +207,12 @@ def subinterval_grad_noalloc(w, precision: str, phi, u, grad, Jn=None, *, batch:
     the library uses only its static device scratch; phi, u, grad and Jn must be device buffers."""
     lib = load()
     k = kind or w.kind
+    B, Nt, N, d = int(batch), int(w.Nt), int(w.N), int(w.d)
+    # the kernels read and write these device buffers in place: refuse short ones
+    _need(phi, 2 * B * (N + 1) * d, "phi")
+    _need(u, B * Nt, "u")
+    _need(grad, B * Nt, "grad")
+    _need(Jn, B * N, "Jn")
     H0p, H1p = pack_hamiltonian(k, w.H0, w.H1)
     psi_i = _c128_interleaved(w.psi_i)
     psi_f = _c128_interleaved(w.psi_f) if w.objective == "overlap" else None
@@ -224,7 +230,7 @@ def subinterval_grad_noalloc(w, precision: str, phi, u, grad, Jn=None, *, batch:
 
 
 def problem_and_options(w, *, precision=None, batch=1, local_iters=None, rho=None, kind=None, cheb_tol=0.0,
-                        subproblem_form=0, step1=0, max_spin_iters=0, scheme="chebyshev"):
+                        subproblem_form=0, step1=0, max_spin_iters=0, scheme="chebyshev", ckpt_stride=0):
     """(ism_problem, ism_options, arrays to keep alive) for a workload object.  scheme: "chebyshev"
     (exact step) or "crank_nicolson" (the Sec. 3 step; FP64, d <= 64, not the grid kinds)."""
     kind = kind or w.kind
@@ -254,7 +260,8 @@ def problem_and_options(w, *, precision=None, batch=1, local_iters=None, rho=Non
     opt = IsmOptions(precision=ISM_FP64 if prec == "fp64" else ISM_MIXED,
                      local_iters=int(local_iters or w.local_iters), rho=float(w.rho if rho is None else rho),
                      cheb_tol=float(cheb_tol), max_spin_iters=int(max_spin_iters),
-                     subproblem_form=int(subproblem_form), step1=int(step1), scheme=_SCHEME[scheme])
+                     subproblem_form=int(subproblem_form), step1=int(step1), scheme=_SCHEME[scheme],
+                     ckpt_stride=int(ckpt_stride))
     return prob, opt, keep
 
 
@@ -272,7 +279,7 @@ class Plan:
     def __init__(self, w, *, precision: str | None = None, batch: int = 1, stream=None,
                  local_iters: int | None = None, rho: float | None = None, kind: str | None = None,
                  cheb_tol: float = 0.0, subproblem_form: int = 0, step1: int = 0, max_spin_iters: int = 0,
-                 scheme: str = "chebyshev"):
+                 scheme: str = "chebyshev", ckpt_stride: int = 0):
         lib = load()
         self.w = w
         self.kind = kind or w.kind
@@ -285,7 +292,8 @@ class Plan:
         prob, opt, self._keep = problem_and_options(w, precision=precision, batch=batch, local_iters=local_iters,
                                                     rho=rho, kind=kind, cheb_tol=cheb_tol,
                                                     subproblem_form=subproblem_form, step1=step1,
-                                                    max_spin_iters=max_spin_iters, scheme=scheme)
+                                                    max_spin_iters=max_spin_iters, scheme=scheme,
+                                                    ckpt_stride=ckpt_stride)
         h = C.c_void_p()
         st = None
         if stream is not None:

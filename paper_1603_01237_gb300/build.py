@@ -17,8 +17,10 @@ INCLUDE = os.path.join(ROOT, "include")
 BUILD = os.path.join(PKG, "_build")
 LIB = os.path.join(PKG, "libism.so")
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
-FLAGS = ["-O3", "-lineinfo", "-std=c++17", "-Xcompiler", "-fPIC", "-I", INCLUDE, "-I", CSRC,
-         "-diag-suppress", "177"]
+# host code: no floating-point contraction, so that x86-64 and aarch64 hosts (where gcc would fuse
+# a*b + c into an FMA at its own discretion) compute the plan's partition weights to the same bits
+FLAGS = ["-O3", "-lineinfo", "-std=c++17", "-Xcompiler", "-fPIC", "-Xcompiler", "-ffp-contract=off",
+         "-I", INCLUDE, "-I", CSRC, "-diag-suppress", "177"]
 
 
 def nvcc() -> str:

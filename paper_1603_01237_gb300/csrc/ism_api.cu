@@ -4,6 +4,7 @@
 #include <cmath>
 #include <cstdio>
 #include <cstring>
+#include <initializer_list>
 #include <string>
 #include <vector>
 
@@ -26,6 +27,24 @@ int fail(int code, const std::string& msg) {
 namespace ism {
 int set_error(int code, const char* msg) { return fail(code, msg); }
 void clear_error() { g_err.clear(); }
+
+void partition(double T, int Nt, int N, double c0, std::vector<int>* jn, std::vector<double>* beta,
+               std::vector<double2>* phase) {
+  const double tau = T / Nt;
+  jn->assign(N + 1, 0);
+  for (int n = 0; n <= N; ++n) (*jn)[n] = (int)(((long long)n * Nt) / N);
+  if (beta) {
+    beta->assign(N, 0.0);
+    for (int n = 0; n < N; ++n) (*beta)[n] = T / ((*jn)[n + 1] * tau - (*jn)[n] * tau);
+  }
+  if (phase) {
+    phase->assign(N, make_double2(1.0, 0.0));
+    for (int n = 0; n < N; ++n) {
+      const double ph = c0 * tau * (double)((*jn)[n + 1] - (*jn)[n]);
+      (*phase)[n] = make_double2(std::cos(ph), std::sin(ph));
+    }
+  }
+}
 }  // namespace ism
 
 namespace {
@@ -51,9 +70,21 @@ bool is_device_ptr(const void* p) {
   return a.type == cudaMemoryTypeDevice || a.type == cudaMemoryTypeManaged;
 }
 
-__global__ void k_check_finite(const double* x, long n, int* status) {
-  for (long i = blockIdx.x * (long)blockDim.x + threadIdx.x; i < n; i += (long)gridDim.x * blockDim.x)
-    if (!isfinite(x[i])) { atomicOr(status, ism::ST_NONFINITE); return; }
+// ISM_EINVAL when an argument is device memory of another GPU than the plan's: the kernels use device
+// arrays in place, and another GPU's memory would be a peer access (or a fault without peer access).
+int check_device_args(int dev, std::initializer_list<const void*> ptrs) {
+  for (const void* p : ptrs) {
+    if (!p) continue;
+    cudaPointerAttributes a;
+    if (cudaPointerGetAttributes(&a, p) != cudaSuccess) {
+      cudaGetLastError();
+      continue;
+    }
+    if (a.type == cudaMemoryTypeDevice && a.device != dev)
+      return fail(ISM_EINVAL, "an array argument is device memory of GPU " + std::to_string(a.device) +
+                                  ", not of the plan's GPU " + std::to_string(dev));
+  }
+  return ISM_OK;
 }
 
 // err_hist[b][k] = sum_n err[b][n]  (Algorithm 1 (e)), one warp per problem
@@ -111,6 +142,11 @@ struct ism_plan_s {
   double2* dphi = nullptr;
   void* dtraj = nullptr;
   void* dtraj2 = nullptr;
+  bool use_sw2 = false;             // first local steps by the concurrent two-trajectory sweeps
+  void* dzs = nullptr;              // [B][Nt+N] per-step overlaps of the sub-interval sweeps (R2)
+  void* dckpt = nullptr;            // literal sub-problem: checkpoints, allocated when first needed
+  void* dsegb = nullptr;            // literal sub-problem: H1 psi of one segment per (problem, n)
+  int cks = 1, nck = 1;             // checkpoint stride and checkpoints per sub-interval
   void* dzp = nullptr;              // large d: per-step, per-warp overlap partials
   double* du = nullptr;
   float* duf = nullptr;             // FP32 copy of the controls (FP32 propagation)
@@ -164,6 +200,27 @@ int dalloc(ism_plan_s* P, T** out, size_t count) {
   P->allocs.push_back(p);
   P->bytes += (bytes + 511) / 512 * 512;   // the same count as the footprint
   *out = reinterpret_cast<T*>(p);
+  return ISM_OK;
+}
+
+// The trajectories of the concurrent two-trajectory sweeps are stored per step; above this size the
+// first local steps run in k_subfwd instead, which stores one overlap per step.
+constexpr size_t kSweeps2MaxBytes = size_t(256) << 20;
+
+// Checkpoints and segment buffer of the literal sub-problem (d <= 64): ceil(ns/S) states (hi + lo in
+// FP32 propagation) and S vectors H1 psi per (problem, n).
+int alloc_literal(ism_plan_s* P) {
+  if (P->dckpt) return ISM_OK;
+  const size_t GE = (size_t)P->ks.G * P->ks.E, BN = (size_t)P->B * P->N;
+  const size_t parts = P->prec == ISM_FP64 ? 1 : 2;
+  unsigned char* c = nullptr;
+  unsigned char* sb = nullptr;
+  int rc = dalloc(P, &c, BN * P->nck * parts * GE * P->r2);
+  if (rc != ISM_OK) return rc;
+  rc = dalloc(P, &sb, BN * P->cks * GE * P->r2);
+  if (rc != ISM_OK) return rc;
+  P->dckpt = c;
+  P->dsegb = sb;
   return ISM_OK;
 }
 
@@ -411,6 +468,7 @@ ism::KParams kparams(ism_plan_s* P, double* u) {
   k.jn = P->djn; k.beta = P->dbeta; k.alpha = P->dalpha; k.H = P->dH; k.H0d = P->dH0d;
   k.cheb = P->dcheb; k.ctab = P->dctab; k.pen = P->dpen; k.phase = P->dphase;
   k.u = u; k.phi = P->dphi; k.M = P->dM; k.traj = P->dtraj; k.traj2 = P->dtraj2;
+  k.zs = P->dzs; k.ckpt = P->dckpt; k.segb = P->dsegb; k.cks = P->cks; k.nck = P->nck;
   k.grad = P->dgrad; k.Jn = P->dJn; k.err = P->derr; k.status = P->dstatus;
   k.count = P->dcount;
   k.psin = P->dpsin; k.chin = P->dchin; k.form = 0;
@@ -492,7 +550,7 @@ int stage_in(ism_plan_s* P, const double* src, long n, double* staging, const do
     if (check) {
       int blocks = (int)std::min<long>(1024, (n + 255) / 256);
       if (blocks < 1) blocks = 1;
-      k_check_finite<<<blocks, 256, 0, P->st>>>(src, n, P->dstatus);
+      ism::k_check_finite<<<blocks, 256, 0, P->st>>>(src, n, P->dstatus);
       P->kernels += 1;
       ISM_CUDA_TRY(cudaGetLastError());
     }
@@ -505,7 +563,7 @@ int stage_in(ism_plan_s* P, const double* src, long n, double* staging, const do
   if (check) {
     int blocks = (int)std::min<long>(1024, (n + 255) / 256);
     if (blocks < 1) blocks = 1;
-    k_check_finite<<<blocks, 256, 0, P->st>>>(staging, n, P->dstatus);
+    ism::k_check_finite<<<blocks, 256, 0, P->st>>>(staging, n, P->dstatus);
     P->kernels += 1;
     ISM_CUDA_TRY(cudaGetLastError());
   }
@@ -557,6 +615,7 @@ int plan_build(const ism_problem* prob, const ism_options* opt, void* cuda_strea
   if (opt->cheb_tol < 0.0) return fail(ISM_EINVAL, "cheb_tol must be >= 0");
   if (opt->subproblem_form < 0 || opt->subproblem_form > 2) return fail(ISM_EINVAL, "subproblem_form must be 0, 1 or 2");
   if (opt->step1 < 0 || opt->step1 > 2) return fail(ISM_EINVAL, "step1 must be 0, 1 or 2");
+  if (opt->ckpt_stride < 0) return fail(ISM_EINVAL, "ckpt_stride must be >= 0");
   if (opt->scheme != ISM_SCHEME_CHEBYSHEV && opt->scheme != ISM_SCHEME_CRANK_NICOLSON)
     return fail(ISM_EINVAL, "scheme must be ISM_SCHEME_CHEBYSHEV or ISM_SCHEME_CRANK_NICOLSON");
   if (opt->scheme == ISM_SCHEME_CRANK_NICOLSON &&
@@ -586,8 +645,8 @@ int plan_build(const ism_problem* prob, const ism_options* opt, void* cuda_strea
     P->gppot = p.kind == ISM_H_GRID_GP_DOUBLE_WELL ? 1 : 0;
     P->gpdw = P->gppot ? p.H0[3] : 0.0;
     P->r2 = P->prec == ISM_FP64 ? sizeof(double2) : sizeof(float2);
-    std::vector<int> jn(P->N + 1);
-    for (int n = 0; n <= P->N; ++n) jn[n] = (int)(((long long)n * P->Nt) / P->N);
+    std::vector<int> jn;
+    ism::partition(P->T, P->Nt, P->N, 0.0, &jn, nullptr, nullptr);
     int rc = ISM_OK;
     const size_t B = P->B;
 #define TRY_GP(ptr, n) if ((rc = dalloc(P, &(ptr), (n))) != ISM_OK) { free_all(P); delete P; return rc; }
@@ -696,10 +755,10 @@ int plan_build(const ism_problem* prob, const ism_options* opt, void* cuda_strea
   }
 
   // partition (Sec. 2): j_n = floor(n Nt / N), t_n = j_n tau, beta_n = T / (t_{n+1} - t_n)
-  std::vector<int> jn(P->N + 1);
-  for (int n = 0; n <= P->N; ++n) jn[n] = (int)(((long long)n * P->Nt) / P->N);
-  std::vector<double> beta(P->N);
-  for (int n = 0; n < P->N; ++n) beta[n] = P->T / (jn[n + 1] * P->tau - jn[n] * P->tau);
+  std::vector<int> jn;
+  std::vector<double> beta;
+  std::vector<double2> phase;   // the global phase of each segment, once per plan
+  ism::partition(P->T, P->Nt, P->N, P->c0, &jn, &beta, &phase);
 
   int rc = ISM_OK;
   const int GE = P->ks.G * P->ks.E;
@@ -746,14 +805,39 @@ int plan_build(const ism_problem* prob, const ism_options* opt, void* cuda_strea
   TRY_ALLOC(P->dchin, B * (P->N + 1) * (size_t)d);
   TRY_ALLOC(P->dphi, B * (P->N + 1) * (size_t)d);
   if (P->direct && !P->ks.large) TRY_ALLOC(P->dnrm, B * (P->N + 1) * 2);
-  unsigned char* dTb = nullptr;
-  TRY_ALLOC(dTb, B * ((size_t)P->Nt + P->N) * GE * P->r2);
-  P->dtraj = dTb;
-  if (!P->ks.large && !P->direct && P->ks.sweeps2) {   // second trajectory of the concurrent sweeps
-    unsigned char* dT2 = nullptr;
-    TRY_ALLOC(dT2, B * ((size_t)P->Nt + P->N) * GE * P->r2);
-    P->dtraj2 = dT2;
-  } else if (P->ks.large) {   // per-slot overlap partials: W warps, or the 2q bit overlaps (Pauli kind)
+  // checkpoint stride of the literal sub-problem (steps between stored states): by default about the
+  // square root of the longest sub-interval, which balances the checkpoints against the segment buffer
+  {
+    const int nsmax = (P->Nt + P->N - 1) / P->N;   // longest sub-interval of j_n = floor(n Nt / N)
+    int S = opt->ckpt_stride > 0 ? opt->ckpt_stride : (int)std::ceil(std::sqrt((double)nsmax));
+    P->cks = S < 1 ? 1 : (S > nsmax ? nsmax : S);
+    P->nck = (nsmax + P->cks - 1) / P->cks;
+  }
+  if (P->ks.large || P->pauli) {
+    unsigned char* dTb = nullptr;
+    TRY_ALLOC(dTb, B * ((size_t)P->Nt + P->N) * GE * P->r2);
+    P->dtraj = dTb;
+  } else {
+    unsigned char* dZ = nullptr;
+    TRY_ALLOC(dZ, B * ((size_t)P->Nt + P->N) * P->r2);
+    P->dzs = dZ;
+    if (P->form == 1 || P->L > 1) {   // ism_iterate runs literal sub-problems
+      if ((rc = alloc_literal(P)) != ISM_OK) { free_all(P); delete P; return rc; }
+    }
+    // first local steps of the assembly path (few problems: latency) by the concurrent sweeps, which
+    // store both sub-interval trajectories, while these stay small
+    const size_t tb = B * ((size_t)P->Nt + P->N) * GE * P->r2;
+    if (!P->direct && P->ks.sweeps2 && P->form == 2 && tb <= kSweeps2MaxBytes) {
+      unsigned char* dTb = nullptr;
+      TRY_ALLOC(dTb, tb);
+      P->dtraj = dTb;
+      unsigned char* dT2 = nullptr;
+      TRY_ALLOC(dT2, tb);
+      P->dtraj2 = dT2;
+      P->use_sw2 = true;
+    }
+  }
+  if (P->ks.large) {   // per-slot overlap partials: W warps, or the 2q bit overlaps (Pauli kind)
     unsigned char* dZ = nullptr;
     TRY_ALLOC(dZ, B * ((size_t)P->Nt + P->N) * (P->pauli ? 2 * P->q : P->ks.W) * P->r2);
     P->dzp = dZ;
@@ -797,11 +881,6 @@ int plan_build(const ism_problem* prob, const ism_options* opt, void* cuda_strea
     h2d(P->dctab, tab.data(), tab.size() * sizeof(double));
   }
   h2d(P->dbeta, beta.data(), beta.size() * sizeof(double));
-  std::vector<double2> phase(P->N);   // the global phase of each segment, once per plan
-  for (int n = 0; n < P->N; ++n) {
-    const double ph = P->c0 * P->tau * (double)(jn[n + 1] - jn[n]);
-    phase[n] = make_double2(std::cos(ph), std::sin(ph));
-  }
   h2d(P->dphase, phase.data(), phase.size() * sizeof(double2));
   {
     std::vector<double2> ab(P->N + 1);   // Eq. (cible): a_n = (T - t_n)/T, b_n = t_n/T
@@ -908,6 +987,7 @@ int ism_intermediate_states(ism_plan_t P, const double* u, double* phi) {
   if (!P || !u || !phi) return fail(ISM_EINVAL, "null argument");
   int rc = begin(P);
   if (rc) return rc;
+  if ((rc = check_device_args(P->dev, {u, phi}))) return rc;
   const double* ud = nullptr;
   if ((rc = stage_in(P, u, (long)P->B * P->Nt * P->m, P->du, &ud, true))) return rc;
   if ((rc = run_states(P, ud, nullptr, 0, 0))) return rc;
@@ -926,6 +1006,7 @@ int ism_subinterval_grad(ism_plan_t P, const double* phi, const double* u, doubl
   if (!P || !phi || !u || !grad) return fail(ISM_EINVAL, "null argument");
   int rc = begin(P);
   if (rc) return rc;
+  if ((rc = check_device_args(P->dev, {phi, u, grad, Jn}))) return rc;
   const double* ud = nullptr;
   if ((rc = stage_in(P, u, (long)P->B * P->Nt * P->m, P->du, &ud, true))) return rc;
   if (P->gp) {
@@ -949,6 +1030,7 @@ int ism_subinterval_grad(ism_plan_t P, const double* phi, const double* u, doubl
     if (!all_finite(phi, nphi)) return fail(ISM_ENONFINITE, "non-finite value in phi");
     ISM_CUDA_TRY(cudaMemcpyAsync(P->dphi, phi, nphi * sizeof(double), cudaMemcpyHostToDevice, P->st));
   }
+  if (!P->ks.large && !P->pauli && (rc = alloc_literal(P)) != ISM_OK) return rc;   // first literal use
   ism::KParams k = kparams(P, const_cast<double*>(ud));
   k.update = 0;
   k.count = P->dcount + 3;
@@ -965,6 +1047,7 @@ int ism_iterate(ism_plan_t P, int iters, double* u_inout, double* J_hist, double
   if (iters < 0) return fail(ISM_EINVAL, "iters must be >= 0");
   int rc = begin(P);
   if (rc) return rc;
+  if ((rc = check_device_args(P->dev, {u_inout, J_hist, err_hist}))) return rc;
   const long nu = (long)P->B * P->Nt * P->m;
   const bool dev_u = is_device_ptr(u_inout);
   double* ud = nullptr;
@@ -1000,7 +1083,7 @@ int ism_iterate(ism_plan_t P, int iters, double* u_inout, double* J_hist, double
         ISM_CUDA_TRY(prep_params(P, k));
         P->kernels += 1;
       }
-      if (k.form && !P->ks.large && !P->direct && P->ks.sweeps2)
+      if (k.form && P->use_sw2)
         ISM_CUDA_TRY(timed(P, 2, 2, [&] { return P->ks.sweeps2(k, P->st); }));
       else ISM_CUDA_TRY(timed(P, 2, 1, [&] { return P->ks.subinterval(k, P->st); }));
     }
@@ -1014,7 +1097,7 @@ int ism_iterate(ism_plan_t P, int iters, double* u_inout, double* J_hist, double
   if (!dev_u) {   // the updated controls: checked on the device, then copied back
     int blocks = (int)std::min<long>(1024, (nu + 255) / 256);
     if (blocks < 1) blocks = 1;
-    k_check_finite<<<blocks, 256, 0, P->st>>>(ud, nu, P->dstatus);
+    ism::k_check_finite<<<blocks, 256, 0, P->st>>>(ud, nu, P->dstatus);
     P->kernels += 1;
     ISM_CUDA_TRY(cudaGetLastError());
     ISM_CUDA_TRY(cudaMemcpyAsync(u_inout, ud, nu * sizeof(double), cudaMemcpyDeviceToHost, P->st));
@@ -1032,6 +1115,7 @@ int ism_gradient(ism_plan_t P, const double* u, double* grad, double* J) {
   if (!P || !u || !grad) return fail(ISM_EINVAL, "null argument");
   int rc = begin(P);
   if (rc) return rc;
+  if ((rc = check_device_args(P->dev, {u, grad, J}))) return rc;
   const double* ud = nullptr;
   if ((rc = stage_in(P, u, (long)P->B * P->Nt * P->m, P->du, &ud, true))) return rc;
   if ((rc = run_states(P, ud, nullptr, 0, 0))) return rc;
@@ -1046,7 +1130,7 @@ int ism_gradient(ism_plan_t P, const double* u, double* grad, double* J) {
     k.form = 1;
     k.global = 1;
     k.count = P->dcount + 3;
-    if (P->ks.large || P->direct || !P->ks.sweeps2) ISM_CUDA_TRY(timed(P, 2, 1, [&] { return P->ks.subinterval(k, P->st); }));
+    if (!P->use_sw2) ISM_CUDA_TRY(timed(P, 2, 1, [&] { return P->ks.subinterval(k, P->st); }));
     else ISM_CUDA_TRY(timed(P, 2, 2, [&] { return P->ks.sweeps2(k, P->st); }));
   }
   if ((rc = copy_out(P, grad, P->dgrad, (long)P->B * P->Nt * P->m))) return rc;
@@ -1058,6 +1142,7 @@ int ism_evaluate(ism_plan_t P, const double* u, double* J, double* F) {
   if (!P || !u) return fail(ISM_EINVAL, "null argument");
   int rc = begin(P);
   if (rc) return rc;
+  if ((rc = check_device_args(P->dev, {u, J, F}))) return rc;
   const double* ud = nullptr;
   if ((rc = stage_in(P, u, (long)P->B * P->Nt * P->m, P->du, &ud, true))) return rc;
   if ((rc = run_states(P, ud, nullptr, 0, 0))) return rc;

@@ -656,6 +656,26 @@ __device__ __forceinline__ void cn_step(Vec<R, E>& v, Vec<R, E>& xi, const Op& o
   }
 }
 
+// The adjoint of the Crank-Nicolson step propagated FORWARD (the two-trajectory form of a first local
+// step): lambda_{j+1} = U_j lambda_j with U_j = A_j^{-1} B_j, and since A_j and B_j commute the
+// quantity xi_j = B_j^{-1} lambda_{j+1} that the exact discrete gradient pairs with H1 (psi_j +
+// psi_{j+1}) equals A_j^{-1} lambda_j.  So: xi <- A^{-1} v (one solve), then v <- B xi (= U v).
+template <typename R, int E, class Op>
+__device__ __forceinline__ void cn_step_fwd_xi(Vec<R, E>& v, Vec<R, E>& xi, const Op& op, R h, int K) {
+  cn_solve(xi, v, op, h, R(1), K);
+  Vec<R, E> o;
+  op.template cn_apply<!Op::CN_LO>(xi, o);
+#pragma unroll
+  for (int e = 0; e < E; ++e) {   // v = xi - i h H xi
+    v.re[e] = fma(h, o.im[e], xi.re[e]);
+    v.im[e] = fma(-h, o.re[e], xi.im[e]);
+    if constexpr (Op::CN_LO) {
+      v.re[e] = fma(op.th[e], xi.im[e], fma(op.tl[e], xi.im[e], v.re[e]));
+      v.im[e] = fma(-op.th[e], xi.re[e], fma(-op.tl[e], xi.re[e], v.im[e]));
+    }
+  }
+}
+
 // Tridiagonal H with the Crank-Nicolson step of Sec. 3 in place of the Chebyshev series: the same lane
 // layout and packed data, but H = H0 + u H1 itself (no centring or scaling).  ah[] holds the H0
 // diagonal (scale), cdg/cof the diagonal and the (e, e+1) couplings of H at the current control.
@@ -942,6 +962,143 @@ __device__ __forceinline__ void cheb_step_p(VecP<E>& v, VecP<E>& lo, const Op& o
         const float2 bb = add2(sm, neg2(x));
         lo.z[r] = add2(add2(x, neg2(add2(sm, neg2(bb)))), add2(t, neg2(bb)));
         v.z[r] = sm;
+      }
+    }
+  }
+}
+
+// Two packed FP32 states stepped forward together under the same U_j (the two trajectories of a
+// sub-problem): the same series, sub-steps and compensation as cheb_step_p, with the recurrences of
+// the two states interleaved in one term loop, so that each supplies independent instructions while
+// the other waits on its shuffles.
+template <bool COMP, bool LOC = true, bool DL = true, int E, class Op>
+__device__ __forceinline__ void cheb_step_p2(VecP<E>& v, VecP<E>& lo, VecP<E>& w, VecP<E>& wlo, const Op& op,
+                                             const Cheb<float>& ch, int K, int Sw) {
+  for (int s = 0; s < Sw; ++s) {
+    const bool on = s < ch.S;
+    VecP<E> t0 = v, t1, acc, o, q0 = w, q1, bcc, oq, zero;
+#pragma unroll
+    for (int r = 0; r < E; ++r) zero.z[r] = make_float2(0.f, 0.f);
+    op.template rec_p<DL>(t0, zero, t1);
+    op.template rec_p<DL>(q0, zero, q1);
+#pragma unroll
+    for (int r = 0; r < E; ++r) {
+      t1.z[r] = mul2(t1.z[r], bc2(0.5f));
+      q1.z[r] = mul2(q1.z[r], bc2(0.5f));
+    }
+    const float b0h = COMP ? ch.c0h : ch.a0h, b0l = COMP ? ch.c0l : ch.a0l;
+#pragma unroll
+    for (int r = 0; r < E; ++r) {
+      acc.z[r] = fma2(bc2(b0h), t0.z[r], mul2(bc2(b0l), t0.z[r]));
+      o.z[r] = fma2(bc2(ch.a1h), t1.z[r], mul2(bc2(ch.a1l), t1.z[r]));
+      bcc.z[r] = fma2(bc2(b0h), q0.z[r], mul2(bc2(b0l), q0.z[r]));
+      oq.z[r] = fma2(bc2(ch.a1h), q1.z[r], mul2(bc2(ch.a1l), q1.z[r]));
+    }
+    for (int k = 2; k < K; k += 2) {
+      op.template rec_p<DL>(t1, t0, t0);
+      op.template rec_p<DL>(q1, q0, q0);
+      const float2 ce = bc2(ch.cf[k]), cel = bc2(ch.cl[k]);
+#pragma unroll
+      for (int r = 0; r < E; ++r) {
+        acc.z[r] = fma2(ce, t0.z[r], LOC ? fma2(cel, t0.z[r], acc.z[r]) : acc.z[r]);
+        bcc.z[r] = fma2(ce, q0.z[r], LOC ? fma2(cel, q0.z[r], bcc.z[r]) : bcc.z[r]);
+      }
+      if (k + 1 < K) {
+        op.template rec_p<DL>(t0, t1, t1);
+        op.template rec_p<DL>(q0, q1, q1);
+        const float2 co = bc2(ch.cf[k + 1]), col = bc2(ch.cl[k + 1]);
+#pragma unroll
+        for (int r = 0; r < E; ++r) {
+          o.z[r] = fma2(co, t1.z[r], LOC ? fma2(col, t1.z[r], o.z[r]) : o.z[r]);
+          oq.z[r] = fma2(co, q1.z[r], LOC ? fma2(col, q1.z[r], oq.z[r]) : oq.z[r]);
+        }
+      }
+    }
+#pragma unroll
+    for (int r = 0; r < E; ++r) {
+      acc.z[r].x += o.z[r].y;
+      acc.z[r].y -= o.z[r].x;
+      bcc.z[r].x += oq.z[r].y;
+      bcc.z[r].y -= oq.z[r].x;
+    }
+    if (!on) continue;
+#pragma unroll
+    for (int r = 0; r < E; ++r) {
+      if (!COMP) {
+        v.z[r] = acc.z[r];
+        w.z[r] = bcc.z[r];
+      } else {
+        float2 x = v.z[r], t = add2(acc.z[r], lo.z[r]), sm = add2(x, t), bb = add2(sm, neg2(x));
+        lo.z[r] = add2(add2(x, neg2(add2(sm, neg2(bb)))), add2(t, neg2(bb)));
+        v.z[r] = sm;
+        x = w.z[r]; t = add2(bcc.z[r], wlo.z[r]); sm = add2(x, t); bb = add2(sm, neg2(x));
+        wlo.z[r] = add2(add2(x, neg2(add2(sm, neg2(bb)))), add2(t, neg2(bb)));
+        w.z[r] = sm;
+      }
+    }
+  }
+}
+
+// cheb_step_p2 with the coefficients in registers (forward, K <= KR terms, warp-uniform).
+template <bool COMP, bool LOC, bool DL, int KR, int E, class Op>
+__device__ __forceinline__ void cheb_step_pr2(VecP<E>& v, VecP<E>& lo, VecP<E>& w, VecP<E>& wlo, const Op& op,
+                                              const CoefP<KR>& cp, int K, int Sw, int S) {
+  for (int s = 0; s < Sw; ++s) {
+    const bool on = s < S;
+    VecP<E> t0 = v, t1, acc, o, q0 = w, q1, bcc, oq, zero;
+#pragma unroll
+    for (int r = 0; r < E; ++r) zero.z[r] = make_float2(0.f, 0.f);
+    op.template rec_p<DL>(t0, zero, t1);
+    op.template rec_p<DL>(q0, zero, q1);
+#pragma unroll
+    for (int r = 0; r < E; ++r) {
+      t1.z[r] = mul2(t1.z[r], bc2(0.5f));
+      q1.z[r] = mul2(q1.z[r], bc2(0.5f));
+      acc.z[r] = fma2(cp.b0h, t0.z[r], mul2(cp.b0l, t0.z[r]));
+      o.z[r] = fma2(cp.a1h, t1.z[r], mul2(cp.a1l, t1.z[r]));
+      bcc.z[r] = fma2(cp.b0h, q0.z[r], mul2(cp.b0l, q0.z[r]));
+      oq.z[r] = fma2(cp.a1h, q1.z[r], mul2(cp.a1l, q1.z[r]));
+    }
+#pragma unroll
+    for (int k = 2; k < KR; k += 2) {
+      if (k >= K) break;
+      op.template rec_p<DL>(t1, t0, t0);
+      op.template rec_p<DL>(q1, q0, q0);
+#pragma unroll
+      for (int r = 0; r < E; ++r) {
+        acc.z[r] = fma2(cp.c[k], t0.z[r], LOC ? fma2(cp.l[k], t0.z[r], acc.z[r]) : acc.z[r]);
+        bcc.z[r] = fma2(cp.c[k], q0.z[r], LOC ? fma2(cp.l[k], q0.z[r], bcc.z[r]) : bcc.z[r]);
+      }
+      if (k + 1 < K && k + 1 < KR) {
+        op.template rec_p<DL>(t0, t1, t1);
+        op.template rec_p<DL>(q0, q1, q1);
+#pragma unroll
+        for (int r = 0; r < E; ++r) {
+          o.z[r] = fma2(cp.c[k + 1], t1.z[r], LOC ? fma2(cp.l[k + 1], t1.z[r], o.z[r]) : o.z[r]);
+          oq.z[r] = fma2(cp.c[k + 1], q1.z[r], LOC ? fma2(cp.l[k + 1], q1.z[r], oq.z[r]) : oq.z[r]);
+        }
+      }
+    }
+#pragma unroll
+    for (int r = 0; r < E; ++r) {
+      acc.z[r].x += o.z[r].y;
+      acc.z[r].y -= o.z[r].x;
+      bcc.z[r].x += oq.z[r].y;
+      bcc.z[r].y -= oq.z[r].x;
+    }
+    if (!on) continue;
+#pragma unroll
+    for (int r = 0; r < E; ++r) {
+      if (!COMP) {
+        v.z[r] = acc.z[r];
+        w.z[r] = bcc.z[r];
+      } else {
+        float2 x = v.z[r], t = add2(acc.z[r], lo.z[r]), sm = add2(x, t), bb = add2(sm, neg2(x));
+        lo.z[r] = add2(add2(x, neg2(add2(sm, neg2(bb)))), add2(t, neg2(bb)));
+        v.z[r] = sm;
+        x = w.z[r]; t = add2(bcc.z[r], wlo.z[r]); sm = add2(x, t); bb = add2(sm, neg2(x));
+        wlo.z[r] = add2(add2(x, neg2(add2(sm, neg2(bb)))), add2(t, neg2(bb)));
+        w.z[r] = sm;
       }
     }
   }

@@ -33,6 +33,10 @@ struct KParams {
   long tile_stride;
   void* traj;             // [B][Nt+N][G*E] (R2)  H1 psi_n(t_j) per step
   void* traj2;            // [B][Nt+N][G*E] (R2)  chi^ per step (concurrent two-trajectory sweeps)
+  void* zs;               // [B][Nt+N] (R2)  per-step overlap z_s of the sub-interval sweeps
+  void* ckpt;             // [B][N][nck][hi (, lo)][G*E] (R2)  checkpoints of the literal sub-problem
+  void* segb;             // [B][N][cks][G*E] (R2)  H1 psi_n of the segment being stepped back
+  int cks, nck;           // checkpoint stride (steps) and checkpoints per sub-interval
   double* grad;           // [B][Nt]
   double* Jn;             // [B][N]
   double* err;            // [B][N]
@@ -114,6 +118,14 @@ __device__ __forceinline__ void count_work(unsigned long long* c, const Cheb<R>&
     atomicAdd(c + 1, (unsigned long long)(steps * ch.S * ch.K));
     atomicAdd(c + 2, (unsigned long long)(steps * ch.S));
   }
+}
+
+// ST_NONFINITE when any of x[0..n) is NaN or infinite (a template so that every translation unit
+// that includes this header may launch it).
+template <int = 0>
+__global__ void k_check_finite(const double* x, long n, int* status) {
+  for (long i = blockIdx.x * (long)blockDim.x + threadIdx.x; i < n; i += (long)gridDim.x * blockDim.x)
+    if (!isfinite(x[i])) { atomicOr(status, ST_NONFINITE); return; }
 }
 
 // ------------------------------------------------------------------------------ k_assemble
@@ -204,291 +216,31 @@ __global__ void __launch_bounds__(128, Op::ASM_MINB) k_assemble(KParams p) {
   }
 }
 
-// ------------------------------------------------------------------------------ k_subinterval
-// One group per (problem, n).  Sequential part per step: the propagation (forward, then adjoint) and
-// an FP32 group reduction; the FP64 gradient, Err and ascent step are done afterwards with the lanes
-// working on different steps.  The trajectory slot of step j (H1 psi_n(t_j), consumed by the backward
-// sweep at step j) is reused to hold the gradient term Im<delta_j|H1 psi_j> for that final pass.
-template <typename R, class Op>
-__global__ void __launch_bounds__(128) k_subinterval(KParams p) {
-  constexpr int G = Op::G, E = Op::E, GPB = 128 / G, GE = G * E;
-  constexpr bool COMP = sizeof(R) == 4;
-  using R2 = typename C2<R>::T;
-  extern __shared__ __align__(128) unsigned char smem_raw[];
-  __shared__ Cheb<R> chs[GPB];
-  const int lg = threadIdx.x % G, gib = threadIdx.x / G;
-  const long gid0 = (long)blockIdx.x * GPB + gib;
-  const long total = (long)p.B * p.N;
-  if (Op::G * Op::E == Op::DP_SMEM) {
-    const R* src = reinterpret_cast<const R*>(p.H);
-    R* dst = reinterpret_cast<R*>(smem_raw);
-    for (int i = threadIdx.x; i < 2 * Op::DP_SMEM * Op::DP_SMEM; i += blockDim.x) dst[i] = src[i];
-    __syncthreads();
-  }
-  // warps whose groups are all past the end leave; partially valid warps keep every lane running
-  const long warp_first = ((long)blockIdx.x * GPB + (threadIdx.x / 32) * (32 / G));
-  if (warp_first >= total) return;
-  const bool valid = gid0 < total;
-  const long gid = valid ? gid0 : total - 1;
-  const int n = (int)(gid % p.N), b = (int)(gid / p.N);
-  const int j0 = p.jn[n], j1 = p.jn[n + 1], ns = j1 - j0;
-  const int nsw = warp_max_i(ns);
-  double* ub = p.u + (long)b * p.Nt;
-  const float* ufb = p.uf + (long)b * p.Nt;
+// ------------------------------------------------------------------------- sub-problem helpers
+// Per-step overlap slots: z_s = <a_s|H1 b_s> of step s of sub-interval n at zs[b][j_n + n + s],
+// s = 0..ns (one complex number per step; the trailing slot of each sub-interval holds its end point).
+//
+// FP64 pass over the steps, lanes of the group on different steps: the trapezoid gradient term of
+// step j from the slots s, s+1 (Crank-Nicolson: slot s holds both ends), the penalty, Err and the
+// ascent step; J_n = w(-|delta(t_{n+1})|^2/2) - penalty.
+template <int G, bool CNs, typename R2>
+__device__ __forceinline__ void sub_grad_pass(const KParams& p, const R2* zs, int b, int n, long gid, int j0, int ns,
+                                              double cPhi, double sPhi, double nrm, int lg, int stride, bool valid) {
   const double beta = p.beta[n];
-
-  Cheb<R>& ch = chs[gib];
-  int Kw, Sw;
-  cheb_load<G, R>(ch, reinterpret_cast<const Cheb<R>*>(p.cheb) + gid, lg, Kw, Sw);
-
-  Op op;
-  op.load(reinterpret_cast<const R*>(p.H), p.H0d, p.d, lg, smem_raw);
-  op.scale(p.H0d, p.d, lg, ch);
-  // Propagation here omits the global phase exp(-i c tau) of each step.  Over the sub-interval it
-  // multiplies psi_n(t_{n+1}) by exp(-i Phi), Phi = c (t_{n+1} - t_n), and every gradient term
-  // <chi_n|H1|psi_n>(t_j) by the same exp(-i Phi) (chi_n carries exp(+i c (t_{n+1} - t_j)), psi_n
-  // exp(-i c (t_j - t_n))); both are applied once, in FP64.
-  const double sPhi = ch.sph, cPhi = ch.cph;
-
-  // form 0: psi_n(t_n) = phi_n (Eq. (dirpara)), adjoint from phi_{n+1};
-  // form 1 (phi = phi^u, first local step): psi from psi(t_n) and chi from chi(t_{n+1}), the two
-  // trajectories of which psi_n, chi_n are combinations (proof of Theorem 2); no cancellation.
-  const long off_n = ((long)b * (p.N + 1) + n) * p.d;
-  const double2* phn = (p.form ? p.psin : p.phi) + off_n;
-  const double2* phn1 = (p.form ? p.chin : p.phi) + off_n + p.d;
-  Vec<R, E> v, lo;
-#pragma unroll
-  for (int r = 0; r < E; ++r) {
-    int e = lg * E + r;
-    double2 z = e < p.d ? phn[e] : make_double2(0.0, 0.0);
-    v.re[r] = (R)z.x;
-    v.im[r] = (R)z.y;
-    lo.re[r] = COMP ? (R)(z.x - (double)v.re[r]) : R(0);
-    lo.im[r] = COMP ? (R)(z.y - (double)v.im[r]) : R(0);
-  }
-  R2* tr0 = reinterpret_cast<R2*>(p.traj) + ((long)b * (p.Nt + p.N) + j0 + n) * GE;   // slot s at tr0 + s*GE
-  R2* tr = tr0 + lg * E;
-
-  // ---- forward sweep: store H1 psi_j, then psi_{j+1} = U_j psi_j
-  constexpr bool PK = sizeof(R) == 4 && Op::PACKED;
-  Vec<R, E> hend;   // end point: H1 psi_n(t_{n+1}) stays in registers
-  if constexpr (PK) {   // packed FP32: both halves per instruction
-    VecP<E> pv, pl;
-#pragma unroll
-    for (int r = 0; r < E; ++r) { pv.z[r] = make_float2(v.re[r], v.im[r]); pl.z[r] = make_float2(lo.re[r], lo.im[r]); }
-    float2* trp = reinterpret_cast<float2*>(tr);
-    float ua = ufb[j0], ub1 = ns > 1 ? ufb[j0 + 1] : ua;
-    for (int s = 0; s < nsw; ++s) {
-      const bool act = s < ns;
-      const float uj = ua;
-      ua = ub1;
-      if (s + 2 < ns) ub1 = ufb[j0 + s + 2];
-      VecP<E> hv;
-      op.h1_p(pv, hv);
-      if (act && valid) {
-#pragma unroll
-        for (int r = 0; r < E; ++r) trp[(long)s * GE + r] = hv.z[r];
-      }
-      VecP<E> w = pv, wl = pl;
-      op.set_u(uj, ch, lg);
-      cheb_step_p<false, true, false, true>(w, wl, op, ch, Kw, Sw);
-      if (act) { pv = w; pl = wl; }
-    }
-    VecP<E> he;
-    op.h1_p(pv, he);
-#pragma unroll
-    for (int r = 0; r < E; ++r) {
-      v.re[r] = pv.z[r].x; v.im[r] = pv.z[r].y; lo.re[r] = pl.z[r].x; lo.im[r] = pl.z[r].y;
-      hend.re[r] = he.z[r].x; hend.im[r] = he.z[r].y;
-    }
-  } else {
-    R ua = uval<R>(ub, ufb, j0), ub1 = ns > 1 ? uval<R>(ub, ufb, j0 + 1) : ua;
-    for (int s = 0; s < nsw; ++s) {
-      const bool act = s < ns;
-      const R uj = ua;
-      ua = ub1;
-      if (s + 2 < ns) ub1 = uval<R>(ub, ufb, j0 + s + 2);
-      Vec<R, E> hv;
-      op.h1(v, hv);
-      if (act && valid) {
-#pragma unroll
-        for (int r = 0; r < E; ++r) { R2 z; z.x = hv.re[r]; z.y = hv.im[r]; tr[(long)s * GE + r] = z; }
-      }
-      Vec<R, E> w = v, wl = lo;
-      op.set_u(uj, ch, lg);
-      prop_step<false, COMP>(w, wl, op, ch, Kw, Sw);
-      if (act) { v = w; lo = wl; }
-    }
-    op.h1(v, hend);
-  }
-
-  // ---- terminal residual delta = phi_{n+1} - psi_n(t_{n+1}) in FP64 (its norm gives J_n).  Form 0
-  // propagates delta backward; form 1 propagates chi from chi(t_{n+1}) and takes delta from the
-  // chain, delta = (chi - psi)(t_{n+1}) / beta_n.
-  double nrm = 0.0;
-  Vec<R, E> dl;
-#pragma unroll
-  for (int r = 0; r < E; ++r) {
-    int e = lg * E + r;
-    double2 z = e < p.d ? phn1[e] : make_double2(0.0, 0.0);
-    double dr, di;
-    if (!p.form) {
-      double pr, pi;
-      phase_rotate(cPhi, sPhi, false, (double)v.re[r] + (double)lo.re[r], (double)v.im[r] + (double)lo.im[r], pr, pi);
-      dr = z.x - pr;
-      di = z.y - pi;
-      dl.re[r] = (R)dr;
-      dl.im[r] = (R)di;
-    } else {
-      double2 ps = e < p.d ? p.psin[off_n + p.d + e] : make_double2(0.0, 0.0);
-      dr = (z.x - ps.x) / beta;
-      di = (z.y - ps.y) / beta;
-      dl.re[r] = (R)z.x;
-      dl.im[r] = (R)z.y;
-    }
-    if (e >= p.d) { dr = 0.0; di = 0.0; }
-    nrm += dr * dr + di * di;
-  }
-  nrm = g_sum<G>(nrm);
-
-  // z = <a|h> over the group, FP32 products, both parts (the phase exp(-i Phi) is applied later)
-  auto zdot = [&](const Vec<R, E>& a, const Vec<R, E>& h, R& zr, R& zi) {
-    R xr = R(0), xi = R(0);
-#pragma unroll
-    for (int r = 0; r < E; ++r) {
-      xr = fma(a.re[r], h.re[r], fma(a.im[r], h.im[r], xr));
-      xi = fma(a.re[r], h.im[r], fma(-a.im[r], h.re[r], xi));
-    }
-    zr = g_sum<G>(xr);
-    zi = g_sum<G>(xi);
-  };
-  {
-    R zr, zi;
-    zdot(dl, hend, zr, zi);
-    if (lg == 0 && valid) { R2 z; z.x = zr; z.y = zi; tr0[(long)ns * GE] = z; }
-  }
-
-  // ---- backward sweep: delta_j = U_j^H delta_{j+1}; gradient term of step j into slot j
-  if constexpr (PK) {
-    const int top = ns - 1;
-    const float2* trp = reinterpret_cast<const float2*>(tr);
-    VecP<E> pd, h0, h1v, dummy;
-#pragma unroll
-    for (int r = 0; r < E; ++r) pd.z[r] = make_float2(dl.re[r], dl.im[r]);
-    auto ldslot = [&](int s, VecP<E>& h) {
-#pragma unroll
-      for (int r = 0; r < E; ++r) h.z[r] = trp[(long)s * GE + r];
-    };
-    // <a|h> over the group from packed products: (re re, im im) and (re im, -im re) pair sums
-    auto zdotp = [&](const VecP<E>& a, const VecP<E>& h, float& zr, float& zi) {
-      float2 s1 = make_float2(0.f, 0.f), s2 = make_float2(0.f, 0.f);
-#pragma unroll
-      for (int r = 0; r < E; ++r) {
-        s1 = fma2(a.z[r], h.z[r], s1);
-        s2 = fma2(a.z[r], make_float2(h.z[r].y, -h.z[r].x), s2);
-      }
-      zr = g_sum<G>(s1.x + s1.y);
-      zi = g_sum<G>(s2.x + s2.y);
-    };
-    ldslot(top, h0);
-    ldslot(top > 0 ? top - 1 : top, h1v);
-    float ua = ufb[j0 + top], ub1 = ufb[j0 + (top > 0 ? top - 1 : top)];
-    for (int s = nsw - 1; s >= 0; --s) {
-      const bool act = s < ns;
-      VecP<E> hc = h0;
-      const float uj = ua;
-      if (act) {
-        h0 = h1v;
-        ua = ub1;
-        if (s - 2 >= 0) { ldslot(s - 2, h1v); ub1 = ufb[j0 + s - 2]; }
-      }
-      VecP<E> w = pd;
-      op.set_u(uj, ch, lg);
-      cheb_step_p<true, false, false, false>(w, dummy, op, ch, Kw, Sw);
-      if (act) pd = w;
-      float zr, zi;
-      zdotp(pd, hc, zr, zi);
-      if (act && lg == 0 && valid) { R2 z; z.x = zr; z.y = zi; tr0[(long)s * GE] = z; }
-    }
-  } else if constexpr (Op::CN) {
-    // Crank-Nicolson (Sec. 3): lambda_j = A_j xi_j, xi_j = B_j^{-1} lambda_{j+1}; the exact gradient of
-    // the discrete J_n pairs xi_j with H1 (psi_j + psi_{j+1}), so slot j receives
-    // <xi_j|H1 psi_j + H1 psi_{j+1}> (H1 psi_{j+1} is the previous slot's, kept in registers).
-    const int top = ns - 1;
-    Vec<R, E> h0, h1v, hn = hend;
-    auto ldslot = [&](int s, Vec<R, E>& h) {
-#pragma unroll
-      for (int r = 0; r < E; ++r) { R2 z = tr[(long)s * GE + r]; h.re[r] = z.x; h.im[r] = z.y; }
-    };
-    ldslot(top, h0);
-    ldslot(top > 0 ? top - 1 : top, h1v);
-    R ua = uval<R>(ub, ufb, j0 + top), ub1 = uval<R>(ub, ufb, j0 + (top > 0 ? top - 1 : top));
-    for (int s = nsw - 1; s >= 0; --s) {
-      const bool act = s < ns;
-      Vec<R, E> hc = h0;
-      const R uj = ua;
-      if (act) {
-        h0 = h1v;
-        ua = ub1;
-        if (s - 2 >= 0) { ldslot(s - 2, h1v); ub1 = uval<R>(ub, ufb, j0 + s - 2); }
-      }
-      Vec<R, E> w = dl, xi, hs;
-      op.set_u(uj, ch, lg);
-      cn_step<true>(w, xi, op, ch.h, Kw);
-#pragma unroll
-      for (int r = 0; r < E; ++r) { hs.re[r] = hc.re[r] + hn.re[r]; hs.im[r] = hc.im[r] + hn.im[r]; }
-      R zr, zi;
-      zdot(xi, hs, zr, zi);
-      if (act) {
-        dl = w;
-        hn = hc;
-        if (lg == 0 && valid) { R2 z; z.x = zr; z.y = zi; tr0[(long)s * GE] = z; }
-      }
-    }
-  } else {
-    const int top = ns - 1;
-    Vec<R, E> h0, h1v;   // slots s and s-1, prefetched
-    auto ldslot = [&](int s, Vec<R, E>& h) {
-#pragma unroll
-      for (int r = 0; r < E; ++r) { R2 z = tr[(long)s * GE + r]; h.re[r] = z.x; h.im[r] = z.y; }
-    };
-    ldslot(top, h0);
-    ldslot(top > 0 ? top - 1 : top, h1v);
-    R ua = uval<R>(ub, ufb, j0 + top), ub1 = uval<R>(ub, ufb, j0 + (top > 0 ? top - 1 : top));
-    for (int s = nsw - 1; s >= 0; --s) {
-      const bool act = s < ns;
-      Vec<R, E> hc = h0;
-      const R uj = ua;
-      if (act) {
-        h0 = h1v;
-        ua = ub1;
-        if (s - 2 >= 0) { ldslot(s - 2, h1v); ub1 = uval<R>(ub, ufb, j0 + s - 2); }
-      }
-      Vec<R, E> w = dl;
-      op.set_u(uj, ch, lg);
-      cheb_step<true>(w, op, ch, Kw, Sw);
-      if (act) dl = w;
-      R zr, zi;
-      zdot(dl, hc, zr, zi);
-      if (act && lg == 0 && valid) { R2 z; z.x = zr; z.y = zi; tr0[(long)s * GE] = z; }
-    }
-  }
-  __syncwarp();
-
-  // ---- FP64 pass over the steps: gradient, Err, ascent step, penalty of J_n
   const double ht = 0.5 * p.tau * p.w / ((p.form && !p.global) ? beta : 1.0);
   const double tb = p.tau / (p.global ? 1.0 : beta);   // Theorem 2: beta_n g_n is the gradient of J
   const double step = p.rho * beta / p.tau;
+  double* ub = p.u + (long)b * p.Nt;
   double* gb = p.grad + (long)b * p.Nt;
   double err = 0.0, pen = 0.0;
-  for (int s = lg; s < ns; s += G) {
+  for (int s = lg; s < ns; s += stride) {
     const int j = j0 + s;
     const double uj = ub[j];
     const double al = p.alpha ? p.alpha[j] : 0.0;
-    const R2 za = tr0[(long)s * GE], zb = tr0[(long)(s + 1) * GE];
-    // Im(exp(-i Phi) z) for the two ends of step j (Crank-Nicolson: slot j holds both ends, Phi = 0)
+    const R2 za = zs[s], zb = zs[s + 1];
+    // Im(exp(-i Phi) z) for the two ends of step j
     const double Ia = cPhi * (double)za.y - sPhi * (double)za.x;
-    const double Ib = Op::CN ? 0.0 : cPhi * (double)zb.y - sPhi * (double)zb.x;
+    const double Ib = CNs ? 0.0 : cPhi * (double)zb.y - sPhi * (double)zb.x;
     const double g = ht * (Ia + Ib) - tb * al * uj;
     err += fabs(g);
     pen += al * uj * uj;
@@ -499,12 +251,394 @@ __global__ void __launch_bounds__(128) k_subinterval(KParams p) {
   }
   err = g_sum<G>(err);
   pen = g_sum<G>(pen);
-  const double Jn = p.w * (-0.5 * nrm) - 0.5 * tb * pen;
   if (lg == 0 && valid) {
-    if (p.Jn) p.Jn[gid] = Jn;
+    if (p.Jn) p.Jn[gid] = p.w * (-0.5 * nrm) - 0.5 * tb * pen;
     if (p.err) p.err[gid] = err;
   }
-  if (valid) count_work<R>(p.count, ch, 2L * ns, lg);   // forward U and backward U^H sweeps
+}
+
+// z = <a|h> over the group, products in the propagation precision
+template <int G, typename R, int E>
+__device__ __forceinline__ void g_zdot(const Vec<R, E>& a, const Vec<R, E>& h, R& zr, R& zi) {
+  R xr = R(0), xi = R(0);
+#pragma unroll
+  for (int r = 0; r < E; ++r) {
+    xr = fma(a.re[r], h.re[r], fma(a.im[r], h.im[r], xr));
+    xi = fma(a.re[r], h.im[r], fma(-a.im[r], h.re[r], xi));
+  }
+  zr = g_sum<G>(xr);
+  zi = g_sum<G>(xi);
+}
+// the same on packed FP32 states: (re re, im im) and (re im, -im re) pair sums
+template <int G, int E>
+__device__ __forceinline__ void g_zdot_p(const VecP<E>& a, const VecP<E>& h, float& zr, float& zi) {
+  float2 s1 = make_float2(0.f, 0.f), s2 = make_float2(0.f, 0.f);
+#pragma unroll
+  for (int r = 0; r < E; ++r) {
+    s1 = fma2(a.z[r], h.z[r], s1);
+    s2 = fma2(a.z[r], make_float2(h.z[r].y, -h.z[r].x), s2);
+  }
+  zr = g_sum<G>(s1.x + s1.y);
+  zi = g_sum<G>(s2.x + s2.y);
+}
+
+// A group's share of an FP64 state (d elements, zero padded) as hi (+ lo for FP32 propagation).
+template <typename R, int E>
+__device__ __forceinline__ void load_group_state(Vec<R, E>& v, Vec<R, E>& lo, const double2* src, int d, int lg) {
+#pragma unroll
+  for (int r = 0; r < E; ++r) {
+    const int e = lg * E + r;
+    const double2 z = e < d ? src[e] : make_double2(0.0, 0.0);
+    v.re[r] = (R)z.x;
+    v.im[r] = (R)z.y;
+    lo.re[r] = sizeof(R) == 4 ? (R)(z.x - (double)v.re[r]) : R(0);
+    lo.im[r] = sizeof(R) == 4 ? (R)(z.y - (double)v.im[r]) : R(0);
+  }
+}
+template <typename R, int E>
+__device__ __forceinline__ void to_packed(const Vec<R, E>& v, const Vec<R, E>& lo, VecP<E>& pv, VecP<E>& pl) {
+#pragma unroll
+  for (int r = 0; r < E; ++r) {
+    pv.z[r] = make_float2((float)v.re[r], (float)v.im[r]);
+    pl.z[r] = make_float2((float)lo.re[r], (float)lo.im[r]);
+  }
+}
+
+// Preamble shared by the sub-interval kernels: group coordinates, the dense op's shared-memory copy.
+#define ISM_SUB_PREAMBLE                                                                              \
+  constexpr int G = Op::G, E = Op::E, GPB = 128 / G, GE = G * E;                                      \
+  constexpr bool COMP = sizeof(R) == 4;                                                               \
+  constexpr bool PK = COMP && Op::PACKED;                                                             \
+  using R2 = typename C2<R>::T;                                                                       \
+  extern __shared__ __align__(128) unsigned char smem_raw[];                                          \
+  __shared__ Cheb<R> chs[GPB];                                                                        \
+  const int lg = threadIdx.x % G, gib = threadIdx.x / G;                                              \
+  const long gid0 = (long)blockIdx.x * GPB + gib;                                                     \
+  const long total = (long)p.B * p.N;                                                                 \
+  if (Op::G * Op::E == Op::DP_SMEM) {                                                                 \
+    const R* src_ = reinterpret_cast<const R*>(p.H);                                                  \
+    R* dst_ = reinterpret_cast<R*>(smem_raw);                                                         \
+    for (int i = threadIdx.x; i < 2 * Op::DP_SMEM * Op::DP_SMEM; i += blockDim.x) dst_[i] = src_[i];  \
+    __syncthreads();                                                                                  \
+  }                                                                                                   \
+  /* warps whose groups are all past the end leave; partially valid warps keep every lane running */ \
+  const long warp_first = ((long)blockIdx.x * GPB + (threadIdx.x / 32) * (32 / G));                   \
+  if (warp_first >= total) return;                                                                    \
+  const bool valid = gid0 < total;                                                                    \
+  const long gid = valid ? gid0 : total - 1;                                                          \
+  const int n = (int)(gid % p.N), b = (int)(gid / p.N);                                               \
+  const int j0 = p.jn[n], j1 = p.jn[n + 1], ns = j1 - j0;                                             \
+  const int nsw = warp_max_i(ns);                                                                     \
+  const double* ub = p.u + (long)b * p.Nt;                                                            \
+  const float* ufb = p.uf + (long)b * p.Nt;                                                           \
+  Cheb<R>& ch = chs[gib];                                                                             \
+  int Kw, Sw;                                                                                         \
+  cheb_load<G, R>(ch, reinterpret_cast<const Cheb<R>*>(p.cheb) + gid, lg, Kw, Sw);                    \
+  Op op;                                                                                              \
+  op.load(reinterpret_cast<const R*>(p.H), p.H0d, p.d, lg, smem_raw);                                 \
+  op.scale(p.H0d, p.d, lg, ch);                                                                       \
+  const long off_n = ((long)b * (p.N + 1) + n) * p.d;                                                 \
+  R2* zs = reinterpret_cast<R2*>(p.zs) + (long)b * (p.Nt + p.N) + j0 + n;                             \
+  (void)ub; (void)GE; (void)PK
+
+// ------------------------------------------------------------------------------ k_subfwd
+// Algorithm 1 step (c) in the two-trajectory form of the proof of Theorem 2 (first local step, phi =
+// phi^u): on sub-interval n, psi_n = a_n psi + b_n chi and chi_n = a_{n+1} psi + b_{n+1} chi with psi,
+// chi the global trajectories, so Im<chi_n|H1|psi_n> = Im<chi|H1|psi> / beta_n and J_n's residual is
+// (chi - psi)(t_{n+1}) / beta_n.  chi obeys the same propagator as psi, so one group per (problem, n)
+// carries BOTH forward from the boundary states psi(t_n), chi(t_n) that steps (a)-(b) stored, and forms
+// z_s = <chi_s|H1 psi_s> at every step on the fly: the global trajectories are checkpointed at the
+// partition and each segment is recomputed once; nothing per step is stored but z_s.  Neither state
+// carries the per-step global phase exp(-i c tau), and the two phases cancel in z_s.  Crank-Nicolson:
+// chi's step gives xi_j = A_j^{-1} chi_j (cn_step_fwd_xi), paired with H1 (psi_j + psi_{j+1}).
+constexpr int SUB_KR = 10;   // series terms held in registers by the packed sub-interval sweeps
+
+template <typename R, class Op>
+__global__ void __launch_bounds__(128) k_subfwd(KParams p) {
+  ISM_SUB_PREAMBLE;
+  Vec<R, E> a, alo, c, clo;   // psi and chi (hi + lo in FP32 propagation)
+  load_group_state<R, E>(a, alo, p.psin + off_n, p.d, lg);
+  load_group_state<R, E>(c, clo, p.chin + off_n, p.d, lg);
+  const bool wr = valid && lg == 0;
+
+  if constexpr (PK) {
+    VecP<E> pa, pal, pc, pcl;
+    to_packed<R, E>(a, alo, pa, pal);
+    to_packed<R, E>(c, clo, pc, pcl);
+    // over one sub-interval (~10^2 steps) the roundings of the diagonal's and the coefficients' low
+    // parts do not accumulate (a ~1e-8 relative change): both are left out (DL = LOC = false)
+    float un = ufb[j0];
+    auto body = [&](auto step) {
+      for (int s = 0; s < nsw; ++s) {
+        const bool act = s < ns;
+        const float uj = un;
+        if (s + 1 < ns) un = __ldg(ufb + j0 + s + 1);
+        VecP<E> h;
+        op.h1_p(pa, h);
+        float zr, zi;
+        g_zdot_p<G, E>(pc, h, zr, zi);
+        if (act && wr) zs[s] = make_float2(zr, zi);
+        VecP<E> wa = pa, wal = pal, wc = pc, wcl = pcl;
+        op.set_u(uj, ch, lg);
+        step(wa, wal, wc, wcl);
+        if (act) { pa = wa; pal = wal; pc = wc; pcl = wcl; }
+      }
+    };
+    if (Kw <= SUB_KR) {   // coefficients in registers
+      CoefP<SUB_KR> cp;
+      load_coef<SUB_KR, false, true>(cp, ch);
+      const int S = ch.S;
+      body([&](VecP<E>& x, VecP<E>& xl, VecP<E>& y, VecP<E>& yl) {
+        cheb_step_pr2<true, false, false>(x, xl, y, yl, op, cp, Kw, Sw, S);
+      });
+    } else {
+      body([&](VecP<E>& x, VecP<E>& xl, VecP<E>& y, VecP<E>& yl) {
+        cheb_step_p2<true, false, false>(x, xl, y, yl, op, ch, Kw, Sw);
+      });
+    }
+    VecP<E> h;
+    op.h1_p(pa, h);
+    float zr, zi;
+    g_zdot_p<G, E>(pc, h, zr, zi);
+    if (wr) zs[ns] = make_float2(zr, zi);
+  } else if constexpr (Op::CN) {
+    Vec<R, E> ha;
+    op.h1(a, ha);
+    R un = uval<R>(ub, ufb, j0);
+    for (int s = 0; s < nsw; ++s) {
+      const bool act = s < ns;
+      const R uj = un;
+      if (s + 1 < ns) un = uval<R>(ub, ufb, j0 + s + 1);
+      op.set_u(uj, ch, lg);
+      Vec<R, E> wa = a, wc = c, xi, dummy, hb, hs;
+      cn_step<false>(wa, dummy, op, ch.h, Kw);
+      cn_step_fwd_xi(wc, xi, op, ch.h, Kw);
+      op.h1(wa, hb);
+#pragma unroll
+      for (int r = 0; r < E; ++r) { hs.re[r] = ha.re[r] + hb.re[r]; hs.im[r] = ha.im[r] + hb.im[r]; }
+      R zr, zi;
+      g_zdot<G, R, E>(xi, hs, zr, zi);
+      if (act) {
+        a = wa; c = wc; ha = hb;
+        if (wr) { R2 z; z.x = zr; z.y = zi; zs[s] = z; }
+      }
+    }
+  } else {
+    R un = uval<R>(ub, ufb, j0);
+    for (int s = 0; s < nsw; ++s) {
+      const bool act = s < ns;
+      const R uj = un;
+      if (s + 1 < ns) un = uval<R>(ub, ufb, j0 + s + 1);
+      Vec<R, E> h;
+      op.h1(a, h);
+      R zr, zi;
+      g_zdot<G, R, E>(c, h, zr, zi);
+      if (act && wr) { R2 z; z.x = zr; z.y = zi; zs[s] = z; }
+      Vec<R, E> wa = a, wal = alo, wc = c, wcl = clo;
+      op.set_u(uj, ch, lg);
+      prop_step<false, COMP>(wa, wal, op, ch, Kw, Sw);
+      prop_step<false, COMP>(wc, wcl, op, ch, Kw, Sw);
+      if (act) { a = wa; alo = wal; c = wc; clo = wcl; }
+    }
+    Vec<R, E> h;
+    op.h1(a, h);
+    R zr, zi;
+    g_zdot<G, R, E>(c, h, zr, zi);
+    if (wr) { R2 z; z.x = zr; z.y = zi; zs[ns] = z; }
+  }
+  __syncwarp();
+
+  // |delta(t_{n+1})|^2 with delta = (chi - psi)(t_{n+1}) / beta_n from the FP64 boundary states
+  const double beta = p.beta[n];
+  double nrm = 0.0;
+#pragma unroll
+  for (int r = 0; r < E; ++r) {
+    const int e = lg * E + r;
+    if (e < p.d) {
+      const double2 x = p.chin[off_n + p.d + e], y = p.psin[off_n + p.d + e];
+      const double dr = (x.x - y.x) / beta, di = (x.y - y.y) / beta;
+      nrm += dr * dr + di * di;
+    }
+  }
+  nrm = g_sum<G>(nrm);
+  sub_grad_pass<G, Op::CN>(p, zs, b, n, gid, j0, ns, 1.0, 0.0, nrm, lg, G, valid);
+  if (valid) count_work<R>(p.count, ch, 2L * ns, lg);   // psi and chi forward
+}
+
+// ------------------------------------------------------------------------------ k_subinterval
+// Algorithm 1 step (c), literal sub-problem (any phi; local steps after the first, and the FP64
+// default): per (problem, n) the forward state psi_n from phi_n (Eq. (dirpara)), then the adjoint
+// backward from phi_{n+1} (proof of Theorem 2) in the delta form delta = chi_n - psi_n, delta(t_{n+1})
+// = phi_{n+1} - psi_n(t_{n+1}) in FP64 (Im<psi|H1|psi> = 0, so Im<chi_n|H1|psi_n> = Im<delta|H1|psi_n>).
+// The adjoint needs psi_n at every step in reverse order.  The forward sweep stores psi_n every
+// p.cks steps (checkpoints; hi + lo in FP32 propagation, so a recomputation repeats the forward sweep
+// bit for bit); the backward sweep runs the segments last to first, recomputing each segment's H1
+// psi_n from its checkpoint into a buffer of p.cks slots, then stepping delta back through it.
+// Storage per sub-interval: ceil(ns / cks) states and cks H1 psi vectors instead of ns.
+template <typename R, class Op>
+__global__ void __launch_bounds__(128) k_subinterval(KParams p) {
+  ISM_SUB_PREAMBLE;
+  const int S = p.cks;
+  constexpr int CKP = COMP ? 2 : 1;   // checkpoint parts: hi (+ lo)
+  R2* ck = reinterpret_cast<R2*>(p.ckpt) + gid * (long)p.nck * CKP * GE + lg * E;   // checkpoint c at ck + c*CKP*GE
+  R2* sb = reinterpret_cast<R2*>(p.segb) + gid * (long)S * GE + lg * E;             // segment slot i at sb + i*GE
+  // Propagation omits the global phase exp(-i c tau) of each step: over the sub-interval it multiplies
+  // psi_n(t_{n+1}) by exp(-i Phi), Phi = c (t_{n+1} - t_n), and every z_s = <delta_s|H1 psi_s> by the
+  // same exp(-i Phi) (delta carries exp(+i c (t_{n+1} - t_j)), psi_n exp(-i c (t_j - t_n))); both are
+  // applied once, in FP64.
+  const double sPhi = ch.sph, cPhi = ch.cph;
+  const double2* phn = p.phi + off_n;
+  const double2* phn1 = p.phi + off_n + p.d;
+  Vec<R, E> v, lo;
+  load_group_state<R, E>(v, lo, phn, p.d, lg);
+  const bool wr = valid && lg == 0;
+  auto put_ck = [&](int c, const Vec<R, E>& x, const Vec<R, E>& xl) {
+#pragma unroll
+    for (int r = 0; r < E; ++r) {
+      R2 z; z.x = x.re[r]; z.y = x.im[r];
+      ck[(long)c * CKP * GE + r] = z;
+      if (COMP) { R2 y; y.x = xl.re[r]; y.y = xl.im[r]; ck[(long)c * CKP * GE + GE + r] = y; }
+    }
+  };
+  auto get_ck = [&](int c, Vec<R, E>& x, Vec<R, E>& xl) {
+#pragma unroll
+    for (int r = 0; r < E; ++r) {
+      const R2 z = ck[(long)c * CKP * GE + r];
+      x.re[r] = z.x; x.im[r] = z.y;
+      if (COMP) { const R2 y = ck[(long)c * CKP * GE + GE + r]; xl.re[r] = y.x; xl.im[r] = y.y; }
+      else { xl.re[r] = R(0); xl.im[r] = R(0); }
+    }
+  };
+  auto uat = [&](int s) { return uval<R>(p.u + (long)b * p.Nt, ufb, j0 + (s < ns ? s : ns - 1)); };
+
+  // ---- forward sweep: checkpoints, then psi_{s+1} = U_s psi_s
+  Vec<R, E> hend;   // H1 psi_n(t_{n+1})
+  {
+    R un = uat(0);
+    int cc = 0;
+    for (int s = 0; s < nsw; ++s) {
+      const bool act = s < ns;
+      const R uj = un;
+      if (s + 1 < nsw) un = uat(s + 1);
+      if (cc == 0 && act && valid) put_ck(s / S, v, lo);
+      if (++cc == S) cc = 0;
+      Vec<R, E> w = v, wl = lo;
+      op.set_u(uj, ch, lg);
+      if constexpr (PK) {
+        VecP<E> pv, pl;
+        to_packed<R, E>(w, wl, pv, pl);
+        cheb_step_p<false, true, false, true>(pv, pl, op, ch, Kw, Sw);
+#pragma unroll
+        for (int r = 0; r < E; ++r) { w.re[r] = pv.z[r].x; w.im[r] = pv.z[r].y; wl.re[r] = pl.z[r].x; wl.im[r] = pl.z[r].y; }
+      } else {
+        prop_step<false, COMP>(w, wl, op, ch, Kw, Sw);
+      }
+      if (act) { v = w; lo = wl; }
+    }
+    op.h1(v, hend);
+  }
+
+  // ---- terminal residual delta = phi_{n+1} - psi_n(t_{n+1}) in FP64 (its norm gives J_n)
+  double nrm = 0.0;
+  Vec<R, E> dl;
+#pragma unroll
+  for (int r = 0; r < E; ++r) {
+    const int e = lg * E + r;
+    const double2 z = e < p.d ? phn1[e] : make_double2(0.0, 0.0);
+    double pr, pi;
+    phase_rotate(cPhi, sPhi, false, (double)v.re[r] + (double)lo.re[r], (double)v.im[r] + (double)lo.im[r], pr, pi);
+    double dr = z.x - pr, di = z.y - pi;
+    dl.re[r] = (R)dr;
+    dl.im[r] = (R)di;
+    if (e >= p.d) { dr = 0.0; di = 0.0; }
+    nrm += dr * dr + di * di;
+  }
+  nrm = g_sum<G>(nrm);
+  if constexpr (!Op::CN) {
+    R zr, zi;
+    g_zdot<G, R, E>(dl, hend, zr, zi);
+    if (wr) { R2 z; z.x = zr; z.y = zi; zs[ns] = z; }
+  }
+
+  // ---- backward sweep over the segments, last to first
+  const int nckw = (nsw + S - 1) / S;
+  Vec<R, E> hn = hend;   // Crank-Nicolson: H1 psi_{s+1} of the step below
+  for (int c = nckw - 1; c >= 0; --c) {
+    const int s0 = c * S, s1 = min(s0 + S, nsw);
+    // recompute H1 psi_s, s = s0..s1-1, from the checkpoint (bit-identical to the forward sweep)
+    {
+      Vec<R, E> x, xl;
+      get_ck(c, x, xl);
+      R un = uat(s0);
+      for (int s = s0; s < s1; ++s) {
+        const bool act = s < ns;
+        const R uj = un;
+        if (s + 1 < s1) un = uat(s + 1);
+        Vec<R, E> h;
+        op.h1(x, h);
+        if (act && valid) {
+#pragma unroll
+          for (int r = 0; r < E; ++r) { R2 z; z.x = h.re[r]; z.y = h.im[r]; sb[(long)(s - s0) * GE + r] = z; }
+        }
+        if (s + 1 < s1) {
+          Vec<R, E> w = x, wl = xl;
+          op.set_u(uj, ch, lg);
+          if constexpr (PK) {
+            VecP<E> pv, pl;
+            to_packed<R, E>(w, wl, pv, pl);
+            cheb_step_p<false, true, false, true>(pv, pl, op, ch, Kw, Sw);
+#pragma unroll
+            for (int r = 0; r < E; ++r) { w.re[r] = pv.z[r].x; w.im[r] = pv.z[r].y; wl.re[r] = pl.z[r].x; wl.im[r] = pl.z[r].y; }
+          } else {
+            prop_step<false, COMP>(w, wl, op, ch, Kw, Sw);
+          }
+          if (act) { x = w; xl = wl; }
+        }
+      }
+    }
+    // delta_s = U_s^H delta_{s+1}; z_s = <delta_s|H1 psi_s> into slot s
+    R un = uat(s1 - 1);
+    for (int s = s1 - 1; s >= s0; --s) {
+      const bool act = s < ns;
+      const R uj = un;
+      if (s - 1 >= s0) un = uat(s - 1);
+      Vec<R, E> hc;
+#pragma unroll
+      for (int r = 0; r < E; ++r) { const R2 z = sb[(long)(s - s0) * GE + r]; hc.re[r] = z.x; hc.im[r] = z.y; }
+      op.set_u(uj, ch, lg);
+      Vec<R, E> w = dl;
+      R zr, zi;
+      if constexpr (Op::CN) {
+        // Crank-Nicolson (Sec. 3): lambda_s = A_s xi_s, xi_s = B_s^{-1} lambda_{s+1}; the exact gradient of
+        // the discrete J_n pairs xi_s with H1 (psi_s + psi_{s+1}); slot s receives both ends
+        Vec<R, E> xi, hs;
+        cn_step<true>(w, xi, op, ch.h, Kw);
+#pragma unroll
+        for (int r = 0; r < E; ++r) { hs.re[r] = hc.re[r] + hn.re[r]; hs.im[r] = hc.im[r] + hn.im[r]; }
+        g_zdot<G, R, E>(xi, hs, zr, zi);
+      } else if constexpr (PK) {
+        VecP<E> pd, dummy, ph;
+#pragma unroll
+        for (int r = 0; r < E; ++r) { pd.z[r] = make_float2(w.re[r], w.im[r]); ph.z[r] = make_float2(hc.re[r], hc.im[r]); }
+        cheb_step_p<true, false, false, false>(pd, dummy, op, ch, Kw, Sw);
+#pragma unroll
+        for (int r = 0; r < E; ++r) { w.re[r] = pd.z[r].x; w.im[r] = pd.z[r].y; }
+        g_zdot_p<G, E>(pd, ph, zr, zi);
+      } else {
+        cheb_step<true>(w, op, ch, Kw, Sw);
+        g_zdot<G, R, E>(w, hc, zr, zi);
+      }
+      if (act) {
+        dl = w;
+        hn = hc;
+        if (wr) { R2 z; z.x = zr; z.y = zi; zs[s] = z; }
+      }
+    }
+  }
+  __syncwarp();
+  sub_grad_pass<G, Op::CN>(p, zs, b, n, gid, j0, ns, Op::CN ? 1.0 : cPhi, Op::CN ? 0.0 : sPhi, nrm, lg, G, valid);
+  // forward U sweep, its recomputation (every segment but the checkpointed state) and the U^H sweep
+  if (valid) count_work<R>(p.count, ch, 3L * ns - (ns + S - 1) / S, lg);
 }
 
 __device__ inline double block_sum(double v, double* red) {

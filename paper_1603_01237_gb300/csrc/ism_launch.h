@@ -66,6 +66,11 @@ Bounds bounds_of(int kind, int d, const double* H0, const double* H1);
 template <typename R>
 std::vector<R> pack_op(int kind, int d, const double* H0, const double* H1, int G, int E);
 int validate_problem(const ism_problem& p, int precision);
+// The partition of Sec. 2 and its per-sub-interval weights, computed in one place so that every
+// entry point uploads the same bits: j_n = floor(n Nt / N) (N+1 values), beta_n = T / (t_{n+1} - t_n)
+// with t_n = j_n tau (N values), and (cos, sin) of the segment phase c0 tau (j_{n+1} - j_n) (N values).
+void partition(double T, int Nt, int N, double c0, std::vector<int>* jn, std::vector<double>* beta,
+               std::vector<double2>* phase);
 int set_error(int code, const char* msg);
 void clear_error();
 

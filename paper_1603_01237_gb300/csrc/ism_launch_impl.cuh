@@ -24,17 +24,21 @@ cudaError_t launch_assemble_t(const KParams& p, cudaStream_t st) {
   return cudaGetLastError();
 }
 
+// The sub-problems of Algorithm 1 step (c): p.form = 1 (two-trajectory form of a first local step)
+// runs k_subfwd, p.form = 0 (literal sub-problem from phi) the checkpointed k_subinterval.
 template <typename R, class Op>
 cudaError_t launch_subinterval_t(const KParams& p, cudaStream_t st) {
   constexpr int GPB = 128 / Op::G;
   const long groups = (long)p.B * p.N;
   const long grid = (groups + GPB - 1) / GPB;
   const size_t smem = op_smem_bytes<R, Op>();
+  const void* fn = p.form ? reinterpret_cast<const void*>(k_subfwd<R, Op>) : reinterpret_cast<const void*>(k_subinterval<R, Op>);
   if (smem > 40 * 1024) {
-    cudaError_t e = raise_smem_cap(reinterpret_cast<const void*>(k_subinterval<R, Op>));
+    cudaError_t e = raise_smem_cap(fn);
     if (e != cudaSuccess) return e;
   }
-  k_subinterval<R, Op><<<(unsigned)grid, 128, smem, st>>>(p);
+  if (p.form) k_subfwd<R, Op><<<(unsigned)grid, 128, smem, st>>>(p);
+  else k_subinterval<R, Op><<<(unsigned)grid, 128, smem, st>>>(p);
   return cudaGetLastError();
 }
 

@@ -4,10 +4,10 @@
 // Some callers cannot call cudaMalloc where they need this gradient: code running inside another
 // framework's memory pool (the pool owns the device memory and a private cudaMalloc would bypass or
 // fragment it), allocation-free real-time loops, and processes whose device-memory budget is fixed up
-// front.  ism_plan allocates the sweep's scratch (the packed Hamiltonian, the partition and the per-step
-// H1 psi trajectory) with cudaMalloc; this entry point keeps all of it in one file-scope __device__
-// array of ISM_NOALLOC_SCRATCH_BYTES instead and never calls cudaMalloc, cudaFree or any allocating
-// library routine.  The caller passes device buffers for the inputs and outputs.
+// front.  ism_plan allocates the sweep's scratch (the packed Hamiltonian, the partition, the per-step
+// overlaps and the literal sub-problem's checkpoints) with cudaMalloc; this entry point keeps all of it
+// in one file-scope __device__ array of ISM_NOALLOC_SCRATCH_BYTES instead and never calls cudaMalloc,
+// cudaFree or any allocating library routine.  The caller passes device buffers for the inputs and outputs.
 //
 // The array is statically part of the module: every GPU that loads libism.so holds it until the
 // process exits.  All calls share it, and it keeps the last call's contents; the only word that must
@@ -15,6 +15,7 @@
 // before it is read.  Two calls whose work overlaps on the GPU (different streams, or different host
 // threads on one device) race on the array.
 #include <cmath>
+#include <algorithm>
 #include <cstring>
 #include <mutex>
 #include <string>
@@ -51,13 +52,17 @@ int scratch_for_current_device(unsigned char** out) {
   return ISM_OK;
 }
 
-bool is_device_ptr(const void* p) {
+// Memory the kernels may dereference in place: device memory of the current GPU, or managed memory
+// (another GPU's memory would be a peer access, or a fault without peer access enabled).
+bool is_local_device_ptr(const void* p) {
   cudaPointerAttributes a;
   if (cudaPointerGetAttributes(&a, p) != cudaSuccess) {
     cudaGetLastError();
     return false;
   }
-  return a.type == cudaMemoryTypeDevice || a.type == cudaMemoryTypeManaged;
+  if (a.type == cudaMemoryTypeManaged) return true;
+  int dev = -1;
+  return a.type == cudaMemoryTypeDevice && cudaGetDevice(&dev) == cudaSuccess && dev == a.device;
 }
 
 size_t up256(size_t x) { return (x + 255) & ~size_t(255); }
@@ -74,10 +79,19 @@ extern "C" int ism_subinterval_grad_noalloc(const ism_problem* prob, int precisi
   // (H0 = a few grid parameters, H1 unused) and the Pauli kind have other layouts and other sweeps
   if (p.kind != ISM_H_DENSE && p.kind != ISM_H_TRIDIAG && p.kind != ISM_H_BITFLIP)
     return ism::set_error(ISM_EUNSUPPORTED, "the allocation-free entry point covers the dense, tridiagonal and bit-flip kinds");
-  if (!is_device_ptr(phi) || !is_device_ptr(u) || !is_device_ptr(grad) || (Jn && !is_device_ptr(Jn)))
-    return ism::set_error(ISM_EINVAL, "phi, u, grad and Jn must be device memory for the allocation-free entry point");
+  if (!is_local_device_ptr(phi) || !is_local_device_ptr(u) || !is_local_device_ptr(grad) ||
+      (Jn && !is_local_device_ptr(Jn)))
+    return ism::set_error(ISM_EINVAL, "phi, u, grad and Jn must be device memory of the current GPU for the "
+                                      "allocation-free entry point");
+  // the kernel variant ism_plan picks for this problem (a tridiagonal H1 without a diagonal has its own)
+  bool h1diag = true;
+  if (p.kind == ISM_H_TRIDIAG) {
+    h1diag = false;
+    for (int e = 0; e < p.d; ++e) h1diag |= p.H1[e] != 0.0;
+  }
   ism::KernelSet ks;
-  if (!ism::select_kernels(precision, p.kind, p.d, &ks)) return ism::set_error(ISM_EUNSUPPORTED, "no compiled kernel for this kind and d");
+  if (!ism::select_kernels(precision, p.kind, p.d, &ks, h1diag))
+    return ism::set_error(ISM_EUNSUPPORTED, "no compiled kernel for this kind and d");
   if (ks.large) return ism::set_error(ISM_EUNSUPPORTED, "the allocation-free entry point covers d <= 64");
 
   const int d = p.d, B = p.batch < 1 ? 1 : p.batch, GE = ks.G * ks.E;
@@ -89,8 +103,14 @@ extern "C" int ism_subinterval_grad_noalloc(const ism_problem* prob, int precisi
   if (precision == ISM_FP64) { hd = ism::pack_op<double>(p.kind, d, p.H0, p.H1, ks.G, ks.E); op_bytes = hd.size() * r1; }
   else { hf = ism::pack_op<float>(p.kind, d, p.H0, p.H1, ks.G, ks.E); op_bytes = hf.size() * r1; }
 
+  // the literal sub-problem's checkpoints: stride S ~ sqrt(longest sub-interval) (as ism_plan's default)
+  const int nsmax = (p.Nt + p.N - 1) / p.N;
+  int cks = (int)std::ceil(std::sqrt((double)nsmax));
+  cks = cks < 1 ? 1 : (cks > nsmax ? nsmax : cks);
+  const int nck = (nsmax + cks - 1) / cks;
+  const size_t BN = (size_t)B * p.N;
   // scratch layout: op data | FP64 diag(H0) | j_n | beta_n | alpha | status | propagator parameters |
-  // Bessel table | segment phases | FP32 controls | trajectory
+  // Bessel table | segment phases | FP32 controls | per-step overlaps | checkpoints | segment buffer
   const size_t off_h0d = up256(op_bytes);
   const size_t off_jn = off_h0d + up256(sizeof(double) * d);
   const size_t off_beta = off_jn + up256(sizeof(int) * (p.N + 1));
@@ -100,8 +120,10 @@ extern "C" int ism_subinterval_grad_noalloc(const ism_problem* prob, int precisi
   const size_t off_ctab = off_cheb + up256((size_t)B * p.N * ism::cheb_bytes(precision));
   const size_t off_phase = off_ctab + up256(sizeof(double) * ism::BESSEL_TABLE);
   const size_t off_uf = off_phase + up256(sizeof(double2) * p.N);
-  const size_t off_traj = off_uf + up256(sizeof(float) * (size_t)B * p.Nt);
-  const size_t need = off_traj + up256((size_t)B * ((size_t)p.Nt + p.N) * GE * r2);
+  const size_t off_zs = off_uf + up256(sizeof(float) * (size_t)B * p.Nt);
+  const size_t off_ckpt = off_zs + up256((size_t)B * ((size_t)p.Nt + p.N) * r2);
+  const size_t off_segb = off_ckpt + up256(BN * nck * (precision == ISM_FP64 ? 1 : 2) * GE * r2);
+  const size_t need = off_segb + up256(BN * cks * GE * r2);
   if (need > kScratchBytes) {
     std::string m = "problem needs " + std::to_string(need) + " bytes of scratch; the static scratch of the "
                     "allocation-free entry point holds " + std::to_string(kScratchBytes) + " bytes";
@@ -110,12 +132,13 @@ extern "C" int ism_subinterval_grad_noalloc(const ism_problem* prob, int precisi
   unsigned char* base = nullptr;
   if ((rc = scratch_for_current_device(&base)) != ISM_OK) return rc;
 
-  std::vector<int> jn(p.N + 1);
-  for (int n = 0; n <= p.N; ++n) jn[n] = (int)(((long long)n * p.Nt) / p.N);
   const double tau = p.T / p.Nt;
-  std::vector<double> beta(p.N);
-  for (int n = 0; n < p.N; ++n) beta[n] = p.T / (jn[n + 1] * tau - jn[n] * tau);
   ism::Bounds bd = ism::bounds_of(p.kind, d, p.H0, p.H1);
+  const double c0 = 0.5 * (bd.lo + bd.hi);
+  std::vector<int> jn;
+  std::vector<double> beta;
+  std::vector<double2> phase;
+  ism::partition(p.T, p.Nt, p.N, c0, &jn, &beta, &phase);
 
   cudaStream_t st = reinterpret_cast<cudaStream_t>(cuda_stream);
   cudaError_t e = cudaSuccess;
@@ -132,12 +155,6 @@ extern "C" int ism_subinterval_grad_noalloc(const ism_problem* prob, int precisi
   std::vector<double> tab(ism::BESSEL_TABLE);
   ism::bessel_table(tab.data());
   h2d(off_ctab, tab.data(), sizeof(double) * tab.size());
-  const double c0 = 0.5 * (bd.lo + bd.hi);
-  std::vector<double2> phase(p.N);
-  for (int n = 0; n < p.N; ++n) {
-    const double ph = c0 * tau * (double)(jn[n + 1] - jn[n]);
-    phase[n] = make_double2(std::cos(ph), std::sin(ph));
-  }
   h2d(off_phase, phase.data(), sizeof(double2) * phase.size());
   if (e == cudaSuccess) e = cudaMemsetAsync(base + off_status, 0, sizeof(int), st);
   if (e != cudaSuccess) return ism::set_error(ISM_ECUDA, (std::string("scratch upload: ") + cudaGetErrorString(e)).c_str());
@@ -155,8 +172,13 @@ extern "C" int ism_subinterval_grad_noalloc(const ism_problem* prob, int precisi
   k.u = const_cast<double*>(u);
   k.phi = reinterpret_cast<const double2*>(phi);
   k.M = nullptr;
-  k.traj = base + off_traj;
+  k.traj = nullptr;
   k.traj2 = nullptr;
+  k.zs = base + off_zs;
+  k.ckpt = base + off_ckpt;
+  k.segb = base + off_segb;
+  k.cks = cks;
+  k.nck = nck;
   k.grad = grad;
   k.Jn = Jn;
   k.err = nullptr;
@@ -172,6 +194,14 @@ extern "C" int ism_subinterval_grad_noalloc(const ism_problem* prob, int precisi
   k.uf = reinterpret_cast<float*>(base + off_uf);
   k.phase = reinterpret_cast<const double2*>(base + off_phase);
   k.ctab = reinterpret_cast<const double*>(base + off_ctab);
+  // non-finite controls or states: ISM_ENONFINITE (the propagator bound below would drop a NaN)
+  {
+    const long nu = (long)B * p.Nt, nphi = 2L * B * (p.N + 1) * d;
+    ism::k_check_finite<<<(unsigned)std::min<long>(1024, (nu + 255) / 256), 256, 0, st>>>(u, nu, k.status);
+    ism::k_check_finite<<<(unsigned)std::min<long>(1024, (nphi + 255) / 256), 256, 0, st>>>(phi, nphi, k.status);
+    if ((e = cudaGetLastError()) != cudaSuccess)
+      return ism::set_error(ISM_ECUDA, (std::string("launch: ") + cudaGetErrorString(e)).c_str());
+  }
   if ((e = ism::launch_cheb_prep(precision, k, st)) != cudaSuccess)
     return ism::set_error(ISM_ECUDA, (std::string("launch: ") + cudaGetErrorString(e)).c_str());
   if ((e = ks.subinterval(k, st)) != cudaSuccess)

@@ -239,13 +239,14 @@ def test_footprint_needs_no_gpu_and_scales_with_the_problem(lib):
 
 def test_crank_nicolson_option_validated_on_the_host(lib):
     """The Crank-Nicolson scheme is accepted in both precisions for the tridiagonal, dense and bit-flip
-    kinds with d <= 64; its plans hold no second trajectory (the sub-problems run in one group)."""
+    kinds with d <= 64; its plans hold none of the per-step trajectories of the concurrent
+    two-trajectory sweeps (its first local steps run both trajectories forward in one group)."""
     import workloads as W
     from paper_1603_01237_gb300 import abi
 
     w = W.config("rotor41", Nt=2000, N=16)
-    f_cn = abi.footprint(w, precision="fp64", scheme="crank_nicolson", step1=1)
-    f_ch = abi.footprint(w, precision="fp64", step1=1)
+    f_cn = abi.footprint(w, precision="mixed", scheme="crank_nicolson", step1=1)
+    f_ch = abi.footprint(w, precision="mixed", step1=1)
     assert 0 < f_cn < f_ch
     assert abi.footprint(w, precision="mixed", scheme="crank_nicolson") > 0   # FP32 Cayley steps
     assert abi.footprint(W.random_dense(5, 3, T=1.0, Nt=50, N=2), scheme="crank_nicolson") > 0
@@ -336,3 +337,44 @@ def test_server_reports_a_failed_request_without_a_gpu(lib):
         lib.ism_server_poll(srv.handle, C.c_longlong(rid), 0, C.byref(state), None, None, None)
         assert state.value == abi.ISM_REQ_FAILED
         assert lib.ism_server_release(srv.handle, C.c_longlong(rid)) == abi.ISM_OK
+
+
+def test_noalloc_binding_refuses_short_arrays():
+    """The allocation-free entry point reads and writes the caller's device buffers in place as
+    [batch][N+1][2d], [batch][Nt], [batch][Nt] and [batch][N]: the binding refuses a short one before
+    the library is called."""
+    import workloads as W
+    from paper_1603_01237_gb300 import abi
+
+    w = W.config("rotor41", Nt=120, N=6)
+    B, nphi, nu = 3, 2 * 3 * 7 * 41, 3 * 120
+    ok = dict(phi=np.zeros(nphi), u=np.zeros(nu), grad=np.zeros(nu), Jn=np.zeros(3 * 6))
+    for name, n in (("phi", nphi), ("u", nu), ("grad", nu), ("Jn", 3 * 6)):
+        args = dict(ok)
+        args[name] = np.zeros(n - 1)
+        with pytest.raises(ValueError, match=name):
+            abi.subinterval_grad_noalloc(w, "mixed", args["phi"], args["u"], args["grad"], args["Jn"], batch=B)
+
+
+def test_checkpoint_stride_sets_the_literal_footprint(lib):
+    """ckpt_stride S: a literal sub-problem holds ceil(n_steps/S) states and S vectors H1 psi per (problem,
+    n), never its whole trajectory; the FP64 plan (literal form by default) grows accordingly, and the
+    mixed plan, whose first local steps store no states, holds neither unless L > 1.  Negative strides
+    are refused."""
+    import workloads as W
+    from paper_1603_01237_gb300 import abi
+
+    w = W.config("rotor41")                       # Nt = 20000, N = 128: 157 steps per sub-interval
+    B, GE, N = 64, 48, 128                        # the sub-interval sweep holds 16 lanes x 3 elements
+    fp = lambda **kw: abi.footprint(w, batch=B, step1=2, **kw)   # noqa: E731
+    base = fp(precision="mixed")
+    for S in (1, 13, 157):
+        nck = -(-157 // S)
+        lit = B * N * (nck * 2 * GE * 8 + S * GE * 8)            # FP32 hi + lo checkpoints, segment
+        got = fp(precision="mixed", local_iters=2, ckpt_stride=S) - base
+        assert abs(got - lit) <= 2 * 512, (S, got, lit)
+    traj = B * (20000 + N) * GE * 8                               # a whole per-step trajectory
+    assert fp(precision="mixed", local_iters=2) - base < traj / 4   # ~3 sqrt(n_steps) vectors vs n_steps
+    prob, opt, keep = abi.problem_and_options(w, precision="fp64", ckpt_stride=-1)
+    n = C.c_size_t()
+    assert lib.ism_plan_footprint(C.byref(prob), C.byref(opt), C.byref(n)) == abi.ISM_EINVAL

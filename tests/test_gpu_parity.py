@@ -362,3 +362,41 @@ def test_norm_drift_is_recorded_and_removed(P):
                 drift = pl.ism_get_stats()["norm_drift"]
             assert lo <= drift <= hi, (prec, step1, drift)
             assert abs(J[0] - J_o) <= tj
+
+
+@pytest.mark.parametrize("prec,w", [
+    ("fp64", W.config("rotor41", Nt=1001, N=7)),
+    ("mixed", W.config("rotor41", Nt=1001, N=7)),
+    ("fp64", _random_target(W.spin_chain(5, 71, T=4.0, Nt=333, N=5, u_amp=1.5), 5)),
+    ("mixed", W.random_dense(16, 72, T=2.0, Nt=257, N=3)),
+], ids=["rotor-fp64", "rotor-mixed", "bitflip32-fp64", "dense16-mixed"])
+def test_checkpoint_stride_changes_nothing(P, prec, w):
+    """The literal sub-problem stores psi_n every ckpt_stride steps and recomputes each segment from
+    its checkpoint (hi + lo in FP32), repeating the forward sweep exactly: the gradient and J_n are the
+    same bit for bit for every stride (1, a ragged 7, the default, the whole sub-interval) and match
+    the oracle's literal sub-problems."""
+    phi_o = O.intermediate_states(w, w.u0)
+    g_o, Jn_o = O.subinterval_all(w, phi_o, w.u0)
+    res = []
+    for S in (1, 7, 0, 10 ** 6):
+        with P.Plan(w, precision=prec, ckpt_stride=S) as pl:
+            res.append(pl.subinterval_grad(phi_o, w.u0))
+    for g, Jn in res[1:]:
+        assert np.array_equal(g, res[0][0]) and np.array_equal(Jn, res[0][1])
+    tol = FP64_GRAD if prec == "fp64" else MIX_GRAD
+    assert rel_l2(res[0][0][0], g_o) <= tol
+    jt = 1e-12 if prec == "fp64" else 1e-5
+    assert np.max(np.abs(res[0][1][0] - Jn_o)) <= jt * max(1.0, np.abs(Jn_o).max())
+
+
+def test_local_iterations_with_checkpoints_match_algorithm1(P):
+    """L = 3 local steps (the later ones literal, so checkpointed) with a small stride, FP64 and mixed,
+    against the oracle's Algorithm 1."""
+    w = W.config("rotor41", Nt=1200, N=8)
+    iters, L = 2, 3
+    u_o, J_o, F_o, E_o = O.ism_solve(w, w.u0, iters, w.rho, L=L)
+    for prec, tol in (("fp64", 1e-9), ("mixed", 1e-4)):
+        with P.Plan(w, precision=prec, local_iters=L, ckpt_stride=5) as pl:
+            u, J, E = pl.iterate(w.u0, iters)
+        assert np.max(np.abs(J[0] - J_o)) <= tol, (prec, np.max(np.abs(J[0] - J_o)))
+        assert rel_l2(u[0] - w.u0, u_o - w.u0) <= tol
