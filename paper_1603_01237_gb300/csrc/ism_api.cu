@@ -813,10 +813,10 @@ int plan_build(const ism_problem* prob, const ism_options* opt, void* cuda_strea
     P->cks = S < 1 ? 1 : (S > nsmax ? nsmax : S);
     P->nck = (nsmax + P->cks - 1) / P->cks;
   }
-  if (P->ks.large || P->pauli) {
-    unsigned char* dTb = nullptr;
-    TRY_ALLOC(dTb, B * ((size_t)P->Nt + P->N) * GE * P->r2);
-    P->dtraj = dTb;
+  if (P->ks.large) {   // CTA-wide states (bit-flip and Pauli kinds)
+    if (P->form == 1 || P->L > 1) {   // ism_iterate runs literal sub-problems
+      if ((rc = alloc_literal(P)) != ISM_OK) { free_all(P); delete P; return rc; }
+    }
   } else {
     unsigned char* dZ = nullptr;
     TRY_ALLOC(dZ, B * ((size_t)P->Nt + P->N) * P->r2);
@@ -1030,7 +1030,7 @@ int ism_subinterval_grad(ism_plan_t P, const double* phi, const double* u, doubl
     if (!all_finite(phi, nphi)) return fail(ISM_ENONFINITE, "non-finite value in phi");
     ISM_CUDA_TRY(cudaMemcpyAsync(P->dphi, phi, nphi * sizeof(double), cudaMemcpyHostToDevice, P->st));
   }
-  if (!P->ks.large && !P->pauli && (rc = alloc_literal(P)) != ISM_OK) return rc;   // first literal use
+  if ((rc = alloc_literal(P)) != ISM_OK) return rc;   // first literal use
   ism::KParams k = kparams(P, const_cast<double*>(ud));
   k.update = 0;
   k.count = P->dcount + 3;

@@ -1199,10 +1199,12 @@ __device__ void chain_produce(const ChainRing<R>& ring, int* status, int max_spi
     issued = m + 1;
   }
   // the drain has its own bound, independent of the caller's wait cap: copies in flight complete
-  // within microseconds, and none may land after the block exits
+  // within microseconds, and none may land after the block exits.  A drain that gives up leaves
+  // ST_TIMEOUT (the call then reports ISM_ETIMEOUT and the caller should not reuse the context).
   if (issued < ring.U)
     for (int m = issued - ring.NS < 0 ? 0 : issued - ring.NS; m < issued; ++m)
-      mbar_wait(&ring.full[m % ring.NS], (unsigned)((m / ring.NS) & 1), CHAIN_DRAIN_SPIN);
+      if (!mbar_wait(&ring.full[m % ring.NS], (unsigned)((m / ring.NS) & 1), CHAIN_DRAIN_SPIN))
+        atomicOr(status, ST_TIMEOUT);
 }
 
 // One chain of N matvecs over uses m0 .. m0+N-1 of the ring, run by the CW consumer warps; x_0 in

@@ -281,81 +281,35 @@ __global__ void __launch_bounds__(Op::NT) k_lsweep(KParams p) {
 }
 
 // -------------------------------------------------------------------------------- k_lsub
-// grid (N, B), Op::NT threads: sub-problem n of problem b, as k_subinterval (forms 0 and 1), with
-// the state over the CTA.  Per step each warp stores its partial <delta|H1 psi> in zp (slot s, warp w);
-// the FP64 pass sums the W partials.
+// grid (N, B), Op::NT threads: sub-problem n of problem b with the state over the CTA, the two forms
+// of k_subfwd / k_subinterval.  p.form = 1: psi and chi carried forward from psi(t_n), chi(t_n)
+// (proof of Theorem 2), nothing per step stored but the overlap partials.  p.form = 0: the literal
+// sub-problem, psi_n checkpointed every p.cks steps and each segment's H1 psi_n recomputed from its
+// checkpoint for the adjoint sweep.  Per step each warp stores its partial <chi|H1 psi> (form 1) or
+// <delta|H1 psi> (form 0) in zp (slot s, warp w); the FP64 pass sums the W partials.
 template <typename R, class Op>
 __global__ void __launch_bounds__(Op::NT) k_lsub(KParams p) {
   constexpr int E = Op::E, D = Op::D, W = Op::W;
   constexpr bool COMP = sizeof(R) == 4;
+  constexpr int CKP = COMP ? 2 : 1;
   using R2 = typename C2<R>::T;
   __shared__ __align__(16) R2 sbuf[2 * D];
   __shared__ Cheb<R> ch;
   __shared__ double red[32];
   const int n = blockIdx.x, b = blockIdx.y, t = threadIdx.x, lane = t & 31, wid = t >> 5;
   const int j0 = p.jn[n], j1 = p.jn[n + 1], ns = j1 - j0;
+  const long gid = (long)b * p.N + n;
   double* ub = p.u + (long)b * p.Nt;
   const float* ufb = p.uf + (long)b * p.Nt;
   const double beta = p.beta[n];
-  cheb_load_cta<R>(ch, p.cheb, (long)b * p.N + n);
+  cheb_load_cta<R>(ch, p.cheb, gid);
   Op op;
   op.load(reinterpret_cast<const R*>(p.H), sbuf);
   op.scale(p.H0d, ch);
   const int K = ch.K, S = ch.S;
-  const double sPhi = ch.sph, cPhi = ch.cph;
-
   const long off_n = ((long)b * (p.N + 1) + n) * D;
-  const double2* phn = (p.form ? p.psin : p.phi) + off_n;
-  const double2* phn1 = (p.form ? p.chin : p.phi) + off_n + D;
-  Vec<R, E> v, lo;
-  load_state<R, E>(v, lo, phn);
   const long slot0 = (long)b * (p.Nt + p.N) + j0 + n;
-  R2* tr0 = reinterpret_cast<R2*>(p.traj) + slot0 * D;   // slot s: H1 psi_n(t_{j0+s}) at tr0 + s*D
-  R2* zp0 = reinterpret_cast<R2*>(p.zp) + slot0 * W;      // slot s: W warp partials
-  R2* tr = tr0 + t * E;
-
-  // ---- forward sweep: store H1 psi_j, then psi_{j+1} = U_j psi_j
-  {
-    R un = uval<R>(ub, ufb, j0);
-    for (int s = 0; s < ns; ++s) {
-      const R uj = un;
-      if (s + 1 < ns) un = uval<R>(ub, ufb, j0 + s + 1);
-      Vec<R, E> hv;
-      op.h1(v, hv);
-#pragma unroll
-      for (int r = 0; r < E; ++r) { R2 z; z.x = hv.re[r]; z.y = hv.im[r]; tr[(long)s * D + r] = z; }
-      op.set_u(uj, ch, 0);
-      cheb_step<false, COMP>(v, lo, op, ch, K, S);
-    }
-  }
-  Vec<R, E> hend;
-  op.h1(v, hend);
-
-  // ---- terminal residual (see k_subinterval)
-  double nrm = 0.0;
-  Vec<R, E> dl;
-#pragma unroll
-  for (int r = 0; r < E; ++r) {
-    const int e = t * E + r;
-    const double2 z = phn1[e];
-    double dr, di;
-    if (!p.form) {
-      double pr, pi;
-      phase_rotate(cPhi, sPhi, false, (double)v.re[r] + (double)lo.re[r], (double)v.im[r] + (double)lo.im[r], pr, pi);
-      dr = z.x - pr;
-      di = z.y - pi;
-      dl.re[r] = (R)dr;
-      dl.im[r] = (R)di;
-    } else {
-      const double2 ps = p.psin[off_n + D + e];
-      dr = (z.x - ps.x) / beta;
-      di = (z.y - ps.y) / beta;
-      dl.re[r] = (R)z.x;
-      dl.im[r] = (R)z.y;
-    }
-    nrm += dr * dr + di * di;
-  }
-  nrm = cta_sum(nrm, red);
+  R2* zp0 = reinterpret_cast<R2*>(p.zp) + slot0 * W;   // slot s: W warp partials
 
   // per-warp partial of <a|h>, FP32 products
   auto zdot = [&](const Vec<R, E>& a, const Vec<R, E>& h, R2* dst) {
@@ -371,24 +325,119 @@ __global__ void __launch_bounds__(Op::NT) k_lsub(KParams p) {
     }
     if (lane == 0) { R2 z; z.x = xr; z.y = xi; dst[wid] = z; }
   };
-  zdot(dl, hend, zp0 + (long)ns * W);
+  double nrm = 0.0, cPhi = 1.0, sPhi = 0.0;
 
-  // ---- backward sweep: delta_j = U_j^H delta_{j+1}; partials of step j into zp slot j
-  {
-    auto ldslot = [&](int s, Vec<R, E>& h) {
-#pragma unroll
-      for (int r = 0; r < E; ++r) { const R2 z = tr[(long)s * D + r]; h.re[r] = z.x; h.im[r] = z.y; }
-    };
-    Vec<R, E> hn;
-    ldslot(ns - 1, hn);
-    R un = uval<R>(ub, ufb, j1 - 1);
-    for (int s = ns - 1; s >= 0; --s) {
-      const Vec<R, E> hc = hn;
+  if (p.form) {
+    Vec<R, E> a, alo, c, clo;
+    load_state<R, E>(a, alo, p.psin + off_n);
+    load_state<R, E>(c, clo, p.chin + off_n);
+    R un = uval<R>(ub, ufb, j0);
+    for (int s = 0; s < ns; ++s) {
       const R uj = un;
-      if (s >= 1) { ldslot(s - 1, hn); un = uval<R>(ub, ufb, j0 + s - 1); }
+      if (s + 1 < ns) un = uval<R>(ub, ufb, j0 + s + 1);
+      Vec<R, E> hv;
+      op.h1(a, hv);
+      zdot(c, hv, zp0 + (long)s * W);
       op.set_u(uj, ch, 0);
-      cheb_step<true>(dl, op, ch, K, S);
-      zdot(dl, hc, zp0 + (long)s * W);
+      cheb_step<false, COMP>(a, alo, op, ch, K, S);
+      cheb_step<false, COMP>(c, clo, op, ch, K, S);
+    }
+    Vec<R, E> hv;
+    op.h1(a, hv);
+    zdot(c, hv, zp0 + (long)ns * W);
+    // |delta(t_{n+1})|^2, delta = (chi - psi)(t_{n+1}) / beta_n from the FP64 boundary states
+#pragma unroll
+    for (int r = 0; r < E; ++r) {
+      const int e = t * E + r;
+      const double2 x = p.chin[off_n + D + e], y = p.psin[off_n + D + e];
+      const double dr = (x.x - y.x) / beta, di = (x.y - y.y) / beta;
+      nrm += dr * dr + di * di;
+    }
+    nrm = cta_sum(nrm, red);
+  } else {
+    sPhi = ch.sph;
+    cPhi = ch.cph;
+    const int SC = p.cks;
+    R2* ck = reinterpret_cast<R2*>(p.ckpt) + gid * (long)p.nck * CKP * D + t * E;
+    R2* sb = reinterpret_cast<R2*>(p.segb) + gid * (long)SC * D + t * E;
+    const double2* phn = p.phi + off_n;
+    const double2* phn1 = p.phi + off_n + D;
+    Vec<R, E> v, lo;
+    load_state<R, E>(v, lo, phn);
+    // ---- forward sweep: checkpoints, then psi_{s+1} = U_s psi_s
+    {
+      R un = uval<R>(ub, ufb, j0);
+      for (int s = 0; s < ns; ++s) {
+        const R uj = un;
+        if (s + 1 < ns) un = uval<R>(ub, ufb, j0 + s + 1);
+        if (s % SC == 0) {
+          R2* c = ck + (long)(s / SC) * CKP * D;
+#pragma unroll
+          for (int r = 0; r < E; ++r) {
+            R2 z; z.x = v.re[r]; z.y = v.im[r]; c[r] = z;
+            if (COMP) { R2 y; y.x = lo.re[r]; y.y = lo.im[r]; c[D + r] = y; }
+          }
+        }
+        op.set_u(uj, ch, 0);
+        cheb_step<false, COMP>(v, lo, op, ch, K, S);
+      }
+    }
+    Vec<R, E> hend;
+    op.h1(v, hend);
+    // ---- terminal residual delta = phi_{n+1} - psi_n(t_{n+1}) in FP64
+    Vec<R, E> dl;
+#pragma unroll
+    for (int r = 0; r < E; ++r) {
+      const int e = t * E + r;
+      const double2 z = phn1[e];
+      double pr, pi;
+      phase_rotate(cPhi, sPhi, false, (double)v.re[r] + (double)lo.re[r], (double)v.im[r] + (double)lo.im[r], pr, pi);
+      const double dr = z.x - pr, di = z.y - pi;
+      dl.re[r] = (R)dr;
+      dl.im[r] = (R)di;
+      nrm += dr * dr + di * di;
+    }
+    nrm = cta_sum(nrm, red);
+    zdot(dl, hend, zp0 + (long)ns * W);
+    // ---- backward sweep over the segments, last to first
+    const int nck = (ns + SC - 1) / SC;
+    for (int c = nck - 1; c >= 0; --c) {
+      const int s0 = c * SC, s1 = min(s0 + SC, ns);
+      {
+        Vec<R, E> x, xl;
+        const R2* cc = ck + (long)c * CKP * D;
+#pragma unroll
+        for (int r = 0; r < E; ++r) {
+          const R2 z = cc[r];
+          x.re[r] = z.x; x.im[r] = z.y;
+          if (COMP) { const R2 y = cc[D + r]; xl.re[r] = y.x; xl.im[r] = y.y; }
+          else { xl.re[r] = R(0); xl.im[r] = R(0); }
+        }
+        R un = uval<R>(ub, ufb, j0 + s0);
+        for (int s = s0; s < s1; ++s) {
+          const R uj = un;
+          if (s + 1 < s1) un = uval<R>(ub, ufb, j0 + s + 1);
+          Vec<R, E> h;
+          op.h1(x, h);
+#pragma unroll
+          for (int r = 0; r < E; ++r) { R2 z; z.x = h.re[r]; z.y = h.im[r]; sb[(long)(s - s0) * D + r] = z; }
+          if (s + 1 < s1) {
+            op.set_u(uj, ch, 0);
+            cheb_step<false, COMP>(x, xl, op, ch, K, S);
+          }
+        }
+      }
+      R un = uval<R>(ub, ufb, j0 + s1 - 1);
+      for (int s = s1 - 1; s >= s0; --s) {
+        const R uj = un;
+        if (s - 1 >= s0) un = uval<R>(ub, ufb, j0 + s - 1);
+        Vec<R, E> hc;
+#pragma unroll
+        for (int r = 0; r < E; ++r) { const R2 z = sb[(long)(s - s0) * D + r]; hc.re[r] = z.x; hc.im[r] = z.y; }
+        op.set_u(uj, ch, 0);
+        cheb_step<true>(dl, op, ch, K, S);
+        zdot(dl, hc, zp0 + (long)s * W);
+      }
     }
   }
   __syncthreads();   // every warp's partials are written
@@ -421,11 +470,11 @@ __global__ void __launch_bounds__(Op::NT) k_lsub(KParams p) {
   err = cta_sum(err, red);
   pen = cta_sum(pen, red);
   if (t == 0) {
-    const long gid = (long)b * p.N + n;
     if (p.Jn) p.Jn[gid] = p.w * (-0.5 * nrm) - 0.5 * tb * pen;
     if (p.err) p.err[gid] = err;
   }
-  if (t == 0) count_work<R>(p.count, ch, 2L * ns, 0);   // forward U and backward U^H sweeps
+  // psi and chi forward (form 1); forward, recomputation and adjoint (form 0)
+  if (t == 0) count_work<R>(p.count, ch, p.form ? 2L * ns : 3L * ns - (ns + p.cks - 1) / p.cks, 0);
 }
 
 }  // namespace ism

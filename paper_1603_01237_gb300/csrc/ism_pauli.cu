@@ -223,14 +223,17 @@ __global__ void __launch_bounds__(32 * W) k_pauli_sweep(KParams p) {
 }
 
 // ------------------------------------------------------------------------------ k_pauli_sub
-// grid (N, B): sub-problem n of problem b (forms 0 and 1 as k_subinterval).  Slot s of the sub-interval
-// (s = 0..ns) holds psi_n(t_{j0+s}) in traj and the 2q overlaps <delta_s|X_b psi_s>, <delta_s|Y_b psi_s>
-// in zq (delta: the sub-problem adjoint in the delta form, or chi in form 1).
+// grid (N, B): sub-problem n of problem b, the two forms of k_subfwd / k_subinterval.  Slot s of the
+// sub-interval (s = 0..ns) receives the 2q overlaps <a_s|X_b psi_s>, <a_s|Y_b psi_s> in zq, a = chi
+// (form 1: psi and chi carried forward from psi(t_n), chi(t_n), nothing per step stored) or a = delta
+// (form 0: the literal sub-problem's adjoint in the delta form; psi_n checkpointed every p.cks steps
+// and each segment's states recomputed from its checkpoint into a buffer of p.cks states).
 template <typename R, int W>
 __global__ void __launch_bounds__(32 * W) k_pauli_sub(KParams p) {
   using Op = OpPauliCTA<R, W>;
   constexpr int E = 4, D = Op::D, Q = Op::Q, NT = 32 * W;
   constexpr bool COMP = sizeof(R) == 4;
+  constexpr int CKP = COMP ? 2 : 1;
   using R2 = typename C2<R>::T;
   __shared__ __align__(16) R2 sbuf[2 * D];
   __shared__ R2 zred[W][2 * Q];
@@ -239,70 +242,23 @@ __global__ void __launch_bounds__(32 * W) k_pauli_sub(KParams p) {
   __shared__ double red[32];
   const int n = blockIdx.x, b = blockIdx.y, t = threadIdx.x, lane = t & 31, wid = t >> 5;
   const int j0 = p.jn[n], j1 = p.jn[n + 1], ns = j1 - j0, m = p.m;
+  const long gid = (long)b * p.N + n;
   const double beta = p.beta[n];
   for (int i = t; i < m * Q * 2; i += NT) wsm[i] = p.wts[i];
-  cheb_load_cta<R>(ch, p.cheb, (long)b * p.N + n);
+  cheb_load_cta<R>(ch, p.cheb, gid);
   const R* cb = reinterpret_cast<const R*>(p.cxy) + (long)b * p.Nt * 2 * Q;
   Op op;
   op.load(sbuf);
   op.scale(p.H0d, ch);
   const int K = ch.K, S = ch.S;
-  const double sPhi = ch.sph, cPhi = ch.cph;
-
   const long off_n = ((long)b * (p.N + 1) + n) * D;
-  const double2* phn = (p.form ? p.psin : p.phi) + off_n;
-  const double2* phn1 = (p.form ? p.chin : p.phi) + off_n + D;
-  Vec<R, E> v, lo;
-  load_state<R, E>(v, lo, phn);
   const long slot0 = (long)b * (p.Nt + p.N) + j0 + n;
-  R2* tr = reinterpret_cast<R2*>(p.traj) + slot0 * D + t * E;   // slot s at tr + s*D
   R2* zq0 = reinterpret_cast<R2*>(p.zq) + slot0 * 2 * Q;         // slot s at zq0 + s*2Q
 
-  auto store_slot = [&](int s, const Vec<R, E>& x) {
-#pragma unroll
-    for (int r = 0; r < E; ++r) { R2 z; z.x = x.re[r]; z.y = x.im[r]; tr[(long)s * D + r] = z; }
-  };
-  // ---- forward sweep: psi_n at every slot
-  for (int s = 0; s < ns; ++s) {
-    store_slot(s, v);
-    op.set_step(cb + (long)(j0 + s) * 2 * Q, ch);
-    cheb_step<false, COMP>(v, lo, op, ch, K, S);
-  }
-  store_slot(ns, v);
-
-  // ---- terminal residual (see k_subinterval)
-  double nrm = 0.0;
-  Vec<R, E> dl;
-#pragma unroll
-  for (int r = 0; r < E; ++r) {
-    const int e = t * E + r;
-    const double2 z = phn1[e];
-    double dr, di;
-    if (!p.form) {
-      double pr, pi;
-      phase_rotate(cPhi, sPhi, false, (double)v.re[r] + (double)lo.re[r], (double)v.im[r] + (double)lo.im[r], pr, pi);
-      dr = z.x - pr;
-      di = z.y - pi;
-      dl.re[r] = (R)dr;
-      dl.im[r] = (R)di;
-    } else {
-      const double2 ps = p.psin[off_n + D + e];
-      dr = (z.x - ps.x) / beta;
-      di = (z.y - ps.y) / beta;
-      dl.re[r] = (R)z.x;
-      dl.im[r] = (R)z.y;
-    }
-    nrm += dr * dr + di * di;
-  }
-  nrm = cta_sum(nrm, red);
-
-  // ---- per-slot overlaps <a|X_b psi_s>, <a|Y_b psi_s> for every bit b (FP32 products in mixed mode):
-  // psi_s goes through the op's next exchange buffer; each bit's four partial sums are reduced over
-  // the warp at once, the W warp partials summed by 2Q threads after one barrier.
-  auto overlaps = [&](int s, const Vec<R, E>& a) {
-    Vec<R, E> ps;
-#pragma unroll
-    for (int r = 0; r < E; ++r) { const R2 z = tr[(long)s * D + r]; ps.re[r] = z.x; ps.im[r] = z.y; }
+  // ---- overlaps <a|X_b ps>, <a|Y_b ps> for every bit b into slot s (FP32 products in mixed mode):
+  // ps goes through the op's next exchange buffer; each bit's four partial sums are reduced over the
+  // warp at once, the W warp partials summed by 2Q threads after one barrier.
+  auto overlaps = [&](int s, const Vec<R, E>& a, const Vec<R, E>& ps) {
     R2* xb = op.next_buf();
     xstore<R, D>(xb, ps);
     __syncthreads();
@@ -352,12 +308,96 @@ __global__ void __launch_bounds__(32 * W) k_pauli_sub(KParams p) {
     }
   };
 
-  // ---- backward sweep: delta_j = U_j^H delta_{j+1}; overlaps at every slot
-  overlaps(ns, dl);
-  for (int s = ns - 1; s >= 0; --s) {
-    op.set_step(cb + (long)(j0 + s) * 2 * Q, ch);
-    cheb_step<true>(dl, op, ch, K, S);
-    overlaps(s, dl);
+  double nrm = 0.0, cPhi = 1.0, sPhi = 0.0;
+  if (p.form) {
+    Vec<R, E> a, alo, c, clo;
+    load_state<R, E>(a, alo, p.psin + off_n);
+    load_state<R, E>(c, clo, p.chin + off_n);
+    for (int s = 0; s < ns; ++s) {
+      overlaps(s, c, a);
+      op.set_step(cb + (long)(j0 + s) * 2 * Q, ch);
+      cheb_step<false, COMP>(a, alo, op, ch, K, S);
+      cheb_step<false, COMP>(c, clo, op, ch, K, S);
+    }
+    overlaps(ns, c, a);
+    // |delta(t_{n+1})|^2, delta = (chi - psi)(t_{n+1}) / beta_n from the FP64 boundary states
+#pragma unroll
+    for (int r = 0; r < E; ++r) {
+      const int e = t * E + r;
+      const double2 x = p.chin[off_n + D + e], y = p.psin[off_n + D + e];
+      const double dr = (x.x - y.x) / beta, di = (x.y - y.y) / beta;
+      nrm += dr * dr + di * di;
+    }
+    nrm = cta_sum(nrm, red);
+  } else {
+    sPhi = ch.sph;
+    cPhi = ch.cph;
+    const int SC = p.cks;
+    R2* ck = reinterpret_cast<R2*>(p.ckpt) + gid * (long)p.nck * CKP * D + t * E;
+    R2* sb = reinterpret_cast<R2*>(p.segb) + gid * (long)SC * D + t * E;
+    const double2* phn1 = p.phi + off_n + D;
+    Vec<R, E> v, lo;
+    load_state<R, E>(v, lo, p.phi + off_n);
+    // ---- forward sweep: checkpoints
+    for (int s = 0; s < ns; ++s) {
+      if (s % SC == 0) {
+        R2* c = ck + (long)(s / SC) * CKP * D;
+#pragma unroll
+        for (int r = 0; r < E; ++r) {
+          R2 z; z.x = v.re[r]; z.y = v.im[r]; c[r] = z;
+          if (COMP) { R2 y; y.x = lo.re[r]; y.y = lo.im[r]; c[D + r] = y; }
+        }
+      }
+      op.set_step(cb + (long)(j0 + s) * 2 * Q, ch);
+      cheb_step<false, COMP>(v, lo, op, ch, K, S);
+    }
+    // ---- terminal residual delta = phi_{n+1} - psi_n(t_{n+1}) in FP64
+    Vec<R, E> dl;
+#pragma unroll
+    for (int r = 0; r < E; ++r) {
+      const int e = t * E + r;
+      const double2 z = phn1[e];
+      double pr, pi;
+      phase_rotate(cPhi, sPhi, false, (double)v.re[r] + (double)lo.re[r], (double)v.im[r] + (double)lo.im[r], pr, pi);
+      const double dr = z.x - pr, di = z.y - pi;
+      dl.re[r] = (R)dr;
+      dl.im[r] = (R)di;
+      nrm += dr * dr + di * di;
+    }
+    nrm = cta_sum(nrm, red);
+    overlaps(ns, dl, v);
+    // ---- backward sweep over the segments, last to first
+    const int nck = (ns + SC - 1) / SC;
+    for (int c = nck - 1; c >= 0; --c) {
+      const int s0 = c * SC, s1 = min(s0 + SC, ns);
+      {
+        Vec<R, E> x, xl;
+        const R2* cc = ck + (long)c * CKP * D;
+#pragma unroll
+        for (int r = 0; r < E; ++r) {
+          const R2 z = cc[r];
+          x.re[r] = z.x; x.im[r] = z.y;
+          if (COMP) { const R2 y = cc[D + r]; xl.re[r] = y.x; xl.im[r] = y.y; }
+          else { xl.re[r] = R(0); xl.im[r] = R(0); }
+        }
+        for (int s = s0; s < s1; ++s) {
+#pragma unroll
+          for (int r = 0; r < E; ++r) { R2 z; z.x = x.re[r]; z.y = x.im[r]; sb[(long)(s - s0) * D + r] = z; }
+          if (s + 1 < s1) {
+            op.set_step(cb + (long)(j0 + s) * 2 * Q, ch);
+            cheb_step<false, COMP>(x, xl, op, ch, K, S);
+          }
+        }
+      }
+      for (int s = s1 - 1; s >= s0; --s) {
+        op.set_step(cb + (long)(j0 + s) * 2 * Q, ch);
+        cheb_step<true>(dl, op, ch, K, S);
+        Vec<R, E> ps;
+#pragma unroll
+        for (int r = 0; r < E; ++r) { const R2 z = sb[(long)(s - s0) * D + r]; ps.re[r] = z.x; ps.im[r] = z.y; }
+        overlaps(s, dl, ps);
+      }
+    }
   }
   __syncthreads();   // every slot's overlaps are written
 
@@ -389,10 +429,9 @@ __global__ void __launch_bounds__(32 * W) k_pauli_sub(KParams p) {
   }
   err = cta_sum(err, red);
   if (t == 0) {
-    const long gid = (long)b * p.N + n;
     if (p.Jn) p.Jn[gid] = p.w * (-0.5 * nrm);
     if (p.err) p.err[gid] = err;
-    count_work<R>(p.count, ch, 2L * ns, 0);
+    count_work<R>(p.count, ch, p.form ? 2L * ns : 3L * ns - (ns + p.cks - 1) / p.cks, 0);
   }
 }
 

@@ -231,7 +231,12 @@ def test_footprint_needs_no_gpu_and_scales_with_the_problem(lib):
     assert 0 < f1 < f2 < f4
     assert abs((f4 - f2) - 2 * (f2 - f1)) <= 8 * 512   # per-problem part, up to allocation rounding
     assert abi.footprint(W.config("rotor41", Nt=4000, N=16)) > f1
-    assert abi.footprint(W.config("ising1024", Nt=2000, N=16)) > 2000 * 1024 * 8   # per-step trajectory
+    # d = 1024: the sub-problems store no per-step states (first local steps recompute both trajectories
+    # from the partition, literal ones checkpoint), so 18000 more steps add per-step scalars, not states
+    f_short, f_long = abi.footprint(W.config("ising1024", Nt=2000, N=16)), abi.footprint(W.config("ising1024", Nt=20000, N=16))
+    assert 0 < f_long - f_short < 18000 * 1024 * 8 / 50
+    f_lit = abi.footprint(W.config("ising1024", Nt=20000, N=16), precision="fp64")
+    assert f_lit - abi.footprint(W.config("ising1024", Nt=2000, N=16), precision="fp64") < 18000 * 1024 * 16 / 5
     with pytest.raises(abi.IsmError) as ei:
         abi.footprint(W.config("rotor41", Nt=100, N=200))
     assert ei.value.status == 1

@@ -116,3 +116,36 @@ def test_autograd_function(P):
         g, Jr = pl.gradient(U)
     assert np.array_equal(J.detach().cpu().numpy(), Jr)
     assert np.allclose(u.grad.cpu().numpy(), np.stack([g[0], -2.0 * g[1]]), rtol=0, atol=0)
+
+
+@pytest.mark.parametrize("prec,tol", [("fp64", 1e-8), ("mixed", 1e-4)])
+def test_gp_autograd_function_vs_central_differences(P, prec, tol):
+    """The condensate's adjoint through torch.autograd: J = objective(u, plan) on a 64-point grid,
+    J.backward() runs ism_gradient (exact reverse mode of the split-step map), and u.grad equals central
+    differences of J (FP64 plan, h = 1e-5) to their truncation error, and the FP64 oracle's
+    reverse-mode gradient at the stated tolerance."""
+    import torch
+
+    from paper_1603_01237_gb300.autograd import objective
+
+    w = _gp(Nt=40, N=4, T=0.8)
+    rng = np.random.default_rng(5)
+    U = np.stack([w.u0, rng.uniform(-0.5, 0.5, w.Nt)])
+    with P.Plan(w, precision=prec, batch=2) as pl:
+        u = torch.tensor(U, dtype=torch.float64, device="cuda", requires_grad=True)
+        J = objective(u, pl)
+        J.sum().backward()
+        g = u.grad.cpu().numpy()
+    h = 1e-5
+    idx = [0, 17, 39]
+    for b in range(2):
+        V = np.repeat(U[b][None], 2 * len(idx), axis=0)
+        for k, j in enumerate(idx):
+            V[2 * k, j] += h
+            V[2 * k + 1, j] -= h
+        with P.Plan(w, precision="fp64", batch=V.shape[0]) as pl:
+            Jp, _ = pl.evaluate(V)
+        fd = np.array([(Jp[2 * k] - Jp[2 * k + 1]) / (2 * h) for k in range(len(idx))])
+        assert np.max(np.abs(g[b][idx] - fd)) <= max(tol, 1e-8) * np.max(np.abs(fd)), (b, g[b][idx], fd)
+        g_o = G.global_gradient(w, U[b])
+        assert rel(g[b], g_o) <= (1e-10 if prec == "fp64" else tol), rel(g[b], g_o)

@@ -30,11 +30,12 @@ def _load(name):
 
 
 @pytest.mark.parametrize("prec,tolJ,tolu", [("fp64", 1e-9, 1e-9), ("mixed", 1e-5, 1e-4)])
-@pytest.mark.parametrize("N,step1", [(16, 1), (128, 1), (128, 2)])
+@pytest.mark.parametrize("N,step1", [(16, 1), (64, 1), (64, 2), (128, 1), (128, 2)])
 def test_rotor41_50_iterations(P, prec, tolJ, tolu, N, step1):
     """J[u^(k)] for k = 0..50 and sampled final controls; with one local step the iterates do not depend
-    on N (Theorem 2), so one oracle history serves N = 16 and 128; step1 = 2 takes the global
-    trajectories by direct sweeps instead of assembly."""
+    on N (Theorem 2, N-independence of Sec. 4), so one oracle history serves N = 16, 64 (the uneven
+    312/313-step partition) and 128; step1 = 2 takes the global trajectories by direct sweeps instead
+    of assembly.  Err_k = sum_n |g_n| depends on N and is compared where the history was taken."""
     g = _load("rotor41.json")
     w = W.config("rotor41", N=N)
     with P.Plan(w, precision=prec, step1=step1) as pl:
@@ -46,6 +47,37 @@ def test_rotor41_50_iterations(P, prec, tolJ, tolu, N, step1):
     idx = np.array(g["u_final_idx"])
     du = u[0][idx] - np.array(g["u_final"])
     assert np.linalg.norm(du) <= tolu * np.linalg.norm(np.array(g["u_final"]) - w.u0[idx])
+    if N == g["N"]:
+        E_o = np.array(g["err_hist"])
+        assert np.max(np.abs(E[0] - E_o) / E_o) <= tolu, np.max(np.abs(E[0] - E_o) / E_o)
+
+
+def test_rotor41_benchmark_batch_50_iterations(P):
+    """The benchmark's own launch configuration: 4864 problems per plan, mixed precision, full size,
+    global trajectories by direct sweeps in the wide lane layout.  Problem 0 (the seeded u0) follows
+    the stored oracle history for 50 iterations; other rows (controls drawn like the benchmark's) agree
+    with their own one-problem plans, which take the assembly path."""
+    g = _load("rotor41.json")
+    w = W.config("rotor41")
+    B = 4864
+    rng = np.random.default_rng(2000)
+    amp = float(np.max(np.abs(w.u0)))
+    U0 = np.stack([w.u0] + [rng.uniform(-amp, amp, w.Nt) for _ in range(B - 1)])
+    with P.Plan(w, precision="mixed", batch=B) as pl:
+        assert pl.info(6) == 2 and pl.info(9) == 8     # direct sweeps, 8 lanes x 6 elements per problem
+        u, J, E = pl.iterate(U0, g["iters"])
+    J_o = np.array(g["J_hist"])
+    assert np.max(np.abs(J[0] - J_o)) <= 1e-5, np.max(np.abs(J[0] - J_o))
+    idx = np.array(g["u_final_idx"])
+    du = u[0][idx] - np.array(g["u_final"])
+    assert np.linalg.norm(du) <= 1e-4 * np.linalg.norm(np.array(g["u_final"]) - w.u0[idx])
+    E_o = np.array(g["err_hist"])
+    assert np.max(np.abs(E[0] - E_o) / E_o) <= 1e-4
+    for b in (1, 2431, 4863):
+        with P.Plan(w, precision="mixed") as p1:
+            u1, J1, _ = p1.iterate(U0[b], g["iters"])
+        assert np.max(np.abs(J[b] - J1[0])) <= 1e-5, (b, np.max(np.abs(J[b] - J1[0])))
+        assert np.linalg.norm(u[b] - u1[0]) <= 1e-4 * np.linalg.norm(u1[0] - U0[b])
 
 
 @pytest.mark.parametrize("prec,tol", [("fp64", 1e-10), ("mixed", 1e-4)])
@@ -63,10 +95,13 @@ def test_rotor41_first_subinterval_gradient(P, prec, tol):
     ref = np.array(g["grad"])
     assert np.linalg.norm(grad[0][idx] - ref) <= tol * np.linalg.norm(ref)
     assert abs(np.linalg.norm(grad[0]) - g["grad_l2"]) <= tol * g["grad_l2"]
+    Jn_o = np.array(g["Jn"])
+    jt = 1e-12 if prec == "fp64" else 1e-5
+    assert np.max(np.abs(Jn[0] - Jn_o)) <= jt * max(1.0, np.abs(Jn_o).max()), np.max(np.abs(Jn[0] - Jn_o))
 
 
 # ---------------------------------------------------------------- condensate, 512-point grid
-@pytest.mark.parametrize("prec,tolJ,tolu", [("fp64", 1e-9, 1e-8), ("mixed", 1e-5, 1e-3)])
+@pytest.mark.parametrize("prec,tolJ,tolu", [("fp64", 1e-9, 1e-8), ("mixed", 1e-5, 1e-4)])
 def test_gp512_20_iterations(P, prec, tolJ, tolu):
     """The condensate benchmark problem (Nt=10000, N=64): J[u^(k)] for k = 0..20 and sampled final
     controls against the stored oracle history."""

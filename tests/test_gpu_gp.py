@@ -70,7 +70,7 @@ def test_gp_iterate(P, prec, tol):
         _, F = pl.evaluate(u[0])
     assert np.max(np.abs(J[0] - J_o)) <= tol, np.max(np.abs(J[0] - J_o))
     assert abs(F[0] - F_o[-1]) <= tol
-    assert rel(E[0], E_o) <= 1e-3 if prec == "mixed" else rel(E[0], E_o) <= 1e-9
+    assert rel(E[0], E_o) <= (1e-4 if prec == "mixed" else 1e-9), rel(E[0], E_o)
 
 
 def test_gp_n_independence(P):
@@ -92,7 +92,7 @@ def test_double_well_iterate(P, prec, tol):
         _, F = pl.evaluate(u[0])
     assert np.max(np.abs(J[0] - J_o)) <= tol, np.max(np.abs(J[0] - J_o))
     assert abs(F[0] - F_o[-1]) <= tol
-    assert rel(E[0], E_o) <= 1e-3 if prec == "mixed" else rel(E[0], E_o) <= 1e-9
+    assert rel(E[0], E_o) <= (1e-4 if prec == "mixed" else 1e-9), rel(E[0], E_o)
 
 
 def test_double_well_full_size_mixed(P):
