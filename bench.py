@@ -50,8 +50,8 @@ SAMPLE_DIV = {"rotor41": 8, "spin16": 1, "ising1024": 64, "gp512": 8, "gp512dw":
 BATCH_DEFAULT = {"rotor41": 4864, "spin16": 2432, "ising1024": 76, "gp512": 304, "gp512dw": 304, "spin5": 76}
 SOLVE_ITERS = {"rotor41": 50, "spin16": 20, "ising1024": 20, "gp512": 20, "gp512dw": 20, "spin5": 20}   # oracle sample = Nt/div steps, N/div sub-intervals
 FP32_LANES_PER_SM = 128
-SMS = 152
-SM_MAX_MHZ = 2070.0
+SM_MAX_MHZ_GB300 = 2070.0   # fallback when nvidia-smi cannot be read
+
 
 
 def parse():
@@ -69,6 +69,8 @@ def parse():
     ap.add_argument("--no-fp64", action="store_true")
     ap.add_argument("--no-serving", action="store_true")
     ap.add_argument("--no-cn", action="store_true", help="skip the Crank-Nicolson (Sec. 3 scheme) leg")
+    ap.add_argument("--no-configs", action="store_true",
+                    help="skip the full-size lines of the other configurations (spin16, gp512, ising1024)")
     return ap.parse_args()
 
 
@@ -196,8 +198,40 @@ def gp_pair_flops(n: int) -> float:
     return 10.0 * n * np.log2(n) + 12.0 * n
 
 
-def fp32_peak_tflops() -> float:
-    return SMS * FP32_LANES_PER_SM * 2 * SM_MAX_MHZ * 1e6 / 1e12
+_PEAKS = {}
+
+
+def alu_peak(P, which: str) -> dict:
+    """The ALU roofline's peak: the FMA rate measured on this GPU by the library's own probe
+    (ism_measure_peak: independent packed-FFMA2 or FP64 FMA chains on every SM, best of three timed
+    launches), beside the figure derived from the device's SM count and the sampled maximum clock."""
+    if which not in _PEAKS:
+        import torch
+
+        from paper_1603_01237_gb300 import abi
+
+        sms = torch.cuda.get_device_properties(torch.cuda.current_device()).multi_processor_count
+        mhz = max_sm_mhz()
+        per = FP32_LANES_PER_SM * 2 if which == "fp32" else 2 * 2   # flops per SM per clock
+        derived = sms * per * mhz * 1e6 / 1e12
+        try:
+            meas = abi.measure_peak(which)
+            _PEAKS[which] = {"peak": meas, "source": f"measured: ism_measure_peak({which}) on {sms} SMs "
+                                                     f"(derived {derived:.1f} from {sms} SMs x {per} flop/clk x {mhz:g} MHz)"}
+        except Exception as exc:   # noqa: BLE001 - reported in the line
+            _PEAKS[which] = {"peak": derived, "source": f"derived: {sms} SMs x {per} flop/clk x {mhz:g} MHz "
+                                                        f"(measurement failed: {exc})"}
+    return _PEAKS[which]
+
+
+def max_sm_mhz() -> float:
+    """The GPU's maximum SM clock as nvidia-smi reports it (clocks.max.sm), else the GB300 figure."""
+    try:
+        out = subprocess.run(["nvidia-smi", "-i", os.environ.get("LOCAL_RANK", "0"), "--query-gpu=clocks.max.sm",
+                              "--format=csv,noheader,nounits"], capture_output=True, text=True, timeout=20)
+        return float(out.stdout.strip().splitlines()[0])
+    except Exception:   # noqa: BLE001
+        return SM_MAX_MHZ_GB300
 
 
 # ------------------------------------------------------------------------------ CPU oracle
@@ -340,8 +374,6 @@ def serving_mix(P, W, seed: int, n_req: int = 48, rate: float = 200.0, slots: in
 # ------------------------------------------------------------------------------ our arm
 # ------------------------------------------------------------------------------ Crank-Nicolson leg
 CN_BATCH = 1024   # saturates the FP64 pipe (256 problems per launch take the same time per launch)
-FP64_PEAK_TFLOPS = SMS * 2 * 2 * SM_MAX_MHZ * 1e6 / 1e12
-FP64_SRC = "derived: 152 SMs x 2 FP64 FMA/clk x 2 flop x 2070 MHz (no measured FP64 peak)"
 
 
 def cn_jacobi_iterations(w, tol: float = 1e-17) -> int:
@@ -391,8 +423,9 @@ def crank_nicolson_leg(P, w, stream, steps: int, cpu: bool):
     ms_launch = st["ms"][dom] / n
     flops = 2.0 * w.Nt * B * cn_flops_per_state_step(int(w.d), K)   # two sweeps per launch
     achieved = flops / (ms_launch / 1e3) / 1e12
-    roof = {"kernel": names[dom], "bound": "alu", "achieved": achieved, "peak": FP64_PEAK_TFLOPS,
-            "unit": "TFLOP/s", "frac": achieved / FP64_PEAK_TFLOPS, "traffic": None, "peak_source": FP64_SRC,
+    pk = alu_peak(P, "fp64")
+    roof = {"kernel": names[dom], "bound": "alu", "achieved": achieved, "peak": pk["peak"],
+            "unit": "TFLOP/s", "frac": achieved / pk["peak"], "traffic": None, "peak_source": pk["source"],
             "flops_per_launch": flops, "ms_per_launch": ms_launch}
     p1 = P.Plan(w, precision="fp64", batch=1, stream=stream, scheme="crank_nicolson")
     u1 = torch.tensor(w.u0, dtype=torch.float64, device="cuda").reshape(1, -1).contiguous()
@@ -452,6 +485,175 @@ def W_config(w, Nt: int, N: int):
     return W.config(w.name, Nt=Nt, N=N)
 
 
+# precision each configuration is specified in, and the parity bar its full-size run is tested at
+CONFIG_PRECISION = {"rotor41": "mixed", "spin16": "fp64", "gp512": "mixed", "gp512dw": "mixed", "ising1024": "mixed",
+                    "spin5": "mixed"}
+TESTED = {
+    "rotor41": "J within 1e-5, controls within 1e-4, Err within 1e-4 of the FP64 oracle over 50 iterations, "
+               "this 4864-problem plan included (tests/test_gpu_fullsize.py)",
+    "spin16": "J, F and controls within 1e-9 of the FP64 oracle over 20 iterations (tests/test_gpu_parity.py)",
+    "gp512": "J within 1e-5, controls within 1e-4 of the FP64 oracle over 20 iterations; gradient within 1e-4 "
+             "(tests/test_gpu_fullsize.py)",
+    "gp512dw": "J within 1e-5 over 2 iterations, gradient within 1e-4 (tests/test_gpu_gp.py)",
+    "ising1024": "J within 1e-5, controls within 1e-4 of the FP64 oracle over 2 iterations; sub-interval gradient "
+                 "within 1e-4 (tests/test_gpu_fullsize.py)",
+    "spin5": "J within 1e-4 of the density-matrix oracle at the paper's size (tests/test_gpu_pauli.py)",
+}
+SUB_CONFIGS = ("spin16", "gp512", "ising1024")
+
+
+def state_steps_per_iteration(plan, w) -> tuple:
+    """Complex state-steps (one U_j applied to one state) of one ISM iteration of one problem, as the
+    plan's kernels execute them: 2 Nt for the global sweeps (direct) and, per sub-interval, psi and chi
+    carried forward (2 Nt; the first local step of the two-trajectory form) or the literal
+    sub-problem's forward sweep, its recomputation from the checkpoints and the adjoint (~3 Nt); the
+    grid model stores its forward states (2 Nt global + 2 Nt sub-interval)."""
+    if plan.gp:
+        return 4 * w.Nt, "2 Nt global sweeps + 2 Nt sub-interval sweeps"
+    if plan.precision == "mixed":
+        return 4 * w.Nt, "2 Nt global sweeps + 2 Nt sub-interval sweeps (psi and chi forward)"
+    return 5 * w.Nt, "2 Nt global sweeps + ~3 Nt literal sub-problems (forward, recomputation, adjoint)"
+
+
+def oracle_worker(cfg: str, N, seconds: float):
+    """One host process: repeat the bounded oracle sample for about `seconds`; (samples, busy s, scale)."""
+    tot, n, scale, sample = 0.0, 0, 1.0, ""
+    while tot < seconds and n < 50:
+        dt, scale, sample = oracle_sample(cfg, N)
+        tot += dt
+        n += 1
+    return n, tot, scale, sample
+
+
+def cpu_baseline_of(cfg: str, N, seconds: float = 10.0) -> dict:
+    """The oracle on the host: one process (the sequential t(eps, 1) of Sec. 4), and one process per host
+    core running independent samples at once (the N-processor analogue); value = the all-core rate."""
+    import concurrent.futures as cf
+    import multiprocessing as mp
+
+    n1, t1, scale, sample = oracle_worker(cfg, N, seconds)
+    one = n1 * scale / t1
+    cores = os.cpu_count() or 1
+    allc, used = one, 1
+    if cores > 1:
+        try:   # spawn: this process has a CUDA context, a forked child would inherit it
+            with cf.ProcessPoolExecutor(max_workers=cores, mp_context=mp.get_context("spawn")) as ex:
+                res = list(ex.map(oracle_worker, [cfg] * cores, [N] * cores, [seconds] * cores))
+            allc = sum(n * sc / t for n, t, sc, _ in res)
+            used = cores
+        except Exception:   # noqa: BLE001 - the single-core figure stands
+            pass
+    return {"value": allc, "unit": UNIT, "cores": used, "kind": "oracle",
+            "sample": f"{sample}; {used} host processes at once, about {seconds:g} s each (the rate is summed over "
+                      f"them)", "single_core": {"value": one, "cores": 1, "seconds": t1, "repetitions": n1},
+            "host_cores": cores}
+
+
+def measure_config(P, W, cfg: str, args, stream, steps: int, warmup: int, world: int, rank: int, N=None, Nt=None,
+                   batch=None) -> dict:
+    """Batched ISM iterations of one configuration at full size: CUDA-event time per iteration (L2
+    flushed between steps), the roofline of the dominant phase (algorithmic flops from the kernels' work
+    counters over the measured FMA peak) and the phase shares."""
+    import torch
+
+    w = load_workload(cfg, N=N, Nt=Nt)
+    d = dim_of(w)
+    B = batch or BATCH_DEFAULT.get(cfg, 1)
+    prec = CONFIG_PRECISION.get(cfg, "mixed")
+    plan = P.Plan(w, precision=prec, batch=B, stream=stream)
+    rng = np.random.default_rng(2000 + rank)
+    amp = float(np.max(np.abs(w.u0)))   # further problems: controls of the same amplitude as u0
+    U0 = np.stack([w.u0] + [rng.uniform(-amp, amp, w.u0.shape) for _ in range(B - 1)])
+    u_dev = torch.tensor(U0, dtype=torch.float64, device="cuda").contiguous()
+    flush = torch.empty(512 * 1024 * 1024 // 4, dtype=torch.float32, device="cuda")   # 512 MB > L2
+    for _ in range(warmup):
+        plan.ism_iterate(1, u_dev, None, None)
+    plan.ism_set_profiling(True)
+    plan.ism_get_stats(reset=True)
+    clocks = Clocks(int(os.environ.get("LOCAL_RANK", "0")))
+    ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(steps)]
+    if world > 1:
+        torch.distributed.barrier()
+    torch.cuda.synchronize()
+    clocks.start()
+    with torch.cuda.stream(stream):
+        for k in range(steps):
+            flush.zero_()                       # evict the previous step's working set from L2
+            ev[k][0].record(stream)
+            plan.ism_iterate(1, u_dev, None, None)
+            ev[k][1].record(stream)
+    torch.cuda.synchronize()
+    if world > 1:
+        torch.distributed.barrier()
+    clk = clocks.stop()
+    step_ms = [a.elapsed_time(b) for a, b in ev]
+    tot_ms = slowest_rank_ms(sum(step_ms), world, "cuda")
+    st = plan.ism_get_stats(reset=True)
+    plan.ism_set_profiling(False)
+    value = job_throughput(B, steps, world, tot_ms)
+    ss, ss_how = state_steps_per_iteration(plan, w)
+
+    large = plan.ks_large
+    direct = plan.info(6) == 2   # Algorithm 1 (a)-(b) by direct sweeps
+    sub = "k_subfwd" if prec == "mixed" else "k_subinterval"
+    if plan.gp:
+        names = ["k_gp_forward", "k_gp_adjoint", "k_gp_sub"]
+        kernels = names
+    elif plan.kind == "pauli":
+        names = ["k_pauli_sweep", "k_phi", "k_pauli_sub"]
+        kernels = ["k_pauli_prep + k_pauli_sweep", "k_phi", "k_pauli_sub"]
+    elif large:
+        names = ["k_lsweep", "k_phi", "k_lsub"]
+        kernels = ["k_cheb_prep + k_lsweep", "k_phi", "k_lsub"]
+    elif direct:
+        names = ["k_gsweep", "k_phi", sub]
+        kernels = ["k_cheb_prep + k_gsweep", "k_phi", sub]
+    else:
+        names = ["k_assemble", "k_chain", "k_sweeps2"]
+        kernels = ["k_cheb_prep + k_assemble", "k_chain + k_phi", "k_sweeps2 + k_gradpass"]
+    dom = int(np.argmax(st["ms"]))
+    ms_launch = st["ms"][dom] / steps
+    peaks = measured_peaks()
+    if plan.gp or dom in (0, 2) or large or direct:
+        if plan.gp:   # FFT pairs counted by the kernels: forward, adjoint, sub-interval
+            pairs = [st["y_apps"][0], st["terms"][0], st["terms"][1]][dom]
+            flops = pairs * gp_pair_flops(d) / steps
+        elif dom == 1:   # k_phi
+            flops = 8.0 * B * (w.N + 1) * d
+        else:
+            k = 0 if dom == 0 else 1
+            flops = cheb_flops(plan.kind, d, st["y_apps"][k], st["terms"][k], st["substeps"][k]) / steps
+        achieved = flops / (ms_launch / 1e3) / 1e12
+        pk = alu_peak(P, "fp64" if prec == "fp64" else "fp32")
+        roof = {"kernel": names[dom], "kernels_timed": kernels[dom], "bound": "alu", "achieved": achieved,
+                "peak": pk["peak"], "unit": "TFLOP/s", "frac": achieved / pk["peak"],
+                "traffic": traffic_of(names[dom], cfg, B), "peak_source": pk["source"], "flops_per_launch": flops,
+                "ms_per_launch": ms_launch}
+    else:
+        # algorithmic bytes: every stored propagator tile read once per chain, both staged state chains written
+        tile = plan.info(4)
+        nbytes = B * (2 * w.N * tile + 2 * (w.N + 1) * d * 8)
+        achieved = nbytes / (ms_launch / 1e3) / 1e9
+        roof = {"kernel": names[dom], "kernels_timed": kernels[dom], "bound": "hbm", "achieved": achieved,
+                "peak": peaks["hbm_gbs"], "unit": "GB/s", "frac": achieved / peaks["hbm_gbs"],
+                "traffic": traffic_of(names[dom], cfg, B), "peak_source": peaks["source"], "bytes_per_launch": nbytes,
+                "ms_per_launch": ms_launch}
+    return {"plan": plan, "w": w, "U0": U0, "B": B, "d": d, "prec": prec, "value": value, "steps": steps,
+            "ms_per_step": tot_ms / steps, "step_ms": step_ms, "state_steps": ss, "state_steps_how": ss_how,
+            "roofline": roof, "phase_share": {n: st["ms"][i] / max(1e-12, sum(st["ms"])) for i, n in enumerate(names)},
+            "gpu_launches": int(st["kernels"]), "clocks": clk}
+
+
+def config_summary(cfg: str, m: dict, cpu) -> dict:
+    w = m["w"]
+    return {"value": m["value"], "unit": UNIT, "ms_per_step": m["ms_per_step"], "steps": m["steps"],
+            "workload": f"{cfg}: {DESCR.get(cfg, cfg)} (d={m['d']}), T={w.T:g}, Nt={w.Nt}, N={w.N}, "
+                        f"batch={m['B']} per GPU", "precision": m["prec"],
+            "state_steps_per_s": m["value"] * m["state_steps"], "state_steps_per_iteration": m["state_steps_how"],
+            "roofline": m["roofline"], "phase_share": m["phase_share"], "cpu_baseline": cpu,
+            "tested": TESTED.get(cfg), "clocks": m["clocks"]}
+
+
 def run_ours(args):
     import torch
 
@@ -467,97 +669,10 @@ def run_ours(args):
     import paper_1603_01237_gb300 as P
     import workloads as W
 
-    w = load_workload(args.config, N=args.N, Nt=args.Nt)
-    d = dim_of(w)
-    B = args.batch or BATCH_DEFAULT.get(args.config, 1)
     stream = torch.cuda.Stream()
-    plan = P.Plan(w, precision="mixed", batch=B, stream=stream)
-    rng = np.random.default_rng(2000 + rank)
-    amp = float(np.max(np.abs(w.u0)))   # further problems: controls of the same amplitude as u0
-    U0 = np.stack([w.u0] + [rng.uniform(-amp, amp, w.u0.shape) for _ in range(B - 1)])
-    u_dev = torch.tensor(U0, dtype=torch.float64, device="cuda").contiguous()
-    flush = torch.empty(512 * 1024 * 1024 // 4, dtype=torch.float32, device="cuda")   # 512 MB > L2
-
-    def step_device():
-        plan.ism_iterate(1, u_dev, None, None)
-
-    for _ in range(args.warmup):
-        step_device()
-    plan.ism_set_profiling(True)
-    plan.ism_get_stats(reset=True)
-    clocks = Clocks(local_rank)
-    ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(args.steps)]
-    if world > 1:
-        torch.distributed.barrier()
-    torch.cuda.synchronize()
-    clocks.start()
-    with torch.cuda.stream(stream):
-        for k in range(args.steps):
-            flush.zero_()                       # evict the previous step's working set from L2
-            ev[k][0].record(stream)
-            step_device()
-            ev[k][1].record(stream)
-    torch.cuda.synchronize()
-    if world > 1:
-        torch.distributed.barrier()
-    clk = clocks.stop()
-    step_ms = [a.elapsed_time(b) for a, b in ev]
-    tot_ms = sum(step_ms)
-    st = plan.ism_get_stats(reset=True)
-    plan.ism_set_profiling(False)
-    tot_ms = slowest_rank_ms(tot_ms, world, "cuda")
-    value = job_throughput(B, args.steps, world, tot_ms)
-    # useful state-steps per ISM iteration: 2 global sweeps + forward, recompute and adjoint per
-    # sub-interval (the grid model stores its forward states: 2 + 2)
-    state_steps = (4 if plan.gp else 5) * w.Nt
-
-    # roofline of the dominant phase (largest share of device time); one launch of a phase per iteration
-    large = plan.ks_large
-    direct = plan.info(6) == 2   # Algorithm 1 (a)-(b) by direct sweeps
-    if plan.gp:
-        names = ["k_gp_forward", "k_gp_adjoint", "k_gp_sub"]
-        kernels = names
-    elif direct and not large:
-        names = ["k_gsweep", "k_phi", "k_subinterval"]
-        kernels = ["k_cheb_prep + k_gsweep", "k_phi", "k_subinterval"]
-    elif plan.kind == "pauli":
-        names = ["k_pauli_sweep", "k_phi", "k_pauli_sub"]
-        kernels = ["k_pauli_prep + k_pauli_sweep", "k_phi", "k_pauli_sub"]
-    elif large:
-        names = ["k_lsweep", "k_phi", "k_lsub"]
-        kernels = ["k_cheb_prep + k_lsweep", "k_phi", "k_lsub"]
-    else:
-        names = ["k_assemble", "k_chain", "k_sweeps2"]
-        kernels = ["k_cheb_prep + k_assemble", "k_chain + k_phi", "k_sweeps2 + k_gradpass"]
-    dom = int(np.argmax(st["ms"]))
-    ms_launch = st["ms"][dom] / args.steps
-    peaks = measured_peaks()
-    alu_src = "derived: 152 SMs x 128 FP32 lanes x 2 flop x 2070 MHz (no measured FP32 peak)"
-    if plan.gp or dom in (0, 2) or large or direct:
-        if plan.gp:   # FFT pairs counted by the kernels: forward, adjoint, sub-interval
-            pairs = [st["y_apps"][0], st["terms"][0], st["terms"][1]][dom]
-            flops = pairs * gp_pair_flops(d) / args.steps
-        elif dom == 1:   # k_phi
-            flops = 8.0 * B * (w.N + 1) * d
-        else:
-            k = 0 if dom == 0 else 1
-            flops = cheb_flops(plan.kind, d, st["y_apps"][k], st["terms"][k], st["substeps"][k]) / args.steps
-        achieved = flops / (ms_launch / 1e3) / 1e12
-        peak = fp32_peak_tflops()
-        roof = {"kernel": names[dom], "kernels_timed": kernels[dom], "bound": "alu", "achieved": achieved,
-                "peak": peak, "unit": "TFLOP/s", "frac": achieved / peak,
-                "traffic": traffic_of(names[dom], args.config, B),
-                "peak_source": alu_src, "flops_per_launch": flops, "ms_per_launch": ms_launch}
-    else:
-        # algorithmic bytes: every stored propagator tile read once per chain, both staged state chains written
-        tile = plan.info(4)
-        nbytes = B * (2 * w.N * tile + 2 * (w.N + 1) * d * 8)
-        achieved = nbytes / (ms_launch / 1e3) / 1e9
-        roof = {"kernel": names[dom], "kernels_timed": kernels[dom], "bound": "hbm", "achieved": achieved,
-                "peak": peaks["hbm_gbs"], "unit": "GB/s", "frac": achieved / peaks["hbm_gbs"],
-                "traffic": traffic_of(names[dom], args.config, B),
-                "peak_source": peaks["source"], "bytes_per_launch": nbytes, "ms_per_launch": ms_launch}
-    phase_share = {n: st["ms"][i] / max(1e-12, sum(st["ms"])) for i, n in enumerate(names)}
+    m = measure_config(P, W, args.config, args, stream, args.steps, args.warmup, world, rank, N=args.N, Nt=args.Nt,
+                       batch=args.batch)
+    plan, w, U0, B, d = m["plan"], m["w"], m["U0"], m["B"], m["d"]
 
     # e2e through the C ABI with host buffers: H2D of u, one iteration, D2H of u and Err
     u_host = torch.tensor(U0, dtype=torch.float64).pin_memory()
@@ -572,6 +687,7 @@ def run_ours(args):
     e2e = {"value": B / statistics.mean(e2e_t) * world, "unit": UNIT,
            "h2d_bytes_per_step": int(u_host.numel() * 8),
            "d2h_bytes_per_step": int(u_host.numel() * 8 + err_host.numel() * 8)}
+    plan.close()
 
     # plain FP64, one problem per launch
     fp64 = None
@@ -593,7 +709,7 @@ def run_ours(args):
 
     # solve latency: complete solves (the workload's iteration count) of one problem per launch
     it_solve = SOLVE_ITERS.get(args.config, 20)
-    p1 = P.Plan(w, precision="mixed", batch=1, stream=stream)
+    p1 = P.Plan(w, precision=m["prec"], batch=1, stream=stream)
     u1 = torch.tensor(w.u0, dtype=torch.float64, device="cuda").reshape(1, -1).contiguous()
     u1_0 = u1.clone()
     p1.ism_iterate(it_solve, u1, None, None)
@@ -617,40 +733,42 @@ def run_ours(args):
     if not args.no_cn and getattr(w, "kind", "") == "tridiag":
         cn = crank_nicolson_leg(P, w, stream, args.steps, cpu=(rank == 0 and world == 1 and not args.no_cpu_baseline))
 
-    cpu = None
-    if rank == 0 and world == 1 and not args.no_cpu_baseline:
-        # repeat the bounded oracle sample until about 10 s of CPU work have been timed
-        tot, scale, n_s = 0.0, 1.0, 0
-        while tot < 10.0 and n_s < 50:
-            dt, scale, sample = oracle_sample(args.config, args.N)
-            tot += dt
-            n_s += 1
-        cpu = {"value": n_s * scale / tot, "unit": UNIT, "cores": 1, "kind": "oracle",
-               "sample": f"{sample}; {n_s} repetitions, {tot:.1f} s"}
+    want_cpu = rank == 0 and world == 1 and not args.no_cpu_baseline
+    cpu = cpu_baseline_of(args.config, args.N) if want_cpu else None
+
+    # the other configurations at full size, in their own precision, fewer timed steps
+    others = {}
+    if args.config == "rotor41" and not args.no_configs and args.N is None and args.Nt is None:
+        for cfg in SUB_CONFIGS:
+            mc = measure_config(P, W, cfg, args, stream, max(3, min(args.steps, 5)), 3, world, rank)
+            mc["plan"].close()
+            others[cfg] = config_summary(cfg, mc, cpu_baseline_of(cfg, None, 5.0) if want_cpu else None)
 
     line = {
-        "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
-        "warmup": args.warmup, "ms_per_step": tot_ms / args.steps, "higher_is_better": True, "scaling": "weak",
-        "vs_baseline": None, "dtype": "f32 propagation, f64 states/overlaps/update", "data": "synthetic",
+        "metric": METRIC, "value": m["value"], "unit": UNIT, "n_gpus": world, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": m["ms_per_step"], "higher_is_better": True, "scaling": "weak",
+        "vs_baseline": None, "dtype": "f32 propagation, f64 states/overlaps/update" if m["prec"] == "mixed" else "f64",
+        "data": "synthetic",
         "config": {"workload": f"{args.config}: {DESCR.get(args.config, args.config)} (d={d}), T={w.T:g}, "
                                f"Nt={w.Nt}, N={w.N}, batch={B} per GPU", "d": d, "Nt": w.Nt, "N": w.N, "batch": B,
-                   "precision": "mixed", "l2": "flushed between steps (512 MB write, outside the timed events)"},
-        "state_steps_per_s": value * state_steps,
-        "step_ms_p50": statistics.median(step_ms), "step_ms_p99": float(np.percentile(step_ms, 99)),
+                   "precision": m["prec"], "l2": "flushed between steps (512 MB write, outside the timed events)"},
+        "state_steps_per_s": m["value"] * m["state_steps"], "state_steps_per_iteration": m["state_steps_how"],
+        "step_ms_p50": statistics.median(m["step_ms"]), "step_ms_p99": float(np.percentile(m["step_ms"], 99)),
+        "tested": TESTED.get(args.config),
         "solve_latency": solve,
         "serving": serving,
         "fp64_plain": fp64,
         "crank_nicolson": cn,
-        "phase_share": phase_share,
-        "roofline": roof,
+        "configs": others or None,
+        "phase_share": m["phase_share"],
+        "roofline": m["roofline"],
         "cpu_baseline": cpu,
         "e2e": e2e,
-        "gpu_launches": int(st["kernels"]),
-        "clocks": clk,
+        "gpu_launches": m["gpu_launches"],
+        "clocks": m["clocks"],
     }
     if rank == 0:
         print(json.dumps(line), flush=True)
-    plan.close()
     if world > 1:
         torch.distributed.destroy_process_group()
     return 0

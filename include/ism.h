@@ -258,6 +258,13 @@ int ism_set_profiling(ism_plan_t plan, int on);
  *   reset != 0 zeroes it afterwards. */
 int ism_get_stats(ism_plan_t plan, ism_stats* out, int reset);
 
+/* ism_measure_peak -- the FMA rate this GPU sustains, in TFLOP/s, measured with CUDA events on the
+ *   current device: which = 0 packed FP32 FMAs (fma.rn.f32x2, 4 flops each), 1 FP64 FMAs (2 flops).
+ *   Every SM runs independent FMA chains for a fixed count; the best of three timed launches after a
+ *   warm-up launch.  These are the peaks of the propagation kernels' ALU rooflines (the paper has no
+ *   counterpart).  Allocates nothing; ISM_EINVAL for another `which`, ISM_ECUDA on a CUDA error. */
+int ism_measure_peak(int which, double* tflops);
+
 /* ism_plan_footprint -- device bytes ism_plan would allocate for (prob, opt), without allocating or
  *   touching a GPU (admission control).  The J/Err history buffers that ism_iterate adds on demand
  *   (16 bytes x batch x (iters + 1)) are not included.  Same validation and errors as ism_plan. */

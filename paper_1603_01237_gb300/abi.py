@@ -28,7 +28,7 @@ EXPORTS = ("ism_plan", "ism_plan_destroy", "ism_intermediate_states", "ism_subin
            "ism_iterate", "ism_evaluate", "ism_gradient", "ism_set_profiling", "ism_get_stats", "ism_plan_info",
            "ism_plan_footprint", "ism_server_create", "ism_server_submit", "ism_server_poll",
            "ism_server_release", "ism_server_destroy",
-           "ism_subinterval_grad_noalloc", "ism_last_error", "ism_version")
+           "ism_subinterval_grad_noalloc", "ism_measure_peak", "ism_last_error", "ism_version")
 
 
 class IsmProblem(C.Structure):
@@ -109,6 +109,8 @@ def load(path: str | None = None):
     lib.ism_server_destroy.restype = i
     lib.ism_subinterval_grad_noalloc.argtypes = [C.POINTER(IsmProblem), i, vp, vp, vp, vp, vp]
     lib.ism_subinterval_grad_noalloc.restype = i
+    lib.ism_measure_peak.argtypes = [i, C.POINTER(d)]
+    lib.ism_measure_peak.restype = i
     lib.ism_last_error.argtypes = []
     lib.ism_last_error.restype = C.c_char_p
     lib.ism_version.argtypes = []
@@ -199,6 +201,13 @@ def pack_hamiltonian(kind: str, H0: np.ndarray, H1: np.ndarray):
             raise ValueError("bitflip kind needs H1 = sum_i h_i X_i")
         return np.diag(H0).astype(np.float64).copy(), h
     raise ValueError(kind)
+
+
+def measure_peak(which: str = "fp32") -> float:
+    """ism_measure_peak: sustained FMA rate of the current GPU in TFLOP/s ("fp32": packed FFMA2, "fp64")."""
+    v = C.c_double()
+    _check(load().ism_measure_peak({"fp32": 0, "fp64": 1}[which], C.byref(v)))
+    return float(v.value)
 
 
 def subinterval_grad_noalloc(w, precision: str, phi, u, grad, Jn=None, *, batch: int = 1, stream=None,
