@@ -20,7 +20,7 @@ ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 # host code: no floating-point contraction, so that x86-64 and aarch64 hosts (where gcc would fuse
 # a*b + c into an FMA at its own discretion) compute the plan's partition weights to the same bits
 FLAGS = ["-O3", "-lineinfo", "-std=c++17", "-Xcompiler", "-fPIC", "-Xcompiler", "-ffp-contract=off",
-         "-I", INCLUDE, "-I", CSRC, "-diag-suppress", "177"]
+         "-I", INCLUDE, "-I", CSRC, "-diag-suppress", "177,1886"]
 
 
 def nvcc() -> str:

@@ -1,7 +1,9 @@
 // ism_api.cu -- the C ABI declared in include/ism.h: plan creation and validation, the partition
 // and weights of Sec. 2, spectral bounds for the Chebyshev propagator, and the orchestration of the
 // hot-path kernels on the plan's stream.
+#include <algorithm>
 #include <cmath>
+#include <cstdint>
 #include <cstdio>
 #include <cstring>
 #include <initializer_list>
@@ -12,6 +14,7 @@
 #include "ism_kernels.cuh"
 #include "ism_launch.h"
 #include "ism_gp.h"
+#include "ism_tc.h"
 
 namespace {
 
@@ -147,6 +150,14 @@ struct ism_plan_s {
   void* dckpt = nullptr;            // literal sub-problem: checkpoints, allocated when first needed
   void* dsegb = nullptr;            // literal sub-problem: H1 psi of one segment per (problem, n)
   int cks = 1, nck = 1;             // checkpoint stride and checkpoints per sub-interval
+  // dense d = 128, 256 on the tensor cores (ism_tc.cu)
+  bool tc = false;
+  ism::TcMaps tcmaps{};
+  float* dHhi = nullptr;            // TF32 hi / lo parts of [H0; H1], [2d][d]
+  float* dHlo = nullptr;
+  ism::TcItem* dtc_items = nullptr; // global sweeps: [psi items | chi items], then the sub-interval items
+  int tc_npsi = 0, tc_nchi = 0, tc_nsub = 0;   // padded item counts of the three groups
+  float* dvstate = nullptr;         // FP32 states of every CTA of the largest launch
   void* dzp = nullptr;              // large d: per-step, per-warp overlap partials
   double* du = nullptr;
   float* duf = nullptr;             // FP32 copy of the controls (FP32 propagation)
@@ -178,6 +189,9 @@ struct ism_plan_s {
 };
 
 namespace {
+
+int tc_global(ism_plan_s* P);
+int tc_sub(ism_plan_s* P, const ism::KParams& k);
 
 template <class T>
 int dalloc(ism_plan_s* P, T** out, size_t count) {
@@ -387,8 +401,8 @@ int validate_problem(const ism_problem& p, int precision) {
     while (q < 30 && (1 << q) < d) ++q;
     if ((1 << q) != d || d < 2) return fail(ISM_EINVAL, "bit-flip kind needs d = 2^q >= 2");
     if (d > 1024) return fail(ISM_EUNSUPPORTED, "this build supports bit-flip d <= 1024");
-  } else if (d > 64) {
-    return fail(ISM_EUNSUPPORTED, "this build supports tridiagonal and dense d <= 64");
+  } else if (d > 64 && !(p.kind == ISM_H_DENSE && ism::tc_supported(d))) {
+    return fail(ISM_EUNSUPPORTED, "this build supports tridiagonal d <= 64 and dense d <= 64, 128 or 256");
   }
   const long nH = p.kind == ISM_H_DENSE ? (long)d * d : p.kind == ISM_H_TRIDIAG ? 2L * d - 1 : d;
   const long nH1 = p.kind == ISM_H_DENSE ? (long)d * d : p.kind == ISM_H_TRIDIAG ? 2L * d - 1 : q;
@@ -509,7 +523,12 @@ int run_states(ism_plan_s* P, const double* u, double* Jhist, int hist_stride, i
     return ISM_OK;
   }
   ism::KParams k = kparams(P, const_cast<double*>(u));
-  if (P->ks.large || P->direct) {   // direct sweeps: psi(t_n), chi(t_n) in FP64
+  if (P->tc) {   // dense d = 128, 256: the stacked global sweeps on the tensor cores
+    ISM_CUDA_TRY(prep_params(P, k));
+    P->kernels += 1;
+    int rc = tc_global(P);
+    if (rc != ISM_OK) return rc;
+  } else if (P->ks.large || P->direct) {   // direct sweeps: psi(t_n), chi(t_n) in FP64
     ism::LaunchFn sweep = P->ks.large ? P->ks.lsweep : P->wide ? P->ks.gsweep_wide : P->ks.gsweep;
     ISM_CUDA_TRY(timed(P, 0, 2, [&] {
       cudaError_t e = prep_params(P, k);
@@ -534,7 +553,7 @@ int run_states(ism_plan_s* P, const double* u, double* Jhist, int hist_stride, i
   c.inv_nrm_psi_i = P->nrm_psi_i > 0.0 ? 1.0 / P->nrm_psi_i : 0.0;
   c.nrm_chi_T = P->obj == ISM_OBJ_OVERLAP ? P->nrm_psi_f : -1.0;
   c.nrm = (P->direct && !P->ks.large) ? P->dnrm : nullptr;   // k_gsweep leaves the squared norms
-  if (P->ks.large || P->direct) {
+  if (P->ks.large || P->direct || P->tc) {
     c.src64 = 1;
     ISM_CUDA_TRY(timed(P, 1, 1, [&] { return ism::launch_phi(P->prec, c, P->st); }));
   } else {
@@ -600,6 +619,184 @@ const char* ism_version(void) { return "ism-gb300 0.1 (sm_103a)"; }
 
 namespace {
 
+// TF32 rounding of an FP32 value (round half away from zero on the 13 dropped mantissa bits).
+float tf32_round(float x) {
+  uint32_t u;
+  std::memcpy(&u, &x, 4);
+  u = (u + 0x1000u) & 0xFFFFE000u;
+  float r;
+  std::memcpy(&r, &u, 4);
+  return r;
+}
+
+// Dense d = 128, 256: [H0; H1] as TF32 hi + lo parts, the stacked states of the global and the
+// sub-interval sweeps, and the plan's FP64 arrays.  Mixed precision and one local step only.
+int plan_build_tc(ism_plan_s* P, const ism_problem& p, bool dry, size_t* bytes_out) {
+  const int d = p.d;
+  if (P->prec != ISM_MIXED)
+    return fail(ISM_EUNSUPPORTED, "dense d = 128 and 256 run on the tensor cores in mixed precision only");
+  if (P->L != 1) return fail(ISM_EUNSUPPORTED, "dense d = 128 and 256 support one local step per iteration");
+  P->tc = true;
+  P->form = 2;
+  P->r2 = sizeof(float2);
+  {
+    Bounds bd = bounds_of(ISM_H_DENSE, d, p.H0, p.H1);
+    P->c0 = 0.5 * (bd.lo + bd.hi);
+    P->r0 = 0.5 * (bd.hi - bd.lo);
+    P->h1n = bd.h1;
+  }
+  std::vector<int> jn;
+  std::vector<double> beta;
+  std::vector<double2> phase;
+  ism::partition(P->T, P->Nt, P->N, P->c0, &jn, &beta, &phase);
+  const int NI = ism::tc_items_per_cta(d);
+  const size_t B = P->B;
+  auto pad = [NI](int n) { return (n + NI - 1) / NI * NI; };
+  P->tc_npsi = pad(P->B);
+  P->tc_nchi = pad(P->B);
+  P->tc_nsub = pad(2 * P->B * P->N);
+  const int ctas = std::max((P->obj == ISM_OBJ_OVERLAP ? P->tc_npsi + P->tc_nchi : P->tc_npsi), P->tc_nsub) / NI;
+  int rc = ISM_OK;
+#define TRY_TC(ptr, n) if ((rc = dalloc(P, &(ptr), (n))) != ISM_OK) return rc;
+  TRY_TC(P->dHhi, 2 * (size_t)d * d);
+  TRY_TC(P->dHlo, 2 * (size_t)d * d);
+  TRY_TC(P->djn, (size_t)P->N + 1);
+  TRY_TC(P->dbeta, (size_t)P->N);
+  TRY_TC(P->dab, (size_t)P->N + 1);
+  TRY_TC(P->dphase, (size_t)P->N);
+  TRY_TC(P->dcheb, B * P->N * ism::cheb_bytes(ISM_MIXED));
+  TRY_TC(P->dpen, B * P->N);
+  TRY_TC(P->dctab, (size_t)ism::BESSEL_TABLE);
+  if (p.alpha) TRY_TC(P->dalpha, (size_t)P->Nt);
+  TRY_TC(P->dpsi_i, (size_t)d);
+  TRY_TC(P->dpsi_f, (size_t)d);
+  if (p.objective == ISM_OBJ_OBSERVABLE) TRY_TC(P->dO, (size_t)d * d);
+  TRY_TC(P->dpsin, B * (P->N + 1) * (size_t)d);
+  TRY_TC(P->dchin, B * (P->N + 1) * (size_t)d);
+  TRY_TC(P->dphi, B * (P->N + 1) * (size_t)d);
+  {
+    unsigned char* dZ = nullptr;
+    TRY_TC(dZ, B * ((size_t)P->Nt + P->N) * sizeof(float2));
+    P->dzs = dZ;
+  }
+  TRY_TC(P->du, B * P->Nt);
+  TRY_TC(P->duf, B * P->Nt);
+  TRY_TC(P->dgrad, B * P->Nt);
+  TRY_TC(P->dJn, B * P->N);
+  TRY_TC(P->derr, B * P->N);
+  TRY_TC(P->dJ, B);
+  TRY_TC(P->dF, B);
+  TRY_TC(P->dstatus, 1);
+  TRY_TC(P->dcount, 7);
+  TRY_TC(P->dtc_items, (size_t)P->tc_npsi + P->tc_nchi + P->tc_nsub);
+  TRY_TC(P->dvstate, (size_t)ctas * 2 * (2 * NI) * d);
+#undef TRY_TC
+  if (dry) {
+    *bytes_out = P->bytes;
+    return ISM_OK;
+  }
+  // [H0; H1] rows as TF32 hi + lo (the tensor cores read the top 19 bits of each word)
+  std::vector<float> hi(2 * (size_t)d * d), lo(2 * (size_t)d * d);
+  for (int m = 0; m < 2 * d; ++m)
+    for (int e = 0; e < d; ++e) {
+      const double x = m < d ? p.H0[(size_t)m * d + e] : p.H1[(size_t)(m - d) * d + e];
+      const float h = tf32_round((float)x);
+      hi[(size_t)m * d + e] = h;
+      lo[(size_t)m * d + e] = tf32_round((float)(x - (double)h));
+    }
+  std::vector<ism::TcItem> items((size_t)P->tc_npsi + P->tc_nchi + P->tc_nsub, ism::TcItem{-1, 0, 0, 0});
+  for (int b = 0; b < P->B; ++b) {
+    items[b] = ism::TcItem{b, 0, 0, 0};
+    items[P->tc_npsi + b] = ism::TcItem{b, 0, 0, 1};
+  }
+  for (int b = 0; b < P->B; ++b)
+    for (int n = 0; n < P->N; ++n)
+      for (int r = 0; r < 2; ++r)
+        items[(size_t)P->tc_npsi + P->tc_nchi + 2 * ((size_t)b * P->N + n) + r] = ism::TcItem{b, n, r, 0};
+  cudaError_t e = cudaSuccess;
+  auto h2d = [&](void* dst, const void* src, size_t n) {
+    if (e == cudaSuccess) e = cudaMemcpyAsync(dst, src, n, cudaMemcpyHostToDevice, P->st);
+  };
+  h2d(P->dHhi, hi.data(), hi.size() * sizeof(float));
+  h2d(P->dHlo, lo.data(), lo.size() * sizeof(float));
+  h2d(P->djn, jn.data(), jn.size() * sizeof(int));
+  h2d(P->dbeta, beta.data(), beta.size() * sizeof(double));
+  h2d(P->dphase, phase.data(), phase.size() * sizeof(double2));
+  std::vector<double2> ab(P->N + 1);
+  for (int n = 0; n <= P->N; ++n) {
+    const double tn = jn[n] * P->tau;
+    ab[n] = make_double2((P->T - tn) / P->T, tn / P->T);
+  }
+  h2d(P->dab, ab.data(), ab.size() * sizeof(double2));
+  std::vector<double> tab(ism::BESSEL_TABLE);
+  ism::bessel_table(tab.data());
+  h2d(P->dctab, tab.data(), tab.size() * sizeof(double));
+  if (p.alpha) h2d(P->dalpha, p.alpha, P->Nt * sizeof(double));
+  h2d(P->dpsi_i, p.psi_i, 2 * sizeof(double) * d);
+  if (p.objective == ISM_OBJ_OVERLAP) h2d(P->dpsi_f, p.psi_f, 2 * sizeof(double) * d);
+  else if (e == cudaSuccess) e = cudaMemsetAsync(P->dpsi_f, 0, 2 * sizeof(double) * d, P->st);
+  if (p.objective == ISM_OBJ_OBSERVABLE) h2d(P->dO, p.O, sizeof(double) * d * d);
+  h2d(P->dtc_items, items.data(), items.size() * sizeof(ism::TcItem));
+  if (e == cudaSuccess) e = cudaMemsetAsync(P->dstatus, 0, sizeof(int), P->st);
+  if (e == cudaSuccess) e = cudaMemsetAsync(P->dcount, 0, 7 * sizeof(unsigned long long), P->st);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(P->st);   // the host arrays above are local
+  if (e == cudaSuccess) e = ism::tc_encode_maps(&P->tcmaps, P->dHhi, P->dHlo, d);
+  if (e != cudaSuccess) return fail(ISM_ECUDA, std::string("plan upload: ") + cudaGetErrorString(e));
+  for (int e0 = 0; e0 < d; ++e0) {
+    P->nrm_psi_i += p.psi_i[2 * e0] * p.psi_i[2 * e0] + p.psi_i[2 * e0 + 1] * p.psi_i[2 * e0 + 1];
+    if (p.objective == ISM_OBJ_OVERLAP)
+      P->nrm_psi_f += p.psi_f[2 * e0] * p.psi_f[2 * e0] + p.psi_f[2 * e0 + 1] * p.psi_f[2 * e0 + 1];
+  }
+  return ISM_OK;
+}
+
+// The stacked tensor-core sweeps of a dense d = 128, 256 plan.  mode 0: psi forward and chi backward
+// (Algorithm 1 (a)-(b)); mode 1: the sub-problems of every (problem, n) in the two-trajectory form.
+ism::TcParams tc_params(ism_plan_s* P, int mode) {
+  ism::TcParams t{};
+  t.d = P->d; t.Nt = P->Nt; t.N = P->N; t.B = P->B; t.obj = P->obj; t.mode = mode;
+  t.nsteps = mode == 0 ? P->Nt : (P->Nt + P->N - 1) / P->N;
+  t.jn = P->djn; t.uf = P->duf; t.cheb = P->dcheb;
+  t.psi_i = P->dpsi_i; t.psi_f = P->dpsi_f; t.psin = P->dpsin; t.chin = P->dchin;
+  t.zs = reinterpret_cast<float2*>(P->dzs);
+  t.vstate = P->dvstate;
+  t.status = P->dstatus;
+  t.max_spin = P->max_spin;
+  t.count = P->dcount + (mode == 0 ? 0 : 3);
+  return t;
+}
+
+int tc_global(ism_plan_s* P) {
+  ism::TcParams t = tc_params(P, 0);
+  if (P->obj == ISM_OBJ_OVERLAP) {   // psi forward and chi backward together
+    t.items = P->dtc_items;
+    t.nitems = P->tc_npsi + P->tc_nchi;
+    ISM_CUDA_TRY(timed(P, 0, 1, [&] { return ism::launch_tc_sweep(P->tcmaps, t, P->st); }));
+    return ISM_OK;
+  }
+  t.items = P->dtc_items;            // observable: psi, then chi(T) = O psi(T), then chi
+  t.nitems = P->tc_npsi;
+  ISM_CUDA_TRY(timed(P, 0, 1, [&] { return ism::launch_tc_sweep(P->tcmaps, t, P->st); }));
+  ISM_CUDA_TRY(ism::launch_tc_chiT(P->dO, P->dpsin, P->dchin, P->d, P->N, P->B, P->st));
+  P->kernels += 1;
+  t.items = P->dtc_items + P->tc_npsi;
+  t.nitems = P->tc_nchi;
+  ISM_CUDA_TRY(timed(P, 0, 1, [&] { return ism::launch_tc_sweep(P->tcmaps, t, P->st); }));
+  return ISM_OK;
+}
+
+// step (c) of a dense d = 128, 256 plan: the stacked sub-interval sweep, then the FP64 gradient pass
+int tc_sub(ism_plan_s* P, const ism::KParams& k) {
+  ism::TcParams t = tc_params(P, 1);
+  t.items = P->dtc_items + P->tc_npsi + P->tc_nchi;
+  t.nitems = P->tc_nsub;
+  ISM_CUDA_TRY(timed(P, 2, 2, [&] {
+    cudaError_t e = ism::launch_tc_sweep(P->tcmaps, t, P->st);
+    return e != cudaSuccess ? e : ism::launch_tc_zgrad(k, P->st);
+  }));
+  return ISM_OK;
+}
+
 // Validate, size and (unless dry) allocate and upload a plan.  dry: only *bytes is produced.
 int plan_build(const ism_problem* prob, const ism_options* opt, void* cuda_stream, ism_plan_t* out, bool dry,
                size_t* bytes_out) {
@@ -637,6 +834,13 @@ int plan_build(const ism_problem* prob, const ism_options* opt, void* cuda_strea
   P->st = reinterpret_cast<cudaStream_t>(cuda_stream);
   cudaGetDevice(&P->dev);
 
+  if (p.kind == ISM_H_DENSE && ism::tc_supported(d)) {   // dense d = 128, 256: the tensor-core path
+    int rc0 = plan_build_tc(P, p, dry, bytes_out);
+    if (rc0 != ISM_OK || dry) { if (!dry || rc0 != ISM_OK) { free_all(P); } delete P; return rc0; }
+    *out = P;
+    g_err.clear();
+    return ISM_OK;
+  }
   if (p.kind == ISM_H_GRID_GP || p.kind == ISM_H_GRID_GP_DOUBLE_WELL) {
     P->gp = true;
     P->gpL = p.H0[0];
@@ -954,6 +1158,7 @@ long long ism_plan_info(ism_plan_t P, int key) {
     case 7: return P->Nc ? P->sblk : 1;
     case 8: return P->scheme;
     case 9: return P->wide ? P->ks.GW : (P->direct ? P->ks.G : 0);
+    case 10: return P->tc ? 1 : 0;
     default: return -1;
   }
 }
@@ -1007,6 +1212,9 @@ int ism_subinterval_grad(ism_plan_t P, const double* phi, const double* u, doubl
   int rc = begin(P);
   if (rc) return rc;
   if ((rc = check_device_args(P->dev, {phi, u, grad, Jn}))) return rc;
+  if (P->tc)
+    return fail(ISM_EUNSUPPORTED, "dense d = 128, 256 plans run the two-trajectory form of first local steps only "
+                                  "(ism_iterate, ism_gradient); literal sub-problems are not built for them");
   const double* ud = nullptr;
   if ((rc = stage_in(P, u, (long)P->B * P->Nt * P->m, P->du, &ud, true))) return rc;
   if (P->gp) {
@@ -1083,7 +1291,9 @@ int ism_iterate(ism_plan_t P, int iters, double* u_inout, double* J_hist, double
         ISM_CUDA_TRY(prep_params(P, k));
         P->kernels += 1;
       }
-      if (k.form && P->use_sw2)
+      if (P->tc) {
+        if ((rc = tc_sub(P, k)) != ISM_OK) return rc;
+      } else if (k.form && P->use_sw2)
         ISM_CUDA_TRY(timed(P, 2, 2, [&] { return P->ks.sweeps2(k, P->st); }));
       else ISM_CUDA_TRY(timed(P, 2, 1, [&] { return P->ks.subinterval(k, P->st); }));
     }
@@ -1130,7 +1340,9 @@ int ism_gradient(ism_plan_t P, const double* u, double* grad, double* J) {
     k.form = 1;
     k.global = 1;
     k.count = P->dcount + 3;
-    if (!P->use_sw2) ISM_CUDA_TRY(timed(P, 2, 1, [&] { return P->ks.subinterval(k, P->st); }));
+    if (P->tc) {
+      if ((rc = tc_sub(P, k)) != ISM_OK) return rc;
+    } else if (!P->use_sw2) ISM_CUDA_TRY(timed(P, 2, 1, [&] { return P->ks.subinterval(k, P->st); }));
     else ISM_CUDA_TRY(timed(P, 2, 2, [&] { return P->ks.sweeps2(k, P->st); }));
   }
   if ((rc = copy_out(P, grad, P->dgrad, (long)P->B * P->Nt * P->m))) return rc;
