@@ -42,13 +42,14 @@ DESCR = {"rotor41": "rigid rotor j<=40, maximise <cos theta>(T)",
          "gp512dw": "1D Gross-Pitaevskii condensate, 512-point grid, double-well splitting control, "
                     "harmonic ground state -> split-trap ground state",
          "spin5": "5 coupled spins, 10 controls (u_x, u_y per spin), density matrix in Liouville space, "
-                  "I_x(1) -> I_x(5)"}
-SAMPLE_DIV = {"rotor41": 8, "spin16": 1, "ising1024": 64, "gp512": 8, "gp512dw": 8, "spin5": 256}
+                  "I_x(1) -> I_x(5)",
+         "dense256": "random dense real-symmetric H0, H1 (d = 256) on the tensor cores, random unit target"}
+SAMPLE_DIV = {"dense256": 8, "rotor41": 8, "spin16": 1, "ising1024": 64, "gp512": 8, "gp512dw": 8, "spin5": 256}
 # independent solves per launch: multiples of the 152 SMs (rotor41: two CTAs of 16 problems per SM in
 # the wide lane layout of the direct sweeps; spin16: two CTAs of 8; one CTA per SM and direction for
 # the CTA-wide kinds; two 152-CTA waves for the grid model)
-BATCH_DEFAULT = {"rotor41": 4864, "spin16": 2432, "ising1024": 76, "gp512": 304, "gp512dw": 304, "spin5": 76}
-SOLVE_ITERS = {"rotor41": 50, "spin16": 20, "ising1024": 20, "gp512": 20, "gp512dw": 20, "spin5": 20}   # oracle sample = Nt/div steps, N/div sub-intervals
+BATCH_DEFAULT = {"dense256": 2432, "rotor41": 4864, "spin16": 2432, "ising1024": 76, "gp512": 304, "gp512dw": 304, "spin5": 76}
+SOLVE_ITERS = {"dense256": 20, "rotor41": 50, "spin16": 20, "ising1024": 20, "gp512": 20, "gp512dw": 20, "spin5": 20}   # oracle sample = Nt/div steps, N/div sub-intervals
 FP32_LANES_PER_SM = 128
 SM_MAX_MHZ_GB300 = 2070.0   # fallback when nvidia-smi cannot be read
 
@@ -252,6 +253,8 @@ def load_workload(cfg: str, N=None, Nt=None):
         return w.with_(rho=0.05)
     if cfg == "spin5":
         return W.spin5_liouville(Nt=Nt or 32768, N=N or 128).with_(rho=100.0, iters=20)
+    if cfg == "dense256":
+        return W.random_dense(256, 401, T=(Nt or 1000) / 1000.0, Nt=Nt or 1000, N=N or 16, u_amp=0.5)
     return W.config(cfg, N=N, Nt=Nt)
 
 
@@ -478,6 +481,74 @@ def crank_nicolson_leg(P, w, stream, steps: int, cpu: bool):
     return out
 
 
+def tf32_peak() -> dict:
+    """The TF32 tensor rate: the measured bf16 GEMM rate (MEASURED_PEAKS.json, else the stated fallback)
+    scaled by the nominal TF32/bf16 ratio (1.1 / 2.25 PFLOP/s dense)."""
+    pk = measured_peaks()
+    return {"peak": pk["bf16_tflops"] * 1.1 / 2.25,
+            "source": f"{pk['source']} bf16 {pk['bf16_tflops']:g} TFLOP/s x 1.1/2.25 (nominal TF32/bf16 ratio)"}
+
+
+def timed_iterations(P, w, B, stream, steps: int, warmup: int = 2, **kw):
+    """ms per batched ISM iteration (CUDA events, mixed precision) and the plan's work/time accounting."""
+    import torch
+
+    rng = np.random.default_rng(7000)
+    amp = float(np.max(np.abs(w.u0)))
+    U0 = np.stack([w.u0] + [rng.uniform(-amp, amp, w.Nt) for _ in range(B - 1)])
+    plan = P.Plan(w, precision="mixed", batch=B, stream=stream, **kw)
+    u = torch.tensor(U0, dtype=torch.float64, device="cuda").contiguous()
+    for _ in range(warmup):
+        plan.ism_iterate(1, u, None, None)
+    plan.ism_set_profiling(True)
+    plan.ism_get_stats(reset=True)
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    torch.cuda.synchronize()
+    with torch.cuda.stream(stream):
+        e0.record(stream)
+        plan.ism_iterate(steps, u, None, None)
+        e1.record(stream)
+    torch.cuda.synchronize()
+    ms = e0.elapsed_time(e1) / steps
+    st = plan.ism_get_stats(reset=True)
+    tc = plan.info(10) == 1
+    plan.close()
+    return ms, st, tc
+
+
+def tensor_core_leg(P, W, stream, steps: int) -> dict:
+    """Dense Hamiltonians on the tensor cores (d = 256; tcgen05, TF32 x 3 split operands): a genuinely
+    dense random H, and the 8-spin chain (d = 256, 9 couplings per row) both as a dense matrix on the
+    tensor cores and through the structured bit-flip path.  Executed tensor flops count every state's
+    Y applications as 2 columns x 2 GEMM halves (H0, H1) x 3 split passes x 2 d^2 flops; useful flops
+    are the algorithmic ones of the operator (dense: 4 d^2 + 2d per Y application of a complex state)."""
+    d, B, Nt, N = 256, 2432, 1000, 16
+    pk = tf32_peak()
+    out = {"d": d, "batch": B, "Nt": Nt, "N": N, "peak_tf32": pk}
+    dense = W.random_dense(d, 401, T=1.0, Nt=Nt, N=N, u_amp=0.5)
+    ms, st, tc = timed_iterations(P, dense, B, stream, steps)
+    tc_ms = st["ms"][0] + st["ms"][2]
+    y = st["y_apps"][0] + st["y_apps"][1]
+    executed = y * 24.0 * d * d
+    useful = cheb_flops("dense", d, y, st["terms"][0] + st["terms"][1], st["substeps"][0] + st["substeps"][1])
+    out["random_dense"] = {"tensor_cores": tc, "value": B / (ms / 1e3), "unit": UNIT, "ms_per_iteration": ms,
+                           "tensor_tflops": executed / (tc_ms / 1e3) / 1e12,
+                           "tensor_frac": executed / (tc_ms / 1e3) / 1e12 / pk["peak"],
+                           "useful_tflops": useful / (tc_ms / 1e3) / 1e12,
+                           "phase_share": {n: st["ms"][i] / max(1e-12, sum(st["ms"]))
+                                           for i, n in enumerate(["k_tc_sweep (global)", "k_phi", "k_tc_sweep + k_tc_zgrad (sub)"])}}
+    chain = W.with_random_target(W.spin_chain(8, 402, T=1.0, Nt=Nt, N=N), 403)
+    ms_d, st_d, tc_d = timed_iterations(P, chain.with_(kind="dense"), B, stream, steps)
+    ms_s, st_s, _ = timed_iterations(P, chain, B, stream, steps)
+    y_s = st_s["y_apps"][0] + st_s["y_apps"][1]
+    useful_s = cheb_flops("bitflip", d, y_s, st_s["terms"][0] + st_s["terms"][1], st_s["substeps"][0] + st_s["substeps"][1])
+    out["spin_chain_8"] = {"dense_on_tensor_cores": {"value": B / (ms_d / 1e3), "ms_per_iteration": ms_d, "tensor_cores": tc_d},
+                           "structured_bitflip": {"value": B / (ms_s / 1e3), "ms_per_iteration": ms_s,
+                                                  "useful_tflops": useful_s / (ms_s / 1e3) / 1e12},
+                           "structured_over_dense": ms_d / ms_s}
+    return out
+
+
 def W_config(w, Nt: int, N: int):
     """The same named workload at another Nt, N (same seed: u0 drawn at the new length)."""
     import workloads as W
@@ -486,7 +557,7 @@ def W_config(w, Nt: int, N: int):
 
 
 # precision each configuration is specified in, and the parity bar its full-size run is tested at
-CONFIG_PRECISION = {"rotor41": "mixed", "spin16": "fp64", "gp512": "mixed", "gp512dw": "mixed", "ising1024": "mixed",
+CONFIG_PRECISION = {"dense256": "mixed", "rotor41": "mixed", "spin16": "fp64", "gp512": "mixed", "gp512dw": "mixed", "ising1024": "mixed",
                     "spin5": "mixed"}
 TESTED = {
     "rotor41": "J within 1e-5, controls within 1e-4, Err within 1e-4 of the FP64 oracle over 50 iterations, "
@@ -498,6 +569,8 @@ TESTED = {
     "ising1024": "J within 1e-5, controls within 1e-4 of the FP64 oracle over 2 iterations; sub-interval gradient "
                  "within 1e-4 (tests/test_gpu_fullsize.py)",
     "spin5": "J within 1e-4 of the density-matrix oracle at the paper's size (tests/test_gpu_pauli.py)",
+    "dense256": "states within 2e-5, gradient within 1e-4 relative and J within 1e-5 of the FP64 oracle on random "
+                "dense d = 128 and 256 (tests/test_gpu_tc.py)",
 }
 SUB_CONFIGS = ("spin16", "gp512", "ising1024")
 
@@ -596,7 +669,11 @@ def measure_config(P, W, cfg: str, args, stream, steps: int, warmup: int, world:
     large = plan.ks_large
     direct = plan.info(6) == 2   # Algorithm 1 (a)-(b) by direct sweeps
     sub = "k_subfwd" if prec == "mixed" else "k_subinterval"
-    if plan.gp:
+    tc = plan.info(10) == 1
+    if tc:
+        names = ["k_tc_sweep (global)", "k_phi", "k_tc_sweep (sub)"]
+        kernels = ["k_cheb_prep + k_tc_sweep", "k_phi", "k_tc_sweep + k_tc_zgrad"]
+    elif plan.gp:
         names = ["k_gp_forward", "k_gp_adjoint", "k_gp_sub"]
         kernels = names
     elif plan.kind == "pauli":
@@ -614,7 +691,17 @@ def measure_config(P, W, cfg: str, args, stream, steps: int, warmup: int, world:
     dom = int(np.argmax(st["ms"]))
     ms_launch = st["ms"][dom] / steps
     peaks = measured_peaks()
-    if plan.gp or dom in (0, 2) or large or direct:
+    if tc and dom in (0, 2):   # executed tensor flops: 2 columns x [H0; H1] x 3 split passes per Y application
+        k = 0 if dom == 0 else 1
+        flops = st["y_apps"][k] * 24.0 * d * d / steps
+        achieved = flops / (ms_launch / 1e3) / 1e12
+        pk = tf32_peak()
+        roof = {"kernel": names[dom], "kernels_timed": kernels[dom], "bound": "tensor", "achieved": achieved,
+                "peak": pk["peak"], "unit": "TFLOP/s", "frac": achieved / pk["peak"], "traffic": None,
+                "peak_source": pk["source"], "flops_per_launch": flops, "ms_per_launch": ms_launch,
+                "useful_tflops": cheb_flops("dense", d, st["y_apps"][k], st["terms"][k], st["substeps"][k]) / steps
+                / (ms_launch / 1e3) / 1e12}
+    elif plan.gp or dom in (0, 2) or large or direct:
         if plan.gp:   # FFT pairs counted by the kernels: forward, adjoint, sub-interval
             pairs = [st["y_apps"][0], st["terms"][0], st["terms"][1]][dom]
             flops = pairs * gp_pair_flops(d) / steps
@@ -733,6 +820,10 @@ def run_ours(args):
     if not args.no_cn and getattr(w, "kind", "") == "tridiag":
         cn = crank_nicolson_leg(P, w, stream, args.steps, cpu=(rank == 0 and world == 1 and not args.no_cpu_baseline))
 
+    tcleg = None
+    if args.config == "rotor41" and not args.no_configs and args.N is None and args.Nt is None:
+        tcleg = tensor_core_leg(P, W, stream, 3)
+
     want_cpu = rank == 0 and world == 1 and not args.no_cpu_baseline
     cpu = cpu_baseline_of(args.config, args.N) if want_cpu else None
 
@@ -760,6 +851,7 @@ def run_ours(args):
         "fp64_plain": fp64,
         "crank_nicolson": cn,
         "configs": others or None,
+        "tensor_cores": tcleg,
         "phase_share": m["phase_share"],
         "roofline": m["roofline"],
         "cpu_baseline": cpu,

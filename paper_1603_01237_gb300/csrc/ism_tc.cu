@@ -23,7 +23,8 @@
 // One CTA owns NS columns (NS/2 states) for the whole sweep (the columns never interact), 1 CTA per SM:
 //   warp 0      : TMEM allocation; one elected lane issues the TMA loads of [H0; H1] (hi and lo, in
 //                 K-chunks through a two-stage ring) and the tcgen05.mma of every chunk, then commits.
-//   warps 1 - 4 : epilogue, one thread per TMEM lane (row f of the output, and f + 128 when d = 256):
+//   warps 1 - 8 : epilogue, two warps per TMEM sub-partition (they split the columns), one thread per
+//                 TMEM lane (row f of the output, and f + 128 when d = 256):
 //                 reads Z from TMEM, forms T_{k+1} and the series sum, writes T_{k+1} (TF32 hi and lo)
 //                 into the shared-memory B operand of the next GEMM and keeps T_k and the sum in TMEM.
 // Shared memory: B operand (the CTA's states, K-major, 128-byte swizzle) hi and lo, 64 KB each; two A
@@ -63,7 +64,8 @@ struct TcCfg {
   static constexpr int BOXR = 2 * D < 256 ? 2 * D : 256;     // rows per TMA box
 };
 
-constexpr int TC_WARPS = 5;   // warp 0: TMA + MMA; warps 1-4: epilogue
+constexpr int TC_WARPS = 9;   // warp 0: TMA + MMA; warps 1-8: epilogue (two per TMEM sub-partition)
+constexpr int TC_CW = 16;     // columns per epilogue chunk (one 32x32b.x16 TMEM load per operand)
 constexpr int TC_THREADS = 32 * TC_WARPS;
 
 // Per-state parameters of the current step, in shared memory.
@@ -111,33 +113,25 @@ __device__ __forceinline__ void mma_commit(uint64_t* bar) {
                : "memory");
 }
 
-// 32 consecutive TMEM columns of this warp's 32 lanes: one register per column
-__device__ __forceinline__ void tmem_ld32(uint32_t taddr, float (&v)[32]) {
-  uint32_t r[32];
+// TC_CW consecutive TMEM columns of this warp's 32 lanes: one register per column
+__device__ __forceinline__ void tmem_ld16(uint32_t taddr, float (&v)[16]) {
+  uint32_t r[16];
   asm volatile(
-      "tcgen05.ld.sync.aligned.32x32b.x32.b32 {%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15,"
-      "%16,%17,%18,%19,%20,%21,%22,%23,%24,%25,%26,%27,%28,%29,%30,%31}, [%32];"
+      "tcgen05.ld.sync.aligned.32x32b.x16.b32 {%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15}, [%16];"
       : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]), "=r"(r[7]), "=r"(r[8]),
-        "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]), "=r"(r[14]), "=r"(r[15]), "=r"(r[16]),
-        "=r"(r[17]), "=r"(r[18]), "=r"(r[19]), "=r"(r[20]), "=r"(r[21]), "=r"(r[22]), "=r"(r[23]), "=r"(r[24]),
-        "=r"(r[25]), "=r"(r[26]), "=r"(r[27]), "=r"(r[28]), "=r"(r[29]), "=r"(r[30]), "=r"(r[31])
+        "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]), "=r"(r[14]), "=r"(r[15])
       : "r"(taddr)
       : "memory");
 #pragma unroll
-  for (int i = 0; i < 32; ++i) v[i] = __uint_as_float(r[i]);
+  for (int i = 0; i < 16; ++i) v[i] = __uint_as_float(r[i]);
 }
-__device__ __forceinline__ void tmem_st32(uint32_t taddr, const float (&v)[32]) {
+__device__ __forceinline__ void tmem_st16(uint32_t taddr, const float (&v)[16]) {
   asm volatile(
-      "tcgen05.st.sync.aligned.32x32b.x32.b32 [%0], {%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15,%16,"
-      "%17,%18,%19,%20,%21,%22,%23,%24,%25,%26,%27,%28,%29,%30,%31,%32};" ::"r"(taddr),
+      "tcgen05.st.sync.aligned.32x32b.x16.b32 [%0], {%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15,%16};" ::"r"(taddr),
       "r"(__float_as_uint(v[0])), "r"(__float_as_uint(v[1])), "r"(__float_as_uint(v[2])), "r"(__float_as_uint(v[3])),
       "r"(__float_as_uint(v[4])), "r"(__float_as_uint(v[5])), "r"(__float_as_uint(v[6])), "r"(__float_as_uint(v[7])),
       "r"(__float_as_uint(v[8])), "r"(__float_as_uint(v[9])), "r"(__float_as_uint(v[10])), "r"(__float_as_uint(v[11])),
-      "r"(__float_as_uint(v[12])), "r"(__float_as_uint(v[13])), "r"(__float_as_uint(v[14])), "r"(__float_as_uint(v[15])),
-      "r"(__float_as_uint(v[16])), "r"(__float_as_uint(v[17])), "r"(__float_as_uint(v[18])), "r"(__float_as_uint(v[19])),
-      "r"(__float_as_uint(v[20])), "r"(__float_as_uint(v[21])), "r"(__float_as_uint(v[22])), "r"(__float_as_uint(v[23])),
-      "r"(__float_as_uint(v[24])), "r"(__float_as_uint(v[25])), "r"(__float_as_uint(v[26])), "r"(__float_as_uint(v[27])),
-      "r"(__float_as_uint(v[28])), "r"(__float_as_uint(v[29])), "r"(__float_as_uint(v[30])), "r"(__float_as_uint(v[31]))
+      "r"(__float_as_uint(v[12])), "r"(__float_as_uint(v[13])), "r"(__float_as_uint(v[14])), "r"(__float_as_uint(v[15]))
       : "memory");
 }
 __device__ __forceinline__ void tmem_wait_ld() { asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory"); }
@@ -154,7 +148,7 @@ __device__ __forceinline__ void tma_load_2d(void* dst, const void* tmap, int x, 
 __device__ __forceinline__ void mbar_expect_tx(uint64_t* bar, unsigned bytes) {
   asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(smem_u32(bar)), "r"(bytes) : "memory");
 }
-__device__ __forceinline__ void epi_sync() { asm volatile("bar.sync 1, 128;" ::: "memory"); }
+__device__ __forceinline__ void epi_sync() { asm volatile("bar.sync 1, 256;" ::: "memory"); }
 
 // Shared-memory matrix descriptor of a K-major operand (SM100 format): start address, leading and
 // stride byte offsets (16-byte units), version 1, swizzle layout (2: 128 B, 4: 64 B, 6: 32 B).
@@ -309,7 +303,8 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
     __syncwarp();
   } else {
     // ============================================================== epilogue (128 threads)
-    const int et = threadIdx.x - 32;                   // 0..127
+    const int et = threadIdx.x - 32;                   // 0..255
+    const int eg = et >> 7;                            // column group: chunks cc = eg, eg + 2, ...
     const int L = 32 * (warp & 3) + lane;              // TMEM lane = output row within a tile
     const uint32_t lane_addr = (uint32_t)(32 * (warp & 3)) << 16;
     const int ew = warp & 3;                           // epilogue warp index for the z partials
@@ -372,7 +367,7 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
     // initial states (FP64) -> FP32 hi + lo in the state scratch, and the B operand of the first GEMM
     for (int lt = 0; lt < C::LT; ++lt) {
       const int f = lt * 128 + L;
-      for (int i = 0; i < NI; ++i) {
+      for (int i = eg; i < NI; i += 2) {
         const TcItem it = p.items[item0 + i];
         double2 z = make_double2(0.0, 0.0);
         if (it.b >= 0) {
@@ -435,24 +430,24 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
           if (!(alive = await_z())) break;
           const bool zterm = p.mode == 1 && g == 0 && sub == 0;   // overlaps <chi|H1 psi> from this Z
           const bool final_g = g + 2 == Kt || (p.mode == 1 && s == p.nsteps);
-          for (int cc = 0; cc < NS / 32; ++cc) {
-            float zloc[8][2];   // the chunk's 8 (psi, chi) pairs: columns 4q .. 4q+3
+          for (int cc = eg; cc < NS / TC_CW; cc += 2) {
+            float zloc[TC_CW / 4][2];   // the chunk's (psi, chi) pairs: columns 4q .. 4q+3
 #pragma unroll
-            for (int q2 = 0; q2 < 8; ++q2) { zloc[q2][0] = 0.f; zloc[q2][1] = 0.f; }
+            for (int q2 = 0; q2 < TC_CW / 4; ++q2) { zloc[q2][0] = 0.f; zloc[q2][1] = 0.f; }
             for (int lt = 0; lt < C::LT; ++lt) {
               const int f = lt * 128 + L;
-              float z0[32], z1[32], tp[32], ac[32];
-              tmem_ld32(tmem + lane_addr + C::TM_Z + lt * NS + cc * 32, z0);
-              tmem_ld32(tmem + lane_addr + C::TM_Z + (C::LT + lt) * NS + cc * 32, z1);
+              float z0[TC_CW], z1[TC_CW], tp[TC_CW], ac[TC_CW];
+              tmem_ld16(tmem + lane_addr + C::TM_Z + lt * NS + cc * TC_CW, z0);
+              tmem_ld16(tmem + lane_addr + C::TM_Z + (C::LT + lt) * NS + cc * TC_CW, z1);
               if (g > 0) {
-                tmem_ld32(tmem + lane_addr + C::TM_TP + lt * NS + cc * 32, tp);
-                tmem_ld32(tmem + lane_addr + C::TM_AC + lt * NS + cc * 32, ac);
+                tmem_ld16(tmem + lane_addr + C::TM_TP + lt * NS + cc * TC_CW, tp);
+                tmem_ld16(tmem + lane_addr + C::TM_AC + lt * NS + cc * TC_CW, ac);
               }
               tmem_wait_ld();
               if (p.mode == 1 && s == p.nsteps) {   // terminal overlap only
 #pragma unroll
-                for (int q2 = 0; q2 < 8; ++q2) {
-                  const int cb = cc * 32 + 4 * q2;
+                for (int q2 = 0; q2 < TC_CW / 4; ++q2) {
+                  const int cb = cc * TC_CW + 4 * q2;
                   const float hr = z1[4 * q2], hi = z1[4 * q2 + 1];
                   const float xr = *reinterpret_cast<const float*>(Bhi + b_off<D>(cb + 2, f)) +
                                    *reinterpret_cast<const float*>(Blo + b_off<D>(cb + 2, f));
@@ -464,8 +459,8 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
                 continue;
               }
 #pragma unroll
-              for (int m = 0; m < 16; ++m) {         // state i = cc*16 + m: columns 2m (re), 2m+1 (im)
-                const int i = cc * 16 + m;
+              for (int m = 0; m < TC_CW / 2; ++m) {   // state i = cc*CW/2 + m: columns 2m (re), 2m+1 (im)
+                const int i = cc * (TC_CW / 2) + m;
                 const TcPar& q = par[i];
                 const int c0 = 2 * i;
                 const uint32_t o0 = b_off<D>(c0, f), o1 = b_off<D>(c0 + 1, f);
@@ -531,18 +526,18 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
                 }
               }
               if (!final_g) {
-                tmem_st32(tmem + lane_addr + C::TM_TP + lt * NS + cc * 32, tp);
-                tmem_st32(tmem + lane_addr + C::TM_AC + lt * NS + cc * 32, ac);
+                tmem_st16(tmem + lane_addr + C::TM_TP + lt * NS + cc * TC_CW, tp);
+                tmem_st16(tmem + lane_addr + C::TM_AC + lt * NS + cc * TC_CW, ac);
               }
             }
             if (zterm || (p.mode == 1 && s == p.nsteps)) {   // the chunk's pair sums over this warp's rows
 #pragma unroll
-              for (int q2 = 0; q2 < 8; ++q2)
+              for (int q2 = 0; q2 < TC_CW / 4; ++q2)
 #pragma unroll
                 for (int h = 0; h < 2; ++h) {
                   float v = zloc[q2][h];
                   for (int o = 16; o >= 1; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
-                  if (lane == 0) zred[(ew * (NI / 2) + cc * 8 + q2) * 2 + h] = v;
+                  if (lane == 0) zred[(ew * (NI / 2) + cc * (TC_CW / 4) + q2) * 2 + h] = v;
                 }
             }
           }
@@ -566,7 +561,7 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
       // global sweeps: the state at each partition point, with the segment phase applied in FP64
       if (p.mode == 0 && alive) {
         epi_sync();
-        for (int i = 0; i < NI; ++i) {
+        for (int i = eg; i < NI; i += 2) {
           const TcItem it = p.items[item0 + i];
           if (it.b < 0) continue;
           TcPar& q = par[i];
