@@ -321,17 +321,24 @@ const char* ism_version(void);
  * Serving loop (no counterpart in the paper, which solves one problem at a time): a server queues
  * submitted solves -- each its own problem, options, initial controls and iteration count, so the
  * Hilbert dimensions, step counts and N of concurrent requests may all differ -- and runs them on
- * `slots` worker threads, one CUDA stream each.  A queued request is admitted, in arrival order, as
- * soon as a slot is free and its plan's device footprint (ism_plan_footprint plus its history
- * buffers) fits in the remaining budget; its plan stays resident on the device for the whole solve
- * and is released when it ends.  Solves of different slots overlap on the GPU, and a request's
- * result does not depend on the other requests.
+ * `slots` worker threads, one CUDA stream each.  Continuous batching: requests of the structured
+ * kinds (tridiagonal, bit-flip) in mixed precision with the Chebyshev step, one local step and one
+ * problem each share launches with the other requests of the same (kind, d, N, objective): a worker
+ * runs a shared plan of group_capacity rows, one ISM pass over all its active rows at a time, retires
+ * the requests that have finished and admits the ones that arrived meanwhile between passes.  Every
+ * row is computed independently of the others, so a request's controls and J history are the same,
+ * bit for bit, alone and in any mix.  Other requests run on a plan of their own.  A shared plan (or a
+ * request's own plan) is admitted when its device footprint fits in what the budget has left; plans
+ * stay resident while they run and are released when their last request ends.
  */
 typedef struct ism_server_s* ism_server_t;
 
 typedef struct {
   int slots;                 /* concurrent solves (worker threads and CUDA streams), 1..64           */
   size_t hbm_budget_bytes;   /* device memory the admitted plans may hold together                   */
+  int group_capacity;        /* rows of a shared plan (continuous batching); 0 = 64; < 0 = no sharing */
+  int group_max_steps;       /* step capacity of a shared plan's rows (longer requests open their own
+                                group); 0 = 50000                                                    */
 } ism_server_options;
 
 enum { ISM_REQ_QUEUED = 0, ISM_REQ_RUNNING = 1, ISM_REQ_DONE = 2, ISM_REQ_FAILED = 3 };
@@ -359,6 +366,11 @@ int ism_server_poll(ism_server_t srv, long long id, int wait, int* state, double
 /* ism_server_release -- forget a finished request (its host copies are freed).  ISM_EINVAL for an
  *   unknown id or a request that is still queued or running. */
 int ism_server_release(ism_server_t srv, long long id);
+
+/* ism_server_stats -- out[0] ISM passes run on shared plans, out[1] request-passes they carried (so
+ *   out[1] / out[0] requests per shared launch sequence), out[2] the most requests in one pass,
+ *   out[3] shared plans opened, out[4] requests run on a plan of their own. */
+int ism_server_stats(ism_server_t srv, long long* out);
 
 /* ism_server_destroy -- finish the running solves, fail the queued ones, stop the workers and free
  *   the server.  The caller must make sure that no other call on srv is in progress (in particular

@@ -27,7 +27,7 @@ STATUS_NAMES = {0: "ISM_OK", 1: "ISM_EINVAL", 2: "ISM_ENOMEM", 3: "ISM_ECUDA", 4
 EXPORTS = ("ism_plan", "ism_plan_destroy", "ism_intermediate_states", "ism_subinterval_grad",
            "ism_iterate", "ism_evaluate", "ism_gradient", "ism_set_profiling", "ism_get_stats", "ism_plan_info",
            "ism_plan_footprint", "ism_server_create", "ism_server_submit", "ism_server_poll",
-           "ism_server_release", "ism_server_destroy",
+           "ism_server_release", "ism_server_stats", "ism_server_destroy",
            "ism_subinterval_grad_noalloc", "ism_measure_peak", "ism_last_error", "ism_version")
 
 
@@ -51,7 +51,8 @@ class IsmStats(C.Structure):
 
 
 class IsmServerOptions(C.Structure):
-    _fields_ = [("slots", C.c_int), ("hbm_budget_bytes", C.c_size_t)]
+    _fields_ = [("slots", C.c_int), ("hbm_budget_bytes", C.c_size_t), ("group_capacity", C.c_int),
+                ("group_max_steps", C.c_int)]
 
 
 ISM_REQ_QUEUED, ISM_REQ_RUNNING, ISM_REQ_DONE, ISM_REQ_FAILED = 0, 1, 2, 3
@@ -105,6 +106,8 @@ def load(path: str | None = None):
     lib.ism_server_poll.restype = i
     lib.ism_server_release.argtypes = [vp, C.c_longlong]
     lib.ism_server_release.restype = i
+    lib.ism_server_stats.argtypes = [vp, C.POINTER(C.c_longlong)]
+    lib.ism_server_stats.restype = i
     lib.ism_server_destroy.argtypes = [vp]
     lib.ism_server_destroy.restype = i
     lib.ism_subinterval_grad_noalloc.argtypes = [C.POINTER(IsmProblem), i, vp, vp, vp, vp, vp]
@@ -433,9 +436,11 @@ class Server:
     """Serving loop of the C ABI (ism_server_*): concurrent solves of different problems on one GPU,
     admitted by device footprint.  submit() returns a request id; result() waits for it."""
 
-    def __init__(self, slots: int = 4, hbm_budget_bytes: int = 16 << 30):
+    def __init__(self, slots: int = 4, hbm_budget_bytes: int = 16 << 30, group_capacity: int = 0,
+                 group_max_steps: int = 0):
         self.handle = C.c_void_p()
-        opt = IsmServerOptions(slots=int(slots), hbm_budget_bytes=int(hbm_budget_bytes))
+        opt = IsmServerOptions(slots=int(slots), hbm_budget_bytes=int(hbm_budget_bytes),
+                               group_capacity=int(group_capacity), group_max_steps=int(group_max_steps))
         rc = load().ism_server_create(C.byref(opt), C.byref(self.handle))
         if rc != ISM_OK:
             raise IsmError(rc, "ism_server_create")
@@ -464,6 +469,13 @@ class Server:
                                       _ptr(t)))
         done = st.value == ISM_REQ_DONE
         return st.value, (u if done else None), (J if done else None), t
+
+    def stats(self) -> dict:
+        """ism_server_stats: shared passes, request-passes they carried, most requests in one pass,
+        shared plans opened, requests run on their own plans."""
+        out = (C.c_longlong * 5)()
+        _check(load().ism_server_stats(self.handle, out))
+        return {"passes": out[0], "request_passes": out[1], "max_rows": out[2], "groups": out[3], "single": out[4]}
 
     def result(self, rid: int):
         st, u, J, t = self.poll(rid, wait=True)

@@ -158,6 +158,11 @@ struct ism_plan_s {
   ism::TcItem* dtc_items = nullptr; // global sweeps: [psi items | chi items], then the sub-interval items
   int tc_npsi = 0, tc_nchi = 0, tc_nsub = 0;   // padded item counts of the three groups
   float* dvstate = nullptr;         // FP32 states of every CTA of the largest launch
+  // heterogeneous batch (continuous batching): every row its own problem (ism::RowTab)
+  bool het = false;
+  int cap = 0;                      // rows allocated; P->B is the number of active rows
+  ism::RowTab rt{};
+  int hstride = 0;
   void* dzp = nullptr;              // large d: per-step, per-warp overlap partials
   double* du = nullptr;
   float* duf = nullptr;             // FP32 copy of the controls (FP32 propagation)
@@ -492,6 +497,8 @@ ism::KParams kparams(ism_plan_s* P, double* u) {
   k.scheme = P->scheme == ISM_SCHEME_CRANK_NICOLSON ? 1 : 0;
   k.m = P->m; k.q = P->q; k.wts = P->dwts; k.cxy = P->dcxy; k.zq = P->dzp;
   k.nrm_w = P->dnrm;
+  k.het = P->het ? 1 : 0;
+  k.rt = P->rt;
   return k;
 }
 
@@ -553,6 +560,8 @@ int run_states(ism_plan_s* P, const double* u, double* Jhist, int hist_stride, i
   c.inv_nrm_psi_i = P->nrm_psi_i > 0.0 ? 1.0 / P->nrm_psi_i : 0.0;
   c.nrm_chi_T = P->obj == ISM_OBJ_OVERLAP ? P->nrm_psi_f : -1.0;
   c.nrm = (P->direct && !P->ks.large) ? P->dnrm : nullptr;   // k_gsweep leaves the squared norms
+  c.het = P->het ? 1 : 0;
+  c.rt = P->rt;
   if (P->ks.large || P->direct || P->tc) {
     c.src64 = 1;
     ISM_CUDA_TRY(timed(P, 1, 1, [&] { return ism::launch_phi(P->prec, c, P->st); }));
@@ -1364,3 +1373,223 @@ int ism_evaluate(ism_plan_t P, const double* u, double* J, double* F) {
 }
 
 }  // extern "C"
+
+// ------------------------------------------------------------------ heterogeneous batch plans
+// Rows of different problems that share the kind, d, N and objective run in the same launches (the
+// continuous-batching server's shared plans): every row holds its own Hamiltonian, states, step
+// count, control time, penalty and step size (ism::RowTab); the direct-sweep kernels, the two-trajectory
+// sub-problems and k_phi read them per row.  Mixed precision, the Chebyshev step, one local step; the
+// structured kinds (tridiagonal, bit-flip).  A row's results do not depend on the other rows: the
+// warp-wide term and step counts only add exact no-ops (zero coefficients, discarded sub-steps,
+// inactive steps).
+namespace ism {
+
+bool het_batchable(const ism_problem& p, const ism_options& o) {
+  if (o.precision != ISM_MIXED || o.scheme != ISM_SCHEME_CHEBYSHEV) return false;
+  if (o.local_iters > 1 || o.subproblem_form == 1 || o.step1 == 1 || o.cheb_tol != 0.0) return false;
+  if (p.batch > 1 || p.controls > 1) return false;
+  if (p.kind == ISM_H_TRIDIAG) return p.d >= 1 && p.d <= 64;
+  if (p.kind == ISM_H_BITFLIP) return p.d >= 2 && p.d <= 1024;
+  return false;
+}
+
+bool het_h1diag(const ism_problem& p) {
+  if (p.kind != ISM_H_TRIDIAG) return true;
+  for (int e = 0; e < p.d; ++e)
+    if (p.H1[e] != 0.0) return true;
+  return false;
+}
+
+int het_create(int kind, int d, int N, int obj, bool h1diag, int Ntmax, int cap, void* stream, ism_plan_t* out,
+               size_t* bytes) {
+  ism_plan_s* P = new (std::nothrow) ism_plan_s();
+  if (!P) return fail(ISM_ENOMEM, "host allocation");
+  P->dry = out == nullptr;
+  P->het = true;
+  P->d = d; P->kind = kind; P->obj = obj; P->Nt = Ntmax; P->N = N; P->B = cap; P->cap = cap;
+  P->prec = ISM_MIXED; P->L = 1; P->form = 2; P->scheme = ISM_SCHEME_CHEBYSHEV;
+  P->T = 1.0; P->tau = 1.0 / Ntmax;   // per row in rt
+  P->tol = 1e-10;
+  P->w = obj == ISM_OBJ_OVERLAP ? 1.0 : 2.0;
+  P->max_spin = 1 << 22;
+  P->st = reinterpret_cast<cudaStream_t>(stream);
+  cudaGetDevice(&P->dev);
+  if (!ism::select_kernels(ISM_MIXED, kind, d, &P->ks, h1diag)) {
+    delete P;
+    return fail(ISM_EUNSUPPORTED, "no compiled kernel for this kind and d");
+  }
+  P->direct = !P->ks.large;
+  P->wide = false;
+  P->r2 = sizeof(float2);
+  const int GE = P->ks.G * P->ks.E;
+  {
+    int q = 0;
+    while (q < 30 && (1 << q) < d) ++q;
+    P->hstride = kind == ISM_H_TRIDIAG ? 4 * d : d + q;
+  }
+  const size_t B = cap, Ns = (size_t)N, Nts = (size_t)Ntmax;
+  int rc = ISM_OK;
+  auto fail_out = [&](int code) { free_all(P); delete P; return code; };
+#define TRY_HET(ptr, n) if ((rc = dalloc(P, &(ptr), (n))) != ISM_OK) return fail_out(rc);
+  unsigned char* dHb = nullptr;
+  TRY_HET(dHb, B * P->hstride * sizeof(float));
+  P->dH = dHb;
+  TRY_HET(P->dH0d, B * d);
+  TRY_HET(P->dpsi_i, B * d);
+  TRY_HET(P->dpsi_f, B * d);
+  if (obj == ISM_OBJ_OBSERVABLE) TRY_HET(P->dO, B * d * d);
+  int* jn = nullptr; double* beta = nullptr; double2* phase = nullptr; double2* ab = nullptr;
+  double* tau = nullptr; double* bnd = nullptr; double* nrm = nullptr; double* rho = nullptr; double* alpha = nullptr;
+  TRY_HET(jn, B * (Ns + 1));
+  TRY_HET(beta, B * Ns);
+  TRY_HET(phase, B * Ns);
+  TRY_HET(ab, B * (Ns + 1));
+  TRY_HET(tau, B);
+  TRY_HET(bnd, B * 3);
+  TRY_HET(nrm, B * 2);
+  TRY_HET(rho, B);
+  TRY_HET(alpha, B * Nts);
+  TRY_HET(P->dcheb, B * Ns * ism::cheb_bytes(ISM_MIXED));
+  TRY_HET(P->dpen, B * Ns);
+  TRY_HET(P->dctab, (size_t)ism::BESSEL_TABLE);
+  TRY_HET(P->dpsin, B * (Ns + 1) * d);
+  TRY_HET(P->dchin, B * (Ns + 1) * d);
+  TRY_HET(P->dphi, B * (Ns + 1) * d);
+  if (P->direct) TRY_HET(P->dnrm, B * (Ns + 1) * 2);
+  if (P->ks.large) {
+    unsigned char* dZ = nullptr;
+    TRY_HET(dZ, B * (Nts + Ns) * P->ks.W * P->r2);
+    P->dzp = dZ;
+  } else {
+    unsigned char* dZ = nullptr;
+    TRY_HET(dZ, B * (Nts + Ns) * P->r2);
+    P->dzs = dZ;
+  }
+  TRY_HET(P->du, B * Nts);
+  TRY_HET(P->duf, B * Nts);
+  TRY_HET(P->dgrad, B * Nts);
+  TRY_HET(P->dJn, B * Ns);
+  TRY_HET(P->derr, B * Ns);
+  TRY_HET(P->dJ, B);
+  TRY_HET(P->dF, B);
+  TRY_HET(P->dstatus, 1);
+  TRY_HET(P->dcount, 7);
+#undef TRY_HET
+  (void)GE;
+  P->rt.jn = jn; P->rt.beta = beta; P->rt.phase = phase; P->rt.ab = ab; P->rt.tau = tau; P->rt.bnd = bnd;
+  P->rt.nrm = nrm; P->rt.rho = rho; P->rt.alpha = alpha; P->rt.hstride = P->hstride; P->rt.ustride = Ntmax;
+  P->dalpha = alpha;   // penalty sums in k_cheb_prep (rows without a penalty hold zeros)
+  if (!out) {
+    *bytes = P->bytes;
+    delete P;
+    return ISM_OK;
+  }
+  std::vector<double> tab(ism::BESSEL_TABLE);
+  ism::bessel_table(tab.data());
+  cudaError_t e = cudaMemcpyAsync(P->dctab, tab.data(), tab.size() * sizeof(double), cudaMemcpyHostToDevice, P->st);
+  if (e == cudaSuccess) e = cudaMemsetAsync(alpha, 0, B * Nts * sizeof(double), P->st);
+  if (e == cudaSuccess) e = cudaMemsetAsync(P->du, 0, B * Nts * sizeof(double), P->st);
+  if (e == cudaSuccess) e = cudaMemsetAsync(P->dstatus, 0, sizeof(int), P->st);
+  if (e == cudaSuccess) e = cudaMemsetAsync(P->dcount, 0, 7 * sizeof(unsigned long long), P->st);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(P->st);
+  if (e != cudaSuccess) return fail_out(fail(ISM_ECUDA, std::string("batch plan upload: ") + cudaGetErrorString(e)));
+  *out = P;
+  return ISM_OK;
+}
+
+int het_set_row(ism_plan_t P, int row, const ism_problem& p, const double* u0, double rho) {
+  if (!P || !P->het || row < 0 || row >= P->cap) return fail(ISM_EINVAL, "bad batch row");
+  if (p.kind != P->kind || p.d != P->d || p.N != P->N || p.objective != P->obj || p.Nt > P->Nt)
+    return fail(ISM_EINVAL, "the problem does not fit this batch plan");
+  const int d = p.d, N = p.N;
+  std::vector<float> hf = pack_op<float>(p.kind, d, p.H0, p.H1, P->ks.G, P->ks.E);
+  hf.resize(P->hstride, 0.f);
+  std::vector<double> h0d(d);
+  for (int e = 0; e < d; ++e) h0d[e] = p.H0[e];
+  Bounds bd = bounds_of(p.kind, d, p.H0, p.H1);
+  const double c0 = 0.5 * (bd.lo + bd.hi);
+  std::vector<int> jn;
+  std::vector<double> beta;
+  std::vector<double2> phase;
+  ism::partition(p.T, p.Nt, N, c0, &jn, &beta, &phase);
+  const double tau = p.T / p.Nt;
+  std::vector<double2> ab(N + 1);
+  for (int n = 0; n <= N; ++n) {
+    const double tn = jn[n] * tau;
+    ab[n] = make_double2((p.T - tn) / p.T, tn / p.T);
+  }
+  const double bnd3[3] = {c0, 0.5 * (bd.hi - bd.lo), bd.h1};
+  double nrm2[2] = {0.0, 0.0};
+  for (int e = 0; e < d; ++e) {
+    nrm2[0] += p.psi_i[2 * e] * p.psi_i[2 * e] + p.psi_i[2 * e + 1] * p.psi_i[2 * e + 1];
+    if (p.objective == ISM_OBJ_OVERLAP) nrm2[1] += p.psi_f[2 * e] * p.psi_f[2 * e] + p.psi_f[2 * e + 1] * p.psi_f[2 * e + 1];
+  }
+  std::vector<double> alpha(P->Nt, 0.0), u(P->Nt, 0.0);
+  if (p.alpha) std::copy(p.alpha, p.alpha + p.Nt, alpha.begin());
+  if (u0) std::copy(u0, u0 + p.Nt, u.begin());
+  cudaError_t e = cudaSuccess;
+  auto h2d = [&](void* dst, const void* src, size_t n) {
+    if (e == cudaSuccess) e = cudaMemcpyAsync(dst, src, n, cudaMemcpyHostToDevice, P->st);
+  };
+  const size_t r = row;
+  h2d(reinterpret_cast<float*>(P->dH) + r * P->hstride, hf.data(), hf.size() * sizeof(float));
+  h2d(P->dH0d + r * d, h0d.data(), d * sizeof(double));
+  h2d(P->dpsi_i + r * d, p.psi_i, 2 * d * sizeof(double));
+  if (p.objective == ISM_OBJ_OVERLAP) h2d(P->dpsi_f + r * d, p.psi_f, 2 * d * sizeof(double));
+  else h2d(P->dO + r * d * d, p.O, (size_t)d * d * sizeof(double));
+  h2d(const_cast<int*>(P->rt.jn) + r * (N + 1), jn.data(), (N + 1) * sizeof(int));
+  h2d(const_cast<double*>(P->rt.beta) + r * N, beta.data(), N * sizeof(double));
+  h2d(const_cast<double2*>(P->rt.phase) + r * N, phase.data(), N * sizeof(double2));
+  h2d(const_cast<double2*>(P->rt.ab) + r * (N + 1), ab.data(), (N + 1) * sizeof(double2));
+  h2d(const_cast<double*>(P->rt.tau) + r, &tau, sizeof(double));
+  h2d(const_cast<double*>(P->rt.bnd) + 3 * r, bnd3, 3 * sizeof(double));
+  h2d(const_cast<double*>(P->rt.nrm) + 2 * r, nrm2, 2 * sizeof(double));
+  h2d(const_cast<double*>(P->rt.rho) + r, &rho, sizeof(double));
+  h2d(const_cast<double*>(P->rt.alpha) + r * P->Nt, alpha.data(), P->Nt * sizeof(double));
+  if (u0) h2d(P->du + r * P->Nt, u.data(), P->Nt * sizeof(double));
+  if (e == cudaSuccess) e = cudaStreamSynchronize(P->st);   // the host vectors above are local
+  if (e != cudaSuccess) return fail(ISM_ECUDA, std::string("batch row upload: ") + cudaGetErrorString(e));
+  return ISM_OK;
+}
+
+int het_move_u(ism_plan_t P, int from, int to) {
+  if (from == to) return ISM_OK;
+  ISM_CUDA_TRY(cudaMemcpyAsync(P->du + (size_t)to * P->Nt, P->du + (size_t)from * P->Nt, P->Nt * sizeof(double),
+                               cudaMemcpyDeviceToDevice, P->st));
+  return ISM_OK;
+}
+
+int het_set_rho(ism_plan_t P, int row, double rho) {
+  ISM_CUDA_TRY(cudaMemcpyAsync(const_cast<double*>(P->rt.rho) + row, &rho, sizeof(double), cudaMemcpyHostToDevice, P->st));
+  ISM_CUDA_TRY(cudaStreamSynchronize(P->st));
+  return ISM_OK;
+}
+
+// One pass of Algorithm 1 (a)-(d) on rows [0, rows): J at the rows' current controls into J (host),
+// the controls updated in place with each row's step size (0: the row is only evaluated).
+int het_step(ism_plan_t P, int rows, double* J) {
+  if (!P || !P->het || rows < 1 || rows > P->cap) return fail(ISM_EINVAL, "bad batch rows");
+  P->B = rows;
+  int rc = begin(P);
+  if (rc) return rc;
+  if ((rc = run_states(P, P->du, nullptr, 0, 0))) return rc;
+  ism::KParams k = kparams(P, P->du);
+  k.update = 1;
+  k.form = 1;
+  k.err = P->derr;
+  k.Jn = P->dJn;
+  k.count = P->dcount + 3;
+  ISM_CUDA_TRY(timed(P, 2, 1, [&] { return P->ks.subinterval(k, P->st); }));
+  ISM_CUDA_TRY(cudaMemcpyAsync(J, P->dJ, rows * sizeof(double), cudaMemcpyDeviceToHost, P->st));
+  return finish(P);
+}
+
+int het_get_u(ism_plan_t P, int row, double* u, int Nt) {
+  ISM_CUDA_TRY(cudaMemcpyAsync(u, P->du + (size_t)row * P->Nt, Nt * sizeof(double), cudaMemcpyDeviceToHost, P->st));
+  ISM_CUDA_TRY(cudaStreamSynchronize(P->st));
+  return ISM_OK;
+}
+
+long long het_kernels(ism_plan_t P) { return P ? P->kernels : 0; }
+
+}  // namespace ism

@@ -143,7 +143,10 @@ __device__ void cheb_params(Cheb<R>& ch, const double* ctab, double tau, double 
   kneed = warp_max_i(kneed);
   if (kneed >= KMAX && lane == 0) atomicOr(status, ST_KOVERFLOW);
   const double sg = ((k >> 1) & 1) ? -1.0 : 1.0;   // (-1)^(k/2) for even k, (-1)^((k-1)/2) for odd k
-  split2<R>(sg * a, ch.cf[k], ch.cl[k]);
+  // terms beyond the sub-interval's own count carry exactly zero: a group whose warp runs more terms
+  // (the largest count of the warp's groups) adds nothing, so a state's rounding does not depend on
+  // the states beside it
+  split2<R>(k < (kneed < 2 ? 2 : kneed) ? sg * a : 0.0, ch.cf[k], ch.cl[k]);
   if (lane == 0) {
     // a_0 - 1 = sum_{m>=1} y^m / (m!)^2 without cancellation
     double t = ctab[M];

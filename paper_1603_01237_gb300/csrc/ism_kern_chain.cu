@@ -92,6 +92,7 @@ cudaError_t launch_phi(int prec, const ChainParams& p, cudaStream_t st) {
 
 cudaError_t launch_cheb_prep(int prec, const KParams& p, cudaStream_t st) {
   if (prec == 0) k_cheb_prep<double><<<dim3(p.N, p.B), 32, 0, st>>>(p);
+  else if (p.het) k_cheb_prep<float, true><<<dim3(p.N, p.B), 32, 0, st>>>(p);
   else k_cheb_prep<float><<<dim3(p.N, p.B), 32, 0, st>>>(p);
   return cudaGetLastError();
 }

@@ -6,12 +6,24 @@ namespace ism {
 
 template <typename R, class Op>
 cudaError_t launch_lsweep_t(const KParams& p, cudaStream_t st) {
+  if constexpr (sizeof(R) == 4) {   // heterogeneous batches (mixed precision only)
+    if (p.het) {
+      k_lsweep<R, Op, true><<<dim3(p.obj == 0 ? 2 : 1, p.B), Op::NT, 0, st>>>(p);
+      return cudaGetLastError();
+    }
+  }
   k_lsweep<R, Op><<<dim3(p.obj == 0 ? 2 : 1, p.B), Op::NT, 0, st>>>(p);
   return cudaGetLastError();
 }
 
 template <typename R, class Op>
 cudaError_t launch_lsub_t(const KParams& p, cudaStream_t st) {
+  if constexpr (sizeof(R) == 4) {
+    if (p.het) {
+      k_lsub<R, Op, true><<<dim3(p.N, p.B), Op::NT, 0, st>>>(p);
+      return cudaGetLastError();
+    }
+  }
   k_lsub<R, Op><<<dim3(p.N, p.B), Op::NT, 0, st>>>(p);
   return cudaGetLastError();
 }

@@ -15,6 +15,35 @@
 
 namespace ism {
 
+// Per-problem data of a heterogeneous batch: problems that share the kind, d, N, precision and
+// objective but each have their own Hamiltonian, initial and target states, step count, control time,
+// penalty and step size (the continuous-batching server merges such requests into one plan).  When
+// KParams::het is set, the direct-sweep kernels read these instead of the plan-wide fields.
+struct RowTab {
+  const int* jn;          // [B][N+1] step boundaries
+  const double* beta;     // [B][N]
+  const double2* phase;   // [B][N] (cos, sin) of each segment's global phase
+  const double2* ab;      // [B][N+1] (a_n, b_n) of Eq. (cible)
+  const double* tau;      // [B]
+  const double* bnd;      // [B][3] spectral centre c0, half-width r0 and the |H1| bound
+  const double* nrm;      // [B][2] |psi_i|^2, |psi_f|^2
+  const double* rho;      // [B] ascent step (0: the problem takes no step)
+  const double* alpha;    // [B][ustride] penalty weights, or null
+  long hstride;           // elements of one problem's packed op data
+  long ustride;           // row stride of u, uf, grad and alpha (the longest Nt)
+};
+
+// The plan-wide or the per-problem view of problem b's data.
+struct RowView {
+  const int* jn;
+  const double* beta;
+  const double2* phase;
+  const double* alpha;
+  double tau, c0, r0, h1n, rho;
+  long us;                // row stride of u, uf, grad
+  long hoff, doff;        // offsets of b's op data (elements) and of its d-vectors (psi_i, psi_f, H0d)
+};
+
 struct KParams {
   int d, Nt, N, B, ldm, dpad;
   double tau, T, c0, r0, h1n, tol, rho, w;
@@ -65,7 +94,33 @@ struct KParams {
   double2* psin_w;             // [B][N+1][d] psi(t_n)
   double2* chin_w;             // [B][N+1][d] chi(t_n)
   void* zp;                    // [B][Nt+N][W] (R2)
+  int het;                     // heterogeneous batch: problem data from rt
+  RowTab rt;
 };
+
+template <bool HET>
+__device__ __forceinline__ RowView row_view(const KParams& p, int b) {
+  RowView r;
+  if constexpr (HET) {
+    r.jn = p.rt.jn + (long)b * (p.N + 1);
+    r.beta = p.rt.beta + (long)b * p.N;
+    r.phase = p.rt.phase + (long)b * p.N;
+    r.alpha = p.rt.alpha ? p.rt.alpha + (long)b * p.rt.ustride : nullptr;
+    r.tau = p.rt.tau[b];
+    r.c0 = p.rt.bnd[3 * b];
+    r.r0 = p.rt.bnd[3 * b + 1];
+    r.h1n = p.rt.bnd[3 * b + 2];
+    r.rho = p.rt.rho[b];
+    r.us = p.rt.ustride;
+    r.hoff = (long)b * p.rt.hstride;
+    r.doff = (long)b * p.d;
+  } else {
+    r.jn = p.jn; r.beta = p.beta; r.phase = p.phase; r.alpha = p.alpha;
+    r.tau = p.tau; r.c0 = p.c0; r.r0 = p.r0; r.h1n = p.h1n; r.rho = p.rho;
+    r.us = p.Nt; r.hoff = 0; r.doff = 0;
+  }
+  return r;
+}
 
 struct ChainParams {
   int d, Nt, N, B, ldm, obj;
@@ -99,6 +154,8 @@ struct ChainParams {
   double nrm_psi_i, inv_nrm_psi_i;   // |psi_i|^2 and its inverse
   double nrm_chi_T;                  // |psi_f|^2 (overlap objective), or -1: summed per problem
   const double* nrm;                 // [B][N+1][2] squared norms from the direct sweeps, or null
+  int het;                           // heterogeneous batch: psi_i, (a_n, b_n), tau and the reference
+  RowTab rt;                         //   norms per problem (k_phi)
 };
 
 template <typename R> __device__ __forceinline__ R ldu_ro(const double* u, long i) { return (R)__ldg(u + i); }
@@ -223,20 +280,21 @@ __global__ void __launch_bounds__(128, Op::ASM_MINB) k_assemble(KParams p) {
 // FP64 pass over the steps, lanes of the group on different steps: the trapezoid gradient term of
 // step j from the slots s, s+1 (Crank-Nicolson: slot s holds both ends), the penalty, Err and the
 // ascent step; J_n = w(-|delta(t_{n+1})|^2/2) - penalty.
-template <int G, bool CNs, typename R2>
+template <int G, bool CNs, bool HET, typename R2>
 __device__ __forceinline__ void sub_grad_pass(const KParams& p, const R2* zs, int b, int n, long gid, int j0, int ns,
                                               double cPhi, double sPhi, double nrm, int lg, int stride, bool valid) {
-  const double beta = p.beta[n];
-  const double ht = 0.5 * p.tau * p.w / ((p.form && !p.global) ? beta : 1.0);
-  const double tb = p.tau / (p.global ? 1.0 : beta);   // Theorem 2: beta_n g_n is the gradient of J
-  const double step = p.rho * beta / p.tau;
-  double* ub = p.u + (long)b * p.Nt;
-  double* gb = p.grad + (long)b * p.Nt;
+  const RowView rv = row_view<HET>(p, b);   // formed here, not kept live across the caller's sweep
+  const double beta = rv.beta[n];
+  const double ht = 0.5 * rv.tau * p.w / ((p.form && !p.global) ? beta : 1.0);
+  const double tb = rv.tau / (p.global ? 1.0 : beta);   // Theorem 2: beta_n g_n is the gradient of J
+  const double step = rv.rho * beta / rv.tau;
+  double* ub = p.u + (long)b * rv.us;
+  double* gb = p.grad + (long)b * rv.us;
   double err = 0.0, pen = 0.0;
   for (int s = lg; s < ns; s += stride) {
     const int j = j0 + s;
     const double uj = ub[j];
-    const double al = p.alpha ? p.alpha[j] : 0.0;
+    const double al = rv.alpha ? rv.alpha[j] : 0.0;
     const R2 za = zs[s], zb = zs[s + 1];
     // Im(exp(-i Phi) z) for the two ends of step j
     const double Ia = cPhi * (double)za.y - sPhi * (double)za.x;
@@ -327,18 +385,19 @@ __device__ __forceinline__ void to_packed(const Vec<R, E>& v, const Vec<R, E>& l
   const bool valid = gid0 < total;                                                                    \
   const long gid = valid ? gid0 : total - 1;                                                          \
   const int n = (int)(gid % p.N), b = (int)(gid / p.N);                                               \
-  const int j0 = p.jn[n], j1 = p.jn[n + 1], ns = j1 - j0;                                             \
+  const RowView rv = row_view<HET>(p, b);                                                             \
+  const int j0 = rv.jn[n], j1 = rv.jn[n + 1], ns = j1 - j0;                                           \
   const int nsw = warp_max_i(ns);                                                                     \
-  const double* ub = p.u + (long)b * p.Nt;                                                            \
-  const float* ufb = p.uf + (long)b * p.Nt;                                                           \
+  const double* ub = p.u + (long)b * rv.us;                                                           \
+  const float* ufb = p.uf + (long)b * rv.us;                                                          \
   Cheb<R>& ch = chs[gib];                                                                             \
   int Kw, Sw;                                                                                         \
   cheb_load<G, R>(ch, reinterpret_cast<const Cheb<R>*>(p.cheb) + gid, lg, Kw, Sw);                    \
   Op op;                                                                                              \
-  op.load(reinterpret_cast<const R*>(p.H), p.H0d, p.d, lg, smem_raw);                                 \
-  op.scale(p.H0d, p.d, lg, ch);                                                                       \
+  op.load(reinterpret_cast<const R*>(p.H) + rv.hoff, p.H0d + rv.doff, p.d, lg, smem_raw);             \
+  op.scale(p.H0d + rv.doff, p.d, lg, ch);                                                             \
   const long off_n = ((long)b * (p.N + 1) + n) * p.d;                                                 \
-  R2* zs = reinterpret_cast<R2*>(p.zs) + (long)b * (p.Nt + p.N) + j0 + n;                             \
+  R2* zs = reinterpret_cast<R2*>(p.zs) + (long)b * (rv.us + p.N) + j0 + n;                            \
   (void)ub; (void)GE; (void)PK
 
 // ------------------------------------------------------------------------------ k_subfwd
@@ -353,7 +412,7 @@ __device__ __forceinline__ void to_packed(const Vec<R, E>& v, const Vec<R, E>& l
 // chi's step gives xi_j = A_j^{-1} chi_j (cn_step_fwd_xi), paired with H1 (psi_j + psi_{j+1}).
 constexpr int SUB_KR = 10;   // series terms held in registers by the packed sub-interval sweeps
 
-template <typename R, class Op>
+template <typename R, class Op, bool HET = false>
 __global__ void __launch_bounds__(128) k_subfwd(KParams p) {
   ISM_SUB_PREAMBLE;
   Vec<R, E> a, alo, c, clo;   // psi and chi (hi + lo in FP32 propagation)
@@ -449,7 +508,7 @@ __global__ void __launch_bounds__(128) k_subfwd(KParams p) {
   __syncwarp();
 
   // |delta(t_{n+1})|^2 with delta = (chi - psi)(t_{n+1}) / beta_n from the FP64 boundary states
-  const double beta = p.beta[n];
+  const double beta = HET ? p.rt.beta[(long)b * p.N + n] : p.beta[n];
   double nrm = 0.0;
 #pragma unroll
   for (int r = 0; r < E; ++r) {
@@ -461,7 +520,7 @@ __global__ void __launch_bounds__(128) k_subfwd(KParams p) {
     }
   }
   nrm = g_sum<G>(nrm);
-  sub_grad_pass<G, Op::CN>(p, zs, b, n, gid, j0, ns, 1.0, 0.0, nrm, lg, G, valid);
+  sub_grad_pass<G, Op::CN, HET>(p, zs, b, n, gid, j0, ns, 1.0, 0.0, nrm, lg, G, valid);
   if (valid) count_work<R>(p.count, ch, 2L * ns, lg);   // psi and chi forward
 }
 
@@ -477,6 +536,7 @@ __global__ void __launch_bounds__(128) k_subfwd(KParams p) {
 // Storage per sub-interval: ceil(ns / cks) states and cks H1 psi vectors instead of ns.
 template <typename R, class Op>
 __global__ void __launch_bounds__(128) k_subinterval(KParams p) {
+  constexpr bool HET = false;   // literal sub-problems: plans of one problem kind only
   ISM_SUB_PREAMBLE;
   const int S = p.cks;
   constexpr int CKP = COMP ? 2 : 1;   // checkpoint parts: hi (+ lo)
@@ -509,7 +569,7 @@ __global__ void __launch_bounds__(128) k_subinterval(KParams p) {
       else { xl.re[r] = R(0); xl.im[r] = R(0); }
     }
   };
-  auto uat = [&](int s) { return uval<R>(p.u + (long)b * p.Nt, ufb, j0 + (s < ns ? s : ns - 1)); };
+  auto uat = [&](int s) { return uval<R>(p.u + (long)b * rv.us, ufb, j0 + (s < ns ? s : ns - 1)); };
 
   // ---- forward sweep: checkpoints, then psi_{s+1} = U_s psi_s
   Vec<R, E> hend;   // H1 psi_n(t_{n+1})
@@ -636,7 +696,7 @@ __global__ void __launch_bounds__(128) k_subinterval(KParams p) {
     }
   }
   __syncwarp();
-  sub_grad_pass<G, Op::CN>(p, zs, b, n, gid, j0, ns, Op::CN ? 1.0 : cPhi, Op::CN ? 0.0 : sPhi, nrm, lg, G, valid);
+  sub_grad_pass<G, Op::CN, HET>(p, zs, b, n, gid, j0, ns, Op::CN ? 1.0 : cPhi, Op::CN ? 0.0 : sPhi, nrm, lg, G, valid);
   // forward U sweep, its recomputation (every segment but the checkpointed state) and the U^H sweep
   if (valid) count_work<R>(p.count, ch, 3L * ns - (ns + S - 1) / S, lg);
 }
@@ -653,19 +713,20 @@ __device__ inline double block_sum(double v, double* red) {
 
 // ---------------------------------------------------------------------------- k_cheb_prep
 // One warp per (problem, n): the bound max|u| on the sub-interval and the propagator parameters.
-template <typename R>
+template <typename R, bool HET = false>
 __global__ void __launch_bounds__(32) k_cheb_prep(KParams p) {
   const int n = blockIdx.x, b = blockIdx.y, lane = threadIdx.x;
-  const int j0 = p.jn[n], j1 = p.jn[n + 1];
-  const double* ub = p.u + (long)b * p.Nt;
+  const RowView rv = row_view<HET>(p, b);
+  const int j0 = rv.jn[n], j1 = rv.jn[n + 1];
+  const double* ub = p.u + (long)b * rv.us;
   float um = 0.f;   // |u| bound; the margin in cheb_params covers its FP32 rounding
   double pen = 0.0;
-  float* ufb = p.uf ? p.uf + (long)b * p.Nt : nullptr;
+  float* ufb = p.uf ? p.uf + (long)b * rv.us : nullptr;
   for (int j = j0 + lane; j < j1; j += 32) {
     const double uj = ub[j];
     if (ufb) ufb[j] = (float)uj;
     um = fmaxf(um, fabsf((float)uj));
-    if (p.alpha) pen += p.alpha[j] * uj * uj;
+    if (rv.alpha) pen += rv.alpha[j] * uj * uj;
   }
   for (int m = 16; m >= 1; m >>= 1) {
     um = fmaxf(um, __shfl_xor_sync(0xffffffffu, um, m));
@@ -674,9 +735,9 @@ __global__ void __launch_bounds__(32) k_cheb_prep(KParams p) {
   if (lane == 0 && p.pen) p.pen[(long)b * p.N + n] = pen;
   __shared__ Cheb<R> ch;
   if (p.scheme == 1) {
-    if (lane == 0) cn_params<R>(ch, p.tau, p.r0, p.h1n, (double)um, p.tol, p.status);
+    if (lane == 0) cn_params<R>(ch, rv.tau, rv.r0, rv.h1n, (double)um, p.tol, p.status);
   } else {
-    cheb_params<R>(ch, p.ctab, p.tau, p.c0, p.r0, p.h1n, (double)um, p.tol, p.phase[n], p.status);
+    cheb_params<R>(ch, p.ctab, rv.tau, rv.c0, rv.r0, rv.h1n, (double)um, p.tol, rv.phase[n], p.status);
   }
   __syncwarp();
   const int* s = reinterpret_cast<const int*>(&ch);
@@ -844,7 +905,7 @@ __global__ void __launch_bounds__(128) k_sweeps2(KParams p) {
 // same group (chi(T) = O psi(T) needs psi(T)).
 constexpr int GSWEEP_KR = 10;   // series terms held in registers by the packed direct sweeps
 
-template <typename R, class Op>
+template <typename R, class Op, bool HET = false>
 __global__ void __launch_bounds__(128) k_gsweep(KParams p) {
   constexpr int G = Op::G, E = Op::E, GPB = 128 / G;
   constexpr bool COMP = sizeof(R) == 4;
@@ -867,13 +928,16 @@ __global__ void __launch_bounds__(128) k_gsweep(KParams p) {
   const long gid = valid ? gid0 : total - 1;
   const int b = (int)gid, dir = (int)blockIdx.y;
   const int d = p.d, N = p.N;
-  const double* ub = p.u + (long)b * p.Nt;
-  const float* ufb = p.uf + (long)b * p.Nt;
+  const RowView rv = row_view<HET>(p, b);
+  const double* ub = p.u + (long)b * rv.us;
+  const float* ufb = p.uf + (long)b * rv.us;
+  const double2* psi_i = p.psi_i + rv.doff;
+  const double2* psi_f = p.psi_f + rv.doff;
   double2* psin = p.psin_w + (long)b * (N + 1) * d;
   double2* chin = p.chin_w + (long)b * (N + 1) * d;
   Cheb<R>& ch = chs[gib];
   Op op;
-  op.load(reinterpret_cast<const R*>(p.H), p.H0d, d, lg, smem_raw);
+  op.load(reinterpret_cast<const R*>(p.H) + rv.hoff, p.H0d + rv.doff, d, lg, smem_raw);
   Vec<R, E> v, lo;
   auto load64 = [&](const double2* src) {
 #pragma unroll
@@ -914,56 +978,77 @@ __global__ void __launch_bounds__(128) k_gsweep(KParams p) {
     int Kw, Sw;
     __syncwarp();
     cheb_load<G, R>(ch, reinterpret_cast<const Cheb<R>*>(p.cheb) + (long)b * N + n, lg, Kw, Sw);
-    op.scale(p.H0d, d, lg, ch);
-    const int j0 = p.jn[n], j1 = p.jn[n + 1];
+    op.scale(p.H0d + rv.doff, d, lg, ch);
+    const int j0 = rv.jn[n], j1 = rv.jn[n + 1];
+    // Heterogeneous batches: the groups of a warp belong to different problems whose sub-intervals
+    // have different step counts; the warp runs the largest count (the group shuffles need every lane)
+    // and a group's steps beyond its own are computed and discarded.
+    const int ns = j1 - j0;
+    const int nsw = HET ? warp_max_i(ns) : ns;
     if constexpr (PK) {
       VecP<E> pv, pl;
 #pragma unroll
       for (int r = 0; r < E; ++r) { pv.z[r] = make_float2(v.re[r], v.im[r]); pl.z[r] = make_float2(lo.re[r], lo.im[r]); }
       // controls two steps ahead in registers: the sweep's steps are its critical path
-      const int ns = j1 - j0;
       auto jof = [&](int s) { return ADJ ? j1 - 1 - s : j0 + s; };
       float ua = __ldg(ufb + jof(0)), ub1 = ns > 1 ? __ldg(ufb + jof(1)) : 0.f;
       if (Kw <= GSWEEP_KR) {   // coefficients in registers
         CoefP<GSWEEP_KR> cp;
         load_coef<GSWEEP_KR, ADJ, true>(cp, ch);
         const int S = ch.S;
-        for (int s = 0; s < ns; ++s) {
+        for (int s = 0; s < nsw; ++s) {
           const float uj = ua;
           ua = ub1;
           if (s + 2 < ns) ub1 = __ldg(ufb + jof(s + 2));
           op.set_u(uj, ch, lg);
-          cheb_step_pr<true>(pv, pl, op, cp, Kw, Sw, S);
+          if constexpr (HET) {
+            VecP<E> w = pv, wl = pl;
+            cheb_step_pr<true>(w, wl, op, cp, Kw, Sw, S);
+            if (s < ns) { pv = w; pl = wl; }
+          } else {
+            cheb_step_pr<true>(pv, pl, op, cp, Kw, Sw, S);
+          }
         }
       } else {
-        for (int s = 0; s < ns; ++s) {
+        for (int s = 0; s < nsw; ++s) {
           const float uj = ua;
           ua = ub1;
           if (s + 2 < ns) ub1 = __ldg(ufb + jof(s + 2));
           op.set_u(uj, ch, lg);
-          cheb_step_p<ADJ, true>(pv, pl, op, ch, Kw, Sw);
+          if constexpr (HET) {
+            VecP<E> w = pv, wl = pl;
+            cheb_step_p<ADJ, true>(w, wl, op, ch, Kw, Sw);
+            if (s < ns) { pv = w; pl = wl; }
+          } else {
+            cheb_step_p<ADJ, true>(pv, pl, op, ch, Kw, Sw);
+          }
         }
       }
 #pragma unroll
       for (int r = 0; r < E; ++r) { v.re[r] = pv.z[r].x; v.im[r] = pv.z[r].y; lo.re[r] = pl.z[r].x; lo.im[r] = pl.z[r].y; }
     } else {
-      const int ns = j1 - j0;
       auto jof = [&](int s) { return ADJ ? j1 - 1 - s : j0 + s; };
       R ua = uval<R>(ub, ufb, jof(0)), ub1 = ns > 1 ? uval<R>(ub, ufb, jof(1)) : R(0);
-      for (int s = 0; s < ns; ++s) {
+      for (int s = 0; s < nsw; ++s) {
         const R uj = ua;
         ua = ub1;
         if (s + 2 < ns) ub1 = uval<R>(ub, ufb, jof(s + 2));
         op.set_u(uj, ch, lg);
-        prop_step<ADJ, COMP>(v, lo, op, ch, Kw, Sw);
+        if constexpr (HET) {
+          Vec<R, E> w = v, wl = lo;
+          prop_step<ADJ, COMP>(w, wl, op, ch, Kw, Sw);
+          if (s < ns) { v = w; lo = wl; }
+        } else {
+          prop_step<ADJ, COMP>(v, lo, op, ch, Kw, Sw);
+        }
       }
     }
     if (valid) count_work<R>(p.count, ch, j1 - j0, lg);
   };
   if (dir == 0) {
-    load64(p.psi_i);
+    load64(psi_i);
     if (valid)
-      for (int e = lg; e < d; e += G) psin[e] = p.psi_i[e];
+      for (int e = lg; e < d; e += G) psin[e] = psi_i[e];
     for (int n = 0; n < N; ++n) {
       segment(n, std::false_type());
       store64(false, psin + (long)(n + 1) * d, nrm ? nrm + 2 * (n + 1) : nullptr);
@@ -973,14 +1058,14 @@ __global__ void __launch_bounds__(128) k_gsweep(KParams p) {
     double2* chT = chin + (long)N * d;
     if (p.obj == 0) {
       if (valid)
-        for (int e = lg; e < d; e += G) chT[e] = p.psi_f[e];
+        for (int e = lg; e < d; e += G) chT[e] = psi_f[e];
     } else {   // chi(T) = O psi(T) in FP64; psi(T) was stored by this group
       __syncwarp();
       const double2* psT = psin + (long)N * d;
       for (int e = lg; e < d; e += G) {
         double sr = 0.0, si = 0.0;
         for (int f = 0; f < d; ++f) {
-          const double o = p.O[(long)e * d + f];
+          const double o = p.O[(HET ? (long)b * d * d : 0L) + (long)e * d + f];
           const double2 z = psT[f];
           sr = fma(o, z.x, sr);
           si = fma(o, z.y, si);
@@ -1451,10 +1536,15 @@ __global__ void __launch_bounds__(128) k_phi(ChainParams p) {
   if (n > N + 1) return;   // whole warps leave
   double2* psin = p.psin + (long)b * (N + 1) * d;
   double2* chin = p.chin + (long)b * (N + 1) * d;
+  const double2* psi_i = p.het ? p.psi_i + (long)b * d : p.psi_i;
+  const double2* ab = p.het ? p.rt.ab + (long)b * (N + 1) : p.ab;
+  const double nrm_psi_i = p.het ? p.rt.nrm[2 * b] : p.nrm_psi_i;
+  const double inv_nrm_psi_i = p.het ? (nrm_psi_i > 0.0 ? 1.0 / nrm_psi_i : 0.0) : p.inv_nrm_psi_i;
+  const double tau = p.het ? p.rt.tau[b] : p.tau;
   const R2* sps = reinterpret_cast<const R2*>(p.stage) + (long)b * 2 * (N + 1) * d;
   const R2* sch = sps + (long)(N + 1) * d;
   auto load_ps = [&](int m, int e) -> double2 {
-    if (m == 0) return p.psi_i[e];
+    if (m == 0) return psi_i[e];
     if (p.src64) return psin[(long)m * d + e];
     const R2 z = sps[(long)m * d + e];
     return make_double2((double)z.x, (double)z.y);
@@ -1470,11 +1560,11 @@ __global__ void __launch_bounds__(128) k_phi(ChainParams p) {
   // reference norms: |psi_i|^2 and, for the overlap objective, |chi(T)|^2 = |psi_f|^2 come from the host;
   // the observable's chi(T) = O psi(T) differs per problem and is summed here (FP64 is scarce on this
   // GPU: no divisions, one reciprocal square root per state)
-  double a = 0.0, c = 0.0, cT = p.nrm_chi_T;
+  double a = 0.0, c = 0.0, cT = p.het ? (p.nrm_chi_T < 0.0 ? -1.0 : p.rt.nrm[2 * b + 1]) : p.nrm_chi_T;
   const int m = n <= N ? n : N;
   const double* nb = p.nrm ? p.nrm + (long)b * (N + 1) * 2 : nullptr;
   if (nb) {   // squared norms left by the direct sweeps (psi(t_0) = psi_i and chi(T) are the references)
-    a = m == 0 ? p.nrm_psi_i : nb[2 * m];
+    a = m == 0 ? nrm_psi_i : nb[2 * m];
     if (cT < 0.0) cT = nb[2 * N + 1];
     c = m == N ? cT : nb[2 * m + 1];
   } else {
@@ -1499,9 +1589,9 @@ __global__ void __launch_bounds__(128) k_phi(ChainParams p) {
   // roots and divisions for each of the ~10^5-10^6 states of a batched step would cost more than
   // the rest of this kernel.  The drift of chi needs |psi_f|^2 or |chi(T)|^2 inverted only to FP32
   // accuracy (it multiplies a drift of ~1e-6).
-  const double a0 = p.nrm_psi_i;
+  const double a0 = nrm_psi_i;
   const bool okp = a > 0.0 && a0 > 0.0, okc = c > 0.0 && cT > 0.0;
-  const double dp = okp ? fma(a, p.inv_nrm_psi_i, -1.0) : 0.0;
+  const double dp = okp ? fma(a, inv_nrm_psi_i, -1.0) : 0.0;
   const double dc = okc ? (c - cT) * (double)(1.0f / (float)cT) : 0.0;
   auto inv_sqrt1p = [](double dl) { return fabs(dl) < 1e-4 ? fma(fma(0.375, dl, -0.5), dl, 1.0) : rsqrt(1.0 + dl); };
   const double s_psi = inv_sqrt1p(dp);
@@ -1520,7 +1610,7 @@ __global__ void __launch_bounds__(128) k_phi(ChainParams p) {
     // concurrently and applies the scale to its sums; chi(T) = O psi(T) was formed from it)
     const double sp = (n == 0 || n == N) ? 1.0 : s_psi;
     const double sc = n == N ? 1.0 : s_chi;
-    const double2 w = p.ab[n];
+    const double2 w = ab[n];
     double2* phi = p.phi + ((long)b * (N + 1) + n) * d;
     for (int e = lane; e < d; e += 32) {
       double2 ps = load_ps(n, e), cs = load_cs(n, e);
@@ -1550,7 +1640,7 @@ __global__ void __launch_bounds__(128) k_phi(ChainParams p) {
   double pen = 0.0;
   if (p.pen)
     for (int n2 = lane; n2 < N; n2 += 32) pen += p.pen[(long)b * N + n2];
-  pen = 0.5 * p.tau * warp_sum_d(pen);
+  pen = 0.5 * tau * warp_sum_d(pen);
   if (lane == 0) {
     const double F = p.obj == 0 ? ovr * ovr + ovi * ovi : ovr;
     const double J = ovr - pen;

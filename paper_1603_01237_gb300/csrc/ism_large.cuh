@@ -204,7 +204,7 @@ __device__ __forceinline__ void phase_store(Vec<R, E>& v, Vec<R, E>& lo, const C
 // from psi_i, CTA 1 chi backward from psi_f, concurrently.  nchains = 1 (observable): one CTA runs
 // psi, forms chi(T) = O psi(T) in FP64 and runs chi.  Both trajectories are compensated (hi + lo)
 // in FP32 and rounded through FP64 at every sub-interval end, where the segment phase is applied.
-template <typename R, class Op>
+template <typename R, class Op, bool HET = false>
 __global__ void __launch_bounds__(Op::NT) k_lsweep(KParams p) {
   constexpr int E = Op::E, D = Op::D;
   constexpr bool COMP = sizeof(R) == 4;
@@ -214,21 +214,24 @@ __global__ void __launch_bounds__(Op::NT) k_lsweep(KParams p) {
   __shared__ double red[32];
   const int b = blockIdx.y, N = p.N;
   const bool single = gridDim.x == 1;
-  const double* ub = p.u + (long)b * p.Nt;
-  const float* ufb = p.uf + (long)b * p.Nt;
+  const RowView rv = row_view<HET>(p, b);
+  const double* ub = p.u + (long)b * rv.us;
+  const float* ufb = p.uf + (long)b * rv.us;
+  const double2* psi_i = p.psi_i + rv.doff;
+  const double2* psi_f = p.psi_f + rv.doff;
   double2* psin = p.psin_w + (long)b * (N + 1) * D;
   double2* chin = p.chin_w + (long)b * (N + 1) * D;
   Op op;
-  op.load(reinterpret_cast<const R*>(p.H), sbuf);
+  op.load(reinterpret_cast<const R*>(p.H) + rv.hoff, sbuf);
   Vec<R, E> v, lo;
   if (single || blockIdx.x == 0) {
-    load_state<R, E>(v, lo, p.psi_i);
+    load_state<R, E>(v, lo, psi_i);
 #pragma unroll
-    for (int r = 0; r < E; ++r) psin[threadIdx.x * E + r] = p.psi_i[threadIdx.x * E + r];
+    for (int r = 0; r < E; ++r) psin[threadIdx.x * E + r] = psi_i[threadIdx.x * E + r];
     for (int n = 0; n < N; ++n) {
       cheb_load_cta<R>(ch, p.cheb, (long)b * N + n);
-      op.scale(p.H0d, ch);
-      const int j0 = p.jn[n], j1 = p.jn[n + 1];
+      op.scale(p.H0d + rv.doff, ch);
+      const int j0 = rv.jn[n], j1 = rv.jn[n + 1];
       R un = uval<R>(ub, ufb, j0);
       for (int j = j0; j < j1; ++j) {
         const R uj = un;
@@ -244,7 +247,7 @@ __global__ void __launch_bounds__(Op::NT) k_lsweep(KParams p) {
     double2* chT = chin + (long)N * D;
     if (p.obj == 0) {
 #pragma unroll
-      for (int r = 0; r < E; ++r) chT[threadIdx.x * E + r] = p.psi_f[threadIdx.x * E + r];
+      for (int r = 0; r < E; ++r) chT[threadIdx.x * E + r] = psi_f[threadIdx.x * E + r];
     } else {   // chi(T) = O psi(T), FP64; psi(T) was written by this CTA
       __syncthreads();
       const double2* psT = psin + (long)N * D;
@@ -253,7 +256,7 @@ __global__ void __launch_bounds__(Op::NT) k_lsweep(KParams p) {
         const int e = threadIdx.x * E + r;
         double sr = 0.0, si = 0.0;
         for (int f = 0; f < D; ++f) {
-          const double o = p.O[(long)e * D + f];
+          const double o = p.O[(HET ? (long)b * D * D : 0L) + (long)e * D + f];
           const double2 z = psT[f];
           sr = fma(o, z.x, sr);
           si = fma(o, z.y, si);
@@ -265,8 +268,8 @@ __global__ void __launch_bounds__(Op::NT) k_lsweep(KParams p) {
     load_state<R, E>(v, lo, chT);
     for (int n = N - 1; n >= 0; --n) {
       cheb_load_cta<R>(ch, p.cheb, (long)b * N + n);
-      op.scale(p.H0d, ch);
-      const int j0 = p.jn[n], j1 = p.jn[n + 1];
+      op.scale(p.H0d + rv.doff, ch);
+      const int j0 = rv.jn[n], j1 = rv.jn[n + 1];
       R un = uval<R>(ub, ufb, j1 - 1);
       for (int j = j1 - 1; j >= j0; --j) {
         const R uj = un;
@@ -287,7 +290,7 @@ __global__ void __launch_bounds__(Op::NT) k_lsweep(KParams p) {
 // sub-problem, psi_n checkpointed every p.cks steps and each segment's H1 psi_n recomputed from its
 // checkpoint for the adjoint sweep.  Per step each warp stores its partial <chi|H1 psi> (form 1) or
 // <delta|H1 psi> (form 0) in zp (slot s, warp w); the FP64 pass sums the W partials.
-template <typename R, class Op>
+template <typename R, class Op, bool HET = false>
 __global__ void __launch_bounds__(Op::NT) k_lsub(KParams p) {
   constexpr int E = Op::E, D = Op::D, W = Op::W;
   constexpr bool COMP = sizeof(R) == 4;
@@ -297,18 +300,19 @@ __global__ void __launch_bounds__(Op::NT) k_lsub(KParams p) {
   __shared__ Cheb<R> ch;
   __shared__ double red[32];
   const int n = blockIdx.x, b = blockIdx.y, t = threadIdx.x, lane = t & 31, wid = t >> 5;
-  const int j0 = p.jn[n], j1 = p.jn[n + 1], ns = j1 - j0;
+  const RowView rv = row_view<HET>(p, b);
+  const int j0 = rv.jn[n], j1 = rv.jn[n + 1], ns = j1 - j0;
   const long gid = (long)b * p.N + n;
-  double* ub = p.u + (long)b * p.Nt;
-  const float* ufb = p.uf + (long)b * p.Nt;
-  const double beta = p.beta[n];
+  double* ub = p.u + (long)b * rv.us;
+  const float* ufb = p.uf + (long)b * rv.us;
+  const double beta = rv.beta[n];
   cheb_load_cta<R>(ch, p.cheb, gid);
   Op op;
-  op.load(reinterpret_cast<const R*>(p.H), sbuf);
-  op.scale(p.H0d, ch);
+  op.load(reinterpret_cast<const R*>(p.H) + rv.hoff, sbuf);
+  op.scale(p.H0d + rv.doff, ch);
   const int K = ch.K, S = ch.S;
   const long off_n = ((long)b * (p.N + 1) + n) * D;
-  const long slot0 = (long)b * (p.Nt + p.N) + j0 + n;
+  const long slot0 = (long)b * (rv.us + p.N) + j0 + n;
   R2* zp0 = reinterpret_cast<R2*>(p.zp) + slot0 * W;   // slot s: W warp partials
 
   // per-warp partial of <a|h>, FP32 products
@@ -443,15 +447,15 @@ __global__ void __launch_bounds__(Op::NT) k_lsub(KParams p) {
   __syncthreads();   // every warp's partials are written
 
   // ---- FP64 pass over the steps: gradient, Err, ascent step, penalty of J_n
-  const double ht = 0.5 * p.tau * p.w / ((p.form && !p.global) ? beta : 1.0);
-  const double tb = p.tau / (p.global ? 1.0 : beta);   // Theorem 2: beta_n g_n is the gradient of J
-  const double step = p.rho * beta / p.tau;
-  double* gb = p.grad + (long)b * p.Nt;
+  const double ht = 0.5 * rv.tau * p.w / ((p.form && !p.global) ? beta : 1.0);
+  const double tb = rv.tau / (p.global ? 1.0 : beta);   // Theorem 2: beta_n g_n is the gradient of J
+  const double step = rv.rho * beta / rv.tau;
+  double* gb = p.grad + (long)b * rv.us;
   double err = 0.0, pen = 0.0;
   for (int s = t; s < ns; s += blockDim.x) {
     const int j = j0 + s;
     const double uj = ub[j];
-    const double al = p.alpha ? p.alpha[j] : 0.0;
+    const double al = rv.alpha ? rv.alpha[j] : 0.0;
     double zar = 0.0, zai = 0.0, zbr = 0.0, zbi = 0.0;
 #pragma unroll
     for (int w = 0; w < W; ++w) {

@@ -71,6 +71,21 @@ int validate_problem(const ism_problem& p, int precision);
 // with t_n = j_n tau (N values), and (cos, sin) of the segment phase c0 tau (j_{n+1} - j_n) (N values).
 void partition(double T, int Nt, int N, double c0, std::vector<int>* jn, std::vector<double>* beta,
                std::vector<double2>* phase);
+
+// Heterogeneous batch plans (ism_api.cu): rows of different problems sharing kind, d, N and objective,
+// used by the serving loop to run requests in shared launches.  het_create with out == NULL only
+// sizes the plan (*bytes).  het_step runs one ISM pass on rows [0, rows) and returns J at the rows'
+// controls before the pass; a row with step size 0 is evaluated only.
+bool het_batchable(const ism_problem& p, const ism_options& o);
+bool het_h1diag(const ism_problem& p);
+int het_create(int kind, int d, int N, int obj, bool h1diag, int Ntmax, int cap, void* stream, ism_plan_t* out,
+               size_t* bytes);
+int het_set_row(ism_plan_t P, int row, const ism_problem& p, const double* u0, double rho);
+int het_move_u(ism_plan_t P, int from, int to);
+int het_set_rho(ism_plan_t P, int row, double rho);
+int het_step(ism_plan_t P, int rows, double* J);
+int het_get_u(ism_plan_t P, int row, double* u, int Nt);
+long long het_kernels(ism_plan_t P);
 int set_error(int code, const char* msg);
 void clear_error();
 

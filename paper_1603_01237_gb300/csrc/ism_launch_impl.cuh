@@ -37,6 +37,12 @@ cudaError_t launch_subinterval_t(const KParams& p, cudaStream_t st) {
     cudaError_t e = raise_smem_cap(fn);
     if (e != cudaSuccess) return e;
   }
+  if constexpr (sizeof(R) == 4 && !Op::CN && Op::DP_SMEM == 0) {   // heterogeneous batches: FP32 structured kinds
+    if (p.het) {
+      k_subfwd<R, Op, true><<<(unsigned)grid, 128, smem, st>>>(p);
+      return cudaGetLastError();
+    }
+  }
   if (p.form) k_subfwd<R, Op><<<(unsigned)grid, 128, smem, st>>>(p);
   else k_subinterval<R, Op><<<(unsigned)grid, 128, smem, st>>>(p);
   return cudaGetLastError();
@@ -67,6 +73,12 @@ cudaError_t launch_gsweep_t(const KParams& p, cudaStream_t st) {
   if (smem > 40 * 1024) {
     cudaError_t e = raise_smem_cap(reinterpret_cast<const void*>(k_gsweep<R, Op>));
     if (e != cudaSuccess) return e;
+  }
+  if constexpr (sizeof(R) == 4 && !Op::CN && Op::DP_SMEM == 0) {
+    if (p.het) {
+      k_gsweep<R, Op, true><<<dim3((unsigned)grid, p.obj == 0 ? 2 : 1), 128, smem, st>>>(p);
+      return cudaGetLastError();
+    }
   }
   k_gsweep<R, Op><<<dim3((unsigned)grid, p.obj == 0 ? 2 : 1), 128, smem, st>>>(p);
   return cudaGetLastError();

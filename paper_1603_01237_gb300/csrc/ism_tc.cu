@@ -725,7 +725,7 @@ __global__ void __launch_bounds__(128) k_tc_zgrad(KParams p) {
   }
   nrm = g_sum<32>(nrm);
   const float2* zs = reinterpret_cast<const float2*>(p.zs) + (long)b * (p.Nt + p.N) + j0 + n;
-  sub_grad_pass<32, false>(p, zs, b, n, gid, j0, ns, 1.0, 0.0, nrm, lane, 32, true);
+  sub_grad_pass<32, false, false>(p, zs, b, n, gid, j0, ns, 1.0, 0.0, nrm, lane, 32, true);
 }
 
 }  // namespace

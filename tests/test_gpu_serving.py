@@ -40,8 +40,23 @@ def _mix():
     ]
 
 
+def _alone(P, w, prec, iters, **kw):
+    """The request alone: submitted to a server of its own and waited for (for the requests that share
+    launches, a shared plan holding just this one)."""
+    with P.Server(slots=1, hbm_budget_bytes=8 << 30, **kw) as srv:
+        u, J, _ = srv.result(srv.submit(w, iters=iters, precision=prec))
+    return u, J
+
+
 def test_results_in_the_mix_equal_results_alone(P):
-    mix = _mix()
+    """Requests arriving while others run, several of them sharing launches (rotor problems of one N and
+    different step counts and controls; spin chains of one d with different couplings and steps) and
+    joining shared plans between their passes, each give exactly the result they give alone."""
+    mix = _mix() + [
+        (W.config("rotor41", Nt=900, N=16).with_(u0=np.random.default_rng(5).uniform(-1, 1, 900)), "mixed", 4),
+        (W.with_random_target(W.spin_chain(7, 58, T=0.8, Nt=260, N=8, u_amp=1.0), 59), "mixed", 6),
+        (W.config("rotor41", Nt=1700, N=16), "mixed", 2),
+    ]
     rng = np.random.default_rng(1)
     with P.Server(slots=3, hbm_budget_bytes=8 << 30) as srv:
         ids = []
@@ -49,12 +64,41 @@ def test_results_in_the_mix_equal_results_alone(P):
             ids.append(srv.submit(w, iters=iters, precision=prec))
             time.sleep(rng.exponential(0.005))   # arrivals while earlier requests run
         got = [srv.result(i) for i in ids]
+        st = srv.stats()
+    assert st["groups"] >= 1 and st["single"] >= 4   # shared plans and plans of their own both ran
     for (w, prec, iters), (u, J, t) in zip(mix, got):
-        with P.Plan(w, precision=prec) as pl:
-            ua, Ja, _ = pl.iterate(w.u0, iters)
+        ua, Ja = _alone(P, w, prec, iters)
         assert np.array_equal(u, ua), w.name
         assert np.array_equal(J, Ja), w.name
         assert t[2] >= t[1] >= 0.0
+
+
+def test_request_joins_a_running_shared_plan(P):
+    """Continuous batching: a request submitted while another of its group is half-way through its
+    solve is admitted into the same shared plan between two passes (one shared plan opened, two
+    requests in one pass), and both results equal their solves alone."""
+    a = W.config("rotor41", Nt=3000, N=16)
+    b = W.config("rotor41", Nt=1000, N=16).with_(u0=np.random.default_rng(8).uniform(-1, 1, 1000))
+    with P.Server(slots=1, hbm_budget_bytes=8 << 30) as srv:
+        ia = srv.submit(a, iters=150, precision="mixed")
+        for _ in range(2000):   # wait until the first request's plan is running
+            if srv.poll(ia)[0] == P.abi.ISM_REQ_RUNNING:
+                break
+            time.sleep(0.001)
+        time.sleep(0.02)
+        ib = srv.submit(b, iters=3, precision="mixed")
+        ua, Ja, _ = srv.result(ia)
+        ub, Jb, _ = srv.result(ib)
+        st = srv.stats()
+    assert st["groups"] == 1 and st["max_rows"] == 2 and st["single"] == 0
+    for (w, it), (u, J) in zip(((a, 150), (b, 3)), ((ua, Ja), (ub, Jb))):
+        u0, J0 = _alone(P, w, "mixed", it)
+        assert np.array_equal(u, u0) and np.array_equal(J, J0)
+    # and the shared plan's results are the FP64 oracle's to the mixed-precision bar
+    from oracle import ism_oracle as O
+
+    u_o, J_o, _, _ = O.ism_solve(b, b.u0, 3, b.rho)
+    assert np.max(np.abs(Jb[0] - J_o)) <= 1e-4
 
 
 def test_admission_by_footprint(P):
@@ -91,7 +135,7 @@ def test_concurrent_blocked_chains_of_different_sizes(P):
         (W.random_dense(57, 57, T=1.0, Nt=256, N=64), "fp64", 2),
     ]
     mix = base * 6
-    with P.Server(slots=6, hbm_budget_bytes=16 << 30) as srv:
+    with P.Server(slots=6, hbm_budget_bytes=16 << 30, group_capacity=-1) as srv:   # every request its own plan
         ids = [srv.submit(w, iters=it, precision=prec) for w, prec, it in mix]
         got = [srv.result(i) for i in ids]
     alone = []
