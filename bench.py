@@ -334,44 +334,102 @@ def job_throughput(batch: int, steps: int, world: int, ms: float) -> float:
 
 
 # ------------------------------------------------------------------------------ serving mix
-def serving_mix(P, W, seed: int, n_req: int = 48, rate: float = 200.0, slots: int = 8):
-    """Continuous-batching server (ism_server_*) on a request mix shaped like the serving workload:
-    spin systems of d in {16, 64, 256, 1024} (4 all-to-all spins; open chains of 6, 8, 10 sites),
-    N in {8, 32, 128}, 20 iterations each, mixed precision, Poisson arrivals at `rate`/s; step counts
-    Nt ~ U{1000..5000} (the serving workload draws up to 50000; reduced to bound the run).  Reports
-    requests/s over the makespan and p50/p99 latency, against the same requests run one at a time."""
+def serving_request(W, rng, k: int):
+    """One request of the serving mix, as the packed C-ABI problem (no dense matrices): a spin system of
+    d = 16 (4 spins, all-to-all ZZ), 64, 256 or 1024 (open chains of 6, 8, 10 sites), each with its own
+    coupling draw J ~ U[0.5, 1.5], X control on every spin, |0..0> -> |1..1>, T = 10; or the rigid rotor
+    of the rotor benchmark (d = 41, <cos theta> objective, T = pi).  Nt ~ U{1000..50000}, N from
+    {8, 32, 128}, controls drawn like the benchmark's initial guesses, 20 iterations, mixed precision.
+    Returns (name, problem arrays, u0, rho)."""
+    kind = int(rng.integers(0, 5))
+    Nt = int(rng.integers(1000, 50001))
+    N = int(rng.choice([8, 32, 128]))
+    if kind == 4:
+        return "rotor41", W.config("rotor41", Nt=Nt, N=N), rng.uniform(-1.0, 1.0, Nt), 1.0
+    q = (4, 6, 8, 10)[kind]
+    d = 1 << q
+    pairs = [(i, j) for i in range(q) for j in range(i + 1, q)] if q == 4 else [(i, i + 1) for i in range(q - 1)]
+    J = np.random.default_rng(50000 + k).uniform(0.5, 1.5, size=len(pairs))
+    prob = {"d": d, "Nt": Nt, "N": N, "T": 10.0, "H0": W._zz_diagonal(q, pairs, J), "H1": np.ones(q),
+            "psi_i": np.eye(1, d, 0)[0].astype(np.complex128), "psi_f": np.eye(1, d, d - 1)[0].astype(np.complex128)}
+    return ("spin16" if q == 4 else f"chain{d}"), prob, rng.uniform(-0.1, 0.1, Nt), 0.2
+
+
+def serving_mix(P, W, seed: int, window_s: float = 10.0, rate: float = 200.0, slots: int = 16):
+    """The serving workload: Poisson arrivals at `rate`/s for a time-bounded window of `window_s`
+    seconds (the full workload is 10 000 requests at the same rate), continuous batching on the
+    server (ism_server_*: shared plans per (kind, d, N, objective), rows refilled between ISM passes,
+    HBM-budget admission).  Reports requests/s over the makespan, p50/p99 latency, how many requests a
+    shared pass carried, and one-at-a-time FP64 (the library in FP64, one request per plan) estimated
+    per request from timed FP64 iterations of each model (a full FP64 replay would take hours)."""
+    import torch
+
+    from paper_1603_01237_gb300 import abi
+
     rng = np.random.default_rng(seed)
-    reqs = []
-    for k in range(n_req):
-        d = int(rng.choice([16, 64, 256, 1024]))
-        Nt = int(rng.integers(1000, 5001))
-        N = int(min(rng.choice([8, 32, 128]), Nt))
-        if d == 16:
-            w = W.spin_all_to_all(4, 5000 + k, T=10.0 * Nt / 1000, Nt=Nt, N=N)
-        else:
-            q = int(round(np.log2(d)))
-            w = W.spin_chain(q, 5000 + k, T=2e-4 * Nt * 5, Nt=Nt, N=N)
-        reqs.append(W.with_random_target(w, 6000 + k).with_(rho=0.2))
-    gaps = rng.exponential(1.0 / rate, n_req)
-    with P.Server(slots=slots, hbm_budget_bytes=32 << 30) as srv:
-        for w in reqs[:2]:                      # warm-up: module load, first plans
-            srv.result(srv.submit(w, iters=1, precision="mixed"))
+    gaps = rng.exponential(1.0 / rate, int(rate * window_s * 1.5) + 10)
+    arrivals = np.cumsum(gaps)
+    n_req = int(np.searchsorted(arrivals, window_s))
+    reqs = [serving_request(W, rng, k) for k in range(n_req)]
+
+    def packed(name, prob, u0, rho, precision="mixed"):
+        """(ism_problem, ism_options, arrays to keep alive) of a request."""
+        if name == "rotor41":
+            return abi.problem_and_options(prob, precision=precision, rho=rho)
+        keep = [np.ascontiguousarray(prob["H0"]), np.ascontiguousarray(prob["H1"]),
+                prob["psi_i"].view(np.float64).copy(), prob["psi_f"].view(np.float64).copy()]
+        pr = abi.IsmProblem(d=prob["d"], kind=abi.ISM_H_BITFLIP, H0=abi._ptr(keep[0]), H1=abi._ptr(keep[1]),
+                            psi_i=abi._ptr(keep[2]), objective=abi.ISM_OBJ_OVERLAP, psi_f=abi._ptr(keep[3]), O=None,
+                            T=prob["T"], Nt=prob["Nt"], N=prob["N"], alpha=None, batch=1, controls=1)
+        op = abi.IsmOptions(precision=abi.ISM_MIXED if precision == "mixed" else abi.ISM_FP64, local_iters=1,
+                            rho=float(rho), cheb_tol=0.0, max_spin_iters=0, subproblem_form=0, step1=0, scheme=0,
+                            ckpt_stride=0)
+        return pr, op, keep
+
+    subs = [packed(*r) for r in reqs]
+    with P.Server(slots=slots, hbm_budget_bytes=64 << 30) as srv:
+        pr, op, keep = subs[0]
+        srv.result(srv.submit_problem(pr, op, reqs[0][2], 1))   # warm-up: module load, first plan
         t0 = time.perf_counter()
         ids = []
-        for w, g in zip(reqs, gaps):
-            time.sleep(g)
-            ids.append(srv.submit(w, iters=20, precision="mixed"))
+        for (pr, op, keep), (name, prob, u0, rho), t_arr in zip(subs, reqs, arrivals[:n_req]):
+            delay = t0 + t_arr - time.perf_counter()
+            if delay > 0:
+                time.sleep(delay)
+            ids.append(srv.submit_problem(pr, op, u0, 20))
         lat = [srv.result(i)[2][2] for i in ids]
         makespan = time.perf_counter() - t0
-    t1 = time.perf_counter()
-    for w in reqs:
-        with P.Plan(w, precision="mixed") as pl:
-            pl.iterate(w.u0, 20)
-    serial = time.perf_counter() - t1
-    return {"requests": n_req, "arrival_rate_per_s": rate, "slots": slots, "iterations": 20,
-            "requests_per_s": n_req / makespan, "latency_p50_ms": float(np.percentile(lat, 50)),
-            "latency_p99_ms": float(np.percentile(lat, 99)), "one_at_a_time_requests_per_s": n_req / serial,
-            "mix": "d in {16,64,256,1024}, Nt ~ U{1000..5000}, N in {8,32,128}, mixed precision"}
+        st = srv.stats()
+    # one-at-a-time FP64: seconds per step of one FP64 ISM iteration of each model (one problem per plan)
+    per_step = {}
+    for name, prob, u0, rho in reqs:
+        if name in per_step:
+            continue
+        if name == "rotor41":
+            ps = W.config("rotor41", Nt=2000, N=32)
+        else:
+            ps = dict(prob, Nt=2000, N=32)
+        pr, op, keep = packed(name, ps, u0[:2000], rho, precision="fp64")
+        plan = abi.Plan.from_problem(pr, op, keep)
+        uu = np.ascontiguousarray(u0[:2000][None, :])
+        J = np.empty((1, 3))
+        plan.ism_iterate(1, uu, None, None)
+        t1 = time.perf_counter()
+        plan.ism_iterate(2, uu, J, None)
+        per_step[name] = (time.perf_counter() - t1) / 3 / 2000   # 2 iterations and the final evaluation
+        plan.close()
+    est = sum(21 * per_step[name] * (prob.Nt if name == "rotor41" else prob["Nt"]) for name, prob, u0, rho in reqs)
+    return {"requests": n_req, "arrival_rate_per_s": rate, "arrival_window_s": window_s, "slots": slots,
+            "iterations": 20, "requests_per_s": n_req / makespan, "makespan_s": makespan,
+            "latency_p50_ms": float(np.percentile(lat, 50)), "latency_p99_ms": float(np.percentile(lat, 99)),
+            "shared_passes": st["passes"], "requests_per_shared_pass": st["request_passes"] / max(1, st["passes"]),
+            "max_requests_in_a_pass": st["max_rows"], "shared_plans": st["groups"], "own_plans": st["single"],
+            "one_at_a_time_fp64_requests_per_s": n_req / est,
+            "one_at_a_time_fp64": "estimated: 21 x Nt x (seconds per step of a timed 2000-step FP64 ISM iteration of "
+                                  "the request's model, one problem per plan), summed over the requests",
+            "mix": "d in {16 (4 spins all-to-all), 64, 256, 1024 (open chains of 6, 8, 10 sites)} with per-request "
+                   "coupling draws, and the rigid rotor (d = 41); Nt ~ U{1000..50000}, N in {8, 32, 128}, 20 "
+                   "iterations, mixed precision; Poisson arrivals, time-bounded window"}
 
 
 # ------------------------------------------------------------------------------ our arm

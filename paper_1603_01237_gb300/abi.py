@@ -313,6 +313,26 @@ class Plan:
         _check(lib.ism_plan(C.byref(prob), C.byref(opt), st, C.byref(h)))
         self.handle = h
 
+    @classmethod
+    def from_problem(cls, prob, opt, keep, stream=None):
+        """A plan over a prepared (ism_problem, ism_options) pair (arrays in `keep` stay alive with it)."""
+        self = object.__new__(cls)
+        self.w = None
+        self.kind = {v: k for k, v in _KIND.items()}.get(int(prob.kind), "gp")
+        self.batch = max(1, int(prob.batch))
+        self.gp = int(prob.kind) in (ISM_H_GRID_GP, ISM_H_GRID_GP_DOUBLE_WELL)
+        self.m = max(1, int(prob.controls))
+        self.d, self.Nt, self.N = int(prob.d), int(prob.Nt), int(prob.N)
+        self.precision = "fp64" if int(opt.precision) == ISM_FP64 else "mixed"
+        self._keep = keep
+        h = C.c_void_p()
+        st = None
+        if stream is not None:
+            st = stream if isinstance(stream, int) else int(getattr(stream, "cuda_stream", stream))
+        _check(load().ism_plan(C.byref(prob), C.byref(opt), st, C.byref(h)))
+        self.handle = h
+        return self
+
     # ---------------------------------------------------------------- raw entry points (same names)
     # Each checks that its arrays hold at least the doubles the call reads or writes (layouts of ism.h).
     def _n_u(self) -> int:
@@ -445,6 +465,15 @@ class Server:
         if rc != ISM_OK:
             raise IsmError(rc, "ism_server_create")
         self._shape = {}
+
+    def submit_problem(self, prob, opt, u0, iters: int) -> int:
+        """Submit a prepared (ism_problem, ism_options) pair for one problem; u0: (Nt,) controls."""
+        u = np.ascontiguousarray(np.asarray(u0, dtype=np.float64)).reshape(1, -1)
+        _need(u, int(prob.Nt), "u0")
+        rid = C.c_longlong()
+        _check(load().ism_server_submit(self.handle, C.byref(prob), C.byref(opt), _ptr(u), int(iters), C.byref(rid)))
+        self._shape[rid.value] = ((1, int(prob.Nt)), int(iters))
+        return rid.value
 
     def submit(self, w, u0=None, iters=None, batch: int = 1, **plan_kw) -> int:
         prob, opt, keep = problem_and_options(w, batch=batch, **plan_kw)
