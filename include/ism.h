@@ -53,7 +53,13 @@ typedef enum {
 } ism_precision;
 
 typedef enum {
-  /* H0 and H1 are d x d real symmetric, row-major, d <= 64.                                    */
+  /* H0 and H1 are d x d, row-major: real symmetric, or complex Hermitian with real parts H0, H1
+     and imaginary parts ism_problem.H0_imag, H1_imag (antisymmetric).  Sec. 2 states the problem
+     for any Hermitian H0, H1; the gradient Im<chi|H1|psi> of Eq. (gradJ) holds unchanged for
+     complex H1.  d <= 64: every precision and scheme (complex H: the Chebyshev scheme).
+     d = 128 or 256, real symmetric only: the global and sub-interval trajectories are propagated
+     as stacked state matrices on the tensor cores (TF32 operands split three ways, FP32
+     accumulation), ISM_MIXED and local_iters = 1 only; ism_subinterval_grad is ISM_EUNSUPPORTED. */
   ISM_H_DENSE = 0,
   /* d = 2^q spins.  H0 is diagonal: H0[0..d-1] = diag(H0).  H1 = sum_i h_i X_i (bit flips of
      basis index s, spin i <-> bit i): H1[0..q-1] = h_i.  d <= 1024.  For d <= 64 a state lives in
@@ -122,6 +128,10 @@ typedef struct {
   const double* alpha;     /* Nt penalty weights alpha_j = alpha(t at step midpoint), or NULL (0)  */
   int batch;               /* independent control problems in the plan, >= 1 (0 is read as 1)    */
   int controls;            /* number of controls m (ISM_H_PAULI; 0 is read as 1, others must be 1) */
+  const double* H0_imag;   /* ISM_H_DENSE only: Im H0, d x d antisymmetric row-major, or NULL (0)  */
+  const double* H1_imag;   /* ISM_H_DENSE only: Im H1, likewise.  Either non-NULL makes H complex
+                              Hermitian (d <= 64, Chebyshev scheme; ISM_EUNSUPPORTED otherwise);
+                              an imaginary part that is not antisymmetric is ISM_EINVAL.         */
 } ism_problem;
 
 typedef struct {

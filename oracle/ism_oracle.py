@@ -6,7 +6,9 @@ path computes.  Only the test suite, ``__graft_entry__.smoke()`` and the ``cpu_b
 ``--impl reference`` legs of ``bench.py`` may import it.  It shares no code with the CUDA path;
 the two meet only in the seeded arrays of the ``workloads`` package.
 
-Everything is complex128 / float64.  Library primitives used as single steps: ``numpy.linalg.eigh``
+Everything is complex128 / float64; H0 and H1 may be real symmetric or complex Hermitian (Sec. 2 poses
+the problem for any Hermitian pair), and every formula below is written for the Hermitian case.
+Library primitives used as single steps: ``numpy.linalg.eigh``
 (the exact exponential of a Hermitian matrix, U = V exp(-i tau Lambda) V^H) for d <= 64; for larger
 d, ``scipy.sparse.linalg.expm_multiply`` (action of the exponential on a vector, Al-Mohy & Higham)
 on the sparse H(u_j); and, for the exact discrete derivative pin only, ``scipy.linalg.expm``.  There is no blocking, fusion or reordering

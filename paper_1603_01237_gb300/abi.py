@@ -35,7 +35,7 @@ class IsmProblem(C.Structure):
     _fields_ = [("d", C.c_int), ("kind", C.c_int), ("H0", C.c_void_p), ("H1", C.c_void_p),
                 ("psi_i", C.c_void_p), ("objective", C.c_int), ("psi_f", C.c_void_p), ("O", C.c_void_p),
                 ("T", C.c_double), ("Nt", C.c_int), ("N", C.c_int), ("alpha", C.c_void_p), ("batch", C.c_int),
-                ("controls", C.c_int)]
+                ("controls", C.c_int), ("H0_imag", C.c_void_p), ("H1_imag", C.c_void_p)]
 
 
 class IsmOptions(C.Structure):
@@ -225,15 +225,7 @@ def subinterval_grad_noalloc(w, precision: str, phi, u, grad, Jn=None, *, batch:
     _need(u, B * Nt, "u")
     _need(grad, B * Nt, "grad")
     _need(Jn, B * N, "Jn")
-    H0p, H1p = pack_hamiltonian(k, w.H0, w.H1)
-    psi_i = _c128_interleaved(w.psi_i)
-    psi_f = _c128_interleaved(w.psi_f) if w.objective == "overlap" else None
-    O = np.ascontiguousarray(w.O, dtype=np.float64) if w.objective == "observable" else None
-    alpha = None if w.alpha is None else np.ascontiguousarray(w.alpha, dtype=np.float64)
-    prob = IsmProblem(d=int(w.d), kind=_KIND[k], H0=_ptr(H0p), H1=_ptr(H1p), psi_i=_ptr(psi_i),
-                      objective=ISM_OBJ_OVERLAP if w.objective == "overlap" else ISM_OBJ_OBSERVABLE,
-                      psi_f=_ptr(psi_f), O=_ptr(O), T=float(w.T), Nt=int(w.Nt), N=int(w.N), alpha=_ptr(alpha),
-                      batch=int(batch))
+    prob, _, keep = problem_and_options(w, precision=precision, batch=B, kind=k)   # noqa: F841 (keep alive)
     st = None
     if stream is not None:
         st = stream if isinstance(stream, int) else int(getattr(stream, "cuda_stream", stream))
@@ -251,6 +243,7 @@ def problem_and_options(w, *, precision=None, batch=1, local_iters=None, rho=Non
     prec = precision or w.precision
     dwell = gp and getattr(w, "potential", "harmonic") == "double_well"
     m = 1
+    H0i = H1i = None
     if gp:   # grid kinds: H0 = {L, x_min, g} (harmonic trap) or {L, x_min, g, D} (double well)
         H0p = np.array([w.L, w.x_min, w.g] + ([w.dw] if dwell else []), dtype=np.float64)
         H1p = None
@@ -258,17 +251,23 @@ def problem_and_options(w, *, precision=None, batch=1, local_iters=None, rho=Non
         m = int(w.m)
         H0p = np.ascontiguousarray(w.H0d, dtype=np.float64)
         H1p = np.ascontiguousarray(np.stack([w.ax, w.ay], axis=-1), dtype=np.float64).reshape(-1)
+    elif np.iscomplexobj(w.H0) or np.iscomplexobj(w.H1):   # complex Hermitian: real and imaginary parts
+        if kind != "dense":
+            raise ValueError("complex H0, H1 are supported for the dense kind only")
+        H0p, H1p = pack_hamiltonian(kind, np.real(w.H0), np.real(w.H1))
+        H0i = np.ascontiguousarray(np.imag(w.H0), dtype=np.float64)
+        H1i = np.ascontiguousarray(np.imag(w.H1), dtype=np.float64)
     else:
         H0p, H1p = pack_hamiltonian(kind, w.H0, w.H1)
     psi_i = _c128_interleaved(w.psi_i)
     psi_f = _c128_interleaved(w.psi_f) if w.objective == "overlap" else None
     O = np.ascontiguousarray(w.O, dtype=np.float64) if w.objective == "observable" else None
     alpha = None if w.alpha is None else np.ascontiguousarray(w.alpha, dtype=np.float64)
-    keep = [H0p, H1p, psi_i, psi_f, O, alpha]
+    keep = [H0p, H1p, psi_i, psi_f, O, alpha, H0i, H1i]
     prob = IsmProblem(d=d, kind=ISM_H_GRID_GP_DOUBLE_WELL if dwell else _KIND[kind], H0=_ptr(H0p), H1=_ptr(H1p),
                       psi_i=_ptr(psi_i), objective=ISM_OBJ_OVERLAP if w.objective == "overlap" else ISM_OBJ_OBSERVABLE,
                       psi_f=_ptr(psi_f), O=_ptr(O), T=float(w.T), Nt=int(w.Nt), N=int(w.N), alpha=_ptr(alpha),
-                      batch=int(batch), controls=m)
+                      batch=int(batch), controls=m, H0_imag=_ptr(H0i), H1_imag=_ptr(H1i))
     opt = IsmOptions(precision=ISM_FP64 if prec == "fp64" else ISM_MIXED,
                      local_iters=int(local_iters or w.local_iters), rho=float(w.rho if rho is None else rho),
                      cheb_tol=float(cheb_tol), max_spin_iters=int(max_spin_iters),

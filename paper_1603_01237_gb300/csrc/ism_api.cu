@@ -288,7 +288,7 @@ void collect_events(ism_plan_s* P) {
 namespace ism {
 
 // Gershgorin enclosures: spec(H0) in [lo, hi], spectral radius of H1 <= h1.
-Bounds bounds_of(int kind, int d, const double* H0, const double* H1) {
+Bounds bounds_of(int kind, int d, const double* H0, const double* H1, const double* H0i, const double* H1i) {
   Bounds b{0, 0, 0};
   b.lo = INFINITY;
   b.hi = -INFINITY;
@@ -308,12 +308,15 @@ Bounds bounds_of(int kind, int d, const double* H0, const double* H1) {
   } else if (kind == ISM_H_PAULI) {   // the controls' bound is taken per sub-interval on the device
     for (int e = 0; e < d; ++e) { b.lo = std::fmin(b.lo, H0[e]); b.hi = std::fmax(b.hi, H0[e]); }
     b.h1 = 1.0;
-  } else {
+  } else {   // dense: |H_ef| of the complex entries when imaginary parts are given
+    auto mag = [d](const double* re, const double* im, int e, int f) {
+      return im ? std::hypot(re[e * d + f], im[e * d + f]) : std::fabs(re[e * d + f]);
+    };
     for (int e = 0; e < d; ++e) {
       double r0 = 0.0, r1 = 0.0;
       for (int f = 0; f < d; ++f) {
-        if (f != e) r0 += std::fabs(H0[e * d + f]);
-        r1 += std::fabs(H1[e * d + f]);
+        if (f != e) r0 += mag(H0, H0i, e, f);
+        r1 += mag(H1, H1i, e, f);
       }
       b.lo = std::fmin(b.lo, H0[e * d + e] - r0);
       b.hi = std::fmax(b.hi, H0[e * d + e] + r0);
@@ -325,7 +328,8 @@ Bounds bounds_of(int kind, int d, const double* H0, const double* H1) {
 
 // Device layout of the op data in precision R (see ism_device.cuh).
 template <typename R>
-std::vector<R> pack_op(int kind, int d, const double* H0, const double* H1, int G, int E) {
+std::vector<R> pack_op(int kind, int d, const double* H0, const double* H1, int G, int E, const double* H0i,
+                       const double* H1i) {
   std::vector<R> out;
   if (kind == ISM_H_TRIDIAG) {
     out.assign(4 * (size_t)d, R(0));
@@ -343,6 +347,17 @@ std::vector<R> pack_op(int kind, int d, const double* H0, const double* H1, int 
     out.assign((size_t)d + q, R(0));
     for (int e = 0; e < d; ++e) out[e] = (R)H0[e];
     for (int i = 0; i < q; ++i) out[d + i] = (R)H1[i];
+  } else if (H0i || H1i) {   // complex Hermitian: {Re H0, Re H1}, {Im H0, Im H1} per entry
+    const int DP = G * E;
+    out.assign(4 * (size_t)DP * DP, R(0));
+    for (int e = 0; e < d; ++e)
+      for (int f = 0; f < d; ++f) {
+        R* o = &out[4 * ((size_t)e * DP + f)];
+        o[0] = (R)H0[e * d + f];
+        o[1] = (R)H1[e * d + f];
+        o[2] = H0i ? (R)H0i[e * d + f] : R(0);
+        o[3] = H1i ? (R)H1i[e * d + f] : R(0);
+      }
   } else {
     const int DP = G * E;
     out.assign(2 * (size_t)DP * DP, R(0));
@@ -354,8 +369,10 @@ std::vector<R> pack_op(int kind, int d, const double* H0, const double* H1, int 
   }
   return out;
 }
-template std::vector<float> pack_op<float>(int, int, const double*, const double*, int, int);
-template std::vector<double> pack_op<double>(int, int, const double*, const double*, int, int);
+template std::vector<float> pack_op<float>(int, int, const double*, const double*, int, int, const double*,
+                                           const double*);
+template std::vector<double> pack_op<double>(int, int, const double*, const double*, int, int, const double*,
+                                             const double*);
 
 // Shape and value checks shared by every entry point that takes an ism_problem.
 int validate_problem(const ism_problem& p, int precision) {
@@ -368,6 +385,9 @@ int validate_problem(const ism_problem& p, int precision) {
   if (p.kind < ISM_H_DENSE || p.kind > ISM_H_PAULI) return fail(ISM_EINVAL, "unknown Hamiltonian kind");
   if (p.controls < 0 || p.controls > 32 || (p.kind != ISM_H_PAULI && p.controls > 1))
     return fail(ISM_EINVAL, "controls must be 1..32, and 1 unless the kind is ISM_H_PAULI");
+  const bool cx = p.H0_imag || p.H1_imag;
+  if (cx && p.kind != ISM_H_DENSE) return fail(ISM_EINVAL, "H0_imag and H1_imag apply to the dense kind only");
+  if (cx && d > 64) return fail(ISM_EUNSUPPORTED, "complex Hermitian H is built for d <= 64");
   if (p.kind == ISM_H_PAULI) {
     const int m = p.controls < 1 ? 1 : p.controls;
     int q = 0;
@@ -413,27 +433,33 @@ int validate_problem(const ism_problem& p, int precision) {
   const long nH1 = p.kind == ISM_H_DENSE ? (long)d * d : p.kind == ISM_H_TRIDIAG ? 2L * d - 1 : q;
   if (!all_finite(p.H0, nH) || !all_finite(p.H1, nH1) || !all_finite(p.psi_i, 2L * d))
     return fail(ISM_ENONFINITE, "non-finite value in H0, H1 or psi_i");
+  if ((p.H0_imag && !all_finite(p.H0_imag, nH)) || (p.H1_imag && !all_finite(p.H1_imag, nH1)))
+    return fail(ISM_ENONFINITE, "non-finite value in H0_imag or H1_imag");
   if (p.objective == ISM_OBJ_OVERLAP && !all_finite(p.psi_f, 2L * d)) return fail(ISM_ENONFINITE, "non-finite psi_f");
   if (p.objective == ISM_OBJ_OBSERVABLE && !all_finite(p.O, (long)d * d)) return fail(ISM_ENONFINITE, "non-finite O");
   if (p.alpha && !all_finite(p.alpha, p.Nt)) return fail(ISM_ENONFINITE, "non-finite alpha");
-  auto symmetric = [d](const double* A) {
+  // sgn = 1: A = A^T; sgn = -1: A = -A^T (zero diagonal), both to 1e-12 of the largest entry
+  auto symmetric = [d](const double* A, double sgn = 1.0) {
     double s = 0.0;
     for (long i = 0; i < (long)d * d; ++i) s = std::fmax(s, std::fabs(A[i]));
     for (int i = 0; i < d; ++i)
-      for (int j = 0; j < i; ++j)
-        if (std::fabs(A[i * d + j] - A[j * d + i]) > 1e-12 * (s + 1e-300)) return false;
+      for (int j = 0; j <= i; ++j)
+        if (std::fabs(A[i * d + j] - sgn * A[j * d + i]) > 1e-12 * (s + 1e-300)) return false;
     return true;
   };
   if (p.kind == ISM_H_DENSE && (!symmetric(p.H0) || !symmetric(p.H1)))
-    return fail(ISM_EINVAL, "dense H0 and H1 must be real symmetric");
+    return fail(ISM_EINVAL, cx ? "the real parts of dense H0 and H1 must be symmetric" : "dense H0 and H1 must be real symmetric");
+  if ((p.H0_imag && !symmetric(p.H0_imag, -1.0)) || (p.H1_imag && !symmetric(p.H1_imag, -1.0)))
+    return fail(ISM_EINVAL, "H0_imag and H1_imag must be antisymmetric (H Hermitian)");
   if (p.objective == ISM_OBJ_OBSERVABLE && !symmetric(p.O)) return fail(ISM_EINVAL, "O must be real symmetric");
   return ISM_OK;
 }
 
-bool select_kernels(int prec, int kind, int d, KernelSet* ks, bool h1diag) {
+bool select_kernels(int prec, int kind, int d, KernelSet* ks, bool h1diag, bool cx) {
   if (kind == ISM_H_PAULI) return kernels_pauli(prec, d, ks);
   return kind == ISM_H_TRIDIAG   ? kernels_tridiag(prec, d, h1diag, ks)
          : kind == ISM_H_BITFLIP ? (d > 64 ? kernels_large_bitflip(prec, d, ks) : kernels_bitflip(prec, d, ks))
+         : cx                    ? kernels_dense_cx(prec, d, ks)
                                  : kernels_dense(prec, d, ks);
 }
 
@@ -828,6 +854,8 @@ int plan_build(const ism_problem* prob, const ism_options* opt, void* cuda_strea
       (p.kind == ISM_H_GRID_GP || p.kind == ISM_H_GRID_GP_DOUBLE_WELL || p.kind == ISM_H_PAULI || p.d > 64))
     return fail(ISM_EUNSUPPORTED, "the Crank-Nicolson scheme is built for the tridiagonal, dense and bit-flip kinds "
                                   "with d <= 64");
+  if (opt->scheme == ISM_SCHEME_CRANK_NICOLSON && (p.H0_imag || p.H1_imag))
+    return fail(ISM_EUNSUPPORTED, "the Crank-Nicolson scheme is built for real symmetric H");
 
   ism_plan_s* P = new (std::nothrow) ism_plan_s();
   if (!P) return fail(ISM_ENOMEM, "host allocation");
@@ -917,7 +945,8 @@ int plan_build(const ism_problem* prob, const ism_options* opt, void* cuda_strea
     for (int e = 0; e < d; ++e) h1diag |= p.H1[e] != 0.0;
   }
   bool ok = P->scheme == ISM_SCHEME_CRANK_NICOLSON ? ism::kernels_cn(P->prec, p.kind, d, h1diag, &P->ks)
-                                                    : ism::select_kernels(P->prec, p.kind, d, &P->ks, h1diag);
+                                                    : ism::select_kernels(P->prec, p.kind, d, &P->ks, h1diag,
+                                                                          p.H0_imag || p.H1_imag);
   if (!ok) { delete P; return fail(ISM_EUNSUPPORTED, "no compiled kernel for this kind and d"); }
   P->direct = !P->ks.large && (opt->step1 == 2 || (opt->step1 == 0 && P->B >= 96));
   if (P->direct && P->ks.gsweep_wide) {
@@ -961,7 +990,7 @@ int plan_build(const ism_problem* prob, const ism_options* opt, void* cuda_strea
       }
     }
   } else {
-    Bounds bd = bounds_of(p.kind, d, p.H0, p.H1);
+    Bounds bd = bounds_of(p.kind, d, p.H0, p.H1, p.H0_imag, p.H1_imag);
     P->c0 = 0.5 * (bd.lo + bd.hi);
     P->r0 = 0.5 * (bd.hi - bd.lo);
     P->h1n = bd.h1;
@@ -981,8 +1010,13 @@ int plan_build(const ism_problem* prob, const ism_options* opt, void* cuda_strea
   size_t hbytes;
   std::vector<double> hd;
   std::vector<float> hf;
-  if (P->prec == ISM_FP64) { hd = pack_op<double>(p.kind, d, p.H0, p.H1, P->ks.G, P->ks.E); hbytes = hd.size() * sizeof(double); }
-  else { hf = pack_op<float>(p.kind, d, p.H0, p.H1, P->ks.G, P->ks.E); hbytes = hf.size() * sizeof(float); }
+  if (P->prec == ISM_FP64) {
+    hd = pack_op<double>(p.kind, d, p.H0, p.H1, P->ks.G, P->ks.E, p.H0_imag, p.H1_imag);
+    hbytes = hd.size() * sizeof(double);
+  } else {
+    hf = pack_op<float>(p.kind, d, p.H0, p.H1, P->ks.G, P->ks.E, p.H0_imag, p.H1_imag);
+    hbytes = hf.size() * sizeof(float);
+  }
   TRY_ALLOC(dHb, hbytes);
   P->dH = dHb;
   TRY_ALLOC(P->dH0d, (size_t)d);

@@ -223,7 +223,7 @@ __device__ void cheb_load(Cheb<R>& ch, const Cheb<R>* src, int lg, int& Kw, int&
 // in registers, to keep the register count of the many-lane assembly low.
 template <typename R, int G_, int E_, bool HB = true>
 struct OpTridiag {
-  static constexpr int G = G_, E = E_, DP_SMEM = 0;
+  static constexpr int G = G_, E = E_, DP_SMEM = 0, SMEM_WORDS = 0;
   static constexpr bool PACKED = true;   // offers rec_p / h1_p on packed FP32 states
   static constexpr bool CN = false;      // time step: Chebyshev series (OpTridiagCN: Crank-Nicolson)
   // resident assembly CTAs per SM to aim for (caps registers at 128 where that costs no spills)
@@ -363,7 +363,7 @@ template <> struct Log2<1> { static constexpr int v = 0; };
 
 template <typename R, int G_, int E_>
 struct OpBitflip {
-  static constexpr int G = G_, E = E_, DP_SMEM = 0;
+  static constexpr int G = G_, E = E_, DP_SMEM = 0, SMEM_WORDS = 0;
   static constexpr bool PACKED = false;
   static constexpr bool CN = false;
   static constexpr int ASM_MINB = 1;
@@ -427,11 +427,14 @@ struct OpBitflip {
   }
 };
 
-// Dense real-symmetric H0, H1 staged as {H0_ef, H1_ef} pairs in shared memory (row-major, padded to
-// DP = G*E).  The state's elements are broadcast with shuffles.
-template <typename R, int G_, int E_>
+// Dense H0, H1 staged in shared memory (row-major, padded to DP = G*E): real symmetric (CX = false) as
+// {H0_ef, H1_ef} pairs; complex Hermitian (CX = true) as {Re H0_ef, Re H1_ef}, {Im H0_ef, Im H1_ef}
+// pair couples, so that (H v)_re = Re H v_re - Im H v_im and (H v)_im = Re H v_im + Im H v_re.  The
+// state's elements are broadcast with shuffles.
+template <typename R, int G_, int E_, bool CX = false>
 struct OpDense {
   static constexpr int G = G_, E = E_, DP = G_ * E_, DP_SMEM = G_ * E_;
+  static constexpr int SMEM_WORDS = (CX ? 4 : 2) * DP * DP;   // R words of shared memory
   static constexpr bool PACKED = false;
   static constexpr bool CN = false;
   static constexpr int ASM_MINB = 1;
@@ -463,10 +466,18 @@ struct OpDense {
         R vr = g_idx<G>(in.re[s], src), vi = g_idx<G>(in.im[s], src);
 #pragma unroll
         for (int r = 0; r < E; ++r) {
-          R2 p = Hs[(lg * E + r) * DP + f];
-          R y = REC ? fma(u2, p.y, s2 * p.x) : p.y;
-          ar[r] = fma(y, vr, ar[r]);
-          ai[r] = fma(y, vi, ai[r]);
+          if constexpr (CX) {
+            const R2 p = Hs[2 * ((lg * E + r) * DP + f)], q = Hs[2 * ((lg * E + r) * DP + f) + 1];
+            const R yr = REC ? fma(u2, p.y, s2 * p.x) : p.y;
+            const R yi = REC ? fma(u2, q.y, s2 * q.x) : q.y;
+            ar[r] = fma(yr, vr, fma(-yi, vi, ar[r]));
+            ai[r] = fma(yr, vi, fma(yi, vr, ai[r]));
+          } else {
+            const R2 p = Hs[(lg * E + r) * DP + f];
+            const R y = REC ? fma(u2, p.y, s2 * p.x) : p.y;
+            ar[r] = fma(y, vr, ar[r]);
+            ai[r] = fma(y, vi, ai[r]);
+          }
         }
       }
     }

@@ -199,7 +199,7 @@ __global__ void __launch_bounds__(128, Op::ASM_MINB) k_assemble(KParams p) {
   if (Op::G * Op::E == Op::DP_SMEM) {            // dense: stage H pairs for the whole CTA
     const R* src = reinterpret_cast<const R*>(p.H);
     R* dst = reinterpret_cast<R*>(smem_raw);
-    for (int i = threadIdx.x; i < 2 * Op::DP_SMEM * Op::DP_SMEM; i += blockDim.x) dst[i] = src[i];
+    for (int i = threadIdx.x; i < Op::SMEM_WORDS; i += blockDim.x) dst[i] = src[i];
     __syncthreads();
   }
   if (gid >= total) return;
@@ -376,7 +376,7 @@ __device__ __forceinline__ void to_packed(const Vec<R, E>& v, const Vec<R, E>& l
   if (Op::G * Op::E == Op::DP_SMEM) {                                                                 \
     const R* src_ = reinterpret_cast<const R*>(p.H);                                                  \
     R* dst_ = reinterpret_cast<R*>(smem_raw);                                                         \
-    for (int i = threadIdx.x; i < 2 * Op::DP_SMEM * Op::DP_SMEM; i += blockDim.x) dst_[i] = src_[i];  \
+    for (int i = threadIdx.x; i < Op::SMEM_WORDS; i += blockDim.x) dst_[i] = src_[i];  \
     __syncthreads();                                                                                  \
   }                                                                                                   \
   /* warps whose groups are all past the end leave; partially valid warps keep every lane running */ \
@@ -765,7 +765,7 @@ __global__ void __launch_bounds__(128) k_sweeps2(KParams p) {
   if (Op::G * Op::E == Op::DP_SMEM) {
     const R* src = reinterpret_cast<const R*>(p.H);
     R* dst = reinterpret_cast<R*>(smem_raw);
-    for (int i = threadIdx.x; i < 2 * Op::DP_SMEM * Op::DP_SMEM; i += blockDim.x) dst[i] = src[i];
+    for (int i = threadIdx.x; i < Op::SMEM_WORDS; i += blockDim.x) dst[i] = src[i];
     __syncthreads();
   }
   const long warp_first = ((long)blockIdx.x * GPB + (threadIdx.x / 32) * (32 / G));
@@ -919,7 +919,7 @@ __global__ void __launch_bounds__(128) k_gsweep(KParams p) {
   if (Op::G * Op::E == Op::DP_SMEM) {
     const R* src = reinterpret_cast<const R*>(p.H);
     R* dst = reinterpret_cast<R*>(smem_raw);
-    for (int i = threadIdx.x; i < 2 * Op::DP_SMEM * Op::DP_SMEM; i += blockDim.x) dst[i] = src[i];
+    for (int i = threadIdx.x; i < Op::SMEM_WORDS; i += blockDim.x) dst[i] = src[i];
     __syncthreads();
   }
   const long warp_first = ((long)blockIdx.x * GPB + (threadIdx.x / 32) * (32 / G));

@@ -39,13 +39,14 @@ struct KernelSet {
 bool kernels_tridiag(int prec, int d, bool h1diag, KernelSet* ks);   // h1diag: H1 has a diagonal
 bool kernels_bitflip(int prec, int d, KernelSet* ks);
 bool kernels_dense(int prec, int d, KernelSet* ks);
+bool kernels_dense_cx(int prec, int d, KernelSet* ks);   // complex Hermitian H0, H1
 bool kernels_large_bitflip(int prec, int d, KernelSet* ks);   // d = 128, 256, 512, 1024
 bool kernels_pauli(int prec, int d, KernelSet* ks);   // several controls, Pauli structure, d = 128..1024
 // Crank-Nicolson step (FP64 or FP32 propagation): tridiagonal, bit-flip (d <= 64) and dense kinds
 bool kernels_cn(int prec, int kind, int d, bool h1diag, KernelSet* ks);
 cudaError_t launch_chain(int prec, const ChainParams& p, size_t smem, cudaStream_t st);   // k_chain + k_phi
 cudaError_t launch_phi(int prec, const ChainParams& p, cudaStream_t st);                   // k_phi alone
-bool select_kernels(int prec, int kind, int d, KernelSet* ks, bool h1diag = true);
+bool select_kernels(int prec, int kind, int d, KernelSet* ks, bool h1diag = true, bool cx = false);
 // per-sub-interval propagator parameters (one warp each) from the current controls
 cudaError_t launch_cheb_prep(int prec, const KParams& p, cudaStream_t st);
 size_t cheb_bytes(int prec);
@@ -62,9 +63,12 @@ namespace ism {
 
 // Host helpers shared by the entry points (defined in ism_api.cu).
 struct Bounds { double lo, hi, h1; };
-Bounds bounds_of(int kind, int d, const double* H0, const double* H1);
+// H0i, H1i: imaginary parts of a complex Hermitian dense H (or null)
+Bounds bounds_of(int kind, int d, const double* H0, const double* H1, const double* H0i = nullptr,
+                 const double* H1i = nullptr);
 template <typename R>
-std::vector<R> pack_op(int kind, int d, const double* H0, const double* H1, int G, int E);
+std::vector<R> pack_op(int kind, int d, const double* H0, const double* H1, int G, int E, const double* H0i = nullptr,
+                       const double* H1i = nullptr);
 int validate_problem(const ism_problem& p, int precision);
 // The partition of Sec. 2 and its per-sub-interval weights, computed in one place so that every
 // entry point uploads the same bits: j_n = floor(n Nt / N) (N+1 values), beta_n = T / (t_{n+1} - t_n)

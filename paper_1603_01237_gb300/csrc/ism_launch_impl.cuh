@@ -7,7 +7,7 @@ namespace ism {
 
 template <typename R, class Op>
 size_t op_smem_bytes() {
-  return Op::DP_SMEM ? (size_t)2 * Op::DP_SMEM * Op::DP_SMEM * sizeof(R) : 0;
+  return (size_t)Op::SMEM_WORDS * sizeof(R);
 }
 
 template <typename R, class Op>

@@ -90,7 +90,7 @@ extern "C" int ism_subinterval_grad_noalloc(const ism_problem* prob, int precisi
     for (int e = 0; e < p.d; ++e) h1diag |= p.H1[e] != 0.0;
   }
   ism::KernelSet ks;
-  if (!ism::select_kernels(precision, p.kind, p.d, &ks, h1diag))
+  if (!ism::select_kernels(precision, p.kind, p.d, &ks, h1diag, p.H0_imag || p.H1_imag))
     return ism::set_error(ISM_EUNSUPPORTED, "no compiled kernel for this kind and d");
   if (ks.large) return ism::set_error(ISM_EUNSUPPORTED, "the allocation-free entry point covers d <= 64");
 
@@ -100,8 +100,13 @@ extern "C" int ism_subinterval_grad_noalloc(const ism_problem* prob, int precisi
   std::vector<double> hd;
   std::vector<float> hf;
   size_t op_bytes;
-  if (precision == ISM_FP64) { hd = ism::pack_op<double>(p.kind, d, p.H0, p.H1, ks.G, ks.E); op_bytes = hd.size() * r1; }
-  else { hf = ism::pack_op<float>(p.kind, d, p.H0, p.H1, ks.G, ks.E); op_bytes = hf.size() * r1; }
+  if (precision == ISM_FP64) {
+    hd = ism::pack_op<double>(p.kind, d, p.H0, p.H1, ks.G, ks.E, p.H0_imag, p.H1_imag);
+    op_bytes = hd.size() * r1;
+  } else {
+    hf = ism::pack_op<float>(p.kind, d, p.H0, p.H1, ks.G, ks.E, p.H0_imag, p.H1_imag);
+    op_bytes = hf.size() * r1;
+  }
 
   // the literal sub-problem's checkpoints: stride S ~ sqrt(longest sub-interval) (as ism_plan's default)
   const int nsmax = (p.Nt + p.N - 1) / p.N;
@@ -133,7 +138,7 @@ extern "C" int ism_subinterval_grad_noalloc(const ism_problem* prob, int precisi
   if ((rc = scratch_for_current_device(&base)) != ISM_OK) return rc;
 
   const double tau = p.T / p.Nt;
-  ism::Bounds bd = ism::bounds_of(p.kind, d, p.H0, p.H1);
+  ism::Bounds bd = ism::bounds_of(p.kind, d, p.H0, p.H1, p.H0_imag, p.H1_imag);
   const double c0 = 0.5 * (bd.lo + bd.hi);
   std::vector<int> jn;
   std::vector<double> beta;

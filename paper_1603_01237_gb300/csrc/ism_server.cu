@@ -50,7 +50,7 @@ struct Request {
   long long id = 0;
   ism_problem prob{};
   ism_options opt{};
-  std::vector<double> H0, H1, psi_i, psi_f, O, alpha, u, J;
+  std::vector<double> H0, H1, H0i, H1i, psi_i, psi_f, O, alpha, u, J;
   int iters = 0;
   size_t bytes = 0;
   bool batchable = false;
@@ -282,6 +282,10 @@ long long enqueue_copy(ism_server_s* S, const ism_problem& p, const ism_options&
                                                : (size_t)q;
   r->H0 = copy_of(p.H0, nH0);
   r->H1 = copy_of(p.H1, nH1);
+  if (p.kind == ISM_H_DENSE) {   // imaginary parts of a complex Hermitian H
+    r->H0i = copy_of(p.H0_imag, nH0);
+    r->H1i = copy_of(p.H1_imag, nH1);
+  }
   r->psi_i = copy_of(p.psi_i, 2 * (size_t)d);
   if (p.objective == ISM_OBJ_OVERLAP) r->psi_f = copy_of(p.psi_f, 2 * (size_t)d);
   else r->O = copy_of(p.O, (size_t)d * d);
@@ -289,6 +293,8 @@ long long enqueue_copy(ism_server_s* S, const ism_problem& p, const ism_options&
   r->prob = p;
   r->prob.H0 = r->H0.empty() ? nullptr : r->H0.data();
   r->prob.H1 = r->H1.empty() ? nullptr : r->H1.data();
+  r->prob.H0_imag = r->H0i.empty() ? nullptr : r->H0i.data();
+  r->prob.H1_imag = r->H1i.empty() ? nullptr : r->H1i.data();
   r->prob.psi_i = r->psi_i.data();
   r->prob.psi_f = r->psi_f.empty() ? nullptr : r->psi_f.data();
   r->prob.O = r->O.empty() ? nullptr : r->O.data();

@@ -383,3 +383,37 @@ def test_checkpoint_stride_sets_the_literal_footprint(lib):
     prob, opt, keep = abi.problem_and_options(w, precision="fp64", ckpt_stride=-1)
     n = C.c_size_t()
     assert lib.ism_plan_footprint(C.byref(prob), C.byref(opt), C.byref(n)) == abi.ISM_EINVAL
+
+
+def test_complex_hermitian_dense_validated_on_the_host(lib):
+    """Imaginary parts: the dense kind only, antisymmetric, finite, d <= 64, Chebyshev scheme; the
+    complex plan stages both parts of H (a larger op array than the real plan's)."""
+    import workloads as W
+    from paper_1603_01237_gb300 import abi
+
+    w = W.random_hermitian(24, 5, T=1.0, Nt=60, N=3)
+    fc = abi.footprint(w, precision="fp64")
+    fr = abi.footprint(w.with_(H0=w.H0.real.copy(), H1=w.H1.real.copy()), precision="fp64")
+    assert fc > fr > 0
+    assert abi.footprint(w, precision="mixed") > 0
+    assert abi.footprint(w.with_(objective="observable", psi_f=None, O=np.eye(24)), precision="fp64") > 0
+    with pytest.raises(abi.IsmError) as ei:
+        abi.footprint(w, precision="fp64", scheme="crank_nicolson")
+    assert ei.value.status == abi.ISM_EUNSUPPORTED
+    n = C.c_size_t()
+    opt = abi.IsmOptions(precision=0, local_iters=1, rho=0.1)
+    for bad_imag, status in ((np.ones((24, 24)), abi.ISM_EINVAL),              # not antisymmetric
+                             (np.diag(np.ones(24)), abi.ISM_EINVAL),           # diagonal must vanish
+                             (np.full((24, 24), np.nan), abi.ISM_ENONFINITE)):
+        prob, _, keep = abi.problem_and_options(w, precision="fp64")
+        bad = np.ascontiguousarray(bad_imag, dtype=np.float64)
+        prob.H1_imag = bad.ctypes.data
+        assert lib.ism_plan_footprint(C.byref(prob), C.byref(opt), C.byref(n)) == status
+    prob, _, keep = abi.problem_and_options(W.config("rotor41", Nt=100, N=4), precision="fp64")
+    im = np.zeros(100)
+    prob.H0_imag = im.ctypes.data                                             # tridiagonal kind
+    assert lib.ism_plan_footprint(C.byref(prob), C.byref(opt), C.byref(n)) == abi.ISM_EINVAL
+    big = W.random_hermitian(128, 6, T=1.0, Nt=20, N=2)                       # the tensor-core sizes are real only
+    with pytest.raises(abi.IsmError) as ei:
+        abi.footprint(big, precision="mixed")
+    assert ei.value.status == abi.ISM_EUNSUPPORTED

@@ -292,6 +292,27 @@ def _o_exact_gradient_wrong_block(mp):
     mp.setattr(O, "exact_gradient", eg)
 
 
+def _o_propagator_transposed_h(mp):
+    # exp(-i tau H^T): the same for real symmetric H; for complex Hermitian H it is exp(-i tau conj(H))
+    def su(w, u, j0, j1):
+        return _su(w.with_(H0=w.H0.T, H1=w.H1.T), u, j0, j1)
+    mp.setattr(O, "step_unitaries", su)
+
+
+def _o_gradient_h1_transposed(mp):
+    def gg(w, u):
+        tau = w.T / w.Nt
+        psi = O.forward_trajectory(w, u)
+        chi = O.backward_trajectory(w, u, O.terminal_adjoint(w, psi[-1]))
+        im = np.imag(np.einsum("jk,jk->j", chi.conj(), psi @ w.H1))   # H1^T psi
+        return O.weight(w) * 0.5 * tau * (im[1:] + im[:-1]) - tau * O._alpha(w) * np.asarray(u)
+    mp.setattr(O, "global_gradient", gg)
+
+
+def _o_subproblem_h1_conjugated(mp):
+    mp.setattr(O, "subinterval", lambda w, phi, u, n: _sub(w.with_(H1=np.conj(w.H1)), phi, u, n))
+
+
 def _o_fidelity_not_squared(mp):
     def obj(w, u, psi=None):
         J, F = _obj(w, u, psi)
@@ -474,6 +495,9 @@ def _m_controls_swapped(mp):
 
 
 MUTANTS = [
+    (O, "propagator built from H^T (conj(H) for complex Hermitian H)", _o_propagator_transposed_h),
+    (O, "gradient applies H1^T", _o_gradient_h1_transposed),
+    (O, "sub-problems with conj(H1)", _o_subproblem_h1_conjugated),
     (O, "a_n and b_n swapped in Eq. (cible)", _o_ab_swapped),
     (O, "beta_n taken as N on an uneven partition", _o_beta_equal_lengths),
     (O, "partition ends one step short", _o_partition_end_off_by_one),

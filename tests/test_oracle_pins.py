@@ -278,3 +278,107 @@ def test_ising1024_norm_and_reversibility():
     assert np.allclose(np.linalg.norm(p, axis=1), 1.0, atol=1e-12)
     back = O.backward_trajectory(w, w.u0, p[-1])
     assert np.abs(back[0] - w.psi_i).max() < 1e-12
+
+
+# ------------------------------------------------- complex Hermitian H (Sec. 2: any Hermitian H0, H1)
+SY = np.array([[0.0, -1j], [1j, 0.0]])
+
+
+def _sigma_y_problem(Nt=25, N=5, seed=4):
+    """H0 = 0, H1 = sy (complex), psi_i = |0>, psi_f = |1>: exp(-i th sy)|0> = cos th |0> + sin th |1>,
+    so J = sin(tau sum u) and dJ/du_j = tau cos(tau sum u) exactly."""
+    rng = np.random.default_rng(seed)
+    w = W.rabi(0.0, 0.0, T=2.0, Nt=Nt, N=N)
+    return w.with_(H0=np.zeros((2, 2), dtype=np.complex128), H1=SY.copy(), psi_f=np.array([0.0, 1.0 + 0j]),
+                   u0=rng.uniform(-1, 1, Nt))
+
+
+@pytest.mark.parametrize("delta,u", [(1.3, 0.7), (0.0, 2.0)])
+def test_sigma_y_rabi_closed_form(delta, u):
+    """H = (delta/2) sz + (u/2) sy: the same populations as the sx drive, P_1 = (u/Omega)^2 sin^2(Omega t/2);
+    at delta = 0, psi(t) = cos(ut/2)|0> + sin(ut/2)|1> (a real rotation, where sx gives -i sin)."""
+    w = W.rabi(delta, u, T=5.0, Nt=50).with_(H1=0.5 * SY)
+    psi = O.forward_trajectory(w, w.u0)
+    t = np.arange(w.Nt + 1) * w.tau
+    assert np.allclose(np.abs(psi[:, 1]) ** 2, _rabi_populations(delta, u, t), atol=1e-13)
+    if delta == 0.0:
+        assert np.allclose(psi[:, 0], np.cos(u * t / 2), atol=1e-13)
+        assert np.allclose(psi[:, 1], np.sin(u * t / 2), atol=1e-13)
+
+
+def test_sigma_y_closed_form_objective_and_gradient():
+    w = _sigma_y_problem()
+    th = w.tau * np.sum(w.u0)
+    J, F = O.objective(w, w.u0)
+    assert np.isclose(J, np.sin(th), atol=1e-14)
+    g_ref = np.full(w.Nt, w.tau * np.cos(th))
+    assert np.allclose(O.global_gradient(w, w.u0), g_ref, atol=1e-14)
+    assert np.allclose(O.exact_gradient(w, w.u0), g_ref, atol=1e-14)
+    phi = O.intermediate_states(w, w.u0)
+    g, _ = O.subinterval_all(w, phi, w.u0)
+    beta = np.repeat(O.interval_weights(w.T, w.Nt, w.N)[4], np.diff(O.partition(w.Nt, w.N)))
+    assert np.allclose(beta * g, g_ref, atol=1e-14)
+
+
+def test_hermitian_step_unitary_matches_pade_expm():
+    w = W.random_hermitian(6, 71, T=1.0, Nt=6, N=1, u_amp=3.0)
+    U = O.step_unitaries(w, w.u0, 0, w.Nt)
+    for k in range(w.Nt):
+        assert np.allclose(U[k], expm(-1j * w.tau * (w.H0 + w.u0[k] * w.H1)), atol=1e-12)
+
+
+def test_gauge_invariance_of_algorithm1():
+    """The basis change D = diag(exp(i theta)) turns a real symmetric problem into a complex Hermitian
+    one (H -> D H D^H, psi -> D psi) with the same objective, gradients, sub-problem values and
+    iterates, and intermediate states rotated by D."""
+    w = W.random_dense(5, 72, T=2.0, Nt=36, N=4).with_(alpha=np.linspace(0.01, 0.05, 36))
+    theta = np.random.default_rng(73).uniform(0, 2 * np.pi, w.d)
+    wc = W.gauge(w, theta)
+    assert np.abs(wc.H1.imag).max() > 0.1                 # genuinely complex
+    J, F = O.objective(w, w.u0)
+    Jc, Fc = O.objective(wc, w.u0)
+    assert abs(J - Jc) <= 1e-13 and abs(F - Fc) <= 1e-13
+    assert np.allclose(O.global_gradient(wc, w.u0), O.global_gradient(w, w.u0), atol=1e-14)
+    assert np.allclose(O.exact_gradient(wc, w.u0), O.exact_gradient(w, w.u0), atol=1e-14)
+    phi, phic = O.intermediate_states(w, w.u0), O.intermediate_states(wc, w.u0)
+    assert np.allclose(phic, np.exp(1j * theta)[None, :] * phi, atol=1e-13)
+    g, Jn = O.subinterval_all(w, phi, w.u0)
+    gc, Jnc = O.subinterval_all(wc, phic, w.u0)
+    assert np.allclose(gc, g, atol=1e-14) and np.allclose(Jnc, Jn, atol=1e-13)
+    u, Jh, _, E = O.ism_solve(w, w.u0, 2, 0.5)
+    uc, Jhc, _, Ec = O.ism_solve(wc, w.u0, 2, 0.5)
+    assert np.allclose(uc, u, atol=1e-12) and np.allclose(Jhc, Jh, atol=1e-13) and np.allclose(Ec, E, atol=1e-12)
+
+
+@pytest.mark.parametrize("objective", ["overlap", "observable"])
+def test_hermitian_exact_gradient_matches_central_differences(objective):
+    w = W.random_hermitian(4, 74, T=2.0, Nt=20, N=2, objective=objective)
+    w = w.with_(alpha=np.linspace(0.01, 0.05, w.Nt))
+    g = O.exact_gradient(w, w.u0)
+    h = 1e-4
+    fd = np.empty(w.Nt)
+
+    def J_at(j, s):
+        v = w.u0.copy()
+        v[j] += s
+        return O.objective(w, v)[0]
+
+    for j in range(w.Nt):
+        fd[j] = (8 * (J_at(j, h) - J_at(j, -h)) - (J_at(j, 2 * h) - J_at(j, -2 * h))) / (12 * h)
+    assert np.linalg.norm(g - fd) <= 1e-9 * np.linalg.norm(fd)
+
+
+@pytest.mark.parametrize("objective,N", [("overlap", 5), ("observable", 3)])
+def test_hermitian_theorem2_and_theorem1(objective, N):
+    """Theorem 2 (beta_n g_n at phi^u = the global gradient) and, for the overlap, Theorem 1's value
+    identity, with complex Hermitian H."""
+    w = W.random_hermitian(5, 75, T=2.5, Nt=41, N=N, objective=objective)
+    w = w.with_(alpha=np.linspace(0.01, 0.1, w.Nt))
+    phi = O.intermediate_states(w, w.u0)
+    g, _ = O.subinterval_all(w, phi, w.u0)
+    beta = np.repeat(O.interval_weights(w.T, w.Nt, w.N)[4], np.diff(O.partition(w.Nt, w.N)))
+    G = O.global_gradient(w, w.u0)
+    assert np.allclose(beta * g, G, atol=1e-13 * max(1.0, np.abs(G).max()))
+    if objective == "overlap":
+        J, _ = O.objective(w, w.u0)
+        assert np.isclose(O.j_parallel(w, phi, w.u0), J - 1.0, atol=1e-12)

@@ -33,6 +33,8 @@ __all__ = [
     "spin_chain",
     "rotor",
     "random_dense",
+    "random_hermitian",
+    "gauge",
     "rabi",
     "config",
     "CONFIG_NAMES",
@@ -53,8 +55,8 @@ class Workload:
 
     name: str
     kind: str                    # structure hint for the CUDA path: "bitflip" | "tridiag" | "dense"
-    H0: np.ndarray               # (d, d) float64, real symmetric
-    H1: np.ndarray               # (d, d) float64, real symmetric
+    H0: np.ndarray               # (d, d) float64 real symmetric, or complex128 Hermitian (dense kind)
+    H1: np.ndarray               # (d, d) float64 real symmetric, or complex128 Hermitian (dense kind)
     psi_i: np.ndarray            # (d,) complex128
     objective: str               # "overlap" (target psi_f) | "observable" (target O)
     psi_f: Optional[np.ndarray]  # (d,) complex128 when objective == "overlap"
@@ -208,6 +210,49 @@ def random_dense(d: int, seed: int, *, T: float, Nt: int, N: int, u_amp: float =
     u0 = rng.uniform(-u_amp, u_amp, size=Nt)
     return Workload(name=name, kind="dense", H0=H0, H1=H1, psi_i=psi_i, objective=objective,
                     psi_f=psi_f, O=O, T=T, Nt=Nt, N=N, u0=u0)
+
+
+def random_hermitian(d: int, seed: int, *, T: float, Nt: int, N: int, u_amp: float = 0.5,
+                     objective: str = "overlap", name: str = "hermitian") -> Workload:
+    """Random complex Hermitian H0, H1: (A + A^H)/sqrt(4d) with Re A, Im A entries N(0,1) (so that
+    E|H_ef|^2 = 1/d off the diagonal, as for random_dense), random unit psi_i and psi_f (or a random
+    real symmetric observable), u0 ~ U[-u_amp, u_amp].  Draw order: Re A0, Im A0, Re A1, Im A1, psi_i
+    (re, im), target, u0."""
+    rng = np.random.default_rng(seed)
+
+    def herm():
+        A = rng.standard_normal((d, d)) + 1j * rng.standard_normal((d, d))
+        return (A + A.conj().T) / np.sqrt(4.0 * d)
+
+    H0 = herm()
+    H1 = herm()
+
+    def unit():
+        v = rng.standard_normal(d) + 1j * rng.standard_normal(d)
+        return v / np.linalg.norm(v)
+
+    psi_i = unit()
+    psi_f = None
+    O = None
+    if objective == "overlap":
+        psi_f = unit()
+    else:
+        A = rng.standard_normal((d, d))
+        O = (A + A.T) / np.sqrt(2.0 * d)
+    u0 = rng.uniform(-u_amp, u_amp, size=Nt)
+    return Workload(name=name, kind="dense", H0=H0, H1=H1, psi_i=psi_i, objective=objective,
+                    psi_f=psi_f, O=O, T=T, Nt=Nt, N=N, u0=u0)
+
+
+def gauge(w: Workload, theta: np.ndarray) -> Workload:
+    """The same control problem in the basis rotated by D = diag(exp(i theta)): H -> D H D^H,
+    psi -> D psi (a real observable O is kept only when theta makes D O D^H = O, i.e. never here:
+    the overlap objective only).  Every quantity of Algorithm 1 is invariant under this change."""
+    if w.objective != "overlap":
+        raise ValueError("gauge() keeps the overlap objective only")
+    D = np.exp(1j * np.asarray(theta, dtype=np.float64))
+    rot = lambda H: D[:, None] * H * D.conj()[None, :]   # noqa: E731
+    return w.with_(H0=rot(w.H0), H1=rot(w.H1), psi_i=D * w.psi_i, psi_f=D * w.psi_f, name=w.name + "-gauge")
 
 
 def rabi(delta: float, u: float, *, T: float, Nt: int, N: int = 1) -> Workload:
