@@ -159,14 +159,19 @@ typedef struct {
                                   lane group, for throughput, rather than in two concurrent ones);
                               0 = default: 2 when batch >= 96, else 1.  Larger d always sweeps. */
   int scheme;              /* ism_scheme: time step of the piecewise-constant propagation          */
-  int ckpt_stride;         /* literal sub-problems (d <= 64): the forward sweep of sub-interval n
-                              stores psi_n every ckpt_stride steps and the adjoint sweep recomputes
-                              each segment of ckpt_stride steps from its stored state, so a
-                              sub-problem holds ceil(n_steps / S) states and S vectors H1 psi_n
-                              instead of its whole trajectory (the first local step of the
-                              two-trajectory form stores no states at all: it recomputes each
-                              segment from psi(t_n), chi(t_n)).  0 = default, ceil(sqrt(longest
-                              sub-interval)); values above the longest sub-interval are clamped.  */
+  int ckpt_stride;         /* S, checkpoint stride of the literal sub-problems (every linear kind):
+                              the forward sweep of sub-interval n stores psi_n every S steps and
+                              the adjoint sweep recomputes each segment of S steps from its stored
+                              state, so a sub-problem holds ceil(n_steps / S) states and S vectors
+                              instead of its whole trajectory (the first local step in the
+                              two-trajectory form propagates psi and chi forward together and
+                              stores no states at all).  0 = default, ceil(sqrt(longest
+                              sub-interval)); values above the longest sub-interval are clamped.
+                              Grid kinds (nonlinear: the adjoint needs every forward state): 0 =
+                              the whole forward trajectory is stored (B (Nt+1) d states, the
+                              fastest); S > 0 = states every S steps of each sub-interval plus one
+                              S-step segment per sub-problem, recomputed forward before its
+                              adjoint steps (one more forward propagation per sweep).          */
 } ism_options;
 
 typedef struct ism_plan_s* ism_plan_t;
@@ -289,7 +294,10 @@ int ism_plan_footprint(const ism_problem* prob, const ism_options* opt, size_t* 
  *   7: tiles per block of the blocked chain (1 = plain chain),
  *   8: the plan's time-step scheme (ism_scheme),
  *   9: lanes per state of the direct sweeps (0 when the plan assembles; fewer lanes with more
- *      elements each once the batch gives every SM two CTAs of that layout).
+ *      elements each once the batch gives every SM two CTAs of that layout),
+ *   10: 1 when the plan propagates on the tensor cores (dense d = 128, 256),
+ *   11: the checkpoint stride in use (ism_options.ckpt_stride after the default and the clamp are
+ *       resolved; grid kinds: 0 when the whole forward trajectory is stored).
  *   Returns -1 for a bad key. */
 long long ism_plan_info(ism_plan_t plan, int key);
 

@@ -539,6 +539,7 @@ ism::GPParams gparams(ism_plan_s* P, double* u) {
   g.tau = P->tau; g.T = P->T; g.L = P->gpL; g.xmin = P->gpxmin; g.dx = P->gpL / P->d; g.g = P->gpg; g.rho = P->rho;
   g.pot = P->gppot; g.dw = P->gpdw;
   g.jn = P->djn; g.u = u; g.psi_i = P->dpsi_i; g.psi_f = P->dpsi_f; g.traj = P->dtraj;
+  g.cks = P->cks; g.nck = P->nck; g.gck = P->dckpt; g.segb = P->dsegb;
   g.psin = P->dpsin; g.chin = P->dchin; g.grad = P->dgrad; g.Jn = P->dJn; g.err = P->derr;
   g.J = P->dJ; g.F = P->dF; g.Jhist = nullptr; g.hist_stride = 0; g.hist_k = 0;
   g.status = P->dstatus; g.count = P->dcount; g.update = 0;
@@ -673,6 +674,7 @@ int plan_build_tc(ism_plan_s* P, const ism_problem& p, bool dry, size_t* bytes_o
   if (P->L != 1) return fail(ISM_EUNSUPPORTED, "dense d = 128 and 256 support one local step per iteration");
   P->tc = true;
   P->form = 2;
+  P->cks = P->nck = 0;   // no literal sub-problems: nothing is checkpointed
   P->r2 = sizeof(float2);
   {
     Bounds bd = bounds_of(ISM_H_DENSE, d, p.H0, p.H1);
@@ -891,9 +893,24 @@ int plan_build(const ism_problem* prob, const ism_options* opt, void* cuda_strea
     int rc = ISM_OK;
     const size_t B = P->B;
 #define TRY_GP(ptr, n) if ((rc = dalloc(P, &(ptr), (n))) != ISM_OK) { free_all(P); delete P; return rc; }
-    unsigned char* dTb = nullptr;
-    TRY_GP(dTb, B * ((size_t)P->Nt + 1) * d * P->r2);
-    P->dtraj = dTb;
+    // the forward states the adjoint sweeps read: the whole trajectory, or (ckpt_stride S > 0) the
+    // states every S steps of each sub-interval plus one S-step segment per (problem, sub-interval)
+    if (opt->ckpt_stride > 0) {
+      const int nsmax = (P->Nt + P->N - 1) / P->N;
+      P->cks = opt->ckpt_stride > nsmax ? nsmax : opt->ckpt_stride;
+      P->nck = (nsmax + P->cks - 1) / P->cks;
+      unsigned char* dC = nullptr;
+      TRY_GP(dC, B * P->N * (size_t)P->nck * d * P->r2);
+      P->dckpt = dC;
+      unsigned char* dS = nullptr;
+      TRY_GP(dS, B * P->N * (size_t)P->cks * d * P->r2);
+      P->dsegb = dS;
+    } else {
+      P->cks = P->nck = 0;
+      unsigned char* dTb = nullptr;
+      TRY_GP(dTb, B * ((size_t)P->Nt + 1) * d * P->r2);
+      P->dtraj = dTb;
+    }
     TRY_GP(P->djn, (size_t)P->N + 1);
     TRY_GP(P->dpsi_i, (size_t)d);
     TRY_GP(P->dpsi_f, (size_t)d);
@@ -1202,6 +1219,7 @@ long long ism_plan_info(ism_plan_t P, int key) {
     case 8: return P->scheme;
     case 9: return P->wide ? P->ks.GW : (P->direct ? P->ks.G : 0);
     case 10: return P->tc ? 1 : 0;
+    case 11: return P->cks;
     default: return -1;
   }
 }

@@ -283,14 +283,26 @@ struct GP {
   // One forward Strang step on a = A (a_{j+1} = F^-1 e^{-i tau k^2/2} F e^{-i tau theta} a_j), with
   // the potential factor applied as the first FFT pass loads each element; `keep`, if not null,
   // receives a_j on the way.
-  __device__ void step(double u, T* keep) {
+  __device__ void step(double u, T* keep) { step_on(A, u, keep); }
+  // the same step on buf (A, or C for a recomputed segment)
+  __device__ void step_on(T* buf, double u, T* keep) {
     const R ur = (R)u, tr = (R)tau;
     const GP* self = this;
-    kinetic<false, true>(A, [self, ur, tr, keep](int m, int, T a) {
+    kinetic<false, true>(buf, [self, ur, tr, keep](int m, int, T a) {
       if (keep) keep[m] = a;
       const T e = expm1i<T, R>(-tr * self->theta(m, ur, a));
       return cadd(a, cmul(e, a));
     });
+  }
+
+  // Checkpointed trajectories: a_{c0} .. a_{c1-1} recomputed from the stored a_{c0} (ck) into seg
+  // (row i - c0), propagated in the spare buffer C with the same steps as the forward sweep that
+  // stored the checkpoint, so every recomputed state equals the one it replaces bit for bit.
+  __device__ void recompute(const T* ck, const double* ub, int c0, int c1, T* seg) {
+    for (int m = threadIdx.x; m < n; m += blockDim.x) C[m] = ck[m];
+    __syncthreads();
+    for (int i = c0; i < c1; ++i) step_on(C, ub[i], seg + (long)(i - c0) * n);
+    __syncthreads();
   }
 
   __device__ double sum(double v) {
@@ -358,7 +370,9 @@ __global__ void k_gp_forward(GPParams p) {
   s.setup(p, smem, red);
   const int b = blockIdx.x, n = p.n;
   const double* ub = p.u + (long)b * p.Nt;
-  T* traj = reinterpret_cast<T*>(p.traj) + (long)b * (p.Nt + 1) * n;
+  // the whole trajectory (cks == 0), or a_j at the checkpoints j = j_n + k cks of every sub-interval
+  T* traj = p.cks ? nullptr : reinterpret_cast<T*>(p.traj) + (long)b * (p.Nt + 1) * n;
+  T* gck = p.cks ? reinterpret_cast<T*>(p.gck) + (long)b * p.N * p.nck * n : nullptr;
   double2* psin = p.psin + (long)b * (p.N + 1) * n;
   for (int m = threadIdx.x; m < n; m += blockDim.x) s.A[m] = ld_state<R>(p.psi_i, m);
   __syncthreads();
@@ -394,7 +408,12 @@ __global__ void k_gp_forward(GPParams p) {
       __syncthreads();
     }
     if (j == p.Nt) break;
-    s.step(ub[j], traj + (long)j * n);   // stores a_j as it goes
+    T* keep = traj ? traj + (long)j * n : nullptr;   // a_j is stored as the step reads it
+    if (gck) {
+      const int o = j - p.jn[nn - 1];                // step j lies in sub-interval nn - 1
+      if (o % p.cks == 0) keep = gck + ((long)(nn - 1) * p.nck + o / p.cks) * n;
+    }
+    s.step(ub[j], keep);
   }
   if (p.count && threadIdx.x == 0) atomicAdd(p.count, (unsigned long long)p.Nt);
 }
@@ -408,7 +427,9 @@ __global__ void k_gp_adjoint(GPParams p) {
   s.setup(p, smem, red);
   const int b = blockIdx.x, n = p.n;
   const double* ub = p.u + (long)b * p.Nt;
-  const T* traj = reinterpret_cast<const T*>(p.traj) + (long)b * (p.Nt + 1) * n;
+  const T* traj = p.cks ? nullptr : reinterpret_cast<const T*>(p.traj) + (long)b * (p.Nt + 1) * n;
+  const T* gck = p.cks ? reinterpret_cast<const T*>(p.gck) + (long)b * p.N * p.nck * n : nullptr;
+  T* seg = p.cks ? reinterpret_cast<T*>(p.segb) + (long)b * p.N * p.cks * n : nullptr;
   double2* chin = p.chin + (long)b * (p.N + 1) * n;
   for (int m = threadIdx.x; m < n; m += blockDim.x) {
     s.A[m] = ld_state<R>(p.psi_f, m);
@@ -418,9 +439,20 @@ __global__ void k_gp_adjoint(GPParams p) {
   s.kinetic<true, false>(s.A);   // nu_Nt = K^H psi_f
   int nn = p.N - 1;
   T acur[8], anext[8];
-  ld_row8(acur, traj + (long)(p.Nt - 1) * n, n);
+  int c0 = p.Nt;                 // first step of the recomputed segment (checkpointed trajectories)
+  if (traj) ld_row8(acur, traj + (long)(p.Nt - 1) * n, n);
   for (int j = p.Nt - 1; j >= 0; --j) {
-    if (j > 0) ld_row8(anext, traj + (long)(j - 1) * n, n);
+    if (gck) {
+      if (j == c0 - 1) {         // the last step of the previous segment: recompute that segment
+        const int jb = p.jn[nn], k = (j - jb) / p.cks;
+        c0 = jb + k * p.cks;
+        s.recompute(gck + ((long)nn * p.nck + k) * n, ub, c0, j + 1, seg);
+        ld_row8(acur, seg + (long)(j - c0) * n, n);
+      }
+      if (j > c0) ld_row8(anext, seg + (long)(j - 1 - c0) * n, n);
+    } else if (j > 0) {
+      ld_row8(anext, traj + (long)(j - 1) * n, n);
+    }
     s.template adjoint_step<false>(acur, ub[j]);
 #pragma unroll
     for (int r = 0; r < 8; ++r) acur[r] = anext[r];
@@ -450,14 +482,20 @@ __global__ void k_gp_sub(GPParams p) {
   const int nsub = blockIdx.x, b = blockIdx.y, n = p.n;
   const int j0 = p.jn[nsub], j1 = p.jn[nsub + 1];
   double* ub = p.u + (long)b * p.Nt;
-  T* traj = reinterpret_cast<T*>(p.traj) + (long)b * (p.Nt + 1) * n;
+  T* traj = p.cks ? nullptr : reinterpret_cast<T*>(p.traj) + (long)b * (p.Nt + 1) * n;
+  T* gck = p.cks ? reinterpret_cast<T*>(p.gck) + ((long)b * p.N + nsub) * p.nck * n : nullptr;
+  T* seg = p.cks ? reinterpret_cast<T*>(p.segb) + ((long)b * p.N + nsub) * p.cks * n : nullptr;
   const double2* psin = p.psin + (long)b * (p.N + 1) * n;
   const double2* chin = p.chin + (long)b * (p.N + 1) * n;
-  // forward from psi(t_n), storing a_j for j0..j1-1
+  // forward from psi(t_n), storing a_j for j0..j1-1 (or every cks-th of them)
   for (int m = threadIdx.x; m < n; m += blockDim.x) s.A[m] = ld_state<R>(psin + (long)nsub * n, m);
   __syncthreads();
   s.kinetic<false, false>(s.A);
-  for (int j = j0; j < j1; ++j) s.step(ub[j], traj + (long)j * n);
+  for (int j = j0; j < j1; ++j) {
+    T* keep = traj ? traj + (long)j * n : nullptr;
+    if (gck && (j - j0) % p.cks == 0) keep = gck + (long)((j - j0) / p.cks) * n;
+    s.step(ub[j], keep);
+  }
   // J_n = Re<psi_n(t_{n+1})|chi(t_{n+1})>, psi_n(t_{n+1}) = K^H a_{j1}
   s.kinetic<true, false>(s.A);
   double jr = 0.0;
@@ -474,10 +512,21 @@ __global__ void k_gp_sub(GPParams p) {
   double err = 0.0;
   double* gb = p.grad + (long)b * p.Nt;
   T acur[8], anext[8];
-  ld_row8(acur, traj + (long)(j1 - 1) * n, n);
+  int c0 = j1;   // first step of the recomputed segment (checkpointed trajectories)
+  if (traj) ld_row8(acur, traj + (long)(j1 - 1) * n, n);
   for (int j = j1 - 1; j >= j0; --j) {
     const double uj = ub[j];
-    if (j > j0) ld_row8(anext, traj + (long)(j - 1) * n, n);
+    if (gck) {
+      if (j == c0 - 1) {   // entering a segment at its last step: recompute it (u not yet updated there)
+        const int k = (j - j0) / p.cks;
+        c0 = j0 + k * p.cks;
+        s.recompute(gck + (long)k * n, ub, c0, j + 1, seg);
+        ld_row8(acur, seg + (long)(j - c0) * n, n);
+      }
+      if (j > c0) ld_row8(anext, seg + (long)(j - 1 - c0) * n, n);
+    } else if (j > j0) {
+      ld_row8(anext, traj + (long)(j - 1) * n, n);
+    }
     const double gj = s.template adjoint_step<true>(acur, uj);
 #pragma unroll
     for (int r = 0; r < 8; ++r) acur[r] = anext[r];

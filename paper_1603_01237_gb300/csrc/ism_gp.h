@@ -13,7 +13,10 @@ struct GPParams {
   double* u;              // [B][Nt]
   const double2* psi_i;   // [n]
   const double2* psi_f;   // [n]
-  void* traj;             // [B][Nt+1][n] complex R: a_j = K psi_j
+  void* traj;             // cks == 0: [B][Nt+1][n] complex R: a_j = K psi_j
+  int cks, nck;           // checkpoint stride (0: the whole trajectory in traj) and checkpoints per sub-interval
+  void* gck;              // cks > 0: [B][N][nck][n] a_j at j = j_n + k cks
+  void* segb;             // cks > 0: [B][N][cks][n] one recomputed segment per (problem, sub-interval)
   double2* psin;          // [B][N+1][n] psi(t_n)
   double2* chin;          // [B][N+1][n] chi(t_n) = lambda_{j_n}
   double* grad;           // [B][Nt]

@@ -417,3 +417,18 @@ def test_complex_hermitian_dense_validated_on_the_host(lib):
     with pytest.raises(abi.IsmError) as ei:
         abi.footprint(big, precision="mixed")
     assert ei.value.status == abi.ISM_EUNSUPPORTED
+
+
+def test_grid_kind_checkpoints_size_the_plan(lib):
+    """Grid kinds: ckpt_stride 0 stores the whole forward trajectory; S > 0 stores every S-th state
+    of each sub-interval and one segment per sub-problem, so the footprint falls with S up to
+    ~sqrt(steps per sub-interval)."""
+    import workloads as W
+    from paper_1603_01237_gb300 import abi
+
+    w = W.gp_double_well(n=512, Nt=10000, N=64, steps=200)
+    f = {S: abi.footprint(w, precision="fp64", ckpt_stride=S) for S in (0, 1, 4, 13, 157)}
+    assert f[13] < f[4] < f[1] and f[13] < f[157] and f[13] < 0.25 * f[0]
+    n = C.c_size_t()
+    prob, opt, keep = abi.problem_and_options(w, precision="fp64", ckpt_stride=-1)
+    assert lib.ism_plan_footprint(C.byref(prob), C.byref(opt), C.byref(n)) == abi.ISM_EINVAL

@@ -120,3 +120,47 @@ def test_double_well_degenerate_partitions(P, N):
         u, J, _ = pl.iterate(w.u0, 2)
     assert np.max(np.abs(phi[0] - ps_o)) <= 1e-11 and np.max(np.abs(phi[1] - ch_o)) <= 1e-11
     assert np.max(np.abs(J[0] - J_o)) <= 1e-10 and np.max(np.abs(u[0] - u_o)) <= 1e-10
+
+
+@pytest.mark.parametrize("prec", ["fp64", "mixed"])
+@pytest.mark.parametrize("S", [1, 4, 13, 1000])
+def test_gp_checkpoints_change_nothing(P, prec, S):
+    """ckpt_stride S > 0 keeps the forward states every S steps of each sub-interval and recomputes
+    each S-step segment before its adjoint steps (the global adjoint sweep and the sub-problems):
+    every result equals the whole-trajectory plan's bit for bit (the recomputation repeats the same
+    steps from a stored copy of the same state).  Ragged partition (Nt = 157, N = 5: 31-32 steps,
+    the last segment of each sub-interval shorter than S); S = 1000 is clamped to one segment per
+    sub-interval."""
+    w = _dw(512, 157, 5, 1.0)
+    rng = np.random.default_rng(12)
+    ps_o, ch_o = G.intermediate_pairs(w, w.u0)
+    phi_in = np.stack([ps_o, ch_o]) * (1 + 1e-3 * rng.standard_normal((2,) + ps_o.shape))
+    out = []
+    for s in (0, S):
+        with P.Plan(w, precision=prec, rho=0.05, ckpt_stride=s) as pl:
+            assert pl.info(11) == (0 if s == 0 else min(s, 32))
+            phi = pl.intermediate_states(w.u0)[0]
+            g, Jn = pl.subinterval_grad(phi_in, w.u0)
+            u, J, E = pl.iterate(w.u0, 3)
+            gg, Jg = pl.gradient(u[0])
+        out.append((phi, g, Jn, u, J, E, gg, Jg))
+    for a, b in zip(out[0], out[1]):
+        assert np.array_equal(a, b)
+
+
+def test_gp_checkpoints_full_size_footprint_and_parity(P):
+    """The condensate benchmark's size (512 points, Nt = 10000, N = 64) with ckpt_stride 13: under a
+    quarter of the whole-trajectory plan's memory, the same iterates, and the oracle's to the mixed bar."""
+    w = W.gp_double_well(n=512, Nt=10000, N=64, steps=20000)
+    from paper_1603_01237_gb300 import abi
+
+    f0 = abi.footprint(w, precision="mixed")
+    f13 = abi.footprint(w, precision="mixed", ckpt_stride=13)
+    assert f13 < 0.25 * f0
+    u_o, J_o, _, _ = G.ism_solve(w, w.u0, 2, 0.05)
+    with P.Plan(w, precision="mixed", rho=0.05, ckpt_stride=13) as pl:
+        u, J, _ = pl.iterate(w.u0, 2)
+    with P.Plan(w, precision="mixed", rho=0.05) as pl:
+        u0_, J0_, _ = pl.iterate(w.u0, 2)
+    assert np.array_equal(u, u0_) and np.array_equal(J, J0_)
+    assert np.max(np.abs(J[0] - J_o)) <= 1e-5
