@@ -50,6 +50,7 @@ CASES = [
     ("chain10-fp64", _random_target(W.spin_chain(10, 85, T=0.5, Nt=100, N=5, u_amp=1.0), 15), "fp64"),
     ("chain7-obs-fp64", _magnetisation(W.spin_chain(7, 86, T=1.0, Nt=150, N=5, u_amp=1.0)), "fp64"),
     ("chain8-obs-mixed", _magnetisation(W.spin_chain(8, 87, T=1.0, Nt=150, N=5, u_amp=1.0)), "mixed"),
+    ("chain10-obs-mixed", _magnetisation(W.spin_chain(10, 90, T=0.5, Nt=120, N=5, u_amp=1.0)), "mixed"),
 ]
 IDS = [c[0] for c in CASES]
 TOL = {"fp64": dict(phi=1e-11, grad=1e-10, J=1e-11), "mixed": dict(phi=2e-5, grad=1e-4, J=1e-6)}
@@ -127,3 +128,4 @@ def test_ising1024_mixed_sampled_full_length(P):
         g, _ = pl.subinterval_grad(phi_o, w.u0)
     assert np.max(np.abs(phi - phi_o)) <= 2e-5
     assert rel_l2(g[0], g_o) <= 1e-4
+

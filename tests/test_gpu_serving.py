@@ -65,7 +65,9 @@ def test_results_in_the_mix_equal_results_alone(P):
             time.sleep(rng.exponential(0.005))   # arrivals while earlier requests run
         got = [srv.result(i) for i in ids]
         st = srv.stats()
-    assert st["groups"] >= 1 and st["single"] >= 4   # shared plans and plans of their own both ran
+    # the FP64, dense and grid requests run on plans of their own; the mixed structured ones fall in
+    # five groups (kind, d, N, objective), each opening at least one shared plan
+    assert st["single"] == 3 and st["groups"] >= 5, st
     for (w, prec, iters), (u, J, t) in zip(mix, got):
         ua, Ja = _alone(P, w, prec, iters)
         assert np.array_equal(u, ua), w.name
