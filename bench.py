@@ -170,8 +170,8 @@ def kernel_source_hash(files=KERNEL_SOURCES) -> str:
 # problems, from a one-pass ncu capture of the default step (4864 rotor problems: k_gsweep in the wide
 # lane layout); reported only while the kernel sources hash to the captured build.
 TRAFFIC_PER_PROBLEM = {
-    ("k_gsweep", "rotor41"): {"bytes_per_problem": (1195000064 + 807092224) / 4864, "source_hash": "e062c45a59f49f5e"},
-    ("k_subfwd", "rotor41"): {"bytes_per_problem": (2212323584 + 2293336320) / 4864, "source_hash": "e062c45a59f49f5e"},
+    ("k_gsweep", "rotor41"): {"bytes_per_problem": (1194749184 + 807319808) / 4864, "source_hash": "e17a8480c715973d"},
+    ("k_subfwd", "rotor41"): {"bytes_per_problem": (2207851520 + 2292089088) / 4864, "source_hash": "e17a8480c715973d"},
 }
 
 

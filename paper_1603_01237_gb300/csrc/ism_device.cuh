@@ -166,6 +166,71 @@ __device__ void cheb_params(Cheb<R>& ch, const double* ctab, double tau, double 
   if (lane == 1) split2<R>(a, ch.a1h, ch.a1l);   // a_1 = 2 J_1 (lane 1 holds it)
 }
 
+// cheb_params computed by one thread instead of a warp: the same operations for every term k, in the
+// same order, so the same bits.  Terms are evaluated from k = 0 until the bound |J_k(x)| <= (x/2)^k / k!
+// puts this and every later a_k below tol / 2 (the bound decreases once k > x/2): those carry zero
+// anyway, so a sub-interval costs its own series length in FP64 work, not KMAX terms.  sa: KMAX
+// doubles of scratch (shared memory).
+template <typename R>
+__device__ void cheb_params_1(Cheb<R>& ch, double* sa, const double* ctab, double tau, double c0, double r0,
+                              double h1n, double umax, double tol, double2 phase, int* status) {
+  const double rad = (r0 + umax * h1n) * (1.0 + 1e-6) + 1e-12;
+  const double x = tau * rad;
+  int S = x < XMAX * SMAX ? (int)ceil(x / XMAX) : SMAX + 1;
+  if (S < 1) S = 1;
+  if (S > SMAX) {
+    atomicOr(status, ST_SPECTRUM);
+    S = SMAX;
+  }
+  const double xs = x / (double)S;
+  const double y = -0.25 * xs * xs, h = 0.5 * xs;
+  int M = 1;
+  {
+    const float ay = (float)fabs(y);
+    float t = 1.f;
+    while (M < BESSEL_M) {
+      t *= ay / (float)(M * M);
+      if (t < 1e-19f) break;
+      ++M;
+    }
+  }
+  int kneed = 0;
+  for (int k = 0; k < KMAX; ++k) {
+    const double* c = ctab + k * (BESSEL_M + 1);
+    double acc = c[M];
+    for (int m = M - 1; m >= 0; --m) acc = fma(acc, y, c[m]);
+    double pw = 1.0, base = h;   // h^k by squaring
+    for (int e = k; e; e >>= 1) {
+      if (e & 1) pw *= base;
+      base *= base;
+    }
+    const double a = acc * pw * (k == 0 ? 1.0 : 2.0);
+    sa[k] = a;
+    if (fabs(a) >= tol) kneed = k + 1;
+    if (k >= 1 && (double)k > h && 2.0 * pw * c[0] < 0.5 * tol) break;   // c[0] = 1/k!
+  }
+  if (kneed >= KMAX) atomicOr(status, ST_KOVERFLOW);
+  const int K2 = kneed < 2 ? 2 : kneed;
+  for (int k = 0; k < KMAX; ++k) {
+    const double sg = ((k >> 1) & 1) ? -1.0 : 1.0;
+    split2<R>(k < K2 ? sg * sa[k] : 0.0, ch.cf[k], ch.cl[k]);
+  }
+  double t = ctab[M];
+  for (int m = M - 1; m >= 1; --m) t = fma(t, y, ctab[m]);
+  const double j0m1 = t * y;
+  split2<R>(1.0 + j0m1, ch.a0h, ch.a0l);
+  split2<R>(j0m1, ch.c0h, ch.c0l);
+  split2<R>(sa[1], ch.a1h, ch.a1l);
+  ch.c = (R)c0;
+  ch.inv_rad = (R)(1.0 / rad);
+  ch.cd = c0;
+  ch.s2d = 2.0 / rad;
+  ch.cph = phase.x;
+  ch.sph = phase.y;
+  ch.K = K2;
+  ch.S = S;
+}
+
 // Crank-Nicolson parameters of one sub-interval (one thread): K Jacobi iterations per linear solve,
 // with rho = (tau/2)(off0 + umax off1) (off0, off1: largest off-diagonal absolute row sums of H0 and
 // H1) the contraction of each iteration, so that rho^K <= tol (at most CN_KMAX).  rho >= 1/2 is flagged

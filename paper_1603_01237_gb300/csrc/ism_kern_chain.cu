@@ -91,9 +91,17 @@ cudaError_t launch_phi(int prec, const ChainParams& p, cudaStream_t st) {
 }
 
 cudaError_t launch_cheb_prep(int prec, const KParams& p, cudaStream_t st) {
-  if (prec == 0) k_cheb_prep<double><<<dim3(p.N, p.B), 32, 0, st>>>(p);
-  else if (p.het) k_cheb_prep<float, true><<<dim3(p.N, p.B), 32, 0, st>>>(p);
-  else k_cheb_prep<float><<<dim3(p.N, p.B), 32, 0, st>>>(p);
+  const long pairs = (long)p.B * p.N;
+  if (pairs <= CHEB_WARP_PAIRS) {   // few pairs: one warp each, lowest latency
+    if (prec == 0) k_cheb_prep_w<double><<<dim3(p.N, p.B), 32, 0, st>>>(p);
+    else if (p.het) k_cheb_prep_w<float, true><<<dim3(p.N, p.B), 32, 0, st>>>(p);
+    else k_cheb_prep_w<float><<<dim3(p.N, p.B), 32, 0, st>>>(p);
+    return cudaGetLastError();
+  }
+  const unsigned grid = (unsigned)((pairs + CHEB_PAIRS - 1) / CHEB_PAIRS);
+  if (prec == 0) k_cheb_prep<double><<<grid, 128, 0, st>>>(p);
+  else if (p.het) k_cheb_prep<float, true><<<grid, 128, 0, st>>>(p);
+  else k_cheb_prep<float><<<grid, 128, 0, st>>>(p);
   return cudaGetLastError();
 }
 

@@ -712,9 +712,13 @@ __device__ inline double block_sum(double v, double* red) {
 }
 
 // ---------------------------------------------------------------------------- k_cheb_prep
-// One warp per (problem, n): the bound max|u| on the sub-interval and the propagator parameters.
+// Per (problem, n): the bound max|u| on the sub-interval, the penalty sum, the FP32 controls and the
+// propagator parameters.  Two layouts with the same arithmetic (the same bits): k_cheb_prep_w, one
+// warp per pair with lane k evaluating the Bessel series of term k, has the shortest latency for few
+// pairs; k_cheb_prep, one warp per pair for the controls and one thread per pair for the parameters,
+// does only the terms a sub-interval needs, so for many pairs it is not bound by the FP64 rate.
 template <typename R, bool HET = false>
-__global__ void __launch_bounds__(32) k_cheb_prep(KParams p) {
+__global__ void __launch_bounds__(32) k_cheb_prep_w(KParams p) {
   const int n = blockIdx.x, b = blockIdx.y, lane = threadIdx.x;
   const RowView rv = row_view<HET>(p, b);
   const int j0 = rv.jn[n], j1 = rv.jn[n + 1];
@@ -743,6 +747,63 @@ __global__ void __launch_bounds__(32) k_cheb_prep(KParams p) {
   const int* s = reinterpret_cast<const int*>(&ch);
   int* d = reinterpret_cast<int*>(const_cast<void*>(p.cheb)) + ((long)b * p.N + n) * (sizeof(Cheb<R>) / sizeof(int));
   for (int i = lane; i < (int)(sizeof(Cheb<R>) / sizeof(int)); i += 32) d[i] = s[i];
+}
+
+// (problem, sub-interval) pairs per block of k_cheb_prep; up to CHEB_WARP_PAIRS pairs per launch the
+// warp-per-pair layout runs instead
+constexpr int CHEB_PAIRS = 32;
+constexpr long CHEB_WARP_PAIRS = 8192;
+
+template <typename R, bool HET = false>
+__global__ void __launch_bounds__(128) k_cheb_prep(KParams p) {
+  __shared__ Cheb<R> chs[CHEB_PAIRS];
+  __shared__ double sa[CHEB_PAIRS][KMAX];
+  __shared__ float sum_[CHEB_PAIRS];
+  const long total = (long)p.B * p.N, i0 = (long)blockIdx.x * CHEB_PAIRS;
+  const int w = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  // (1) one warp per pair: the |u| bound, the penalty sum and the FP32 controls (coalesced reads)
+  for (int q = w; q < CHEB_PAIRS; q += 4) {
+    const long i = i0 + q;
+    if (i >= total) break;   // warp-uniform
+    const int b = (int)(i / p.N), n = (int)(i % p.N);
+    const RowView rv = row_view<HET>(p, b);
+    const int j0 = rv.jn[n], j1 = rv.jn[n + 1];
+    const double* ub = p.u + (long)b * rv.us;
+    float um = 0.f;   // |u| bound; the margin in the parameters covers its FP32 rounding
+    double pen = 0.0;
+    float* ufb = p.uf ? p.uf + (long)b * rv.us : nullptr;
+    for (int j = j0 + lane; j < j1; j += 32) {
+      const double uj = ub[j];
+      if (ufb) ufb[j] = (float)uj;
+      um = fmaxf(um, fabsf((float)uj));
+      if (rv.alpha) pen += rv.alpha[j] * uj * uj;
+    }
+    for (int m = 16; m >= 1; m >>= 1) {
+      um = fmaxf(um, __shfl_xor_sync(0xffffffffu, um, m));
+      pen += __shfl_xor_sync(0xffffffffu, pen, m);
+    }
+    if (lane == 0) {
+      if (p.pen) p.pen[i] = pen;
+      sum_[q] = um;
+    }
+  }
+  __syncthreads();
+  // (2) one thread per pair: the propagator parameters (FP64 work per pair, not per lane)
+  if (w == 0 && i0 + lane < total) {
+    const long i = i0 + lane;
+    const int b = (int)(i / p.N), n = (int)(i % p.N);
+    const RowView rv = row_view<HET>(p, b);
+    if (p.scheme == 1) cn_params<R>(chs[lane], rv.tau, rv.r0, rv.h1n, (double)sum_[lane], p.tol, p.status);
+    else cheb_params_1<R>(chs[lane], sa[lane], p.ctab, rv.tau, rv.c0, rv.r0, rv.h1n, (double)sum_[lane], p.tol,
+                          rv.phase[n], p.status);
+  }
+  __syncthreads();
+  // (3) the pairs' parameters out, as consecutive words
+  constexpr int words = sizeof(Cheb<R>) / sizeof(int);
+  const long np = total - i0 < CHEB_PAIRS ? total - i0 : CHEB_PAIRS;
+  const int* src = reinterpret_cast<const int*>(chs);
+  int* dst = reinterpret_cast<int*>(const_cast<void*>(p.cheb)) + i0 * words;
+  for (long x = threadIdx.x; x < np * words; x += blockDim.x) dst[x] = src[x];
 }
 
 // ---------------------------------------------------------------------- k_sweeps2 / k_gradpass

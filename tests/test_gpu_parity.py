@@ -150,6 +150,21 @@ def test_batch_equals_singles(P):
         assert np.array_equal(Jb[b], J1[0])
 
 
+@pytest.mark.parametrize("prec", ["mixed", "fp64"])
+def test_parameter_layouts_agree(P, prec):
+    """The propagator parameters of few (problem, sub-interval) pairs come from one warp per pair, of
+    many from one thread per pair: the same arithmetic, so a problem's iterates are the same bits in
+    a one-problem plan and in a batch of 65 x 128 pairs (both assemble the sub-interval propagators)."""
+    w = W.config("rotor41", Nt=1280, N=128)
+    rng = np.random.default_rng(6)
+    U = np.stack([w.u0] + [rng.uniform(-1, 1, w.Nt) for _ in range(64)])
+    with P.Plan(w, precision=prec, batch=65, step1=1) as pl:
+        ub, Jb, Eb = pl.iterate(U, 2)
+    with P.Plan(w, precision=prec, step1=1) as pl:
+        u1, J1, E1 = pl.iterate(w.u0, 2)
+    assert np.array_equal(ub[0], u1[0]) and np.array_equal(Jb[0], J1[0]) and np.array_equal(Eb[0], E1[0])
+
+
 def test_local_iterations(P):
     w = W.random_dense(6, 71, T=2.0, Nt=120, N=4)
     u_o, J_o, _, _ = O.ism_solve(w, w.u0, 2, 0.2, L=3)
