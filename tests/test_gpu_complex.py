@@ -140,3 +140,14 @@ def test_noalloc_and_server_take_the_imaginary_parts(P):
     with P.Server(slots=1, hbm_budget_bytes=4 << 30) as srv:
         u2, J2, _ = srv.result(srv.submit(w, iters=3, precision="fp64"))
     assert np.array_equal(u2, u1) and np.array_equal(J2, J1)
+
+
+def test_checkpoint_stride_changes_nothing(P):
+    w = CASES[4][1]
+    phi_o = O.intermediate_states(w, w.u0)
+    res = []
+    for S in (1, 6, 0, 10 ** 6):
+        with P.Plan(w, precision="mixed", ckpt_stride=S) as pl:
+            res.append(pl.subinterval_grad(phi_o, w.u0))
+    for g, Jn in res[1:]:
+        assert np.array_equal(g, res[0][0]) and np.array_equal(Jn, res[0][1])

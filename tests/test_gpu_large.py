@@ -129,3 +129,19 @@ def test_ising1024_mixed_sampled_full_length(P):
     assert np.max(np.abs(phi - phi_o)) <= 2e-5
     assert rel_l2(g[0], g_o) <= 1e-4
 
+
+
+@pytest.mark.parametrize("prec", ["fp64", "mixed"])
+def test_large_checkpoint_stride_changes_nothing(P, prec):
+    """CTA-wide literal sub-problems (d = 512, ragged): the stored states every S steps and the
+    recomputed segments give the same gradient and J_n bit for bit for every stride, and the oracle's."""
+    w = _random_target(W.spin_chain(9, 92, T=1.0, Nt=203, N=7, u_amp=1.0), 22)
+    phi_o = O.intermediate_states(w, w.u0)
+    g_o, _ = O.subinterval_all(w, phi_o, w.u0)
+    res = []
+    for S in (1, 5, 0, 10 ** 6):
+        with P.Plan(w, precision=prec, ckpt_stride=S) as pl:
+            res.append(pl.subinterval_grad(phi_o, w.u0))
+    for g, Jn in res[1:]:
+        assert np.array_equal(g, res[0][0]) and np.array_equal(Jn, res[0][1])
+    assert rel_l2(res[0][0][0], g_o) <= TOL[prec]["grad"]

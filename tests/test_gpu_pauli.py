@@ -119,3 +119,19 @@ def test_pauli_most_controls_and_one_step_sub_intervals(P, prec):
     assert rel(g[0], g_o) <= TOL[prec][1]
     assert np.max(np.abs(J[0] - J_o)) <= (1e-9 if prec == "fp64" else 1e-5)
     assert rel(u[0] - w.u0, u_o - w.u0) <= (1e-9 if prec == "fp64" else 1e-4)
+
+
+@pytest.mark.parametrize("prec", ["fp64", "mixed"])
+def test_pauli_checkpoint_stride_changes_nothing(P, prec):
+    """Several controls, literal sub-problems: every stride gives the same gradients of all controls
+    and J_n bit for bit."""
+    w = CASES[1][1]
+    res = []
+    phi_o = M.intermediate_states(w, w.u0)
+    for S in (1, 4, 0, 10 ** 6):
+        with P.Plan(w, precision=prec, ckpt_stride=S) as pl:
+            res.append(pl.subinterval_grad(phi_o, w.u0))
+    for g, Jn in res[1:]:
+        assert np.array_equal(g, res[0][0]) and np.array_equal(Jn, res[0][1])
+    g_o, _ = M.subinterval_all(w, phi_o, w.u0)
+    assert rel(res[0][0][0], g_o) <= TOL[prec][1]
