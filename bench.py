@@ -170,8 +170,8 @@ def kernel_source_hash(files=KERNEL_SOURCES) -> str:
 # problems, from a one-pass ncu capture of the default step (4864 rotor problems: k_gsweep in the wide
 # lane layout); reported only while the kernel sources hash to the captured build.
 TRAFFIC_PER_PROBLEM = {
-    ("k_gsweep", "rotor41"): {"bytes_per_problem": (1194749184 + 807319808) / 4864, "source_hash": "e17a8480c715973d"},
-    ("k_subfwd", "rotor41"): {"bytes_per_problem": (2207851520 + 2292089088) / 4864, "source_hash": "e17a8480c715973d"},
+    ("k_gsweep", "rotor41"): {"bytes_per_problem": (1193538304 + 806773248) / 4864, "source_hash": "73cb90b7a0d46563"},
+    ("k_subfwd", "rotor41"): {"bytes_per_problem": (2211457792 + 2292974592) / 4864, "source_hash": "73cb90b7a0d46563"},
 }
 
 

@@ -1673,14 +1673,23 @@ __global__ void __launch_bounds__(128) k_phi(ChainParams p) {
     const double sc = n == N ? 1.0 : s_chi;
     const double2 w = ab[n];
     double2* phi = p.phi + ((long)b * (N + 1) + n) * d;
-    for (int e = lane; e < d; e += 32) {
-      double2 ps = load_ps(n, e), cs = load_cs(n, e);
+    auto put = [&](int e, double2 ps, double2 cs) {
       ps.x *= sp; ps.y *= sp;
       cs.x *= sc; cs.y *= sc;
       psin[(long)n * d + e] = ps;   // psi(t_0) = psi_i too: the chain path has not written it
       if (n < N) chin[(long)n * d + e] = cs;
       phi[e] = n == 0 ? ps : (n == N ? cs : make_double2(w.x * ps.x + w.y * cs.x, w.x * ps.y + w.y * cs.y));
+    };
+    if (d <= 64) {   // both elements of each lane loaded before any store: one round trip, not two
+      const int e0 = lane, e1 = lane + 32;
+      double2 ps0 = make_double2(0.0, 0.0), cs0 = ps0, ps1 = ps0, cs1 = ps0;
+      if (e0 < d) { ps0 = load_ps(n, e0); cs0 = load_cs(n, e0); }
+      if (e1 < d) { ps1 = load_ps(n, e1); cs1 = load_cs(n, e1); }
+      if (e0 < d) put(e0, ps0, cs0);
+      if (e1 < d) put(e1, ps1, cs1);
+      return;
     }
+    for (int e = lane; e < d; e += 32) put(e, load_ps(n, e), load_cs(n, e));
     return;
   }
   // J and F: <psi(T)|chi(T)> is the overlap with psi_f or <psi|O|psi>, with psi(T) renormalised (the
