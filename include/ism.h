@@ -315,15 +315,15 @@ long long ism_plan_info(ism_plan_t plan, int key);
  *   phi, u:    [batch][N+1][2d] and [batch][Nt] inputs, DEVICE memory of the current GPU.
  *   grad, Jn:  [batch][Nt] and [batch][N] (Jn may be NULL) outputs, DEVICE memory of the current GPU.
  *   cuda_stream: the stream the work is ordered on.  The call synchronises that stream and reads the
- *   status word back before it returns, so it must not be called while the stream is being captured.
- *   The first call on a device looks up the array's device address (cudaGetSymbolAddress) with that
- *   device current.  All calls share the array and it keeps the last call's contents (the status word
- *   is cleared on entry); calls whose work overlaps on the GPU race on it.  A problem needing more
- *   scratch than the array holds is rejected with ISM_EINVAL and a message giving both sizes; host
- *   pointers, or device memory of another GPU, for phi, u, grad or Jn give ISM_EINVAL; NaN or Inf in
- *   u or phi gives ISM_ENONFINITE.  Covers the dense, tridiagonal and bit-flip kinds with d <= 64
- *   (the Chebyshev step); other kinds and larger d give ISM_EUNSUPPORTED.  Other errors as
- *   ism_subinterval_grad.
+ *   status word back before it returns.  The first call on a device does a one-time set-up: it looks
+ *   up the array's device address (cudaGetSymbolAddress) with that device current; make that first
+ *   call before any stream capture.  All calls share the array and it keeps the last call's contents
+ *   (the status word is cleared on entry); calls whose work overlaps on the GPU race on it.  A problem
+ *   needing more scratch than the array holds is rejected with ISM_EINVAL and a message giving both
+ *   sizes; host pointers, or device memory of another GPU, for phi, u, grad or Jn give ISM_EINVAL; NaN
+ *   or Inf in u or phi gives ISM_ENONFINITE.  Covers the dense (real or complex Hermitian),
+ *   tridiagonal and bit-flip kinds with d <= 64 (the Chebyshev step); other kinds and larger d give
+ *   ISM_EUNSUPPORTED.  Other errors as ism_subinterval_grad.
  */
 #define ISM_NOALLOC_SCRATCH_BYTES (32u << 20)
 int ism_subinterval_grad_noalloc(const ism_problem* prob, int precision, const double* phi, const double* u,
