@@ -48,7 +48,7 @@ SAMPLE_DIV = {"dense256": 8, "rotor41": 8, "spin16": 1, "ising1024": 64, "gp512"
 # independent solves per launch: multiples of the 152 SMs (rotor41: two CTAs of 16 problems per SM in
 # the wide lane layout of the direct sweeps; spin16: two CTAs of 8; one CTA per SM and direction for
 # the CTA-wide kinds; two 152-CTA waves for the grid model)
-BATCH_DEFAULT = {"dense256": 2432, "rotor41": 4864, "spin16": 2432, "ising1024": 152, "gp512": 760, "gp512dw": 760, "spin5": 152}
+BATCH_DEFAULT = {"dense256": 2432, "rotor41": 4864, "spin16": 2432, "ising1024": 152, "gp512": 1520, "gp512dw": 1520, "spin5": 152}
 SOLVE_ITERS = {"dense256": 20, "rotor41": 50, "spin16": 20, "ising1024": 20, "gp512": 20, "gp512dw": 20, "spin5": 20}   # oracle sample = Nt/div steps, N/div sub-intervals
 FP32_LANES_PER_SM = 128
 SM_MAX_MHZ_GB300 = 2070.0   # fallback when nvidia-smi cannot be read

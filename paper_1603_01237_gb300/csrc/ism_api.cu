@@ -144,6 +144,7 @@ struct ism_plan_s {
   double2* dchin = nullptr;
   double2* dphi = nullptr;
   void* dtraj = nullptr;
+  void* dgptab = nullptr;           // grid kinds: twiddle, kinetic-factor and grid tables
   void* dtraj2 = nullptr;
   bool use_sw2 = false;             // first local steps by the concurrent two-trajectory sweeps
   void* dzs = nullptr;              // [B][Nt+N] per-step overlaps of the sub-interval sweeps (R2)
@@ -539,7 +540,7 @@ ism::GPParams gparams(ism_plan_s* P, double* u) {
   g.tau = P->tau; g.T = P->T; g.L = P->gpL; g.xmin = P->gpxmin; g.dx = P->gpL / P->d; g.g = P->gpg; g.rho = P->rho;
   g.pot = P->gppot; g.dw = P->gpdw;
   g.jn = P->djn; g.u = u; g.psi_i = P->dpsi_i; g.psi_f = P->dpsi_f; g.traj = P->dtraj;
-  g.cks = P->cks; g.nck = P->nck; g.gck = P->dckpt; g.segb = P->dsegb;
+  g.cks = P->cks; g.nck = P->nck; g.gck = P->dckpt; g.segb = P->dsegb; g.tab = P->dgptab;
   g.psin = P->dpsin; g.chin = P->dchin; g.grad = P->dgrad; g.Jn = P->dJn; g.err = P->derr;
   g.J = P->dJ; g.F = P->dF; g.Jhist = nullptr; g.hist_stride = 0; g.hist_k = 0;
   g.status = P->dstatus; g.count = P->dcount; g.update = 0;
@@ -924,6 +925,11 @@ int plan_build(const ism_problem* prob, const ism_options* opt, void* cuda_strea
     TRY_GP(P->dF, B);
     TRY_GP(P->dstatus, 1);
     TRY_GP(P->dcount, 7);
+    {
+      unsigned char* dT = nullptr;
+      TRY_GP(dT, ism::gp_table_bytes(P->prec == ISM_FP64 ? 0 : 1, d));
+      P->dgptab = dT;
+    }
 #undef TRY_GP
     if (dry) {
       *bytes_out = P->bytes;
@@ -935,6 +941,10 @@ int plan_build(const ism_problem* prob, const ism_options* opt, void* cuda_strea
     if (e == cudaSuccess) e = cudaMemcpyAsync(P->dpsi_f, p.psi_f, 2 * sizeof(double) * d, cudaMemcpyHostToDevice, P->st);
     if (e == cudaSuccess) e = cudaMemsetAsync(P->dstatus, 0, sizeof(int), P->st);
     if (e == cudaSuccess) e = cudaMemsetAsync(P->dcount, 0, 7 * sizeof(unsigned long long), P->st);
+    if (e == cudaSuccess) {   // the plan's tables (n, L, tau, x_min are fixed for its life)
+      ism::GPParams g = gparams(P, P->du);
+      e = ism::launch_gp_tables(P->prec == ISM_FP64 ? 0 : 1, g, P->st);
+    }
     if (e == cudaSuccess) e = cudaStreamSynchronize(P->st);   // the host arrays above are local
     if (e != cudaSuccess) {
       free_all(P);

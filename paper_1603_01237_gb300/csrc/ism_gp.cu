@@ -160,12 +160,64 @@ __device__ typename C2<R>::T* fft8(typename C2<R>::T* x, typename C2<R>::T* y, c
   return x;
 }
 
+// The per-plan tables of the grid model (n, L, tau and x_min fixed by the plan): twiddles
+// exp(-2 pi i m / n), the kinetic factors exp(-i tau k^2/2) - 1 and exp(-i tau k^2/4), each as hi + lo,
+// and the grid points x_m as hi + lo.  Layout in units of complex R: W, D2m1, DH, Wl, D2l, DHl
+// (n each), then X, Xl (n reals each): 7 n complex R.  Computed once per plan (k_gp_tables) and read
+// by every CTA through the L1 cache, so that a CTA's shared memory holds only its three state buffers
+// and more CTAs share an SM.
+template <typename R>
+__device__ void gp_fill_tables(const GPParams& p, typename C2<R>::T* tab) {
+  using T = typename C2<R>::T;
+  const int n = p.n;
+  const double tau = p.tau;
+  T *W = tab, *D2m1 = tab + n, *DH = tab + 2 * n, *Wl = tab + 3 * n, *D2l = tab + 4 * n, *DHl = tab + 5 * n;
+  R* X = reinterpret_cast<R*>(tab + 6 * n);
+  R* Xl = X + n;
+  for (int m = blockIdx.x * blockDim.x + threadIdx.x; m < n; m += gridDim.x * blockDim.x) {
+    double s, co;
+    sincospi(-2.0 * (double)m / (double)n, &s, &co);
+    T w, wl;
+    w.x = (R)co;
+    w.y = (R)s;
+    wl.x = (R)(co - (double)w.x);
+    wl.y = (R)(s - (double)w.y);
+    W[m] = w;
+    Wl[m] = wl;
+    const int kk = m < n / 2 ? m : m - n;   // frequency ordering of an unshifted FFT
+    const double k = 2.0 * M_PI * (double)kk / p.L;
+    const double ph2 = -0.5 * tau * k * k, ph4 = -0.25 * tau * k * k;
+    const double h = sin(0.5 * ph2);
+    T d, dl;
+    const double dx_ = -2.0 * h * h, dy_ = sin(ph2);
+    d.x = (R)dx_;
+    d.y = (R)dy_;
+    dl.x = (R)(dx_ - (double)d.x);
+    dl.y = (R)(dy_ - (double)d.y);
+    D2m1[m] = d;
+    D2l[m] = dl;
+    double s4, c4;
+    sincos(ph4, &s4, &c4);
+    T e, el;
+    e.x = (R)c4;
+    e.y = (R)s4;
+    el.x = (R)(c4 - (double)e.x);
+    el.y = (R)(s4 - (double)e.y);
+    DH[m] = e;
+    DHl[m] = el;
+    const double xm = p.xmin + m * p.dx;
+    X[m] = (R)xm;
+    Xl[m] = (R)(xm - (double)X[m]);
+  }
+}
+
 template <typename R>
 struct GP {
   using T = typename C2<R>::T;
-  T *A, *B, *C, *W, *D2m1, *DH;   // state, scratch, spare, twiddles, exp(-i tau k^2/2)-1, exp(-i tau k^2/4)
-  T *Wl, *D2l, *DHl;              // low parts of the three tables (zero in FP64)
-  R *X, *Xl;                      // grid points x_m as hi + lo
+  T *A, *B, *C;                   // state, scratch, spare (shared memory)
+  const T *W, *D2m1, *DH;         // twiddles, exp(-i tau k^2/2)-1, exp(-i tau k^2/4) (per-plan table)
+  const T *Wl, *D2l, *DHl;        // low parts of the three tables (zero in FP64)
+  const R *X, *Xl;                // grid points x_m as hi + lo
   int n;
   double dx, tau, g, xmin;
   int pot;            // 0 harmonic, 1 double well
@@ -174,17 +226,18 @@ struct GP {
 
   __device__ void setup(const GPParams& p, unsigned char* smem, double* red_) {
     T* base = reinterpret_cast<T*>(smem);
+    const T* tab = reinterpret_cast<const T*>(p.tab);
     n = p.n;
     A = base;
     B = base + n;
     C = base + 2 * n;
-    W = base + 3 * n;
-    D2m1 = base + 4 * n;
-    DH = base + 5 * n;
-    Wl = base + 6 * n;
-    D2l = base + 7 * n;
-    DHl = base + 8 * n;
-    X = reinterpret_cast<R*>(base + 9 * n);
+    W = tab;
+    D2m1 = tab + n;
+    DH = tab + 2 * n;
+    Wl = tab + 3 * n;
+    D2l = tab + 4 * n;
+    DHl = tab + 5 * n;
+    X = reinterpret_cast<const R*>(tab + 6 * n);
     Xl = X + n;
     dx = p.dx;
     tau = p.tau;
@@ -195,42 +248,6 @@ struct GP {
     dq = (R)(0.25 * p.dw);
     d28 = (R)(0.125 * p.dw * p.dw);
     red = red_;
-    for (int m = threadIdx.x; m < n; m += blockDim.x) {
-      double s, co;
-      sincospi(-2.0 * (double)m / (double)n, &s, &co);
-      T w, wl;
-      w.x = (R)co;
-      w.y = (R)s;
-      wl.x = (R)(co - (double)w.x);
-      wl.y = (R)(s - (double)w.y);
-      W[m] = w;
-      Wl[m] = wl;
-      const int kk = m < n / 2 ? m : m - n;   // frequency ordering of an unshifted FFT
-      const double k = 2.0 * M_PI * (double)kk / p.L;
-      const double ph2 = -0.5 * tau * k * k, ph4 = -0.25 * tau * k * k;
-      const double h = sin(0.5 * ph2);
-      T d, dl;
-      const double dx_ = -2.0 * h * h, dy_ = sin(ph2);
-      d.x = (R)dx_;
-      d.y = (R)dy_;
-      dl.x = (R)(dx_ - (double)d.x);
-      dl.y = (R)(dy_ - (double)d.y);
-      D2m1[m] = d;
-      D2l[m] = dl;
-      double s4, c4;
-      sincos(ph4, &s4, &c4);
-      T e, el;
-      e.x = (R)c4;
-      e.y = (R)s4;
-      el.x = (R)(c4 - (double)e.x);
-      el.y = (R)(s4 - (double)e.y);
-      DH[m] = e;
-      DHl[m] = el;
-      const double xm = p.xmin + m * p.dx;
-      X[m] = (R)xm;
-      Xl[m] = (R)(xm - (double)X[m]);
-    }
-    __syncthreads();
   }
 
   // buf <- F^-1 diag(f) F pre(buf) (f = full-step factor, or half-step; conjugated for the adjoint).
@@ -544,7 +561,12 @@ __global__ void k_gp_sub(GPParams p) {
   }
 }
 
-template <typename R> size_t gp_smem(int n) { return 10 * (size_t)n * sizeof(typename C2<R>::T); }
+template <typename R> size_t gp_smem(int n) { return 3 * (size_t)n * sizeof(typename C2<R>::T); }
+
+template <typename R>
+__global__ void k_gp_tables(GPParams p) {
+  gp_fill_tables<R>(p, static_cast<typename C2<R>::T*>(const_cast<void*>(p.tab)));
+}
 int gp_threads(int n) { return n / 8 < 32 ? 32 : n / 8; }
 
 template <typename R, class K>
@@ -568,6 +590,15 @@ cudaError_t launch_gp_adjoint(int prec, const GPParams& p, cudaStream_t st) {
   return prec == 0 ? launch<double>(k_gp_adjoint<double>, p, dim3(p.B), st)
                    : launch<float>(k_gp_adjoint<float>, p, dim3(p.B), st);
 }
+size_t gp_table_bytes(int prec, int n) { return 7 * (size_t)n * (prec == 0 ? sizeof(double2) : sizeof(float2)); }
+
+cudaError_t launch_gp_tables(int prec, const GPParams& p, cudaStream_t st) {
+  const unsigned blocks = (unsigned)((p.n + 127) / 128);
+  if (prec == 0) k_gp_tables<double><<<blocks, 128, 0, st>>>(p);
+  else k_gp_tables<float><<<blocks, 128, 0, st>>>(p);
+  return cudaGetLastError();
+}
+
 cudaError_t launch_gp_sub(int prec, const GPParams& p, cudaStream_t st) {
   return prec == 0 ? launch<double>(k_gp_sub<double>, p, dim3(p.N, p.B), st)
                    : launch<float>(k_gp_sub<float>, p, dim3(p.N, p.B), st);

@@ -29,10 +29,14 @@ struct GPParams {
   int* status;
   unsigned long long* count;   // [2]: FFT pairs (sequential sweeps), FFT pairs (sub-interval sweeps)
   int update;
+  const void* tab;        // [7n] complex R: the plan's twiddle, kinetic-factor and grid tables (k_gp_tables)
 };
 
-// prec: 0 FP64, 1 FP32.  n must be 64 or 512 (radix-8 Stockham, tables in shared memory).
+// prec: 0 FP64, 1 FP32.  n must be 64 or 512 (radix-8 Stockham; the states in shared memory, the
+// per-plan tables in global memory, filled once by launch_gp_tables before the first sweep).
 bool gp_supported(int n);
+size_t gp_table_bytes(int prec, int n);
+cudaError_t launch_gp_tables(int prec, const GPParams& p, cudaStream_t st);   // fills p.tab (once per plan)
 cudaError_t launch_gp_forward(int prec, const GPParams& p, cudaStream_t st);
 cudaError_t launch_gp_adjoint(int prec, const GPParams& p, cudaStream_t st);
 cudaError_t launch_gp_sub(int prec, const GPParams& p, cudaStream_t st);
