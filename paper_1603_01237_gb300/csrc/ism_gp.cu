@@ -108,9 +108,19 @@ __device__ __forceinline__ void dft8(typename C2<R>::T* v) {
   for (int m = 0; m < 4; ++m) { v[2 * m] = a[m]; v[2 * m + 1] = b[m]; }
 }
 
+// Shared-memory position of state element m: its low four index bits XORed with bits 3..6 (a
+// permutation of every aligned block of 128 elements, so buffers keep their size).  The Stockham
+// stores of the first two radix-8 passes go to strides of 8 and 64 elements, which fall on the same
+// banks unswizzled (up to 8 wavefronts per 8-byte warp access); swizzled, every load and store of the
+// transform and every element-wise loop over m takes the minimum of two.
+__device__ __forceinline__ int sw(int m) { return m ^ ((m >> 3) & 15); }
+
 struct Ident {
   template <class T> __device__ __forceinline__ T operator()(int, int, T v) const { return v; }
   template <class T> __device__ __forceinline__ T operator()(int, T v) const { return v; }
+};
+struct NoOp {
+  __device__ __forceinline__ void operator()() const {}
 };
 
 // Stockham radix-8 FFT (unnormalised) of length n = 8^P from x, using y as the other buffer; twiddle
@@ -118,12 +128,13 @@ struct Ident {
 // t < n/8 compute.
 // pre(m, r, v) is applied to every input element as the first pass loads it (thread t loads elements
 // m = t + r n/8, r = 0..7), post(m, v) to every output element as the last pass stores it, so
-// pointwise factors cost no pass and no barrier of their own.
+// pointwise factors cost no pass and no barrier of their own.  mid() runs once, after the first
+// pass has applied pre (a caller's loads for the next step start there, in registers pre has freed).
 // Returns the buffer that holds the result.
-template <typename R, bool INV, class Pre = Ident, class Post = Ident>
+template <typename R, bool INV, class Pre = Ident, class Post = Ident, class Mid = NoOp>
 __device__ typename C2<R>::T* fft8(typename C2<R>::T* x, typename C2<R>::T* y, const typename C2<R>::T* W,
                                    const typename C2<R>::T* Wl, int n, const Pre& pre = Pre(),
-                                   const Post& post = Post()) {
+                                   const Post& post = Post(), const Mid& mid = Mid()) {
   using T = typename C2<R>::T;
   const int t = threadIdx.x, q = n >> 3;
   for (int Ns = 1; Ns < n; Ns <<= 3) {
@@ -133,15 +144,17 @@ __device__ typename C2<R>::T* fft8(typename C2<R>::T* x, typename C2<R>::T* y, c
 #pragma unroll
       for (int r = 0; r < 8; ++r) {
         const int m = t + r * q;
-        v[r] = Ns == 1 ? pre(m, r, x[m]) : x[m];
+        v[r] = Ns == 1 ? pre(m, r, x[sw(m)]) : x[sw(m)];
       }
-      const int step = n / (Ns << 3);
+      if (Ns > 1) {   // the first pass's twiddles are all 1
+        const int step = n / (Ns << 3);
 #pragma unroll
-      for (int r = 1; r < 8; ++r) {
-        const int i = (k * r * step) & (n - 1);
-        T w = W[i], wl = Wl[i];
-        if (INV) { w = cconj(w); wl = cconj(wl); }
-        v[r] = cmul_hl(v[r], w, wl);
+        for (int r = 1; r < 8; ++r) {
+          const int i = (k * r * step) & (n - 1);
+          T w = W[i], wl = Wl[i];
+          if (INV) { w = cconj(w); wl = cconj(wl); }
+          v[r] = cmul_hl(v[r], w, wl);
+        }
       }
       dft8<R, INV>(v);
       const int base = (t / Ns) * (Ns << 3) + k;
@@ -149,9 +162,10 @@ __device__ typename C2<R>::T* fft8(typename C2<R>::T* x, typename C2<R>::T* y, c
 #pragma unroll
       for (int r = 0; r < 8; ++r) {
         const int m = base + r * Ns;
-        y[m] = last ? post(m, v[r]) : v[r];
+        y[sw(m)] = last ? post(m, v[r]) : v[r];
       }
     }
+    if (Ns == 1) mid();
     __syncthreads();
     T* tmp = x;
     x = y;
@@ -211,6 +225,15 @@ __device__ void gp_fill_tables(const GPParams& p, typename C2<R>::T* tab) {
   }
 }
 
+// This thread's 8 first-pass elements of a stored row (threads beyond n/8 load nothing).
+template <typename T> __device__ __forceinline__ void ld_row8(T (&a)[8], const T* row, int n) {
+  const int t = threadIdx.x, q = n >> 3;
+  if (t < q) {
+#pragma unroll
+    for (int r = 0; r < 8; ++r) a[r] = row[t + r * q];
+  }
+}
+
 template <typename R>
 struct GP {
   using T = typename C2<R>::T;
@@ -254,8 +277,8 @@ struct GP {
   // buf is A or C; B is the scratch of every transform.  The forward transform applies pre on load
   // and f on store, the inverse the 1/n normalisation on store; with 2 log_8(n) passes in all (an
   // even number) the result lands back in buf.
-  template <bool ADJ, bool FULL, class Pre = Ident>
-  __device__ void kinetic(T* buf, const Pre& pre = Pre()) {
+  template <bool ADJ, bool FULL, class Pre = Ident, class Mid = NoOp>
+  __device__ void kinetic(T* buf, const Pre& pre = Pre(), const Mid& mid = Mid()) {
     const T* fh = FULL ? D2m1 : DH;
     const T* fl = FULL ? D2l : DHl;
     auto factor = [fh, fl](int m, T v) {
@@ -263,7 +286,7 @@ struct GP {
       if (ADJ) { f = cconj(f); g = cconj(g); }
       return FULL ? cadd(v, cmul_hl(v, f, g)) : cmul_hl(v, f, g);
     };
-    T* X = fft8<R, false>(buf, B, W, Wl, n, pre, factor);
+    T* X = fft8<R, false>(buf, B, W, Wl, n, pre, factor, mid);
     T* other = (X == buf) ? B : buf;
     const R inv_n = (R)(1.0 / (double)n);
     auto scale = [inv_n](int, T v) {
@@ -316,7 +339,7 @@ struct GP {
   // (row i - c0), propagated in the spare buffer C with the same steps as the forward sweep that
   // stored the checkpoint, so every recomputed state equals the one it replaces bit for bit.
   __device__ void recompute(const T* ck, const double* ub, int c0, int c1, T* seg) {
-    for (int m = threadIdx.x; m < n; m += blockDim.x) C[m] = ck[m];
+    for (int m = threadIdx.x; m < n; m += blockDim.x) C[sw(m)] = ck[m];
     __syncthreads();
     for (int i = c0; i < c1; ++i) step_on(C, ub[i], seg + (long)(i - c0) * n);
     __syncthreads();
@@ -336,10 +359,12 @@ struct GP {
   // adjoint step at a_j (global, complex R, per element): A holds nu_{j+1} on entry and nu_j on exit;
   // the pointwise part runs as the first FFT pass loads each element.  GRAD: also return dJ/du_j
   // (FP64 block sum of FP32 per-thread partials); the global adjoint sweep needs only the states.
-  // aj[r] = a_j at element t + r n/8 (this thread's elements of the first FFT pass), loaded by the
-  // caller one step ahead so that the global-memory latency is off the step's critical path.
+  // aj[r] = a_j at element t + r n/8 (this thread's elements of the first FFT pass), loaded one step
+  // ahead so that the global-memory latency is off the step's critical path: once the first pass has
+  // consumed a_j, aj is refilled from next_row (a_{j-1}; null: left as is) while the remaining five
+  // passes run.
   template <bool GRAD>
-  __device__ double adjoint_step(const T (&aj)[8], double u) {
+  __device__ double adjoint_step(T (&aj)[8], double u, const T* next_row) {
     const R ur = (R)u, tr = (R)tau, f2 = R(2) * (R)tau * (R)g;
     R part = R(0);
     const GP* self = this;
@@ -354,20 +379,22 @@ struct GP {
       w.x = mu.x + f * a.x;
       w.y = mu.y + f * a.y;
       return w;
+    }, [&aj, next_row, self] {
+      if (next_row) ld_row8(aj, next_row, self->n);
     });
     if (!GRAD) return 0.0;
     return tau * dx * sum((double)part);
   }
 };
 
-// This thread's 8 first-pass elements of a stored row (threads beyond n/8 load nothing).
-template <typename T> __device__ __forceinline__ void ld_row8(T (&a)[8], const T* row, int n) {
-  const int t = threadIdx.x, q = n >> 3;
-  if (t < q) {
-#pragma unroll
-    for (int r = 0; r < 8; ++r) a[r] = row[t + r * q];
-  }
-}
+
+// Resident CTAs per SM an FP32 sweep is compiled for (64 threads each at n = 512).  Each FP32 kernel
+// comes twice: unbounded (TP = false), where the compiler spends up to 255 registers on the unrolled
+// transforms -- the shortest step, four CTAs per SM -- for launches that fill no more than that; and
+// bounded (TP = true) for batches: ten CTAs per SM for the sequential sweeps (one CTA per problem,
+// 1520 problems in one wave on 152 SMs), eight for the sub-problems.  FP64 is never bounded.
+template <typename R, bool TP> constexpr int gp_min_ctas(int fp32) { return TP && sizeof(R) == 4 ? fp32 : 1; }
+constexpr long GP_TP_MIN_CTAS = 4L * 152;   // CTAs of a launch from which the bounded kernels run
 
 template <typename R> __device__ __forceinline__ typename C2<R>::T ld_state(const double2* src, int m) {
   typename C2<R>::T v;
@@ -378,8 +405,8 @@ template <typename R> __device__ __forceinline__ typename C2<R>::T ld_state(cons
 }
 
 // ------------------------------------------------------------------------------------ kernels
-template <typename R>
-__global__ void k_gp_forward(GPParams p) {
+template <typename R, bool TP>
+__global__ void __launch_bounds__(64, (gp_min_ctas<R, TP>(10))) k_gp_forward(GPParams p) {
   using T = typename C2<R>::T;
   extern __shared__ __align__(128) unsigned char smem[];
   __shared__ double red[32];
@@ -391,23 +418,23 @@ __global__ void k_gp_forward(GPParams p) {
   T* traj = p.cks ? nullptr : reinterpret_cast<T*>(p.traj) + (long)b * (p.Nt + 1) * n;
   T* gck = p.cks ? reinterpret_cast<T*>(p.gck) + (long)b * p.N * p.nck * n : nullptr;
   double2* psin = p.psin + (long)b * (p.N + 1) * n;
-  for (int m = threadIdx.x; m < n; m += blockDim.x) s.A[m] = ld_state<R>(p.psi_i, m);
+  for (int m = threadIdx.x; m < n; m += blockDim.x) s.A[sw(m)] = ld_state<R>(p.psi_i, m);
   __syncthreads();
   s.kinetic<false, false>(s.A);   // a_0 = K psi_i
   int nn = 0;
   for (int j = 0; j <= p.Nt; ++j) {
     if (nn <= p.N && j == p.jn[nn]) {   // psi(t_n) = K^H a_j, and J, F at the end
-      for (int m = threadIdx.x; m < n; m += blockDim.x) s.C[m] = s.A[m];
+      for (int m = threadIdx.x; m < n; m += blockDim.x) s.C[sw(m)] = s.A[sw(m)];
       __syncthreads();
       s.kinetic<true, false>(s.C);   // scratch B; the live state A is untouched
       for (int m = threadIdx.x; m < n; m += blockDim.x) {
-        const T v = s.C[m];
+        const T v = s.C[sw(m)];
         psin[(long)nn * n + m] = make_double2((double)v.x, (double)v.y);
       }
       if (j == p.Nt) {
         double orr = 0.0, oi = 0.0;
         for (int m = threadIdx.x; m < n; m += blockDim.x) {
-          const T v = s.C[m];
+          const T v = s.C[sw(m)];
           const double2 f = p.psi_f[m];
           orr += (double)v.x * f.x + (double)v.y * f.y;
           oi += (double)v.x * f.y - (double)v.y * f.x;
@@ -435,8 +462,8 @@ __global__ void k_gp_forward(GPParams p) {
   if (p.count && threadIdx.x == 0) atomicAdd(p.count, (unsigned long long)p.Nt);
 }
 
-template <typename R>
-__global__ void k_gp_adjoint(GPParams p) {
+template <typename R, bool TP>
+__global__ void __launch_bounds__(64, (gp_min_ctas<R, TP>(10))) k_gp_adjoint(GPParams p) {
   using T = typename C2<R>::T;
   extern __shared__ __align__(128) unsigned char smem[];
   __shared__ double red[32];
@@ -449,16 +476,17 @@ __global__ void k_gp_adjoint(GPParams p) {
   T* seg = p.cks ? reinterpret_cast<T*>(p.segb) + (long)b * p.N * p.cks * n : nullptr;
   double2* chin = p.chin + (long)b * (p.N + 1) * n;
   for (int m = threadIdx.x; m < n; m += blockDim.x) {
-    s.A[m] = ld_state<R>(p.psi_f, m);
+    s.A[sw(m)] = ld_state<R>(p.psi_f, m);
     chin[(long)p.N * n + m] = p.psi_f[m];
   }
   __syncthreads();
   s.kinetic<true, false>(s.A);   // nu_Nt = K^H psi_f
   int nn = p.N - 1;
-  T acur[8], anext[8];
+  T acur[8];
   int c0 = p.Nt;                 // first step of the recomputed segment (checkpointed trajectories)
   if (traj) ld_row8(acur, traj + (long)(p.Nt - 1) * n, n);
   for (int j = p.Nt - 1; j >= 0; --j) {
+    const T* next_row = nullptr;
     if (gck) {
       if (j == c0 - 1) {         // the last step of the previous segment: recompute that segment
         const int jb = p.jn[nn], k = (j - jb) / p.cks;
@@ -466,19 +494,17 @@ __global__ void k_gp_adjoint(GPParams p) {
         s.recompute(gck + ((long)nn * p.nck + k) * n, ub, c0, j + 1, seg);
         ld_row8(acur, seg + (long)(j - c0) * n, n);
       }
-      if (j > c0) ld_row8(anext, seg + (long)(j - 1 - c0) * n, n);
+      if (j > c0) next_row = seg + (long)(j - 1 - c0) * n;
     } else if (j > 0) {
-      ld_row8(anext, traj + (long)(j - 1) * n, n);
+      next_row = traj + (long)(j - 1) * n;
     }
-    s.template adjoint_step<false>(acur, ub[j]);
-#pragma unroll
-    for (int r = 0; r < 8; ++r) acur[r] = anext[r];
+    s.template adjoint_step<false>(acur, ub[j], next_row);
     if (nn >= 0 && j == p.jn[nn]) {   // chi(t_n) = lambda_j = K nu_j
-      for (int m = threadIdx.x; m < n; m += blockDim.x) s.C[m] = s.A[m];
+      for (int m = threadIdx.x; m < n; m += blockDim.x) s.C[sw(m)] = s.A[sw(m)];
       __syncthreads();
       s.kinetic<false, false>(s.C);   // scratch B; the live state A is untouched
       for (int m = threadIdx.x; m < n; m += blockDim.x) {
-        const T v = s.C[m];
+        const T v = s.C[sw(m)];
         chin[(long)nn * n + m] = make_double2((double)v.x, (double)v.y);
       }
       --nn;
@@ -489,8 +515,8 @@ __global__ void k_gp_adjoint(GPParams p) {
 }
 
 // grid (N, B): sub-problem n of problem b
-template <typename R>
-__global__ void k_gp_sub(GPParams p) {
+template <typename R, bool TP>
+__global__ void __launch_bounds__(64, (gp_min_ctas<R, TP>(8))) k_gp_sub(GPParams p) {
   using T = typename C2<R>::T;
   extern __shared__ __align__(128) unsigned char smem[];
   __shared__ double red[32];
@@ -505,7 +531,7 @@ __global__ void k_gp_sub(GPParams p) {
   const double2* psin = p.psin + (long)b * (p.N + 1) * n;
   const double2* chin = p.chin + (long)b * (p.N + 1) * n;
   // forward from psi(t_n), storing a_j for j0..j1-1 (or every cks-th of them)
-  for (int m = threadIdx.x; m < n; m += blockDim.x) s.A[m] = ld_state<R>(psin + (long)nsub * n, m);
+  for (int m = threadIdx.x; m < n; m += blockDim.x) s.A[sw(m)] = ld_state<R>(psin + (long)nsub * n, m);
   __syncthreads();
   s.kinetic<false, false>(s.A);
   for (int j = j0; j < j1; ++j) {
@@ -517,22 +543,23 @@ __global__ void k_gp_sub(GPParams p) {
   s.kinetic<true, false>(s.A);
   double jr = 0.0;
   for (int m = threadIdx.x; m < n; m += blockDim.x) {
-    const T v = s.A[m];
+    const T v = s.A[sw(m)];
     const double2 c = chin[(long)(nsub + 1) * n + m];
     jr += (double)v.x * c.x + (double)v.y * c.y;
   }
   jr = s.sum(jr) * p.dx;
   // adjoint from chi(t_{n+1}): nu_{j1} = K^H chi(t_{n+1})
-  for (int m = threadIdx.x; m < n; m += blockDim.x) s.A[m] = ld_state<R>(chin + (long)(nsub + 1) * n, m);
+  for (int m = threadIdx.x; m < n; m += blockDim.x) s.A[sw(m)] = ld_state<R>(chin + (long)(nsub + 1) * n, m);
   __syncthreads();
   s.kinetic<true, false>(s.A);
   double err = 0.0;
   double* gb = p.grad + (long)b * p.Nt;
-  T acur[8], anext[8];
+  T acur[8];
   int c0 = j1;   // first step of the recomputed segment (checkpointed trajectories)
   if (traj) ld_row8(acur, traj + (long)(j1 - 1) * n, n);
   for (int j = j1 - 1; j >= j0; --j) {
     const double uj = ub[j];
+    const T* next_row = nullptr;
     if (gck) {
       if (j == c0 - 1) {   // entering a segment at its last step: recompute it (u not yet updated there)
         const int k = (j - j0) / p.cks;
@@ -540,13 +567,11 @@ __global__ void k_gp_sub(GPParams p) {
         s.recompute(gck + (long)k * n, ub, c0, j + 1, seg);
         ld_row8(acur, seg + (long)(j - c0) * n, n);
       }
-      if (j > c0) ld_row8(anext, seg + (long)(j - 1 - c0) * n, n);
+      if (j > c0) next_row = seg + (long)(j - 1 - c0) * n;
     } else if (j > j0) {
-      ld_row8(anext, traj + (long)(j - 1) * n, n);
+      next_row = traj + (long)(j - 1) * n;
     }
-    const double gj = s.template adjoint_step<true>(acur, uj);
-#pragma unroll
-    for (int r = 0; r < 8; ++r) acur[r] = anext[r];
+    const double gj = s.template adjoint_step<true>(acur, uj, next_row);
     err += fabs(gj);
     if (threadIdx.x == 0) {
       gb[j] = gj;
@@ -580,15 +605,17 @@ cudaError_t launch(K kern, const GPParams& p, dim3 grid, cudaStream_t st) {
 
 }  // namespace
 
-bool gp_supported(int n) { return n == 64 || n == 512; }   // 8^P points whose tables fit in shared memory
+bool gp_supported(int n) { return n == 64 || n == 512; }   // 8^P points, three states in shared memory
 
 cudaError_t launch_gp_forward(int prec, const GPParams& p, cudaStream_t st) {
-  return prec == 0 ? launch<double>(k_gp_forward<double>, p, dim3(p.B), st)
-                   : launch<float>(k_gp_forward<float>, p, dim3(p.B), st);
+  if (prec == 0) return launch<double>(k_gp_forward<double, false>, p, dim3(p.B), st);
+  return p.B >= GP_TP_MIN_CTAS ? launch<float>(k_gp_forward<float, true>, p, dim3(p.B), st)
+                               : launch<float>(k_gp_forward<float, false>, p, dim3(p.B), st);
 }
 cudaError_t launch_gp_adjoint(int prec, const GPParams& p, cudaStream_t st) {
-  return prec == 0 ? launch<double>(k_gp_adjoint<double>, p, dim3(p.B), st)
-                   : launch<float>(k_gp_adjoint<float>, p, dim3(p.B), st);
+  if (prec == 0) return launch<double>(k_gp_adjoint<double, false>, p, dim3(p.B), st);
+  return p.B >= GP_TP_MIN_CTAS ? launch<float>(k_gp_adjoint<float, true>, p, dim3(p.B), st)
+                               : launch<float>(k_gp_adjoint<float, false>, p, dim3(p.B), st);
 }
 size_t gp_table_bytes(int prec, int n) { return 7 * (size_t)n * (prec == 0 ? sizeof(double2) : sizeof(float2)); }
 
@@ -600,8 +627,9 @@ cudaError_t launch_gp_tables(int prec, const GPParams& p, cudaStream_t st) {
 }
 
 cudaError_t launch_gp_sub(int prec, const GPParams& p, cudaStream_t st) {
-  return prec == 0 ? launch<double>(k_gp_sub<double>, p, dim3(p.N, p.B), st)
-                   : launch<float>(k_gp_sub<float>, p, dim3(p.N, p.B), st);
+  if (prec == 0) return launch<double>(k_gp_sub<double, false>, p, dim3(p.N, p.B), st);
+  return (long)p.N * p.B >= GP_TP_MIN_CTAS ? launch<float>(k_gp_sub<float, true>, p, dim3(p.N, p.B), st)
+                                           : launch<float>(k_gp_sub<float, false>, p, dim3(p.N, p.B), st);
 }
 
 }  // namespace ism

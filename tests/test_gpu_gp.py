@@ -164,3 +164,24 @@ def test_gp_checkpoints_full_size_footprint_and_parity(P):
         u0_, J0_, _ = pl.iterate(w.u0, 2)
     assert np.array_equal(u, u0_) and np.array_equal(J, J0_)
     assert np.max(np.abs(J[0] - J_o)) <= 1e-5
+
+
+def test_gp_batched_launches_match_single_problem_plans(P):
+    """640 problems per plan (Nt = 40, N = 8): the FP32 sweeps then run the kernels compiled for ten
+    (sequential sweeps) and eight (sub-problems) resident CTAs per SM, a one-problem plan the
+    unbounded ones.  Same arithmetic: three problems' controls, J and Err after two iterations agree
+    with their one-problem plans, and with the FP64 oracle to the mixed bar."""
+    w = _gp(512, 40, 8, 0.5)
+    B = 640
+    rng = np.random.default_rng(21)
+    U = w.u0[None, :] + 0.2 * rng.standard_normal((B, w.Nt))
+    with P.Plan(w, precision="mixed", rho=0.5, batch=B) as pl:
+        u, J, E = pl.iterate(U, 2)
+    for b in (0, 317, B - 1):
+        with P.Plan(w, precision="mixed", rho=0.5) as pl1:
+            u1, J1, E1 = pl1.iterate(U[b], 2)
+        assert np.max(np.abs(u[b] - u1[0])) <= 1e-12 * np.max(np.abs(u1[0])), np.max(np.abs(u[b] - u1[0]))
+        assert np.max(np.abs(J[b] - J1[0])) <= 1e-12 and np.max(np.abs(E[b] - E1[0])) <= 1e-12 * np.max(E1[0])
+        u_o, J_o, _, _ = G.ism_solve(w, U[b], 2, 0.5)
+        assert np.max(np.abs(J[b] - J_o)) <= 1e-5, np.max(np.abs(J[b] - J_o))
+        assert np.max(np.abs(u[b] - u_o)) <= 1e-4 * np.max(np.abs(u_o)), np.max(np.abs(u[b] - u_o))
