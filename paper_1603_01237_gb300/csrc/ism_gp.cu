@@ -50,17 +50,15 @@ template <typename T> __device__ __forceinline__ T cmul_hl(T a, T bh, T bl) {
 
 __device__ __forceinline__ void sc(float x, float& s, float& c) { sincosf(x, &s, &c); }
 __device__ __forceinline__ void sc(double x, double& s, double& c) { sincos(x, &s, &c); }
-__device__ __forceinline__ float sn(float x) { return sinf(x); }
-__device__ __forceinline__ double sn(double x) { return sin(x); }
 
-// exp(i phi) - 1 = -2 sin^2(phi/2) + i sin(phi), without cancellation for small phi
+// exp(i phi) - 1 = -2 sin^2(phi/2) + 2i sin(phi/2) cos(phi/2): one sine-cosine pair of the half
+// angle, without cancellation for small phi
 template <typename T, typename R> __device__ __forceinline__ T expm1i(R phi) {
   R s, c;
-  sc(phi, s, c);
-  const R h = sn(R(0.5) * phi);
+  sc(R(0.5) * phi, s, c);
   T e;
-  e.x = R(-2) * h * h;
-  e.y = s;
+  e.x = R(-2) * s * s;
+  e.y = R(2) * s * c;
   return e;
 }
 
