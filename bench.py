@@ -638,9 +638,10 @@ def state_steps_per_iteration(plan, w) -> tuple:
     plan's kernels execute them: 2 Nt for the global sweeps (direct) and, per sub-interval, psi and chi
     carried forward (2 Nt; the first local step of the two-trajectory form) or the literal
     sub-problem's forward sweep, its recomputation from the checkpoints and the adjoint (~3 Nt); the
-    grid model stores its forward states (2 Nt global + 2 Nt sub-interval)."""
+    grid model's first local step takes the sub-problems' forward trajectories from the global forward
+    sweep's stored states and runs their adjoints (2 Nt global + Nt sub-interval)."""
     if plan.gp:
-        return 4 * w.Nt, "2 Nt global sweeps + 2 Nt sub-interval sweeps"
+        return 3 * w.Nt, "2 Nt global sweeps + Nt sub-interval adjoint steps (the sub-problems' forward trajectories are the global sweep's stored states)"
     if plan.precision == "mixed":
         return 4 * w.Nt, "2 Nt global sweeps + 2 Nt sub-interval sweeps (psi and chi forward)"
     return 5 * w.Nt, "2 Nt global sweeps + ~3 Nt literal sub-problems (forward, recomputation, adjoint)"

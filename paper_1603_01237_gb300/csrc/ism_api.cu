@@ -543,7 +543,7 @@ ism::GPParams gparams(ism_plan_s* P, double* u) {
   g.cks = P->cks; g.nck = P->nck; g.gck = P->dckpt; g.segb = P->dsegb; g.tab = P->dgptab;
   g.psin = P->dpsin; g.chin = P->dchin; g.grad = P->dgrad; g.Jn = P->dJn; g.err = P->derr;
   g.J = P->dJ; g.F = P->dF; g.Jhist = nullptr; g.hist_stride = 0; g.hist_k = 0;
-  g.status = P->dstatus; g.count = P->dcount; g.update = 0;
+  g.status = P->dstatus; g.count = P->dcount; g.update = 0; g.reuse = 0;
   return g;
 }
 
@@ -1346,6 +1346,7 @@ int ism_iterate(ism_plan_t P, int iters, double* u_inout, double* J_hist, double
     for (int l = 0; l < P->L && P->gp; ++l) {
       ism::GPParams g = gparams(P, ud);
       g.update = 1;
+      g.reuse = l == 0;   // phi_n = psi(t_n) at these controls: the forward sweep's stored trajectory
       g.err = l == 0 ? P->derr : nullptr;
       g.Jn = l == 0 ? P->dJn : nullptr;
       g.count = P->dcount + 3;
@@ -1403,6 +1404,7 @@ int ism_gradient(ism_plan_t P, const double* u, double* grad, double* J) {
   if (P->gp) {   // the sub-problem gradients at the adjoint targets are the global gradient
     ism::GPParams g = gparams(P, const_cast<double*>(ud));
     g.update = 0;
+    g.reuse = 1;   // psi(t_n) of the sweep just run: its stored trajectory is the sub-problems'
     g.count = P->dcount + 3;
     ISM_CUDA_TRY(timed(P, 2, 1, [&] { return ism::launch_gp_sub(P->prec, g, P->st); }));
   } else {       // Theorem 2 two-trajectory form, scaled by beta_n

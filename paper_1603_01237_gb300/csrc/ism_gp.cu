@@ -19,8 +19,9 @@
 // as (factor - 1) and applied as v + (factor - 1) v, so their rounding is relative to the change.
 //   k_gp_forward   full forward sweep: psi(t_n) at the partition, a_j for every step, J and F;
 //   k_gp_adjoint   full adjoint sweep: chi(t_n) = lambda_{j_n}, the sub-problem targets;
-//   k_gp_sub       all sub-problems at once (grid N x B): forward from psi(t_n) storing a_j, adjoint
-//                  from chi(t_{n+1}), gradient of J_n = Re<psi_n(t_{n+1})|chi(t_{n+1})>, ascent step.
+//   k_gp_sub       all sub-problems at once (grid N x B): forward from psi(t_n) storing a_j (skipped in
+//                  a first local step, whose trajectories the forward sweep stored), adjoint from
+//                  chi(t_{n+1}), gradient of J_n = Re<psi_n(t_{n+1})|chi(t_{n+1})>, ascent step.
 #include <cmath>
 
 #include "ism_device.cuh"
@@ -528,22 +529,33 @@ __global__ void __launch_bounds__(64, (gp_min_ctas<R, TP>(8))) k_gp_sub(GPParams
   T* seg = p.cks ? reinterpret_cast<T*>(p.segb) + ((long)b * p.N + nsub) * p.cks * n : nullptr;
   const double2* psin = p.psin + (long)b * (p.N + 1) * n;
   const double2* chin = p.chin + (long)b * (p.N + 1) * n;
-  // forward from psi(t_n), storing a_j for j0..j1-1 (or every cks-th of them)
-  for (int m = threadIdx.x; m < n; m += blockDim.x) s.A[sw(m)] = ld_state<R>(psin + (long)nsub * n, m);
-  __syncthreads();
-  s.kinetic<false, false>(s.A);
-  for (int j = j0; j < j1; ++j) {
-    T* keep = traj ? traj + (long)j * n : nullptr;
-    if (gck && (j - j0) % p.cks == 0) keep = gck + (long)((j - j0) / p.cks) * n;
-    s.step(ub[j], keep);
-  }
-  // J_n = Re<psi_n(t_{n+1})|chi(t_{n+1})>, psi_n(t_{n+1}) = K^H a_{j1}
-  s.kinetic<true, false>(s.A);
   double jr = 0.0;
-  for (int m = threadIdx.x; m < n; m += blockDim.x) {
-    const T v = s.A[sw(m)];
-    const double2 c = chin[(long)(nsub + 1) * n + m];
-    jr += (double)v.x * c.x + (double)v.y * c.y;
+  if (p.reuse) {
+    // first local step: phi_n = psi(t_n) under the same controls, so the sub-problem's trajectory on
+    // [t_n, t_{n+1}] is the global forward sweep's -- a_j (or its checkpoints) are already stored, and
+    // J_n = Re<psi(t_{n+1})|chi(t_{n+1})> with the stored psi(t_{n+1})
+    for (int m = threadIdx.x; m < n; m += blockDim.x) {
+      const double2 v = psin[(long)(nsub + 1) * n + m];
+      const double2 c = chin[(long)(nsub + 1) * n + m];
+      jr += v.x * c.x + v.y * c.y;
+    }
+  } else {
+    // forward from psi(t_n), storing a_j for j0..j1-1 (or every cks-th of them)
+    for (int m = threadIdx.x; m < n; m += blockDim.x) s.A[sw(m)] = ld_state<R>(psin + (long)nsub * n, m);
+    __syncthreads();
+    s.kinetic<false, false>(s.A);
+    for (int j = j0; j < j1; ++j) {
+      T* keep = traj ? traj + (long)j * n : nullptr;
+      if (gck && (j - j0) % p.cks == 0) keep = gck + (long)((j - j0) / p.cks) * n;
+      s.step(ub[j], keep);
+    }
+    // J_n = Re<psi_n(t_{n+1})|chi(t_{n+1})>, psi_n(t_{n+1}) = K^H a_{j1}
+    s.kinetic<true, false>(s.A);
+    for (int m = threadIdx.x; m < n; m += blockDim.x) {
+      const T v = s.A[sw(m)];
+      const double2 c = chin[(long)(nsub + 1) * n + m];
+      jr += (double)v.x * c.x + (double)v.y * c.y;
+    }
   }
   jr = s.sum(jr) * p.dx;
   // adjoint from chi(t_{n+1}): nu_{j1} = K^H chi(t_{n+1})
@@ -580,7 +592,7 @@ __global__ void __launch_bounds__(64, (gp_min_ctas<R, TP>(8))) k_gp_sub(GPParams
     const long id = (long)b * p.N + nsub;
     if (p.Jn) p.Jn[id] = jr;
     if (p.err) p.err[id] = err;
-    if (p.count) atomicAdd(p.count + 1, (unsigned long long)(2 * (j1 - j0)));
+    if (p.count) atomicAdd(p.count + 1, (unsigned long long)((p.reuse ? 1 : 2) * (j1 - j0)));
   }
 }
 

@@ -29,6 +29,9 @@ struct GPParams {
   int* status;
   unsigned long long* count;   // [2]: FFT pairs (sequential sweeps), FFT pairs (sub-interval sweeps)
   int update;
+  int reuse;              // k_gp_sub: the sub-problems start from psi(t_n) at the controls of the last
+                          // k_gp_forward (a first local step), so their forward trajectories are its
+                          // stored states (traj, or the checkpoints gck): only the adjoint runs
   const void* tab;        // [7n] complex R: the plan's twiddle, kinetic-factor and grid tables (k_gp_tables)
 };
 
