@@ -185,3 +185,20 @@ def test_gp_batched_launches_match_single_problem_plans(P):
         u_o, J_o, _, _ = G.ism_solve(w, U[b], 2, 0.5)
         assert np.max(np.abs(J[b] - J_o)) <= 1e-5, np.max(np.abs(J[b] - J_o))
         assert np.max(np.abs(u[b] - u_o)) <= 1e-4 * np.max(np.abs(u_o)), np.max(np.abs(u[b] - u_o))
+
+
+@pytest.mark.parametrize("S", [0, 7])
+def test_gp_first_local_step_equals_literal_subproblems(P, S):
+    """A first local step starts every sub-problem from phi_n = psi(t_n) under the controls of the
+    forward sweep, so `ism_iterate` takes the sub-problems' forward trajectories from that sweep (or
+    its checkpoints, S > 0) and runs only their adjoints.  In FP64 the update equals the literal
+    sub-problems' (`subinterval_grad` at the sweep's own phi, forward propagated from phi_n) to
+    rounding: u + rho g / tau, and Err = sum_j |g_j| per sub-interval."""
+    w = _dw(512, 157, 5, 1.0)
+    rho, tau = 0.05, w.T / w.Nt
+    with P.Plan(w, precision="fp64", rho=rho, ckpt_stride=S) as pl:
+        phi = pl.intermediate_states(w.u0)[0]
+        g, Jn = pl.subinterval_grad(phi, w.u0)
+        u1, J, E = pl.iterate(w.u0, 1)
+    assert np.max(np.abs(u1[0] - (w.u0 + rho * g[0] / tau))) <= 1e-10 * np.max(np.abs(w.u0))
+    assert abs(E[0, 0] - np.sum(np.abs(g[0]))) <= 1e-10 * np.sum(np.abs(g[0]))
