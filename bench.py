@@ -642,9 +642,7 @@ def state_steps_per_iteration(plan, w) -> tuple:
     sweep's stored states and runs their adjoints (2 Nt global + Nt sub-interval)."""
     if plan.gp:
         return 3 * w.Nt, "2 Nt global sweeps + Nt sub-interval adjoint steps (the sub-problems' forward trajectories are the global sweep's stored states)"
-    if plan.precision == "mixed":
-        return 4 * w.Nt, "2 Nt global sweeps + 2 Nt sub-interval sweeps (psi and chi forward)"
-    return 5 * w.Nt, "2 Nt global sweeps + ~3 Nt literal sub-problems (forward, recomputation, adjoint)"
+    return 4 * w.Nt, "2 Nt global sweeps + 2 Nt sub-interval sweeps (psi and chi forward)"
 
 
 def oracle_worker(cfg: str, N, seconds: float):

@@ -148,8 +148,10 @@ typedef struct {
                                   nothing per step is stored but one overlap): identical at phi = phi^u
                                   in exact arithmetic, and free of the O(1/N) cancellation of
                                   phi_{n+1} - psi_n(t_{n+1}) that FP32 propagation cannot resolve;
-                              0 = default: 2 in ISM_MIXED, 1 in ISM_FP64.  Later local steps
-                              (L > 1) and ism_subinterval_grad always use the literal form.      */
+                              0 = default: 2 (in FP64 the two forms agree to rounding; 2
+                              propagates 2 Nt states per iteration where 1 propagates ~3 Nt).
+                              Later local steps (L > 1) and ism_subinterval_grad always use
+                              the literal form.                                                  */
   int step1;               /* how Algorithm 1 (a)-(b) obtains psi(t_n), chi(t_n) for d <= 64:
                               1 = propagator assembly and chain (Sec. 3): d Nt state-steps per
                                   problem, parallel over sub-intervals -- lowest latency;

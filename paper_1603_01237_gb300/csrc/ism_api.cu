@@ -869,7 +869,7 @@ int plan_build(const ism_problem* prob, const ism_options* opt, void* cuda_strea
   P->tol = opt->cheb_tol > 0 ? opt->cheb_tol : (P->prec == ISM_FP64 ? 1e-17 : 1e-10);
   P->w = p.objective == ISM_OBJ_OVERLAP ? 1.0 : 2.0;
   P->max_spin = opt->max_spin_iters > 0 ? opt->max_spin_iters : (1 << 22);
-  P->form = opt->subproblem_form != 0 ? opt->subproblem_form : (P->prec == ISM_MIXED ? 2 : 1);
+  P->form = opt->subproblem_form != 0 ? opt->subproblem_form : 2;
   P->scheme = opt->scheme;
   P->st = reinterpret_cast<cudaStream_t>(cuda_stream);
   cudaGetDevice(&P->dev);
