@@ -479,7 +479,7 @@ def crank_nicolson_leg(P, w, stream, steps: int, cpu: bool):
     ms = e0.elapsed_time(e1) / n
     st = plan.ism_get_stats(reset=True)
     plan.close()
-    names = ["k_gsweep", "k_phi", "k_subinterval"]
+    names = ["k_gsweep", "k_phi", "k_subfwd"]
     dom = 0 if st["ms"][0] >= st["ms"][2] else 2
     ms_launch = st["ms"][dom] / n
     flops = 2.0 * w.Nt * B * cn_flops_per_state_step(int(w.d), K)   # two sweeps per launch
@@ -725,7 +725,7 @@ def measure_config(P, W, cfg: str, args, stream, steps: int, warmup: int, world:
 
     large = plan.ks_large
     direct = plan.info(6) == 2   # Algorithm 1 (a)-(b) by direct sweeps
-    sub = "k_subfwd" if prec == "mixed" else "k_subinterval"
+    sub = "k_subfwd"   # first local steps run the two-trajectory form in both precisions
     tc = plan.info(10) == 1
     if tc:
         names = ["k_tc_sweep (global)", "k_phi", "k_tc_sweep (sub)"]
