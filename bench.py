@@ -170,13 +170,13 @@ def kernel_source_hash(files=KERNEL_SOURCES) -> str:
 # problems, from a one-pass ncu capture of the default step (4864 rotor problems: k_gsweep in the wide
 # lane layout); reported only while the kernel sources hash to the captured build.
 TRAFFIC_PER_PROBLEM = {
-    ("k_gsweep", "rotor41"): {"bytes_per_problem": (1193538304 + 806773248) / 4864, "source_hash": "73cb90b7a0d46563"},
-    ("k_subfwd", "rotor41"): {"bytes_per_problem": (2211457792 + 2292974592) / 4864, "source_hash": "73cb90b7a0d46563"},
+    ("k_gsweep", "rotor41", "mixed"): {"bytes_per_problem": (1193538304 + 806773248) / 4864, "source_hash": "73cb90b7a0d46563"},
+    ("k_subfwd", "rotor41", "mixed"): {"bytes_per_problem": (2211457792 + 2292974592) / 4864, "source_hash": "73cb90b7a0d46563"},
 }
 
 
-def traffic_of(kernel: str, workload: str, batch: int):
-    rec = TRAFFIC_PER_PROBLEM.get((kernel, workload))
+def traffic_of(kernel: str, workload: str, batch: int, precision: str):
+    rec = TRAFFIC_PER_PROBLEM.get((kernel, workload, precision))
     if rec is None or rec["source_hash"] != kernel_source_hash():
         return None
     return rec["bytes_per_problem"] * batch
@@ -771,7 +771,7 @@ def measure_config(P, W, cfg: str, args, stream, steps: int, warmup: int, world:
         pk = alu_peak(P, "fp64" if prec == "fp64" else "fp32")
         roof = {"kernel": names[dom], "kernels_timed": kernels[dom], "bound": "alu", "achieved": achieved,
                 "peak": pk["peak"], "unit": "TFLOP/s", "frac": achieved / pk["peak"],
-                "traffic": traffic_of(names[dom], cfg, B), "peak_source": pk["source"], "flops_per_launch": flops,
+                "traffic": traffic_of(names[dom], cfg, B, prec), "peak_source": pk["source"], "flops_per_launch": flops,
                 "ms_per_launch": ms_launch}
     else:
         # algorithmic bytes: every stored propagator tile read once per chain, both staged state chains written
@@ -780,7 +780,7 @@ def measure_config(P, W, cfg: str, args, stream, steps: int, warmup: int, world:
         achieved = nbytes / (ms_launch / 1e3) / 1e9
         roof = {"kernel": names[dom], "kernels_timed": kernels[dom], "bound": "hbm", "achieved": achieved,
                 "peak": peaks["hbm_gbs"], "unit": "GB/s", "frac": achieved / peaks["hbm_gbs"],
-                "traffic": traffic_of(names[dom], cfg, B), "peak_source": peaks["source"], "bytes_per_launch": nbytes,
+                "traffic": traffic_of(names[dom], cfg, B, prec), "peak_source": peaks["source"], "bytes_per_launch": nbytes,
                 "ms_per_launch": ms_launch}
     return {"plan": plan, "w": w, "U0": U0, "B": B, "d": d, "prec": prec, "value": value, "steps": steps,
             "ms_per_step": tot_ms / steps, "step_ms": step_ms, "state_steps": ss, "state_steps_how": ss_how,
