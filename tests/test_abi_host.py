@@ -363,8 +363,8 @@ def test_noalloc_binding_refuses_short_arrays():
 
 def test_checkpoint_stride_sets_the_literal_footprint(lib):
     """ckpt_stride S: a literal sub-problem holds ceil(n_steps/S) states and S vectors H1 psi per (problem,
-    n), never its whole trajectory; the FP64 plan (literal form by default) grows accordingly, and the
-    mixed plan, whose first local steps store no states, holds neither unless L > 1.  Negative strides
+    n), never its whole trajectory; a plan whose first local steps run the two-trajectory form (the
+    default in both precisions) stores no states and holds neither unless L > 1.  Negative strides
     are refused."""
     import workloads as W
     from paper_1603_01237_gb300 import abi
