@@ -17,8 +17,8 @@
 // One CTA of max(n/8, 32) threads per state; the FFT is a radix-8 Stockham transform in shared memory
 // (element m at a swizzled position), its twiddles and the kinetic factors computed once per plan in
 // FP64 and held as hi + lo (FP32 pairs in mixed precision) in a global table.  Phase factors applied
-// at every step are held
-// as (factor - 1) and applied as v + (factor - 1) v, so their rounding is relative to the change.
+// at every step are held as (factor - 1) and applied as v + (factor - 1) v, so their rounding is
+// relative to the change.
 //   k_gp_forward   full forward sweep: psi(t_n) at the partition, a_j for every step, J and F;
 //   k_gp_adjoint   full adjoint sweep: chi(t_n) = lambda_{j_n}, the sub-problem targets;
 //   k_gp_sub       all sub-problems at once (grid N x B): forward from psi(t_n) storing a_j (skipped in
