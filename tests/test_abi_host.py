@@ -432,3 +432,18 @@ def test_grid_kind_checkpoints_size_the_plan(lib):
     n = C.c_size_t()
     prob, opt, keep = abi.problem_and_options(w, precision="fp64", ckpt_stride=-1)
     assert lib.ism_plan_footprint(C.byref(prob), C.byref(opt), C.byref(n)) == abi.ISM_EINVAL
+
+
+def test_fp64_first_local_steps_default_to_the_two_trajectory_form(lib):
+    """FP64 plans run a first local step in the two-trajectory form, as mixed ones do: the default
+    FP64 plan holds no literal checkpoints, and asking for the literal form (subproblem_form 1) or a
+    second local step adds them (one state every S steps and an S-step segment per (problem, n))."""
+    import workloads as W
+    from paper_1603_01237_gb300 import abi
+
+    w = W.config("rotor41")                       # Nt = 20000, N = 128
+    fp = lambda **kw: abi.footprint(w, batch=64, step1=2, precision="fp64", **kw)   # noqa: E731
+    default, two, literal, local2 = fp(), fp(subproblem_form=2), fp(subproblem_form=1), fp(local_iters=2)
+    assert default == two
+    assert literal > default and local2 > default
+    assert literal - default > 64 * 128 * 41 * 16   # at least one FP64 complex state per (problem, n)
